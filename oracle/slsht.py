@@ -42,9 +42,8 @@ def grid_angles(Na, Nb, Ng):
 # --------------------------------------------------------------------------
 
 class ModulatedSHT:
-    """k_{l m}(p, q) = conj((conj(f) Y_l^m)_p^q), p < Lh, |q| <= p.
-
-    Appendix A (Eq. sht_sep_variable) separates the variables:
+    """k_{l m}(p, q) = conj((conj(f) Y_l^m)_p^q), p < Lh, |q| <= p, by the
+    separation of variables of Appendix A (Eq. sht_sep_variable):
       (conj(f) Y_l^m)_p^q = N_l^m N_p^q int_0^pi P_l^m P_p^q I(theta, m-q) sin(theta) dtheta,
       I(theta, m-q) = int_0^{2pi} conj(f(theta, phi)) e^{i(m-q)phi} dphi.
     For a band-limited f given by its coefficients, I(theta, mu) is exactly
@@ -53,23 +52,20 @@ class ModulatedSHT:
     a polynomial in x = cos(theta) of degree l' + p + l, so Gauss-Legendre
     quadrature with enough nodes is exact.  Hence
       k_{lm}(p, q) = 2 pi sum_i w_i F_{m-q}(x_i) Ptilde_p^q(x_i) Ptilde_l^m(x_i).
-    Equivalently k = sum_l' f_{l',m-q} T(l', m-q; p, q; l, m), the form used in
-    Eq. harmonic_formulation; the tests pin one against the other with exact
-    3j symbols.
+    Only degrees with |l-p| <= l' <= l+p can contribute (the triangle rule of
+    the triple product), so F is summed over l' in [l-Lh+1, l+Lh-1]: the
+    exact value is unchanged and the cancellation of the rest of f's energy is
+    avoided.  Rounding of the oscillatory integrand still limits this route to
+    about 1e-11 relative at l ~ 255 (pinned in the tests); GauntCoefficients is
+    the exact route used by default.
     """
 
     def __init__(self, f, Lf, Lh, lmax_out):
-        f = np.asarray(f, dtype=np.complex128)
-        assert f.shape == (Lf * Lf,)
+        self.f = np.asarray(f, dtype=np.complex128)
+        assert self.f.shape == (Lf * Lf,)
         self.Lf, self.Lh = Lf, Lh
         deg = (Lf - 1) + (Lh - 1) + lmax_out
         self.x, self.w = special.gauss_legendre(deg // 2 + 1)
-        # F[mu + Lf - 1, i] = sum_l' f_{l' mu} Ptilde_l'^mu(x_i)
-        self.F = np.zeros((2 * Lf - 1, self.x.size), dtype=np.complex128)
-        for mu in range(-(Lf - 1), Lf):
-            p = special.plm(Lf - 1, mu, self.x)
-            ls = np.arange(abs(mu), Lf)
-            self.F[mu + Lf - 1] = f[ls * ls + ls + mu] @ p[abs(mu):]
         # Ptilde_p^q at the nodes, [Lh, 2Lh-1, nx]
         self.Pw = np.zeros((Lh, 2 * Lh - 1, self.x.size))
         for q in range(-(Lh - 1), Lh):
@@ -77,31 +73,56 @@ class ModulatedSHT:
 
     def coeffs(self, l, m):
         """k_{lm}(p, q) as an array [Lh, 2Lh-1] (entry [p, q+Lh-1], zero for |q|>p)."""
-        Lf, Lh = self.Lf, self.Lh
+        Lf, Lh, f = self.Lf, self.Lh, self.f
         plm_l = special.plm(l, m, self.x)[l]
+        lo, hi = max(0, l - (Lh - 1)), min(Lf - 1, l + Lh - 1)
         k = np.zeros((Lh, 2 * Lh - 1), dtype=np.complex128)
         for q in range(-(Lh - 1), Lh):
             mu = m - q
-            if abs(mu) > Lf - 1:
+            if abs(mu) > Lf - 1 or hi < max(abs(mu), lo):
                 continue
-            integrand = self.w * self.F[mu + Lf - 1] * plm_l      # [nx]
-            k[:, q + Lh - 1] = 2.0 * pi * (self.Pw[:, q + Lh - 1] @ integrand)
+            ls = np.arange(max(abs(mu), lo), hi + 1)
+            F = f[ls * ls + ls + mu] @ special.plm(hi, mu, self.x)[ls]     # F_mu, band only
+            k[:, q + Lh - 1] = 2.0 * pi * (self.Pw[:, q + Lh - 1] @ (self.w * F * plm_l))
         return k
+
+
+class GauntCoefficients:
+    """k_{lm}(p, q) = sum_l' f_{l', m-q} T(l', m-q; p, q; l, m) (Eq. harmonic_formulation,
+    the triple product T 'evaluated using Wigner-3j symbols', Sec. III-B), with
+    every T from exact rational 3j symbols (special.gaunt_exact); only the
+    final sum over at most Lh degrees l' is rounded.  The default source of
+    k in forward_coeff."""
+
+    def __init__(self, f, Lf, Lh, lmax_out=None):
+        self.f = np.asarray(f, dtype=np.complex128)
+        self.Lf, self.Lh = Lf, Lh
+
+    def coeffs(self, l, m):
+        return modulated_coeffs_gaunt(self.f, self.Lf, self.Lh, l, m)
 
 
 def modulated_coeffs_gaunt(f, Lf, Lh, l, m):
     """k_{lm}(p,q) = sum_l' f_{l',m-q} T(l',m-q; p,q; l,m) with T from exact
-    3j symbols (Eq. harmonic_formulation).  Slow; a pin for ModulatedSHT."""
+    3j symbols (Eq. harmonic_formulation and the Gaunt form of T):
+      T = (-1)^m sqrt((2l'+1)(2p+1)(2l+1)/(4 pi)) (l' p l; 0 0 0)(l' p l; m' q -m)."""
     k = np.zeros((Lh, 2 * Lh - 1), dtype=np.complex128)
+    w0 = {}
     for p in range(Lh):
         for q in range(-p, p + 1):
             mu = m - q
             acc = 0.0j
             for lp in range(max(abs(mu), abs(l - p)), min(Lf - 1, l + p) + 1):
-                t = special.gaunt_exact(lp, mu, p, q, l, m)
-                if t != 0.0:
-                    acc += f[lp * lp + lp + mu] * t
-            k[p, q + Lh - 1] = acc
+                if (lp + p + l) % 2:
+                    continue                      # (l' p l; 0 0 0) = 0
+                if (lp, p) not in w0:
+                    w0[(lp, p)] = special.wigner3j_exact(lp, p, l, 0, 0, 0)
+                w1 = special.wigner3j_exact(lp, p, l, mu, q, -m)
+                if w1 == 0.0:
+                    continue
+                t = sqrt((2 * lp + 1) * (2 * p + 1) * (2 * l + 1) / (4.0 * pi)) * w0[(lp, p)] * w1
+                acc += f[lp * lp + lp + mu] * t
+            k[p, q + Lh - 1] = (-1) ** (m % 2) * acc
     return k
 
 
@@ -118,13 +139,16 @@ def h_table(h, Lh):
     return out
 
 
-def forward_coeff(f, h, Lf, Lh, pairs, grid, beta_rows=None, msht=None, dtab=None):
+def forward_coeff(f, h, Lf, Lh, pairs, grid, beta_rows=None, msht=None, dtab=None,
+                  kroute="exact"):
     """g(rho; l, m) on the grid via the convolution form
       g = sum_p sum_q sum_q' k_{lm}(p,q) h_p^{q'} d^p_{q,q'}(beta) e^{-i q' gamma} e^{-i q alpha}
     (Eq. alternative_harmonic_formulation and ..._wigner, with
-    D^p_{q,q'} from Eq. Dlm), k from Appendix A (ModulatedSHT), d^p from the
-    degree recurrence (special.wigner_d_table).  The triple sum is done as
-    three library contractions (p, then q', then q); nothing else is reordered.
+    D^p_{q,q'} from Eq. Dlm), k from exact 3j symbols (GauntCoefficients,
+    kroute="exact") or from the Appendix A quadrature (ModulatedSHT,
+    kroute="quadrature"), d^p from the degree recurrence
+    (special.wigner_d_table).  The triple sum is done as three library
+    contractions (p, then q', then q); nothing else is reordered.
 
     pairs: iterable of (l, m).  grid: (Na, Nb, Ng).  beta_rows: optional
     subset of beta indices (returns only those rows).
@@ -143,14 +167,16 @@ def forward_coeff(f, h, Lf, Lh, pairs, grid, beta_rows=None, msht=None, dtab=Non
     ht = h_table(h, Lh)
     if msht is None:
         lmax = max(l for l, _ in pairs)
-        msht = ModulatedSHT(f, Lf, Lh, lmax)
-    out = np.zeros((len(pairs), Na, b.size, Ng), dtype=np.complex128)
+        msht = (GauntCoefficients if kroute == "exact" else ModulatedSHT)(f, Lf, Lh, lmax)
+    K = 2 * Lh - 1
+    nb = b.size
+    out = np.zeros((len(pairs), Na, nb, Ng), dtype=np.complex128)
     for i, (l, m) in enumerate(pairs):
         k = msht.coeffs(l, m)                                   # [Lh, K]
         kh = k[:, :, None] * ht[:, None, :]                      # [Lh, K(q), K(q')]
         G = np.einsum('pij,pijn->ijn', kh, dtab)                 # sum over p
-        X = np.einsum('ijn,jc->inc', G, Eg)                      # sum over q'
-        out[i] = np.einsum('inc,ia->anc', X, Ea)                 # sum over q
+        X = np.matmul(G.transpose(0, 2, 1), Eg)                  # sum over q': [q, n, c]
+        out[i] = (Ea.T @ X.reshape(K, nb * Ng)).reshape(Na, nb, Ng)   # sum over q
     return out
 
 

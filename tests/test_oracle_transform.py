@@ -62,6 +62,18 @@ def test_modulated_sht_vs_exact_gaunt():
         assert np.max(np.abs(k1 - k2)) < 1e-14, (l, m)
 
 
+def test_modulated_sht_accuracy_at_high_degree():
+    """At l = 255 (workload 3) the quadrature route of Appendix A stays within
+    its documented ~1e-11 of the exact-3j route the oracle uses by default."""
+    Lf, Lh = 256, 16
+    f = synth.signal_powerlaw(Lf, 3001)
+    ms = O.ModulatedSHT(f, Lf, Lh, 255)
+    for l, m in [(255, -1), (255, 255), (128, 3)]:
+        ke = O.modulated_coeffs_gaunt(f, Lf, Lh, l, m)
+        kq = ms.coeffs(l, m)
+        assert np.linalg.norm(kq - ke) / np.linalg.norm(ke) < 5e-11
+
+
 # ------------------------------------------------------ conventions
 
 def test_rotation_geometric_equals_wigner_D():
