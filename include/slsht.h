@@ -1,0 +1,230 @@
+/*
+ * slsht.h -- C ABI of libslsht, a GB300 (sm_103a) implementation of the
+ * directional spatially localised spherical harmonic transform (directional
+ * SLSHT) of Khalid, Kennedy, Durrani, Sadeghi, Wiaux and McEwen,
+ * arXiv:1207.5558.
+ *
+ * What is computed (Sec. III-A, Definition 1, Eq. stft_spatial): for a signal
+ * f and a window h on the sphere, given by spherical-harmonic coefficients,
+ *     g(rho; l, m) = int_{S^2} f(x) (D_rho h)(x) conj(Y_l^m(x)) ds(x),
+ * sampled on an equiangular grid of rotations rho = (alpha, beta, gamma)
+ * (Sec. II-D, the tessellation E_L, generalised to independent sizes):
+ *     alpha_a = 2 pi a / n_alpha,  beta_b = 2 pi b / (2 n_beta - 1),
+ *     gamma_c = 2 pi c / n_gamma.
+ * Rotations are zyz Euler angles acting as (D_rho h)(x) = h(R^{-1} x) with
+ * R = R_z(alpha) R_y(beta) R_z(gamma) (Sec. II-B, Eq. rotation_non_symm,
+ * Eq. Dlm).  The inverse recovers f_lm = fhat_lm / (sqrt(16 pi^3) h_0^0) with
+ * fhat_lm = int_SO(3) g(rho; l, m) drho (Sec. III-C, Eq. inversion_1,
+ * Eq. inversion_2, Eq. sig_reconstruction_discrete).
+ *
+ * Conventions shared by every entry point
+ *  - Band limits are EXCLUSIVE: f_lm = 0 for l >= L_f, h_pq = 0 for p >= L_h
+ *    (the paper's inclusive band limit is L - 1).  g(rho; l, m) is non-zero
+ *    only for l <= L_f + L_h - 2.
+ *  - Spherical harmonics carry the Condon-Shortley phase
+ *    (Y_l^{-m} = (-1)^m conj Y_l^m), Eq. Sph_harmonics.
+ *  - Coefficient vectors are complex128 stored as interleaved (re, im)
+ *    doubles, flat index l*l + l + m: f_lm has L_f*L_f entries, h_lm L_h*L_h.
+ *  - Pair lists are int32 [n_pairs][2] = (l, m), 0 <= l <= L_f + L_h - 2,
+ *    |m| <= l.
+ *  - g is laid out [pair][a][b][c] (gamma fastest, then beta, then alpha),
+ *    interleaved complex: complex128 for SLSHT_FP64, complex64 for
+ *    SLSHT_FP32_BULK.  One pair occupies n_alpha*n_beta*n_gamma samples.
+ *  - Memory spaces: every pointer argument may be host or device memory of
+ *    the context's device unless stated otherwise; the library detects which
+ *    (cudaPointerGetAttributes).  Host outputs are filled by stream-ordered
+ *    copies: synchronise the stream before reading them.
+ *  - The caller owns every buffer it passes; the context owns its cached
+ *    device tables and scratch.  Nothing is retained after a call returns.
+ *  - All work is issued on the caller's CUDA stream (cudaStream_t passed as
+ *    void*; NULL = legacy default stream) and is asynchronous: argument
+ *    validation happens before anything is enqueued and is synchronous.
+ *  - Errors: every int-returning call returns SLSHT_OK (0) or a negative
+ *    SLSHT_E_* code; slsht_strerror() describes it.  No exception crosses the
+ *    ABI.  On an error nothing has been enqueued unless the code is
+ *    SLSHT_E_CUDA (a CUDA call failed; the message of the last failure is
+ *    available from slsht_last_error()).
+ *  - There is no CPU fallback: every step of the transform runs in this
+ *    library's CUDA kernels.
+ */
+#ifndef SLSHT_H
+#define SLSHT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- codes */
+#define SLSHT_OK          0
+#define SLSHT_PENDING     1   /* slsht_poll: request admitted, not finished   */
+#define SLSHT_E_ARG      -1   /* invalid argument (sizes, indices, null)      */
+#define SLSHT_E_H00      -2   /* inverse with h_0^0 == 0 (Eq. inversion_2)    */
+#define SLSHT_E_NOMEM    -3   /* allocation failed or over the memory budget  */
+#define SLSHT_E_BUSY     -4   /* serving queue full; retry later              */
+#define SLSHT_E_TIMEOUT  -5   /* a bounded device-side wait gave up           */
+#define SLSHT_E_CUDA     -6   /* a CUDA runtime/driver call failed            */
+#define SLSHT_E_STATE    -7   /* unknown ticket / context misuse              */
+
+/* ---------------------------------------------------------------- types */
+typedef struct slsht_ctx slsht_ctx;   /* opaque; one device, owns tables */
+
+typedef enum {
+  SLSHT_FP64 = 0,       /* every stage in FP64; g is complex128            */
+  SLSHT_FP32_BULK = 1   /* 3j, Delta, phases in FP64; coupling in FP64;
+                           beta/gamma sums in FP32; alpha stage on tcgen05
+                           tensor cores (split-FP16 operands, FP32
+                           accumulate); g is complex64                      */
+} slsht_prec;
+
+typedef struct {
+  int32_t L_f;        /* signal band limit (exclusive), >= 1              */
+  int32_t L_h;        /* window band limit (exclusive), 1 <= L_h <= 64    */
+  int32_t n_alpha;    /* grid sizes, each >= 1                            */
+  int32_t n_beta;
+  int32_t n_gamma;
+  int32_t prec;       /* slsht_prec                                       */
+} slsht_desc;
+
+/* Per-stage device timings, filled when profiling is on (slsht_profile). */
+#define SLSHT_NSTAGES 8
+enum {
+  SLSHT_STAGE_TABLES = 0,  /* Delta recursion, d(beta) tables, phase tables */
+  SLSHT_STAGE_COUPLE = 1,  /* 3j chains + Gaunt coupling k_lm(p, q)         */
+  SLSHT_STAGE_CTENSOR = 2, /* C_{q,q',q''} tensor (factoring-of-rotations)  */
+  SLSHT_STAGE_BETA = 3,    /* beta and gamma sums                           */
+  SLSHT_STAGE_ALPHA = 4,   /* alpha sum and store of g                      */
+  SLSHT_STAGE_INVERSE = 5, /* SO(3) quadrature reduction                    */
+  SLSHT_STAGE_COPY = 6,    /* host<->device copies issued by the library    */
+  SLSHT_STAGE_OTHER = 7
+};
+typedef struct {
+  uint64_t launches[SLSHT_NSTAGES];  /* kernel launches (copies for COPY)   */
+  double   ms[SLSHT_NSTAGES];        /* summed device time, milliseconds    */
+  uint64_t samples_written;          /* g samples written by forward calls  */
+} slsht_stats;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`.  `mem_budget_bytes` caps the
+ * device memory the context may hold for tables and scratch (0 = 8 GiB).
+ * Returns SLSHT_E_ARG (ctx NULL / bad device), SLSHT_E_CUDA. */
+int slsht_create(slsht_ctx** ctx, int device, size_t mem_budget_bytes);
+
+/* Synchronise the context's own streams and free everything it owns.
+ * NULL is a no-op. */
+void slsht_destroy(slsht_ctx* ctx);
+
+/* ---------------------------------------------------------------- forward */
+
+/* g(rho; l, m) for every listed pair on the desc's grid (Definition 1,
+ * evaluated through the convolution form Eq. alternative_harmonic_formulation
+ * with Gaunt coupling, Wigner-d from the Delta = d(pi/2) recursion of
+ * Sec. IV-B and separable beta / gamma / alpha sums).
+ *   f_lm  complex128 [L_f*L_f]        (host or device)
+ *   h_lm  complex128 [L_h*L_h]        (host or device)
+ *   lm    int32 [n_pairs][2]          (host or device)
+ *   g_out [n_pairs][n_alpha][n_beta][n_gamma] complex128 (FP64) or complex64
+ *         (FP32_BULK), device or host, 8-byte aligned, caller-owned.
+ * n_pairs == 0 is valid and does nothing.  Errors: SLSHT_E_ARG (null ctx /
+ * desc / pointers, L_f < 1, L_h < 1 or > 64, a grid size < 1, unknown prec,
+ * l outside [0, L_f+L_h-2], |m| > l), SLSHT_E_NOMEM, SLSHT_E_CUDA. */
+int slsht_forward(slsht_ctx* ctx, const slsht_desc* desc,
+                  const double* f_lm, const double* h_lm,
+                  const int32_t* lm, int32_t n_pairs,
+                  void* g_out, void* stream);
+
+/* ---------------------------------------------------------------- inverse */
+
+/* f_lm for every listed pair from sampled g (Eq. inversion_1, inversion_2,
+ * with the exact SO(3) quadrature of Eq. sig_reconstruction_discrete
+ * generalised to the desc's grid):
+ *   f_lm = (2 pi/n_alpha)(2 pi/n_gamma) sum_{a,b,c} q_b g[a][b][c]
+ *          / (sqrt(16 pi^3) h_0^0),
+ * with q_b the beta weights of the printed w(m) rule.  Exact when the grid
+ * resolves the window: n_alpha, n_beta, n_gamma >= L_h.
+ *   g_in   device buffer laid out as slsht_forward's g_out (desc->prec
+ *          selects complex128 / complex64)
+ *   h00    host double[2], the window's (re, im) h_0^0
+ *   lm     int32 [n_pairs][2] (host or device; only used for validation)
+ *   f_out  complex128 [n_pairs] (host or device)
+ * Errors: SLSHT_E_ARG (as forward, plus a grid size < L_h, or g_in not in
+ * device memory), SLSHT_E_H00 (h_0^0 == 0), SLSHT_E_NOMEM, SLSHT_E_CUDA.
+ * The reduction order is fixed: results are bitwise reproducible. */
+int slsht_inverse(slsht_ctx* ctx, const slsht_desc* desc,
+                  const void* g_in, const double h00[2],
+                  const int32_t* lm, int32_t n_pairs,
+                  double* f_out, void* stream);
+
+/* ---------------------------------------------------------------- serving */
+
+/* Non-blocking forward request for a continuous-batching server.  The
+ * library copies f_lm, h_lm and lm before returning (host or device input);
+ * g_out must be DEVICE memory and stay valid until the request completes.
+ * Requests run on the context's own pool of streams, so requests that arrive
+ * while others are on the GPU overlap with them; each is admitted when its
+ * scratch fits the context's memory budget.  *ticket receives the request
+ * id.  Returns SLSHT_OK, SLSHT_E_BUSY (queue full), or the errors of
+ * slsht_forward (validation is synchronous). */
+int slsht_submit(slsht_ctx* ctx, const slsht_desc* desc,
+                 const double* f_lm, const double* h_lm,
+                 const int32_t* lm, int32_t n_pairs,
+                 void* g_out, uint64_t* ticket);
+
+/* SLSHT_OK if the request's g_out is complete (and device-visible),
+ * SLSHT_PENDING if not yet, or the request's error code.  A ticket can be
+ * polled until it has returned a final status once; then it is forgotten
+ * (SLSHT_E_STATE afterwards). */
+int slsht_poll(slsht_ctx* ctx, uint64_t ticket);
+
+/* Block until every submitted request has finished (bounded by timeout_ms;
+ * SLSHT_E_TIMEOUT if it expires). */
+int slsht_drain(slsht_ctx* ctx, int64_t timeout_ms);
+
+/* ---------------------------------------------------------------- tools */
+
+/* Human-readable text for a status code (static storage). */
+const char* slsht_strerror(int code);
+
+/* Text of the most recent SLSHT_E_CUDA failure in this process. */
+const char* slsht_last_error(void);
+
+/* Validate a descriptor and pair list without touching the GPU (host memory
+ * only).  Returns SLSHT_OK or SLSHT_E_ARG. */
+int slsht_check_args(const slsht_desc* desc, const int32_t* lm_host, int32_t n_pairs);
+
+/* Turn per-stage device timing on (1) or off (0).  While on, every kernel
+ * launch and library copy is bracketed by CUDA events on its stream. */
+int slsht_profile(slsht_ctx* ctx, int enable);
+
+/* Read (and with reset != 0 clear) the per-stage statistics.  Synchronises
+ * on the recorded events. */
+int slsht_get_stats(slsht_ctx* ctx, slsht_stats* out, int reset);
+
+/* Execution options of a context (defaults 0 = automatic):
+ *  SLSHT_OPT_BETA_ROUTE   1: beta sum from a table of d^p(beta_b) built from
+ *                            Delta (separation of variables, Sec. IV-B remark);
+ *                         2: factoring of rotations: C tensor
+ *                            (Eq. constant_alternative_formulation) + DFT in q''.
+ *  SLSHT_OPT_ALPHA_ENGINE 1: CUDA cores; 2: tcgen05 tensor cores (FP32_BULK
+ *                            only; L_h <= 32).
+ *  SLSHT_OPT_CHUNK_PAIRS  pairs per launch chunk (scratch size).
+ * Returns SLSHT_OK or SLSHT_E_ARG. */
+#define SLSHT_OPT_BETA_ROUTE   1
+#define SLSHT_OPT_ALPHA_ENGINE 2
+#define SLSHT_OPT_CHUNK_PAIRS  3
+int slsht_set_option(slsht_ctx* ctx, int option, int64_t value);
+
+/* Bytes of device memory the context currently holds. */
+size_t slsht_mem_used(slsht_ctx* ctx);
+
+/* Library version string. */
+const char* slsht_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SLSHT_H */

@@ -1,0 +1,195 @@
+"""GB300-native directional SLSHT (Khalid et al., arXiv:1207.5558).
+
+A thin Python layer over libslsht (include/slsht.h).  The functions keep the
+C names; ``Context`` bundles a context handle with convenience marshalling of
+torch tensors / numpy arrays.  PyTorch is used only for device memory and
+streams.  The CUDA library must be built (``__graft_entry__.build()``): there
+is no CPU fallback, and every call raises if the library is missing.
+"""
+import ctypes
+
+from . import _abi
+from ._abi import (SLSHT_FP32_BULK, SLSHT_FP64, SLSHT_OPT_ALPHA_ENGINE,  # noqa: F401
+                   SLSHT_OPT_BETA_ROUTE, SLSHT_OPT_CHUNK_PAIRS, SlshtError, STAGE_NAMES,
+                   slsht_desc, slsht_stats)
+
+__all__ = ["Context", "make_desc", "SLSHT_FP64", "SLSHT_FP32_BULK", "SlshtError",
+           "slsht_create", "slsht_destroy", "slsht_forward", "slsht_inverse", "slsht_submit",
+           "slsht_poll", "slsht_drain", "slsht_strerror", "slsht_check_args", "slsht_profile",
+           "slsht_get_stats", "slsht_set_option", "slsht_mem_used", "slsht_version"]
+
+
+def make_desc(L_f, L_h, grid, prec=SLSHT_FP64):
+    na, nb, ng = grid
+    return slsht_desc(int(L_f), int(L_h), int(na), int(nb), int(ng), int(prec))
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ------------------------------------------------------------ C-named calls
+def slsht_create(device=0, mem_budget_bytes=0):
+    lib = _abi.load()
+    h = ctypes.c_void_p()
+    _abi.check(lib.slsht_create(ctypes.byref(h), int(device), int(mem_budget_bytes)), "slsht_create")
+    return h
+
+
+def slsht_destroy(ctx):
+    _abi.load().slsht_destroy(ctx)
+
+
+def slsht_forward(ctx, desc, f_lm, h_lm, lm, n_pairs, g_out, stream=None):
+    return _abi.check(_abi.load().slsht_forward(ctx, ctypes.byref(desc), _abi.ptr(f_lm), _abi.ptr(h_lm),
+                                                _abi.ptr(lm), int(n_pairs), _abi.ptr(g_out),
+                                                _stream(stream)), "slsht_forward")
+
+
+def slsht_inverse(ctx, desc, g_in, h00, lm, n_pairs, f_out, stream=None):
+    hv = (ctypes.c_double * 2)(float(complex(h00).real), float(complex(h00).imag))
+    return _abi.check(_abi.load().slsht_inverse(ctx, ctypes.byref(desc), _abi.ptr(g_in), hv, _abi.ptr(lm),
+                                                int(n_pairs), _abi.ptr(f_out), _stream(stream)),
+                      "slsht_inverse")
+
+
+def slsht_submit(ctx, desc, f_lm, h_lm, lm, n_pairs, g_out):
+    t = ctypes.c_uint64()
+    _abi.check(_abi.load().slsht_submit(ctx, ctypes.byref(desc), _abi.ptr(f_lm), _abi.ptr(h_lm),
+                                        _abi.ptr(lm), int(n_pairs), _abi.ptr(g_out), ctypes.byref(t)),
+               "slsht_submit")
+    return t.value
+
+
+def slsht_poll(ctx, ticket):
+    return _abi.load().slsht_poll(ctx, ctypes.c_uint64(ticket))
+
+
+def slsht_drain(ctx, timeout_ms=60000):
+    return _abi.check(_abi.load().slsht_drain(ctx, int(timeout_ms)), "slsht_drain")
+
+
+def slsht_strerror(code):
+    return _abi.load().slsht_strerror(int(code)).decode()
+
+
+def slsht_check_args(desc, lm_host, n_pairs):
+    return _abi.load().slsht_check_args(ctypes.byref(desc), _abi.ptr(lm_host), int(n_pairs))
+
+
+def slsht_profile(ctx, enable):
+    return _abi.check(_abi.load().slsht_profile(ctx, int(bool(enable))), "slsht_profile")
+
+
+def slsht_get_stats(ctx, reset=False):
+    s = slsht_stats()
+    _abi.check(_abi.load().slsht_get_stats(ctx, ctypes.byref(s), int(bool(reset))), "slsht_get_stats")
+    return {"launches": {n: int(s.launches[i]) for i, n in enumerate(STAGE_NAMES)},
+            "ms": {n: float(s.ms[i]) for i, n in enumerate(STAGE_NAMES)},
+            "samples_written": int(s.samples_written)}
+
+
+def slsht_set_option(ctx, option, value):
+    return _abi.check(_abi.load().slsht_set_option(ctx, int(option), int(value)), "slsht_set_option")
+
+
+def slsht_mem_used(ctx):
+    return int(_abi.load().slsht_mem_used(ctx))
+
+
+def slsht_version():
+    return _abi.load().slsht_version().decode()
+
+
+# ------------------------------------------------------------ convenience
+class Context:
+    """One libslsht context on one CUDA device."""
+
+    def __init__(self, device=0, mem_budget_bytes=0):
+        self.device = device
+        self.h = slsht_create(device, mem_budget_bytes)
+
+    def close(self):
+        if self.h is not None:
+            slsht_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_option(self, option, value):
+        slsht_set_option(self.h, option, value)
+
+    def forward(self, L_f, L_h, grid, f, h, lm, prec=SLSHT_FP64, g_out=None, stream=None):
+        """g(rho; l, m) for the pairs in lm ([n, 2] int32).  f, h: complex128
+        (numpy on the host or torch on the device).  Returns g_out (a new
+        torch tensor [n, Na, Nb, Ng] on the device when not given)."""
+        import numpy as np
+        import torch
+        lm = _as_pairs(lm)
+        n = int(lm.shape[0])
+        if g_out is None:
+            dt = torch.complex128 if prec == SLSHT_FP64 else torch.complex64
+            g_out = torch.empty((n,) + tuple(grid), dtype=dt, device="cuda:%d" % self.device)
+        f = _as_c128(f)
+        h = _as_c128(h)
+        slsht_forward(self.h, make_desc(L_f, L_h, grid, prec), f, h, lm, n, g_out, stream)
+        _ = np
+        return g_out
+
+    def inverse(self, L_f, L_h, grid, g, h00, lm, prec=SLSHT_FP64, f_out=None, stream=None):
+        """f_lm for each pair from g (device tensor).  Returns a host numpy
+        complex128 array unless f_out is given."""
+        import numpy as np
+        lm = _as_pairs(lm)
+        n = int(lm.shape[0])
+        host = f_out is None
+        if host:
+            f_out = np.zeros(n, dtype=np.complex128)
+        slsht_inverse(self.h, make_desc(L_f, L_h, grid, prec), g, h00, lm, n, f_out, stream)
+        if host:
+            import torch
+            torch.cuda.synchronize(self.device)
+        return f_out
+
+    def submit(self, L_f, L_h, grid, f, h, lm, g_out, prec=SLSHT_FP64):
+        lm = _as_pairs(lm)
+        return slsht_submit(self.h, make_desc(L_f, L_h, grid, prec), _as_c128(f), _as_c128(h), lm,
+                            int(lm.shape[0]), g_out)
+
+    def poll(self, ticket):
+        return slsht_poll(self.h, ticket)
+
+    def drain(self, timeout_ms=60000):
+        return slsht_drain(self.h, timeout_ms)
+
+    def profile(self, enable=True):
+        slsht_profile(self.h, enable)
+
+    def stats(self, reset=False):
+        return slsht_get_stats(self.h, reset)
+
+    def mem_used(self):
+        return slsht_mem_used(self.h)
+
+
+def _as_pairs(lm):
+    import numpy as np
+    if hasattr(lm, "data_ptr") and getattr(lm, "is_cuda", False):
+        return lm
+    return np.ascontiguousarray(np.asarray(lm, dtype=np.int32).reshape(-1, 2))
+
+
+def _as_c128(x):
+    import numpy as np
+    if hasattr(x, "data_ptr"):
+        return x.contiguous()
+    return np.ascontiguousarray(np.asarray(x, dtype=np.complex128))

@@ -1,0 +1,920 @@
+// libslsht host side: the C ABI of include/slsht.h.
+//
+// Owns: argument validation, the per-context caches of device tables (Delta,
+// d(beta) tables, phase tables, beta weights), scratch workspaces, the chunked
+// launch sequence of the forward transform, the inverse, per-stage profiling
+// and the continuous-batching request scheduler behind slsht_submit/poll.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <tuple>
+#include <vector>
+
+#include "../../include/slsht.h"
+#include "common.cuh"
+#include "tc.cuh"
+
+// ---------------------------------------------------------------- errors
+static std::mutex g_err_mu;
+static std::string g_last_err = "no CUDA error recorded";
+
+static void record_cuda_error(const char* what, cudaError_t e) {
+  std::lock_guard<std::mutex> g(g_err_mu);
+  g_last_err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+}
+
+#define CK(call)                                     \
+  do {                                               \
+    cudaError_t _e = (call);                         \
+    if (_e != cudaSuccess) {                         \
+      record_cuda_error(#call, _e);                  \
+      return SLSHT_E_CUDA;                           \
+    }                                                \
+  } while (0)
+
+#define CKS(call)                                    \
+  do {                                               \
+    int _s = (call);                                 \
+    if (_s != SLSHT_OK) return _s;                   \
+  } while (0)
+
+// ---------------------------------------------------------------- validation
+static int check_desc(const slsht_desc* d) {
+  if (!d) return SLSHT_E_ARG;
+  if (d->L_f < 1 || d->L_h < 1 || d->L_h > SLSHT_MAX_LH) return SLSHT_E_ARG;
+  if (d->L_f > 1 << 15) return SLSHT_E_ARG;
+  if (d->n_alpha < 1 || d->n_beta < 1 || d->n_gamma < 1) return SLSHT_E_ARG;
+  if (d->n_beta > 65535) return SLSHT_E_ARG;   // beta rows index a grid dimension
+  if ((long long)d->n_beta * d->n_gamma > (1LL << 30)) return SLSHT_E_ARG;
+  if (d->prec != SLSHT_FP64 && d->prec != SLSHT_FP32_BULK) return SLSHT_E_ARG;
+  return SLSHT_OK;
+}
+
+static int check_pairs(const slsht_desc* d, const int32_t* lm, int32_t n) {
+  if (n < 0) return SLSHT_E_ARG;
+  if (n > 0 && !lm) return SLSHT_E_ARG;
+  const int lmax = d->L_f + d->L_h - 2;
+  for (int32_t i = 0; i < n; ++i) {
+    const int l = lm[2 * i], m = lm[2 * i + 1];
+    if (l < 0 || l > lmax || m < -l || m > l) return SLSHT_E_ARG;
+  }
+  return SLSHT_OK;
+}
+
+extern "C" int slsht_check_args(const slsht_desc* desc, const int32_t* lm_host, int32_t n_pairs) {
+  CKS(check_desc(desc));
+  return check_pairs(desc, lm_host, n_pairs);
+}
+
+static bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// ---------------------------------------------------------------- context
+struct TableEntry {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  cudaEvent_t ready = nullptr;   // recorded after the generating kernels
+};
+
+struct ProfRec {
+  int stage;
+  cudaEvent_t a, b;
+};
+
+struct Workspace {
+  // device scratch, grow-only
+  void* f = nullptr; size_t f_cap = 0;
+  void* h = nullptr; size_t h_cap = 0;
+  void* lm = nullptr; size_t lm_cap = 0;
+  void* kc = nullptr; size_t kc_cap = 0;
+  void* X = nullptr; size_t X_cap = 0;
+  void* C = nullptr; size_t C_cap = 0;
+  void* Y = nullptr; size_t Y_cap = 0;
+  void* stage[2] = {nullptr, nullptr}; size_t stage_cap[2] = {0, 0};
+  cudaEvent_t done = nullptr;          // last use of this workspace
+  cudaEvent_t stage_ev[2] = {nullptr, nullptr};
+  cudaEvent_t copy_ev[2] = {nullptr, nullptr};
+  cudaStream_t copy_stream = nullptr;  // D2H of host outputs
+  size_t bytes = 0;
+};
+
+struct Request {
+  uint64_t id = 0;
+  slsht_desc desc{};
+  std::vector<double> f, h;
+  std::vector<int32_t> lm;
+  void* g_out = nullptr;
+};
+
+struct Slot {
+  cudaStream_t stream = nullptr;
+  Workspace ws;
+  std::unique_ptr<Request> req;
+  cudaEvent_t fin = nullptr;
+  bool busy = false;
+};
+
+#define SERVE_SLOTS 4
+#define SERVE_MAX_QUEUE 4096
+
+struct slsht_ctx {
+  int device = 0;
+  size_t budget = 0;
+  std::atomic<size_t> used{0};
+  std::mutex mu;                       // caches, profile records, counters
+  std::mutex sync_mu;                  // serialises users of sync_ws
+  std::map<int, TableEntry> delta;                                  // Lh
+  std::map<std::tuple<int, int, int>, TableEntry> dtab;             // Lh, Nb, prec
+  std::map<std::tuple<int, int, int, int>, TableEntry> phase;       // N, R, r0, prec
+  std::map<int, TableEntry> wbeta;                                  // Nb
+  std::map<std::tuple<int, int>, TableEntry> etab;                  // Na, Lh (tensor-core E blobs)
+  Workspace sync_ws;
+  int opt_beta_route = 0, opt_alpha_engine = 0;
+  int64_t opt_chunk = 0;
+  bool profile = false;
+  std::vector<ProfRec> prof;
+  std::vector<cudaEvent_t> ev_pool;
+  uint64_t launches[SLSHT_NSTAGES] = {0};
+  double prof_ms[SLSHT_NSTAGES] = {0};
+  uint64_t samples = 0;
+  int num_sms = 148;
+  // serving
+  std::mutex smu;
+  std::condition_variable scv;
+  std::deque<std::unique_ptr<Request>> queue;
+  std::map<uint64_t, int> status;      // final or pending status per ticket
+  Slot slots[SERVE_SLOTS];
+  std::thread worker;
+  bool stop = false, worker_started = false;
+  uint64_t next_id = 1;
+  int inflight = 0;
+};
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) { cudaGetLastError(); prev = -1; }
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+static int ctx_alloc(slsht_ctx* c, size_t bytes, void** out) {
+  *out = nullptr;
+  if (bytes == 0) return SLSHT_OK;
+  size_t cur = c->used.load();
+  if (cur + bytes > c->budget) return SLSHT_E_NOMEM;
+  cudaError_t e = cudaMalloc(out, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *out = nullptr;
+    record_cuda_error("cudaMalloc", e);
+    return SLSHT_E_NOMEM;
+  }
+  c->used += bytes;
+  return SLSHT_OK;
+}
+
+static void ctx_free(slsht_ctx* c, void* p, size_t bytes) {
+  if (!p) return;
+  cudaFree(p);
+  c->used -= bytes;
+}
+
+// grow-only scratch buffer
+static int ws_reserve(slsht_ctx* c, Workspace& w, void** buf, size_t* cap, size_t need) {
+  if (need <= *cap) return SLSHT_OK;
+  if (*buf) {
+    // the previous user of this workspace may still be running
+    cudaEventSynchronize(w.done);
+    ctx_free(c, *buf, *cap);
+    w.bytes -= *cap;
+    *buf = nullptr;
+    *cap = 0;
+  }
+  size_t alloc = need + need / 8;
+  CKS(ctx_alloc(c, alloc, buf));
+  *cap = alloc;
+  w.bytes += alloc;
+  return SLSHT_OK;
+}
+
+static int ws_init(Workspace& w) {
+  if (!w.done) {
+    CK(cudaEventCreateWithFlags(&w.done, cudaEventDisableTiming));
+    CK(cudaEventRecord(w.done, 0));
+  }
+  return SLSHT_OK;
+}
+
+static int ws_init_copy(Workspace& w) {
+  if (!w.copy_stream) {
+    CK(cudaStreamCreateWithFlags(&w.copy_stream, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; ++i) {
+      CK(cudaEventCreateWithFlags(&w.stage_ev[i], cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&w.copy_ev[i], cudaEventDisableTiming));
+      CK(cudaEventRecord(w.copy_ev[i], w.copy_stream));
+    }
+  }
+  return SLSHT_OK;
+}
+
+static void ws_release(slsht_ctx* c, Workspace& w) {
+  if (w.done) cudaEventSynchronize(w.done);
+  if (w.copy_stream) cudaStreamSynchronize(w.copy_stream);
+  ctx_free(c, w.f, w.f_cap);
+  ctx_free(c, w.h, w.h_cap);
+  ctx_free(c, w.lm, w.lm_cap);
+  ctx_free(c, w.kc, w.kc_cap);
+  ctx_free(c, w.X, w.X_cap);
+  ctx_free(c, w.C, w.C_cap);
+  ctx_free(c, w.Y, w.Y_cap);
+  for (int i = 0; i < 2; ++i) ctx_free(c, w.stage[i], w.stage_cap[i]);
+  for (int i = 0; i < 2; ++i) {
+    if (w.stage_ev[i]) cudaEventDestroy(w.stage_ev[i]);
+    if (w.copy_ev[i]) cudaEventDestroy(w.copy_ev[i]);
+  }
+  if (w.copy_stream) cudaStreamDestroy(w.copy_stream);
+  if (w.done) cudaEventDestroy(w.done);
+  w = Workspace();
+}
+
+// ---------------------------------------------------------------- profiling
+static cudaEvent_t pool_event(slsht_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Brackets one launch with timing events when profiling is on; counts it always.
+struct StageTimer {
+  slsht_ctx* c;
+  int stage;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  StageTimer(slsht_ctx* c_, int stage_, cudaStream_t st_) : c(c_), stage(stage_), st(st_) {
+    std::lock_guard<std::mutex> g(c->mu);
+    c->launches[stage]++;
+    if (c->profile) {
+      a = pool_event(c);
+      if (a) cudaEventRecord(a, st);
+    }
+  }
+  ~StageTimer() {
+    if (!a) return;
+    std::lock_guard<std::mutex> g(c->mu);
+    cudaEvent_t b = pool_event(c);
+    if (!b) return;
+    cudaEventRecord(b, st);
+    c->prof.push_back({stage, a, b});
+  }
+};
+
+#define LAUNCH(stage, st, call)                      \
+  do {                                               \
+    StageTimer _t(ctx, stage, st);                   \
+    cudaError_t _e = (call);                         \
+    if (_e != cudaSuccess) {                         \
+      record_cuda_error(#call, _e);                  \
+      return SLSHT_E_CUDA;                           \
+    }                                                \
+  } while (0)
+
+// ---------------------------------------------------------------- tables
+static int make_entry(slsht_ctx* c, TableEntry& e, size_t bytes) {
+  CKS(ctx_alloc(c, bytes, &e.ptr));
+  e.bytes = bytes;
+  CK(cudaEventCreateWithFlags(&e.ready, cudaEventDisableTiming));
+  return SLSHT_OK;
+}
+
+// All table getters run under ctx->mu; they enqueue generation on `st` on a
+// miss and make `st` wait for the table in any case.
+static int get_delta(slsht_ctx* ctx, int Lh, cudaStream_t st, const double** out) {
+  auto it = ctx->delta.find(Lh);
+  if (it == ctx->delta.end()) {
+    TableEntry e;
+    CKS(make_entry(ctx, e, sizeof(double) * (size_t)blk_off(Lh)));
+    {
+      ctx->launches[SLSHT_STAGE_TABLES]++;
+      cudaError_t er = launch_delta((double*)e.ptr, Lh, st);
+      if (er != cudaSuccess) { record_cuda_error("launch_delta", er); return SLSHT_E_CUDA; }
+    }
+    CK(cudaEventRecord(e.ready, st));
+    it = ctx->delta.emplace(Lh, e).first;
+  }
+  CK(cudaStreamWaitEvent(st, it->second.ready, 0));
+  *out = (const double*)it->second.ptr;
+  return SLSHT_OK;
+}
+
+static int get_dtab(slsht_ctx* ctx, int Lh, int Nb, int prec, cudaStream_t st, const void** out) {
+  auto key = std::make_tuple(Lh, Nb, prec);
+  auto it = ctx->dtab.find(key);
+  if (it == ctx->dtab.end()) {
+    const double* D;
+    CKS(get_delta(ctx, Lh, st, &D));
+    TableEntry e;
+    const size_t el = prec == SLSHT_FP64 ? sizeof(double) : sizeof(float);
+    CKS(make_entry(ctx, e, el * (size_t)blk_off(Lh) * Nb));
+    ctx->launches[SLSHT_STAGE_TABLES]++;
+    cudaError_t er = prec == SLSHT_FP64 ? launch_dtable_f64(D, (double*)e.ptr, Lh, Nb, st)
+                                        : launch_dtable_f32(D, (float*)e.ptr, Lh, Nb, st);
+    if (er != cudaSuccess) { record_cuda_error("launch_dtable", er); return SLSHT_E_CUDA; }
+    CK(cudaEventRecord(e.ready, st));
+    it = ctx->dtab.emplace(key, e).first;
+  }
+  CK(cudaStreamWaitEvent(st, it->second.ready, 0));
+  *out = it->second.ptr;
+  return SLSHT_OK;
+}
+
+static int get_phase(slsht_ctx* ctx, int N, int R, int r0, int prec, cudaStream_t st, const void** out) {
+  auto key = std::make_tuple(N, R, r0, prec);
+  auto it = ctx->phase.find(key);
+  if (it == ctx->phase.end()) {
+    TableEntry e;
+    const size_t el = prec == SLSHT_FP64 ? sizeof(double2) : sizeof(float2);
+    CKS(make_entry(ctx, e, el * (size_t)N * R));
+    ctx->launches[SLSHT_STAGE_TABLES]++;
+    cudaError_t er = prec == SLSHT_FP64 ? launch_phase_f64((double2*)e.ptr, N, R, r0, st)
+                                        : launch_phase_f32((float2*)e.ptr, N, R, r0, st);
+    if (er != cudaSuccess) { record_cuda_error("launch_phase", er); return SLSHT_E_CUDA; }
+    CK(cudaEventRecord(e.ready, st));
+    it = ctx->phase.emplace(key, e).first;
+  }
+  CK(cudaStreamWaitEvent(st, it->second.ready, 0));
+  *out = it->second.ptr;
+  return SLSHT_OK;
+}
+
+static int get_wbeta(slsht_ctx* ctx, int Nb, cudaStream_t st, const double** out) {
+  auto it = ctx->wbeta.find(Nb);
+  if (it == ctx->wbeta.end()) {
+    TableEntry e;
+    CKS(make_entry(ctx, e, sizeof(double) * (size_t)Nb));
+    ctx->launches[SLSHT_STAGE_TABLES]++;
+    cudaError_t er = launch_beta_weights((double*)e.ptr, Nb, st);
+    if (er != cudaSuccess) { record_cuda_error("launch_beta_weights", er); return SLSHT_E_CUDA; }
+    CK(cudaEventRecord(e.ready, st));
+    it = ctx->wbeta.emplace(Nb, e).first;
+  }
+  CK(cudaStreamWaitEvent(st, it->second.ready, 0));
+  *out = (const double*)it->second.ptr;
+  return SLSHT_OK;
+}
+
+static int get_etab(slsht_ctx* ctx, int Na, int Lh, cudaStream_t st, const void** out) {
+  auto key = std::make_tuple(Na, Lh);
+  auto it = ctx->etab.find(key);
+  if (it == ctx->etab.end()) {
+    TableEntry e;
+    CKS(make_entry(ctx, e, tc_etab_bytes(Na, Lh)));
+    ctx->launches[SLSHT_STAGE_TABLES]++;
+    cudaError_t er = launch_tc_etab(e.ptr, Na, Lh, st);
+    if (er != cudaSuccess) { record_cuda_error("launch_tc_etab", er); return SLSHT_E_CUDA; }
+    CK(cudaEventRecord(e.ready, st));
+    it = ctx->etab.emplace(key, e).first;
+  }
+  CK(cudaStreamWaitEvent(st, it->second.ready, 0));
+  *out = it->second.ptr;
+  return SLSHT_OK;
+}
+
+// ---------------------------------------------------------------- create/destroy
+extern "C" int slsht_create(slsht_ctx** out, int device, size_t budget) {
+  if (!out) return SLSHT_E_ARG;
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess) { record_cuda_error("cudaGetDeviceCount", e); cudaGetLastError(); return SLSHT_E_CUDA; }
+  if (device < 0 || device >= n) return SLSHT_E_ARG;
+  DeviceGuard g(device);
+  CK(cudaFree(0));   // create / bind the primary context
+  slsht_ctx* c = new slsht_ctx();
+  c->device = device;
+  c->budget = budget ? budget : ((size_t)8 << 30);
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  int s = ws_init(c->sync_ws);
+  if (s != SLSHT_OK) { delete c; return s; }
+  *out = c;
+  return SLSHT_OK;
+}
+
+static void free_entry(slsht_ctx* c, TableEntry& e) {
+  ctx_free(c, e.ptr, e.bytes);
+  if (e.ready) cudaEventDestroy(e.ready);
+}
+
+extern "C" void slsht_destroy(slsht_ctx* c) {
+  if (!c) return;
+  DeviceGuard g(c->device);
+  {
+    std::unique_lock<std::mutex> l(c->smu);
+    c->stop = true;
+  }
+  c->scv.notify_all();
+  if (c->worker.joinable()) c->worker.join();
+  for (auto& s : c->slots) {
+    if (s.stream) cudaStreamSynchronize(s.stream);
+    ws_release(c, s.ws);
+    if (s.fin) cudaEventDestroy(s.fin);
+    if (s.stream) cudaStreamDestroy(s.stream);
+  }
+  ws_release(c, c->sync_ws);
+  for (auto& kv : c->delta) free_entry(c, kv.second);
+  for (auto& kv : c->dtab) free_entry(c, kv.second);
+  for (auto& kv : c->phase) free_entry(c, kv.second);
+  for (auto& kv : c->wbeta) free_entry(c, kv.second);
+  for (auto& kv : c->etab) free_entry(c, kv.second);
+  for (auto& r : c->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
+  delete c;
+}
+
+extern "C" int slsht_set_option(slsht_ctx* c, int option, int64_t v) {
+  if (!c) return SLSHT_E_ARG;
+  std::lock_guard<std::mutex> g(c->mu);
+  switch (option) {
+    case SLSHT_OPT_BETA_ROUTE:
+      if (v < 0 || v > 2) return SLSHT_E_ARG;
+      c->opt_beta_route = (int)v;
+      return SLSHT_OK;
+    case SLSHT_OPT_ALPHA_ENGINE:
+      if (v < 0 || v > 2) return SLSHT_E_ARG;
+      c->opt_alpha_engine = (int)v;
+      return SLSHT_OK;
+    case SLSHT_OPT_CHUNK_PAIRS:
+      if (v < 0 || v > (1 << 20)) return SLSHT_E_ARG;
+      c->opt_chunk = v;
+      return SLSHT_OK;
+    default:
+      return SLSHT_E_ARG;
+  }
+}
+
+// ---------------------------------------------------------------- forward
+// Copies (or aliases) an input array to device memory of the workspace.
+static int stage_input(slsht_ctx* ctx, Workspace& w, void** buf, size_t* cap, const void* src,
+                       size_t bytes, cudaStream_t st, const void** dev) {
+  if (is_device_ptr(src)) {
+    *dev = src;
+    return SLSHT_OK;
+  }
+  CKS(ws_reserve(ctx, w, buf, cap, bytes));
+  {
+    StageTimer t(ctx, SLSHT_STAGE_COPY, st);
+    CK(cudaMemcpyAsync(*buf, src, bytes, cudaMemcpyHostToDevice, st));
+  }
+  *dev = *buf;
+  return SLSHT_OK;
+}
+
+static bool use_tensor_cores(slsht_ctx* ctx, const slsht_desc* d) {
+  if (d->prec != SLSHT_FP32_BULK) return false;
+  if (!tc_supported(d->L_h, d->n_alpha)) return false;
+  if (ctx->opt_alpha_engine == 1) return false;
+  return true;   // default for FP32_BULK when supported
+}
+
+// The forward transform on workspace `w` and stream `st` (ctx->mu NOT held).
+static int forward_impl(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const double* f_lm,
+                        const double* h_lm, const int32_t* lm, int32_t n_pairs, void* g_out,
+                        cudaStream_t st) {
+  const int Lf = d->L_f, Lh = d->L_h, Na = d->n_alpha, Nb = d->n_beta, Ng = d->n_gamma;
+  const int K = 2 * Lh - 1;
+  const bool f64 = d->prec == SLSHT_FP64;
+  const size_t J = (size_t)Nb * Ng;
+  const size_t per_pair_g = (size_t)Na * J * (f64 ? sizeof(double2) : sizeof(float2));
+  const bool host_out = !is_device_ptr(g_out);
+  CK(cudaStreamWaitEvent(st, w.done, 0));
+
+  int route, tc;
+  int64_t chunk_opt;
+  {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    route = ctx->opt_beta_route ? ctx->opt_beta_route : 1;
+    tc = use_tensor_cores(ctx, d) ? 1 : 0;
+    chunk_opt = ctx->opt_chunk;
+  }
+  // tables
+  const double* D = nullptr;
+  const void* dt = nullptr;
+  const void* csa = nullptr;
+  const void* eg = nullptr;
+  const void* etab = nullptr;
+  {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    CKS(get_delta(ctx, Lh, st, &D));
+    if (route == 1) CKS(get_dtab(ctx, Lh, Nb, d->prec, st, &dt));
+    CKS(get_phase(ctx, Ng, K, -(Lh - 1), d->prec, st, &eg));
+    if (tc) CKS(get_etab(ctx, Na, Lh, st, &etab));
+    else CKS(get_phase(ctx, Na, Lh, 0, d->prec, st, &csa));
+  }
+  // inputs
+  const void *f_dev, *h_dev, *lm_dev;
+  CKS(stage_input(ctx, w, &w.f, &w.f_cap, f_lm, sizeof(double2) * (size_t)Lf * Lf, st, &f_dev));
+  CKS(stage_input(ctx, w, &w.h, &w.h_cap, h_lm, sizeof(double2) * (size_t)Lh * Lh, st, &h_dev));
+  CKS(stage_input(ctx, w, &w.lm, &w.lm_cap, lm, sizeof(int2) * (size_t)n_pairs, st, &lm_dev));
+
+  // chunking: X scratch of the chunk kept near L2 size
+  const size_t x_per_pair = tc ? tc_xblob_bytes(Nb, Ng, Lh) : (size_t)K * J * (f64 ? sizeof(double2) : sizeof(float2));
+  int P;
+  if (chunk_opt > 0) {
+    P = (int)std::min<int64_t>(chunk_opt, n_pairs);
+  } else {
+    const size_t target = (size_t)96 << 20;
+    P = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_pairs, target / std::max<size_t>(1, x_per_pair)));
+    P = std::min(P, 256);
+  }
+  if (host_out) {
+    // staging buffers for the chunk outputs (double-buffered, D2H on the copy stream)
+    const size_t stage_limit = (size_t)1 << 30;
+    P = (int)std::max<size_t>(1, std::min<size_t>((size_t)P, stage_limit / std::max<size_t>(1, per_pair_g)));
+  }
+  CKS(ws_reserve(ctx, w, &w.kc, &w.kc_cap, sizeof(double2) * (size_t)P * Lh * Lh));
+  CKS(ws_reserve(ctx, w, &w.X, &w.X_cap, x_per_pair * (size_t)P));
+  if (route == 2) {
+    CKS(ws_reserve(ctx, w, &w.C, &w.C_cap, sizeof(double2) * (size_t)P * K * K * K));
+    CKS(ws_reserve(ctx, w, &w.Y, &w.Y_cap, sizeof(double2) * (size_t)P * Nb * K * K));
+  }
+  if (host_out) {
+    CKS(ws_init_copy(w));
+    for (int i = 0; i < 2; ++i) CKS(ws_reserve(ctx, w, &w.stage[i], &w.stage_cap[i], per_pair_g * (size_t)P));
+  }
+
+  int ci = 0;
+  for (int32_t off = 0; off < n_pairs; off += P, ++ci) {
+    const int np = std::min<int>(P, n_pairs - off);
+    const int2* lmc = (const int2*)lm_dev + off;
+    void* gdst;
+    if (host_out) {
+      CK(cudaStreamWaitEvent(st, w.copy_ev[ci & 1], 0));   // staging buffer free again
+      gdst = w.stage[ci & 1];
+    } else {
+      gdst = (char*)g_out + per_pair_g * (size_t)off;
+    }
+    LAUNCH(SLSHT_STAGE_COUPLE, st,
+           launch_couple((const double2*)f_dev, Lf, Lh, lmc, np, (double2*)w.kc, st));
+    if (route == 2) {
+      LAUNCH(SLSHT_STAGE_CTENSOR, st,
+             launch_ctensor((const double2*)w.kc, (const double2*)h_dev, D, Lh, np, (double2*)w.C, st));
+      LAUNCH(SLSHT_STAGE_CTENSOR, st, launch_beta_dft((const double2*)w.C, Lh, Nb, np, (double2*)w.Y, st));
+    }
+    const double2* Ysrc = route == 2 ? (const double2*)w.Y : nullptr;
+    if (tc) {
+      LAUNCH(SLSHT_STAGE_BETA, st,
+             launch_betagamma_tc((const double2*)w.kc, (const double2*)h_dev, (const float*)dt, Ysrc,
+                                 (const float2*)eg, Lh, Nb, Ng, np, w.X, st));
+      LAUNCH(SLSHT_STAGE_ALPHA, st,
+             launch_alpha_tc(w.X, etab, Lh, Na, Nb, Ng, np, (float2*)gdst, ctx->num_sms, st));
+    } else if (f64) {
+      LAUNCH(SLSHT_STAGE_BETA, st,
+             launch_betagamma_f64((const double2*)w.kc, (const double2*)h_dev, (const double*)dt, Ysrc,
+                                  (const double2*)eg, Lh, Nb, Ng, np, (double2*)w.X, st));
+      LAUNCH(SLSHT_STAGE_ALPHA, st,
+             launch_alpha_f64((const double2*)w.X, (const double2*)csa, Lh, Na, (int)J, np,
+                              (double2*)gdst, st));
+    } else {
+      LAUNCH(SLSHT_STAGE_BETA, st,
+             launch_betagamma_f32((const double2*)w.kc, (const double2*)h_dev, (const float*)dt, Ysrc,
+                                  (const float2*)eg, Lh, Nb, Ng, np, (float2*)w.X, st));
+      LAUNCH(SLSHT_STAGE_ALPHA, st,
+             launch_alpha_f32((const float2*)w.X, (const float2*)csa, Lh, Na, (int)J, np,
+                              (float2*)gdst, st));
+    }
+    if (host_out) {
+      CK(cudaEventRecord(w.stage_ev[ci & 1], st));
+      CK(cudaStreamWaitEvent(w.copy_stream, w.stage_ev[ci & 1], 0));
+      {
+        StageTimer t(ctx, SLSHT_STAGE_COPY, w.copy_stream);
+        CK(cudaMemcpyAsync((char*)g_out + per_pair_g * (size_t)off, gdst, per_pair_g * (size_t)np,
+                           cudaMemcpyDeviceToHost, w.copy_stream));
+      }
+      CK(cudaEventRecord(w.copy_ev[ci & 1], w.copy_stream));
+    }
+  }
+  if (host_out) {
+    CK(cudaStreamWaitEvent(st, w.copy_ev[0], 0));
+    CK(cudaStreamWaitEvent(st, w.copy_ev[1], 0));
+  }
+  CK(cudaEventRecord(w.done, st));
+  {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    ctx->samples += (uint64_t)n_pairs * (uint64_t)Na * J;
+  }
+  return SLSHT_OK;
+}
+
+extern "C" int slsht_forward(slsht_ctx* ctx, const slsht_desc* desc, const double* f_lm,
+                             const double* h_lm, const int32_t* lm, int32_t n_pairs, void* g_out,
+                             void* stream) {
+  if (!ctx) return SLSHT_E_ARG;
+  CKS(check_desc(desc));
+  if (n_pairs < 0) return SLSHT_E_ARG;
+  if (n_pairs == 0) return SLSHT_OK;
+  if (!f_lm || !h_lm || !lm || !g_out) return SLSHT_E_ARG;
+  if (((uintptr_t)g_out) & 7) return SLSHT_E_ARG;
+  DeviceGuard g(ctx->device);
+  // pair validation needs host-visible indices
+  std::vector<int32_t> lm_host;
+  const int32_t* lmv = lm;
+  if (is_device_ptr(lm)) {
+    lm_host.resize(2 * (size_t)n_pairs);
+    CK(cudaMemcpy(lm_host.data(), lm, sizeof(int32_t) * 2 * (size_t)n_pairs, cudaMemcpyDeviceToHost));
+    lmv = lm_host.data();
+  }
+  CKS(check_pairs(desc, lmv, n_pairs));
+  std::lock_guard<std::mutex> serial(ctx->sync_mu);
+  return forward_impl(ctx, ctx->sync_ws, desc, f_lm, h_lm, lm, n_pairs, g_out, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------- inverse
+extern "C" int slsht_inverse(slsht_ctx* ctx, const slsht_desc* desc, const void* g_in,
+                             const double h00[2], const int32_t* lm, int32_t n_pairs, double* f_out,
+                             void* stream) {
+  if (!ctx) return SLSHT_E_ARG;
+  CKS(check_desc(desc));
+  if (n_pairs < 0) return SLSHT_E_ARG;
+  if (n_pairs == 0) return SLSHT_OK;
+  if (!g_in || !h00 || !lm || !f_out) return SLSHT_E_ARG;
+  const int Lh = desc->L_h, Na = desc->n_alpha, Nb = desc->n_beta, Ng = desc->n_gamma;
+  if (Na < Lh || Nb < Lh || Ng < Lh) return SLSHT_E_ARG;
+  if (h00[0] == 0.0 && h00[1] == 0.0) return SLSHT_E_H00;
+  DeviceGuard g(ctx->device);
+  if (!is_device_ptr(g_in)) return SLSHT_E_ARG;
+  std::vector<int32_t> lm_host;
+  const int32_t* lmv = lm;
+  if (is_device_ptr(lm)) {
+    lm_host.resize(2 * (size_t)n_pairs);
+    CK(cudaMemcpy(lm_host.data(), lm, sizeof(int32_t) * 2 * (size_t)n_pairs, cudaMemcpyDeviceToHost));
+    lmv = lm_host.data();
+  }
+  CKS(check_pairs(desc, lmv, n_pairs));
+  std::lock_guard<std::mutex> serial(ctx->sync_mu);
+  Workspace& w = ctx->sync_ws;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaStreamWaitEvent(st, w.done, 0));
+  const double* wb;
+  {
+    std::lock_guard<std::mutex> gl(ctx->mu);
+    CKS(get_wbeta(ctx, Nb, st, &wb));
+  }
+  // slabs of alpha rows: about four CTAs per SM over all pairs
+  const int want = std::max(1, (4 * ctx->num_sms + n_pairs - 1) / n_pairs);
+  const int nslab = std::min(Na, want);
+  const size_t pbytes = sizeof(double2) * (size_t)n_pairs * nslab;
+  CKS(ws_reserve(ctx, w, &w.kc, &w.kc_cap, pbytes + sizeof(double2) * (size_t)n_pairs));
+  double2* partial = (double2*)w.kc;
+  double2* fdev = is_device_ptr(f_out) ? (double2*)f_out : partial + (size_t)n_pairs * nslab;
+  if (desc->prec == SLSHT_FP64) {
+    LAUNCH(SLSHT_STAGE_INVERSE, st,
+           launch_inverse_f64((const double2*)g_in, wb, Na, Nb, Ng, n_pairs, partial, nslab, st));
+  } else {
+    LAUNCH(SLSHT_STAGE_INVERSE, st,
+           launch_inverse_f32((const float2*)g_in, wb, Na, Nb, Ng, n_pairs, partial, nslab, st));
+  }
+  // scale = (2 pi/Na)(2 pi/Ng) / (sqrt(16 pi^3) h00)
+  const double pi = 3.14159265358979323846;
+  const double q = (2.0 * pi / Na) * (2.0 * pi / Ng) / std::sqrt(16.0 * pi * pi * pi);
+  const double den = h00[0] * h00[0] + h00[1] * h00[1];
+  const double sre = q * h00[0] / den, sim = -q * h00[1] / den;
+  LAUNCH(SLSHT_STAGE_INVERSE, st, launch_inverse_final(partial, nslab, n_pairs, sre, sim, fdev, st));
+  if ((void*)fdev != (void*)f_out) {
+    StageTimer t(ctx, SLSHT_STAGE_COPY, st);
+    CK(cudaMemcpyAsync(f_out, fdev, sizeof(double2) * (size_t)n_pairs, cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaEventRecord(w.done, st));
+  return SLSHT_OK;
+}
+
+// ---------------------------------------------------------------- serving
+// Continuous batching: requests wait in a FIFO; the worker admits the head
+// request as soon as a stream slot is free and its scratch fits the memory
+// budget, launches it on that slot's stream (so it overlaps with requests
+// already on the GPU) and retires slots whose completion event has fired.
+static size_t request_scratch_estimate(const slsht_desc* d, int32_t n_pairs) {
+  const int Lh = d->L_h, K = 2 * Lh - 1;
+  const size_t J = (size_t)d->n_beta * d->n_gamma;
+  const size_t x = (d->prec == SLSHT_FP64 ? sizeof(double2) : sizeof(float2)) * (size_t)K * J;
+  const size_t P = std::max<size_t>(1, std::min<size_t>((size_t)n_pairs, ((size_t)96 << 20) / std::max<size_t>(1, x)));
+  return P * (x + sizeof(double2) * Lh * Lh) + sizeof(double2) * ((size_t)d->L_f * d->L_f + Lh * Lh) +
+         sizeof(int2) * (size_t)n_pairs;
+}
+
+static void worker_loop(slsht_ctx* c) {
+  DeviceGuard g(c->device);
+  std::unique_lock<std::mutex> l(c->smu);
+  while (true) {
+    // retire finished slots
+    for (auto& s : c->slots) {
+      if (!s.busy) continue;
+      cudaError_t q = cudaEventQuery(s.fin);
+      if (q == cudaErrorNotReady) continue;
+      int st = SLSHT_OK;
+      if (q != cudaSuccess) { record_cuda_error("request", q); st = SLSHT_E_CUDA; }
+      c->status[s.req->id] = st;
+      s.req.reset();
+      s.busy = false;
+      c->inflight--;
+      c->scv.notify_all();
+    }
+    // admit
+    while (!c->queue.empty()) {
+      Slot* free_slot = nullptr;
+      for (auto& s : c->slots) if (!s.busy) { free_slot = &s; break; }
+      if (!free_slot) break;
+      Request* r = c->queue.front().get();
+      const size_t need = request_scratch_estimate(&r->desc, (int32_t)(r->lm.size() / 2));
+      const size_t avail = c->budget > c->used.load() ? c->budget - c->used.load() : 0;
+      if (need > avail + free_slot->ws.bytes && c->inflight > 0) break;   // wait for memory
+      std::unique_ptr<Request> req = std::move(c->queue.front());
+      c->queue.pop_front();
+      Slot& s = *free_slot;
+      int st = SLSHT_OK;
+      if (!s.stream) {
+        if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&s.fin, cudaEventDisableTiming) != cudaSuccess) {
+          cudaGetLastError();
+          st = SLSHT_E_CUDA;
+        } else {
+          st = ws_init(s.ws);
+        }
+      }
+      if (st == SLSHT_OK) {
+        l.unlock();
+        st = forward_impl(c, s.ws, &req->desc, req->f.data(), req->h.data(), req->lm.data(),
+                          (int32_t)(req->lm.size() / 2), req->g_out, s.stream);
+        if (st == SLSHT_OK && cudaEventRecord(s.fin, s.stream) != cudaSuccess) st = SLSHT_E_CUDA;
+        l.lock();
+      }
+      if (st != SLSHT_OK) {
+        c->status[req->id] = st;
+        c->scv.notify_all();
+        continue;
+      }
+      s.req = std::move(req);
+      s.busy = true;
+      c->inflight++;
+    }
+    if (c->stop && c->queue.empty() && c->inflight == 0) break;
+    if (c->inflight > 0) {
+      c->scv.wait_for(l, std::chrono::microseconds(50));
+    } else {
+      c->scv.wait(l, [c] { return c->stop || !c->queue.empty(); });
+    }
+  }
+}
+
+static int copy_in(const double* src, size_t n, std::vector<double>& dst) {
+  dst.resize(n);
+  if (is_device_ptr(src)) {
+    CK(cudaMemcpy(dst.data(), src, n * sizeof(double), cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(dst.data(), src, n * sizeof(double));
+  }
+  return SLSHT_OK;
+}
+
+extern "C" int slsht_submit(slsht_ctx* c, const slsht_desc* desc, const double* f_lm,
+                            const double* h_lm, const int32_t* lm, int32_t n_pairs, void* g_out,
+                            uint64_t* ticket) {
+  if (!c || !ticket) return SLSHT_E_ARG;
+  CKS(check_desc(desc));
+  if (n_pairs <= 0 || !f_lm || !h_lm || !lm || !g_out) return SLSHT_E_ARG;
+  DeviceGuard g(c->device);
+  if (!is_device_ptr(g_out) || (((uintptr_t)g_out) & 7)) return SLSHT_E_ARG;
+  std::unique_ptr<Request> r(new Request());
+  r->desc = *desc;
+  r->g_out = g_out;
+  CKS(copy_in(f_lm, 2 * (size_t)desc->L_f * desc->L_f, r->f));
+  CKS(copy_in(h_lm, 2 * (size_t)desc->L_h * desc->L_h, r->h));
+  r->lm.resize(2 * (size_t)n_pairs);
+  if (is_device_ptr(lm)) {
+    CK(cudaMemcpy(r->lm.data(), lm, sizeof(int32_t) * 2 * (size_t)n_pairs, cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(r->lm.data(), lm, sizeof(int32_t) * 2 * (size_t)n_pairs);
+  }
+  CKS(check_pairs(desc, r->lm.data(), n_pairs));
+  std::unique_lock<std::mutex> l(c->smu);
+  if (c->queue.size() >= SERVE_MAX_QUEUE) return SLSHT_E_BUSY;
+  if (!c->worker_started) {
+    c->worker = std::thread(worker_loop, c);
+    c->worker_started = true;
+  }
+  r->id = c->next_id++;
+  *ticket = r->id;
+  c->status[r->id] = SLSHT_PENDING;
+  c->queue.push_back(std::move(r));
+  c->scv.notify_all();
+  return SLSHT_OK;
+}
+
+extern "C" int slsht_poll(slsht_ctx* c, uint64_t ticket) {
+  if (!c) return SLSHT_E_ARG;
+  std::lock_guard<std::mutex> l(c->smu);
+  auto it = c->status.find(ticket);
+  if (it == c->status.end()) return SLSHT_E_STATE;
+  const int s = it->second;
+  if (s != SLSHT_PENDING) c->status.erase(it);
+  return s;
+}
+
+extern "C" int slsht_drain(slsht_ctx* c, int64_t timeout_ms) {
+  if (!c) return SLSHT_E_ARG;
+  std::unique_lock<std::mutex> l(c->smu);
+  const auto until = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms);
+  while (!c->queue.empty() || c->inflight > 0) {
+    if (c->scv.wait_until(l, until) == std::cv_status::timeout &&
+        (!c->queue.empty() || c->inflight > 0))
+      return SLSHT_E_TIMEOUT;
+  }
+  return SLSHT_OK;
+}
+
+// ---------------------------------------------------------------- tools
+extern "C" const char* slsht_strerror(int code) {
+  switch (code) {
+    case SLSHT_OK: return "ok";
+    case SLSHT_PENDING: return "request pending";
+    case SLSHT_E_ARG: return "invalid argument";
+    case SLSHT_E_H00: return "window DC coefficient h_0^0 is zero; the inverse needs it non-zero";
+    case SLSHT_E_NOMEM: return "out of device memory or over the context's memory budget";
+    case SLSHT_E_BUSY: return "request queue full";
+    case SLSHT_E_TIMEOUT: return "bounded wait expired";
+    case SLSHT_E_CUDA: return "CUDA call failed (see slsht_last_error)";
+    case SLSHT_E_STATE: return "unknown ticket or invalid context state";
+    default: return "unknown status code";
+  }
+}
+
+extern "C" const char* slsht_last_error(void) {
+  static thread_local std::string copy;
+  std::lock_guard<std::mutex> g(g_err_mu);
+  copy = g_last_err;
+  return copy.c_str();
+}
+
+extern "C" int slsht_profile(slsht_ctx* c, int enable) {
+  if (!c) return SLSHT_E_ARG;
+  std::lock_guard<std::mutex> g(c->mu);
+  c->profile = enable != 0;
+  return SLSHT_OK;
+}
+
+extern "C" int slsht_get_stats(slsht_ctx* c, slsht_stats* out, int reset) {
+  if (!c || !out) return SLSHT_E_ARG;
+  DeviceGuard dg(c->device);
+  std::lock_guard<std::mutex> g(c->mu);
+  for (auto& r : c->prof) {
+    float ms = 0.f;
+    CK(cudaEventSynchronize(r.b));
+    CK(cudaEventElapsedTime(&ms, r.a, r.b));
+    c->prof_ms[r.stage] += ms;
+    c->ev_pool.push_back(r.a);
+    c->ev_pool.push_back(r.b);
+  }
+  c->prof.clear();
+  for (int i = 0; i < SLSHT_NSTAGES; ++i) {
+    out->launches[i] = c->launches[i];
+    out->ms[i] = c->prof_ms[i];
+  }
+  out->samples_written = c->samples;
+  if (reset) {
+    for (int i = 0; i < SLSHT_NSTAGES; ++i) { c->launches[i] = 0; c->prof_ms[i] = 0.0; }
+    c->samples = 0;
+  }
+  return SLSHT_OK;
+}
+
+extern "C" size_t slsht_mem_used(slsht_ctx* c) { return c ? c->used.load() : 0; }
+
+extern "C" const char* slsht_version(void) { return "libslsht 0.1 (sm_103a)"; }

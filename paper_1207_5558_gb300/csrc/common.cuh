@@ -1,0 +1,80 @@
+// Shared device helpers and launcher declarations for libslsht.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define SLSHT_MAX_LH 64          // largest window band limit (exclusive)
+#define SLSHT_CHAIN_MAX 128      // >= 2*SLSHT_MAX_LH - 1: longest 3j chain in j1
+
+// Offset of the (2p+1)^2 block of degree p in tables that store every degree
+// p < Lh back to back: sum_{p' < p} (2p'+1)^2 = p (4p^2 - 1) / 3.
+__host__ __device__ __forceinline__ int blk_off(int p) { return p * (4 * p * p - 1) / 3; }
+
+// cos and sin of 2 pi k / N, with the integer product reduced modulo N first
+// so the argument passed to sincospi lies in [0, 2).
+__device__ __forceinline__ void sincos_2pi_frac(long long k, long long N, double* s, double* c) {
+  long long r = k % N;
+  if (r < 0) r += N;
+  sincospi(2.0 * (double)r / (double)N, s, c);
+}
+
+template <typename T> struct vec2;
+template <> struct vec2<double> { typedef double2 t; };
+template <> struct vec2<float> { typedef float2 t; };
+
+__device__ __forceinline__ double2 mk2(double a, double b) { return make_double2(a, b); }
+__device__ __forceinline__ float2 mk2(float a, float b) { return make_float2(a, b); }
+
+// ----------------------------------------------------------------- launchers
+// Every launcher enqueues on `st` and returns the launch status
+// (cudaGetLastError after the launch).
+
+// Delta^p = d^p(pi/2), p < Lh, full (2p+1)^2 blocks at blk_off(p).
+cudaError_t launch_delta(double* D, int Lh, cudaStream_t st);
+// d^p_{q,q'}(beta_b) for b < Nb from Delta (Eq. WignerD_expansion_new):
+// dt[b * S + blk_off(p) + (q+p)(2p+1) + (q'+p)], S = blk_off(Lh).
+cudaError_t launch_dtable_f64(const double* D, double* dt, int Lh, int Nb, cudaStream_t st);
+cudaError_t launch_dtable_f32(const double* D, float* dt, int Lh, int Nb, cudaStream_t st);
+// tab[i * R + r] = (cos, sin)(2 pi (r0 + r) i / N), i < N, r < R.
+cudaError_t launch_phase_f64(double2* tab, int N, int R, int r0, cudaStream_t st);
+cudaError_t launch_phase_f32(float2* tab, int N, int R, int r0, cudaStream_t st);
+// beta quadrature weights q_b, b < Nb (see the inverse).
+cudaError_t launch_beta_weights(double* w, int Nb, cudaStream_t st);
+
+// k_lm(p, q) for each pair: kc[pair * Lh*Lh + p*p + p + q] (complex128).
+cudaError_t launch_couple(const double2* f, int Lf, int Lh, const int2* lm, int npairs,
+                          double2* kc, cudaStream_t st);
+
+// C_{q,q',q''}(l, m) (Eq. constant_alternative_formulation), [pair][q][q'][q''].
+cudaError_t launch_ctensor(const double2* kc, const double2* h, const double* D, int Lh,
+                           int npairs, double2* C, cudaStream_t st);
+// Y[pair][b][q][q'] = sum_q'' C[q][q'][q''] e^{-i q'' beta_b}.
+cudaError_t launch_beta_dft(const double2* C, int Lh, int Nb, int npairs, double2* Y,
+                            cudaStream_t st);
+
+// Output of the beta/gamma stage for the CUDA-core alpha stage: paired sums
+// Xs[pair][c][j], j = b*Ng + gamma index, c = 0: X_0, c = 2r-1: X_r + X_-r,
+// c = 2r: X_r - X_-r (r = 1 .. Lh-1).
+// src_y == nullptr: beta sum from the d table (separation of variables);
+// otherwise from Y of launch_beta_dft (factoring of rotations).
+cudaError_t launch_betagamma_f64(const double2* kc, const double2* h, const double* dt,
+                                 const double2* Y, const double2* eg, int Lh, int Nb, int Ng,
+                                 int npairs, double2* Xs, cudaStream_t st);
+cudaError_t launch_betagamma_f32(const double2* kc, const double2* h, const float* dt,
+                                 const double2* Y, const float2* eg, int Lh, int Nb, int Ng,
+                                 int npairs, float2* Xs, cudaStream_t st);
+
+// g[pair][a][j] = X_0 + sum_r (P_r cos(r alpha_a) - i M_r sin(r alpha_a)).
+cudaError_t launch_alpha_f64(const double2* Xs, const double2* csa, int Lh, int Na, int J,
+                             int npairs, double2* g, cudaStream_t st);
+cudaError_t launch_alpha_f32(const float2* Xs, const float2* csa, int Lh, int Na, int J,
+                             int npairs, float2* g, cudaStream_t st);
+
+// Inverse: partial sums then final scaling (deterministic order).
+cudaError_t launch_inverse_f64(const double2* g, const double* wb, int Na, int Nb, int Ng,
+                               int npairs, double2* partial, int nslab, cudaStream_t st);
+cudaError_t launch_inverse_f32(const float2* g, const double* wb, int Na, int Nb, int Ng,
+                               int npairs, double2* partial, int nslab, cudaStream_t st);
+cudaError_t launch_inverse_final(const double2* partial, int nslab, int npairs, double scale_re,
+                                 double scale_im, double2* fout, cudaStream_t st);

@@ -1,0 +1,19 @@
+// Tensor-core (tcgen05) alpha stage of the FP32_BULK path: interface.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+// Whether the tensor-core alpha stage handles this window band limit / grid.
+bool tc_supported(int Lh, int Na);
+// Bytes of the per-grid E operand tables (split-FP16 cos / sin of q alpha_a).
+size_t tc_etab_bytes(int Na, int Lh);
+cudaError_t launch_tc_etab(void* etab, int Na, int Lh, cudaStream_t st);
+// Bytes of the A operand (split-FP16 X, per-row scales) of ONE pair.
+size_t tc_xblob_bytes(int Nb, int Ng, int Lh);
+// beta + gamma stages writing the A operand blobs (FP32 sums).
+cudaError_t launch_betagamma_tc(const double2* kc, const double2* h, const float* dt,
+                                const double2* Y, const float2* eg, int Lh, int Nb, int Ng,
+                                int npairs, void* xblob, cudaStream_t st);
+// alpha stage on tcgen05: g[pair][a][j] complex64.
+cudaError_t launch_alpha_tc(const void* xblob, const void* etab, int Lh, int Na, int Nb, int Ng,
+                            int npairs, float2* g, int num_sms, cudaStream_t st);

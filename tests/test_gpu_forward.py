@@ -1,0 +1,189 @@
+"""GPU parity of the forward transform through the C ABI against the FP64
+oracle.  Tolerances: relative L2 <= 1e-12 for the FP64 path and <= 1e-5 for
+FP32_BULK, per call (the bounds the method's precision targets state)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import slsht as O
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-5
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1207_5558_gb300 as pkg
+    from paper_1207_5558_gb300 import build
+    build.build()
+    c = pkg.Context(0)
+    yield c
+    c.close()
+
+
+def _fw(ctx, Lf, Lh, grid, f, h, pairs, prec):
+    return ctx.forward(Lf, Lh, grid, f, h, pairs, prec=prec).cpu().numpy()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_config1_vs_direct_quadrature(ctx, prec):
+    """Workload 1 in full: L_f=16, L_h=4, all l<16, grid 31x16x7, against the
+    quadrature of the definition (Eq. stft_spatial)."""
+    c = synth.CONFIGS[1]
+    f, h, pairs = synth.config_inputs(1)
+    ref = O.forward_quadrature(f, h, c["Lf"], c["Lh"], pairs, c["grid"])
+    g = _fw(ctx, c["Lf"], c["Lh"], c["grid"], f, h, pairs, prec)
+    assert rel(g, ref) < (TOL64 if prec == 0 else TOL32)
+
+
+@pytest.mark.parametrize("route", [1, 2])
+def test_beta_routes_agree_with_oracle(ctx, route):
+    """Both beta-stage routes: d(beta) table (separation of variables) and the
+    factoring of rotations (C tensor + DFT in q'')."""
+    import paper_1207_5558_gb300 as pkg
+    Lf, Lh, grid = 12, 5, (23, 12, 9)
+    f = synth.signal_powerlaw(Lf, 3)
+    h = synth.window_cn(Lh, 4)
+    pairs = synth.pairs_all(Lf + Lh - 1)
+    ref = O.forward_coeff(f, h, Lf, Lh, pairs, grid)
+    ctx.set_option(pkg.SLSHT_OPT_BETA_ROUTE, route)
+    try:
+        for prec, tol in [(0, TOL64), (1, TOL32)]:
+            g = _fw(ctx, Lf, Lh, grid, f, h, pairs, prec)
+            assert rel(g, ref) < tol, (route, prec)
+    finally:
+        ctx.set_option(pkg.SLSHT_OPT_BETA_ROUTE, 0)
+
+
+@pytest.mark.parametrize("Lf,Lh,grid", [
+    (1, 1, (1, 1, 1)),        # K = 1, one sample
+    (5, 1, (3, 2, 1)),        # window = constant
+    (4, 2, (5, 3, 1)),        # N_gamma = 1
+    (6, 6, (11, 6, 11)),      # L_h = L_f, native grid
+    (3, 7, (13, 7, 13)),      # L_h > L_f
+    (9, 4, (2, 1, 3)),        # fewer samples than the band limit
+    (7, 3, (130, 5, 33)),     # ragged: several alpha tiles, columns not a multiple of a warp
+])
+def test_edge_shapes(ctx, Lf, Lh, grid):
+    f = synth.signal_cn_real(Lf, Lf * 100 + Lh)
+    h = synth.window_cn(Lh, Lh * 7 + 1)
+    pairs = synth.pairs_all(Lf + Lh - 1)        # includes l > Lf - 1 and |m| = l
+    ref = O.forward_coeff(f, h, Lf, Lh, pairs, grid)
+    for prec, tol in [(0, TOL64), (1, TOL32)]:
+        g = _fw(ctx, Lf, Lh, grid, f, h, pairs, prec)
+        assert rel(g, ref) < tol, (prec, rel(g, ref))
+
+
+def test_vanishing_and_window_y00(ctx):
+    Lf, Lh, grid = 6, 1, (4, 3, 2)
+    f = synth.signal_cn_real(Lf, 2)
+    h = np.ones(1, complex)
+    pairs = synth.pairs_all(Lf)
+    g = _fw(ctx, Lf, Lh, grid, f, h, pairs, 0)
+    ref = f[:, None, None, None] / np.sqrt(4 * np.pi) * np.ones((1,) + grid)
+    assert np.max(np.abs(g - ref)) < 1e-14
+
+
+def test_config2_sampled_pairs(ctx):
+    """Workload 2 (power-law f, 20x10 deg elliptical window, grid 127x64x15):
+    the whole map in the bench's launch configuration, sampled pairs checked."""
+    c = synth.CONFIGS[2]
+    f, h, pairs = synth.config_inputs(2)
+    g = ctx.forward(c["Lf"], c["Lh"], c["grid"], f, h, pairs, prec=0)
+    rng = np.random.default_rng(0)
+    idx = np.unique(np.concatenate([[0, len(pairs) - 1, len(pairs) // 2], rng.choice(len(pairs), 20, replace=False)]))
+    ref = O.forward_coeff(f, h, c["Lf"], c["Lh"], pairs[idx], c["grid"])
+    got = g[idx].cpu().numpy()
+    assert rel(got, ref) < TOL64
+
+
+def test_config3_sampled_pairs_full_grid(ctx):
+    """Workload 3 (L_f=256, L_h=16, grid 511x256x31): one whole map computed
+    in the bench's launch configuration, seeded sampled pairs (including the
+    extreme orders of l = 255) compared with the oracle over their full grid."""
+    import torch
+    c = synth.CONFIGS[3]
+    f, h, pairs = synth.config_inputs(3, map_index=1)
+    sel = [0, 32, 33, 161, 929, 928, 673]
+    ref = O.forward_coeff(f, h, c["Lf"], c["Lh"], pairs[sel], c["grid"])
+    for prec, tol in [(0, TOL64), (1, TOL32)]:
+        g = ctx.forward(c["Lf"], c["Lh"], c["grid"], f, h, pairs, prec=prec)
+        got = g[sel].cpu().numpy()
+        del g
+        torch.cuda.empty_cache()
+        assert rel(got, ref) < tol, prec
+        for i in range(len(sel)):
+            assert rel(got[i], ref[i]) < tol * 10, (prec, sel[i])
+
+
+def test_host_output_buffer(ctx):
+    """g_out in host memory: the library stages chunks and copies them back."""
+    import torch
+    import paper_1207_5558_gb300 as pkg
+    Lf, Lh, grid = 10, 4, (19, 10, 7)
+    f = synth.signal_powerlaw(Lf, 5)
+    h = synth.window_cn(Lh, 6)
+    pairs = synth.pairs_all(Lf)
+    ref = O.forward_coeff(f, h, Lf, Lh, pairs, grid)
+    ctx.set_option(pkg.SLSHT_OPT_CHUNK_PAIRS, 7)
+    try:
+        for prec, tol, dt in [(0, TOL64, np.complex128), (1, TOL32, np.complex64)]:
+            host = np.zeros((len(pairs),) + grid, dtype=dt)
+            pkg.slsht_forward(ctx.h, pkg.make_desc(Lf, Lh, grid, prec), f, h, pairs, len(pairs), host)
+            torch.cuda.synchronize()
+            assert rel(host, ref) < tol
+    finally:
+        ctx.set_option(pkg.SLSHT_OPT_CHUNK_PAIRS, 0)
+
+
+def test_device_inputs_and_chunking(ctx):
+    import torch
+    import paper_1207_5558_gb300 as pkg
+    Lf, Lh, grid = 9, 3, (17, 9, 5)
+    f = synth.signal_cn_real(Lf, 8)
+    h = synth.window_cn(Lh, 9)
+    pairs = synth.pairs_all(Lf + Lh - 1)
+    ref = O.forward_coeff(f, h, Lf, Lh, pairs, grid)
+    fd = torch.from_numpy(f).cuda()
+    hd = torch.from_numpy(h).cuda()
+    lmd = torch.from_numpy(pairs).cuda()
+    for chunk in (1, 5, 0):
+        ctx.set_option(pkg.SLSHT_OPT_CHUNK_PAIRS, chunk)
+        g = torch.empty((len(pairs),) + grid, dtype=torch.complex128, device="cuda")
+        pkg.slsht_forward(ctx.h, pkg.make_desc(Lf, Lh, grid, 0), fd, hd, lmd, len(pairs), g)
+        assert rel(g.cpu().numpy(), ref) < TOL64
+    ctx.set_option(pkg.SLSHT_OPT_CHUNK_PAIRS, 0)
+
+
+def test_invalid_arguments_rejected(ctx):
+    import torch
+    import paper_1207_5558_gb300 as pkg
+    g = torch.empty((1, 3, 3, 3), dtype=torch.complex128, device="cuda")
+    f = np.zeros(16, complex)
+    h = np.ones(4, complex)
+    with pytest.raises(pkg.SlshtError) as e:
+        pkg.slsht_forward(ctx.h, pkg.make_desc(4, 2, (3, 3, 3)), f, h, np.array([[5, 0]], np.int32), 1, g)
+    assert e.value.code == -1
+    with pytest.raises(pkg.SlshtError):
+        pkg.slsht_forward(ctx.h, pkg.make_desc(4, 2, (3, 3, 3)), f, h, np.array([[2, 3]], np.int32), 1, g)
+    assert pkg.slsht_forward(ctx.h, pkg.make_desc(4, 2, (3, 3, 3)), f, h, np.zeros((0, 2), np.int32), 0, g) == 0
+
+
+def test_determinism(ctx):
+    Lf, Lh, grid = 12, 6, (23, 12, 11)
+    f = synth.signal_powerlaw(Lf, 1)
+    h = synth.window_cn(Lh, 2)
+    pairs = synth.pairs_all(Lf)
+    for prec in (0, 1):
+        a = _fw(ctx, Lf, Lh, grid, f, h, pairs, prec)
+        b = _fw(ctx, Lf, Lh, grid, f, h, pairs, prec)
+        assert np.array_equal(a, b)

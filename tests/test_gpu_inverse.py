@@ -1,0 +1,81 @@
+"""GPU inverse (Eq. inversion_1/2 with the exact SO(3) quadrature) through the
+C ABI: against the oracle's inverse on the same g, and the round trip f -> g -> f
+(the paper's own accuracy check, Sec. V-A)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import slsht as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1207_5558_gb300 as pkg
+    from paper_1207_5558_gb300 import build
+    build.build()
+    c = pkg.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("cfg", [1, 2])
+def test_round_trip(ctx, cfg):
+    c = synth.CONFIGS[cfg]
+    f, h, _ = synth.config_inputs(cfg)
+    pairs = synth.pairs_all(c["Lf"])
+    for prec, tol in [(0, 1e-12), (1, 1e-5)]:
+        g = ctx.forward(c["Lf"], c["Lh"], c["grid"], f, h, pairs, prec=prec)
+        fr = ctx.inverse(c["Lf"], c["Lh"], c["grid"], g, h[0], pairs, prec=prec)
+        err = np.linalg.norm(fr - f) / np.linalg.norm(f)
+        assert err < tol, (cfg, prec, err)
+
+
+def test_inverse_matches_oracle_inverse(ctx):
+    import torch
+    Lf, Lh, grid = 9, 4, (7, 5, 9)
+    f = synth.signal_powerlaw(Lf, 11)
+    h = synth.window_cn(Lh, 12)
+    pairs = synth.pairs_all(Lf + Lh - 1)
+    rng = np.random.default_rng(3)
+    g = rng.standard_normal((len(pairs),) + grid) + 1j * rng.standard_normal((len(pairs),) + grid)
+    ref = O.inverse(g, h[0], grid)
+    gd = torch.from_numpy(g).cuda()
+    fr = ctx.inverse(Lf, Lh, grid, gd, h[0], pairs, prec=0)
+    assert np.max(np.abs(fr - ref)) / np.max(np.abs(ref)) < 1e-13
+    g32 = torch.from_numpy(g.astype(np.complex64)).cuda()
+    ref32 = O.inverse(g.astype(np.complex64).astype(np.complex128), h[0], grid)
+    fr32 = ctx.inverse(Lf, Lh, grid, g32, h[0], pairs, prec=1)
+    assert np.max(np.abs(fr32 - ref32)) / np.max(np.abs(ref32)) < 1e-13
+
+
+def test_inverse_is_bitwise_reproducible(ctx):
+    Lf, Lh, grid = 8, 3, (9, 6, 5)
+    f = synth.signal_cn_real(Lf, 1)
+    h = synth.window_cn(Lh, 2)
+    pairs = synth.pairs_all(Lf)
+    g = ctx.forward(Lf, Lh, grid, f, h, pairs, prec=0)
+    a = ctx.inverse(Lf, Lh, grid, g, h[0], pairs, prec=0)
+    b = ctx.inverse(Lf, Lh, grid, g, h[0], pairs, prec=0)
+    assert np.array_equal(a, b)
+
+
+def test_inverse_argument_errors(ctx):
+    import paper_1207_5558_gb300 as pkg
+    import torch
+    g = torch.zeros((1, 4, 4, 4), dtype=torch.complex128, device="cuda")
+    out = np.zeros(1, complex)
+    with pytest.raises(pkg.SlshtError) as e:
+        pkg.slsht_inverse(ctx.h, pkg.make_desc(4, 2, (4, 4, 4)), g, 0.0, np.array([[1, 0]], np.int32), 1, out)
+    assert e.value.code == -2
+    with pytest.raises(pkg.SlshtError) as e:      # grid coarser than the window band limit
+        pkg.slsht_inverse(ctx.h, pkg.make_desc(4, 5, (4, 4, 4)), g, 1.0, np.array([[1, 0]], np.int32), 1, out)
+    assert e.value.code == -1
+    with pytest.raises(pkg.SlshtError) as e:      # g in host memory
+        pkg.slsht_inverse(ctx.h, pkg.make_desc(4, 2, (4, 4, 4)), g.cpu().numpy(), 1.0,
+                          np.array([[1, 0]], np.int32), 1, out)
+    assert e.value.code == -1
