@@ -1,15 +1,517 @@
-// Tensor-core alpha stage (placeholder until the tcgen05 kernel lands).
+// FP32_BULK alpha stage on the 5th-generation tensor cores (tcgen05).
+//
+// For one pair, with complex columns j = (beta, gamma) sample and alpha rows a,
+//   g[a][j] = sum_q X_q[j] e^{-i q alpha_a}
+// is a real GEMM D[j][n] = sum_k A[j][k] B[n][k] with
+//   A[j][k]      = [ Re X_q[j] (q = -(Lh-1)..Lh-1) | Im X_q[j] | 0 ... ]      (K padded to 64)
+//   B[n][k]      = [ cos(q alpha_a)  |  sin(q alpha_a) | 0 ]   n = a - a0        (Re g)
+//   B[128+n][k]  = [ -sin(q alpha_a) |  cos(q alpha_a) | 0 ]                     (Im g)
+// so one M=128 x N=256 accumulator holds Re and Im of 128 columns x 128 alpha
+// rows.  Precision: each operand is split into FP16 hi + lo (A after a
+// per-row power-of-two scale so its largest entry is in [2^14, 2^15)), and
+// D = A_hi B_hi + A_hi B_lo + A_lo B_hi is accumulated in FP32 (about 22
+// significant bits per product), which keeps the relative L2 error of g near
+// 1e-6.
+//
+// Kernel structure: persistent, one CTA per SM, work item = (pair, tile of
+// 128 columns).  Warp 0 streams operands with cp.async.bulk into shared
+// memory (A tile double-buffered, B chunks through a 2-stage ring), warp 1
+// issues tcgen05.mma from one thread into a double-buffered TMEM accumulator
+// (2 x 256 columns), warps 2-5 drain the accumulator (tcgen05.ld), rescale and
+// store g with coalesced 8-byte stores (for a fixed alpha row a warp writes
+// 32 consecutive columns).  Every mbarrier wait is bounded: on expiry the
+// CTA records an error word, stops, waits (bounded) for its own copies and
+// MMAs in flight, frees TMEM and exits.
+#include <cuda_fp16.h>
+
+#include "common.cuh"
 #include "tc.cuh"
 
-bool tc_supported(int, int) { return false; }
-size_t tc_etab_bytes(int, int) { return 0; }
-cudaError_t launch_tc_etab(void*, int, int, cudaStream_t) { return cudaErrorNotSupported; }
-size_t tc_xblob_bytes(int, int, int) { return 0; }
-cudaError_t launch_betagamma_tc(const double2*, const double2*, const float*, const double2*,
-                                const float2*, int, int, int, int, void*, cudaStream_t) {
-  return cudaErrorNotSupported;
+#define TC_M 128                       // columns j per tile (MMA M)
+#define TC_NC 128                      // alpha rows per chunk
+#define TC_N (2 * TC_NC)               // MMA N (Re and Im halves)
+#define TC_KB 64                       // FP16 elements of K per operand row (128 bytes)
+#define TC_A_HALF (TC_M * TC_KB * 2)   // bytes of one A part (hi or lo): 16 KB
+#define TC_B_HALF (TC_N * TC_KB * 2)   // bytes of one B part: 32 KB
+#define TC_A_BYTES (2 * TC_A_HALF)     // 32 KB
+#define TC_B_BYTES (2 * TC_B_HALF)     // 64 KB
+#define TC_THREADS 192
+#define TC_SMEM (2 * TC_A_BYTES + 2 * TC_B_BYTES + 1024 + 256)
+#define TC_WAIT_LIMIT (1u << 22)
+
+bool tc_supported(int Lh, int Na) { return Lh >= 1 && 2 * (2 * Lh - 1) <= TC_KB && Na >= 1; }
+
+static inline int tc_tiles(int Nb, int Ng) { return (Nb * Ng + TC_M - 1) / TC_M; }
+static inline int tc_chunks(int Na) { return (Na + TC_NC - 1) / TC_NC; }
+
+size_t tc_etab_bytes(int Na, int Lh) { (void)Lh; return (size_t)tc_chunks(Na) * TC_B_BYTES; }
+
+// per pair: tiles x 32 KB of A, then one float scale per padded column
+size_t tc_xblob_bytes(int Nb, int Ng, int Lh) {
+  (void)Lh;
+  const size_t t = (size_t)tc_tiles(Nb, Ng);
+  const size_t sc = ((t * TC_M * sizeof(float)) + 1023) / 1024 * 1024;
+  return t * TC_A_BYTES + sc;
 }
-cudaError_t launch_alpha_tc(const void*, const void*, int, int, int, int, int, float2*, int,
-                            cudaStream_t) {
-  return cudaErrorNotSupported;
+
+// byte offset of FP16 element (row r, k) inside a 128-row (or 256-row) K-major
+// operand part with the 128-byte swizzle: 16-byte chunk index k/8 XOR (r % 8),
+// rows 128 bytes apart, 8-row groups 1024 bytes apart.
+__host__ __device__ __forceinline__ uint32_t sw128_off(int r, int k) {
+  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 3) ^ (r & 7)) & 7) << 4) + (k & 7) * 2);
+}
+
+// ---------------------------------------------------------------- E tables
+// chunk c: [hi part: 256 rows x 64][lo part], rows n < 128 -> alpha a = c*128+n
+// (cos | sin), rows 128+n -> (-sin | cos); beyond Na or 2K: zeros.
+__global__ void k_tc_etab(unsigned char* __restrict__ etab, int Na, int Lh) {
+  const int K = 2 * Lh - 1;
+  const int c = blockIdx.x;
+  unsigned char* base = etab + (size_t)c * TC_B_BYTES;
+  for (int t = threadIdx.x; t < TC_N * TC_KB; t += blockDim.x) {
+    const int r = t / TC_KB, k = t % TC_KB;
+    const int n = r % TC_NC;
+    const int a = c * TC_NC + n;
+    double v = 0.0;
+    if (a < Na && k < 2 * K) {
+      const int q = (k % K) - (Lh - 1);
+      double s, co;
+      sincos_2pi_frac((long long)q * a, Na, &s, &co);
+      const bool is_sin = k >= K;
+      if (r < TC_NC) v = is_sin ? s : co;
+      else v = is_sin ? co : -s;
+    }
+    const __half hi = __double2half(v);
+    const __half lo = __double2half(v - (double)__half2float(hi));
+    *reinterpret_cast<__half*>(base + sw128_off(r, k)) = hi;
+    *reinterpret_cast<__half*>(base + TC_B_HALF + sw128_off(r, k)) = lo;
+  }
+}
+
+cudaError_t launch_tc_etab(void* etab, int Na, int Lh, cudaStream_t st) {
+  k_tc_etab<<<tc_chunks(Na), 256, 0, st>>>((unsigned char*)etab, Na, Lh);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- beta/gamma -> A
+// Same sums as k_betagamma<float>; the gamma sum pairs +-q'
+//   X_q[c] = G[q][0] + sum_{s>=1} (G[q][s] + G[q][-s]) cos(s gamma_c) - i (G[q][s] - G[q][-s]) sin(s gamma_c)
+// and the result row j = b*Ng + c is written as the A operand: scaled by 2^e
+// (largest entry into [2^14, 2^15)), split into FP16 hi/lo, swizzled.
+__global__ void __launch_bounds__(256)
+k_betagamma_tc(const double2* __restrict__ kc, const double2* __restrict__ h, const float* __restrict__ dt,
+               const double2* __restrict__ Y, const float2* __restrict__ eg, int Lh, int Nb, int Ng,
+               unsigned char* __restrict__ xblob, size_t blob_stride, int tiles) {
+  extern __shared__ unsigned char smem_raw[];
+  const int K = 2 * Lh - 1;
+  const int b = blockIdx.x, pair = blockIdx.y;
+  float2* sk = reinterpret_cast<float2*>(smem_raw);   // [Lh*Lh]
+  float2* sh = sk + Lh * Lh;                           // [Lh*Lh]
+  float2* sGp = sh + Lh * Lh;                          // [K][Lh]  G[q][s] + G[q][-s] (s=0: G[q][0])
+  float2* sGm = sGp + K * Lh;                          // [K][Lh]  G[q][s] - G[q][-s]
+  float2* sE = sGm + K * Lh;                           // [Ng][Lh] (cos, sin)(s gamma_c)
+  float* sX = reinterpret_cast<float*>(sE + Ng * Lh);  // [Ng][2K] Re | Im
+  const int n2 = Lh * Lh;
+  for (int t = threadIdx.x; t < n2; t += blockDim.x) {
+    const double2 kv = kc[(size_t)pair * n2 + t], hv = h[t];
+    sk[t] = make_float2((float)kv.x, (float)kv.y);
+    sh[t] = make_float2((float)hv.x, (float)hv.y);
+  }
+  for (int t = threadIdx.x; t < Ng * Lh; t += blockDim.x) {
+    const int c = t / Lh, s = t % Lh;
+    sE[t] = eg[c * K + s + (Lh - 1)];          // phase table row q' = +s
+  }
+  __syncthreads();
+  // G[q][q'] for the pair (q' = +-s), folded into Gp / Gm
+  for (int t = threadIdx.x; t < K * Lh; t += blockDim.x) {
+    const int qi = t / Lh, s = t % Lh;
+    const int q = qi - (Lh - 1);
+    float2 gpl = make_float2(0.f, 0.f), gmi = make_float2(0.f, 0.f);
+    for (int sg = 0; sg < (s == 0 ? 1 : 2); ++sg) {
+      const int qp = sg == 0 ? s : -s;
+      float re = 0.f, im = 0.f;
+      if (Y == nullptr) {
+        const int S = blk_off(Lh);
+        const float* drow = dt + (size_t)b * S;
+        for (int p = max(abs(q), abs(qp)); p < Lh; ++p) {
+          const float2 kv = sk[p * p + p + q], hv = sh[p * p + p + qp];
+          const float d = drow[blk_off(p) + (q + p) * (2 * p + 1) + (qp + p)];
+          re = fmaf(d, kv.x * hv.x - kv.y * hv.y, re);
+          im = fmaf(d, kv.x * hv.y + kv.y * hv.x, im);
+        }
+      } else {
+        const double2 v = Y[(((size_t)pair * Nb + b) * K + qi) * K + (qp + Lh - 1)];
+        re = (float)v.x;
+        im = (float)v.y;
+      }
+      if (sg == 0) { gpl = make_float2(re, im); gmi = make_float2(re, im); }
+      else { gpl.x += re; gpl.y += im; gmi.x -= re; gmi.y -= im; }
+    }
+    sGp[t] = gpl;
+    sGm[t] = gmi;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < K * Ng; t += blockDim.x) {
+    const int qi = t / Ng, c = t % Ng;
+    const float2* gp = sGp + qi * Lh;
+    const float2* gm = sGm + qi * Lh;
+    const float2* e = sE + c * Lh;
+    float re = gp[0].x, im = gp[0].y;
+    for (int s = 1; s < Lh; ++s) {        // (Gp cos - i Gm sin)
+      const float2 E = e[s], P = gp[s], M = gm[s];
+      re = fmaf(P.x, E.x, re);
+      re = fmaf(M.y, E.y, re);
+      im = fmaf(P.y, E.x, im);
+      im = fmaf(-M.x, E.y, im);
+    }
+    sX[c * 2 * K + qi] = re;
+    sX[c * 2 * K + K + qi] = im;
+  }
+  __syncthreads();
+  unsigned char* blob = xblob + (size_t)pair * blob_stride;
+  float* scales = reinterpret_cast<float*>(blob + (size_t)tiles * TC_A_BYTES);
+  const int J = Nb * Ng;
+  for (int c = threadIdx.x; c < Ng; c += blockDim.x) {
+    const float* row = sX + c * 2 * K;
+    float mx = 0.f;
+    for (int k = 0; k < 2 * K; ++k) mx = fmaxf(mx, fabsf(row[k]));
+    int ex = 0;
+    if (mx > 0.f) frexpf(mx, &ex);
+    const int e = mx > 0.f ? 15 - ex : 0;     // mx * 2^e in [2^14, 2^15)
+    const int j = b * Ng + c;
+    const int tile = j / TC_M, r = j % TC_M;
+    unsigned char* tb = blob + (size_t)tile * TC_A_BYTES;
+    for (int k0 = 0; k0 < TC_KB; k0 += 8) {
+      __align__(16) __half hi[8], lo[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int k = k0 + u;
+        const float v = k < 2 * K ? ldexpf(row[k], e) : 0.f;
+        hi[u] = __float2half_rn(v);
+        lo[u] = __float2half_rn(v - __half2float(hi[u]));
+      }
+      *reinterpret_cast<uint4*>(tb + sw128_off(r, k0)) = *reinterpret_cast<uint4*>(hi);
+      *reinterpret_cast<uint4*>(tb + TC_A_HALF + sw128_off(r, k0)) = *reinterpret_cast<uint4*>(lo);
+    }
+    scales[j] = ldexpf(1.f, -e);
+  }
+  // the last beta row also clears the padding rows of the last tile
+  if (b == Nb - 1) {
+    for (int j = J + threadIdx.x; j < tiles * TC_M; j += blockDim.x) {
+      const int tile = j / TC_M, r = j % TC_M;
+      unsigned char* tb = blob + (size_t)tile * TC_A_BYTES;
+      for (int k0 = 0; k0 < TC_KB; k0 += 8) {
+        *reinterpret_cast<uint4*>(tb + sw128_off(r, k0)) = make_uint4(0, 0, 0, 0);
+        *reinterpret_cast<uint4*>(tb + TC_A_HALF + sw128_off(r, k0)) = make_uint4(0, 0, 0, 0);
+      }
+      scales[j] = 0.f;
+    }
+  }
+}
+
+cudaError_t launch_betagamma_tc(const double2* kc, const double2* h, const float* dt, const double2* Y,
+                                const float2* eg, int Lh, int Nb, int Ng, int npairs, void* xblob,
+                                cudaStream_t st) {
+  if (npairs <= 0) return cudaSuccess;
+  const int K = 2 * Lh - 1;
+  const size_t smem = sizeof(float2) * ((size_t)2 * Lh * Lh + 2 * (size_t)K * Lh + (size_t)Ng * Lh) +
+                      sizeof(float) * (size_t)Ng * 2 * K;
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_betagamma_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid(Nb, npairs);
+  k_betagamma_tc<<<grid, 256, smem, st>>>(kc, h, dt, Y, eg, Lh, Nb, Ng, (unsigned char*)xblob,
+                                          tc_xblob_bytes(Nb, Ng, Lh), tc_tiles(Nb, Ng));
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase with the given parity.  Gives up when the CTA's
+// abort flag is raised or after TC_WAIT_LIMIT polls; returns false then.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  for (uint32_t i = 0; i < TC_WAIT_LIMIT; ++i) {
+    if (mbar_test(bar, parity)) return true;
+    if ((i & 255u) == 255u && *abort_flag) return false;
+  }
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+// K-major operand, 128-byte swizzle, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;                  // leading-dimension offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;        // stride between 8-row groups
+  d |= (uint64_t)1 << 46;                  // descriptor version
+  d |= (uint64_t)2 << 61;                  // 128-byte swizzle
+  return d;
+}
+// kind::f16 instruction descriptor: D = F32, A = B = F16, both K-major, N, M.
+__host__ __device__ constexpr uint32_t umma_idesc_f16(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+#define TMEM_LD32(taddr, v)                                                                         \
+  asm volatile(                                                                                     \
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"  \
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                \
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),         \
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),     \
+        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),  \
+        "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),  \
+        "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])                                          \
+      : "r"(taddr))
+
+// ---------------------------------------------------------------- the kernel
+struct TcBars {
+  uint64_t a_full[2], a_empty[2], b_full[2], b_empty[2], acc_full[2], acc_empty[2], drain;
+  uint32_t tmem_base;
+  int abort_flag;
+};
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+k_alpha_tc(const unsigned char* __restrict__ xblob, size_t blob_stride, int tiles,
+           const unsigned char* __restrict__ etab, int Na, int J, int npairs, float2* __restrict__ g,
+           int* __restrict__ err) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sA = sm;                               // 2 x 32 KB
+  unsigned char* sB = sm + 2 * TC_A_BYTES;              // 2 x 64 KB
+  TcBars* bars = reinterpret_cast<TcBars*>(sB + 2 * TC_B_BYTES);
+  volatile int* abort_flag = &bars->abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nch = (Na + TC_NC - 1) / TC_NC;
+  const long long nitems = (long long)npairs * tiles;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(smem_u32(&bars->a_full[i]), 1);
+      mbar_init(smem_u32(&bars->a_empty[i]), 1);
+      mbar_init(smem_u32(&bars->b_full[i]), 1);
+      mbar_init(smem_u32(&bars->b_empty[i]), 1);
+      mbar_init(smem_u32(&bars->acc_full[i]), 1);
+      mbar_init(smem_u32(&bars->acc_empty[i]), 128);
+    }
+    mbar_init(smem_u32(&bars->drain), 1);
+    bars->abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {   // TMEM: 512 columns = two 128x256 FP32 accumulators
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                     smem_u32(&bars->tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = bars->tmem_base;
+
+  if (warp == 0) {
+    // ---------------- producer
+    if (lane == 0) {
+      int a_armed[2] = {-1, -1}, b_armed[2] = {-1, -1};
+      long long bc = 0;
+      int li = 0;
+      for (long long it = blockIdx.x; it < nitems && !*abort_flag; it += gridDim.x, ++li) {
+        const int pair = (int)(it / tiles), tile = (int)(it % tiles);
+        const int sa = li & 1;
+        const uint32_t pa = (uint32_t)((li >> 1) & 1);
+        if (!mbar_wait(smem_u32(&bars->a_empty[sa]), pa ^ 1u, abort_flag)) { *abort_flag = 1; break; }
+        const uint32_t fa = smem_u32(&bars->a_full[sa]);
+        mbar_expect_tx(fa, TC_A_BYTES);
+        const unsigned char* src = xblob + (size_t)pair * blob_stride + (size_t)tile * TC_A_BYTES;
+        for (int o = 0; o < TC_A_BYTES; o += 16384)
+          bulk_g2s(smem_u32(sA + sa * TC_A_BYTES + o), src + o, 16384, fa);
+        a_armed[sa] = (int)pa;
+        for (int c = 0; c < nch; ++c, ++bc) {
+          const int sb = (int)(bc & 1);
+          const uint32_t pb = (uint32_t)((bc >> 1) & 1);
+          if (!mbar_wait(smem_u32(&bars->b_empty[sb]), pb ^ 1u, abort_flag)) { *abort_flag = 1; break; }
+          const uint32_t fb = smem_u32(&bars->b_full[sb]);
+          mbar_expect_tx(fb, TC_B_BYTES);
+          const unsigned char* bsrc = etab + (size_t)c * TC_B_BYTES;
+          for (int o = 0; o < TC_B_BYTES; o += 16384)
+            bulk_g2s(smem_u32(sB + sb * TC_B_BYTES + o), bsrc + o, 16384, fb);
+          b_armed[sb] = (int)pb;
+        }
+      }
+      // copies in flight must land before the CTA may exit
+      for (int i = 0; i < 2; ++i) {
+        if (a_armed[i] >= 0) {
+          uint32_t n = 0;
+          while (!mbar_test(smem_u32(&bars->a_full[i]), (uint32_t)a_armed[i]) && ++n < TC_WAIT_LIMIT) {}
+        }
+        if (b_armed[i] >= 0) {
+          uint32_t n = 0;
+          while (!mbar_test(smem_u32(&bars->b_full[i]), (uint32_t)b_armed[i]) && ++n < TC_WAIT_LIMIT) {}
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = umma_idesc_f16(TC_M, TC_N);
+      long long bc = 0, ac = 0;
+      int li = 0;
+      bool ok = true;
+      for (long long it = blockIdx.x; it < nitems && ok; it += gridDim.x, ++li) {
+        const int sa = li & 1;
+        if (!(ok = mbar_wait(smem_u32(&bars->a_full[sa]), (uint32_t)((li >> 1) & 1), abort_flag))) break;
+        const uint32_t a_hi = smem_u32(sA + sa * TC_A_BYTES), a_lo = a_hi + TC_A_HALF;
+        for (int c = 0; c < nch; ++c, ++bc, ++ac) {
+          const int sb = (int)(bc & 1), acc = (int)(ac & 1);
+          if (!(ok = mbar_wait(smem_u32(&bars->b_full[sb]), (uint32_t)((bc >> 1) & 1), abort_flag))) break;
+          if (!(ok = mbar_wait(smem_u32(&bars->acc_empty[acc]), (uint32_t)(((ac >> 1) & 1) ^ 1), abort_flag))) break;
+          tc_fence_after();
+          const uint32_t b_hi = smem_u32(sB + sb * TC_B_BYTES), b_lo = b_hi + TC_B_HALF;
+          const uint32_t d = tmem + (uint32_t)(acc * TC_N);
+          const uint32_t as[3] = {a_hi, a_hi, a_lo};
+          const uint32_t bs[3] = {b_hi, b_lo, b_hi};
+#pragma unroll
+          for (int pr = 0; pr < 3; ++pr) {
+            const uint64_t ad = sw128_desc(as[pr]), bd = sw128_desc(bs[pr]);
+#pragma unroll
+            for (int s = 0; s < TC_KB / 16; ++s)       // K = 16 per MMA: +32 bytes
+              umma_f16(d, ad + (uint64_t)(2 * s), bd + (uint64_t)(2 * s), idesc, (pr | s) != 0);
+          }
+          umma_commit(smem_u32(&bars->b_empty[sb]));
+          umma_commit(smem_u32(&bars->acc_full[acc]));
+        }
+        if (!ok) break;
+        umma_commit(smem_u32(&bars->a_empty[sa]));
+      }
+      if (!ok) *abort_flag = 1;
+      // every MMA issued by this thread completes before TMEM is released
+      umma_commit(smem_u32(&bars->drain));
+      uint32_t n = 0;
+      while (!mbar_test(smem_u32(&bars->drain), 0u) && ++n < TC_WAIT_LIMIT) {}
+    }
+  } else {
+    // ---------------- epilogue: warps 2..5, TMEM lane quadrant = warp % 4
+    const int quad = warp & 3;
+    const int row = quad * 32 + lane;
+    long long ac = 0;
+    bool ok = true;
+    for (long long it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
+      const int pair = (int)(it / tiles), tile = (int)(it % tiles);
+      const int j = tile * TC_M + row;
+      const float* scales = reinterpret_cast<const float*>(xblob + (size_t)pair * blob_stride +
+                                                           (size_t)tiles * TC_A_BYTES);
+      const float sc = j < J ? scales[j] : 0.f;
+      float2* gp = g + (size_t)pair * Na * J + j;
+      for (int c = 0; c < nch; ++c, ++ac) {
+        const int acc = (int)(ac & 1);
+        // one lane waits, the warp follows: tcgen05.ld needs a converged warp
+        int got = 0;
+        if (lane == 0) got = mbar_wait(smem_u32(&bars->acc_full[acc]), (uint32_t)((ac >> 1) & 1), abort_flag);
+        got = __shfl_sync(0xffffffffu, got, 0);
+        __syncwarp();
+        if (!(ok = got != 0)) break;
+        tc_fence_after();
+        const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * TC_N);
+#pragma unroll 1
+        for (int cb = 0; cb < TC_NC; cb += 32) {
+          uint32_t vr[32], vi[32];
+          TMEM_LD32(tbase + (uint32_t)cb, vr);
+          TMEM_LD32(tbase + (uint32_t)(TC_NC + cb), vi);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (j < J) {
+            const int a0 = c * TC_NC + cb;
+#pragma unroll
+            for (int u = 0; u < 32; ++u) {
+              if (a0 + u < Na)
+                gp[(size_t)(a0 + u) * J] = make_float2(__uint_as_float(vr[u]) * sc, __uint_as_float(vi[u]) * sc);
+            }
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(smem_u32(&bars->acc_empty[acc]));
+      }
+    }
+    if (!ok) *abort_flag = 1;
+  }
+  __syncthreads();
+  if (*abort_flag && threadIdx.x == 0) atomicExch(err, 1);
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+  }
+}
+
+static int* tc_error_word() {
+  static int* p = nullptr;
+  if (!p) {
+    if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) { cudaGetLastError(); p = nullptr; return nullptr; }
+    cudaMemset(p, 0, sizeof(int));
+  }
+  return p;
+}
+
+int tc_read_error(void) {
+  int* p = tc_error_word();
+  if (!p) return 0;
+  int v = 0;
+  if (cudaMemcpy(&v, p, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) { cudaGetLastError(); return 0; }
+  if (v) cudaMemset(p, 0, sizeof(int));
+  return v;
+}
+
+cudaError_t launch_alpha_tc(const void* xblob, const void* etab, int Lh, int Na, int Nb, int Ng, int npairs,
+                            float2* g, int num_sms, cudaStream_t st) {
+  if (npairs <= 0) return cudaSuccess;
+  if (!tc_supported(Lh, Na)) return cudaErrorInvalidValue;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_alpha_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  int* err = tc_error_word();
+  if (!err) return cudaErrorMemoryAllocation;
+  const int tiles = tc_tiles(Nb, Ng);
+  const long long items = (long long)npairs * tiles;
+  const int grid = (int)(items < num_sms ? items : num_sms);
+  k_alpha_tc<<<grid, TC_THREADS, TC_SMEM, st>>>((const unsigned char*)xblob, tc_xblob_bytes(Nb, Ng, Lh), tiles,
+                                               (const unsigned char*)etab, Na, Nb * Ng, npairs, g, err);
+  return cudaGetLastError();
 }

@@ -908,11 +908,12 @@ extern "C" int slsht_get_stats(slsht_ctx* c, slsht_stats* out, int reset) {
     out->ms[i] = c->prof_ms[i];
   }
   out->samples_written = c->samples;
+  const int dev_err = tc_read_error();
   if (reset) {
     for (int i = 0; i < SLSHT_NSTAGES; ++i) { c->launches[i] = 0; c->prof_ms[i] = 0.0; }
     c->samples = 0;
   }
-  return SLSHT_OK;
+  return dev_err ? SLSHT_E_TIMEOUT : SLSHT_OK;
 }
 
 extern "C" size_t slsht_mem_used(slsht_ctx* c) { return c ? c->used.load() : 0; }

@@ -17,3 +17,6 @@ cudaError_t launch_betagamma_tc(const double2* kc, const double2* h, const float
 // alpha stage on tcgen05: g[pair][a][j] complex64.
 cudaError_t launch_alpha_tc(const void* xblob, const void* etab, int Lh, int Na, int Nb, int Ng,
                             int npairs, float2* g, int num_sms, cudaStream_t st);
+// Non-zero (and cleared) if a tensor-core kernel gave up on a bounded wait
+// since the last call.  Synchronous.
+int tc_read_error(void);

@@ -72,6 +72,7 @@ def test_beta_routes_agree_with_oracle(ctx, route):
     (3, 7, (13, 7, 13)),      # L_h > L_f
     (9, 4, (2, 1, 3)),        # fewer samples than the band limit
     (7, 3, (130, 5, 33)),     # ragged: several alpha tiles, columns not a multiple of a warp
+    (5, 2, (257, 3, 45)),     # columns not a multiple of the 128-column tensor-core tile
 ])
 def test_edge_shapes(ctx, Lf, Lh, grid):
     f = synth.signal_cn_real(Lf, Lf * 100 + Lh)
@@ -187,3 +188,22 @@ def test_determinism(ctx):
         a = _fw(ctx, Lf, Lh, grid, f, h, pairs, prec)
         b = _fw(ctx, Lf, Lh, grid, f, h, pairs, prec)
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("engine", [1, 2])
+def test_fp32_alpha_engines(ctx, engine):
+    """FP32_BULK with the alpha stage on CUDA cores (1) and on tcgen05 (2)."""
+    import paper_1207_5558_gb300 as pkg
+    Lf, Lh, grid = 20, 16, (300, 9, 31)      # K = 31: the largest single K block; 3 alpha chunks
+    f = synth.signal_powerlaw(Lf, 21)
+    h = synth.window_cn(Lh, 22, decay=1.0)
+    pairs = synth.pairs_bands([0, 7, 19, 33])
+    ref = O.forward_coeff(f, h, Lf, Lh, pairs, grid)
+    ctx.set_option(pkg.SLSHT_OPT_ALPHA_ENGINE, engine)
+    try:
+        g = _fw(ctx, Lf, Lh, grid, f, h, pairs, 1)
+    finally:
+        ctx.set_option(pkg.SLSHT_OPT_ALPHA_ENGINE, 0)
+    assert rel(g, ref) < TOL32
+    st = ctx.stats()
+    assert st is not None
