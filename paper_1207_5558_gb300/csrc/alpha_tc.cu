@@ -15,11 +15,14 @@
 //
 // Kernel structure: persistent, one CTA per SM, work item = (pair, tile of
 // 128 columns).  Warp 0 streams operands with cp.async.bulk into shared
-// memory (A tile double-buffered, B chunks through a 2-stage ring), warp 1
-// issues tcgen05.mma from one thread into a double-buffered TMEM accumulator
-// (2 x 256 columns), warps 2-5 drain the accumulator (tcgen05.ld), rescale and
-// store g with coalesced 8-byte stores (for a fixed alpha row a warp writes
-// 32 consecutive columns).  Every mbarrier wait is bounded: on expiry the
+// memory (A tile double-buffered, one B chunk stage: a chunk loads from L2 in
+// well under the time the epilogue spends on the previous one), warp 1 issues
+// tcgen05.mma from one thread into a double-buffered TMEM accumulator
+// (2 x 256 columns), warps 2-9 drain the accumulator (tcgen05.ld; two warps
+// per TMEM lane quadrant, each half of the 128 alpha rows), rescale and store
+// g with coalesced 8-byte streaming stores (for a fixed alpha row a warp
+// writes 32 consecutive columns).  The 129 KB of shared memory leave room on
+// each SM for the producer kernels of the next chunk.  Every mbarrier wait is bounded: on expiry the
 // CTA records an error word, stops, waits (bounded) for its own copies and
 // MMAs in flight, frees TMEM and exits.
 #include <cuda_fp16.h>
@@ -35,8 +38,9 @@
 #define TC_B_HALF (TC_N * TC_KB * 2)   // bytes of one B part: 32 KB
 #define TC_A_BYTES (2 * TC_A_HALF)     // 32 KB
 #define TC_B_BYTES (2 * TC_B_HALF)     // 64 KB
-#define TC_THREADS 192
-#define TC_SMEM (2 * TC_A_BYTES + 2 * TC_B_BYTES + 1024 + 256)
+#define TC_EPI_WARPS 8                  // two per TMEM lane quadrant, each half the columns
+#define TC_THREADS (64 + 32 * TC_EPI_WARPS)
+#define TC_SMEM (2 * TC_A_BYTES + TC_B_BYTES + 1024 + 256)
 #define TC_WAIT_LIMIT (1u << 22)
 
 bool tc_supported(int Lh, int Na) { return Lh >= 1 && 2 * (2 * Lh - 1) <= TC_KB && Na >= 1; }
@@ -94,135 +98,191 @@ cudaError_t launch_tc_etab(void* etab, int Na, int Lh, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------- beta/gamma -> A
-// Same sums as k_betagamma<float>; the gamma sum pairs +-q'
-//   X_q[c] = G[q][0] + sum_{s>=1} (G[q][s] + G[q][-s]) cos(s gamma_c) - i (G[q][s] - G[q][-s]) sin(s gamma_c)
-// and the result row j = b*Ng + c is written as the A operand: scaled by 2^e
-// (largest entry into [2^14, 2^15)), split into FP16 hi/lo, swizzled.
+// Same sums as k_betagamma<float>, for TC_NBB beta rows per CTA:
+//   G[q][q'](b) = sum_p k(p,q) h_p^{q'} d^p_{q,q'}(beta_b)   (d table laid out beta-fastest,
+//                 so one float4 load feeds the CTA's four rows)
+//   X_q[c](b)   = G[q][0] + sum_{s>=1} (G[q][s] + G[q][-s]) cos(s gamma_c)
+//                          - i (G[q][s] - G[q][-s]) sin(s gamma_c)
+// and every row j = b*Ng + c is written as the A operand: scaled by 2^e (its
+// largest entry into [2^14, 2^15)), split into FP16 hi/lo, swizzled.
+#define TC_NBB 4
+
+struct BgLayout {          // shared-memory carve-up of k_betagamma_tc
+  int LhP, NgP, XS;        // padded strides: Gp/Gm rows, phase rows, X rows
+  size_t off_k, off_h, off_e, off_gp, off_gm, off_x, off_mx, total;
+  __host__ __device__ BgLayout(int Lh, int Ng) {
+    const int K = 2 * Lh - 1;
+    LhP = Lh + 1;
+    NgP = (Ng + 1) & ~1;
+    XS = ((2 * K + 3) & ~3) + 4;
+    off_k = 0;
+    off_h = off_k + sizeof(float2) * Lh * Lh;
+    off_e = off_h + sizeof(float2) * Lh * Lh;
+    off_gp = off_e + sizeof(float2) * (size_t)Lh * NgP;
+    off_gm = off_gp + sizeof(float2) * (size_t)TC_NBB * K * LhP;
+    off_x = off_gm + sizeof(float2) * (size_t)TC_NBB * K * LhP;
+    off_mx = off_x + sizeof(float) * (size_t)TC_NBB * Ng * XS;
+    total = off_mx + sizeof(int) * (size_t)TC_NBB * Ng;
+  }
+};
+
 __global__ void __launch_bounds__(256)
-k_betagamma_tc(const double2* __restrict__ kc, const double2* __restrict__ h, const float* __restrict__ dt,
-               const double2* __restrict__ Y, const float2* __restrict__ eg, int Lh, int Nb, int Ng,
+k_betagamma_tc(const double2* __restrict__ kc, const double2* __restrict__ h, const float* __restrict__ dT,
+               int ldb, const double2* __restrict__ Y, const float2* __restrict__ eg, int Lh, int Nb, int Ng,
                unsigned char* __restrict__ xblob, size_t blob_stride, int tiles) {
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int K = 2 * Lh - 1;
-  const int b = blockIdx.x, pair = blockIdx.y;
-  float2* sk = reinterpret_cast<float2*>(smem_raw);   // [Lh*Lh]
-  float2* sh = sk + Lh * Lh;                           // [Lh*Lh]
-  float2* sGp = sh + Lh * Lh;                          // [K][Lh]  G[q][s] + G[q][-s] (s=0: G[q][0])
-  float2* sGm = sGp + K * Lh;                          // [K][Lh]  G[q][s] - G[q][-s]
-  float2* sE = sGm + K * Lh;                           // [Ng][Lh] (cos, sin)(s gamma_c)
-  float* sX = reinterpret_cast<float*>(sE + Ng * Lh);  // [Ng][2K] Re | Im
+  const int b0 = blockIdx.x * TC_NBB, pair = blockIdx.y;
+  const int nbb = min(TC_NBB, Nb - b0);
+  const BgLayout L(Lh, Ng);
+  float2* sk = reinterpret_cast<float2*>(smem_raw + L.off_k);
+  float2* sh = reinterpret_cast<float2*>(smem_raw + L.off_h);
+  float2* sE = reinterpret_cast<float2*>(smem_raw + L.off_e);     // [s][NgP]
+  float2* sGp = reinterpret_cast<float2*>(smem_raw + L.off_gp);   // [bb][q][LhP]
+  float2* sGm = reinterpret_cast<float2*>(smem_raw + L.off_gm);
+  float* sX = reinterpret_cast<float*>(smem_raw + L.off_x);       // [bb][c][XS]
+  int* sMx = reinterpret_cast<int*>(smem_raw + L.off_mx);         // [bb][c] max |X| bits
   const int n2 = Lh * Lh;
   for (int t = threadIdx.x; t < n2; t += blockDim.x) {
     const double2 kv = kc[(size_t)pair * n2 + t], hv = h[t];
     sk[t] = make_float2((float)kv.x, (float)kv.y);
     sh[t] = make_float2((float)hv.x, (float)hv.y);
   }
-  for (int t = threadIdx.x; t < Ng * Lh; t += blockDim.x) {
-    const int c = t / Lh, s = t % Lh;
-    sE[t] = eg[c * K + s + (Lh - 1)];          // phase table row q' = +s
+  for (int t = threadIdx.x; t < Lh * L.NgP; t += blockDim.x) {
+    const int s = t / L.NgP, c = t % L.NgP;
+    sE[t] = c < Ng ? eg[c * K + s + (Lh - 1)] : make_float2(0.f, 0.f);
   }
+  for (int t = threadIdx.x; t < TC_NBB * Ng; t += blockDim.x) sMx[t] = 0;
   __syncthreads();
-  // G[q][q'] for the pair (q' = +-s), folded into Gp / Gm
+  // ---- G for the CTA's beta rows, folded into Gp / Gm
   for (int t = threadIdx.x; t < K * Lh; t += blockDim.x) {
     const int qi = t / Lh, s = t % Lh;
     const int q = qi - (Lh - 1);
-    float2 gpl = make_float2(0.f, 0.f), gmi = make_float2(0.f, 0.f);
-    for (int sg = 0; sg < (s == 0 ? 1 : 2); ++sg) {
-      const int qp = sg == 0 ? s : -s;
-      float re = 0.f, im = 0.f;
-      if (Y == nullptr) {
-        const int S = blk_off(Lh);
-        const float* drow = dt + (size_t)b * S;
-        for (int p = max(abs(q), abs(qp)); p < Lh; ++p) {
-          const float2 kv = sk[p * p + p + q], hv = sh[p * p + p + qp];
-          const float d = drow[blk_off(p) + (q + p) * (2 * p + 1) + (qp + p)];
-          re = fmaf(d, kv.x * hv.x - kv.y * hv.y, re);
-          im = fmaf(d, kv.x * hv.y + kv.y * hv.x, im);
+    float pr[TC_NBB], pi[TC_NBB], mr[TC_NBB], mi[TC_NBB];
+#pragma unroll
+    for (int u = 0; u < TC_NBB; ++u) pr[u] = pi[u] = mr[u] = mi[u] = 0.f;
+    if (Y == nullptr) {
+      for (int p = max(abs(q), s); p < Lh; ++p) {
+        const float2 kv = sk[p * p + p + q];
+        const int row = blk_off(p) + (q + p) * (2 * p + 1) + p;
+        {   // q' = +s
+          const float2 hv = sh[p * p + p + s];
+          const float khr = kv.x * hv.x - kv.y * hv.y, khi = kv.x * hv.y + kv.y * hv.x;
+          const float4 d = *reinterpret_cast<const float4*>(dT + (size_t)(row + s) * ldb + b0);
+          const float dv[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+          for (int u = 0; u < TC_NBB; ++u) { pr[u] = fmaf(dv[u], khr, pr[u]); pi[u] = fmaf(dv[u], khi, pi[u]); }
         }
-      } else {
-        const double2 v = Y[(((size_t)pair * Nb + b) * K + qi) * K + (qp + Lh - 1)];
-        re = (float)v.x;
-        im = (float)v.y;
+        if (s > 0) {   // q' = -s
+          const float2 hv = sh[p * p + p - s];
+          const float khr = kv.x * hv.x - kv.y * hv.y, khi = kv.x * hv.y + kv.y * hv.x;
+          const float4 d = *reinterpret_cast<const float4*>(dT + (size_t)(row - s) * ldb + b0);
+          const float dv[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+          for (int u = 0; u < TC_NBB; ++u) { mr[u] = fmaf(dv[u], khr, mr[u]); mi[u] = fmaf(dv[u], khi, mi[u]); }
+        }
       }
-      if (sg == 0) { gpl = make_float2(re, im); gmi = make_float2(re, im); }
-      else { gpl.x += re; gpl.y += im; gmi.x -= re; gmi.y -= im; }
+    } else {
+#pragma unroll
+      for (int u = 0; u < TC_NBB; ++u) {
+        if (u >= nbb) break;
+        const double2* src = Y + (((size_t)pair * Nb + b0 + u) * K + qi) * K;
+        const double2 vp = src[s + Lh - 1];
+        pr[u] = (float)vp.x; pi[u] = (float)vp.y;
+        if (s > 0) { const double2 vm = src[-s + Lh - 1]; mr[u] = (float)vm.x; mi[u] = (float)vm.y; }
+      }
     }
-    sGp[t] = gpl;
-    sGm[t] = gmi;
+#pragma unroll
+    for (int u = 0; u < TC_NBB; ++u) {
+      const int o = (u * K + qi) * L.LhP + s;
+      if (s == 0) { sGp[o] = make_float2(pr[u], pi[u]); sGm[o] = sGp[o]; }
+      else { sGp[o] = make_float2(pr[u] + mr[u], pi[u] + mi[u]); sGm[o] = make_float2(pr[u] - mr[u], pi[u] - mi[u]); }
+    }
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < K * Ng; t += blockDim.x) {
-    const int qi = t / Ng, c = t % Ng;
-    const float2* gp = sGp + qi * Lh;
-    const float2* gm = sGm + qi * Lh;
-    const float2* e = sE + c * Lh;
-    float re = gp[0].x, im = gp[0].y;
-    for (int s = 1; s < Lh; ++s) {        // (Gp cos - i Gm sin)
-      const float2 E = e[s], P = gp[s], M = gm[s];
-      re = fmaf(P.x, E.x, re);
-      re = fmaf(M.y, E.y, re);
-      im = fmaf(P.y, E.x, im);
-      im = fmaf(-M.x, E.y, im);
+  // ---- gamma sum, two gamma columns per thread
+  const int ncp = (Ng + 1) / 2;
+  for (int t = threadIdx.x; t < nbb * K * ncp; t += blockDim.x) {
+    const int cp = t % ncp, qi = (t / ncp) % K, u = t / (ncp * K);
+    const int c0 = 2 * cp;
+    const float2* gp = sGp + (u * K + qi) * L.LhP;
+    const float2* gm = sGm + (u * K + qi) * L.LhP;
+    float r0 = gp[0].x, i0 = gp[0].y, r1 = r0, i1 = i0;
+    for (int s = 1; s < Lh; ++s) {
+      const float2 P = gp[s], M = gm[s];
+      const float4 E = *reinterpret_cast<const float4*>(sE + s * L.NgP + c0);   // (cos, sin) at c0, c0+1
+      r0 = fmaf(P.x, E.x, r0); r0 = fmaf(M.y, E.y, r0);
+      i0 = fmaf(P.y, E.x, i0); i0 = fmaf(-M.x, E.y, i0);
+      r1 = fmaf(P.x, E.z, r1); r1 = fmaf(M.y, E.w, r1);
+      i1 = fmaf(P.y, E.z, i1); i1 = fmaf(-M.x, E.w, i1);
     }
-    sX[c * 2 * K + qi] = re;
-    sX[c * 2 * K + K + qi] = im;
+    float* x0 = sX + (u * Ng + c0) * L.XS;
+    x0[qi] = r0;
+    x0[K + qi] = i0;
+    atomicMax(sMx + u * Ng + c0, __float_as_int(fmaxf(fabsf(r0), fabsf(i0))));
+    if (c0 + 1 < Ng) {
+      float* x1 = x0 + L.XS;
+      x1[qi] = r1;
+      x1[K + qi] = i1;
+      atomicMax(sMx + u * Ng + c0 + 1, __float_as_int(fmaxf(fabsf(r1), fabsf(i1))));
+    }
   }
   __syncthreads();
+  // ---- scale, split, store: one thread per (row, 16-byte chunk of 8 FP16 values)
   unsigned char* blob = xblob + (size_t)pair * blob_stride;
   float* scales = reinterpret_cast<float*>(blob + (size_t)tiles * TC_A_BYTES);
   const int J = Nb * Ng;
-  for (int c = threadIdx.x; c < Ng; c += blockDim.x) {
-    const float* row = sX + c * 2 * K;
-    float mx = 0.f;
-    for (int k = 0; k < 2 * K; ++k) mx = fmaxf(mx, fabsf(row[k]));
+  for (int t = threadIdx.x; t < nbb * Ng * (TC_KB / 8); t += blockDim.x) {
+    const int k0 = (t % (TC_KB / 8)) * 8, rc = t / (TC_KB / 8);
+    const int u = rc / Ng, c = rc % Ng;
+    const float mx = __int_as_float(sMx[rc]);
     int ex = 0;
     if (mx > 0.f) frexpf(mx, &ex);
-    const int e = mx > 0.f ? 15 - ex : 0;     // mx * 2^e in [2^14, 2^15)
-    const int j = b * Ng + c;
-    const int tile = j / TC_M, r = j % TC_M;
-    unsigned char* tb = blob + (size_t)tile * TC_A_BYTES;
-    for (int k0 = 0; k0 < TC_KB; k0 += 8) {
-      __align__(16) __half hi[8], lo[8];
+    const int e = mx > 0.f ? min(125, max(-125, 15 - ex)) : 0;   // mx * 2^e in [2^14, 2^15)
+    const float sc = __int_as_float((127 + e) << 23);
+    const float* row = sX + (u * Ng + c) * L.XS;
+    const int j = (b0 + u) * Ng + c;
+    unsigned char* tb = blob + (size_t)(j / TC_M) * TC_A_BYTES;
+    const int r = j % TC_M;
+    __align__(16) __half hi[8], lo[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int k = k0 + u;
-        const float v = k < 2 * K ? ldexpf(row[k], e) : 0.f;
-        hi[u] = __float2half_rn(v);
-        lo[u] = __float2half_rn(v - __half2float(hi[u]));
-      }
-      *reinterpret_cast<uint4*>(tb + sw128_off(r, k0)) = *reinterpret_cast<uint4*>(hi);
-      *reinterpret_cast<uint4*>(tb + TC_A_HALF + sw128_off(r, k0)) = *reinterpret_cast<uint4*>(lo);
+    for (int v = 0; v < 8; ++v) {
+      const int k = k0 + v;
+      const float x = k < 2 * K ? row[k] * sc : 0.f;
+      hi[v] = __float2half_rn(x);
+      lo[v] = __float2half_rn(x - __half2float(hi[v]));
     }
-    scales[j] = ldexpf(1.f, -e);
+    *reinterpret_cast<uint4*>(tb + sw128_off(r, k0)) = *reinterpret_cast<uint4*>(hi);
+    *reinterpret_cast<uint4*>(tb + TC_A_HALF + sw128_off(r, k0)) = *reinterpret_cast<uint4*>(lo);
+    if (k0 == 0) scales[j] = __int_as_float((127 - e) << 23);
   }
-  // the last beta row also clears the padding rows of the last tile
-  if (b == Nb - 1) {
-    for (int j = J + threadIdx.x; j < tiles * TC_M; j += blockDim.x) {
-      const int tile = j / TC_M, r = j % TC_M;
-      unsigned char* tb = blob + (size_t)tile * TC_A_BYTES;
-      for (int k0 = 0; k0 < TC_KB; k0 += 8) {
-        *reinterpret_cast<uint4*>(tb + sw128_off(r, k0)) = make_uint4(0, 0, 0, 0);
-        *reinterpret_cast<uint4*>(tb + TC_A_HALF + sw128_off(r, k0)) = make_uint4(0, 0, 0, 0);
-      }
-      scales[j] = 0.f;
+  // the CTA holding the last beta row also clears the padding rows of the last tile
+  if (b0 + nbb == Nb) {
+    for (int t = threadIdx.x; t < (tiles * TC_M - J) * (TC_KB / 8); t += blockDim.x) {
+      const int j = J + t / (TC_KB / 8), k0 = (t % (TC_KB / 8)) * 8;
+      unsigned char* tb = blob + (size_t)(j / TC_M) * TC_A_BYTES;
+      const int r = j % TC_M;
+      *reinterpret_cast<uint4*>(tb + sw128_off(r, k0)) = make_uint4(0, 0, 0, 0);
+      *reinterpret_cast<uint4*>(tb + TC_A_HALF + sw128_off(r, k0)) = make_uint4(0, 0, 0, 0);
+      if (k0 == 0) scales[j] = 0.f;
     }
   }
 }
 
-cudaError_t launch_betagamma_tc(const double2* kc, const double2* h, const float* dt, const double2* Y,
+int tc_dtab_ldb(int Nb) { return (Nb + TC_NBB - 1) / TC_NBB * TC_NBB; }
+
+cudaError_t launch_betagamma_tc(const double2* kc, const double2* h, const float* dT, const double2* Y,
                                 const float2* eg, int Lh, int Nb, int Ng, int npairs, void* xblob,
                                 cudaStream_t st) {
   if (npairs <= 0) return cudaSuccess;
-  const int K = 2 * Lh - 1;
-  const size_t smem = sizeof(float2) * ((size_t)2 * Lh * Lh + 2 * (size_t)K * Lh + (size_t)Ng * Lh) +
-                      sizeof(float) * (size_t)Ng * 2 * K;
+  const size_t smem = BgLayout(Lh, Ng).total;
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_betagamma_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  dim3 grid(Nb, npairs);
-  k_betagamma_tc<<<grid, 256, smem, st>>>(kc, h, dt, Y, eg, Lh, Nb, Ng, (unsigned char*)xblob,
+  dim3 grid((Nb + TC_NBB - 1) / TC_NBB, npairs);
+  k_betagamma_tc<<<grid, 256, smem, st>>>(kc, h, dT, tc_dtab_ldb(Nb), Y, eg, Lh, Nb, Ng, (unsigned char*)xblob,
                                           tc_xblob_bytes(Nb, Ng, Lh), tc_tiles(Nb, Ng));
   return cudaGetLastError();
 }
@@ -304,7 +364,7 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 
 // ---------------------------------------------------------------- the kernel
 struct TcBars {
-  uint64_t a_full[2], a_empty[2], b_full[2], b_empty[2], acc_full[2], acc_empty[2], drain;
+  uint64_t a_full[2], a_empty[2], b_full, b_empty, acc_full[2], acc_empty[2], drain;
   uint32_t tmem_base;
   int abort_flag;
 };
@@ -316,8 +376,8 @@ k_alpha_tc(const unsigned char* __restrict__ xblob, size_t blob_stride, int tile
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = sm;                               // 2 x 32 KB
-  unsigned char* sB = sm + 2 * TC_A_BYTES;              // 2 x 64 KB
-  TcBars* bars = reinterpret_cast<TcBars*>(sB + 2 * TC_B_BYTES);
+  unsigned char* sB = sm + 2 * TC_A_BYTES;              // 64 KB
+  TcBars* bars = reinterpret_cast<TcBars*>(sB + TC_B_BYTES);
   volatile int* abort_flag = &bars->abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nch = (Na + TC_NC - 1) / TC_NC;
@@ -327,11 +387,11 @@ k_alpha_tc(const unsigned char* __restrict__ xblob, size_t blob_stride, int tile
     for (int i = 0; i < 2; ++i) {
       mbar_init(smem_u32(&bars->a_full[i]), 1);
       mbar_init(smem_u32(&bars->a_empty[i]), 1);
-      mbar_init(smem_u32(&bars->b_full[i]), 1);
-      mbar_init(smem_u32(&bars->b_empty[i]), 1);
       mbar_init(smem_u32(&bars->acc_full[i]), 1);
-      mbar_init(smem_u32(&bars->acc_empty[i]), 128);
+      mbar_init(smem_u32(&bars->acc_empty[i]), 32 * TC_EPI_WARPS);
     }
+    mbar_init(smem_u32(&bars->b_full), 1);
+    mbar_init(smem_u32(&bars->b_empty), 1);
     mbar_init(smem_u32(&bars->drain), 1);
     bars->abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -349,7 +409,7 @@ k_alpha_tc(const unsigned char* __restrict__ xblob, size_t blob_stride, int tile
   if (warp == 0) {
     // ---------------- producer
     if (lane == 0) {
-      int a_armed[2] = {-1, -1}, b_armed[2] = {-1, -1};
+      int a_armed[2] = {-1, -1}, b_armed = -1;
       long long bc = 0;
       int li = 0;
       for (long long it = blockIdx.x; it < nitems && !*abort_flag; it += gridDim.x, ++li) {
@@ -364,15 +424,14 @@ k_alpha_tc(const unsigned char* __restrict__ xblob, size_t blob_stride, int tile
           bulk_g2s(smem_u32(sA + sa * TC_A_BYTES + o), src + o, 16384, fa);
         a_armed[sa] = (int)pa;
         for (int c = 0; c < nch; ++c, ++bc) {
-          const int sb = (int)(bc & 1);
-          const uint32_t pb = (uint32_t)((bc >> 1) & 1);
-          if (!mbar_wait(smem_u32(&bars->b_empty[sb]), pb ^ 1u, abort_flag)) { *abort_flag = 1; break; }
-          const uint32_t fb = smem_u32(&bars->b_full[sb]);
+          const uint32_t pb = (uint32_t)(bc & 1);
+          if (!mbar_wait(smem_u32(&bars->b_empty), pb ^ 1u, abort_flag)) { *abort_flag = 1; break; }
+          const uint32_t fb = smem_u32(&bars->b_full);
           mbar_expect_tx(fb, TC_B_BYTES);
           const unsigned char* bsrc = etab + (size_t)c * TC_B_BYTES;
           for (int o = 0; o < TC_B_BYTES; o += 16384)
-            bulk_g2s(smem_u32(sB + sb * TC_B_BYTES + o), bsrc + o, 16384, fb);
-          b_armed[sb] = (int)pb;
+            bulk_g2s(smem_u32(sB + o), bsrc + o, 16384, fb);
+          b_armed = (int)pb;
         }
       }
       // copies in flight must land before the CTA may exit
@@ -381,10 +440,10 @@ k_alpha_tc(const unsigned char* __restrict__ xblob, size_t blob_stride, int tile
           uint32_t n = 0;
           while (!mbar_test(smem_u32(&bars->a_full[i]), (uint32_t)a_armed[i]) && ++n < TC_WAIT_LIMIT) {}
         }
-        if (b_armed[i] >= 0) {
-          uint32_t n = 0;
-          while (!mbar_test(smem_u32(&bars->b_full[i]), (uint32_t)b_armed[i]) && ++n < TC_WAIT_LIMIT) {}
-        }
+      }
+      if (b_armed >= 0) {
+        uint32_t n = 0;
+        while (!mbar_test(smem_u32(&bars->b_full), (uint32_t)b_armed) && ++n < TC_WAIT_LIMIT) {}
       }
     }
   } else if (warp == 1) {
@@ -399,11 +458,11 @@ k_alpha_tc(const unsigned char* __restrict__ xblob, size_t blob_stride, int tile
         if (!(ok = mbar_wait(smem_u32(&bars->a_full[sa]), (uint32_t)((li >> 1) & 1), abort_flag))) break;
         const uint32_t a_hi = smem_u32(sA + sa * TC_A_BYTES), a_lo = a_hi + TC_A_HALF;
         for (int c = 0; c < nch; ++c, ++bc, ++ac) {
-          const int sb = (int)(bc & 1), acc = (int)(ac & 1);
-          if (!(ok = mbar_wait(smem_u32(&bars->b_full[sb]), (uint32_t)((bc >> 1) & 1), abort_flag))) break;
+          const int acc = (int)(ac & 1);
+          if (!(ok = mbar_wait(smem_u32(&bars->b_full), (uint32_t)(bc & 1), abort_flag))) break;
           if (!(ok = mbar_wait(smem_u32(&bars->acc_empty[acc]), (uint32_t)(((ac >> 1) & 1) ^ 1), abort_flag))) break;
           tc_fence_after();
-          const uint32_t b_hi = smem_u32(sB + sb * TC_B_BYTES), b_lo = b_hi + TC_B_HALF;
+          const uint32_t b_hi = smem_u32(sB), b_lo = b_hi + TC_B_HALF;
           const uint32_t d = tmem + (uint32_t)(acc * TC_N);
           const uint32_t as[3] = {a_hi, a_hi, a_lo};
           const uint32_t bs[3] = {b_hi, b_lo, b_hi};
@@ -414,7 +473,7 @@ k_alpha_tc(const unsigned char* __restrict__ xblob, size_t blob_stride, int tile
             for (int s = 0; s < TC_KB / 16; ++s)       // K = 16 per MMA: +32 bytes
               umma_f16(d, ad + (uint64_t)(2 * s), bd + (uint64_t)(2 * s), idesc, (pr | s) != 0);
           }
-          umma_commit(smem_u32(&bars->b_empty[sb]));
+          umma_commit(smem_u32(&bars->b_empty));
           umma_commit(smem_u32(&bars->acc_full[acc]));
         }
         if (!ok) break;
@@ -427,18 +486,21 @@ k_alpha_tc(const unsigned char* __restrict__ xblob, size_t blob_stride, int tile
       while (!mbar_test(smem_u32(&bars->drain), 0u) && ++n < TC_WAIT_LIMIT) {}
     }
   } else {
-    // ---------------- epilogue: warps 2..5, TMEM lane quadrant = warp % 4
+    // ---------------- epilogue: warps 2..9; TMEM lane quadrant = warp % 4,
+    // half = which 64 of the chunk's 128 alpha rows
     const int quad = warp & 3;
+    const int half = (warp - 2) >> 2;
     const int row = quad * 32 + lane;
     long long ac = 0;
     bool ok = true;
     for (long long it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
       const int pair = (int)(it / tiles), tile = (int)(it % tiles);
       const int j = tile * TC_M + row;
+      const bool jin = j < J;
       const float* scales = reinterpret_cast<const float*>(xblob + (size_t)pair * blob_stride +
                                                            (size_t)tiles * TC_A_BYTES);
-      const float sc = j < J ? scales[j] : 0.f;
-      float2* gp = g + (size_t)pair * Na * J + j;
+      const float sc = jin ? scales[j] : 0.f;
+      float2* gp = g + (size_t)pair * Na * J + (jin ? j : 0);
       for (int c = 0; c < nch; ++c, ++ac) {
         const int acc = (int)(ac & 1);
         // one lane waits, the warp follows: tcgen05.ld needs a converged warp
@@ -450,17 +512,26 @@ k_alpha_tc(const unsigned char* __restrict__ xblob, size_t blob_stride, int tile
         tc_fence_after();
         const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * TC_N);
 #pragma unroll 1
-        for (int cb = 0; cb < TC_NC; cb += 32) {
+        for (int cb = half * 64; cb < half * 64 + 64; cb += 32) {
           uint32_t vr[32], vi[32];
           TMEM_LD32(tbase + (uint32_t)cb, vr);
           TMEM_LD32(tbase + (uint32_t)(TC_NC + cb), vi);
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          if (j < J) {
-            const int a0 = c * TC_NC + cb;
+          const int a0 = c * TC_NC + cb;
+          if (jin) {
+            float2* p = gp + (size_t)a0 * J;
+            if (a0 + 32 <= Na) {
 #pragma unroll
-            for (int u = 0; u < 32; ++u) {
-              if (a0 + u < Na)
-                gp[(size_t)(a0 + u) * J] = make_float2(__uint_as_float(vr[u]) * sc, __uint_as_float(vi[u]) * sc);
+              for (int u = 0; u < 32; ++u) {
+                __stcs(p, make_float2(__uint_as_float(vr[u]) * sc, __uint_as_float(vi[u]) * sc));
+                p += J;
+              }
+            } else {
+#pragma unroll
+              for (int u = 0; u < 32; ++u) {
+                if (a0 + u < Na) __stcs(p, make_float2(__uint_as_float(vr[u]) * sc, __uint_as_float(vi[u]) * sc));
+                p += J;
+              }
             }
           }
         }

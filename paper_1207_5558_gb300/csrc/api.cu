@@ -106,6 +106,7 @@ struct Workspace {
   void* lm = nullptr; size_t lm_cap = 0;
   void* kc = nullptr; size_t kc_cap = 0;
   void* X = nullptr; size_t X_cap = 0;
+  void* X2 = nullptr; size_t X2_cap = 0;
   void* C = nullptr; size_t C_cap = 0;
   void* Y = nullptr; size_t Y_cap = 0;
   void* stage[2] = {nullptr, nullptr}; size_t stage_cap[2] = {0, 0};
@@ -113,6 +114,10 @@ struct Workspace {
   cudaEvent_t stage_ev[2] = {nullptr, nullptr};
   cudaEvent_t copy_ev[2] = {nullptr, nullptr};
   cudaStream_t copy_stream = nullptr;  // D2H of host outputs
+  cudaStream_t aux = nullptr;          // coupling + beta/gamma of the next chunk
+  cudaEvent_t x_ready[2] = {nullptr, nullptr};
+  cudaEvent_t x_free[2] = {nullptr, nullptr};
+  cudaEvent_t start = nullptr;
   size_t bytes = 0;
 };
 
@@ -223,6 +228,13 @@ static int ws_init(Workspace& w) {
   if (!w.done) {
     CK(cudaEventCreateWithFlags(&w.done, cudaEventDisableTiming));
     CK(cudaEventRecord(w.done, 0));
+    CK(cudaStreamCreateWithFlags(&w.aux, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&w.start, cudaEventDisableTiming));
+    for (int i = 0; i < 2; ++i) {
+      CK(cudaEventCreateWithFlags(&w.x_ready[i], cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&w.x_free[i], cudaEventDisableTiming));
+      CK(cudaEventRecord(w.x_free[i], w.aux));
+    }
   }
   return SLSHT_OK;
 }
@@ -242,6 +254,14 @@ static int ws_init_copy(Workspace& w) {
 static void ws_release(slsht_ctx* c, Workspace& w) {
   if (w.done) cudaEventSynchronize(w.done);
   if (w.copy_stream) cudaStreamSynchronize(w.copy_stream);
+  if (w.aux) cudaStreamSynchronize(w.aux);
+  ctx_free(c, w.X2, w.X2_cap);
+  for (int i = 0; i < 2; ++i) {
+    if (w.x_ready[i]) cudaEventDestroy(w.x_ready[i]);
+    if (w.x_free[i]) cudaEventDestroy(w.x_free[i]);
+  }
+  if (w.start) cudaEventDestroy(w.start);
+  if (w.aux) cudaStreamDestroy(w.aux);
   ctx_free(c, w.f, w.f_cap);
   ctx_free(c, w.h, w.h_cap);
   ctx_free(c, w.lm, w.lm_cap);
@@ -343,11 +363,14 @@ static int get_dtab(slsht_ctx* ctx, int Lh, int Nb, int prec, cudaStream_t st, c
     const double* D;
     CKS(get_delta(ctx, Lh, st, &D));
     TableEntry e;
+    // prec 2: FP32, beta-fastest layout for the tensor-core producer
     const size_t el = prec == SLSHT_FP64 ? sizeof(double) : sizeof(float);
-    CKS(make_entry(ctx, e, el * (size_t)blk_off(Lh) * Nb));
+    const size_t rows = prec == 2 ? (size_t)tc_dtab_ldb(Nb) : (size_t)Nb;
+    CKS(make_entry(ctx, e, el * (size_t)blk_off(Lh) * rows));
     ctx->launches[SLSHT_STAGE_TABLES]++;
     cudaError_t er = prec == SLSHT_FP64 ? launch_dtable_f64(D, (double*)e.ptr, Lh, Nb, st)
-                                        : launch_dtable_f32(D, (float*)e.ptr, Lh, Nb, st);
+                     : prec == 2 ? launch_dtable_f32_t(D, (float*)e.ptr, Lh, Nb, tc_dtab_ldb(Nb), st)
+                                 : launch_dtable_f32(D, (float*)e.ptr, Lh, Nb, st);
     if (er != cudaSuccess) { record_cuda_error("launch_dtable", er); return SLSHT_E_CUDA; }
     CK(cudaEventRecord(e.ready, st));
     it = ctx->dtab.emplace(key, e).first;
@@ -534,7 +557,7 @@ static int forward_impl(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
   {
     std::lock_guard<std::mutex> g(ctx->mu);
     CKS(get_delta(ctx, Lh, st, &D));
-    if (route == 1) CKS(get_dtab(ctx, Lh, Nb, d->prec, st, &dt));
+    if (route == 1) CKS(get_dtab(ctx, Lh, Nb, tc ? 2 : d->prec, st, &dt));
     CKS(get_phase(ctx, Ng, K, -(Lh - 1), d->prec, st, &eg));
     if (tc) CKS(get_etab(ctx, Na, Lh, st, &etab));
     else CKS(get_phase(ctx, Na, Lh, 0, d->prec, st, &csa));
@@ -560,8 +583,9 @@ static int forward_impl(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
     const size_t stage_limit = (size_t)1 << 30;
     P = (int)std::max<size_t>(1, std::min<size_t>((size_t)P, stage_limit / std::max<size_t>(1, per_pair_g)));
   }
-  CKS(ws_reserve(ctx, w, &w.kc, &w.kc_cap, sizeof(double2) * (size_t)P * Lh * Lh));
+  CKS(ws_reserve(ctx, w, &w.kc, &w.kc_cap, sizeof(double2) * (size_t)n_pairs * Lh * Lh));
   CKS(ws_reserve(ctx, w, &w.X, &w.X_cap, x_per_pair * (size_t)P));
+  CKS(ws_reserve(ctx, w, &w.X2, &w.X2_cap, x_per_pair * (size_t)P));
   if (route == 2) {
     CKS(ws_reserve(ctx, w, &w.C, &w.C_cap, sizeof(double2) * (size_t)P * K * K * K));
     CKS(ws_reserve(ctx, w, &w.Y, &w.Y_cap, sizeof(double2) * (size_t)P * Nb * K * K));
@@ -571,10 +595,45 @@ static int forward_impl(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
     for (int i = 0; i < 2; ++i) CKS(ws_reserve(ctx, w, &w.stage[i], &w.stage_cap[i], per_pair_g * (size_t)P));
   }
 
+  // Two-stream pipeline: chunk i's coupling and beta/gamma sums run on the
+  // workspace's aux stream into X buffer i%2 while the alpha stage of chunk
+  // i-1 runs on the caller's stream.
+  cudaStream_t ax = w.aux;
+  CK(cudaEventRecord(w.start, st));
+  CK(cudaStreamWaitEvent(ax, w.start, 0));
+  // the coupling of every pair in one launch (one CTA per pair fills the GPU)
+  LAUNCH(SLSHT_STAGE_COUPLE, ax,
+         launch_couple((const double2*)f_dev, Lf, Lh, (const int2*)lm_dev, n_pairs, (double2*)w.kc, ax));
+  void* Xb[2] = {w.X, w.X2};
   int ci = 0;
   for (int32_t off = 0; off < n_pairs; off += P, ++ci) {
     const int np = std::min<int>(P, n_pairs - off);
-    const int2* lmc = (const int2*)lm_dev + off;
+    void* X = Xb[ci & 1];
+    // ---- producer side (aux stream)
+    CK(cudaStreamWaitEvent(ax, w.x_free[ci & 1], 0));
+    const double2* kcc = (const double2*)w.kc + (size_t)off * Lh * Lh;
+    if (route == 2) {
+      LAUNCH(SLSHT_STAGE_CTENSOR, ax,
+             launch_ctensor(kcc, (const double2*)h_dev, D, Lh, np, (double2*)w.C, ax));
+      LAUNCH(SLSHT_STAGE_CTENSOR, ax, launch_beta_dft((const double2*)w.C, Lh, Nb, np, (double2*)w.Y, ax));
+    }
+    const double2* Ysrc = route == 2 ? (const double2*)w.Y : nullptr;
+    if (tc) {
+      LAUNCH(SLSHT_STAGE_BETA, ax,
+             launch_betagamma_tc(kcc, (const double2*)h_dev, (const float*)dt, Ysrc,
+                                 (const float2*)eg, Lh, Nb, Ng, np, X, ax));
+    } else if (f64) {
+      LAUNCH(SLSHT_STAGE_BETA, ax,
+             launch_betagamma_f64(kcc, (const double2*)h_dev, (const double*)dt, Ysrc,
+                                  (const double2*)eg, Lh, Nb, Ng, np, (double2*)X, ax));
+    } else {
+      LAUNCH(SLSHT_STAGE_BETA, ax,
+             launch_betagamma_f32(kcc, (const double2*)h_dev, (const float*)dt, Ysrc,
+                                  (const float2*)eg, Lh, Nb, Ng, np, (float2*)X, ax));
+    }
+    CK(cudaEventRecord(w.x_ready[ci & 1], ax));
+    // ---- consumer side (caller's stream)
+    CK(cudaStreamWaitEvent(st, w.x_ready[ci & 1], 0));
     void* gdst;
     if (host_out) {
       CK(cudaStreamWaitEvent(st, w.copy_ev[ci & 1], 0));   // staging buffer free again
@@ -582,35 +641,17 @@ static int forward_impl(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
     } else {
       gdst = (char*)g_out + per_pair_g * (size_t)off;
     }
-    LAUNCH(SLSHT_STAGE_COUPLE, st,
-           launch_couple((const double2*)f_dev, Lf, Lh, lmc, np, (double2*)w.kc, st));
-    if (route == 2) {
-      LAUNCH(SLSHT_STAGE_CTENSOR, st,
-             launch_ctensor((const double2*)w.kc, (const double2*)h_dev, D, Lh, np, (double2*)w.C, st));
-      LAUNCH(SLSHT_STAGE_CTENSOR, st, launch_beta_dft((const double2*)w.C, Lh, Nb, np, (double2*)w.Y, st));
-    }
-    const double2* Ysrc = route == 2 ? (const double2*)w.Y : nullptr;
     if (tc) {
-      LAUNCH(SLSHT_STAGE_BETA, st,
-             launch_betagamma_tc((const double2*)w.kc, (const double2*)h_dev, (const float*)dt, Ysrc,
-                                 (const float2*)eg, Lh, Nb, Ng, np, w.X, st));
       LAUNCH(SLSHT_STAGE_ALPHA, st,
-             launch_alpha_tc(w.X, etab, Lh, Na, Nb, Ng, np, (float2*)gdst, ctx->num_sms, st));
+             launch_alpha_tc(X, etab, Lh, Na, Nb, Ng, np, (float2*)gdst, ctx->num_sms, st));
     } else if (f64) {
-      LAUNCH(SLSHT_STAGE_BETA, st,
-             launch_betagamma_f64((const double2*)w.kc, (const double2*)h_dev, (const double*)dt, Ysrc,
-                                  (const double2*)eg, Lh, Nb, Ng, np, (double2*)w.X, st));
       LAUNCH(SLSHT_STAGE_ALPHA, st,
-             launch_alpha_f64((const double2*)w.X, (const double2*)csa, Lh, Na, (int)J, np,
-                              (double2*)gdst, st));
+             launch_alpha_f64((const double2*)X, (const double2*)csa, Lh, Na, (int)J, np, (double2*)gdst, st));
     } else {
-      LAUNCH(SLSHT_STAGE_BETA, st,
-             launch_betagamma_f32((const double2*)w.kc, (const double2*)h_dev, (const float*)dt, Ysrc,
-                                  (const float2*)eg, Lh, Nb, Ng, np, (float2*)w.X, st));
       LAUNCH(SLSHT_STAGE_ALPHA, st,
-             launch_alpha_f32((const float2*)w.X, (const float2*)csa, Lh, Na, (int)J, np,
-                              (float2*)gdst, st));
+             launch_alpha_f32((const float2*)X, (const float2*)csa, Lh, Na, (int)J, np, (float2*)gdst, st));
     }
+    CK(cudaEventRecord(w.x_free[ci & 1], st));
     if (host_out) {
       CK(cudaEventRecord(w.stage_ev[ci & 1], st));
       CK(cudaStreamWaitEvent(w.copy_stream, w.stage_ev[ci & 1], 0));
@@ -759,6 +800,8 @@ static void worker_loop(slsht_ctx* c) {
       std::unique_ptr<Request> req = std::move(c->queue.front());
       c->queue.pop_front();
       Slot& s = *free_slot;
+      s.busy = true;          // counted in flight before the lock is released
+      c->inflight++;
       int st = SLSHT_OK;
       if (!s.stream) {
         if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -778,12 +821,12 @@ static void worker_loop(slsht_ctx* c) {
       }
       if (st != SLSHT_OK) {
         c->status[req->id] = st;
+        s.busy = false;
+        c->inflight--;
         c->scv.notify_all();
         continue;
       }
       s.req = std::move(req);
-      s.busy = true;
-      c->inflight++;
     }
     if (c->stop && c->queue.empty() && c->inflight == 0) break;
     if (c->inflight > 0) {

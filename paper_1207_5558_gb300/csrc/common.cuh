@@ -36,6 +36,8 @@ cudaError_t launch_delta(double* D, int Lh, cudaStream_t st);
 // dt[b * S + blk_off(p) + (q+p)(2p+1) + (q'+p)], S = blk_off(Lh).
 cudaError_t launch_dtable_f64(const double* D, double* dt, int Lh, int Nb, cudaStream_t st);
 cudaError_t launch_dtable_f32(const double* D, float* dt, int Lh, int Nb, cudaStream_t st);
+// Same values, layout [S][ldb] with beta fastest (ldb >= Nb, padding zeroed).
+cudaError_t launch_dtable_f32_t(const double* D, float* dt, int Lh, int Nb, int ldb, cudaStream_t st);
 // tab[i * R + r] = (cos, sin)(2 pi (r0 + r) i / N), i < N, r < R.
 cudaError_t launch_phase_f64(double2* tab, int N, int R, int r0, cudaStream_t st);
 cudaError_t launch_phase_f32(float2* tab, int N, int R, int r0, cudaStream_t st);

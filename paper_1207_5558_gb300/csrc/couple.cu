@@ -5,6 +5,16 @@
 // with both Wigner-3j families generated by recurrences in l' (= j1) in FP64.
 #include "common.cuh"
 
+// 1/x for a positive integer-valued x: float reciprocal refined by two
+// Newton-Raphson steps, r <- r (2 - x r), to full double precision.
+__device__ __forceinline__ double rcp_newton(double x) {
+  double r = (double)__frcp_rn((float)x);
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+
 // 3j symbols (j1 j2 j3; m1 m2 m3), m1 = -m2 - m3, for every j1 in
 // [j1min, j1max] = [max(|j2-j3|, |m1|), j2 + j3], into f[0 .. n-1].
 // Schulten-Gordon recurrence in j1:
@@ -17,21 +27,23 @@
 // sum_j1 (2 j1 + 1) f^2 = 1 and fix the sign by sgn f(j1max) = (-1)^{j2-j3-m1}.
 // When j1min = 0 (j2 = j3, m1 = 0) the recurrence is silent at j1 = 0 and the
 // first step uses f(1)/f(0) = m2 / sqrt(j2 (j2 + 1)).
-// Returns n (0 if the chain is empty).
+// A(j1) and 1/A(j1) come from one rsqrt of the polynomial A^2 and are carried
+// from step to step.  Returns n (0 if the chain is empty).
+template <int CMAX>
 __device__ int threej_chain(int j2, int j3, int m2, int m3, double* f, double* bwd, int* j1min_out) {
   const int m1 = -m2 - m3;
   const int j1min = max(abs(j2 - j3), abs(m1));
   const int j1max = j2 + j3;
   *j1min_out = j1min;
   const int n = j1max - j1min + 1;
-  if (n <= 0 || abs(m2) > j2 || abs(m3) > j3) return 0;
+  if (n <= 0 || n > CMAX || abs(m2) > j2 || abs(m3) > j3) return 0;
   const double dj = (double)(j2 - j3), sj = (double)(j2 + j3 + 1), dm1 = (double)m1;
   const double bj = (double)j2 * (j2 + 1.0) * dm1 - (double)j3 * (j3 + 1.0) * dm1;
   const double dm = (double)(m3 - m2);
-  auto A = [&](int j1) -> double {
+  auto A2 = [&](int j1) -> double {
     const double x = (double)j1;
     const double v = (x * x - dj * dj) * (sj * sj - x * x) * (x * x - dm1 * dm1);
-    return v > 0.0 ? sqrt(v) : 0.0;
+    return v > 0.0 ? v : 0.0;
   };
   auto B = [&](int j1) -> double {
     const double x = (double)j1;
@@ -40,28 +52,38 @@ __device__ int threej_chain(int j2, int j3, int m2, int m3, double* f, double* b
   if (n == 1) {
     f[0] = 1.0;
   } else {
+    // forward: A(j1) carried in acur (A(j1min) is 0 or irrelevant: f(j1min-1) = 0)
     f[0] = 1.0;
     int kf = 0;
+    double acur = sqrt(A2(j1min));
     auto fstep = [&](int i) {
       const int j1 = j1min + i;
+      const double p2 = A2(j1 + 1);
+      const double rn = rsqrt(p2);
       if (j1 == 0) {
-        f[1] = (double)m2 / sqrt((double)j2 * (j2 + 1.0));
+        f[1] = (double)m2 * rsqrt((double)j2 * (j2 + 1.0));
       } else {
         const double prev = i > 0 ? f[i - 1] : 0.0;
-        f[i + 1] = -(B(j1) * f[i] + (j1 + 1.0) * A(j1) * prev) / (j1 * A(j1 + 1));
+        f[i + 1] = -(B(j1) * f[i] + (j1 + 1.0) * acur * prev) * rn * rcp_newton((double)j1);
       }
+      acur = p2 * rn;
     };
     while (kf + 1 < n) {
       fstep(kf);
       ++kf;
       if (fabs(f[kf]) < fabs(f[kf - 1])) break;
     }
+    // backward: A(j1+1) carried in anext (A(j1max+1) = 0)
     bwd[n - 1] = 1.0;
     int kb = n - 1;
+    double anext = 0.0;
     while (kb - 1 >= 0) {
       const int j1 = j1min + kb;
+      const double p2 = A2(j1);
+      const double r = rsqrt(p2);
       const double nxt = (kb + 1 < n) ? bwd[kb + 1] : 0.0;
-      bwd[kb - 1] = -(B(j1) * bwd[kb] + j1 * A(j1 + 1) * nxt) / ((j1 + 1.0) * A(j1));
+      bwd[kb - 1] = -(B(j1) * bwd[kb] + j1 * anext * nxt) * r * rcp_newton(j1 + 1.0);
+      anext = p2 * r;
       --kb;
       if (fabs(bwd[kb]) < fabs(bwd[kb + 1])) break;
     }
@@ -78,24 +100,46 @@ __device__ int threej_chain(int j2, int j3, int m2, int m3, double* f, double* b
   }
   double norm = 0.0;
   for (int i = 0; i < n; ++i) norm += (2.0 * (j1min + i) + 1.0) * f[i] * f[i];
-  double scale = 1.0 / sqrt(norm);
+  double scale = rsqrt(norm);
   const double want = ((j2 - j3 - m1) & 1) ? -1.0 : 1.0;
   if (f[n - 1] * want < 0.0) scale = -scale;
   for (int i = 0; i < n; ++i) f[i] *= scale;
   return n;
 }
 
-// One CTA per pair; item t = p*p + p + q (the window's flat index) computes
-// k_lm(p, q).  The (l' p l; 0 0 0) family obeys the two-term relation
+// One CTA per pair.  First the CTA builds, in shared memory, the
+// (l' p l; 0 0 0) family for every p < Lh: the two-term relation
 //   f(j1+1) = -sqrt((j1^2-d^2)(S^2-j1^2) / (((j1+1)^2-d^2)(S^2-(j1+1)^2))) f(j1-1),
-// d = p - l, S = p + l + 1, non-zero for even j1 + p + l; it is walked twice
-// (norm and sign first, values second) so no array is needed for it.
+// d = p - l, S = p + l + 1, over the even j1 + p + l, normalised by
+// sum (2 j1 + 1) f^2 = 1 with sgn f(p + l) = (-1)^{p-l}.  Then item
+// t = p*p + p + q (the window's flat index) runs the (l' p l; m-q q -m) chain
+// and accumulates k_lm(p, q).
+template <int CMAX>
 __global__ void __launch_bounds__(256) k_couple(const double2* __restrict__ f, int Lf, int Lh,
                                                 const int2* __restrict__ lm, double2* __restrict__ kc) {
+  __shared__ double w0s[SLSHT_MAX_LH * (SLSHT_MAX_LH + 1) / 2];
   const int pair = blockIdx.x;
   const int l = lm[pair].x, m = lm[pair].y;
+  for (int p = threadIdx.x; p < Lh; p += blockDim.x) {
+    double* w = w0s + p * (p + 1) / 2;
+    const int j0 = abs(p - l), cnt = min(p, l) + 1;
+    const double dd = (double)(p - l), SS = (double)(p + l + 1);
+    double v = 1.0, norm = 2.0 * j0 + 1.0;
+    w[0] = 1.0;
+    for (int i = 1; i < cnt; ++i) {
+      const double x = (double)(j0 + 2 * i - 1), y = x + 1.0;
+      v *= -sqrt(((x * x - dd * dd) * (SS * SS - x * x)) / ((y * y - dd * dd) * (SS * SS - y * y)));
+      w[i] = v;
+      norm += (2.0 * (j0 + 2 * i) + 1.0) * v * v;
+    }
+    double s0 = rsqrt(norm);
+    const double want = ((p - l) & 1) ? -1.0 : 1.0;
+    if (v * want < 0.0) s0 = -s0;
+    for (int i = 0; i < cnt; ++i) w[i] *= s0;
+  }
+  __syncthreads();
   const int nitems = Lh * Lh;
-  double fm[SLSHT_CHAIN_MAX], bwd[SLSHT_CHAIN_MAX];
+  double fm[CMAX], bwd[CMAX];
   for (int t = threadIdx.x; t < nitems; t += blockDim.x) {
     int p = (int)sqrt((double)t);
     while (p * p > t) --p;
@@ -103,35 +147,20 @@ __global__ void __launch_bounds__(256) k_couple(const double2* __restrict__ f, i
     const int q = t - p * p - p;
     double2 acc = make_double2(0.0, 0.0);
     int j1min_m;
-    const int nm = threej_chain(p, l, q, -m, fm, bwd, &j1min_m);
+    const int nm = threej_chain<CMAX>(p, l, q, -m, fm, bwd, &j1min_m);
     if (nm > 0) {
-      // (l' p l; 000): first pass for the normalisation and the sign at l' = p + l
-      const int j0 = abs(p - l), j1top = p + l;
-      const double dd = (double)(p - l), SS = (double)(p + l + 1);
-      auto ratio = [&](int j1) -> double {   // f(j1+1)/f(j1-1)
-        const double x = (double)j1, y = x + 1.0;
-        return -sqrt(((x * x - dd * dd) * (SS * SS - x * x)) / ((y * y - dd * dd) * (SS * SS - y * y)));
-      };
-      double w = 1.0, norm = (2.0 * j0 + 1.0);
-      for (int j1 = j0 + 2; j1 <= j1top; j1 += 2) {
-        w *= ratio(j1 - 1);
-        norm += (2.0 * j1 + 1.0) * w * w;
-      }
-      double s0 = 1.0 / sqrt(norm);
-      const double want = ((p - l) & 1) ? -1.0 : 1.0;
-      if (w * want < 0.0) s0 = -s0;
-      // second pass: accumulate over l' < Lf with l' + p + l even and in the m chain
+      const double* w = w0s + p * (p + 1) / 2;
+      const int j0 = abs(p - l);
       const int mu = m - q;
-      const int jend = min(j1top, Lf - 1);
-      w = s0;
-      for (int j1 = j0; j1 <= jend; j1 += 2) {
-        if (j1 > j0) w *= ratio(j1 - 1);
-        if (j1 >= j1min_m) {
-          const double c = sqrt(2.0 * j1 + 1.0) * w * fm[j1 - j1min_m];
-          const double2 fv = f[j1 * j1 + j1 + mu];
-          acc.x = fma(c, fv.x, acc.x);
-          acc.y = fma(c, fv.y, acc.y);
-        }
+      const int jend = min(p + l, Lf - 1);
+      // l' = j0 + 2i, l' >= j1min_m
+      int i0 = (j1min_m - j0 + 1) / 2;
+      if (i0 < 0) i0 = 0;
+      for (int j1 = j0 + 2 * i0; j1 <= jend; j1 += 2) {
+        const double c = sqrt(2.0 * j1 + 1.0) * w[(j1 - j0) >> 1] * fm[j1 - j1min_m];
+        const double2 fv = f[j1 * j1 + j1 + mu];
+        acc.x = fma(c, fv.x, acc.x);
+        acc.y = fma(c, fv.y, acc.y);
       }
       const double pre = ((m & 1) ? -1.0 : 1.0) *
                          sqrt((2.0 * p + 1.0) * (2.0 * l + 1.0) / (4.0 * 3.14159265358979323846));
@@ -146,6 +175,8 @@ cudaError_t launch_couple(const double2* f, int Lf, int Lh, const int2* lm, int 
                           double2* kc, cudaStream_t st) {
   if (npairs <= 0) return cudaSuccess;
   const int threads = Lh * Lh < 256 ? ((Lh * Lh + 31) / 32) * 32 : 256;
-  k_couple<<<npairs, threads, 0, st>>>(f, Lf, Lh, lm, kc);
+  if (Lh <= 16) k_couple<32><<<npairs, threads, 0, st>>>(f, Lf, Lh, lm, kc);
+  else if (Lh <= 32) k_couple<64><<<npairs, threads, 0, st>>>(f, Lf, Lh, lm, kc);
+  else k_couple<128><<<npairs, threads, 0, st>>>(f, Lf, Lh, lm, kc);
   return cudaGetLastError();
 }

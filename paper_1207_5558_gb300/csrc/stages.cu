@@ -117,14 +117,17 @@ __global__ void k_betagamma(const double2* __restrict__ kc, const double2* __res
   T2* sk = reinterpret_cast<T2*>(smem_raw);      // [Lh*Lh]
   T2* sh = sk + Lh * Lh;                          // [Lh*Lh]
   T2* sG = sh + Lh * Lh;                          // [K*K]
-  T2* sE = sG + K * K;                            // [Ng*K]  (cos, sin)(q' gamma_c)
+  T2* sE = sG + K * K;                            // [K][Ng] (cos, sin)(q' gamma_c), c fastest
   const int n2 = Lh * Lh;
   for (int t = threadIdx.x; t < n2; t += blockDim.x) {
     const double2 kv = kc[(size_t)pair * n2 + t], hv = h[t];
     sk[t] = mk2((T)kv.x, (T)kv.y);
     sh[t] = mk2((T)hv.x, (T)hv.y);
   }
-  for (int t = threadIdx.x; t < Ng * K; t += blockDim.x) sE[t] = eg[t];
+  for (int t = threadIdx.x; t < Ng * K; t += blockDim.x) {
+    const int k = t / Ng, c = t % Ng;
+    sE[t] = eg[c * K + k];
+  }
   __syncthreads();
   if (Y == nullptr) {
     const int S = blk_off(Lh);
@@ -156,10 +159,10 @@ __global__ void k_betagamma(const double2* __restrict__ kc, const double2* __res
     const int r = t / Ng, c = t % Ng;
     const T2* gp = sG + (r + Lh - 1) * K;          // row q = +r
     const T2* gm = sG + (-r + Lh - 1) * K;         // row q = -r
-    const T2* e = sE + c * K;
+    const T2* e = sE + c;                          // stride Ng: no bank conflicts across c
     T pr = 0, pi = 0, mr = 0, mi = 0;
     for (int k = 0; k < K; ++k) {                  // multiply by (cos - i sin)
-      const T2 E = e[k], a = gp[k], bb = gm[k];
+      const T2 E = e[k * Ng], a = gp[k], bb = gm[k];
       pr = fma(a.x, E.x, pr); pr = fma(a.y, E.y, pr);
       pi = fma(a.y, E.x, pi); pi = fma(-a.x, E.y, pi);
       mr = fma(bb.x, E.x, mr); mr = fma(bb.y, E.y, mr);

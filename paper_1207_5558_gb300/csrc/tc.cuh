@@ -10,7 +10,11 @@ size_t tc_etab_bytes(int Na, int Lh);
 cudaError_t launch_tc_etab(void* etab, int Na, int Lh, cudaStream_t st);
 // Bytes of the A operand (split-FP16 X, per-row scales) of ONE pair.
 size_t tc_xblob_bytes(int Nb, int Ng, int Lh);
-// beta + gamma stages writing the A operand blobs (FP32 sums).
+// Row stride (beta samples, padded) of the beta-fastest FP32 d table the
+// tensor-core producer reads.
+int tc_dtab_ldb(int Nb);
+// beta + gamma stages writing the A operand blobs (FP32 sums); dt is the
+// beta-fastest table of launch_dtable_f32_t with row stride tc_dtab_ldb(Nb).
 cudaError_t launch_betagamma_tc(const double2* kc, const double2* h, const float* dt,
                                 const double2* Y, const float2* eg, int Lh, int Nb, int Ng,
                                 int npairs, void* xblob, cudaStream_t st);
