@@ -158,6 +158,33 @@ int slsht_inverse(slsht_ctx* ctx, const slsht_desc* desc,
                   const int32_t* lm, int32_t n_pairs,
                   double* f_out, void* stream);
 
+/* ---------------------------------------------------------------- no-alloc */
+
+/* Size of the static device scratch array behind slsht_forward_noalloc. */
+#define SLSHT_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* The forward transform for callers that cannot allocate device memory when
+ * they need it: code in host callbacks or real-time sections where
+ * cudaMalloc's implicit synchronisation is not allowed, plug-ins whose host
+ * application owns the device allocator, and processes that have given the
+ * whole device to a fixed pool.  The paper has no counterpart to this call.
+ * It needs no context and allocates nothing: it works in one static device
+ * array of SLSHT_NOALLOC_SCRATCH_BYTES that every GPU loading this library
+ * holds until the process exits.  Arguments, layouts and results are those of
+ * slsht_forward, except that g_out must be device memory; FP32_BULK runs its
+ * alpha stage on CUDA cores here.  Tables are rebuilt on every call; pairs are
+ * processed in chunks that fit the array.
+ *  - Requests whose tables plus one pair exceed the array are rejected with
+ *    SLSHT_E_NOMEM before anything is enqueued (slsht_last_error explains).
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current: make that first call
+ *    before any stream capture.
+ *  - Calls share the array and it keeps the last call's contents: calls whose
+ *    work can overlap on the GPU race with each other; order them on one
+ *    stream (or with events). */
+int slsht_forward_noalloc(const slsht_desc* desc, const double* f_lm, const double* h_lm,
+                          const int32_t* lm, int32_t n_pairs, void* g_out, void* stream);
+
 /* ---------------------------------------------------------------- serving */
 
 /* Non-blocking forward request for a continuous-batching server.  The

@@ -14,7 +14,7 @@ from ._abi import (SLSHT_FP32_BULK, SLSHT_FP64, SLSHT_OPT_ALPHA_ENGINE,  # noqa:
                    slsht_desc, slsht_stats)
 
 __all__ = ["Context", "make_desc", "SLSHT_FP64", "SLSHT_FP32_BULK", "SlshtError",
-           "slsht_create", "slsht_destroy", "slsht_forward", "slsht_inverse", "slsht_submit",
+           "slsht_create", "slsht_destroy", "slsht_forward", "slsht_forward_noalloc", "slsht_inverse", "slsht_submit",
            "slsht_poll", "slsht_drain", "slsht_strerror", "slsht_check_args", "slsht_profile",
            "slsht_get_stats", "slsht_set_option", "slsht_mem_used", "slsht_version"]
 
@@ -56,6 +56,14 @@ def slsht_inverse(ctx, desc, g_in, h00, lm, n_pairs, f_out, stream=None):
     return _abi.check(_abi.load().slsht_inverse(ctx, ctypes.byref(desc), _abi.ptr(g_in), hv, _abi.ptr(lm),
                                                 int(n_pairs), _abi.ptr(f_out), _stream(stream)),
                       "slsht_inverse")
+
+
+def slsht_forward_noalloc(desc, f_lm, h_lm, lm, n_pairs, g_out, stream=None):
+    """slsht_forward without a context and without device allocation (static
+    scratch of SLSHT_NOALLOC_SCRATCH_BYTES); g_out must be device memory."""
+    return _abi.check(_abi.load().slsht_forward_noalloc(ctypes.byref(desc), _abi.ptr(f_lm), _abi.ptr(h_lm),
+                                                        _abi.ptr(lm), int(n_pairs), _abi.ptr(g_out),
+                                                        _stream(stream)), "slsht_forward_noalloc")
 
 
 def slsht_submit(ctx, desc, f_lm, h_lm, lm, n_pairs, g_out):

@@ -27,6 +27,7 @@ SLSHT_OPT_ALPHA_ENGINE = 2
 SLSHT_OPT_CHUNK_PAIRS = 3
 
 SLSHT_NSTAGES = 8
+SLSHT_NOALLOC_SCRATCH_BYTES = 32 << 20
 STAGE_NAMES = ["tables", "couple", "ctensor", "beta_gamma", "alpha", "inverse", "copy", "other"]
 
 
@@ -58,6 +59,7 @@ def load(path=LIB_PATH):
         "slsht_destroy": (None, [vp]),
         "slsht_forward": (ctypes.c_int, [vp, ctypes.POINTER(slsht_desc), vp, vp, vp, i32, vp, vp]),
         "slsht_inverse": (ctypes.c_int, [vp, ctypes.POINTER(slsht_desc), vp, vp, vp, i32, vp, vp]),
+        "slsht_forward_noalloc": (ctypes.c_int, [ctypes.POINTER(slsht_desc), vp, vp, vp, i32, vp, vp]),
         "slsht_submit": (ctypes.c_int, [vp, ctypes.POINTER(slsht_desc), vp, vp, vp, i32, vp,
                                         ctypes.POINTER(u64)]),
         "slsht_poll": (ctypes.c_int, [vp, u64]),

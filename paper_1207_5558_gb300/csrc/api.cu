@@ -33,6 +33,13 @@ static void record_cuda_error(const char* what, cudaError_t e) {
   g_last_err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
 }
 
+// Lets other translation units of the library explain their failures through
+// slsht_last_error.
+void slsht_record_error_text(const char* text) {
+  std::lock_guard<std::mutex> g(g_err_mu);
+  g_last_err = text;
+}
+
 #define CK(call)                                     \
   do {                                               \
     cudaError_t _e = (call);                         \
