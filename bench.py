@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="Poisson-arriving requests of the serving run (0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--profile-pairs", type=int, default=0,
+                    help="profiling case: two forwards (FP32_BULK) over the last N pairs of map 0, "
+                         "48 pairs per chunk, then exit")
     return ap.parse_args()
 
 
@@ -177,37 +180,42 @@ def serve_requests(n, seed):
     return reqs
 
 
-def serve_bench(pkg, device, n, rate, seed=4000):
+def serve_bench(pkg, device, n, rate, seed=4000, max_outstanding_bytes=48 << 30, time_cap_s=120.0):
     """Continuous batching: requests arrive as a Poisson process; each is
-    submitted at its arrival time (slsht_submit) while earlier ones are still
-    on the GPU; latency = completion seen by the poller - arrival."""
+    submitted (slsht_submit) as soon as it has arrived and its output fits the
+    cap on outstanding output bytes, while earlier ones are still on the GPU;
+    latency = completion seen by the poller - arrival (host clock), so time a
+    request waits behind the cap is included."""
     import numpy as np
     import torch
     reqs = serve_requests(n, seed)
     rng = np.random.default_rng(seed + 1)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
     ctx = pkg.Context(device, mem_budget_bytes=(24 << 30))
-    # warm the tables of every (L_h, grid, precision) once, outside the measurement
+    # build the tables of every (L_h, native grid, precision) once, outside the measurement
     for Lh in (4, 8, 16, 32):
         for prec in (0, 1):
-            r = dict(Lf=32, Lh=Lh, grid=serve_native(Lh), prec=prec)
-            f = np.zeros(32 * 32, complex)
-            h = np.ones(Lh * Lh, complex)
-            ctx.forward(32, Lh, r["grid"], f, h, [[1, 0]], prec=prec)
+            grid = serve_native(Lh)
+            ctx.forward(32, Lh, grid, np.zeros(32 * 32, complex), np.ones(Lh * Lh, complex), [[1, 0]], prec=prec)
     torch.cuda.synchronize()
-    done_at = np.zeros(n)
+    done_at = np.full(n, np.nan)
     outstanding = {}
+    out_bytes = 0
     samples = 0
     t0 = time.perf_counter()
     i = 0
-    while i < n or outstanding:
+    while (i < n or outstanding) and time.perf_counter() - t0 < time_cap_s:
         now = time.perf_counter() - t0
         while i < n and arrivals[i] <= now:
             r = reqs[i]
             dt = torch.complex128 if r["prec"] == 0 else torch.complex64
+            nbytes = len(r["pairs"]) * int(np.prod(r["grid"])) * (16 if r["prec"] == 0 else 8)
+            if outstanding and out_bytes + nbytes > max_outstanding_bytes:
+                break
             g = torch.empty((len(r["pairs"]),) + tuple(r["grid"]), dtype=dt, device="cuda:%d" % device)
             tk = ctx.submit(r["Lf"], r["Lh"], r["grid"], r["f"], r["h"], r["pairs"], g, prec=r["prec"])
-            outstanding[tk] = (i, g)
+            outstanding[tk] = (i, g, nbytes)
+            out_bytes += nbytes
             samples += g.numel()
             i += 1
         for tk in list(outstanding):
@@ -215,18 +223,44 @@ def serve_bench(pkg, device, n, rate, seed=4000):
             if st != 1:
                 if st != 0:
                     raise RuntimeError("serving request failed: %d" % st)
-                done_at[outstanding[tk][0]] = time.perf_counter() - t0
-                del outstanding[tk]
+                k, _, nb = outstanding.pop(tk)
+                done_at[k] = time.perf_counter() - t0
+                out_bytes -= nb
         time.sleep(0.0002)
-    lat = (done_at - arrivals) * 1e3
-    span = done_at.max() - arrivals[0]
+    ctx.drain(600000)
+    ok = ~np.isnan(done_at)
+    lat = (done_at[ok] - arrivals[ok]) * 1e3
+    span = np.nanmax(done_at) - arrivals[0]
+    done_samples = sum(len(reqs[k]["pairs"]) * int(np.prod(reqs[k]["grid"])) for k in np.nonzero(ok)[0])
     ctx.close()
-    return {"requests": n, "rate_per_s": rate, "p50_ms": float(np.percentile(lat, 50)),
-            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
-            "max_ms": float(lat.max()), "g_samples_per_s": samples / span, "span_s": float(span),
-            "mean_samples_per_request": samples / n,
+    return {"requests": n, "completed": int(ok.sum()), "offered_rate_per_s": rate,
+            "achieved_rate_per_s": float(ok.sum() / span), "sustained": bool(ok.sum() / span >= 0.95 * rate),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
+            "g_samples_per_s": done_samples / span, "span_s": float(span),
+            "mean_samples_per_request": done_samples / max(1, ok.sum()),
             "workload": "L_f in {32..512}, L_h in {4,8,16,32}, 1-8 degrees x all m, native grid "
-                        "2L_h-1 x L_h x 2L_h-1, FP64/FP32_BULK 50/50, Poisson arrivals (seed 4000)"}
+                        "2L_h-1 x L_h x 2L_h-1, FP64/FP32_BULK 50/50, Poisson arrivals (seed 4000); "
+                        "outstanding outputs capped at 48 GB, later arrivals wait (latency from arrival)"}
+
+
+def profile_case(pkg, n):
+    """A small case of workload 3 for kernel captures: one chunk of 48 pairs per
+    launch, a few GB on the device, two passes."""
+    import numpy as np
+    import torch
+    import synth
+    c = synth.CONFIGS[3]
+    f, h, pairs = synth.config_inputs(3, 0)
+    sub = np.ascontiguousarray(pairs[-n:])
+    ctx = pkg.Context(0, 16 << 30)
+    ctx.set_option(pkg.SLSHT_OPT_CHUNK_PAIRS, 48)
+    g = torch.empty((n,) + c["grid"], dtype=torch.complex64, device="cuda")
+    for _ in range(2):
+        pkg.slsht_forward(ctx.h, pkg.make_desc(c["Lf"], c["Lh"], c["grid"], 1), f, h, sub, n, g)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_pairs": n, "max_abs_g": float(g.abs().max())}))
+    ctx.close()
 
 
 def serve_native(Lh):
@@ -300,6 +334,9 @@ def main():
     import synth
 
     torch.cuda.set_device(local)
+    if args.profile_pairs > 0:
+        profile_case(pkg, args.profile_pairs)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist

@@ -3,9 +3,9 @@
 // For one pair, with complex columns j = (beta, gamma) sample and alpha rows a,
 //   g[a][j] = sum_q X_q[j] e^{-i q alpha_a}
 // is a real GEMM D[j][n] = sum_k A[j][k] B[n][k] with
-//   A[j][k]      = [ Re X_q[j] (q = -(Lh-1)..Lh-1) | Im X_q[j] | 0 ... ]      (K padded to 64)
-//   B[n][k]      = [ cos(q alpha_a)  |  sin(q alpha_a) | 0 ]   n = a - a0        (Re g)
-//   B[128+n][k]  = [ -sin(q alpha_a) |  cos(q alpha_a) | 0 ]                     (Im g)
+//   A[j][k]      = Re X_q[j] at k = 15 + q,  Im X_q[j] at k = 47 + q   (|q| <= 15, zeros elsewhere)
+//   B[n][k]      = cos(q alpha_a) at k = 15 + q,  sin(q alpha_a) at k = 47 + q   n = a - a0   (Re g)
+//   B[128+n][k]  = -sin(q alpha_a) at k = 15 + q, cos(q alpha_a) at k = 47 + q               (Im g)
 // so one M=128 x N=256 accumulator holds Re and Im of 128 columns x 128 alpha
 // rows.  Precision: each operand is split into FP16 hi + lo (A after a
 // per-row power-of-two scale so its largest entry is in [2^14, 2^15)), and
@@ -67,7 +67,8 @@ __host__ __device__ __forceinline__ uint32_t sw128_off(int r, int k) {
 
 // ---------------------------------------------------------------- E tables
 // chunk c: [hi part: 256 rows x 64][lo part], rows n < 128 -> alpha a = c*128+n
-// (cos | sin), rows 128+n -> (-sin | cos); beyond Na or 2K: zeros.
+// (cos at k = 15+q | sin at k = 47+q), rows 128+n -> (-sin | cos); zeros beyond Na
+// and for |q| >= Lh.
 __global__ void k_tc_etab(unsigned char* __restrict__ etab, int Na, int Lh) {
   const int K = 2 * Lh - 1;
   const int c = blockIdx.x;
@@ -77,11 +78,11 @@ __global__ void k_tc_etab(unsigned char* __restrict__ etab, int Na, int Lh) {
     const int n = r % TC_NC;
     const int a = c * TC_NC + n;
     double v = 0.0;
-    if (a < Na && k < 2 * K) {
-      const int q = (k % K) - (Lh - 1);
+    const int q = (k & 31) - 15;
+    if (a < Na && (k & 31) < 31 && abs(q) < Lh) {
       double s, co;
       sincos_2pi_frac((long long)q * a, Na, &s, &co);
-      const bool is_sin = k >= K;
+      const bool is_sin = k >= 32;
       if (r < TC_NC) v = is_sin ? s : co;
       else v = is_sin ? co : -s;
     }
@@ -98,9 +99,8 @@ cudaError_t launch_tc_etab(void* etab, int Na, int Lh, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------- beta/gamma -> A
-// Same sums as k_betagamma<float>, for TC_NBB beta rows per CTA:
-//   G[q][q'](b) = sum_p k(p,q) h_p^{q'} d^p_{q,q'}(beta_b)   (d table laid out beta-fastest,
-//                 so one float4 load feeds the CTA's four rows)
+// Factoring-of-rotations route: G[q][q'](b) = Y[pair][b][q][q'] (the q''-DFT of
+// the C tensor), for TC_NBB beta rows per CTA, then
 //   X_q[c](b)   = G[q][0] + sum_{s>=1} (G[q][s] + G[q][-s]) cos(s gamma_c)
 //                          - i (G[q][s] - G[q][-s]) sin(s gamma_c)
 // and every row j = b*Ng + c is written as the A operand: scaled by 2^e (its
@@ -108,27 +108,29 @@ cudaError_t launch_tc_etab(void* etab, int Na, int Lh, cudaStream_t st) {
 #define TC_NBB 4
 
 struct BgLayout {          // shared-memory carve-up of k_betagamma_tc
-  int LhP, NgP, XS;        // padded strides: Gp/Gm rows, phase rows, X rows
-  size_t off_k, off_h, off_e, off_gp, off_gm, off_x, off_mx, total;
+  int LhP, NgP;            // padded strides: Gp/Gm rows, phase and X rows (multiple of 4)
+  size_t off_k, off_h, off_e, off_gp, off_gm, off_x, off_ex, total;
   __host__ __device__ BgLayout(int Lh, int Ng) {
     const int K = 2 * Lh - 1;
     LhP = Lh + 1;
-    NgP = (Ng + 1) & ~1;
-    XS = ((2 * K + 3) & ~3) + 4;
+    NgP = (Ng + 3) & ~3;
+    // every region starts on a 16-byte boundary (float4 accesses)
     off_k = 0;
-    off_h = off_k + sizeof(float2) * Lh * Lh;
-    off_e = off_h + sizeof(float2) * Lh * Lh;
-    off_gp = off_e + sizeof(float2) * (size_t)Lh * NgP;
-    off_gm = off_gp + sizeof(float2) * (size_t)TC_NBB * K * LhP;
-    off_x = off_gm + sizeof(float2) * (size_t)TC_NBB * K * LhP;
-    off_mx = off_x + sizeof(float) * (size_t)TC_NBB * Ng * XS;
-    total = off_mx + sizeof(int) * (size_t)TC_NBB * Ng;
+    off_h = a16(off_k + sizeof(float2) * Lh * Lh);
+    off_e = a16(off_h + sizeof(float2) * Lh * Lh);
+    off_gp = a16(off_e + sizeof(float2) * (size_t)Lh * NgP);
+    off_gm = a16(off_gp + sizeof(float2) * (size_t)TC_NBB * K * LhP);
+    off_x = a16(off_gm + sizeof(float2) * (size_t)TC_NBB * K * LhP);
+    off_ex = a16(off_x + sizeof(float) * (size_t)TC_NBB * 2 * K * NgP);
+    total = a16(off_ex + sizeof(int) * (size_t)TC_NBB * NgP);
+  }
+  __host__ __device__ static size_t a16(size_t n) { return (n + 15) & ~(size_t)15;
   }
 };
 
 __global__ void __launch_bounds__(256)
 k_betagamma_tc(const double2* __restrict__ kc, const double2* __restrict__ h, const float* __restrict__ dT,
-               int ldb, const double2* __restrict__ Y, const float2* __restrict__ eg, int Lh, int Nb, int Ng,
+               const double2* __restrict__ Y, const float2* __restrict__ eg, int Lh, int Nb, int Ng,
                unsigned char* __restrict__ xblob, size_t blob_stride, int tiles) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int K = 2 * Lh - 1;
@@ -140,8 +142,8 @@ k_betagamma_tc(const double2* __restrict__ kc, const double2* __restrict__ h, co
   float2* sE = reinterpret_cast<float2*>(smem_raw + L.off_e);     // [s][NgP]
   float2* sGp = reinterpret_cast<float2*>(smem_raw + L.off_gp);   // [bb][q][LhP]
   float2* sGm = reinterpret_cast<float2*>(smem_raw + L.off_gm);
-  float* sX = reinterpret_cast<float*>(smem_raw + L.off_x);       // [bb][c][XS]
-  int* sMx = reinterpret_cast<int*>(smem_raw + L.off_mx);         // [bb][c] max |X| bits
+  float* sX = reinterpret_cast<float*>(smem_raw + L.off_x);       // [bb][k][NgP], k < 2K: Re | Im
+  int* sEx = reinterpret_cast<int*>(smem_raw + L.off_ex);         // [bb][c] row scale exponent
   const int n2 = Lh * Lh;
   for (int t = threadIdx.x; t < n2; t += blockDim.x) {
     const double2 kv = kc[(size_t)pair * n2 + t], hv = h[t];
@@ -152,7 +154,6 @@ k_betagamma_tc(const double2* __restrict__ kc, const double2* __restrict__ h, co
     const int s = t / L.NgP, c = t % L.NgP;
     sE[t] = c < Ng ? eg[c * K + s + (Lh - 1)] : make_float2(0.f, 0.f);
   }
-  for (int t = threadIdx.x; t < TC_NBB * Ng; t += blockDim.x) sMx[t] = 0;
   __syncthreads();
   // ---- G for the CTA's beta rows, folded into Gp / Gm
   for (int t = threadIdx.x; t < K * Lh; t += blockDim.x) {
@@ -161,28 +162,7 @@ k_betagamma_tc(const double2* __restrict__ kc, const double2* __restrict__ h, co
     float pr[TC_NBB], pi[TC_NBB], mr[TC_NBB], mi[TC_NBB];
 #pragma unroll
     for (int u = 0; u < TC_NBB; ++u) pr[u] = pi[u] = mr[u] = mi[u] = 0.f;
-    if (Y == nullptr) {
-      for (int p = max(abs(q), s); p < Lh; ++p) {
-        const float2 kv = sk[p * p + p + q];
-        const int row = blk_off(p) + (q + p) * (2 * p + 1) + p;
-        {   // q' = +s
-          const float2 hv = sh[p * p + p + s];
-          const float khr = kv.x * hv.x - kv.y * hv.y, khi = kv.x * hv.y + kv.y * hv.x;
-          const float4 d = *reinterpret_cast<const float4*>(dT + (size_t)(row + s) * ldb + b0);
-          const float dv[4] = {d.x, d.y, d.z, d.w};
-#pragma unroll
-          for (int u = 0; u < TC_NBB; ++u) { pr[u] = fmaf(dv[u], khr, pr[u]); pi[u] = fmaf(dv[u], khi, pi[u]); }
-        }
-        if (s > 0) {   // q' = -s
-          const float2 hv = sh[p * p + p - s];
-          const float khr = kv.x * hv.x - kv.y * hv.y, khi = kv.x * hv.y + kv.y * hv.x;
-          const float4 d = *reinterpret_cast<const float4*>(dT + (size_t)(row - s) * ldb + b0);
-          const float dv[4] = {d.x, d.y, d.z, d.w};
-#pragma unroll
-          for (int u = 0; u < TC_NBB; ++u) { mr[u] = fmaf(dv[u], khr, mr[u]); mi[u] = fmaf(dv[u], khi, mi[u]); }
-        }
-      }
-    } else {
+    {
 #pragma unroll
       for (int u = 0; u < TC_NBB; ++u) {
         if (u >= nbb) break;
@@ -200,47 +180,58 @@ k_betagamma_tc(const double2* __restrict__ kc, const double2* __restrict__ h, co
     }
   }
   __syncthreads();
-  // ---- gamma sum, two gamma columns per thread
-  const int ncp = (Ng + 1) / 2;
-  for (int t = threadIdx.x; t < nbb * K * ncp; t += blockDim.x) {
-    const int cp = t % ncp, qi = (t / ncp) % K, u = t / (ncp * K);
-    const int c0 = 2 * cp;
+  // ---- gamma sum, four gamma columns per thread
+  const int ncq = L.NgP / 4;
+  for (int t = threadIdx.x; t < nbb * K * ncq; t += blockDim.x) {
+    const int cq = t % ncq, qi = (t / ncq) % K, u = t / (ncq * K);
+    const int c0 = 4 * cq;
     const float2* gp = sGp + (u * K + qi) * L.LhP;
     const float2* gm = sGm + (u * K + qi) * L.LhP;
-    float r0 = gp[0].x, i0 = gp[0].y, r1 = r0, i1 = i0;
+    float re[4], im[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) { re[v] = gp[0].x; im[v] = gp[0].y; }
     for (int s = 1; s < Lh; ++s) {
       const float2 P = gp[s], M = gm[s];
-      const float4 E = *reinterpret_cast<const float4*>(sE + s * L.NgP + c0);   // (cos, sin) at c0, c0+1
-      r0 = fmaf(P.x, E.x, r0); r0 = fmaf(M.y, E.y, r0);
-      i0 = fmaf(P.y, E.x, i0); i0 = fmaf(-M.x, E.y, i0);
-      r1 = fmaf(P.x, E.z, r1); r1 = fmaf(M.y, E.w, r1);
-      i1 = fmaf(P.y, E.z, i1); i1 = fmaf(-M.x, E.w, i1);
+      const float4 Ea = *reinterpret_cast<const float4*>(sE + s * L.NgP + c0);       // c0, c0+1
+      const float4 Eb = *reinterpret_cast<const float4*>(sE + s * L.NgP + c0 + 2);   // c0+2, c0+3
+      const float cs[4] = {Ea.x, Ea.z, Eb.x, Eb.z}, sn[4] = {Ea.y, Ea.w, Eb.y, Eb.w};
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {            // (Gp cos - i Gm sin)
+        re[v] = fmaf(P.x, cs[v], re[v]); re[v] = fmaf(M.y, sn[v], re[v]);
+        im[v] = fmaf(P.y, cs[v], im[v]); im[v] = fmaf(-M.x, sn[v], im[v]);
+      }
     }
-    float* x0 = sX + (u * Ng + c0) * L.XS;
-    x0[qi] = r0;
-    x0[K + qi] = i0;
-    atomicMax(sMx + u * Ng + c0, __float_as_int(fmaxf(fabsf(r0), fabsf(i0))));
-    if (c0 + 1 < Ng) {
-      float* x1 = x0 + L.XS;
-      x1[qi] = r1;
-      x1[K + qi] = i1;
-      atomicMax(sMx + u * Ng + c0 + 1, __float_as_int(fmaxf(fabsf(r1), fabsf(i1))));
-    }
+    float* xr = sX + ((size_t)u * 2 * K + qi) * L.NgP + c0;
+    float* xi = sX + ((size_t)u * 2 * K + K + qi) * L.NgP + c0;
+    *reinterpret_cast<float4*>(xr) = make_float4(re[0], re[1], re[2], re[3]);
+    *reinterpret_cast<float4*>(xi) = make_float4(im[0], im[1], im[2], im[3]);
   }
   __syncthreads();
-  // ---- scale, split, store: one thread per (row, 16-byte chunk of 8 FP16 values)
+  // ---- per row (u, c): e such that max |X| * 2^e lies in [2^14, 2^15), clamped
+  // so that 2^e and 2^-e are normal floats
   unsigned char* blob = xblob + (size_t)pair * blob_stride;
   float* scales = reinterpret_cast<float*>(blob + (size_t)tiles * TC_A_BYTES);
   const int J = Nb * Ng;
-  for (int t = threadIdx.x; t < nbb * Ng * (TC_KB / 8); t += blockDim.x) {
-    const int k0 = (t % (TC_KB / 8)) * 8, rc = t / (TC_KB / 8);
-    const int u = rc / Ng, c = rc % Ng;
-    const float mx = __int_as_float(sMx[rc]);
+  for (int t = threadIdx.x; t < nbb * L.NgP; t += blockDim.x) {
+    const int u = t / L.NgP, c = t % L.NgP;
+    if (c >= Ng) continue;
+    const float* col = sX + (size_t)u * 2 * K * L.NgP + c;
+    float mx = 0.f;
+    for (int k = 0; k < 2 * K; ++k) mx = fmaxf(mx, fabsf(col[(size_t)k * L.NgP]));
     int ex = 0;
     if (mx > 0.f) frexpf(mx, &ex);
-    const int e = mx > 0.f ? min(125, max(-125, 15 - ex)) : 0;   // mx * 2^e in [2^14, 2^15)
-    const float sc = __int_as_float((127 + e) << 23);
-    const float* row = sX + (u * Ng + c) * L.XS;
+    const int e = mx > 0.f ? min(125, max(-125, 15 - ex)) : 0;
+    sEx[t] = e;
+    scales[(b0 + u) * Ng + c] = __int_as_float((127 - e) << 23);
+  }
+  __syncthreads();
+  // ---- scale, split, store: one thread per (row, 16-byte chunk of 8 FP16 values),
+  // rows fastest so a warp's shared-memory reads are consecutive columns
+  for (int t = threadIdx.x; t < nbb * L.NgP * (TC_KB / 8); t += blockDim.x) {
+    const int c = t % L.NgP, k0 = ((t / L.NgP) % (TC_KB / 8)) * 8, u = t / (L.NgP * (TC_KB / 8));
+    if (c >= Ng) continue;
+    const float sc = __int_as_float((127 + sEx[u * L.NgP + c]) << 23);
+    const float* col = sX + (size_t)u * 2 * K * L.NgP + c;
     const int j = (b0 + u) * Ng + c;
     unsigned char* tb = blob + (size_t)(j / TC_M) * TC_A_BYTES;
     const int r = j % TC_M;
@@ -248,13 +239,14 @@ k_betagamma_tc(const double2* __restrict__ kc, const double2* __restrict__ h, co
 #pragma unroll
     for (int v = 0; v < 8; ++v) {
       const int k = k0 + v;
-      const float x = k < 2 * K ? row[k] * sc : 0.f;
+      const int q = (k & 31) - 15;                 // Re X_q at 15 + q, Im X_q at 47 + q
+      const int src = (k < 32 ? 0 : K) + q + (Lh - 1);
+      const float x = ((k & 31) < 31 && abs(q) < Lh) ? col[(size_t)src * L.NgP] * sc : 0.f;
       hi[v] = __float2half_rn(x);
       lo[v] = __float2half_rn(x - __half2float(hi[v]));
     }
     *reinterpret_cast<uint4*>(tb + sw128_off(r, k0)) = *reinterpret_cast<uint4*>(hi);
     *reinterpret_cast<uint4*>(tb + TC_A_HALF + sw128_off(r, k0)) = *reinterpret_cast<uint4*>(lo);
-    if (k0 == 0) scales[j] = __int_as_float((127 - e) << 23);
   }
   // the CTA holding the last beta row also clears the padding rows of the last tile
   if (b0 + nbb == Nb) {
@@ -269,8 +261,6 @@ k_betagamma_tc(const double2* __restrict__ kc, const double2* __restrict__ h, co
   }
 }
 
-int tc_dtab_ldb(int Nb) { return (Nb + TC_NBB - 1) / TC_NBB * TC_NBB; }
-
 cudaError_t launch_betagamma_tc(const double2* kc, const double2* h, const float* dT, const double2* Y,
                                 const float2* eg, int Lh, int Nb, int Ng, int npairs, void* xblob,
                                 cudaStream_t st) {
@@ -281,9 +271,99 @@ cudaError_t launch_betagamma_tc(const double2* kc, const double2* h, const float
     cudaError_t e = cudaFuncSetAttribute(k_betagamma_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
+  {
+    cudaError_t e = cudaFuncSetAttribute(k_betagamma_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+  }
   dim3 grid((Nb + TC_NBB - 1) / TC_NBB, npairs);
-  k_betagamma_tc<<<grid, 256, smem, st>>>(kc, h, dT, tc_dtab_ldb(Nb), Y, eg, Lh, Nb, Ng, (unsigned char*)xblob,
+  if (Y == nullptr) return cudaErrorInvalidValue;       // the factoring route only
+  k_betagamma_tc<<<grid, 256, smem, st>>>(kc, h, dT, Y, eg, Lh, Nb, Ng, (unsigned char*)xblob,
                                           tc_xblob_bytes(Nb, Ng, Lh), tc_tiles(Nb, Ng));
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- A operand from H
+// Rotated-window route: X_q(j) = sum_{p>=|q|} k(p,q) H^p_q(j) (H from launch_rotwin_f32),
+// one thread per column j of a 128-column tile; the row is scaled (largest entry
+// into [2^14, 2^15)), split into FP16 hi/lo and written swizzled; padding rows
+// of the last tile are zero.
+__global__ void __launch_bounds__(TC_M)
+k_xa_from_h(const double2* __restrict__ kc, const float2* __restrict__ H, int Lh, int J,
+            unsigned char* __restrict__ xblob, size_t blob_stride, int tiles) {
+  extern __shared__ float2 skf[];               // [Lh*Lh]
+  const int tile = blockIdx.x, pair = blockIdx.y, r = threadIdx.x;
+  const int n2 = Lh * Lh;
+  for (int t = threadIdx.x; t < n2; t += blockDim.x) {
+    const double2 v = kc[(size_t)pair * n2 + t];
+    skf[t] = make_float2((float)v.x, (float)v.y);
+  }
+  __syncthreads();
+  unsigned char* blob = xblob + (size_t)pair * blob_stride;
+  unsigned char* tb = blob + (size_t)tile * TC_A_BYTES;
+  float* scales = reinterpret_cast<float*>(blob + (size_t)tiles * TC_A_BYTES);
+  const int j = tile * TC_M + r;
+  if (j >= J) {
+#pragma unroll
+    for (int k0 = 0; k0 < TC_KB; k0 += 8) {
+      *reinterpret_cast<uint4*>(tb + sw128_off(r, k0)) = make_uint4(0, 0, 0, 0);
+      *reinterpret_cast<uint4*>(tb + TC_A_HALF + sw128_off(r, k0)) = make_uint4(0, 0, 0, 0);
+    }
+    scales[j] = 0.f;
+    return;
+  }
+  float xr[32], xi[32];                          // slot 15 + q, |q| <= 15
+#pragma unroll
+  for (int u = 0; u < 32; ++u) {
+    const int q = u - 15;
+    // every degree's load is issued before the multiply-adds use them
+    float2 hv[16];
+#pragma unroll
+    for (int p = 0; p < 16; ++p) {
+      const bool on = u < 31 && p >= (q < 0 ? -q : q) && p < Lh;
+      hv[p] = on ? __ldg(H + (size_t)(p * p + p + q) * J + j) : make_float2(0.f, 0.f);
+    }
+    float ar = 0.f, ai = 0.f;
+#pragma unroll
+    for (int p = 0; p < 16; ++p) {
+      const bool on = u < 31 && p >= (q < 0 ? -q : q) && p < Lh;
+      const float2 kv = on ? skf[p * p + p + q] : make_float2(0.f, 0.f);
+      ar = fmaf(kv.x, hv[p].x, ar); ar = fmaf(-kv.y, hv[p].y, ar);
+      ai = fmaf(kv.x, hv[p].y, ai); ai = fmaf(kv.y, hv[p].x, ai);
+    }
+    xr[u] = ar;
+    xi[u] = ai;
+  }
+  float mx = 0.f;
+#pragma unroll
+  for (int u = 0; u < 32; ++u) mx = fmaxf(mx, fmaxf(fabsf(xr[u]), fabsf(xi[u])));
+  int ex = 0;
+  if (mx > 0.f) frexpf(mx, &ex);
+  const int e = mx > 0.f ? min(125, max(-125, 15 - ex)) : 0;    // mx * 2^e in [2^14, 2^15)
+  const float sc = __int_as_float((127 + e) << 23);
+#pragma unroll
+  for (int k0 = 0; k0 < TC_KB; k0 += 8) {
+    __align__(16) __half hi[8], lo[8];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      const int k = k0 + v;
+      const float x = (k < 32 ? xr[k & 31] : xi[k & 31]) * sc;
+      hi[v] = __float2half_rn(x);
+      lo[v] = __float2half_rn(x - __half2float(hi[v]));
+    }
+    *reinterpret_cast<uint4*>(tb + sw128_off(r, k0)) = *reinterpret_cast<uint4*>(hi);
+    *reinterpret_cast<uint4*>(tb + TC_A_HALF + sw128_off(r, k0)) = *reinterpret_cast<uint4*>(lo);
+  }
+  scales[j] = __int_as_float((127 - e) << 23);
+}
+
+cudaError_t launch_xa_from_h(const double2* kc, const float2* H, int Lh, int Nb, int Ng, int npairs, void* xblob,
+                             cudaStream_t st) {
+  if (npairs <= 0) return cudaSuccess;
+  const int tiles = tc_tiles(Nb, Ng);
+  dim3 grid(tiles, npairs);
+  k_xa_from_h<<<grid, TC_M, sizeof(float2) * (size_t)Lh * Lh, st>>>(kc, H, Lh, Nb * Ng, (unsigned char*)xblob,
+                                                                    tc_xblob_bytes(Nb, Ng, Lh), tiles);
   return cudaGetLastError();
 }
 
@@ -574,6 +654,11 @@ cudaError_t launch_alpha_tc(const void* xblob, const void* etab, int Lh, int Na,
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_alpha_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    if (e != cudaSuccess) return e;
+    // the whole unified L1/shared array as shared memory, so the producer
+    // kernels of the next chunk fit beside this kernel's CTA on every SM
+    e = cudaFuncSetAttribute(k_alpha_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     attr = true;
   }

@@ -116,6 +116,7 @@ struct Workspace {
   void* X2 = nullptr; size_t X2_cap = 0;
   void* C = nullptr; size_t C_cap = 0;
   void* Y = nullptr; size_t Y_cap = 0;
+  void* H = nullptr; size_t H_cap = 0;   // rotated window of the call (route 1)
   void* stage[2] = {nullptr, nullptr}; size_t stage_cap[2] = {0, 0};
   cudaEvent_t done = nullptr;          // last use of this workspace
   cudaEvent_t stage_ev[2] = {nullptr, nullptr};
@@ -276,6 +277,7 @@ static void ws_release(slsht_ctx* c, Workspace& w) {
   ctx_free(c, w.X, w.X_cap);
   ctx_free(c, w.C, w.C_cap);
   ctx_free(c, w.Y, w.Y_cap);
+  ctx_free(c, w.H, w.H_cap);
   for (int i = 0; i < 2; ++i) ctx_free(c, w.stage[i], w.stage_cap[i]);
   for (int i = 0; i < 2; ++i) {
     if (w.stage_ev[i]) cudaEventDestroy(w.stage_ev[i]);
@@ -370,14 +372,11 @@ static int get_dtab(slsht_ctx* ctx, int Lh, int Nb, int prec, cudaStream_t st, c
     const double* D;
     CKS(get_delta(ctx, Lh, st, &D));
     TableEntry e;
-    // prec 2: FP32, beta-fastest layout for the tensor-core producer
     const size_t el = prec == SLSHT_FP64 ? sizeof(double) : sizeof(float);
-    const size_t rows = prec == 2 ? (size_t)tc_dtab_ldb(Nb) : (size_t)Nb;
-    CKS(make_entry(ctx, e, el * (size_t)blk_off(Lh) * rows));
+    CKS(make_entry(ctx, e, el * (size_t)blk_off(Lh) * Nb));
     ctx->launches[SLSHT_STAGE_TABLES]++;
     cudaError_t er = prec == SLSHT_FP64 ? launch_dtable_f64(D, (double*)e.ptr, Lh, Nb, st)
-                     : prec == 2 ? launch_dtable_f32_t(D, (float*)e.ptr, Lh, Nb, tc_dtab_ldb(Nb), st)
-                                 : launch_dtable_f32(D, (float*)e.ptr, Lh, Nb, st);
+                                        : launch_dtable_f32(D, (float*)e.ptr, Lh, Nb, st);
     if (er != cudaSuccess) { record_cuda_error("launch_dtable", er); return SLSHT_E_CUDA; }
     CK(cudaEventRecord(e.ready, st));
     it = ctx->dtab.emplace(key, e).first;
@@ -564,7 +563,7 @@ static int forward_impl(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
   {
     std::lock_guard<std::mutex> g(ctx->mu);
     CKS(get_delta(ctx, Lh, st, &D));
-    if (route == 1) CKS(get_dtab(ctx, Lh, Nb, tc ? 2 : d->prec, st, &dt));
+    if (route == 1) CKS(get_dtab(ctx, Lh, Nb, d->prec, st, &dt));
     CKS(get_phase(ctx, Ng, K, -(Lh - 1), d->prec, st, &eg));
     if (tc) CKS(get_etab(ctx, Na, Lh, st, &etab));
     else CKS(get_phase(ctx, Na, Lh, 0, d->prec, st, &csa));
@@ -593,6 +592,8 @@ static int forward_impl(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
   CKS(ws_reserve(ctx, w, &w.kc, &w.kc_cap, sizeof(double2) * (size_t)n_pairs * Lh * Lh));
   CKS(ws_reserve(ctx, w, &w.X, &w.X_cap, x_per_pair * (size_t)P));
   CKS(ws_reserve(ctx, w, &w.X2, &w.X2_cap, x_per_pair * (size_t)P));
+  const size_t el2 = f64 ? sizeof(double2) : sizeof(float2);
+  if (route == 1) CKS(ws_reserve(ctx, w, &w.H, &w.H_cap, el2 * (size_t)Lh * Lh * J));
   if (route == 2) {
     CKS(ws_reserve(ctx, w, &w.C, &w.C_cap, sizeof(double2) * (size_t)P * K * K * K));
     CKS(ws_reserve(ctx, w, &w.Y, &w.Y_cap, sizeof(double2) * (size_t)P * Nb * K * K));
@@ -611,6 +612,17 @@ static int forward_impl(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
   // the coupling of every pair in one launch (one CTA per pair fills the GPU)
   LAUNCH(SLSHT_STAGE_COUPLE, ax,
          launch_couple((const double2*)f_dev, Lf, Lh, (const int2*)lm_dev, n_pairs, (double2*)w.kc, ax));
+  // route 1: the window rotated to every (beta, gamma) sample, once per call
+  if (route == 1) {
+    if (f64)
+      LAUNCH(SLSHT_STAGE_BETA, ax,
+             launch_rotwin_f64((const double2*)h_dev, (const double*)dt, (const double2*)eg, Lh, Nb, Ng,
+                               (double2*)w.H, ax));
+    else
+      LAUNCH(SLSHT_STAGE_BETA, ax,
+             launch_rotwin_f32((const double2*)h_dev, (const float*)dt, (const float2*)eg, Lh, Nb, Ng,
+                               (float2*)w.H, ax));
+  }
   void* Xb[2] = {w.X, w.X2};
   int ci = 0;
   for (int32_t off = 0; off < n_pairs; off += P, ++ci) {
@@ -625,17 +637,27 @@ static int forward_impl(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
       LAUNCH(SLSHT_STAGE_CTENSOR, ax, launch_beta_dft((const double2*)w.C, Lh, Nb, np, (double2*)w.Y, ax));
     }
     const double2* Ysrc = route == 2 ? (const double2*)w.Y : nullptr;
-    if (tc) {
+    if (route == 1) {
+      if (tc) {
+        LAUNCH(SLSHT_STAGE_BETA, ax,
+               launch_xa_from_h(kcc, (const float2*)w.H, Lh, Nb, Ng, np, X, ax));
+      } else if (f64) {
+        LAUNCH(SLSHT_STAGE_BETA, ax,
+               launch_x_from_h_f64(kcc, (const double2*)w.H, Lh, (int)J, np, (double2*)X, ax));
+      } else {
+        LAUNCH(SLSHT_STAGE_BETA, ax,
+               launch_x_from_h_f32(kcc, (const float2*)w.H, Lh, (int)J, np, (float2*)X, ax));
+      }
+    } else if (tc) {
       LAUNCH(SLSHT_STAGE_BETA, ax,
-             launch_betagamma_tc(kcc, (const double2*)h_dev, (const float*)dt, Ysrc,
-                                 (const float2*)eg, Lh, Nb, Ng, np, X, ax));
+             launch_betagamma_tc(kcc, (const double2*)h_dev, nullptr, Ysrc, (const float2*)eg, Lh, Nb, Ng, np, X, ax));
     } else if (f64) {
       LAUNCH(SLSHT_STAGE_BETA, ax,
-             launch_betagamma_f64(kcc, (const double2*)h_dev, (const double*)dt, Ysrc,
+             launch_betagamma_f64(kcc, (const double2*)h_dev, nullptr, Ysrc,
                                   (const double2*)eg, Lh, Nb, Ng, np, (double2*)X, ax));
     } else {
       LAUNCH(SLSHT_STAGE_BETA, ax,
-             launch_betagamma_f32(kcc, (const double2*)h_dev, (const float*)dt, Ysrc,
+             launch_betagamma_f32(kcc, (const double2*)h_dev, nullptr, Ysrc,
                                   (const float2*)eg, Lh, Nb, Ng, np, (float2*)X, ax));
     }
     CK(cudaEventRecord(w.x_ready[ci & 1], ax));

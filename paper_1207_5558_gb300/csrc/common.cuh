@@ -36,8 +36,6 @@ cudaError_t launch_delta(double* D, int Lh, cudaStream_t st);
 // dt[b * S + blk_off(p) + (q+p)(2p+1) + (q'+p)], S = blk_off(Lh).
 cudaError_t launch_dtable_f64(const double* D, double* dt, int Lh, int Nb, cudaStream_t st);
 cudaError_t launch_dtable_f32(const double* D, float* dt, int Lh, int Nb, cudaStream_t st);
-// Same values, layout [S][ldb] with beta fastest (ldb >= Nb, padding zeroed).
-cudaError_t launch_dtable_f32_t(const double* D, float* dt, int Lh, int Nb, int ldb, cudaStream_t st);
 // tab[i * R + r] = (cos, sin)(2 pi (r0 + r) i / N), i < N, r < R.
 cudaError_t launch_phase_f64(double2* tab, int N, int R, int r0, cudaStream_t st);
 cudaError_t launch_phase_f32(float2* tab, int N, int R, int r0, cudaStream_t st);
@@ -66,6 +64,19 @@ cudaError_t launch_betagamma_f64(const double2* kc, const double2* h, const doub
 cudaError_t launch_betagamma_f32(const double2* kc, const double2* h, const float* dt,
                                  const double2* Y, const float2* eg, int Lh, int Nb, int Ng,
                                  int npairs, float2* Xs, cudaStream_t st);
+
+// Rotated window H^p_q(j) = sum_q' h_p^q' d^p_{q,q'}(beta_b) e^{-i q' gamma_c},
+// H[(p*p+p+q) * J + j], j = b*Ng + c; dt in the [b][S] layout.
+cudaError_t launch_rotwin_f64(const double2* h, const double* dt, const double2* eg, int Lh, int Nb, int Ng,
+                              double2* H, cudaStream_t st);
+cudaError_t launch_rotwin_f32(const double2* h, const float* dt, const float2* eg, int Lh, int Nb, int Ng,
+                              float2* H, cudaStream_t st);
+// X_q(j) = sum_{p>=|q|} k(p,q) H^p_q(j), written in the paired form of
+// launch_betagamma_* for the CUDA-core alpha stage.
+cudaError_t launch_x_from_h_f64(const double2* kc, const double2* H, int Lh, int J, int npairs, double2* Xs,
+                                cudaStream_t st);
+cudaError_t launch_x_from_h_f32(const double2* kc, const float2* H, int Lh, int J, int npairs, float2* Xs,
+                                cudaStream_t st);
 
 // g[pair][a][j] = X_0 + sum_r (P_r cos(r alpha_a) - i M_r sin(r alpha_a)).
 cudaError_t launch_alpha_f64(const double2* Xs, const double2* csa, int Lh, int Na, int J,

@@ -175,6 +175,10 @@ cudaError_t launch_couple(const double2* f, int Lf, int Lh, const int2* lm, int 
                           double2* kc, cudaStream_t st) {
   if (npairs <= 0) return cudaSuccess;
   const int threads = Lh * Lh < 256 ? ((Lh * Lh + 31) / 32) * 32 : 256;
+  // same carveout as the kernels it runs beside (see the tensor-core alpha stage)
+  cudaFuncSetAttribute(k_couple<32>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  cudaFuncSetAttribute(k_couple<64>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  cudaFuncSetAttribute(k_couple<128>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   if (Lh <= 16) k_couple<32><<<npairs, threads, 0, st>>>(f, Lf, Lh, lm, kc);
   else if (Lh <= 32) k_couple<64><<<npairs, threads, 0, st>>>(f, Lf, Lh, lm, kc);
   else k_couple<128><<<npairs, threads, 0, st>>>(f, Lf, Lh, lm, kc);

@@ -11,6 +11,8 @@
 //     (Eq. alternative_harmonic_formulation_2_2),
 // and both feed the same gamma sum, which also forms the +-q pairs the alpha
 // stage consumes.
+#include <algorithm>
+
 #include "common.cuh"
 
 // ---------------------------------------------------------------------------
@@ -103,6 +105,8 @@ cudaError_t launch_beta_dft(const double2* C, int Lh, int Nb, int npairs, double
 // beta + gamma for one (pair, beta row):
 //   G[q][q'] = sum_p k(p,q) h_p^{q'} d^p_{q,q'}(beta_b)   (or G = Y[pair][b])
 //   X_q[c]   = sum_q' G[q][q'] e^{-i q' gamma_c}
+//            = G[q][0] + sum_{s>=1} (G[q][s] + G[q][-s]) cos(s gamma_c)
+//                      - i (G[q][s] - G[q][-s]) sin(s gamma_c)        (+-q' paired)
 // and the +-q pairs for the alpha stage: Xs[c=0] = X_0, Xs[2r-1] = X_r + X_-r,
 // Xs[2r] = X_r - X_-r.  T is the arithmetic type of the sums.
 template <typename T>
@@ -113,67 +117,81 @@ __global__ void k_betagamma(const double2* __restrict__ kc, const double2* __res
   typedef typename vec2<T>::t T2;
   extern __shared__ unsigned char smem_raw[];
   const int K = 2 * Lh - 1;
+  const int LhP = Lh + 1;                         // padded row: rows q, q+1 on different banks
   const int b = blockIdx.x, pair = blockIdx.y;
   T2* sk = reinterpret_cast<T2*>(smem_raw);      // [Lh*Lh]
   T2* sh = sk + Lh * Lh;                          // [Lh*Lh]
-  T2* sG = sh + Lh * Lh;                          // [K*K]
-  T2* sE = sG + K * K;                            // [K][Ng] (cos, sin)(q' gamma_c), c fastest
+  T2* sGp = sh + Lh * Lh;                         // [K][LhP]  G[q][s] + G[q][-s] (s = 0: G[q][0])
+  T2* sGm = sGp + K * LhP;                        // [K][LhP]  G[q][s] - G[q][-s]
+  T2* sE = sGm + K * LhP;                         // [Lh][Ng] (cos, sin)(s gamma_c), c fastest
   const int n2 = Lh * Lh;
   for (int t = threadIdx.x; t < n2; t += blockDim.x) {
     const double2 kv = kc[(size_t)pair * n2 + t], hv = h[t];
     sk[t] = mk2((T)kv.x, (T)kv.y);
     sh[t] = mk2((T)hv.x, (T)hv.y);
   }
-  for (int t = threadIdx.x; t < Ng * K; t += blockDim.x) {
-    const int k = t / Ng, c = t % Ng;
-    sE[t] = eg[c * K + k];
+  for (int t = threadIdx.x; t < Ng * Lh; t += blockDim.x) {
+    const int sidx = t / Ng, c = t % Ng;
+    sE[t] = eg[c * K + sidx + (Lh - 1)];
   }
   __syncthreads();
-  if (Y == nullptr) {
-    const int S = blk_off(Lh);
-    const T* drow = dt + (size_t)b * S;
-    for (int t = threadIdx.x; t < K * K; t += blockDim.x) {
-      const int q = t / K - (Lh - 1), qp = t % K - (Lh - 1);
-      const int p0 = max(abs(q), abs(qp));
-      T re = 0, im = 0;
-      for (int p = p0; p < Lh; ++p) {
-        const T2 kv = sk[p * p + p + q], hv = sh[p * p + p + qp];
-        const T d = drow[blk_off(p) + (q + p) * (2 * p + 1) + (qp + p)];
-        const T khr = kv.x * hv.x - kv.y * hv.y, khi = kv.x * hv.y + kv.y * hv.x;
-        re = fma(d, khr, re);
-        im = fma(d, khi, im);
+  const int S = blk_off(Lh);
+  const T* drow = dt ? dt + (size_t)b * S : nullptr;
+  for (int t = threadIdx.x; t < K * Lh; t += blockDim.x) {
+    const int qi = t / Lh, sidx = t % Lh;
+    const int q = qi - (Lh - 1);
+    T pr = 0, pim = 0, mr = 0, mim = 0;
+    if (Y == nullptr) {
+      for (int p = max(abs(q), sidx); p < Lh; ++p) {
+        const T2 kv = sk[p * p + p + q];
+        const int row = blk_off(p) + (q + p) * (2 * p + 1) + p;
+        {
+          const T2 hv = sh[p * p + p + sidx];
+          const T d = drow[row + sidx];
+          pr = fma(d, kv.x * hv.x - kv.y * hv.y, pr);
+          pim = fma(d, kv.x * hv.y + kv.y * hv.x, pim);
+        }
+        if (sidx > 0) {
+          const T2 hv = sh[p * p + p - sidx];
+          const T d = drow[row - sidx];
+          mr = fma(d, kv.x * hv.x - kv.y * hv.y, mr);
+          mim = fma(d, kv.x * hv.y + kv.y * hv.x, mim);
+        }
       }
-      sG[t] = mk2(re, im);
+    } else {
+      const double2* src = Y + (((size_t)pair * Nb + b) * K + qi) * K;
+      const double2 vp = src[sidx + Lh - 1];
+      pr = (T)vp.x; pim = (T)vp.y;
+      if (sidx > 0) { const double2 vm = src[-sidx + Lh - 1]; mr = (T)vm.x; mim = (T)vm.y; }
     }
-  } else {
-    const double2* src = Y + ((size_t)pair * Nb + b) * K * K;
-    for (int t = threadIdx.x; t < K * K; t += blockDim.x) {
-      const double2 v = src[t];
-      sG[t] = mk2((T)v.x, (T)v.y);
-    }
+    const int o = qi * LhP + sidx;
+    if (sidx == 0) { sGp[o] = mk2(pr, pim); sGm[o] = mk2(pr, pim); }
+    else { sGp[o] = mk2(pr + mr, pim + mim); sGm[o] = mk2(pr - mr, pim - mim); }
   }
   __syncthreads();
   const size_t J = (size_t)Nb * Ng;
   T2* out = Xs + (size_t)pair * K * J;
   for (int t = threadIdx.x; t < Lh * Ng; t += blockDim.x) {
     const int r = t / Ng, c = t % Ng;
-    const T2* gp = sG + (r + Lh - 1) * K;          // row q = +r
-    const T2* gm = sG + (-r + Lh - 1) * K;         // row q = -r
-    const T2* e = sE + c;                          // stride Ng: no bank conflicts across c
-    T pr = 0, pi = 0, mr = 0, mi = 0;
-    for (int k = 0; k < K; ++k) {                  // multiply by (cos - i sin)
-      const T2 E = e[k * Ng], a = gp[k], bb = gm[k];
-      pr = fma(a.x, E.x, pr); pr = fma(a.y, E.y, pr);
-      pi = fma(a.y, E.x, pi); pi = fma(-a.x, E.y, pi);
-      mr = fma(bb.x, E.x, mr); mr = fma(bb.y, E.y, mr);
-      mi = fma(bb.y, E.x, mi); mi = fma(-bb.x, E.y, mi);
+    const T2* ap = sGp + (r + Lh - 1) * LhP;      // row q = +r
+    const T2* am = sGm + (r + Lh - 1) * LhP;
+    const T2* bp = sGp + (-r + Lh - 1) * LhP;     // row q = -r
+    const T2* bm = sGm + (-r + Lh - 1) * LhP;
+    T xr = ap[0].x, xi = ap[0].y, yr = bp[0].x, yi = bp[0].y;
+    for (int sidx = 1; sidx < Lh; ++sidx) {       // (Gp cos - i Gm sin)
+      const T2 E = sE[sidx * Ng + c];
+      const T2 P1 = ap[sidx], M1 = am[sidx], P2 = bp[sidx], M2 = bm[sidx];
+      xr = fma(P1.x, E.x, xr); xr = fma(M1.y, E.y, xr);
+      xi = fma(P1.y, E.x, xi); xi = fma(-M1.x, E.y, xi);
+      yr = fma(P2.x, E.x, yr); yr = fma(M2.y, E.y, yr);
+      yi = fma(P2.y, E.x, yi); yi = fma(-M2.x, E.y, yi);
     }
     const size_t j = (size_t)b * Ng + c;
     if (r == 0) {
-      out[j] = mk2(pr, pi);
+      out[j] = mk2(xr, xi);
     } else {
-      out[(size_t)(2 * r - 1) * J + j] = mk2(pr + mr, pi + mi);
-      out[(size_t)(2 * r) * J + j] = mk2(pr - mr, pi - mi);
+      out[(size_t)(2 * r - 1) * J + j] = mk2(xr + yr, xi + yi);
+      out[(size_t)(2 * r) * J + j] = mk2(xr - yr, xi - yi);
     }
   }
 }
@@ -186,7 +204,7 @@ static cudaError_t launch_betagamma_t(const double2* kc, const double2* h, const
   if (npairs <= 0) return cudaSuccess;
   typedef typename vec2<T>::t T2;
   const int K = 2 * Lh - 1;
-  const size_t smem = sizeof(T2) * ((size_t)2 * Lh * Lh + (size_t)K * K + (size_t)Ng * K);
+  const size_t smem = sizeof(T2) * ((size_t)2 * Lh * Lh + (size_t)2 * K * (Lh + 1) + (size_t)Ng * Lh);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_betagamma<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -207,4 +225,132 @@ cudaError_t launch_betagamma_f32(const double2* kc, const double2* h, const floa
                                  const double2* Y, const float2* eg, int Lh, int Nb, int Ng,
                                  int npairs, float2* Xs, cudaStream_t st) {
   return launch_betagamma_t<float>(kc, h, dt, Y, eg, Lh, Nb, Ng, npairs, Xs, st);
+}
+
+// ---------------------------------------------------------------------------
+// Rotated-window route.  Regrouping the sums of
+// Eq. alternative_harmonic_formulation_wigner,
+//   g(a, j) = sum_q e^{-i q alpha_a} sum_{p>=|q|} k(p,q) H^p_q(j),
+//   H^p_q(j) = sum_{q'} h_p^{q'} d^p_{q,q'}(beta_b) e^{-i q' gamma_c},   j = b*Ng + c,
+// H is the window's coefficients rotated by (0, beta_b, gamma_c) (Eq. rotation_non_symm
+// with Eq. Dlm): it does not depend on the pair (l, m), so it is built once per call and
+// every pair costs only Lh^2 multiply-adds per column.
+// H layout: [p*p + p + q][J] (column index fastest).
+template <typename T>
+__global__ void k_rotwin(const double2* __restrict__ h, const T* __restrict__ dt,
+                         const typename vec2<T>::t* __restrict__ eg, int Lh, int Nb, int Ng,
+                         typename vec2<T>::t* __restrict__ H) {
+  typedef typename vec2<T>::t T2;
+  const int K = 2 * Lh - 1, S = blk_off(Lh), n2 = Lh * Lh;
+  const int b = blockIdx.x;
+  const size_t J = (size_t)Nb * Ng;
+  for (int t = blockIdx.y * blockDim.x + threadIdx.x; t < n2 * Ng; t += gridDim.y * blockDim.x) {
+    const int pq = t / Ng, c = t % Ng;
+    int p = (int)sqrt((double)pq);
+    while (p * p > pq) --p;
+    while ((p + 1) * (p + 1) <= pq) ++p;
+    const int q = pq - p * p - p;
+    const T* drow = dt + (size_t)b * S + blk_off(p) + (q + p) * (2 * p + 1);
+    const T2* erow = eg + (size_t)c * K + (Lh - 1);
+    T re = 0, im = 0;
+    for (int qp = -p; qp <= p; ++qp) {           // h d (cos - i sin)
+      const double2 hv = __ldg(h + p * p + p + qp);
+      const T d = __ldg(drow + qp + p);
+      const T2 E = erow[qp];
+      const T ar = d * (T)hv.x, ai = d * (T)hv.y;
+      re = fma(ar, E.x, re); re = fma(ai, E.y, re);
+      im = fma(ai, E.x, im); im = fma(-ar, E.y, im);
+    }
+    H[(size_t)pq * J + (size_t)b * Ng + c] = mk2(re, im);
+  }
+}
+
+template <typename T>
+static cudaError_t launch_rotwin_t(const double2* h, const T* dt, const typename vec2<T>::t* eg, int Lh,
+                                   int Nb, int Ng, typename vec2<T>::t* H, cudaStream_t st) {
+  const long long items = (long long)Lh * Lh * Ng;
+  dim3 grid(Nb, (unsigned)std::min<long long>((items + 255) / 256, 64));
+  k_rotwin<T><<<grid, 256, 0, st>>>(h, dt, eg, Lh, Nb, Ng, H);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rotwin_f64(const double2* h, const double* dt, const double2* eg, int Lh, int Nb, int Ng,
+                              double2* H, cudaStream_t st) {
+  return launch_rotwin_t<double>(h, dt, eg, Lh, Nb, Ng, H, st);
+}
+cudaError_t launch_rotwin_f32(const double2* h, const float* dt, const float2* eg, int Lh, int Nb, int Ng,
+                              float2* H, cudaStream_t st) {
+  return launch_rotwin_t<float>(h, dt, eg, Lh, Nb, Ng, H, st);
+}
+
+// X from H for the CUDA-core alpha stage (paired output as k_betagamma):
+//   X_q(j) = sum_{p>=|q|} k(p,q) H^p_q(j); Xs[0] = X_0, Xs[2r-1] = X_r + X_-r, Xs[2r] = X_r - X_-r.
+// One thread per column j, loads of H coalesced across the warp.
+template <typename T>
+__global__ void __launch_bounds__(128) k_x_from_h(const double2* __restrict__ kc, const typename vec2<T>::t* __restrict__ H,
+                                                  int Lh, int J, typename vec2<T>::t* __restrict__ Xs) {
+  typedef typename vec2<T>::t T2;
+  extern __shared__ unsigned char smem_raw[];
+  T2* sk = reinterpret_cast<T2*>(smem_raw);      // [Lh*Lh]
+  const int pair = blockIdx.y, n2 = Lh * Lh, K = 2 * Lh - 1;
+  for (int t = threadIdx.x; t < n2; t += blockDim.x) {
+    const double2 v = kc[(size_t)pair * n2 + t];
+    sk[t] = mk2((T)v.x, (T)v.y);
+  }
+  __syncthreads();
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= J) return;
+  T2* out = Xs + (size_t)pair * K * J;
+  for (int r = 0; r < Lh; ++r) {
+    T xr = 0, xi = 0, yr = 0, yi = 0;             // X_r and X_-r
+    for (int p0 = r; p0 < Lh; p0 += 8) {          // eight degrees' loads in flight at once
+      T2 ha[8], hb[8];
+#pragma unroll
+      for (int v = 0; v < 8; ++v) {
+        const int p = p0 + v;
+        ha[v] = p < Lh ? H[(size_t)(p * p + p + r) * J + j] : mk2((T)0, (T)0);
+        hb[v] = (p < Lh && r > 0) ? H[(size_t)(p * p + p - r) * J + j] : mk2((T)0, (T)0);
+      }
+#pragma unroll
+      for (int v = 0; v < 8; ++v) {
+        const int p = p0 + v;
+        if (p < Lh) {
+          const T2 ka = sk[p * p + p + r], kb = sk[p * p + p - r];
+          xr = fma(ka.x, ha[v].x, xr); xr = fma(-ka.y, ha[v].y, xr);
+          xi = fma(ka.x, ha[v].y, xi); xi = fma(ka.y, ha[v].x, xi);
+          yr = fma(kb.x, hb[v].x, yr); yr = fma(-kb.y, hb[v].y, yr);
+          yi = fma(kb.x, hb[v].y, yi); yi = fma(kb.y, hb[v].x, yi);
+        }
+      }
+    }
+    if (r == 0) {
+      out[j] = mk2(xr, xi);
+    } else {
+      out[(size_t)(2 * r - 1) * J + j] = mk2(xr + yr, xi + yi);
+      out[(size_t)(2 * r) * J + j] = mk2(xr - yr, xi - yi);
+    }
+  }
+}
+
+template <typename T>
+static cudaError_t launch_x_from_h_t(const double2* kc, const typename vec2<T>::t* H, int Lh, int J, int npairs,
+                                     typename vec2<T>::t* Xs, cudaStream_t st) {
+  if (npairs <= 0 || J <= 0) return cudaSuccess;
+  typedef typename vec2<T>::t T2;
+  const size_t smem = sizeof(T2) * (size_t)Lh * Lh;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_x_from_h<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid((J + 127) / 128, npairs);
+  k_x_from_h<T><<<grid, 128, smem, st>>>(kc, H, Lh, J, Xs);
+  return cudaGetLastError();
+}
+cudaError_t launch_x_from_h_f64(const double2* kc, const double2* H, int Lh, int J, int npairs, double2* Xs,
+                                cudaStream_t st) {
+  return launch_x_from_h_t<double>(kc, H, Lh, J, npairs, Xs, st);
+}
+cudaError_t launch_x_from_h_f32(const double2* kc, const float2* H, int Lh, int J, int npairs, float2* Xs,
+                                cudaStream_t st) {
+  return launch_x_from_h_t<float>(kc, H, Lh, J, npairs, Xs, st);
 }

@@ -78,9 +78,9 @@ __device__ __forceinline__ int degree_of(int idx, int Lh) {
 
 // d^p_{q,q'}(beta_b) = Re[ i^{q-q'} sum_{q''} Delta^p_{q''q} Delta^p_{q''q'} e^{-i q'' beta_b} ]
 // (Eq. WignerD_expansion_new at alpha = gamma = 0), beta_b = 2 pi b / (2 Nb - 1).
-// ldb == 0: layout [b][S]; ldb > 0: layout [S][ldb] (b fastest, rows padded to ldb).
+// Layout [b][S].
 template <typename T>
-__global__ void k_dtable(const double* __restrict__ D, T* __restrict__ dt, int Lh, int Nb, int ldb) {
+__global__ void k_dtable(const double* __restrict__ D, T* __restrict__ dt, int Lh, int Nb) {
   const int S = blk_off(Lh);
   const int b = blockIdx.y;
   const long long M = 2LL * Nb - 1;
@@ -105,32 +105,22 @@ __global__ void k_dtable(const double* __restrict__ D, T* __restrict__ dt, int L
       case 2: v = -sr; break;
       default: v = si; break;
     }
-    if (ldb > 0) dt[(size_t)idx * ldb + b] = (T)v;
-    else dt[(size_t)b * S + idx] = (T)v;
+    dt[(size_t)b * S + idx] = (T)v;
   }
 }
 
 cudaError_t launch_dtable_f64(const double* D, double* dt, int Lh, int Nb, cudaStream_t st) {
   const int S = blk_off(Lh);
   dim3 grid((S + 255) / 256, Nb);
-  k_dtable<double><<<grid, 256, 0, st>>>(D, dt, Lh, Nb, 0);
+  k_dtable<double><<<grid, 256, 0, st>>>(D, dt, Lh, Nb);
   return cudaGetLastError();
 }
 cudaError_t launch_dtable_f32(const double* D, float* dt, int Lh, int Nb, cudaStream_t st) {
   const int S = blk_off(Lh);
   dim3 grid((S + 255) / 256, Nb);
-  k_dtable<float><<<grid, 256, 0, st>>>(D, dt, Lh, Nb, 0);
+  k_dtable<float><<<grid, 256, 0, st>>>(D, dt, Lh, Nb);
   return cudaGetLastError();
 }
-cudaError_t launch_dtable_f32_t(const double* D, float* dt, int Lh, int Nb, int ldb, cudaStream_t st) {
-  const int S = blk_off(Lh);
-  cudaError_t e = cudaMemsetAsync(dt, 0, sizeof(float) * (size_t)S * ldb, st);
-  if (e != cudaSuccess) return e;
-  dim3 grid((S + 255) / 256, Nb);
-  k_dtable<float><<<grid, 256, 0, st>>>(D, dt, Lh, Nb, ldb);
-  return cudaGetLastError();
-}
-
 template <typename T2>
 __global__ void k_phase(T2* __restrict__ tab, int N, int R, int r0) {
   const long long n = (long long)N * R;

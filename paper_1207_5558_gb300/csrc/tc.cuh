@@ -10,14 +10,14 @@ size_t tc_etab_bytes(int Na, int Lh);
 cudaError_t launch_tc_etab(void* etab, int Na, int Lh, cudaStream_t st);
 // Bytes of the A operand (split-FP16 X, per-row scales) of ONE pair.
 size_t tc_xblob_bytes(int Nb, int Ng, int Lh);
-// Row stride (beta samples, padded) of the beta-fastest FP32 d table the
-// tensor-core producer reads.
-int tc_dtab_ldb(int Nb);
-// beta + gamma stages writing the A operand blobs (FP32 sums); dt is the
-// beta-fastest table of launch_dtable_f32_t with row stride tc_dtab_ldb(Nb).
+// Factoring route: gamma sum of Y (launch_beta_dft) writing the A operand blobs
+// (FP32 sums); dt is unused (pass nullptr), Y is required.
 cudaError_t launch_betagamma_tc(const double2* kc, const double2* h, const float* dt,
                                 const double2* Y, const float2* eg, int Lh, int Nb, int Ng,
                                 int npairs, void* xblob, cudaStream_t st);
+// Rotated-window route: the A operand blobs from H (launch_rotwin_f32).
+cudaError_t launch_xa_from_h(const double2* kc, const float2* H, int Lh, int Nb, int Ng, int npairs, void* xblob,
+                             cudaStream_t st);
 // alpha stage on tcgen05: g[pair][a][j] complex64.
 cudaError_t launch_alpha_tc(const void* xblob, const void* etab, int Lh, int Na, int Nb, int Ng,
                             int npairs, float2* g, int num_sms, cudaStream_t st);
