@@ -285,85 +285,96 @@ cudaError_t launch_betagamma_tc(const double2* kc, const double2* h, const float
 
 // ---------------------------------------------------------------- A operand from H
 // Rotated-window route: X_q(j) = sum_{p>=|q|} k(p,q) H^p_q(j) (H from launch_rotwin_f32),
-// one thread per column j of a 128-column tile; the row is scaled (largest entry
-// into [2^14, 2^15)), split into FP16 hi/lo and written swizzled; padding rows
-// of the last tile are zero.
-__global__ void __launch_bounds__(TC_M)
+// for one pair and one 128-column tile per CTA.
+//   phase 1: one item per (q, column): a loop over exactly its degrees p >= |q|,
+//            H loads coalesced across columns, k(p,q) broadcast; X goes to a shared
+//            tile [64 slots][128 columns] (Re X_q at slot 15+q, Im at 47+q);
+//   phase 2: per column, the largest |entry| -> scale 2^e into [2^14, 2^15);
+//   phase 3: per (column, 16-byte chunk): scale, split into FP16 hi/lo, store
+//            swizzled.  Columns beyond J (padding of the last tile) are zero.
+__global__ void __launch_bounds__(256)
 k_xa_from_h(const double2* __restrict__ kc, const float2* __restrict__ H, int Lh, int J,
             unsigned char* __restrict__ xblob, size_t blob_stride, int tiles) {
-  extern __shared__ float2 skf[];               // [Lh*Lh]
-  const int tile = blockIdx.x, pair = blockIdx.y, r = threadIdx.x;
+  __shared__ float sX[TC_KB][TC_M];
+  __shared__ float2 sk[16 * 16];
+  __shared__ int sEx[TC_M];
+  const int tile = blockIdx.x, pair = blockIdx.y;
   const int n2 = Lh * Lh;
   for (int t = threadIdx.x; t < n2; t += blockDim.x) {
     const double2 v = kc[(size_t)pair * n2 + t];
-    skf[t] = make_float2((float)v.x, (float)v.y);
+    sk[t] = make_float2((float)v.x, (float)v.y);
+  }
+  __syncthreads();
+  const int jt = tile * TC_M;
+  for (int it = threadIdx.x; it < 32 * TC_M; it += blockDim.x) {
+    const int u = it / TC_M, r = it % TC_M;
+    const int q = u - 15, aq = q < 0 ? -q : q;
+    const int j = jt + r;
+    float ar = 0.f, ai = 0.f;
+    if (u < 31 && aq < Lh && j < J) {
+      const float2* hp = H + j;
+      int p = aq;
+      for (; p + 3 < Lh; p += 4) {                  // four loads in flight per step
+        float2 hv[4], kv[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int pq = (p + v) * (p + v) + (p + v) + q;
+          hv[v] = __ldg(hp + (size_t)pq * J);
+          kv[v] = sk[pq];
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          ar = fmaf(kv[v].x, hv[v].x, ar); ar = fmaf(-kv[v].y, hv[v].y, ar);
+          ai = fmaf(kv[v].x, hv[v].y, ai); ai = fmaf(kv[v].y, hv[v].x, ai);
+        }
+      }
+      for (; p < Lh; ++p) {
+        const int pq = p * p + p + q;
+        const float2 hv = __ldg(hp + (size_t)pq * J), kv = sk[pq];
+        ar = fmaf(kv.x, hv.x, ar); ar = fmaf(-kv.y, hv.y, ar);
+        ai = fmaf(kv.x, hv.y, ai); ai = fmaf(kv.y, hv.x, ai);
+      }
+    }
+    sX[u][r] = ar;
+    sX[32 + u][r] = ai;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < TC_M; r += blockDim.x) {
+    float mx = 0.f;
+#pragma unroll 8
+    for (int k = 0; k < TC_KB; ++k) mx = fmaxf(mx, fabsf(sX[k][r]));
+    int ex = 0;
+    if (mx > 0.f) frexpf(mx, &ex);
+    sEx[r] = mx > 0.f ? min(125, max(-125, 15 - ex)) : 0;
   }
   __syncthreads();
   unsigned char* blob = xblob + (size_t)pair * blob_stride;
   unsigned char* tb = blob + (size_t)tile * TC_A_BYTES;
   float* scales = reinterpret_cast<float*>(blob + (size_t)tiles * TC_A_BYTES);
-  const int j = tile * TC_M + r;
-  if (j >= J) {
-#pragma unroll
-    for (int k0 = 0; k0 < TC_KB; k0 += 8) {
-      *reinterpret_cast<uint4*>(tb + sw128_off(r, k0)) = make_uint4(0, 0, 0, 0);
-      *reinterpret_cast<uint4*>(tb + TC_A_HALF + sw128_off(r, k0)) = make_uint4(0, 0, 0, 0);
-    }
-    scales[j] = 0.f;
-    return;
-  }
-  float xr[32], xi[32];                          // slot 15 + q, |q| <= 15
-#pragma unroll
-  for (int u = 0; u < 32; ++u) {
-    const int q = u - 15;
-    // every degree's load is issued before the multiply-adds use them
-    float2 hv[16];
-#pragma unroll
-    for (int p = 0; p < 16; ++p) {
-      const bool on = u < 31 && p >= (q < 0 ? -q : q) && p < Lh;
-      hv[p] = on ? __ldg(H + (size_t)(p * p + p + q) * J + j) : make_float2(0.f, 0.f);
-    }
-    float ar = 0.f, ai = 0.f;
-#pragma unroll
-    for (int p = 0; p < 16; ++p) {
-      const bool on = u < 31 && p >= (q < 0 ? -q : q) && p < Lh;
-      const float2 kv = on ? skf[p * p + p + q] : make_float2(0.f, 0.f);
-      ar = fmaf(kv.x, hv[p].x, ar); ar = fmaf(-kv.y, hv[p].y, ar);
-      ai = fmaf(kv.x, hv[p].y, ai); ai = fmaf(kv.y, hv[p].x, ai);
-    }
-    xr[u] = ar;
-    xi[u] = ai;
-  }
-  float mx = 0.f;
-#pragma unroll
-  for (int u = 0; u < 32; ++u) mx = fmaxf(mx, fmaxf(fabsf(xr[u]), fabsf(xi[u])));
-  int ex = 0;
-  if (mx > 0.f) frexpf(mx, &ex);
-  const int e = mx > 0.f ? min(125, max(-125, 15 - ex)) : 0;    // mx * 2^e in [2^14, 2^15)
-  const float sc = __int_as_float((127 + e) << 23);
-#pragma unroll
-  for (int k0 = 0; k0 < TC_KB; k0 += 8) {
+  for (int it = threadIdx.x; it < TC_M * (TC_KB / 8); it += blockDim.x) {
+    const int r = it % TC_M, k0 = (it / TC_M) * 8;
+    const int e = sEx[r];
+    const float sc = __int_as_float((127 + e) << 23);
     __align__(16) __half hi[8], lo[8];
 #pragma unroll
     for (int v = 0; v < 8; ++v) {
-      const int k = k0 + v;
-      const float x = (k < 32 ? xr[k & 31] : xi[k & 31]) * sc;
+      const float x = sX[k0 + v][r] * sc;
       hi[v] = __float2half_rn(x);
       lo[v] = __float2half_rn(x - __half2float(hi[v]));
     }
     *reinterpret_cast<uint4*>(tb + sw128_off(r, k0)) = *reinterpret_cast<uint4*>(hi);
     *reinterpret_cast<uint4*>(tb + TC_A_HALF + sw128_off(r, k0)) = *reinterpret_cast<uint4*>(lo);
+    if (k0 == 0) scales[jt + r] = jt + r < J ? __int_as_float((127 - e) << 23) : 0.f;
   }
-  scales[j] = __int_as_float((127 - e) << 23);
 }
 
 cudaError_t launch_xa_from_h(const double2* kc, const float2* H, int Lh, int Nb, int Ng, int npairs, void* xblob,
                              cudaStream_t st) {
   if (npairs <= 0) return cudaSuccess;
+  if (Lh > 16) return cudaErrorInvalidValue;
   const int tiles = tc_tiles(Nb, Ng);
   dim3 grid(tiles, npairs);
-  k_xa_from_h<<<grid, TC_M, sizeof(float2) * (size_t)Lh * Lh, st>>>(kc, H, Lh, Nb * Ng, (unsigned char*)xblob,
-                                                                    tc_xblob_bytes(Nb, Ng, Lh), tiles);
+  k_xa_from_h<<<grid, 256, 0, st>>>(kc, H, Lh, Nb * Ng, (unsigned char*)xblob, tc_xblob_bytes(Nb, Ng, Lh), tiles);
   return cudaGetLastError();
 }
 
