@@ -133,18 +133,21 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def traffic_record():
-    """dram bytes per launch of the alpha kernel from the committed ncu summary,
-    valid only while the kernel source is unchanged (else null)."""
-    src = os.path.join(ROOT, "paper_1207_5558_gb300", "csrc", "alpha_tc.cu")
-    rec = os.path.join(ROOT, "profiles", "alpha_tc_traffic.json")
-    if not (os.path.exists(src) and os.path.exists(rec)):
-        return None, None
+def traffic_record(kernel):
+    """DRAM bytes per output sample of `kernel` from the committed ncu summary
+    (profiles/traffic.json), valid only while the kernel's source file is
+    unchanged since the capture (else None)."""
+    rec = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(rec):
+        return None
+    d = json.load(open(rec)).get(kernel)
+    if not d:
+        return None
+    src = os.path.join(ROOT, d["source"])
+    if not os.path.exists(src):
+        return None
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    d = json.load(open(rec))
-    if d.get("source_sha256_16") != h:
-        return None, d
-    return d, d
+    return d if d.get("source_sha256_16") == h else None
 
 
 def reduce_max(value, dist):
@@ -392,11 +395,11 @@ def main():
     alpha_bytes = 8.0 * samples_step * args.steps
     pk, pk_kind = peaks()
     achieved = alpha_bytes / (alpha_ms / 1e3) / 1e9 if alpha_ms > 0 else None
-    tr, _ = traffic_record()
+    tr = traffic_record("k_alpha_fused")
     roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / pk["hbm_gbs"] if achieved else None,
             "traffic": (tr["dram_bytes_per_sample"] * alpha_bytes / 8.0 / alpha_n) if (tr and alpha_n) else None,
-            "kernel": "k_alpha_tc (tcgen05 alpha stage + store of g)",
+            "kernel": "k_alpha_fused (producer warps build the A operand from H; tcgen05 alpha stage; store of g)",
             "algorithmic_bytes_per_launch": alpha_bytes / alpha_n if alpha_n else None,
             "avg_launch_ms": alpha_ms / alpha_n if alpha_n else None,
             "peak_kind": pk_kind + " (MEASURED_PEAKS hbm_gbs, copy burst)" if pk_kind == "measured" else pk_kind,

@@ -29,19 +29,7 @@
 
 #include "common.cuh"
 #include "tc.cuh"
-
-#define TC_M 128                       // columns j per tile (MMA M)
-#define TC_NC 128                      // alpha rows per chunk
-#define TC_N (2 * TC_NC)               // MMA N (Re and Im halves)
-#define TC_KB 64                       // FP16 elements of K per operand row (128 bytes)
-#define TC_A_HALF (TC_M * TC_KB * 2)   // bytes of one A part (hi or lo): 16 KB
-#define TC_B_HALF (TC_N * TC_KB * 2)   // bytes of one B part: 32 KB
-#define TC_A_BYTES (2 * TC_A_HALF)     // 32 KB
-#define TC_B_BYTES (2 * TC_B_HALF)     // 64 KB
-#define TC_EPI_WARPS 8                  // two per TMEM lane quadrant, each half the columns
-#define TC_THREADS (64 + 32 * TC_EPI_WARPS)
-#define TC_SMEM (2 * TC_A_BYTES + TC_B_BYTES + 1024 + 256)
-#define TC_WAIT_LIMIT (1u << 22)
+#include "tc_ptx.cuh"
 
 bool tc_supported(int Lh, int Na) { return Lh >= 1 && 2 * (2 * Lh - 1) <= TC_KB && Na >= 1; }
 
@@ -56,13 +44,6 @@ size_t tc_xblob_bytes(int Nb, int Ng, int Lh) {
   const size_t t = (size_t)tc_tiles(Nb, Ng);
   const size_t sc = ((t * TC_M * sizeof(float)) + 1023) / 1024 * 1024;
   return t * TC_A_BYTES + sc;
-}
-
-// byte offset of FP16 element (row r, k) inside a 128-row (or 256-row) K-major
-// operand part with the 128-byte swizzle: 16-byte chunk index k/8 XOR (r % 8),
-// rows 128 bytes apart, 8-row groups 1024 bytes apart.
-__host__ __device__ __forceinline__ uint32_t sw128_off(int r, int k) {
-  return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 3) ^ (r & 7)) & 7) << 4) + (k & 7) * 2);
 }
 
 // ---------------------------------------------------------------- E tables
@@ -312,14 +293,14 @@ k_xa_from_h(const double2* __restrict__ kc, const float2* __restrict__ H, int Lh
     const int j = jt + r;
     float ar = 0.f, ai = 0.f;
     if (u < 31 && aq < Lh && j < J) {
-      const float2* hp = H + j;
+      const float2* hp = H + h_index(0, j, n2);      // row pq at hp + pq * 128
       int p = aq;
       for (; p + 3 < Lh; p += 4) {                  // four loads in flight per step
         float2 hv[4], kv[4];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           const int pq = (p + v) * (p + v) + (p + v) + q;
-          hv[v] = __ldg(hp + (size_t)pq * J);
+          hv[v] = __ldg(hp + (size_t)pq * 128);
           kv[v] = sk[pq];
         }
 #pragma unroll
@@ -330,7 +311,7 @@ k_xa_from_h(const double2* __restrict__ kc, const float2* __restrict__ H, int Lh
       }
       for (; p < Lh; ++p) {
         const int pq = p * p + p + q;
-        const float2 hv = __ldg(hp + (size_t)pq * J), kv = sk[pq];
+        const float2 hv = __ldg(hp + (size_t)pq * 128), kv = sk[pq];
         ar = fmaf(kv.x, hv.x, ar); ar = fmaf(-kv.y, hv.y, ar);
         ai = fmaf(kv.x, hv.y, ai); ai = fmaf(kv.y, hv.x, ai);
       }
@@ -377,81 +358,6 @@ cudaError_t launch_xa_from_h(const double2* kc, const float2* H, int Lh, int Nb,
   k_xa_from_h<<<grid, 256, 0, st>>>(kc, H, Lh, Nb * Ng, (unsigned char*)xblob, tc_xblob_bytes(Nb, Ng, Lh), tiles);
   return cudaGetLastError();
 }
-
-// ---------------------------------------------------------------- PTX wrappers
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait for the phase with the given parity.  Gives up when the CTA's
-// abort flag is raised or after TC_WAIT_LIMIT polls; returns false then.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
-  for (uint32_t i = 0; i < TC_WAIT_LIMIT; ++i) {
-    if (mbar_test(bar, parity)) return true;
-    if ((i & 255u) == 255u && *abort_flag) return false;
-  }
-  return false;
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-      "l"(src), "r"(bytes), "r"(bar)
-      : "memory");
-}
-// K-major operand, 128-byte swizzle, 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;                  // leading-dimension offset (unused for this layout)
-  d |= (uint64_t)(1024 >> 4) << 32;        // stride between 8-row groups
-  d |= (uint64_t)1 << 46;                  // descriptor version
-  d |= (uint64_t)2 << 61;                  // 128-byte swizzle
-  return d;
-}
-// kind::f16 instruction descriptor: D = F32, A = B = F16, both K-major, N, M.
-__host__ __device__ constexpr uint32_t umma_idesc_f16(int M, int N) {
-  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
-}
-__device__ __forceinline__ void umma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-               : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-#define TMEM_LD32(taddr, v)                                                                         \
-  asm volatile(                                                                                     \
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"  \
-      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                \
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),         \
-        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),     \
-        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),  \
-        "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),  \
-        "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])                                          \
-      : "r"(taddr))
 
 // ---------------------------------------------------------------- the kernel
 struct TcBars {
@@ -640,7 +546,8 @@ k_alpha_tc(const unsigned char* __restrict__ xblob, size_t blob_stride, int tile
   }
 }
 
-static int* tc_error_word() {
+// Device word a tensor-core kernel sets when it gives up on a bounded wait.
+int* tc_error_word() {
   static int* p = nullptr;
   if (!p) {
     if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) { cudaGetLastError(); p = nullptr; return nullptr; }

@@ -498,7 +498,7 @@ extern "C" int slsht_set_option(slsht_ctx* c, int option, int64_t v) {
       c->opt_beta_route = (int)v;
       return SLSHT_OK;
     case SLSHT_OPT_ALPHA_ENGINE:
-      if (v < 0 || v > 2) return SLSHT_E_ARG;
+      if (v < 0 || v > 3) return SLSHT_E_ARG;
       c->opt_alpha_engine = (int)v;
       return SLSHT_OK;
     case SLSHT_OPT_CHUNK_PAIRS:
@@ -546,14 +546,18 @@ static int forward_impl(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
   const bool host_out = !is_device_ptr(g_out);
   CK(cudaStreamWaitEvent(st, w.done, 0));
 
-  int route, tc;
+  int route, tc, engine;
   int64_t chunk_opt;
   {
     std::lock_guard<std::mutex> g(ctx->mu);
     route = ctx->opt_beta_route ? ctx->opt_beta_route : 1;
     tc = use_tensor_cores(ctx, d) ? 1 : 0;
+    engine = ctx->opt_alpha_engine;
     chunk_opt = ctx->opt_chunk;
   }
+  // rotated-window route on the tensor cores: producer and alpha stage fused
+  // into one kernel unless the separate producer kernel was asked for
+  const bool fused = tc && route == 1 && Lh <= 16 && engine != 2;
   // tables
   const double* D = nullptr;
   const void* dt = nullptr;
@@ -579,6 +583,8 @@ static int forward_impl(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
   int P;
   if (chunk_opt > 0) {
     P = (int)std::min<int64_t>(chunk_opt, n_pairs);
+  } else if (fused) {
+    P = n_pairs;                 // no X scratch: one launch per call
   } else {
     const size_t target = (size_t)96 << 20;
     P = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_pairs, target / std::max<size_t>(1, x_per_pair)));
@@ -590,10 +596,12 @@ static int forward_impl(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
     P = (int)std::max<size_t>(1, std::min<size_t>((size_t)P, stage_limit / std::max<size_t>(1, per_pair_g)));
   }
   CKS(ws_reserve(ctx, w, &w.kc, &w.kc_cap, sizeof(double2) * (size_t)n_pairs * Lh * Lh));
-  CKS(ws_reserve(ctx, w, &w.X, &w.X_cap, x_per_pair * (size_t)P));
-  CKS(ws_reserve(ctx, w, &w.X2, &w.X2_cap, x_per_pair * (size_t)P));
+  if (!fused) {
+    CKS(ws_reserve(ctx, w, &w.X, &w.X_cap, x_per_pair * (size_t)P));
+    CKS(ws_reserve(ctx, w, &w.X2, &w.X2_cap, x_per_pair * (size_t)P));
+  }
   const size_t el2 = f64 ? sizeof(double2) : sizeof(float2);
-  if (route == 1) CKS(ws_reserve(ctx, w, &w.H, &w.H_cap, el2 * (size_t)Lh * Lh * J));
+  if (route == 1) CKS(ws_reserve(ctx, w, &w.H, &w.H_cap, el2 * h_elems(J, Lh * Lh)));
   if (route == 2) {
     CKS(ws_reserve(ctx, w, &w.C, &w.C_cap, sizeof(double2) * (size_t)P * K * K * K));
     CKS(ws_reserve(ctx, w, &w.Y, &w.Y_cap, sizeof(double2) * (size_t)P * Nb * K * K));
@@ -628,41 +636,49 @@ static int forward_impl(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
   for (int32_t off = 0; off < n_pairs; off += P, ++ci) {
     const int np = std::min<int>(P, n_pairs - off);
     void* X = Xb[ci & 1];
-    // ---- producer side (aux stream)
-    CK(cudaStreamWaitEvent(ax, w.x_free[ci & 1], 0));
     const double2* kcc = (const double2*)w.kc + (size_t)off * Lh * Lh;
-    if (route == 2) {
-      LAUNCH(SLSHT_STAGE_CTENSOR, ax,
-             launch_ctensor(kcc, (const double2*)h_dev, D, Lh, np, (double2*)w.C, ax));
-      LAUNCH(SLSHT_STAGE_CTENSOR, ax, launch_beta_dft((const double2*)w.C, Lh, Nb, np, (double2*)w.Y, ax));
-    }
-    const double2* Ysrc = route == 2 ? (const double2*)w.Y : nullptr;
-    if (route == 1) {
-      if (tc) {
+    if (fused) {
+      // every chunk reads the couplings and H that the aux stream produced once
+      if (ci == 0) {
+        CK(cudaEventRecord(w.x_ready[0], ax));
+        CK(cudaStreamWaitEvent(st, w.x_ready[0], 0));
+      }
+    } else {
+      // ---- producer side (aux stream)
+      CK(cudaStreamWaitEvent(ax, w.x_free[ci & 1], 0));
+      if (route == 2) {
+        LAUNCH(SLSHT_STAGE_CTENSOR, ax,
+               launch_ctensor(kcc, (const double2*)h_dev, D, Lh, np, (double2*)w.C, ax));
+        LAUNCH(SLSHT_STAGE_CTENSOR, ax, launch_beta_dft((const double2*)w.C, Lh, Nb, np, (double2*)w.Y, ax));
+      }
+      const double2* Ysrc = route == 2 ? (const double2*)w.Y : nullptr;
+      if (route == 1) {
+        if (tc) {
+          LAUNCH(SLSHT_STAGE_BETA, ax,
+                 launch_xa_from_h(kcc, (const float2*)w.H, Lh, Nb, Ng, np, X, ax));
+        } else if (f64) {
+          LAUNCH(SLSHT_STAGE_BETA, ax,
+                 launch_x_from_h_f64(kcc, (const double2*)w.H, Lh, (int)J, np, (double2*)X, ax));
+        } else {
+          LAUNCH(SLSHT_STAGE_BETA, ax,
+                 launch_x_from_h_f32(kcc, (const float2*)w.H, Lh, (int)J, np, (float2*)X, ax));
+        }
+      } else if (tc) {
         LAUNCH(SLSHT_STAGE_BETA, ax,
-               launch_xa_from_h(kcc, (const float2*)w.H, Lh, Nb, Ng, np, X, ax));
+               launch_betagamma_tc(kcc, (const double2*)h_dev, nullptr, Ysrc, (const float2*)eg, Lh, Nb, Ng, np, X, ax));
       } else if (f64) {
         LAUNCH(SLSHT_STAGE_BETA, ax,
-               launch_x_from_h_f64(kcc, (const double2*)w.H, Lh, (int)J, np, (double2*)X, ax));
+               launch_betagamma_f64(kcc, (const double2*)h_dev, nullptr, Ysrc,
+                                    (const double2*)eg, Lh, Nb, Ng, np, (double2*)X, ax));
       } else {
         LAUNCH(SLSHT_STAGE_BETA, ax,
-               launch_x_from_h_f32(kcc, (const float2*)w.H, Lh, (int)J, np, (float2*)X, ax));
+               launch_betagamma_f32(kcc, (const double2*)h_dev, nullptr, Ysrc,
+                                    (const float2*)eg, Lh, Nb, Ng, np, (float2*)X, ax));
       }
-    } else if (tc) {
-      LAUNCH(SLSHT_STAGE_BETA, ax,
-             launch_betagamma_tc(kcc, (const double2*)h_dev, nullptr, Ysrc, (const float2*)eg, Lh, Nb, Ng, np, X, ax));
-    } else if (f64) {
-      LAUNCH(SLSHT_STAGE_BETA, ax,
-             launch_betagamma_f64(kcc, (const double2*)h_dev, nullptr, Ysrc,
-                                  (const double2*)eg, Lh, Nb, Ng, np, (double2*)X, ax));
-    } else {
-      LAUNCH(SLSHT_STAGE_BETA, ax,
-             launch_betagamma_f32(kcc, (const double2*)h_dev, nullptr, Ysrc,
-                                  (const float2*)eg, Lh, Nb, Ng, np, (float2*)X, ax));
+      CK(cudaEventRecord(w.x_ready[ci & 1], ax));
+      // ---- consumer side (caller's stream)
+      CK(cudaStreamWaitEvent(st, w.x_ready[ci & 1], 0));
     }
-    CK(cudaEventRecord(w.x_ready[ci & 1], ax));
-    // ---- consumer side (caller's stream)
-    CK(cudaStreamWaitEvent(st, w.x_ready[ci & 1], 0));
     void* gdst;
     if (host_out) {
       CK(cudaStreamWaitEvent(st, w.copy_ev[ci & 1], 0));   // staging buffer free again
@@ -670,7 +686,10 @@ static int forward_impl(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
     } else {
       gdst = (char*)g_out + per_pair_g * (size_t)off;
     }
-    if (tc) {
+    if (fused) {
+      LAUNCH(SLSHT_STAGE_ALPHA, st,
+             launch_alpha_fused(kcc, (const float2*)w.H, etab, Lh, Na, Nb, Ng, np, (float2*)gdst, ctx->num_sms, st));
+    } else if (tc) {
       LAUNCH(SLSHT_STAGE_ALPHA, st,
              launch_alpha_tc(X, etab, Lh, Na, Nb, Ng, np, (float2*)gdst, ctx->num_sms, st));
     } else if (f64) {
@@ -680,7 +699,7 @@ static int forward_impl(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
       LAUNCH(SLSHT_STAGE_ALPHA, st,
              launch_alpha_f32((const float2*)X, (const float2*)csa, Lh, Na, (int)J, np, (float2*)gdst, st));
     }
-    CK(cudaEventRecord(w.x_free[ci & 1], st));
+    if (!fused) CK(cudaEventRecord(w.x_free[ci & 1], st));
     if (host_out) {
       CK(cudaEventRecord(w.stage_ev[ci & 1], st));
       CK(cudaStreamWaitEvent(w.copy_stream, w.stage_ev[ci & 1], 0));

@@ -65,8 +65,18 @@ cudaError_t launch_betagamma_f32(const double2* kc, const double2* h, const floa
                                  const double2* Y, const float2* eg, int Lh, int Nb, int Ng,
                                  int npairs, float2* Xs, cudaStream_t st);
 
+// Tiled layout of the rotated window: columns j in tiles of 128, each tile
+// holding all n2 = Lh^2 rows pq = p*p + p + q back to back, so one tile's rows
+// are one contiguous block (128 x n2 elements; columns past J in the last
+// tile are never written).
+__host__ __device__ __forceinline__ size_t h_index(int pq, int j, int n2) {
+  return ((size_t)(j >> 7) * (size_t)n2 + (size_t)pq) * 128 + (size_t)(j & 127);
+}
+// Elements of the tiled H for J columns.
+__host__ __device__ __forceinline__ size_t h_elems(size_t J, int n2) { return (J + 127) / 128 * 128 * (size_t)n2; }
+
 // Rotated window H^p_q(j) = sum_q' h_p^q' d^p_{q,q'}(beta_b) e^{-i q' gamma_c},
-// H[(p*p+p+q) * J + j], j = b*Ng + c; dt in the [b][S] layout.
+// at H[h_index(p*p+p+q, j, Lh*Lh)], j = b*Ng + c; dt in the [b][S] layout.
 cudaError_t launch_rotwin_f64(const double2* h, const double* dt, const double2* eg, int Lh, int Nb, int Ng,
                               double2* H, cudaStream_t st);
 cudaError_t launch_rotwin_f32(const double2* h, const float* dt, const float2* eg, int Lh, int Nb, int Ng,

@@ -235,7 +235,7 @@ cudaError_t launch_betagamma_f32(const double2* kc, const double2* h, const floa
 // H is the window's coefficients rotated by (0, beta_b, gamma_c) (Eq. rotation_non_symm
 // with Eq. Dlm): it does not depend on the pair (l, m), so it is built once per call and
 // every pair costs only Lh^2 multiply-adds per column.
-// H layout: [p*p + p + q][J] (column index fastest).
+// H in the tiled layout of h_index.
 template <typename T>
 __global__ void k_rotwin(const double2* __restrict__ h, const T* __restrict__ dt,
                          const typename vec2<T>::t* __restrict__ eg, int Lh, int Nb, int Ng,
@@ -243,7 +243,6 @@ __global__ void k_rotwin(const double2* __restrict__ h, const T* __restrict__ dt
   typedef typename vec2<T>::t T2;
   const int K = 2 * Lh - 1, S = blk_off(Lh), n2 = Lh * Lh;
   const int b = blockIdx.x;
-  const size_t J = (size_t)Nb * Ng;
   for (int t = blockIdx.y * blockDim.x + threadIdx.x; t < n2 * Ng; t += gridDim.y * blockDim.x) {
     const int pq = t / Ng, c = t % Ng;
     int p = (int)sqrt((double)pq);
@@ -261,7 +260,7 @@ __global__ void k_rotwin(const double2* __restrict__ h, const T* __restrict__ dt
       re = fma(ar, E.x, re); re = fma(ai, E.y, re);
       im = fma(ai, E.x, im); im = fma(-ar, E.y, im);
     }
-    H[(size_t)pq * J + (size_t)b * Ng + c] = mk2(re, im);
+    H[h_index(pq, b * Ng + c, n2)] = mk2(re, im);
   }
 }
 
@@ -308,8 +307,8 @@ __global__ void __launch_bounds__(128) k_x_from_h(const double2* __restrict__ kc
 #pragma unroll
       for (int v = 0; v < 8; ++v) {
         const int p = p0 + v;
-        ha[v] = p < Lh ? H[(size_t)(p * p + p + r) * J + j] : mk2((T)0, (T)0);
-        hb[v] = (p < Lh && r > 0) ? H[(size_t)(p * p + p - r) * J + j] : mk2((T)0, (T)0);
+        ha[v] = p < Lh ? H[h_index(p * p + p + r, j, n2)] : mk2((T)0, (T)0);
+        hb[v] = (p < Lh && r > 0) ? H[h_index(p * p + p - r, j, n2)] : mk2((T)0, (T)0);
       }
 #pragma unroll
       for (int v = 0; v < 8; ++v) {

@@ -21,6 +21,15 @@ cudaError_t launch_xa_from_h(const double2* kc, const float2* H, int Lh, int Nb,
 // alpha stage on tcgen05: g[pair][a][j] complex64.
 cudaError_t launch_alpha_tc(const void* xblob, const void* etab, int Lh, int Na, int Nb, int Ng,
                             int npairs, float2* g, int num_sms, cudaStream_t st);
+// Fused rotated-window producer + alpha stage (one persistent kernel): the A
+// operand of every (pair, 128-column tile) is built in shared memory from H
+// (launch_rotwin_f32, tiled layout of h_index) and the pair's coupling row
+// kc, then multiplied by the E tables on tcgen05; g[pair][a][j] complex64.
+// Lh <= 16.
+cudaError_t launch_alpha_fused(const double2* kc, const float2* H, const void* etab, int Lh, int Na, int Nb,
+                               int Ng, int npairs, float2* g, int num_sms, cudaStream_t st);
+// Device error word shared by the tensor-core kernels (allocated on first use).
+int* tc_error_word();
 // Non-zero (and cleared) if a tensor-core kernel gave up on a bounded wait
 // since the last call.  Synchronous.
 int tc_read_error(void);

@@ -190,9 +190,10 @@ def test_determinism(ctx):
         assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("engine", [1, 2])
+@pytest.mark.parametrize("engine", [1, 2, 3])
 def test_fp32_alpha_engines(ctx, engine):
-    """FP32_BULK with the alpha stage on CUDA cores (1) and on tcgen05 (2)."""
+    """FP32_BULK with the alpha stage on CUDA cores (1), on tcgen05 fed by the
+    separate producer kernel (2) and in the fused producer + tcgen05 kernel (3)."""
     import paper_1207_5558_gb300 as pkg
     Lf, Lh, grid = 20, 16, (300, 9, 31)      # K = 31: the largest single K block; 3 alpha chunks
     f = synth.signal_powerlaw(Lf, 21)
@@ -207,3 +208,29 @@ def test_fp32_alpha_engines(ctx, engine):
     assert rel(g, ref) < TOL32
     st = ctx.stats()
     assert st is not None
+
+
+@pytest.mark.parametrize("engine", [2, 3])
+@pytest.mark.parametrize("Lf,Lh,grid,chunk", [
+    (6, 3, (130, 5, 33), 7),      # 165 columns: a ragged second tile; 2 alpha chunks; 5 launches
+    (8, 7, (257, 3, 45), 0),      # 3 alpha chunks, the last one row long
+    (10, 12, (140, 11, 23), 5),   # the 16-degree producer bucket with L_h = 12
+])
+def test_tensor_core_engines_ragged(ctx, engine, Lf, Lh, grid, chunk):
+    """Both tensor-core engines on tiles and alpha chunks that do not divide
+    the grid, with the pairs split over several launches."""
+    import paper_1207_5558_gb300 as pkg
+    f = synth.signal_powerlaw(Lf, 40 + Lh)
+    h = synth.window_cn(Lh, 50 + Lh, decay=1.0)
+    every = synth.pairs_all(Lf + Lh - 1)
+    pairs = synth.subsample_pairs(every, 23 / len(every), seed=Lh)
+    ref = O.forward_coeff(f, h, Lf, Lh, pairs, grid)
+    ctx.set_option(pkg.SLSHT_OPT_ALPHA_ENGINE, engine)
+    ctx.set_option(pkg.SLSHT_OPT_CHUNK_PAIRS, chunk)
+    try:
+        g = _fw(ctx, Lf, Lh, grid, f, h, pairs, 1)
+    finally:
+        ctx.set_option(pkg.SLSHT_OPT_ALPHA_ENGINE, 0)
+        ctx.set_option(pkg.SLSHT_OPT_CHUNK_PAIRS, 0)
+    assert rel(g, ref) < TOL32
+    assert np.abs(g - ref).max() <= 1e-5 * np.abs(ref).max()
