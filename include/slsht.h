@@ -242,10 +242,18 @@ int slsht_get_stats(slsht_ctx* ctx, slsht_stats* out, int reset);
  *                            FP32_BULK and L_h <= 16 only.  0 (default): 3
  *                            where it applies, else 2, else 1.
  *  SLSHT_OPT_CHUNK_PAIRS  pairs per launch chunk (scratch size).
+ *  SLSHT_OPT_GAUNT_TABLE  the 3j part of the coupling (Sec. III-B: T through
+ *                            Wigner-3j symbols) depends only on (L_f, L_h, the
+ *                            pair list): 0 (default): each workspace keeps
+ *                            the table of the last pair list it saw when it
+ *                            fits in 256 MB, and a call with the same list
+ *                            only gathers k = sum T f; 1: always keep it;
+ *                            2: never (3j chains recomputed in every call).
  * Returns SLSHT_OK or SLSHT_E_ARG. */
 #define SLSHT_OPT_BETA_ROUTE   1
 #define SLSHT_OPT_ALPHA_ENGINE 2
 #define SLSHT_OPT_CHUNK_PAIRS  3
+#define SLSHT_OPT_GAUNT_TABLE  4
 int slsht_set_option(slsht_ctx* ctx, int option, int64_t value);
 
 /* Bytes of device memory the context currently holds. */

@@ -117,6 +117,11 @@ struct Workspace {
   void* C = nullptr; size_t C_cap = 0;
   void* Y = nullptr; size_t Y_cap = 0;
   void* H = nullptr; size_t H_cap = 0;   // rotated window of the call (route 1)
+  // Gaunt coefficient table of the last pair list this workspace saw
+  void* gt = nullptr; size_t gt_cap = 0;
+  bool gt_valid = false;
+  int gt_Lf = 0, gt_Lh = 0;
+  std::vector<int32_t> gt_lm;
   void* stage[2] = {nullptr, nullptr}; size_t stage_cap[2] = {0, 0};
   cudaEvent_t done = nullptr;          // last use of this workspace
   cudaEvent_t stage_ev[2] = {nullptr, nullptr};
@@ -160,7 +165,7 @@ struct slsht_ctx {
   std::map<int, TableEntry> wbeta;                                  // Nb
   std::map<std::tuple<int, int>, TableEntry> etab;                  // Na, Lh (tensor-core E blobs)
   Workspace sync_ws;
-  int opt_beta_route = 0, opt_alpha_engine = 0;
+  int opt_beta_route = 0, opt_alpha_engine = 0, opt_gaunt_table = 0;
   int64_t opt_chunk = 0;
   bool profile = false;
   std::vector<ProfRec> prof;
@@ -278,6 +283,8 @@ static void ws_release(slsht_ctx* c, Workspace& w) {
   ctx_free(c, w.C, w.C_cap);
   ctx_free(c, w.Y, w.Y_cap);
   ctx_free(c, w.H, w.H_cap);
+  ctx_free(c, w.gt, w.gt_cap);
+  w.gt_valid = false;
   for (int i = 0; i < 2; ++i) ctx_free(c, w.stage[i], w.stage_cap[i]);
   for (int i = 0; i < 2; ++i) {
     if (w.stage_ev[i]) cudaEventDestroy(w.stage_ev[i]);
@@ -505,6 +512,10 @@ extern "C" int slsht_set_option(slsht_ctx* c, int option, int64_t v) {
       if (v < 0 || v > (1 << 20)) return SLSHT_E_ARG;
       c->opt_chunk = v;
       return SLSHT_OK;
+    case SLSHT_OPT_GAUNT_TABLE:
+      if (v < 0 || v > 2) return SLSHT_E_ARG;
+      c->opt_gaunt_table = (int)v;
+      return SLSHT_OK;
     default:
       return SLSHT_E_ARG;
   }
@@ -536,8 +547,8 @@ static bool use_tensor_cores(slsht_ctx* ctx, const slsht_desc* d) {
 
 // The forward transform on workspace `w` and stream `st` (ctx->mu NOT held).
 static int forward_impl(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const double* f_lm,
-                        const double* h_lm, const int32_t* lm, int32_t n_pairs, void* g_out,
-                        cudaStream_t st) {
+                        const double* h_lm, const int32_t* lm, const int32_t* lm_host, int32_t n_pairs,
+                        void* g_out, cudaStream_t st) {
   const int Lf = d->L_f, Lh = d->L_h, Na = d->n_alpha, Nb = d->n_beta, Ng = d->n_gamma;
   const int K = 2 * Lh - 1;
   const bool f64 = d->prec == SLSHT_FP64;
@@ -546,7 +557,7 @@ static int forward_impl(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
   const bool host_out = !is_device_ptr(g_out);
   CK(cudaStreamWaitEvent(st, w.done, 0));
 
-  int route, tc, engine;
+  int route, tc, engine, gt_opt;
   int64_t chunk_opt;
   {
     std::lock_guard<std::mutex> g(ctx->mu);
@@ -554,6 +565,7 @@ static int forward_impl(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
     tc = use_tensor_cores(ctx, d) ? 1 : 0;
     engine = ctx->opt_alpha_engine;
     chunk_opt = ctx->opt_chunk;
+    gt_opt = ctx->opt_gaunt_table;
   }
   // rotated-window route on the tensor cores: producer and alpha stage fused
   // into one kernel unless the separate producer kernel was asked for
@@ -617,9 +629,29 @@ static int forward_impl(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
   cudaStream_t ax = w.aux;
   CK(cudaEventRecord(w.start, st));
   CK(cudaStreamWaitEvent(ax, w.start, 0));
-  // the coupling of every pair in one launch (one CTA per pair fills the GPU)
-  LAUNCH(SLSHT_STAGE_COUPLE, ax,
-         launch_couple((const double2*)f_dev, Lf, Lh, (const int2*)lm_dev, n_pairs, (double2*)w.kc, ax));
+  // the coupling of every pair in one launch (one CTA per pair fills the GPU).
+  // With the Gaunt table: the 3j part is kept per workspace for its last
+  // pair list (signal independent) and only the gather-sum runs per call.
+  const size_t gt_bytes = gaunt_table_bytes(Lh, n_pairs);
+  const bool use_gt = gt_opt == 1 || (gt_opt == 0 && gt_bytes <= ((size_t)256 << 20));
+  if (use_gt) {
+    const bool hit = w.gt_valid && w.gt_Lf == Lf && w.gt_Lh == Lh && w.gt_lm.size() == 2 * (size_t)n_pairs &&
+                     std::memcmp(w.gt_lm.data(), lm_host, sizeof(int32_t) * 2 * (size_t)n_pairs) == 0;
+    if (!hit) {
+      w.gt_valid = false;
+      CKS(ws_reserve(ctx, w, &w.gt, &w.gt_cap, gt_bytes));
+      LAUNCH(SLSHT_STAGE_COUPLE, ax, launch_gaunt_table(Lf, Lh, (const int2*)lm_dev, n_pairs, w.gt, ax));
+      w.gt_Lf = Lf;
+      w.gt_Lh = Lh;
+      w.gt_lm.assign(lm_host, lm_host + 2 * (size_t)n_pairs);
+      w.gt_valid = true;
+    }
+    LAUNCH(SLSHT_STAGE_COUPLE, ax,
+           launch_couple_apply((const double2*)f_dev, Lh, (const int2*)lm_dev, n_pairs, w.gt, (double2*)w.kc, ax));
+  } else {
+    LAUNCH(SLSHT_STAGE_COUPLE, ax,
+           launch_couple((const double2*)f_dev, Lf, Lh, (const int2*)lm_dev, n_pairs, (double2*)w.kc, ax));
+  }
   // route 1: the window rotated to every (beta, gamma) sample, once per call
   if (route == 1) {
     if (f64)
@@ -743,7 +775,7 @@ extern "C" int slsht_forward(slsht_ctx* ctx, const slsht_desc* desc, const doubl
   }
   CKS(check_pairs(desc, lmv, n_pairs));
   std::lock_guard<std::mutex> serial(ctx->sync_mu);
-  return forward_impl(ctx, ctx->sync_ws, desc, f_lm, h_lm, lm, n_pairs, g_out, (cudaStream_t)stream);
+  return forward_impl(ctx, ctx->sync_ws, desc, f_lm, h_lm, lm, lmv, n_pairs, g_out, (cudaStream_t)stream);
 }
 
 // ---------------------------------------------------------------- inverse
@@ -862,7 +894,7 @@ static void worker_loop(slsht_ctx* c) {
       }
       if (st == SLSHT_OK) {
         l.unlock();
-        st = forward_impl(c, s.ws, &req->desc, req->f.data(), req->h.data(), req->lm.data(),
+        st = forward_impl(c, s.ws, &req->desc, req->f.data(), req->h.data(), req->lm.data(), req->lm.data(),
                           (int32_t)(req->lm.size() / 2), req->g_out, s.stream);
         if (st == SLSHT_OK && cudaEventRecord(s.fin, s.stream) != cudaSuccess) st = SLSHT_E_CUDA;
         l.lock();

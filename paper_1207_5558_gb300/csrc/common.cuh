@@ -46,6 +46,14 @@ cudaError_t launch_beta_weights(double* w, int Nb, cudaStream_t st);
 cudaError_t launch_couple(const double2* f, int Lf, int Lh, const int2* lm, int npairs,
                           double2* kc, cudaStream_t st);
 
+// The same k through a signal-independent table of Gaunt coefficients:
+// launch_gaunt_table fills `table` (gaunt_table_bytes) for a pair list,
+// launch_couple_apply then forms k for any signal f with that pair list.
+size_t gaunt_table_bytes(int Lh, int npairs);
+cudaError_t launch_gaunt_table(int Lf, int Lh, const int2* lm, int npairs, void* table, cudaStream_t st);
+cudaError_t launch_couple_apply(const double2* f, int Lh, const int2* lm, int npairs, const void* table, double2* kc,
+                                cudaStream_t st);
+
 // C_{q,q',q''}(l, m) (Eq. constant_alternative_formulation), [pair][q][q'][q''].
 cudaError_t launch_ctensor(const double2* kc, const double2* h, const double* D, int Lh,
                            int npairs, double2* C, cudaStream_t st);

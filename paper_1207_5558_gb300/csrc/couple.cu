@@ -184,3 +184,114 @@ cudaError_t launch_couple(const double2* f, int Lf, int Lh, const int2* lm, int 
   else k_couple<128><<<npairs, threads, 0, st>>>(f, Lf, Lh, lm, kc);
   return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------- cached form
+// The coupling splits into a signal-independent table and a gather:
+//   k_lm(p, q) = sum_i c_i(l, m; p, q) f_{l'_i, m-q},   l'_i = l'_0 + 2 i,
+//   c_i = T(l'_i, m-q; p, q; l, m)   (both 3j families, FP64, as in k_couple).
+// k_gaunt_table writes c[pair][i][t] (i < Lh, zero past the item's count;
+// t = p*p + p + q fastest) and meta[pair][t] = (l'_0, count); the table
+// depends only on (L_f, L_h, the pair list), so a caller that repeats a pair
+// list for many signals builds it once, like the Delta and d(beta) tables.
+template <int CMAX>
+__global__ void __launch_bounds__(256) k_gaunt_table(int Lf, int Lh, const int2* __restrict__ lm,
+                                                     double* __restrict__ coef, int2* __restrict__ meta) {
+  __shared__ double w0s[SLSHT_MAX_LH * (SLSHT_MAX_LH + 1) / 2];
+  const int pair = blockIdx.x;
+  const int l = lm[pair].x, m = lm[pair].y;
+  for (int p = threadIdx.x; p < Lh; p += blockDim.x) {
+    double* w = w0s + p * (p + 1) / 2;
+    const int j0 = abs(p - l), cnt = min(p, l) + 1;
+    const double dd = (double)(p - l), SS = (double)(p + l + 1);
+    double v = 1.0, norm = 2.0 * j0 + 1.0;
+    w[0] = 1.0;
+    for (int i = 1; i < cnt; ++i) {
+      const double x = (double)(j0 + 2 * i - 1), y = x + 1.0;
+      v *= -sqrt(((x * x - dd * dd) * (SS * SS - x * x)) / ((y * y - dd * dd) * (SS * SS - y * y)));
+      w[i] = v;
+      norm += (2.0 * (j0 + 2 * i) + 1.0) * v * v;
+    }
+    double s0 = rsqrt(norm);
+    const double want = ((p - l) & 1) ? -1.0 : 1.0;
+    if (v * want < 0.0) s0 = -s0;
+    for (int i = 0; i < cnt; ++i) w[i] *= s0;
+  }
+  __syncthreads();
+  const int n2 = Lh * Lh;
+  double fm[CMAX], bwd[CMAX];
+  for (int t = threadIdx.x; t < n2; t += blockDim.x) {
+    int p = (int)sqrt((double)t);
+    while (p * p > t) --p;
+    while ((p + 1) * (p + 1) <= t) ++p;
+    const int q = t - p * p - p;
+    int j1min_m, first = 0, cnt = 0;
+    const int nm = threej_chain<CMAX>(p, l, q, -m, fm, bwd, &j1min_m);
+    if (nm > 0) {
+      const double* w = w0s + p * (p + 1) / 2;
+      const int j0 = abs(p - l);
+      const int jend = min(p + l, Lf - 1);
+      int i0 = (j1min_m - j0 + 1) / 2;
+      if (i0 < 0) i0 = 0;
+      first = j0 + 2 * i0;
+      const double pre = ((m & 1) ? -1.0 : 1.0) *
+                         sqrt((2.0 * p + 1.0) * (2.0 * l + 1.0) / (4.0 * 3.14159265358979323846));
+      for (int j1 = first; j1 <= jend; j1 += 2, ++cnt)
+        coef[((size_t)pair * Lh + cnt) * n2 + t] = pre * sqrt(2.0 * j1 + 1.0) * w[(j1 - j0) >> 1] * fm[j1 - j1min_m];
+    }
+    for (int i = cnt; i < Lh; ++i) coef[((size_t)pair * Lh + i) * n2 + t] = 0.0;
+    meta[(size_t)pair * n2 + t] = make_int2(first, cnt);
+  }
+}
+
+// k_lm(p, q) from the table: one thread per (pair, t), coefficient rows
+// read coalesced across t, f gathered (L2 resident).
+__global__ void __launch_bounds__(256) k_couple_apply(const double2* __restrict__ f, int Lh, const int2* __restrict__ lm,
+                                                      const double* __restrict__ coef, const int2* __restrict__ meta,
+                                                      int npairs, double2* __restrict__ kc) {
+  const int n2 = Lh * Lh;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)npairs * n2) return;
+  const int pair = (int)(idx / n2), t = (int)(idx % n2);
+  int p = (int)sqrtf((float)t);
+  while (p * p > t) --p;
+  while ((p + 1) * (p + 1) <= t) ++p;
+  const int q = t - p * p - p;
+  const int mu = lm[pair].y - q;
+  const int2 md = meta[idx];
+  double2 acc = make_double2(0.0, 0.0);
+  const double* c = coef + (size_t)pair * Lh * n2 + t;
+  for (int i = 0; i < md.y; ++i) {
+    const int j1 = md.x + 2 * i;
+    const double ci = c[(size_t)i * n2];
+    const double2 fv = __ldg(f + j1 * j1 + j1 + mu);
+    acc.x = fma(ci, fv.x, acc.x);
+    acc.y = fma(ci, fv.y, acc.y);
+  }
+  kc[idx] = acc;
+}
+
+size_t gaunt_table_bytes(int Lh, int npairs) {
+  const size_t n2 = (size_t)Lh * Lh;
+  return (size_t)npairs * (n2 * Lh * sizeof(double) + n2 * sizeof(int2));
+}
+
+cudaError_t launch_gaunt_table(int Lf, int Lh, const int2* lm, int npairs, void* table, cudaStream_t st) {
+  if (npairs <= 0) return cudaSuccess;
+  const int threads = Lh * Lh < 256 ? ((Lh * Lh + 31) / 32) * 32 : 256;
+  double* coef = (double*)table;
+  int2* meta = (int2*)(coef + (size_t)npairs * Lh * Lh * Lh);
+  if (Lh <= 16) k_gaunt_table<32><<<npairs, threads, 0, st>>>(Lf, Lh, lm, coef, meta);
+  else if (Lh <= 32) k_gaunt_table<64><<<npairs, threads, 0, st>>>(Lf, Lh, lm, coef, meta);
+  else k_gaunt_table<128><<<npairs, threads, 0, st>>>(Lf, Lh, lm, coef, meta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_couple_apply(const double2* f, int Lh, const int2* lm, int npairs, const void* table, double2* kc,
+                                cudaStream_t st) {
+  if (npairs <= 0) return cudaSuccess;
+  const double* coef = (const double*)table;
+  const int2* meta = (const int2*)(coef + (size_t)npairs * Lh * Lh * Lh);
+  const long long n = (long long)npairs * Lh * Lh;
+  k_couple_apply<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(f, Lh, lm, coef, meta, npairs, kc);
+  return cudaGetLastError();
+}

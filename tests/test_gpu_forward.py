@@ -234,3 +234,26 @@ def test_tensor_core_engines_ragged(ctx, engine, Lf, Lh, grid, chunk):
         ctx.set_option(pkg.SLSHT_OPT_CHUNK_PAIRS, 0)
     assert rel(g, ref) < TOL32
     assert np.abs(g - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+def test_gaunt_table_reuse_and_invalidation(ctx):
+    """The per-workspace Gaunt table: a repeated pair list with a new signal,
+    then a different pair list, then the first again, each against the path
+    that recomputes the 3j chains in the call, and against the oracle."""
+    import paper_1207_5558_gb300 as pkg
+    Lf, Lh, grid = 24, 6, (47, 24, 11)
+    h = synth.window_cn(Lh, 61)
+    lists = [synth.pairs_bands([3, 17, 28]), synth.pairs_bands([0, 9, 23]), synth.pairs_bands([3, 17, 28])]
+    sigs = [synth.signal_powerlaw(Lf, 62), synth.signal_powerlaw(Lf, 63), synth.signal_powerlaw(Lf, 64)]
+    got = []
+    for f, pairs in zip(sigs, lists):
+        got.append(_fw(ctx, Lf, Lh, grid, f, h, pairs, 0))
+    ctx.set_option(pkg.SLSHT_OPT_GAUNT_TABLE, 2)
+    try:
+        for (f, pairs), g in zip(zip(sigs, lists), got):
+            ref_gpu = _fw(ctx, Lf, Lh, grid, f, h, pairs, 0)
+            assert rel(g, ref_gpu) < 1e-13
+    finally:
+        ctx.set_option(pkg.SLSHT_OPT_GAUNT_TABLE, 0)
+    for (f, pairs), g in zip(zip(sigs, lists), got):
+        assert rel(g, O.forward_coeff(f, h, Lf, Lh, pairs, grid)) < TOL64
