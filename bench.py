@@ -36,7 +36,7 @@ WORKLOAD = "4 maps L_f=256 L_h=16 l in {16,64,128,255} all m, grid 511x256x31 (w
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=2)
@@ -70,6 +70,7 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.window = None
 
     def start(self):
         try:
@@ -83,7 +84,11 @@ class ClockSampler:
 
     def _read(self):
         for ln in self.proc.stdout:
-            self.lines.append(ln.strip())
+            self.lines.append((time.time(), ln.strip()))
+
+    def mark(self, t0, t1):
+        """Keep only the samples taken between host times t0 and t1."""
+        self.window = (t0, t1)
 
     def stop(self):
         if self.proc is None:
@@ -94,7 +99,8 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         mhz, mx, reasons, util = [], None, set(), []
-        for ln in self.lines:
+        lines = [ln for t, ln in self.lines if self.window is None or self.window[0] <= t <= self.window[1]]
+        for ln in lines:
             p = [x.strip() for x in ln.split(",")]
             if len(p) < 10:
                 continue
@@ -104,14 +110,15 @@ class ClockSampler:
                 continue
             mx = smax
             util.append(u)
-            if u > 50:
-                mhz.append(sm)
+            mhz.append(sm)
             names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
             for n, v in zip(names, p[6:10]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
         return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(self.lines), "samples_under_load": len(mhz)}
+                "reasons": sorted(reasons), "samples": len(lines), "samples_under_load": len(mhz),
+                "util_pct_median": statistics.median(util) if util else None,
+                "window": "samples taken while the timed steps ran (host clock)"}
 
 
 # ---------------------------------------------------------------- inputs
@@ -365,19 +372,23 @@ def main():
             dist.barrier()
 
     def timed(prec, gbuf, steps, warmup, sampler=None):
+        if sampler:
+            sampler.start()          # running before the timed region starts
         for _ in range(warmup):
             run_step(prec, gbuf)
         barrier()
         ctx.stats(reset=True)
         ctx.profile(True)
-        if sampler:
-            sampler.start()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.time()
         e0.record(stream)
         for _ in range(steps):
             run_step(prec, gbuf)
         e1.record(stream)
         barrier()
+        t1 = time.time()
+        if sampler:
+            sampler.mark(t0, t1)
         clk = sampler.stop() if sampler else None
         ms = e0.elapsed_time(e1)
         ctx.profile(False)

@@ -264,9 +264,62 @@ __global__ void k_rotwin(const double2* __restrict__ h, const T* __restrict__ dt
   }
 }
 
+// The same H with one CTA per (beta row b, degree p): the (2p+1)^2 products
+// h_p^{q'} d^p_{q,q'}(beta_b) and the gamma phases of the orders |q'| <= p are
+// staged in shared memory once, then each output (q, c) is a (2p+1)-term dot
+// product read from shared memory (a warp shares q: broadcast rows of the
+// products, odd-stride phase rows without bank conflicts).
+template <typename T>
+__global__ void __launch_bounds__(128) k_rotwin_smem(const double2* __restrict__ h, const T* __restrict__ dt,
+                                                     const typename vec2<T>::t* __restrict__ eg, int Lh, int Nb,
+                                                     int Ng, typename vec2<T>::t* __restrict__ H) {
+  typedef typename vec2<T>::t T2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int K = 2 * Lh - 1, S = blk_off(Lh), n2 = Lh * Lh;
+  const int b = blockIdx.x, p = blockIdx.y, w = 2 * p + 1;
+  T2* hd = reinterpret_cast<T2*>(smem_raw);   // [q + p][q' + p]
+  T2* ep = hd + w * w;                        // [c][q' + p]
+  const T* dblk = dt + (size_t)b * S + blk_off(p);
+  for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
+    const int qp = t % w;
+    const double2 hv = __ldg(h + p * p + qp);
+    const T d = __ldg(dblk + t);
+    hd[t] = mk2(d * (T)hv.x, d * (T)hv.y);
+  }
+  for (int t = threadIdx.x; t < Ng * w; t += blockDim.x) {
+    const int c = t / w, qp = t % w;
+    ep[t] = eg[(size_t)c * K + (Lh - 1) - p + qp];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < w * Ng; t += blockDim.x) {
+    const int qi = t / Ng, c = t % Ng;
+    const T2* hr = hd + qi * w;
+    const T2* er = ep + c * w;
+    T re = 0, im = 0;
+    for (int u = 0; u < w; ++u) {                // h d (cos - i sin)
+      const T2 a = hr[u], E = er[u];
+      re = fma(a.x, E.x, re); re = fma(a.y, E.y, re);
+      im = fma(a.y, E.x, im); im = fma(-a.x, E.y, im);
+    }
+    H[h_index(p * p + qi, b * Ng + c, n2)] = mk2(re, im);
+  }
+}
+
 template <typename T>
 static cudaError_t launch_rotwin_t(const double2* h, const T* dt, const typename vec2<T>::t* eg, int Lh,
                                    int Nb, int Ng, typename vec2<T>::t* H, cudaStream_t st) {
+  typedef typename vec2<T>::t T2;
+  const int K = 2 * Lh - 1;
+  const size_t smem = sizeof(T2) * ((size_t)K * K + (size_t)Ng * K);
+  if (smem <= 200 * 1024) {
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(k_rotwin_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    dim3 grid(Nb, Lh);
+    k_rotwin_smem<T><<<grid, 128, smem, st>>>(h, dt, eg, Lh, Nb, Ng, H);
+    return cudaGetLastError();
+  }
   const long long items = (long long)Lh * Lh * Ng;
   dim3 grid(Nb, (unsigned)std::min<long long>((items + 255) / 256, 64));
   k_rotwin<T><<<grid, 256, 0, st>>>(h, dt, eg, Lh, Nb, Ng, H);
