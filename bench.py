@@ -396,6 +396,34 @@ def main():
         ms = reduce_max(ms, dist)
         return ms, st, clk
 
+    def inverse_leg(prec, gbuf, reps):
+        """The inverse (Sec. III-C) of the last map's g, still in gbuf: time
+        per call (events on the stream), read bandwidth against the measured
+        copy peak, and the recovered f against the map's own coefficients."""
+        f, h, p = maps[-1]
+        pd = dev_inputs[-1][2]
+        n = pd.shape[0]
+        fout = torch.empty(n, dtype=torch.complex128, device="cuda")
+        desc = pkg.make_desc(Lf, Lh, grid, prec)
+        pkg.slsht_inverse(ctx.h, desc, gbuf, complex(h[0]), pd, n, fout, stream)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            pkg.slsht_inverse(ctx.h, desc, gbuf, complex(h[0]), pd, n, fout, stream)
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1) / reps
+        nbytes = n * spp * (8 if prec == 1 else 16)
+        fr = fout.cpu().numpy()
+        ftrue = f[p[:, 0] ** 2 + p[:, 0] + p[:, 1]]
+        gbs = nbytes / (ms / 1e3) / 1e9
+        pk_, _ = peaks()
+        return {"pairs": int(n), "ms_per_call": ms, "g_samples_per_s": n * spp / (ms / 1e3),
+                "read_GB_per_s": gbs, "frac_of_measured_copy": gbs / pk_["hbm_gbs"],
+                "rel_l2_recovered_f": float(np.linalg.norm(fr - ftrue) / np.linalg.norm(ftrue)),
+                "bound": "hbm read (g read once, FP64 accumulation)"}
+
     # ---------------- FP32_BULK headline
     g32 = torch.empty((npairs_map,) + grid, dtype=torch.complex64, device="cuda")
     ms32, st32, clk = timed(1, g32, args.steps, args.warmup, ClockSampler(local))
@@ -417,6 +445,7 @@ def main():
             "stage_ms_per_step": {k: v / args.steps for k, v in st32["ms"].items()},
             "step_frac": (alpha_bytes / (ms32 / 1e3) / 1e9) / pk["hbm_gbs"]}
     # relative L2 of the FP32 path against the FP64 path on the last map, sampled pairs
+    inv32 = inverse_leg(1, g32, 5)
     sel = torch.tensor([0, 200, 500, npairs_map - 1], device="cuda")
     a32 = g32[sel].to(torch.complex128).clone()
     del g32
@@ -431,6 +460,7 @@ def main():
         value64 = samples_step * args.fp64_steps * world / (ms64 / 1e3)
         a64 = g64[sel]
         rel32 = float(torch.linalg.vector_norm(a32 - a64) / torch.linalg.vector_norm(a64))
+        inv64 = inverse_leg(0, g64, 2)
         fp64_alpha_ms = st64["ms"]["alpha"]
         fp64_alpha_tflops = (samples_step * args.fp64_steps * (8 * (Lh - 1) + 4)) / (fp64_alpha_ms / 1e3) / 1e12
         fp64 = {"value": value64, "unit": UNIT, "steps": args.fp64_steps,
@@ -438,7 +468,8 @@ def main():
                 "stage_ms_per_step": {k: v / args.fp64_steps for k, v in st64["ms"].items()},
                 "alpha_fp64_tflops": fp64_alpha_tflops,
                 "alpha_fp64_frac_of_nominal_1.25TF": fp64_alpha_tflops / 1.25,
-                "note": "FP64 alpha stage is FP64-pipe bound; stage times overlap (two streams)"}
+                "note": "FP64 alpha stage is FP64-pipe bound; stage times overlap (two streams)",
+                "inverse": inv64}
         del g64, a64
     del a32
     torch.cuda.empty_cache()
@@ -497,6 +528,7 @@ def main():
             "fp64_path": fp64,
             "fp32_over_fp64_speedup": (value / fp64["value"]) if fp64 else None,
             "rel_l2_fp32_vs_fp64_sampled": rel32,
+            "inverse_fp32": inv32,
             "serve": serve,
         }
         print(json.dumps(line), flush=True)

@@ -809,13 +809,16 @@ extern "C" int slsht_inverse(slsht_ctx* ctx, const slsht_desc* desc, const void*
     std::lock_guard<std::mutex> gl(ctx->mu);
     CKS(get_wbeta(ctx, Nb, st, &wb));
   }
-  // slabs of alpha rows: about four CTAs per SM over all pairs
-  const int want = std::max(1, (4 * ctx->num_sms + n_pairs - 1) / n_pairs);
+  // CTAs = column blocks x pairs x slabs of alpha rows: slabs only when the
+  // first two leave the GPU short of about 16 CTAs per SM
+  const int ncb = inverse_col_blocks(Nb, Ng);
+  const long long base = (long long)ncb * n_pairs;
+  const int want = (int)std::max<long long>(1, (16LL * ctx->num_sms + base - 1) / base);
   const int nslab = std::min(Na, want);
-  const size_t pbytes = sizeof(double2) * (size_t)n_pairs * nslab;
-  CKS(ws_reserve(ctx, w, &w.kc, &w.kc_cap, pbytes + sizeof(double2) * (size_t)n_pairs));
+  const size_t nparts = (size_t)n_pairs * nslab * ncb;
+  CKS(ws_reserve(ctx, w, &w.kc, &w.kc_cap, sizeof(double2) * (nparts + (size_t)n_pairs)));
   double2* partial = (double2*)w.kc;
-  double2* fdev = is_device_ptr(f_out) ? (double2*)f_out : partial + (size_t)n_pairs * nslab;
+  double2* fdev = is_device_ptr(f_out) ? (double2*)f_out : partial + nparts;
   if (desc->prec == SLSHT_FP64) {
     LAUNCH(SLSHT_STAGE_INVERSE, st,
            launch_inverse_f64((const double2*)g_in, wb, Na, Nb, Ng, n_pairs, partial, nslab, st));
@@ -828,7 +831,7 @@ extern "C" int slsht_inverse(slsht_ctx* ctx, const slsht_desc* desc, const void*
   const double q = (2.0 * pi / Na) * (2.0 * pi / Ng) / std::sqrt(16.0 * pi * pi * pi);
   const double den = h00[0] * h00[0] + h00[1] * h00[1];
   const double sre = q * h00[0] / den, sim = -q * h00[1] / den;
-  LAUNCH(SLSHT_STAGE_INVERSE, st, launch_inverse_final(partial, nslab, n_pairs, sre, sim, fdev, st));
+  LAUNCH(SLSHT_STAGE_INVERSE, st, launch_inverse_final(partial, nslab * ncb, n_pairs, sre, sim, fdev, st));
   if ((void*)fdev != (void*)f_out) {
     StageTimer t(ctx, SLSHT_STAGE_COPY, st);
     CK(cudaMemcpyAsync(f_out, fdev, sizeof(double2) * (size_t)n_pairs, cudaMemcpyDeviceToHost, st));

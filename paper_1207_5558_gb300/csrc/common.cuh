@@ -102,7 +102,9 @@ cudaError_t launch_alpha_f64(const double2* Xs, const double2* csa, int Lh, int 
 cudaError_t launch_alpha_f32(const float2* Xs, const float2* csa, int Lh, int Na, int J,
                              int npairs, float2* g, cudaStream_t st);
 
-// Inverse: partial sums then final scaling (deterministic order).
+// Inverse: partial sums then final scaling (deterministic order).  The
+// partial sums of one pair are nslab * inverse_col_blocks(Nb, Ng) entries.
+int inverse_col_blocks(int Nb, int Ng);
 cudaError_t launch_inverse_f64(const double2* g, const double* wb, int Na, int Nb, int Ng,
                                int npairs, double2* partial, int nslab, cudaStream_t st);
 cudaError_t launch_inverse_f32(const float2* g, const double* wb, int Na, int Nb, int Ng,

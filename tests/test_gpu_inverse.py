@@ -47,10 +47,11 @@ def test_inverse_matches_oracle_inverse(ctx):
     gd = torch.from_numpy(g).cuda()
     fr = ctx.inverse(Lf, Lh, grid, gd, h[0], pairs, prec=0)
     assert np.max(np.abs(fr - ref)) / np.max(np.abs(ref)) < 1e-13
+    # complex64 g: FP32 block sums feeding FP64 totals, held to the FP32_BULK bound
     g32 = torch.from_numpy(g.astype(np.complex64)).cuda()
     ref32 = O.inverse(g.astype(np.complex64).astype(np.complex128), h[0], grid)
     fr32 = ctx.inverse(Lf, Lh, grid, g32, h[0], pairs, prec=1)
-    assert np.max(np.abs(fr32 - ref32)) / np.max(np.abs(ref32)) < 1e-13
+    assert np.max(np.abs(fr32 - ref32)) / np.max(np.abs(ref32)) < 1e-5
 
 
 def test_inverse_is_bitwise_reproducible(ctx):
@@ -79,3 +80,18 @@ def test_inverse_argument_errors(ctx):
         pkg.slsht_inverse(ctx.h, pkg.make_desc(4, 2, (4, 4, 4)), g.cpu().numpy(), 1.0,
                           np.array([[1, 0]], np.int32), 1, out)
     assert e.value.code == -1
+
+
+def test_inverse_fp32_long_rows(ctx):
+    """complex64 inverse over rows longer than four thread strides (the
+    unrolled loop and its tail) and several alpha rows per slab, against the
+    oracle's inverse of the same complex64 values."""
+    import torch
+    Lf, Lh, grid = 6, 3, (37, 41, 29)       # 1189 columns: 4 strides of 256 plus a tail
+    h = synth.window_cn(Lh, 21)
+    pairs = synth.pairs_all(4)
+    rng = np.random.default_rng(9)
+    g = (rng.standard_normal((len(pairs),) + grid) + 1j * rng.standard_normal((len(pairs),) + grid)).astype(np.complex64)
+    ref = O.inverse(g.astype(np.complex128), h[0], grid)
+    fr = ctx.inverse(Lf, Lh, grid, torch.from_numpy(g).cuda(), h[0], pairs, prec=1)
+    assert np.max(np.abs(fr - ref)) / np.max(np.abs(ref)) < 1e-5
