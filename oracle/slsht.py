@@ -56,8 +56,10 @@ class ModulatedSHT:
     the triple product), so F is summed over l' in [l-Lh+1, l+Lh-1]: the
     exact value is unchanged and the cancellation of the rest of f's energy is
     avoided.  Rounding of the oscillatory integrand still limits this route to
-    about 1e-11 relative at l ~ 255 (pinned in the tests); GauntCoefficients is
-    the exact route used by default.
+    about 1e-11 relative at l ~ 255 (pinned in the tests); at l ~ 2000 with a
+    64-degree window band the degrees of F that T removes cancel badly (errors
+    near 1e-2 were seen), so workload 5 uses GauntRecurrence.
+    GauntCoefficients is the exact route used by default.
     """
 
     def __init__(self, f, Lf, Lh, lmax_out):
@@ -100,6 +102,37 @@ class GauntCoefficients:
 
     def coeffs(self, l, m):
         return modulated_coeffs_gaunt(self.f, self.Lf, self.Lh, l, m)
+
+
+class GauntRecurrence:
+    """The same k_{lm}(p, q) as GauntCoefficients, with the 3j symbols of T
+    from their order families (special.wigner3j_m_family: the J^2
+    eigen-equation in the coupled basis, run in 60-digit decimal arithmetic)
+    instead of Racah's rational sum, which costs milliseconds a symbol at the
+    degrees of workload 5 (l ~ 2000).  Pinned against GauntCoefficients at
+    small and at large degree."""
+
+    def __init__(self, f, Lf, Lh, lmax_out=None):
+        self.f = np.asarray(f, dtype=np.complex128)
+        self.Lf, self.Lh = Lf, Lh
+
+    def coeffs(self, l, m):
+        Lf, Lh, f = self.Lf, self.Lh, self.f
+        k = np.zeros((Lh, 2 * Lh - 1), dtype=np.complex128)
+        for p in range(Lh):
+            for lp in range(abs(l - p), min(Lf - 1, l + p) + 1):
+                if (lp + p + l) % 2:
+                    continue                          # (l' p l; 0 0 0) = 0
+                lo0, fam0 = special.wigner3j_m_family(lp, p, l, 0)
+                w0 = fam0[-lo0]                       # the order mu = 0
+                if w0 == 0.0:
+                    continue
+                lo, fam = special.wigner3j_m_family(lp, p, l, m)
+                t0 = sqrt((2 * lp + 1) * (2 * p + 1) * (2 * l + 1) / (4.0 * pi)) * w0
+                for i, w1 in enumerate(fam):
+                    mu = lo + i                       # order of l'; q = m - mu
+                    k[p, m - mu + Lh - 1] += f[lp * lp + lp + mu] * (t0 * w1)
+        return (-1) ** (m % 2) * k
 
 
 def modulated_coeffs_gaunt(f, Lf, Lh, l, m):
@@ -145,8 +178,9 @@ def forward_coeff(f, h, Lf, Lh, pairs, grid, beta_rows=None, msht=None, dtab=Non
       g = sum_p sum_q sum_q' k_{lm}(p,q) h_p^{q'} d^p_{q,q'}(beta) e^{-i q' gamma} e^{-i q alpha}
     (Eq. alternative_harmonic_formulation and ..._wigner, with
     D^p_{q,q'} from Eq. Dlm), k from exact 3j symbols (GauntCoefficients,
-    kroute="exact") or from the Appendix A quadrature (ModulatedSHT,
-    kroute="quadrature"), d^p from the degree recurrence
+    kroute="exact"), from order-recursion 3j families (GauntRecurrence,
+    kroute="recurrence", for large degrees) or from the Appendix A quadrature
+    (ModulatedSHT, kroute="quadrature"), d^p from the degree recurrence
     (special.wigner_d_table).  The triple sum is done as three library
     contractions (p, then q', then q); nothing else is reordered.
 
@@ -167,7 +201,8 @@ def forward_coeff(f, h, Lf, Lh, pairs, grid, beta_rows=None, msht=None, dtab=Non
     ht = h_table(h, Lh)
     if msht is None:
         lmax = max(l for l, _ in pairs)
-        msht = (GauntCoefficients if kroute == "exact" else ModulatedSHT)(f, Lf, Lh, lmax)
+        msht = {"exact": GauntCoefficients, "quadrature": ModulatedSHT,
+                "recurrence": GauntRecurrence}[kroute](f, Lf, Lh, lmax)
     K = 2 * Lh - 1
     nb = b.size
     out = np.zeros((len(pairs), Na, nb, Ng), dtype=np.complex128)

@@ -9,24 +9,25 @@
 // coalesced: for a fixed row a, a warp writes 32 consecutive columns.
 #include "common.cuh"
 
-#define ALPHA_THREADS 128
 #define ABLK 4
 
-template <typename T>
-__global__ void __launch_bounds__(ALPHA_THREADS)
+// NT columns per CTA: 128, or 64 when the 2Lh-1 staged coefficients of 128
+// columns would not fit in shared memory (FP64 at Lh = 64).
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT)
 k_alpha_cc(const typename vec2<T>::t* __restrict__ Xs, const typename vec2<T>::t* __restrict__ csa,
            int Lh, int Na, int J, typename vec2<T>::t* __restrict__ g) {
   typedef typename vec2<T>::t T2;
   extern __shared__ unsigned char smem_raw[];
-  T2* sx = reinterpret_cast<T2*>(smem_raw);      // [2Lh-1][ALPHA_THREADS]
+  T2* sx = reinterpret_cast<T2*>(smem_raw);      // [2Lh-1][NT]
   const int K = 2 * Lh - 1;
   const int pair = blockIdx.y;
-  const int j0 = blockIdx.x * ALPHA_THREADS;
+  const int j0 = blockIdx.x * NT;
   const int t = threadIdx.x;
   const int j = j0 + t;
   const T2* src = Xs + (size_t)pair * K * J;
   for (int c = 0; c < K; ++c)
-    sx[c * ALPHA_THREADS + t] = (j < J) ? src[(size_t)c * J + j] : mk2((T)0, (T)0);
+    sx[c * NT + t] = (j < J) ? src[(size_t)c * J + j] : mk2((T)0, (T)0);
   __syncthreads();
   if (j >= J) return;
   T2* dst = g + (size_t)pair * Na * J + j;
@@ -36,8 +37,8 @@ k_alpha_cc(const typename vec2<T>::t* __restrict__ Xs, const typename vec2<T>::t
 #pragma unroll
     for (int u = 0; u < ABLK; ++u) { re[u] = x0.x; im[u] = x0.y; }
     for (int r = 1; r < Lh; ++r) {
-      const T2 P = sx[(2 * r - 1) * ALPHA_THREADS + t];
-      const T2 M = sx[(2 * r) * ALPHA_THREADS + t];
+      const T2 P = sx[(2 * r - 1) * NT + t];
+      const T2 M = sx[(2 * r) * NT + t];
 #pragma unroll
       for (int u = 0; u < ABLK; ++u) {
         const int a = min(a0 + u, Na - 1);
@@ -60,14 +61,23 @@ static cudaError_t launch_alpha_t(const typename vec2<T>::t* Xs, const typename 
                                   cudaStream_t st) {
   if (npairs <= 0 || J <= 0) return cudaSuccess;
   typedef typename vec2<T>::t T2;
-  const size_t smem = sizeof(T2) * (size_t)(2 * Lh - 1) * ALPHA_THREADS;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_alpha_cc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
+  const size_t smem128 = sizeof(T2) * (size_t)(2 * Lh - 1) * 128;
+  if (smem128 <= 200 * 1024) {
+    if (smem128 > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(k_alpha_cc<T, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem128);
+      if (e != cudaSuccess) return e;
+    }
+    dim3 grid((J + 127) / 128, npairs);
+    k_alpha_cc<T, 128><<<grid, 128, smem128, st>>>(Xs, csa, Lh, Na, J, g);
+    return cudaGetLastError();
   }
-  dim3 grid((J + ALPHA_THREADS - 1) / ALPHA_THREADS, npairs);
-  k_alpha_cc<T><<<grid, ALPHA_THREADS, smem, st>>>(Xs, csa, Lh, Na, J, g);
+  const size_t smem64 = smem128 / 2;
+  if (smem64 > 200 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_alpha_cc<T, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64);
+  if (e != cudaSuccess) return e;
+  dim3 grid((J + 63) / 64, npairs);
+  k_alpha_cc<T, 64><<<grid, 64, smem64, st>>>(Xs, csa, Lh, Na, J, g);
   return cudaGetLastError();
 }
 

@@ -257,3 +257,22 @@ def test_gaunt_table_reuse_and_invalidation(ctx):
         ctx.set_option(pkg.SLSHT_OPT_GAUNT_TABLE, 0)
     for (f, pairs), g in zip(zip(sigs, lists), got):
         assert rel(g, O.forward_coeff(f, h, Lf, Lh, pairs, grid)) < TOL64
+
+
+def test_gaunt_table_mirror_pairs_with_duplicates(ctx):
+    """Mirror pairs (l, m), (l, -m) share one chain in the Gaunt table; lists
+    with repeated pairs, unmatched mirrors and m = 0 against the per-call
+    chains and the oracle."""
+    import paper_1207_5558_gb300 as pkg
+    Lf, Lh, grid = 20, 7, (39, 20, 13)
+    f = synth.signal_powerlaw(Lf, 71)
+    h = synth.window_cn(Lh, 72)
+    pairs = np.array([[5, 2], [5, 2], [5, -2], [7, 3], [7, 0], [9, -4], [24, 1], [24, -1], [3, -3]], dtype=np.int32)
+    g = _fw(ctx, Lf, Lh, grid, f, h, pairs, 0)
+    ctx.set_option(pkg.SLSHT_OPT_GAUNT_TABLE, 2)
+    try:
+        g2 = _fw(ctx, Lf, Lh, grid, f, h, pairs, 0)
+    finally:
+        ctx.set_option(pkg.SLSHT_OPT_GAUNT_TABLE, 0)
+    assert rel(g, g2) < 1e-13
+    assert rel(g, O.forward_coeff(f, h, Lf, Lh, pairs, grid)) < TOL64

@@ -231,3 +231,24 @@ def test_gaunt_quadrature_vs_3j():
             continue
         n += 1
         assert abs(S.gaunt_exact(lp, mp, p, q, l, m) - S.gaunt_quadrature(lp, mp, p, q, l, m)) < 1e-14
+
+
+def test_wigner3j_order_family_matches_racah():
+    """The order-recursion families agree with Racah's exact sum, at small
+    degrees for every order and at l ~ 2000 (workload 5) at both ends and in
+    the middle of a 127-term family."""
+    import random
+    rng = random.Random(7)
+    for _ in range(150):
+        j1, j2 = rng.randint(0, 22), rng.randint(0, 22)
+        j3 = rng.randint(abs(j1 - j2), j1 + j2)
+        M = rng.randint(-j3, j3)
+        lo, fam = S.wigner3j_m_family(j1, j2, j3, M)
+        for i, v in enumerate(fam):
+            mu = lo + i
+            assert abs(v - S.wigner3j_exact(j1, j2, j3, mu, M - mu, -M)) <= 1e-15 * max(1.0, abs(v))
+    lo, fam = S.wigner3j_m_family(1999, 63, 2022, 1202)
+    assert len(fam) == 127
+    for mu in (lo, lo + 1, lo + 63, lo + 126):
+        e = S.wigner3j_exact(1999, 63, 2022, mu, 1202 - mu, -1202)
+        assert abs(fam[mu - lo] - e) <= 1e-14 * abs(e)

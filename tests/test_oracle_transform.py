@@ -270,3 +270,34 @@ def test_inversion_constant_printed():
 def test_inverse_rejects_zero_dc():
     with pytest.raises(ValueError):
         O.inverse(np.zeros((1, 2, 2, 2)), 0.0, (2, 2, 2))
+
+
+def test_modulated_sht_accuracy_at_large_band_limit():
+    """The quadrature route of Appendix A at l ~ 1800 with a short window
+    band, against exact 3j symbols (Racah, rationals), where every T needs
+    only a few exact symbols.  (With a 64-degree band at l ~ 2000 the route
+    loses accuracy to cancellation; workload 5 uses GauntRecurrence.)"""
+    Lf, Lh = 1900, 3
+    f = synth.signal_powerlaw(Lf, 3002)
+    ms = O.ModulatedSHT(f, Lf, Lh, 1899)
+    for l, m in [(1800, 1200), (1899, -1899), (1850, 7)]:
+        ke = O.modulated_coeffs_gaunt(f, Lf, Lh, l, m)
+        kq = ms.coeffs(l, m)
+        assert np.linalg.norm(kq - ke) / np.linalg.norm(ke) < 1e-9, (l, m)
+
+
+def test_gaunt_recurrence_route_matches_exact():
+    """k from the order-recursion 3j families equals k from Racah's exact
+    3j symbols: every pair of a small case, and large-degree pairs."""
+    Lf, Lh = 20, 6
+    f = synth.signal_powerlaw(Lf, 3003)
+    gr = O.GauntRecurrence(f, Lf, Lh)
+    for l, m in [(0, 0), (3, -2), (12, 12), (19, 5), (24, -20)]:
+        ke = O.modulated_coeffs_gaunt(f, Lf, Lh, l, m)
+        assert np.abs(gr.coeffs(l, m) - ke).max() <= 1e-14 * max(np.abs(ke).max(), 1e-300)
+    Lf, Lh = 1900, 3
+    f = synth.signal_powerlaw(Lf, 3002)
+    gr = O.GauntRecurrence(f, Lf, Lh)
+    for l, m in [(1800, 1200), (1850, 7)]:
+        ke = O.modulated_coeffs_gaunt(f, Lf, Lh, l, m)
+        assert np.linalg.norm(gr.coeffs(l, m) - ke) / np.linalg.norm(ke) < 1e-13
