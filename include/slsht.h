@@ -249,11 +249,19 @@ int slsht_get_stats(slsht_ctx* ctx, slsht_stats* out, int reset);
  *                            fits in 256 MB, and a call with the same list
  *                            only gathers k = sum T f; 1: always keep it;
  *                            2: never (3j chains recomputed in every call).
+ *  SLSHT_OPT_WAIT_TEST    1: the next forward call that runs the fused
+ *                            tensor-core kernel withholds one internal
+ *                            hand-off, so the kernel's bounded waits expire
+ *                            (short limit), it exits cleanly and the next
+ *                            slsht_get_stats returns SLSHT_E_TIMEOUT; that
+ *                            call's g is not computed.  Resets itself.  For
+ *                            testing the timeout path; the context stays usable.
  * Returns SLSHT_OK or SLSHT_E_ARG. */
 #define SLSHT_OPT_BETA_ROUTE   1
 #define SLSHT_OPT_ALPHA_ENGINE 2
 #define SLSHT_OPT_CHUNK_PAIRS  3
 #define SLSHT_OPT_GAUNT_TABLE  4
+#define SLSHT_OPT_WAIT_TEST    5
 int slsht_set_option(slsht_ctx* ctx, int option, int64_t value);
 
 /* Bytes of device memory the context currently holds. */

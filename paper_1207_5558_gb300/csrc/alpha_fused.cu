@@ -96,14 +96,14 @@ __host__ __device__ constexpr int isqrt_c(int n) {
 template <int LHB, bool NEG>
 __device__ __forceinline__ void accumulate_half(float* ar, float* ai, const float2* sH, const float2* sk, int col,
                                                 FuShared* S, int& h_slot, uint32_t& h_phase,
-                                                volatile int* abort_flag) {
+                                                volatile int* abort_flag, uint32_t wlim) {
   constexpr int NST = LHB * LHB / FU_HR;
 #pragma unroll
   for (int st = 0; st < NST; ++st) {
     const int slot = h_slot;
     // on expiry: raise the abort flag and go on with stale rows (in bounds);
     // the item is dropped at the next hand-off
-    if (!mbar_wait(smem_u32(&S->h_full[slot]), h_phase, abort_flag)) *abort_flag = 1;
+    if (!mbar_wait_n(smem_u32(&S->h_full[slot]), h_phase, abort_flag, wlim)) *abort_flag = 1;
     if (++h_slot == FU_HS) { h_slot = 0; h_phase ^= 1u; }
     const float2* hst = sH + (size_t)slot * FU_HR * TC_M + col;
 #pragma unroll
@@ -127,7 +127,7 @@ template <int LHB>
 __global__ void __launch_bounds__(FU_THREADS, 1)
 k_alpha_fused(const double2* __restrict__ kc, const float2* __restrict__ H, int Lh, int J, int tiles,
               const unsigned char* __restrict__ etab, int Na, int npairs, float2* __restrict__ g,
-              int* __restrict__ err) {
+              int* __restrict__ err, uint32_t wlim, int wait_test) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = sm;                               // 2 x 32 KB
@@ -178,7 +178,7 @@ k_alpha_fused(const double2* __restrict__ kc, const float2* __restrict__ H, int 
       for (long long it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
         for (int c = 0; c < nch; ++c, ++bc) {
           const uint32_t pb = (uint32_t)(bc & 1);
-          if (!(ok = mbar_wait(smem_u32(&S->b_empty), pb ^ 1u, abort_flag))) break;
+          if (!(ok = mbar_wait_n(smem_u32(&S->b_empty), pb ^ 1u, abort_flag, wlim))) break;
           const uint32_t fb = smem_u32(&S->b_full);
           mbar_expect_tx(fb, TC_B_BYTES);
           const unsigned char* bsrc = etab + (size_t)c * TC_B_BYTES;
@@ -201,13 +201,13 @@ k_alpha_fused(const double2* __restrict__ kc, const float2* __restrict__ H, int 
       bool ok = true;
       for (long long it = blockIdx.x; it < nitems && ok; it += gridDim.x, ++li) {
         const int sa = li & 1;
-        if (!(ok = mbar_wait(smem_u32(&S->a_full[sa]), (uint32_t)((li >> 1) & 1), abort_flag))) break;
+        if (!(ok = mbar_wait_n(smem_u32(&S->a_full[sa]), (uint32_t)((li >> 1) & 1), abort_flag, wlim))) break;
         tc_fence_after();
         const uint32_t a_hi = smem_u32(sA + sa * TC_A_BYTES), a_lo = a_hi + TC_A_HALF;
         for (int c = 0; c < nch; ++c, ++bc, ++ac) {
           const int acc = (int)(ac & 1);
-          if (!(ok = mbar_wait(smem_u32(&S->b_full), (uint32_t)(bc & 1), abort_flag))) break;
-          if (!(ok = mbar_wait(smem_u32(&S->acc_empty[acc]), (uint32_t)(((ac >> 1) & 1) ^ 1), abort_flag))) break;
+          if (!(ok = mbar_wait_n(smem_u32(&S->b_full), (uint32_t)(bc & 1), abort_flag, wlim))) break;
+          if (!(ok = mbar_wait_n(smem_u32(&S->acc_empty[acc]), (uint32_t)(((ac >> 1) & 1) ^ 1), abort_flag, wlim))) break;
           tc_fence_after();
           const uint32_t b_hi = smem_u32(sB), b_lo = b_hi + TC_B_HALF;
           const uint32_t d = tmem + (uint32_t)(acc * TC_N);
@@ -257,7 +257,7 @@ k_alpha_fused(const double2* __restrict__ kc, const float2* __restrict__ H, int 
         sk[t] = v;
       }
       if (x == 0)
-        S->x_ok[sa] = mbar_wait(smem_u32(&S->a_empty[sa]), (uint32_t)(((li >> 1) & 1) ^ 1), abort_flag) ? 1 : 0;
+        S->x_ok[sa] = mbar_wait_n(smem_u32(&S->a_empty[sa]), (uint32_t)(((li >> 1) & 1) ^ 1), abort_flag, wlim) ? 1 : 0;
       named_bar_sync(FU_XBAR, 32 * FU_XWARPS);
       if (!S->x_ok[sa]) break;          // uniform across the producer warps
 
@@ -268,9 +268,9 @@ k_alpha_fused(const double2* __restrict__ kc, const float2* __restrict__ H, int 
 #pragma unroll
       for (int i = 0; i < LHB; ++i) ar[i] = ai[i] = 0.f;
       if (neg)
-        accumulate_half<LHB, true>(ar, ai, sH, sk, col, S, h_slot, h_phase, abort_flag);
+        accumulate_half<LHB, true>(ar, ai, sH, sk, col, S, h_slot, h_phase, abort_flag, wlim);
       else
-        accumulate_half<LHB, false>(ar, ai, sH, sk, col, S, h_slot, h_phase, abort_flag);
+        accumulate_half<LHB, false>(ar, ai, sH, sk, col, S, h_slot, h_phase, abort_flag, wlim);
       if (!jin) {            // padding columns of the last tile: exact zeros
 #pragma unroll
         for (int i = 0; i < LHB; ++i) ar[i] = ai[i] = 0.f;
@@ -320,7 +320,9 @@ k_alpha_fused(const double2* __restrict__ kc, const float2* __restrict__ H, int 
       }
       // generic-proxy stores -> visible to the tensor core's async proxy
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive(smem_u32(&S->a_full[sa]));
+      // wait_test: the first item's A tile is never handed over, so the
+      // issuer's and the epilogue's bounded waits run out (timeout path test)
+      if (!(wait_test && li == 0)) mbar_arrive(smem_u32(&S->a_full[sa]));
     }
   } else if (warp == FU_HL) {
     // ---------------- H-ring loader: the item's n2 rows, FU_HR rows a stage
@@ -334,7 +336,7 @@ k_alpha_fused(const double2* __restrict__ kc, const float2* __restrict__ H, int 
       for (long long it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
         const int tile = (int)(it % tiles);
         for (int s = 0; s < NST; ++s) {
-          if (!(ok = mbar_wait(smem_u32(&S->h_empty[slot]), use ^ 1u, abort_flag))) break;
+          if (!(ok = mbar_wait_n(smem_u32(&S->h_empty[slot]), use ^ 1u, abort_flag, wlim))) break;
           const uint32_t fb = smem_u32(&S->h_full[slot]);
           mbar_expect_tx(fb, (uint32_t)(FU_HR * TC_M * 8));
           const float2* tsrc = H + (size_t)tile * n2 * TC_M;        // the tile's rows, contiguous
@@ -379,7 +381,7 @@ k_alpha_fused(const double2* __restrict__ kc, const float2* __restrict__ H, int 
       const bool jin = j < J;
       // the item's scales: every lane waits for the A stage itself, then
       // releases it (its MMAs release it too)
-      const int w_ok = mbar_wait(smem_u32(&S->a_full[sa]), (uint32_t)((li >> 1) & 1), abort_flag) ? 1 : 0;
+      const int w_ok = mbar_wait_n(smem_u32(&S->a_full[sa]), (uint32_t)((li >> 1) & 1), abort_flag, wlim) ? 1 : 0;
       if (!(ok = __all_sync(0xffffffffu, w_ok) != 0)) break;
       const float sc = S->scale[sa][row];
       mbar_arrive(smem_u32(&S->a_empty[sa]));
@@ -388,7 +390,7 @@ k_alpha_fused(const double2* __restrict__ kc, const float2* __restrict__ H, int 
         const int acc = (int)(ac & 1);
         // one lane waits, the warp follows: tcgen05.ld needs a converged warp
         int got = 0;
-        if (lane == 0) got = mbar_wait(smem_u32(&S->acc_full[acc]), (uint32_t)((ac >> 1) & 1), abort_flag);
+        if (lane == 0) got = mbar_wait_n(smem_u32(&S->acc_full[acc]), (uint32_t)((ac >> 1) & 1), abort_flag, wlim);
         got = __shfl_sync(0xffffffffu, got, 0);
         __syncwarp();
         if (!(ok = got != 0)) break;
@@ -434,20 +436,23 @@ k_alpha_fused(const double2* __restrict__ kc, const float2* __restrict__ H, int 
 
 template <int LHB>
 static cudaError_t launch_fused_t(const double2* kc, const float2* H, const void* etab, int Lh, int Na, int J,
-                                  int tiles, int npairs, float2* g, int* err, int grid, cudaStream_t st) {
+                                  int tiles, int npairs, float2* g, int* err, int grid, int wait_test,
+                                  cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_alpha_fused<LHB>, cudaFuncAttributeMaxDynamicSharedMemorySize, FU_SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
+  // the wait test uses a short limit so the expiry comes quickly
+  const uint32_t wlim = wait_test ? (1u << 14) : TC_WAIT_LIMIT;
   k_alpha_fused<LHB><<<grid, FU_THREADS, FU_SMEM, st>>>(kc, H, Lh, J, tiles, (const unsigned char*)etab, Na,
-                                                        npairs, g, err);
+                                                        npairs, g, err, wlim, wait_test);
   return cudaGetLastError();
 }
 
 cudaError_t launch_alpha_fused(const double2* kc, const float2* H, const void* etab, int Lh, int Na, int Nb,
-                               int Ng, int npairs, float2* g, int num_sms, cudaStream_t st) {
+                               int Ng, int npairs, float2* g, int num_sms, int wait_test, cudaStream_t st) {
   if (npairs <= 0) return cudaSuccess;
   if (!tc_supported(Lh, Na) || Lh > 16) return cudaErrorInvalidValue;
   // bulk copies of whole 1 KB rows of the tiled H need a 16-byte aligned base
@@ -458,7 +463,7 @@ cudaError_t launch_alpha_fused(const double2* kc, const float2* H, const void* e
   const int tiles = (J + TC_M - 1) / TC_M;
   const long long items = (long long)npairs * tiles;
   const int grid = (int)(items < num_sms ? items : num_sms);
-  if (Lh <= 4) return launch_fused_t<4>(kc, H, etab, Lh, Na, J, tiles, npairs, g, err, grid, st);
-  if (Lh <= 8) return launch_fused_t<8>(kc, H, etab, Lh, Na, J, tiles, npairs, g, err, grid, st);
-  return launch_fused_t<16>(kc, H, etab, Lh, Na, J, tiles, npairs, g, err, grid, st);
+  if (Lh <= 4) return launch_fused_t<4>(kc, H, etab, Lh, Na, J, tiles, npairs, g, err, grid, wait_test, st);
+  if (Lh <= 8) return launch_fused_t<8>(kc, H, etab, Lh, Na, J, tiles, npairs, g, err, grid, wait_test, st);
+  return launch_fused_t<16>(kc, H, etab, Lh, Na, J, tiles, npairs, g, err, grid, wait_test, st);
 }

@@ -119,6 +119,8 @@ struct Workspace {
   void* H = nullptr; size_t H_cap = 0;   // rotated window of the call (route 1)
   // Gaunt coefficient table of the last pair list this workspace saw
   void* gt = nullptr; size_t gt_cap = 0;
+  void* gtw = nullptr; size_t gtw_cap = 0;   // its work items (pair, mirror pair)
+  std::vector<int32_t> gt_work;              // host copy (source of the upload)
   bool gt_valid = false;
   int gt_Lf = 0, gt_Lh = 0;
   std::vector<int32_t> gt_lm;
@@ -165,7 +167,7 @@ struct slsht_ctx {
   std::map<int, TableEntry> wbeta;                                  // Nb
   std::map<std::tuple<int, int>, TableEntry> etab;                  // Na, Lh (tensor-core E blobs)
   Workspace sync_ws;
-  int opt_beta_route = 0, opt_alpha_engine = 0, opt_gaunt_table = 0;
+  int opt_beta_route = 0, opt_alpha_engine = 0, opt_gaunt_table = 0, opt_wait_test = 0;
   int64_t opt_chunk = 0;
   bool profile = false;
   std::vector<ProfRec> prof;
@@ -284,6 +286,7 @@ static void ws_release(slsht_ctx* c, Workspace& w) {
   ctx_free(c, w.Y, w.Y_cap);
   ctx_free(c, w.H, w.H_cap);
   ctx_free(c, w.gt, w.gt_cap);
+  ctx_free(c, w.gtw, w.gtw_cap);
   w.gt_valid = false;
   for (int i = 0; i < 2; ++i) ctx_free(c, w.stage[i], w.stage_cap[i]);
   for (int i = 0; i < 2; ++i) {
@@ -516,6 +519,10 @@ extern "C" int slsht_set_option(slsht_ctx* c, int option, int64_t v) {
       if (v < 0 || v > 2) return SLSHT_E_ARG;
       c->opt_gaunt_table = (int)v;
       return SLSHT_OK;
+    case SLSHT_OPT_WAIT_TEST:
+      if (v < 0 || v > 1) return SLSHT_E_ARG;
+      c->opt_wait_test = (int)v;
+      return SLSHT_OK;
     default:
       return SLSHT_E_ARG;
   }
@@ -545,6 +552,32 @@ static bool use_tensor_cores(slsht_ctx* ctx, const slsht_desc* d) {
   return true;   // default for FP32_BULK when supported
 }
 
+// Work items of the Gaunt table: (i, j) with pair j = (l, -m) the mirror of
+// pair i = (l, m), m != 0 (one chain fills both), else (i, -1); every pair is
+// in exactly one item.
+static void mirror_work(const int32_t* lm, int32_t n, std::vector<int32_t>* out) {
+  std::map<std::pair<int, int>, std::vector<int32_t>> free_idx;
+  for (int32_t i = n - 1; i >= 0; --i) free_idx[{lm[2 * i], lm[2 * i + 1]}].push_back(i);
+  std::vector<char> used((size_t)n, 0);
+  out->clear();
+  for (int32_t i = 0; i < n; ++i) {
+    if (used[i]) continue;
+    used[i] = 1;
+    const int l = lm[2 * i], m = lm[2 * i + 1];
+    int32_t j = -1;
+    if (m != 0) {
+      auto it = free_idx.find({l, -m});
+      if (it != free_idx.end()) {
+        auto& v = it->second;
+        while (!v.empty() && used[v.back()]) v.pop_back();
+        if (!v.empty()) { j = v.back(); v.pop_back(); used[j] = 1; }
+      }
+    }
+    out->push_back(i);
+    out->push_back(j);
+  }
+}
+
 // The forward transform on workspace `w` and stream `st` (ctx->mu NOT held).
 static int forward_impl(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const double* f_lm,
                         const double* h_lm, const int32_t* lm, const int32_t* lm_host, int32_t n_pairs,
@@ -557,7 +590,7 @@ static int forward_impl(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
   const bool host_out = !is_device_ptr(g_out);
   CK(cudaStreamWaitEvent(st, w.done, 0));
 
-  int route, tc, engine, gt_opt;
+  int route, tc, engine, gt_opt, wait_test;
   int64_t chunk_opt;
   {
     std::lock_guard<std::mutex> g(ctx->mu);
@@ -566,6 +599,7 @@ static int forward_impl(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
     engine = ctx->opt_alpha_engine;
     chunk_opt = ctx->opt_chunk;
     gt_opt = ctx->opt_gaunt_table;
+    wait_test = ctx->opt_wait_test;
   }
   // rotated-window route on the tensor cores: producer and alpha stage fused
   // into one kernel unless the separate producer kernel was asked for
@@ -640,7 +674,12 @@ static int forward_impl(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
     if (!hit) {
       w.gt_valid = false;
       CKS(ws_reserve(ctx, w, &w.gt, &w.gt_cap, gt_bytes));
-      LAUNCH(SLSHT_STAGE_COUPLE, ax, launch_gaunt_table(Lf, Lh, (const int2*)lm_dev, n_pairs, w.gt, ax));
+      mirror_work(lm_host, n_pairs, &w.gt_work);
+      const int nwork = (int)(w.gt_work.size() / 2);
+      CKS(ws_reserve(ctx, w, &w.gtw, &w.gtw_cap, sizeof(int32_t) * w.gt_work.size()));
+      CK(cudaMemcpyAsync(w.gtw, w.gt_work.data(), sizeof(int32_t) * w.gt_work.size(), cudaMemcpyHostToDevice, ax));
+      LAUNCH(SLSHT_STAGE_COUPLE, ax,
+             launch_gaunt_table(Lf, Lh, (const int2*)lm_dev, n_pairs, (const int2*)w.gtw, nwork, w.gt, ax));
       w.gt_Lf = Lf;
       w.gt_Lh = Lh;
       w.gt_lm.assign(lm_host, lm_host + 2 * (size_t)n_pairs);
@@ -720,7 +759,12 @@ static int forward_impl(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
     }
     if (fused) {
       LAUNCH(SLSHT_STAGE_ALPHA, st,
-             launch_alpha_fused(kcc, (const float2*)w.H, etab, Lh, Na, Nb, Ng, np, (float2*)gdst, ctx->num_sms, st));
+             launch_alpha_fused(kcc, (const float2*)w.H, etab, Lh, Na, Nb, Ng, np, (float2*)gdst, ctx->num_sms,
+                                ci == 0 ? wait_test : 0, st));
+      if (ci == 0 && wait_test) {      // one launch only
+        std::lock_guard<std::mutex> g(ctx->mu);
+        ctx->opt_wait_test = 0;
+      }
     } else if (tc) {
       LAUNCH(SLSHT_STAGE_ALPHA, st,
              launch_alpha_tc(X, etab, Lh, Na, Nb, Ng, np, (float2*)gdst, ctx->num_sms, st));

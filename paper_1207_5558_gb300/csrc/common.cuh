@@ -47,10 +47,13 @@ cudaError_t launch_couple(const double2* f, int Lf, int Lh, const int2* lm, int 
                           double2* kc, cudaStream_t st);
 
 // The same k through a signal-independent table of Gaunt coefficients:
-// launch_gaunt_table fills `table` (gaunt_table_bytes) for a pair list,
-// launch_couple_apply then forms k for any signal f with that pair list.
+// launch_gaunt_table fills `table` (gaunt_table_bytes) for a pair list from
+// nwork work items (pair, mirror index of (l, -m) or -1; every pair appears in
+// exactly one item, as pair or as mirror), launch_couple_apply then forms k
+// for any signal f with that pair list.
 size_t gaunt_table_bytes(int Lh, int npairs);
-cudaError_t launch_gaunt_table(int Lf, int Lh, const int2* lm, int npairs, void* table, cudaStream_t st);
+cudaError_t launch_gaunt_table(int Lf, int Lh, const int2* lm, int npairs, const int2* work, int nwork, void* table,
+                               cudaStream_t st);
 cudaError_t launch_couple_apply(const double2* f, int Lh, const int2* lm, int npairs, const void* table, double2* kc,
                                 cudaStream_t st);
 

@@ -193,11 +193,18 @@ cudaError_t launch_couple(const double2* f, int Lf, int Lh, const int2* lm, int 
 // t = p*p + p + q fastest) and meta[pair][t] = (l'_0, count); the table
 // depends only on (L_f, L_h, the pair list), so a caller that repeats a pair
 // list for many signals builds it once, like the Delta and d(beta) tables.
+// Mirror pairs share their chains: with q -> -q,
+//   (l' p l; -m+q, -q, m) = (-1)^{l'+p+l} (l' p l; m-q, q, -m)
+// and l'+p+l is even wherever (l' p l; 0 0 0) is non-zero, so
+// T(l', -m+q; p, -q; l, -m) = T(l', m-q; p, q; l, m) with the same l' range:
+// work item w = (pair, mirror) fills item (p, q) of `pair` and item (p, -q) of
+// `mirror` (when mirror >= 0) from one chain.
 template <int CMAX>
 __global__ void __launch_bounds__(256) k_gaunt_table(int Lf, int Lh, const int2* __restrict__ lm,
-                                                     double* __restrict__ coef, int2* __restrict__ meta) {
+                                                     const int2* __restrict__ work, double* __restrict__ coef,
+                                                     int2* __restrict__ meta) {
   __shared__ double w0s[SLSHT_MAX_LH * (SLSHT_MAX_LH + 1) / 2];
-  const int pair = blockIdx.x;
+  const int pair = work[blockIdx.x].x, mirror = work[blockIdx.x].y;
   const int l = lm[pair].x, m = lm[pair].y;
   for (int p = threadIdx.x; p < Lh; p += blockDim.x) {
     double* w = w0s + p * (p + 1) / 2;
@@ -235,11 +242,19 @@ __global__ void __launch_bounds__(256) k_gaunt_table(int Lf, int Lh, const int2*
       first = j0 + 2 * i0;
       const double pre = ((m & 1) ? -1.0 : 1.0) *
                          sqrt((2.0 * p + 1.0) * (2.0 * l + 1.0) / (4.0 * 3.14159265358979323846));
-      for (int j1 = first; j1 <= jend; j1 += 2, ++cnt)
-        coef[((size_t)pair * Lh + cnt) * n2 + t] = pre * sqrt(2.0 * j1 + 1.0) * w[(j1 - j0) >> 1] * fm[j1 - j1min_m];
+      const int tm = p * p + p - q;          // the mirror pair's item (p, -q)
+      for (int j1 = first; j1 <= jend; j1 += 2, ++cnt) {
+        const double c = pre * sqrt(2.0 * j1 + 1.0) * w[(j1 - j0) >> 1] * fm[j1 - j1min_m];
+        coef[((size_t)pair * Lh + cnt) * n2 + t] = c;
+        if (mirror >= 0) coef[((size_t)mirror * Lh + cnt) * n2 + tm] = c;
+      }
     }
-    for (int i = cnt; i < Lh; ++i) coef[((size_t)pair * Lh + i) * n2 + t] = 0.0;
+    for (int i = cnt; i < Lh; ++i) {
+      coef[((size_t)pair * Lh + i) * n2 + t] = 0.0;
+      if (mirror >= 0) coef[((size_t)mirror * Lh + i) * n2 + (p * p + p - q)] = 0.0;
+    }
     meta[(size_t)pair * n2 + t] = make_int2(first, cnt);
+    if (mirror >= 0) meta[(size_t)mirror * n2 + (p * p + p - q)] = make_int2(first, cnt);
   }
 }
 
@@ -275,14 +290,15 @@ size_t gaunt_table_bytes(int Lh, int npairs) {
   return (size_t)npairs * (n2 * Lh * sizeof(double) + n2 * sizeof(int2));
 }
 
-cudaError_t launch_gaunt_table(int Lf, int Lh, const int2* lm, int npairs, void* table, cudaStream_t st) {
-  if (npairs <= 0) return cudaSuccess;
+cudaError_t launch_gaunt_table(int Lf, int Lh, const int2* lm, int npairs, const int2* work, int nwork, void* table,
+                               cudaStream_t st) {
+  if (npairs <= 0 || nwork <= 0) return cudaSuccess;
   const int threads = Lh * Lh < 256 ? ((Lh * Lh + 31) / 32) * 32 : 256;
   double* coef = (double*)table;
   int2* meta = (int2*)(coef + (size_t)npairs * Lh * Lh * Lh);
-  if (Lh <= 16) k_gaunt_table<32><<<npairs, threads, 0, st>>>(Lf, Lh, lm, coef, meta);
-  else if (Lh <= 32) k_gaunt_table<64><<<npairs, threads, 0, st>>>(Lf, Lh, lm, coef, meta);
-  else k_gaunt_table<128><<<npairs, threads, 0, st>>>(Lf, Lh, lm, coef, meta);
+  if (Lh <= 16) k_gaunt_table<32><<<nwork, threads, 0, st>>>(Lf, Lh, lm, work, coef, meta);
+  else if (Lh <= 32) k_gaunt_table<64><<<nwork, threads, 0, st>>>(Lf, Lh, lm, work, coef, meta);
+  else k_gaunt_table<128><<<nwork, threads, 0, st>>>(Lf, Lh, lm, work, coef, meta);
   return cudaGetLastError();
 }
 

@@ -26,8 +26,11 @@ cudaError_t launch_alpha_tc(const void* xblob, const void* etab, int Lh, int Na,
 // (launch_rotwin_f32, tiled layout of h_index) and the pair's coupling row
 // kc, then multiplied by the E tables on tcgen05; g[pair][a][j] complex64.
 // Lh <= 16.
+// wait_test != 0: the launch withholds the first A tile of every CTA so its
+// bounded waits expire and it reports through the error word (tests the
+// timeout path; the output is not computed).
 cudaError_t launch_alpha_fused(const double2* kc, const float2* H, const void* etab, int Lh, int Na, int Nb,
-                               int Ng, int npairs, float2* g, int num_sms, cudaStream_t st);
+                               int Ng, int npairs, float2* g, int num_sms, int wait_test, cudaStream_t st);
 // Device error word shared by the tensor-core kernels (allocated on first use).
 int* tc_error_word();
 // Non-zero (and cleared) if a tensor-core kernel gave up on a bounded wait

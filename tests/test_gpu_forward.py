@@ -276,3 +276,27 @@ def test_gaunt_table_mirror_pairs_with_duplicates(ctx):
         ctx.set_option(pkg.SLSHT_OPT_GAUNT_TABLE, 0)
     assert rel(g, g2) < 1e-13
     assert rel(g, O.forward_coeff(f, h, Lf, Lh, pairs, grid)) < TOL64
+
+
+def test_bounded_wait_expiry_reports_and_context_recovers(ctx):
+    """The timeout path of the fused tensor-core kernel: with one internal
+    hand-off withheld (SLSHT_OPT_WAIT_TEST) every bounded wait expires, the
+    kernel leaves cleanly, slsht_get_stats reports SLSHT_E_TIMEOUT, and the
+    next call on the same context is correct."""
+    import torch
+    import paper_1207_5558_gb300 as pkg
+    from paper_1207_5558_gb300 import _abi
+    Lf, Lh, grid = 10, 5, (130, 10, 13)
+    f = synth.signal_powerlaw(Lf, 81)
+    h = synth.window_cn(Lh, 82)
+    pairs = synth.pairs_bands([2, 9])
+    ctx.stats(reset=True)
+    ctx.set_option(pkg.SLSHT_OPT_WAIT_TEST, 1)
+    ctx.forward(Lf, Lh, grid, f, h, pairs, prec=1)
+    torch.cuda.synchronize()
+    with pytest.raises(pkg.SlshtError) as e:
+        ctx.stats()
+    assert e.value.code == _abi.SLSHT_E_TIMEOUT
+    ctx.stats()                                    # the error word was cleared
+    g = _fw(ctx, Lf, Lh, grid, f, h, pairs, 1)
+    assert rel(g, O.forward_coeff(f, h, Lf, Lh, pairs, grid)) < TOL32
