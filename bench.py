@@ -256,7 +256,8 @@ def serve_bench(pkg, device, n, rate, seed=4000, max_outstanding_bytes=48 << 30,
 
 def profile_case(pkg, n):
     """A small case of workload 3 for kernel captures: one chunk of 48 pairs per
-    launch, a few GB on the device, two passes."""
+    launch, a few GB on the device, two forward passes, then two inverses of
+    the result."""
     import numpy as np
     import torch
     import synth
@@ -268,6 +269,9 @@ def profile_case(pkg, n):
     g = torch.empty((n,) + c["grid"], dtype=torch.complex64, device="cuda")
     for _ in range(2):
         pkg.slsht_forward(ctx.h, pkg.make_desc(c["Lf"], c["Lh"], c["grid"], 1), f, h, sub, n, g)
+    fout = torch.empty(n, dtype=torch.complex128, device="cuda")
+    for _ in range(2):
+        pkg.slsht_inverse(ctx.h, pkg.make_desc(c["Lf"], c["Lh"], c["grid"], 1), g, complex(h[0]), sub, n, fout)
     torch.cuda.synchronize()
     print(json.dumps({"profile_pairs": n, "max_abs_g": float(g.abs().max())}))
     ctx.close()
