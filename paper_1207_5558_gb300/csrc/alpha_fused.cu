@@ -1,41 +1,46 @@
 // FP32_BULK forward transform, rotated-window route, as ONE persistent
 // tcgen05 kernel: the beta/gamma producer and the alpha stage fused.
 //
-// For one pair (l, m) and columns j = (beta_b, gamma_c) (Sec. IV, Eq. 24 with
-// the sums over q' and p reordered):
+// For one pair (l, m) and columns j = (beta_b, gamma_c) (Sec. IV-B,
+// Eq. alternative_harmonic_formulation_wigner with the sums over q' and p
+// regrouped):
 //   X_q(j)   = sum_{p >= |q|} k_lm(p, q) H^p_q(j),
 //   g[a][j]  = sum_q X_q(j) e^{-i q alpha_a},
 // where H^p_q(j) = sum_q' h_p^q' d^p_{q,q'}(beta_b) e^{-i q' gamma_c} is the
 // rotated window (pair independent, computed once per call).  The alpha sum
 // is the real GEMM of the tensor-core alpha stage (same split-FP16 operands,
 // same 128-byte swizzled K-major layout, same E tables); what changes is where
-// A comes from: four producer warps build the A tile of the next
-// (pair, 128-column tile) item directly in shared memory while the tensor
-// cores and the epilogue work on the current one, so the X blobs never
-// travel through HBM and the producer needs no separate kernel beside this
-// one on the SMs.
+// A comes from: producer warps build the A tile of the next (pair, 128-column
+// tile) item directly in shared memory while the tensor cores and the
+// epilogue work on the current one, so the A operand never travels through
+// HBM and no second kernel competes for the SMs.
 //
-// Warp roles (480 threads, one CTA per SM):
-//   warp 0      loads E-table chunks (cp.async.bulk) into the single B stage;
-//   warp 1      allocates TMEM, issues tcgen05.mma from one thread;
-//   warps 2-5   X producers: thread t owns column j = tile*128 + t, sums
-//               k(p,q) H^p_q(j) over every (p, q) (H rows from a shared-memory
-//               ring, k broadcast from shared memory), scales the column by
-//               2^e (largest entry into [2^14, 2^15)), splits it into FP16
-//               hi/lo and writes its 128-byte swizzled A rows; the per-column
-//               2^-e goes to shared memory beside the A stage;
-//   warps 6-13  epilogue: TMEM -> registers, rescale, streaming stores of g;
-//   warp 14     streams the item's H tile (H resident in L2, tiled so that
+// Warp roles (608 threads, one CTA per SM):
+//   warp 0      streams E-table chunks (TC_NC = 64 alpha rows, 32 KB) into a
+//               double-buffered B stage with cp.async.bulk;
+//   warp 1      allocates TMEM, issues tcgen05.mma from one thread into four
+//               128 x TC_N FP32 accumulators;
+//   warps 2-9   X producers: thread t owns column j = tile*128 + (t & 127)
+//               and the sign half t >> 7 of q; it sums k(p,q) H^p_q(j) for
+//               its orders (H rows from a shared-memory ring, k broadcast
+//               from shared memory), the two halves exchange the column
+//               maximum, scale the column by 2^e (largest entry into
+//               [2^14, 2^15)), split into FP16 hi/lo and write their halves
+//               of the 128-byte swizzled A row; the per-column 2^-e goes to
+//               shared memory beside the A stage;
+//   warps 10-17 epilogue: TMEM -> registers, rescale, streaming stores of g;
+//   warp 18     streams the item's H tile (H resident in L2, tiled so that
 //               a tile's rows are contiguous) into a 5-stage ring of 16 rows
 //               (16 KB a stage, one cp.async.bulk each).
 // Hand-offs (mbarriers; every wait is bounded):
-//   a_full[s]   X producers -> MMA and epilogue (128 arrivals, after a
+//   a_full[s]   X producers -> MMA and epilogue (256 arrivals, after a
 //               proxy fence so the tensor core sees the generic stores);
 //   a_empty[s]  MMA commit + every epilogue thread once it has read the
 //               stage's scales -> X producers (257 arrivals);
-//   h_full[s] / h_empty[s]  H ring: loader (+ bytes) -> producers (128
+//   h_full[s] / h_empty[s]  H ring: loader (+ bytes) -> producers (256
 //               arrivals when a stage's rows are consumed) -> loader;
-//   b_full / b_empty, acc_full[2] / acc_empty[2] as in the unfused kernel.
+//   b_full[s] / b_empty[s]  E loader (+ bytes) -> MMA (commit) -> E loader;
+//   acc_full[i] / acc_empty[i]  MMA (commit) -> epilogue (256 arrivals) -> MMA.
 // On a bounded wait's expiry the CTA raises its abort flag, every role leaves
 // its loop (the producer warps decide together through one named barrier so
 // they cannot split), waits (bounded) for its copies and MMAs in flight,
@@ -56,8 +61,10 @@
 #define FU_HS 5                                  // ring stages
 #define FU_H_BYTES (FU_HS * FU_HR * TC_M * 8)    // 80 KB
 
+#define FU_ACC 4                                 // TMEM accumulators (TC_N columns each)
+
 struct FuShared {
-  uint64_t a_full[2], a_empty[2], b_full, b_empty, acc_full[2], acc_empty[2], drain;
+  uint64_t a_full[2], a_empty[2], b_full[2], b_empty[2], acc_full[FU_ACC], acc_empty[FU_ACC], drain;
   uint64_t h_full[FU_HS], h_empty[FU_HS];
   uint32_t tmem_base;
   int abort_flag;
@@ -67,7 +74,7 @@ struct FuShared {
   float2 k[2][16 * 16];         // coupling row of the item's pair, FP32
 };
 
-#define FU_SMEM (2 * TC_A_BYTES + TC_B_BYTES + FU_H_BYTES + 1024 + (int)sizeof(FuShared))
+#define FU_SMEM (2 * TC_A_BYTES + 2 * TC_B_BYTES + FU_H_BYTES + 1024 + (int)sizeof(FuShared))
 
 __device__ __forceinline__ uint32_t pack_h2(float a, float b, uint32_t* lo_word) {
   const __half ha = __float2half_rn(a), hb = __float2half_rn(b);
@@ -131,9 +138,9 @@ k_alpha_fused(const double2* __restrict__ kc, const float2* __restrict__ H, int 
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = sm;                               // 2 x 32 KB
-  unsigned char* sB = sm + 2 * TC_A_BYTES;              // 64 KB
-  float2* sH = reinterpret_cast<float2*>(sB + TC_B_BYTES);   // [stage][row][128 columns]
-  FuShared* S = reinterpret_cast<FuShared*>(sB + TC_B_BYTES + FU_H_BYTES);
+  unsigned char* sB = sm + 2 * TC_A_BYTES;              // 2 x 32 KB (double-buffered E chunk)
+  float2* sH = reinterpret_cast<float2*>(sB + 2 * TC_B_BYTES);   // [stage][row][128 columns]
+  FuShared* S = reinterpret_cast<FuShared*>(sB + 2 * TC_B_BYTES + FU_H_BYTES);
   volatile int* abort_flag = &S->abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nch = (Na + TC_NC - 1) / TC_NC;
@@ -146,11 +153,13 @@ k_alpha_fused(const double2* __restrict__ kc, const float2* __restrict__ H, int 
     for (int i = 0; i < 2; ++i) {
       mbar_init(smem_u32(&S->a_full[i]), 32 * FU_XWARPS);
       mbar_init(smem_u32(&S->a_empty[i]), 1 + 32 * TC_EPI_WARPS);
+      mbar_init(smem_u32(&S->b_full[i]), 1);
+      mbar_init(smem_u32(&S->b_empty[i]), 1);
+    }
+    for (int i = 0; i < FU_ACC; ++i) {
       mbar_init(smem_u32(&S->acc_full[i]), 1);
       mbar_init(smem_u32(&S->acc_empty[i]), 32 * TC_EPI_WARPS);
     }
-    mbar_init(smem_u32(&S->b_full), 1);
-    mbar_init(smem_u32(&S->b_empty), 1);
     mbar_init(smem_u32(&S->drain), 1);
     for (int i = 0; i < FU_HS; ++i) {
       mbar_init(smem_u32(&S->h_full[i]), 1);
@@ -159,7 +168,7 @@ k_alpha_fused(const double2* __restrict__ kc, const float2* __restrict__ H, int 
     S->abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 1) {   // TMEM: 512 columns = two 128x256 FP32 accumulators
+  if (warp == 1) {   // TMEM: 512 columns = FU_ACC accumulators of 128 x TC_N FP32
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
                      smem_u32(&S->tmem_base)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -172,24 +181,28 @@ k_alpha_fused(const double2* __restrict__ kc, const float2* __restrict__ H, int 
   if (warp == 0) {
     // ---------------- E-table loader
     if (lane == 0) {
-      int b_armed = -1;
+      int b_armed[2] = {-1, -1};
       long long bc = 0;
       bool ok = true;
       for (long long it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
         for (int c = 0; c < nch; ++c, ++bc) {
-          const uint32_t pb = (uint32_t)(bc & 1);
-          if (!(ok = mbar_wait_n(smem_u32(&S->b_empty), pb ^ 1u, abort_flag, wlim))) break;
-          const uint32_t fb = smem_u32(&S->b_full);
+          const int sb = (int)(bc & 1);                    // E stage of this chunk
+          const uint32_t pb = (uint32_t)((bc >> 1) & 1);   // its use parity
+          if (!(ok = mbar_wait_n(smem_u32(&S->b_empty[sb]), pb ^ 1u, abort_flag, wlim))) break;
+          const uint32_t fb = smem_u32(&S->b_full[sb]);
           mbar_expect_tx(fb, TC_B_BYTES);
           const unsigned char* bsrc = etab + (size_t)c * TC_B_BYTES;
-          for (int o = 0; o < TC_B_BYTES; o += 16384) bulk_g2s(smem_u32(sB + o), bsrc + o, 16384, fb);
-          b_armed = (int)pb;
+          for (int o = 0; o < TC_B_BYTES; o += 16384)
+            bulk_g2s(smem_u32(sB + sb * TC_B_BYTES + o), bsrc + o, 16384, fb);
+          if (sb == 0) b_armed[0] = (int)pb; else b_armed[1] = (int)pb;
         }
       }
       if (!ok) *abort_flag = 1;
-      if (b_armed >= 0) {   // the last copy must land before the CTA may exit
-        uint32_t n = 0;
-        while (!mbar_test(smem_u32(&S->b_full), (uint32_t)b_armed) && ++n < TC_WAIT_LIMIT) {}
+      for (int i = 0; i < 2; ++i) {   // copies in flight must land before the CTA may exit
+        if (b_armed[i] >= 0) {
+          uint32_t n = 0;
+          while (!mbar_test(smem_u32(&S->b_full[i]), (uint32_t)b_armed[i]) && ++n < TC_WAIT_LIMIT) {}
+        }
       }
     }
   } else if (warp == 1) {
@@ -205,11 +218,14 @@ k_alpha_fused(const double2* __restrict__ kc, const float2* __restrict__ H, int 
         tc_fence_after();
         const uint32_t a_hi = smem_u32(sA + sa * TC_A_BYTES), a_lo = a_hi + TC_A_HALF;
         for (int c = 0; c < nch; ++c, ++bc, ++ac) {
-          const int acc = (int)(ac & 1);
-          if (!(ok = mbar_wait_n(smem_u32(&S->b_full), (uint32_t)(bc & 1), abort_flag, wlim))) break;
-          if (!(ok = mbar_wait_n(smem_u32(&S->acc_empty[acc]), (uint32_t)(((ac >> 1) & 1) ^ 1), abort_flag, wlim))) break;
+          const int acc = (int)(ac % FU_ACC);
+          const int sb = (int)(bc & 1);
+          if (!(ok = mbar_wait_n(smem_u32(&S->b_full[sb]), (uint32_t)((bc >> 1) & 1), abort_flag, wlim))) break;
+          if (!(ok = mbar_wait_n(smem_u32(&S->acc_empty[acc]), (uint32_t)(((ac / FU_ACC) & 1) ^ 1), abort_flag,
+                                 wlim)))
+            break;
           tc_fence_after();
-          const uint32_t b_hi = smem_u32(sB), b_lo = b_hi + TC_B_HALF;
+          const uint32_t b_hi = smem_u32(sB + sb * TC_B_BYTES), b_lo = b_hi + TC_B_HALF;
           const uint32_t d = tmem + (uint32_t)(acc * TC_N);
           const uint32_t as[3] = {a_hi, a_hi, a_lo};
           const uint32_t bs[3] = {b_hi, b_lo, b_hi};
@@ -220,7 +236,7 @@ k_alpha_fused(const double2* __restrict__ kc, const float2* __restrict__ H, int 
             for (int s = 0; s < TC_KB / 16; ++s)       // K = 16 per MMA: +32 bytes
               umma_f16(d, ad + (uint64_t)(2 * s), bd + (uint64_t)(2 * s), idesc, (pr | s) != 0);
           }
-          umma_commit(smem_u32(&S->b_empty));
+          umma_commit(smem_u32(&S->b_empty[sb]));
           umma_commit(smem_u32(&S->acc_full[acc]));
         }
         if (!ok) break;
@@ -367,7 +383,7 @@ k_alpha_fused(const double2* __restrict__ kc, const float2* __restrict__ H, int 
     }
   } else {
     // ---------------- epilogue: TMEM lane quadrant = warp % 4, half = which
-    // 64 of the chunk's 128 alpha rows
+    // TC_NC / 2 of the chunk's TC_NC alpha rows
     const int quad = warp & 3;
     const int half = (warp - FU_E0) >> 2;
     const int row = quad * 32 + lane;
@@ -387,17 +403,17 @@ k_alpha_fused(const double2* __restrict__ kc, const float2* __restrict__ H, int 
       mbar_arrive(smem_u32(&S->a_empty[sa]));
       float2* gp = g + (size_t)pair * Na * J + (jin ? j : 0);
       for (int c = 0; c < nch; ++c, ++ac) {
-        const int acc = (int)(ac & 1);
+        const int acc = (int)(ac % FU_ACC);
         // one lane waits, the warp follows: tcgen05.ld needs a converged warp
         int got = 0;
-        if (lane == 0) got = mbar_wait_n(smem_u32(&S->acc_full[acc]), (uint32_t)((ac >> 1) & 1), abort_flag, wlim);
+        if (lane == 0) got = mbar_wait_n(smem_u32(&S->acc_full[acc]), (uint32_t)((ac / FU_ACC) & 1), abort_flag, wlim);
         got = __shfl_sync(0xffffffffu, got, 0);
         __syncwarp();
         if (!(ok = got != 0)) break;
         tc_fence_after();
         const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * TC_N);
 #pragma unroll 1
-        for (int cb = half * 64; cb < half * 64 + 64; cb += 16) {
+        for (int cb = half * (TC_NC / 2); cb < half * (TC_NC / 2) + TC_NC / 2; cb += 16) {
           uint32_t vr[16], vi[16];
           TMEM_LD16(tbase + (uint32_t)cb, vr);
           TMEM_LD16(tbase + (uint32_t)(TC_NC + cb), vi);

@@ -47,9 +47,9 @@ size_t tc_xblob_bytes(int Nb, int Ng, int Lh) {
 }
 
 // ---------------------------------------------------------------- E tables
-// chunk c: [hi part: 256 rows x 64][lo part], rows n < 128 -> alpha a = c*128+n
-// (cos at k = 15+q | sin at k = 47+q), rows 128+n -> (-sin | cos); zeros beyond Na
-// and for |q| >= Lh.
+// chunk c: [hi part: TC_N = 128 rows x 64][lo part], rows n < TC_NC = 64 -> alpha
+// a = c*64+n (cos at k = 15+q | sin at k = 47+q), rows 64+n -> (-sin | cos); zeros
+// beyond Na and for |q| >= Lh.
 __global__ void k_tc_etab(unsigned char* __restrict__ etab, int Na, int Lh) {
   const int K = 2 * Lh - 1;
   const int c = blockIdx.x;
@@ -393,7 +393,7 @@ k_alpha_tc(const unsigned char* __restrict__ xblob, size_t blob_stride, int tile
     bars->abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 1) {   // TMEM: 512 columns = two 128x256 FP32 accumulators
+  if (warp == 1) {   // TMEM: 512 columns (two 128 x TC_N FP32 accumulators in use)
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
                      smem_u32(&bars->tmem_base)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -509,7 +509,7 @@ k_alpha_tc(const unsigned char* __restrict__ xblob, size_t blob_stride, int tile
         tc_fence_after();
         const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * TC_N);
 #pragma unroll 1
-        for (int cb = half * 64; cb < half * 64 + 64; cb += 32) {
+        for (int cb = half * (TC_NC / 2); cb < half * (TC_NC / 2) + TC_NC / 2; cb += 32) {
           uint32_t vr[32], vi[32];
           TMEM_LD32(tbase + (uint32_t)cb, vr);
           TMEM_LD32(tbase + (uint32_t)(TC_NC + cb), vi);

@@ -6,13 +6,13 @@
 #include <stdint.h>
 
 #define TC_M 128                       // columns j per tile (MMA M)
-#define TC_NC 128                      // alpha rows per chunk
+#define TC_NC 64                       // alpha rows per chunk
 #define TC_N (2 * TC_NC)               // MMA N (Re and Im halves)
 #define TC_KB 64                       // FP16 elements of K per operand row (128 bytes)
 #define TC_A_HALF (TC_M * TC_KB * 2)   // bytes of one A part (hi or lo): 16 KB
-#define TC_B_HALF (TC_N * TC_KB * 2)   // bytes of one B part: 32 KB
+#define TC_B_HALF (TC_N * TC_KB * 2)   // bytes of one B part: 16 KB
 #define TC_A_BYTES (2 * TC_A_HALF)     // 32 KB
-#define TC_B_BYTES (2 * TC_B_HALF)     // 64 KB
+#define TC_B_BYTES (2 * TC_B_HALF)     // 32 KB
 #define TC_EPI_WARPS 8                  // two per TMEM lane quadrant, each half the columns
 #define TC_THREADS (64 + 32 * TC_EPI_WARPS)
 #define TC_SMEM (2 * TC_A_BYTES + TC_B_BYTES + 1024 + 256)
