@@ -428,6 +428,36 @@ def main():
                 "rel_l2_recovered_f": float(np.linalg.norm(fr - ftrue) / np.linalg.norm(ftrue)),
                 "bound": "hbm read (g read once, FP64 accumulation)"}
 
+    def real_fields_leg():
+        """F2 of the scope table: workload 2 (real power-law f, the real
+        elliptical eigenfunction window, all l < 64, 127 x 64 x 15, FP64)
+        with and without SLSHT_OPT_REAL_FIELDS, which computes one of each
+        mirrored pair and writes both."""
+        c2 = synth.CONFIGS[2]
+        f2, h2, p2 = synth.config_inputs(2)
+        n2 = len(p2)
+        g2 = torch.empty((n2,) + c2["grid"], dtype=torch.complex128, device="cuda")
+        fd, hd, pd = (torch.from_numpy(f2).cuda(), torch.from_numpy(h2).cuda(), torch.from_numpy(p2).cuda())
+        desc2 = pkg.make_desc(c2["Lf"], c2["Lh"], c2["grid"], 0)
+        out = {}
+        for name, opt in (("full", 0), ("real_fields", 1)):
+            ctx.set_option(pkg.SLSHT_OPT_REAL_FIELDS, opt)
+            pkg.slsht_forward(ctx.h, desc2, fd, hd, pd, n2, g2, stream)
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(3):
+                pkg.slsht_forward(ctx.h, desc2, fd, hd, pd, n2, g2, stream)
+            e1.record(stream)
+            barrier()
+            ms = e0.elapsed_time(e1) / 3
+            out[name] = {"ms_per_map": ms, "g_samples_per_s": n2 * synth.samples_per_pair(c2["grid"]) / (ms / 1e3)}
+        ctx.set_option(pkg.SLSHT_OPT_REAL_FIELDS, 0)
+        out["speedup"] = out["full"]["ms_per_map"] / out["real_fields"]["ms_per_map"]
+        out["workload"] = "workload 2: L_f=64, L_h=8 ellipse window, all l<64 (4096 pairs), grid 127x64x15, FP64"
+        del g2
+        return out
+
     # ---------------- FP32_BULK headline
     g32 = torch.empty((npairs_map,) + grid, dtype=torch.complex64, device="cuda")
     ms32, st32, clk = timed(1, g32, args.steps, args.warmup, ClockSampler(local))
@@ -475,6 +505,7 @@ def main():
                 "note": "FP64 alpha stage is FP64-pipe bound; stage times overlap (two streams)",
                 "inverse": inv64}
         del g64, a64
+        fp64["real_fields_workload2"] = real_fields_leg()
     del a32
     torch.cuda.empty_cache()
 

@@ -256,12 +256,20 @@ int slsht_get_stats(slsht_ctx* ctx, slsht_stats* out, int reset);
  *                            slsht_get_stats returns SLSHT_E_TIMEOUT; that
  *                            call's g is not computed.  Resets itself.  For
  *                            testing the timeout path; the context stays usable.
+ *  SLSHT_OPT_REAL_FIELDS  1: the caller guarantees that f and h are real
+ *                            fields (f_{l,-m} = (-1)^m conj f_lm, and the same
+ *                            for h).  Then g(rho; l, -m) = (-1)^m conj
+ *                            g(rho; l, m), and of every pair whose mirror
+ *                            (l, -m) is also listed only one is computed:
+ *                            the alpha stage stores both outputs (device g_out
+ *                            only; host g_out is computed in full).  0: off.
  * Returns SLSHT_OK or SLSHT_E_ARG. */
 #define SLSHT_OPT_BETA_ROUTE   1
 #define SLSHT_OPT_ALPHA_ENGINE 2
 #define SLSHT_OPT_CHUNK_PAIRS  3
 #define SLSHT_OPT_GAUNT_TABLE  4
 #define SLSHT_OPT_WAIT_TEST    5
+#define SLSHT_OPT_REAL_FIELDS  6
 int slsht_set_option(slsht_ctx* ctx, int option, int64_t value);
 
 /* Bytes of device memory the context currently holds. */

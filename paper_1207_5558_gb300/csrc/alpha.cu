@@ -16,7 +16,7 @@
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT)
 k_alpha_cc(const typename vec2<T>::t* __restrict__ Xs, const typename vec2<T>::t* __restrict__ csa,
-           int Lh, int Na, int J, typename vec2<T>::t* __restrict__ g) {
+           int Lh, int Na, int J, typename vec2<T>::t* __restrict__ g, const int2* __restrict__ slots) {
   typedef typename vec2<T>::t T2;
   extern __shared__ unsigned char smem_raw[];
   T2* sx = reinterpret_cast<T2*>(smem_raw);      // [2Lh-1][NT]
@@ -30,7 +30,11 @@ k_alpha_cc(const typename vec2<T>::t* __restrict__ Xs, const typename vec2<T>::t
     sx[c * NT + t] = (j < J) ? src[(size_t)c * J + j] : mk2((T)0, (T)0);
   __syncthreads();
   if (j >= J) return;
-  T2* dst = g + (size_t)pair * Na * J + j;
+  // output slot and, for a mirrored pair, the slot of (l, -m) with (-1)^m
+  const int2 sl = slots != nullptr ? slots[pair] : make_int2(pair, -1);
+  T2* dst = g + (size_t)sl.x * Na * J + j;
+  T2* mdst = sl.y >= 0 ? g + (size_t)(sl.y >> 1) * Na * J + j : nullptr;
+  const T ms = (sl.y & 1) ? (T)-1 : (T)1;
   const T2 x0 = sx[t];
   for (int a0 = 0; a0 < Na; a0 += ABLK) {
     T re[ABLK], im[ABLK];
@@ -52,13 +56,18 @@ k_alpha_cc(const typename vec2<T>::t* __restrict__ Xs, const typename vec2<T>::t
 #pragma unroll
     for (int u = 0; u < ABLK; ++u)
       if (a0 + u < Na) dst[(size_t)(a0 + u) * J] = mk2(re[u], im[u]);
+    if (mdst != nullptr) {
+#pragma unroll
+      for (int u = 0; u < ABLK; ++u)
+        if (a0 + u < Na) mdst[(size_t)(a0 + u) * J] = mk2(ms * re[u], -ms * im[u]);
+    }
   }
 }
 
 template <typename T>
 static cudaError_t launch_alpha_t(const typename vec2<T>::t* Xs, const typename vec2<T>::t* csa,
                                   int Lh, int Na, int J, int npairs, typename vec2<T>::t* g,
-                                  cudaStream_t st) {
+                                  const int2* slots, cudaStream_t st) {
   if (npairs <= 0 || J <= 0) return cudaSuccess;
   typedef typename vec2<T>::t T2;
   const size_t smem128 = sizeof(T2) * (size_t)(2 * Lh - 1) * 128;
@@ -69,7 +78,7 @@ static cudaError_t launch_alpha_t(const typename vec2<T>::t* Xs, const typename 
       if (e != cudaSuccess) return e;
     }
     dim3 grid((J + 127) / 128, npairs);
-    k_alpha_cc<T, 128><<<grid, 128, smem128, st>>>(Xs, csa, Lh, Na, J, g);
+    k_alpha_cc<T, 128><<<grid, 128, smem128, st>>>(Xs, csa, Lh, Na, J, g, slots);
     return cudaGetLastError();
   }
   const size_t smem64 = smem128 / 2;
@@ -77,15 +86,15 @@ static cudaError_t launch_alpha_t(const typename vec2<T>::t* Xs, const typename 
   cudaError_t e = cudaFuncSetAttribute(k_alpha_cc<T, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64);
   if (e != cudaSuccess) return e;
   dim3 grid((J + 63) / 64, npairs);
-  k_alpha_cc<T, 64><<<grid, 64, smem64, st>>>(Xs, csa, Lh, Na, J, g);
+  k_alpha_cc<T, 64><<<grid, 64, smem64, st>>>(Xs, csa, Lh, Na, J, g, slots);
   return cudaGetLastError();
 }
 
 cudaError_t launch_alpha_f64(const double2* Xs, const double2* csa, int Lh, int Na, int J,
-                             int npairs, double2* g, cudaStream_t st) {
-  return launch_alpha_t<double>(Xs, csa, Lh, Na, J, npairs, g, st);
+                             int npairs, double2* g, const int2* slots, cudaStream_t st) {
+  return launch_alpha_t<double>(Xs, csa, Lh, Na, J, npairs, g, slots, st);
 }
 cudaError_t launch_alpha_f32(const float2* Xs, const float2* csa, int Lh, int Na, int J,
-                             int npairs, float2* g, cudaStream_t st) {
-  return launch_alpha_t<float>(Xs, csa, Lh, Na, J, npairs, g, st);
+                             int npairs, float2* g, const int2* slots, cudaStream_t st) {
+  return launch_alpha_t<float>(Xs, csa, Lh, Na, J, npairs, g, slots, st);
 }

@@ -134,7 +134,7 @@ template <int LHB>
 __global__ void __launch_bounds__(FU_THREADS, 1)
 k_alpha_fused(const double2* __restrict__ kc, const float2* __restrict__ H, int Lh, int J, int tiles,
               const unsigned char* __restrict__ etab, int Na, int npairs, float2* __restrict__ g,
-              int* __restrict__ err, uint32_t wlim, int wait_test) {
+              int* __restrict__ err, uint32_t wlim, int wait_test, const int2* __restrict__ slots) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = sm;                               // 2 x 32 KB
@@ -401,7 +401,11 @@ k_alpha_fused(const double2* __restrict__ kc, const float2* __restrict__ H, int 
       if (!(ok = __all_sync(0xffffffffu, w_ok) != 0)) break;
       const float sc = S->scale[sa][row];
       mbar_arrive(smem_u32(&S->a_empty[sa]));
-      float2* gp = g + (size_t)pair * Na * J + (jin ? j : 0);
+      // output slot of the pair and, for a mirrored pair, of (l, -m) with its sign
+      const int2 sl = slots != nullptr ? slots[pair] : make_int2(pair, -1);
+      float2* gp = g + (size_t)sl.x * Na * J + (jin ? j : 0);
+      float2* gm = sl.y >= 0 ? g + (size_t)(sl.y >> 1) * Na * J + (jin ? j : 0) : nullptr;
+      const float msc = (sl.y & 1) ? -sc : sc;
       for (int c = 0; c < nch; ++c, ++ac) {
         const int acc = (int)(ac % FU_ACC);
         // one lane waits, the warp follows: tcgen05.ld needs a converged warp
@@ -435,6 +439,15 @@ k_alpha_fused(const double2* __restrict__ kc, const float2* __restrict__ H, int 
               }
             }
           }
+          if (jin && gm != nullptr) {     // (l, -m): (-1)^m conj g (real f and h)
+            float2* p = gm + (size_t)a0 * J;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+              if (a0 + u < Na)
+                __stcs(p, make_float2(__uint_as_float(vr[u]) * msc, -__uint_as_float(vi[u]) * msc));
+              p += J;
+            }
+          }
         }
         tc_fence_before();
         mbar_arrive(smem_u32(&S->acc_empty[acc]));
@@ -453,7 +466,7 @@ k_alpha_fused(const double2* __restrict__ kc, const float2* __restrict__ H, int 
 template <int LHB>
 static cudaError_t launch_fused_t(const double2* kc, const float2* H, const void* etab, int Lh, int Na, int J,
                                   int tiles, int npairs, float2* g, int* err, int grid, int wait_test,
-                                  cudaStream_t st) {
+                                  const int2* slots, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_alpha_fused<LHB>, cudaFuncAttributeMaxDynamicSharedMemorySize, FU_SMEM);
@@ -463,12 +476,13 @@ static cudaError_t launch_fused_t(const double2* kc, const float2* H, const void
   // the wait test uses a short limit so the expiry comes quickly
   const uint32_t wlim = wait_test ? (1u << 14) : TC_WAIT_LIMIT;
   k_alpha_fused<LHB><<<grid, FU_THREADS, FU_SMEM, st>>>(kc, H, Lh, J, tiles, (const unsigned char*)etab, Na,
-                                                        npairs, g, err, wlim, wait_test);
+                                                        npairs, g, err, wlim, wait_test, slots);
   return cudaGetLastError();
 }
 
 cudaError_t launch_alpha_fused(const double2* kc, const float2* H, const void* etab, int Lh, int Na, int Nb,
-                               int Ng, int npairs, float2* g, int num_sms, int wait_test, cudaStream_t st) {
+                               int Ng, int npairs, float2* g, int num_sms, int wait_test, const int2* slots,
+                               cudaStream_t st) {
   if (npairs <= 0) return cudaSuccess;
   if (!tc_supported(Lh, Na) || Lh > 16) return cudaErrorInvalidValue;
   // bulk copies of whole 1 KB rows of the tiled H need a 16-byte aligned base
@@ -479,7 +493,7 @@ cudaError_t launch_alpha_fused(const double2* kc, const float2* H, const void* e
   const int tiles = (J + TC_M - 1) / TC_M;
   const long long items = (long long)npairs * tiles;
   const int grid = (int)(items < num_sms ? items : num_sms);
-  if (Lh <= 4) return launch_fused_t<4>(kc, H, etab, Lh, Na, J, tiles, npairs, g, err, grid, wait_test, st);
-  if (Lh <= 8) return launch_fused_t<8>(kc, H, etab, Lh, Na, J, tiles, npairs, g, err, grid, wait_test, st);
-  return launch_fused_t<16>(kc, H, etab, Lh, Na, J, tiles, npairs, g, err, grid, wait_test, st);
+  if (Lh <= 4) return launch_fused_t<4>(kc, H, etab, Lh, Na, J, tiles, npairs, g, err, grid, wait_test, slots, st);
+  if (Lh <= 8) return launch_fused_t<8>(kc, H, etab, Lh, Na, J, tiles, npairs, g, err, grid, wait_test, slots, st);
+  return launch_fused_t<16>(kc, H, etab, Lh, Na, J, tiles, npairs, g, err, grid, wait_test, slots, st);
 }

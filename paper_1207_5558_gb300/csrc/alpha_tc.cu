@@ -369,7 +369,7 @@ struct TcBars {
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_alpha_tc(const unsigned char* __restrict__ xblob, size_t blob_stride, int tiles,
            const unsigned char* __restrict__ etab, int Na, int J, int npairs, float2* __restrict__ g,
-           int* __restrict__ err) {
+           int* __restrict__ err, const int2* __restrict__ slots) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = sm;                               // 2 x 32 KB
@@ -497,7 +497,10 @@ k_alpha_tc(const unsigned char* __restrict__ xblob, size_t blob_stride, int tile
       const float* scales = reinterpret_cast<const float*>(xblob + (size_t)pair * blob_stride +
                                                            (size_t)tiles * TC_A_BYTES);
       const float sc = jin ? scales[j] : 0.f;
-      float2* gp = g + (size_t)pair * Na * J + (jin ? j : 0);
+      const int2 sl = slots != nullptr ? slots[pair] : make_int2(pair, -1);
+      float2* gp = g + (size_t)sl.x * Na * J + (jin ? j : 0);
+      float2* gm = sl.y >= 0 ? g + (size_t)(sl.y >> 1) * Na * J + (jin ? j : 0) : nullptr;
+      const float msc = (sl.y & 1) ? -sc : sc;
       for (int c = 0; c < nch; ++c, ++ac) {
         const int acc = (int)(ac & 1);
         // one lane waits, the warp follows: tcgen05.ld needs a converged warp
@@ -529,6 +532,15 @@ k_alpha_tc(const unsigned char* __restrict__ xblob, size_t blob_stride, int tile
                 if (a0 + u < Na) __stcs(p, make_float2(__uint_as_float(vr[u]) * sc, __uint_as_float(vi[u]) * sc));
                 p += J;
               }
+            }
+          }
+          if (jin && gm != nullptr) {     // (l, -m): (-1)^m conj g (real f and h)
+            float2* p = gm + (size_t)a0 * J;
+#pragma unroll
+            for (int u = 0; u < 32; ++u) {
+              if (a0 + u < Na)
+                __stcs(p, make_float2(__uint_as_float(vr[u]) * msc, -__uint_as_float(vi[u]) * msc));
+              p += J;
             }
           }
         }
@@ -566,7 +578,7 @@ int tc_read_error(void) {
 }
 
 cudaError_t launch_alpha_tc(const void* xblob, const void* etab, int Lh, int Na, int Nb, int Ng, int npairs,
-                            float2* g, int num_sms, cudaStream_t st) {
+                            float2* g, int num_sms, const int2* slots, cudaStream_t st) {
   if (npairs <= 0) return cudaSuccess;
   if (!tc_supported(Lh, Na)) return cudaErrorInvalidValue;
   static bool attr = false;
@@ -586,6 +598,6 @@ cudaError_t launch_alpha_tc(const void* xblob, const void* etab, int Lh, int Na,
   const long long items = (long long)npairs * tiles;
   const int grid = (int)(items < num_sms ? items : num_sms);
   k_alpha_tc<<<grid, TC_THREADS, TC_SMEM, st>>>((const unsigned char*)xblob, tc_xblob_bytes(Nb, Ng, Lh), tiles,
-                                               (const unsigned char*)etab, Na, Nb * Ng, npairs, g, err);
+                                               (const unsigned char*)etab, Na, Nb * Ng, npairs, g, err, slots);
   return cudaGetLastError();
 }

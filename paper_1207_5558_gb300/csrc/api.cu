@@ -120,6 +120,10 @@ struct Workspace {
   // Gaunt coefficient table of the last pair list this workspace saw
   void* gt = nullptr; size_t gt_cap = 0;
   void* gtw = nullptr; size_t gtw_cap = 0;   // its work items (pair, mirror pair)
+  // real-field calls: the computed pairs, their output slots (host copies kept
+  // until the next call: sources of the uploads) and the device slot map
+  std::vector<int32_t> rf_lm, rf_slots;
+  void* rfs = nullptr; size_t rfs_cap = 0;
   std::vector<int32_t> gt_work;              // host copy (source of the upload)
   bool gt_valid = false;
   int gt_Lf = 0, gt_Lh = 0;
@@ -167,7 +171,7 @@ struct slsht_ctx {
   std::map<int, TableEntry> wbeta;                                  // Nb
   std::map<std::tuple<int, int>, TableEntry> etab;                  // Na, Lh (tensor-core E blobs)
   Workspace sync_ws;
-  int opt_beta_route = 0, opt_alpha_engine = 0, opt_gaunt_table = 0, opt_wait_test = 0;
+  int opt_beta_route = 0, opt_alpha_engine = 0, opt_gaunt_table = 0, opt_wait_test = 0, opt_real_fields = 0;
   int64_t opt_chunk = 0;
   bool profile = false;
   std::vector<ProfRec> prof;
@@ -287,6 +291,7 @@ static void ws_release(slsht_ctx* c, Workspace& w) {
   ctx_free(c, w.H, w.H_cap);
   ctx_free(c, w.gt, w.gt_cap);
   ctx_free(c, w.gtw, w.gtw_cap);
+  ctx_free(c, w.rfs, w.rfs_cap);
   w.gt_valid = false;
   for (int i = 0; i < 2; ++i) ctx_free(c, w.stage[i], w.stage_cap[i]);
   for (int i = 0; i < 2; ++i) {
@@ -523,6 +528,10 @@ extern "C" int slsht_set_option(slsht_ctx* c, int option, int64_t v) {
       if (v < 0 || v > 1) return SLSHT_E_ARG;
       c->opt_wait_test = (int)v;
       return SLSHT_OK;
+    case SLSHT_OPT_REAL_FIELDS:
+      if (v < 0 || v > 1) return SLSHT_E_ARG;
+      c->opt_real_fields = (int)v;
+      return SLSHT_OK;
     default:
       return SLSHT_E_ARG;
   }
@@ -579,9 +588,11 @@ static void mirror_work(const int32_t* lm, int32_t n, std::vector<int32_t>* out)
 }
 
 // The forward transform on workspace `w` and stream `st` (ctx->mu NOT held).
-static int forward_impl(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const double* f_lm,
+// slots (device, nullable): per listed pair {output slot, mirror} (see
+// launch_alpha_tc); g_out must then be device memory.
+static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const double* f_lm,
                         const double* h_lm, const int32_t* lm, const int32_t* lm_host, int32_t n_pairs,
-                        void* g_out, cudaStream_t st) {
+                        void* g_out, cudaStream_t st, const int2* slots) {
   const int Lf = d->L_f, Lh = d->L_h, Na = d->n_alpha, Nb = d->n_beta, Ng = d->n_gamma;
   const int K = 2 * Lh - 1;
   const bool f64 = d->prec == SLSHT_FP64;
@@ -755,25 +766,26 @@ static int forward_impl(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
       CK(cudaStreamWaitEvent(st, w.copy_ev[ci & 1], 0));   // staging buffer free again
       gdst = w.stage[ci & 1];
     } else {
-      gdst = (char*)g_out + per_pair_g * (size_t)off;
+      gdst = slots != nullptr ? g_out : (void*)((char*)g_out + per_pair_g * (size_t)off);
     }
+    const int2* sl = slots != nullptr ? slots + off : nullptr;
     if (fused) {
       LAUNCH(SLSHT_STAGE_ALPHA, st,
              launch_alpha_fused(kcc, (const float2*)w.H, etab, Lh, Na, Nb, Ng, np, (float2*)gdst, ctx->num_sms,
-                                ci == 0 ? wait_test : 0, st));
+                                ci == 0 ? wait_test : 0, sl, st));
       if (ci == 0 && wait_test) {      // one launch only
         std::lock_guard<std::mutex> g(ctx->mu);
         ctx->opt_wait_test = 0;
       }
     } else if (tc) {
       LAUNCH(SLSHT_STAGE_ALPHA, st,
-             launch_alpha_tc(X, etab, Lh, Na, Nb, Ng, np, (float2*)gdst, ctx->num_sms, st));
+             launch_alpha_tc(X, etab, Lh, Na, Nb, Ng, np, (float2*)gdst, ctx->num_sms, sl, st));
     } else if (f64) {
       LAUNCH(SLSHT_STAGE_ALPHA, st,
-             launch_alpha_f64((const double2*)X, (const double2*)csa, Lh, Na, (int)J, np, (double2*)gdst, st));
+             launch_alpha_f64((const double2*)X, (const double2*)csa, Lh, Na, (int)J, np, (double2*)gdst, sl, st));
     } else {
       LAUNCH(SLSHT_STAGE_ALPHA, st,
-             launch_alpha_f32((const float2*)X, (const float2*)csa, Lh, Na, (int)J, np, (float2*)gdst, st));
+             launch_alpha_f32((const float2*)X, (const float2*)csa, Lh, Na, (int)J, np, (float2*)gdst, sl, st));
     }
     if (!fused) CK(cudaEventRecord(w.x_free[ci & 1], st));
     if (host_out) {
@@ -797,6 +809,48 @@ static int forward_impl(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
     ctx->samples += (uint64_t)n_pairs * (uint64_t)Na * J;
   }
   return SLSHT_OK;
+}
+
+// The forward transform with the real-field symmetry when the context's
+// option says f and h are real fields (f_{l,-m} = (-1)^m conj f_lm, same for
+// h): then g(rho; l, -m) = (-1)^m conj g(rho; l, m) (the integrand of
+// Eq. stft_spatial is real apart from conj(Y_l^m), and Y_l^{-m} =
+// (-1)^m conj Y_l^m), so of each mirrored pair only (l, m) is computed and the
+// alpha stage stores both outputs.  Device outputs only.
+static int forward_impl(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const double* f_lm,
+                        const double* h_lm, const int32_t* lm, const int32_t* lm_host, int32_t n_pairs,
+                        void* g_out, cudaStream_t st) {
+  int real;
+  {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    real = ctx->opt_real_fields;
+  }
+  if (!real || !is_device_ptr(g_out))
+    return forward_core(ctx, w, d, f_lm, h_lm, lm, lm_host, n_pairs, g_out, st, nullptr);
+  std::vector<int32_t> pw;
+  mirror_work(lm_host, n_pairs, &pw);
+  const int32_t nw = (int32_t)(pw.size() / 2);
+  if (nw == n_pairs) return forward_core(ctx, w, d, f_lm, h_lm, lm, lm_host, n_pairs, g_out, st, nullptr);
+  w.rf_lm.resize(2 * (size_t)nw);
+  w.rf_slots.resize(2 * (size_t)nw);
+  for (int32_t k = 0; k < nw; ++k) {
+    const int32_t i = pw[2 * k], j = pw[2 * k + 1];
+    w.rf_lm[2 * k] = lm_host[2 * i];
+    w.rf_lm[2 * k + 1] = lm_host[2 * i + 1];
+    w.rf_slots[2 * k] = i;
+    w.rf_slots[2 * k + 1] = j < 0 ? -1 : 2 * j + (lm_host[2 * i + 1] & 1);
+  }
+  CK(cudaStreamWaitEvent(st, w.done, 0));
+  CKS(ws_reserve(ctx, w, &w.rfs, &w.rfs_cap, sizeof(int32_t) * w.rf_slots.size()));
+  CK(cudaMemcpyAsync(w.rfs, w.rf_slots.data(), sizeof(int32_t) * w.rf_slots.size(), cudaMemcpyHostToDevice, st));
+  const int s = forward_core(ctx, w, d, f_lm, h_lm, w.rf_lm.data(), w.rf_lm.data(), nw, g_out, st,
+                             (const int2*)w.rfs);
+  if (s == SLSHT_OK) {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    const slsht_desc* dd = d;
+    ctx->samples += (uint64_t)(n_pairs - nw) * (uint64_t)dd->n_alpha * dd->n_beta * dd->n_gamma;
+  }
+  return s;
 }
 
 extern "C" int slsht_forward(slsht_ctx* ctx, const slsht_desc* desc, const double* f_lm,

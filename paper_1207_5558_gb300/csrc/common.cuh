@@ -100,10 +100,11 @@ cudaError_t launch_x_from_h_f32(const double2* kc, const float2* H, int Lh, int 
                                 cudaStream_t st);
 
 // g[pair][a][j] = X_0 + sum_r (P_r cos(r alpha_a) - i M_r sin(r alpha_a)).
+// slots (nullable): per pair {output slot, mirror} as for launch_alpha_tc.
 cudaError_t launch_alpha_f64(const double2* Xs, const double2* csa, int Lh, int Na, int J,
-                             int npairs, double2* g, cudaStream_t st);
+                             int npairs, double2* g, const int2* slots, cudaStream_t st);
 cudaError_t launch_alpha_f32(const float2* Xs, const float2* csa, int Lh, int Na, int J,
-                             int npairs, float2* g, cudaStream_t st);
+                             int npairs, float2* g, const int2* slots, cudaStream_t st);
 
 // Inverse: partial sums then final scaling (deterministic order).  The
 // partial sums of one pair are nslab * inverse_col_blocks(Nb, Ng) entries.

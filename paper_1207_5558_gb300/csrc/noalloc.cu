@@ -168,12 +168,12 @@ extern "C" int slsht_forward_noalloc(const slsht_desc* desc, const double* f_lm,
       NA_CK(launch_betagamma_f64(kc, h_dev, (const double*)(base + o_dt), nullptr,
                                  (const double2*)(base + o_eg), Lh, Nb, Ng, np, (double2*)(base + o_X), st));
       NA_CK(launch_alpha_f64((const double2*)(base + o_X), (const double2*)(base + o_csa), Lh, Na, (int)J, np,
-                             (double2*)gdst, st));
+                             (double2*)gdst, nullptr, st));
     } else {
       NA_CK(launch_betagamma_f32(kc, h_dev, (const float*)(base + o_dt), nullptr,
                                  (const float2*)(base + o_eg), Lh, Nb, Ng, np, (float2*)(base + o_X), st));
       NA_CK(launch_alpha_f32((const float2*)(base + o_X), (const float2*)(base + o_csa), Lh, Na, (int)J, np,
-                             (float2*)gdst, st));
+                             (float2*)gdst, nullptr, st));
     }
   }
 #undef NA_CK

@@ -19,8 +19,11 @@ cudaError_t launch_betagamma_tc(const double2* kc, const double2* h, const float
 cudaError_t launch_xa_from_h(const double2* kc, const float2* H, int Lh, int Nb, int Ng, int npairs, void* xblob,
                              cudaStream_t st);
 // alpha stage on tcgen05: g[pair][a][j] complex64.
+// slots (nullable, device): per pair {output slot, mirror}, mirror = -1 or
+// 2 * slot of (l, -m) + (m & 1): that slot receives (-1)^m conj of the pair's
+// g (valid when f and h are real fields); without slots pair i writes slot i.
 cudaError_t launch_alpha_tc(const void* xblob, const void* etab, int Lh, int Na, int Nb, int Ng,
-                            int npairs, float2* g, int num_sms, cudaStream_t st);
+                            int npairs, float2* g, int num_sms, const int2* slots, cudaStream_t st);
 // Fused rotated-window producer + alpha stage (one persistent kernel): the A
 // operand of every (pair, 128-column tile) is built in shared memory from H
 // (launch_rotwin_f32, tiled layout of h_index) and the pair's coupling row
@@ -30,7 +33,8 @@ cudaError_t launch_alpha_tc(const void* xblob, const void* etab, int Lh, int Na,
 // bounded waits expire and it reports through the error word (tests the
 // timeout path; the output is not computed).
 cudaError_t launch_alpha_fused(const double2* kc, const float2* H, const void* etab, int Lh, int Na, int Nb,
-                               int Ng, int npairs, float2* g, int num_sms, int wait_test, cudaStream_t st);
+                               int Ng, int npairs, float2* g, int num_sms, int wait_test, const int2* slots,
+                               cudaStream_t st);
 // Device error word shared by the tensor-core kernels (allocated on first use).
 int* tc_error_word();
 // Non-zero (and cleared) if a tensor-core kernel gave up on a bounded wait

@@ -300,3 +300,28 @@ def test_bounded_wait_expiry_reports_and_context_recovers(ctx):
     ctx.stats()                                    # the error word was cleared
     g = _fw(ctx, Lf, Lh, grid, f, h, pairs, 1)
     assert rel(g, O.forward_coeff(f, h, Lf, Lh, pairs, grid)) < TOL32
+
+
+@pytest.mark.parametrize("prec,engine", [(0, 0), (1, 0), (1, 1), (1, 2)])
+def test_real_fields_mirror_pairs(ctx, prec, engine):
+    """SLSHT_OPT_REAL_FIELDS: for real f and h, g(l, -m) = (-1)^m conj g(l, m)
+    (Sec. IV-B; pin (iv) of the oracle tests), so only one of each mirrored
+    pair is computed and the alpha stage writes both.  Against the full
+    computation and the oracle, with unmatched pairs and m = 0 in the list."""
+    import paper_1207_5558_gb300 as pkg
+    Lf, Lh, grid = 14, 6, (131, 14, 11)
+    f = synth.signal_powerlaw(Lf, 91)
+    h = synth.signal_cn_real(Lh, 92)
+    pairs = np.concatenate([synth.pairs_bands([3, 13]), np.array([[9, 4], [18, -5]], dtype=np.int32)])
+    ref = O.forward_coeff(f, h, Lf, Lh, pairs, grid)
+    ctx.set_option(pkg.SLSHT_OPT_ALPHA_ENGINE, engine)
+    try:
+        full = _fw(ctx, Lf, Lh, grid, f, h, pairs, prec)
+        ctx.set_option(pkg.SLSHT_OPT_REAL_FIELDS, 1)
+        half = _fw(ctx, Lf, Lh, grid, f, h, pairs, prec)
+    finally:
+        ctx.set_option(pkg.SLSHT_OPT_REAL_FIELDS, 0)
+        ctx.set_option(pkg.SLSHT_OPT_ALPHA_ENGINE, 0)
+    tol = TOL64 if prec == 0 else TOL32
+    assert rel(half, ref) < tol
+    assert rel(half, full) < (1e-13 if prec == 0 else 2e-6)
