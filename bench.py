@@ -157,6 +157,26 @@ def traffic_record(kernel):
     return d if d.get("source_sha256_16") == h else None
 
 
+def alpha_fp64_cost(Lh, Na):
+    """FP64 work of the CUDA-core alpha stage per output sample, for the form
+    the library picks (the same rule as alpha_split_factor in csrc/alpha.cu):
+    (P, FP64 instructions, flops, description)."""
+    K = 2 * Lh - 1
+    direct = 4.0 * (Lh - 1) + 2.0
+    best, cost = 0, direct
+    for P in (9, 7, 5, 3):
+        if Na % P == 0:
+            c = 4.0 * K / P + P + 3.0
+            if c < cost:
+                best, cost = P, c
+    if best == 0:
+        return 0, direct, 2 * direct, "direct sum, +-q paired"
+    H = (best - 1) // 2
+    fma = 4 * K + 4 * H * H
+    adds = 10 * H
+    return best, (fma + adds) / best, (2 * fma + adds) / best, "split DFT, a = Q s + t with P = %d" % best
+
+
 def reduce_max(value, dist):
     """Max over ranks of a host float (the job time is the slowest rank's)."""
     if dist is None:
@@ -496,13 +516,19 @@ def main():
         rel32 = float(torch.linalg.vector_norm(a32 - a64) / torch.linalg.vector_norm(a64))
         inv64 = inverse_leg(0, g64, 2)
         fp64_alpha_ms = st64["ms"]["alpha"]
-        fp64_alpha_tflops = (samples_step * args.fp64_steps * (8 * (Lh - 1) + 4)) / (fp64_alpha_ms / 1e3) / 1e12
+        P, instr, flops, form = alpha_fp64_cost(Lh, grid[0])
+        alpha_rate = samples_step * args.fp64_steps / (fp64_alpha_ms / 1e3)
         fp64 = {"value": value64, "unit": UNIT, "steps": args.fp64_steps,
                 "ms_per_step": ms64 / args.fp64_steps,
                 "stage_ms_per_step": {k: v / args.fp64_steps for k, v in st64["ms"].items()},
-                "alpha_fp64_tflops": fp64_alpha_tflops,
-                "alpha_fp64_frac_of_nominal_1.25TF": fp64_alpha_tflops / 1.25,
-                "note": "FP64 alpha stage is FP64-pipe bound; stage times overlap (two streams)",
+                "alpha_form": form,
+                "alpha_fp64_instructions_per_sample": instr,
+                "alpha_fp64_flops_per_sample": flops,
+                "alpha_fp64_tflops": alpha_rate * flops / 1e12,
+                "alpha_fp64_pipe_frac": alpha_rate * instr / 0.625e12,
+                "note": "FP64 alpha stage is FP64-pipe bound: the fraction is FP64 instructions (FMA or add) "
+                        "issued per second over the 0.625e12/s of a 1.25 TFLOP/s FMA pipe; stage times "
+                        "overlap (two streams)",
                 "inverse": inv64}
         del g64, a64
         fp64["real_fields_workload2"] = real_fields_leg()

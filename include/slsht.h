@@ -235,12 +235,15 @@ int slsht_get_stats(slsht_ctx* ctx, slsht_stats* out, int reset);
  *                            Delta (separation of variables, Sec. IV-B remark);
  *                         2: factoring of rotations: C tensor
  *                            (Eq. constant_alternative_formulation) + DFT in q''.
- *  SLSHT_OPT_ALPHA_ENGINE 1: CUDA cores; 2: tcgen05 tensor cores fed by a
- *                            separate producer kernel; 3: one fused kernel
- *                            (producer warps build the tensor-core operand in
- *                            shared memory; route 1 only).  Tensor cores:
- *                            FP32_BULK and L_h <= 16 only.  0 (default): 3
- *                            where it applies, else 2, else 1.
+ *  SLSHT_OPT_ALPHA_ENGINE 1: CUDA cores (the alpha index split as
+ *                            a = Q s + t with a small odd factor P of n_alpha
+ *                            when that saves work, else the direct sum);
+ *                            2: tcgen05 tensor cores fed by a separate
+ *                            producer kernel; 3: one fused kernel (producer
+ *                            warps build the tensor-core operand in shared
+ *                            memory; route 1 only); 4: CUDA cores, direct sum
+ *                            only.  Tensor cores: FP32_BULK and L_h <= 16 only.
+ *                            0 (default): 3 where it applies, else 2, else 1.
  *  SLSHT_OPT_CHUNK_PAIRS  pairs per launch chunk (scratch size).
  *  SLSHT_OPT_GAUNT_TABLE  the 3j part of the coupling (Sec. III-B: T through
  *                            Wigner-3j symbols) depends only on (L_f, L_h, the

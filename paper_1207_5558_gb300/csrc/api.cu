@@ -513,7 +513,7 @@ extern "C" int slsht_set_option(slsht_ctx* c, int option, int64_t v) {
       c->opt_beta_route = (int)v;
       return SLSHT_OK;
     case SLSHT_OPT_ALPHA_ENGINE:
-      if (v < 0 || v > 3) return SLSHT_E_ARG;
+      if (v < 0 || v > 4) return SLSHT_E_ARG;
       c->opt_alpha_engine = (int)v;
       return SLSHT_OK;
     case SLSHT_OPT_CHUNK_PAIRS:
@@ -557,7 +557,7 @@ static int stage_input(slsht_ctx* ctx, Workspace& w, void** buf, size_t* cap, co
 static bool use_tensor_cores(slsht_ctx* ctx, const slsht_desc* d) {
   if (d->prec != SLSHT_FP32_BULK) return false;
   if (!tc_supported(d->L_h, d->n_alpha)) return false;
-  if (ctx->opt_alpha_engine == 1) return false;
+  if (ctx->opt_alpha_engine == 1 || ctx->opt_alpha_engine == 4) return false;
   return true;   // default for FP32_BULK when supported
 }
 
@@ -615,6 +615,9 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
   // rotated-window route on the tensor cores: producer and alpha stage fused
   // into one kernel unless the separate producer kernel was asked for
   const bool fused = tc && route == 1 && Lh <= 16 && engine != 2;
+  // CUDA-core alpha stage: split DFT over the alpha index when Na has a small
+  // odd factor that saves work (SLSHT_OPT_ALPHA_ENGINE 4 forces the direct sum)
+  const bool split = !tc && engine != 4 && alpha_split_factor(Lh, Na) > 0;
   // tables
   const double* D = nullptr;
   const void* dt = nullptr;
@@ -627,6 +630,7 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
     if (route == 1) CKS(get_dtab(ctx, Lh, Nb, d->prec, st, &dt));
     CKS(get_phase(ctx, Ng, K, -(Lh - 1), d->prec, st, &eg));
     if (tc) CKS(get_etab(ctx, Na, Lh, st, &etab));
+    else if (split) CKS(get_phase(ctx, Na, K, -(Lh - 1), d->prec, st, &csa));   // twiddles of the split DFT
     else CKS(get_phase(ctx, Na, Lh, 0, d->prec, st, &csa));
   }
   // inputs
@@ -782,10 +786,16 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
              launch_alpha_tc(X, etab, Lh, Na, Nb, Ng, np, (float2*)gdst, ctx->num_sms, sl, st));
     } else if (f64) {
       LAUNCH(SLSHT_STAGE_ALPHA, st,
-             launch_alpha_f64((const double2*)X, (const double2*)csa, Lh, Na, (int)J, np, (double2*)gdst, sl, st));
+             split ? launch_alpha_split_f64((const double2*)X, (const double2*)csa, Lh, Na, (int)J, np,
+                                            (double2*)gdst, sl, st)
+                   : launch_alpha_f64((const double2*)X, (const double2*)csa, Lh, Na, (int)J, np, (double2*)gdst, sl,
+                                      st));
     } else {
       LAUNCH(SLSHT_STAGE_ALPHA, st,
-             launch_alpha_f32((const float2*)X, (const float2*)csa, Lh, Na, (int)J, np, (float2*)gdst, sl, st));
+             split ? launch_alpha_split_f32((const float2*)X, (const float2*)csa, Lh, Na, (int)J, np,
+                                            (float2*)gdst, sl, st)
+                   : launch_alpha_f32((const float2*)X, (const float2*)csa, Lh, Na, (int)J, np, (float2*)gdst, sl,
+                                      st));
     }
     if (!fused) CK(cudaEventRecord(w.x_free[ci & 1], st));
     if (host_out) {

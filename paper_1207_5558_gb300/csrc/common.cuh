@@ -106,6 +106,15 @@ cudaError_t launch_alpha_f64(const double2* Xs, const double2* csa, int Lh, int 
 cudaError_t launch_alpha_f32(const float2* Xs, const float2* csa, int Lh, int Na, int J,
                              int npairs, float2* g, const int2* slots, cudaStream_t st);
 
+// The alpha sum as a split DFT (Na = P Q, P in {3,5,7,9}); tw[t * (2Lh-1) +
+// q + Lh - 1] = (cos, sin)(2 pi q t / Na).  alpha_split_factor returns the P
+// used for (Lh, Na), 0 when the direct sum is cheaper or no factor divides Na.
+int alpha_split_factor(int Lh, int Na);
+cudaError_t launch_alpha_split_f64(const double2* Xs, const double2* tw, int Lh, int Na, int J, int npairs,
+                                   double2* g, const int2* slots, cudaStream_t st);
+cudaError_t launch_alpha_split_f32(const float2* Xs, const float2* tw, int Lh, int Na, int J, int npairs,
+                                   float2* g, const int2* slots, cudaStream_t st);
+
 // Inverse: partial sums then final scaling (deterministic order).  The
 // partial sums of one pair are nslab * inverse_col_blocks(Nb, Ng) entries.
 int inverse_col_blocks(int Nb, int Ng);

@@ -325,3 +325,34 @@ def test_real_fields_mirror_pairs(ctx, prec, engine):
     tol = TOL64 if prec == 0 else TOL32
     assert rel(half, ref) < tol
     assert rel(half, full) < (1e-13 if prec == 0 else 2e-6)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("Na", [15, 33, 45, 105, 511])
+def test_split_dft_alpha_stage(ctx, prec, Na):
+    """The CUDA-core alpha stage as a split DFT over a = Q s + t (P = 3, 5, 7
+    or 9 dividing N_alpha) against the direct sum (engine 4) and the oracle,
+    with mirrored pairs under the real-field option as well."""
+    import paper_1207_5558_gb300 as pkg
+    Lf, Lh = 12, 12
+    grid = (Na, 7, 9)
+    f = synth.signal_powerlaw(Lf, 100 + Na)
+    h = synth.signal_cn_real(Lh, 200 + Na)
+    pairs = synth.pairs_bands([4, 15])
+    ref = O.forward_coeff(f, h, Lf, Lh, pairs, grid)
+    tol = TOL64 if prec == 0 else TOL32
+    try:
+        ctx.set_option(pkg.SLSHT_OPT_ALPHA_ENGINE, 1)
+        split = _fw(ctx, Lf, Lh, grid, f, h, pairs, prec)
+        ctx.set_option(pkg.SLSHT_OPT_REAL_FIELDS, 1)
+        split_mirror = _fw(ctx, Lf, Lh, grid, f, h, pairs, prec)
+        ctx.set_option(pkg.SLSHT_OPT_REAL_FIELDS, 0)
+        ctx.set_option(pkg.SLSHT_OPT_ALPHA_ENGINE, 4)
+        direct = _fw(ctx, Lf, Lh, grid, f, h, pairs, prec)
+    finally:
+        ctx.set_option(pkg.SLSHT_OPT_REAL_FIELDS, 0)
+        ctx.set_option(pkg.SLSHT_OPT_ALPHA_ENGINE, 0)
+    assert rel(split, ref) < tol
+    assert rel(split_mirror, ref) < tol
+    assert rel(direct, ref) < tol
+    assert rel(split, direct) < (1e-13 if prec == 0 else 2e-6)
