@@ -478,6 +478,42 @@ def main():
         del g2
         return out
 
+    def windows_leg(nwin=4):
+        """F4 of the scope table: map 0 of workload 3 analysed with nwin
+        windows (CN(0,1)/(l+1), seeds of the other maps), FP32_BULK: one
+        slsht_forward_windows call (coupling once) against nwin slsht_forward
+        calls, with the Gaunt table off so that the coupling is the 3j chains
+        of every call, and with the default table."""
+        f0 = dev_inputs[0][0]
+        pd = dev_inputs[0][2]
+        n = pd.shape[0]
+        hs = torch.stack([dev_inputs[i % len(dev_inputs)][1] for i in range(nwin)])
+        gw = torch.empty((nwin, n) + grid, dtype=torch.complex64, device="cuda")
+        desc = pkg.make_desc(Lf, Lh, grid, 1)
+        out = {"windows": nwin, "pairs": int(n)}
+        for tag, gt in (("gaunt_table_off", 2), ("gaunt_table_default", 0)):
+            ctx.set_option(pkg.SLSHT_OPT_GAUNT_TABLE, gt)
+            for name in ("separate_calls", "forward_windows"):
+                def run():
+                    if name == "forward_windows":
+                        pkg.slsht_forward_windows(ctx.h, desc, f0, nwin, hs, pd, n, gw, stream)
+                    else:
+                        for i in range(nwin):
+                            pkg.slsht_forward(ctx.h, desc, f0, hs[i], pd, n, gw[i], stream)
+                run()
+                barrier()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(2):
+                    run()
+                e1.record(stream)
+                barrier()
+                out.setdefault(tag, {})[name + "_ms"] = e0.elapsed_time(e1) / 2
+            out[tag]["speedup"] = out[tag]["separate_calls_ms"] / out[tag]["forward_windows_ms"]
+        ctx.set_option(pkg.SLSHT_OPT_GAUNT_TABLE, 0)
+        del gw
+        return out
+
     # ---------------- FP32_BULK headline
     g32 = torch.empty((npairs_map,) + grid, dtype=torch.complex64, device="cuda")
     ms32, st32, clk = timed(1, g32, args.steps, args.warmup, ClockSampler(local))
@@ -500,6 +536,7 @@ def main():
             "step_frac": (alpha_bytes / (ms32 / 1e3) / 1e9) / pk["hbm_gbs"]}
     # relative L2 of the FP32 path against the FP64 path on the last map, sampled pairs
     inv32 = inverse_leg(1, g32, 5)
+    wins = None
     sel = torch.tensor([0, 200, 500, npairs_map - 1], device="cuda")
     a32 = g32[sel].to(torch.complex128).clone()
     del g32
@@ -534,6 +571,8 @@ def main():
         fp64["real_fields_workload2"] = real_fields_leg()
     del a32
     torch.cuda.empty_cache()
+    if args.fp64_steps > 0:
+        wins = windows_leg()
 
     # ---------------- e2e through the C ABI with host buffers
     e2e = None
@@ -595,6 +634,7 @@ def main():
             "fp32_over_fp64_speedup": (value / fp64["value"]) if fp64 else None,
             "rel_l2_fp32_vs_fp64_sampled": rel32,
             "inverse_fp32": inv32,
+            "multi_window": wins,
             "serve": serve,
         }
         print(json.dumps(line), flush=True)

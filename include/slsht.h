@@ -136,6 +136,18 @@ int slsht_forward(slsht_ctx* ctx, const slsht_desc* desc,
                   const int32_t* lm, int32_t n_pairs,
                   void* g_out, void* stream);
 
+/* g for n_windows windows over the same signal and pair list (Sec. IV-B,
+ * the remark on analysing one signal with several windows): the coupling
+ * k_lm (window independent) is formed once; everything per window (the
+ * rotated window H and the alpha stage) runs for each.  Equal to n_windows
+ * slsht_forward calls with the same f and lm.
+ *   h_lms  complex128 [n_windows][L_h*L_h]          (host or device)
+ *   g_out  [n_windows][n_pairs][n_alpha][n_beta][n_gamma], as slsht_forward.
+ * Other arguments and errors as slsht_forward; n_windows < 0 is SLSHT_E_ARG,
+ * 0 does nothing. */
+int slsht_forward_windows(slsht_ctx* ctx, const slsht_desc* desc, const double* f_lm, int32_t n_windows,
+                          const double* h_lms, const int32_t* lm, int32_t n_pairs, void* g_out, void* stream);
+
 /* ---------------------------------------------------------------- inverse */
 
 /* f_lm for every listed pair from sampled g (Eq. inversion_1, inversion_2,

@@ -15,7 +15,8 @@ from ._abi import (SLSHT_FP32_BULK, SLSHT_FP64, SLSHT_OPT_ALPHA_ENGINE,  # noqa:
                    slsht_desc, slsht_stats)
 
 __all__ = ["Context", "make_desc", "SLSHT_FP64", "SLSHT_FP32_BULK", "SlshtError",
-           "slsht_create", "slsht_destroy", "slsht_forward", "slsht_forward_noalloc", "slsht_inverse", "slsht_submit",
+           "slsht_create", "slsht_destroy", "slsht_forward", "slsht_forward_noalloc", "slsht_forward_windows",
+           "slsht_inverse", "slsht_submit",
            "slsht_poll", "slsht_drain", "slsht_strerror", "slsht_check_args", "slsht_profile",
            "slsht_get_stats", "slsht_set_option", "slsht_mem_used", "slsht_version"]
 
@@ -50,6 +51,13 @@ def slsht_forward(ctx, desc, f_lm, h_lm, lm, n_pairs, g_out, stream=None):
     return _abi.check(_abi.load().slsht_forward(ctx, ctypes.byref(desc), _abi.ptr(f_lm), _abi.ptr(h_lm),
                                                 _abi.ptr(lm), int(n_pairs), _abi.ptr(g_out),
                                                 _stream(stream)), "slsht_forward")
+
+
+def slsht_forward_windows(ctx, desc, f_lm, n_windows, h_lms, lm, n_pairs, g_out, stream=None):
+    return _abi.check(_abi.load().slsht_forward_windows(ctx, ctypes.byref(desc), _abi.ptr(f_lm), int(n_windows),
+                                                        _abi.ptr(h_lms), _abi.ptr(lm), int(n_pairs),
+                                                        _abi.ptr(g_out), _stream(stream)),
+                      "slsht_forward_windows")
 
 
 def slsht_inverse(ctx, desc, g_in, h00, lm, n_pairs, f_out, stream=None):
@@ -152,6 +160,21 @@ class Context:
         h = _as_c128(h)
         slsht_forward(self.h, make_desc(L_f, L_h, grid, prec), f, h, lm, n, g_out, stream)
         _ = np
+        return g_out
+
+    def forward_windows(self, L_f, L_h, grid, f, hs, lm, prec=SLSHT_FP64, g_out=None, stream=None):
+        """g for several windows hs ([n_windows, L_h^2] complex128) over one
+        signal: the coupling is formed once.  Returns g_out
+        [n_windows, n, Na, Nb, Ng] (a new device tensor when not given)."""
+        import torch
+        lm = _as_pairs(lm)
+        n = int(lm.shape[0])
+        hs = _as_c128(hs)
+        nw = int(hs.shape[0])
+        if g_out is None:
+            dt = torch.complex128 if prec == SLSHT_FP64 else torch.complex64
+            g_out = torch.empty((nw, n) + tuple(grid), dtype=dt, device="cuda:%d" % self.device)
+        slsht_forward_windows(self.h, make_desc(L_f, L_h, grid, prec), _as_c128(f), nw, hs, lm, n, g_out, stream)
         return g_out
 
     def inverse(self, L_f, L_h, grid, g, h00, lm, prec=SLSHT_FP64, f_out=None, stream=None):

@@ -592,7 +592,7 @@ static void mirror_work(const int32_t* lm, int32_t n, std::vector<int32_t>* out)
 // launch_alpha_tc); g_out must then be device memory.
 static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const double* f_lm,
                         const double* h_lm, const int32_t* lm, const int32_t* lm_host, int32_t n_pairs,
-                        void* g_out, cudaStream_t st, const int2* slots) {
+                        void* g_out, cudaStream_t st, const int2* slots, bool reuse_k) {
   const int Lf = d->L_f, Lh = d->L_h, Na = d->n_alpha, Nb = d->n_beta, Ng = d->n_gamma;
   const int K = 2 * Lh - 1;
   const bool f64 = d->prec == SLSHT_FP64;
@@ -683,7 +683,9 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
   // pair list (signal independent) and only the gather-sum runs per call.
   const size_t gt_bytes = gaunt_table_bytes(Lh, n_pairs);
   const bool use_gt = gt_opt == 1 || (gt_opt == 0 && gt_bytes <= ((size_t)256 << 20));
-  if (use_gt) {
+  if (reuse_k) {
+    // k of this signal and pair list is still in w.kc (multi-window calls)
+  } else if (use_gt) {
     const bool hit = w.gt_valid && w.gt_Lf == Lf && w.gt_Lh == Lh && w.gt_lm.size() == 2 * (size_t)n_pairs &&
                      std::memcmp(w.gt_lm.data(), lm_host, sizeof(int32_t) * 2 * (size_t)n_pairs) == 0;
     if (!hit) {
@@ -829,18 +831,18 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
 // alpha stage stores both outputs.  Device outputs only.
 static int forward_impl(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const double* f_lm,
                         const double* h_lm, const int32_t* lm, const int32_t* lm_host, int32_t n_pairs,
-                        void* g_out, cudaStream_t st) {
+                        void* g_out, cudaStream_t st, bool reuse_k = false) {
   int real;
   {
     std::lock_guard<std::mutex> g(ctx->mu);
     real = ctx->opt_real_fields;
   }
   if (!real || !is_device_ptr(g_out))
-    return forward_core(ctx, w, d, f_lm, h_lm, lm, lm_host, n_pairs, g_out, st, nullptr);
+    return forward_core(ctx, w, d, f_lm, h_lm, lm, lm_host, n_pairs, g_out, st, nullptr, reuse_k);
   std::vector<int32_t> pw;
   mirror_work(lm_host, n_pairs, &pw);
   const int32_t nw = (int32_t)(pw.size() / 2);
-  if (nw == n_pairs) return forward_core(ctx, w, d, f_lm, h_lm, lm, lm_host, n_pairs, g_out, st, nullptr);
+  if (nw == n_pairs) return forward_core(ctx, w, d, f_lm, h_lm, lm, lm_host, n_pairs, g_out, st, nullptr, reuse_k);
   w.rf_lm.resize(2 * (size_t)nw);
   w.rf_slots.resize(2 * (size_t)nw);
   for (int32_t k = 0; k < nw; ++k) {
@@ -854,7 +856,7 @@ static int forward_impl(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
   CKS(ws_reserve(ctx, w, &w.rfs, &w.rfs_cap, sizeof(int32_t) * w.rf_slots.size()));
   CK(cudaMemcpyAsync(w.rfs, w.rf_slots.data(), sizeof(int32_t) * w.rf_slots.size(), cudaMemcpyHostToDevice, st));
   const int s = forward_core(ctx, w, d, f_lm, h_lm, w.rf_lm.data(), w.rf_lm.data(), nw, g_out, st,
-                             (const int2*)w.rfs);
+                             (const int2*)w.rfs, reuse_k);
   if (s == SLSHT_OK) {
     std::lock_guard<std::mutex> g(ctx->mu);
     const slsht_desc* dd = d;
@@ -884,6 +886,34 @@ extern "C" int slsht_forward(slsht_ctx* ctx, const slsht_desc* desc, const doubl
   CKS(check_pairs(desc, lmv, n_pairs));
   std::lock_guard<std::mutex> serial(ctx->sync_mu);
   return forward_impl(ctx, ctx->sync_ws, desc, f_lm, h_lm, lm, lmv, n_pairs, g_out, (cudaStream_t)stream);
+}
+
+extern "C" int slsht_forward_windows(slsht_ctx* ctx, const slsht_desc* desc, const double* f_lm,
+                                     int32_t n_windows, const double* h_lms, const int32_t* lm, int32_t n_pairs,
+                                     void* g_out, void* stream) {
+  if (!ctx) return SLSHT_E_ARG;
+  CKS(check_desc(desc));
+  if (n_pairs < 0 || n_windows < 0) return SLSHT_E_ARG;
+  if (n_pairs == 0 || n_windows == 0) return SLSHT_OK;
+  if (!f_lm || !h_lms || !lm || !g_out) return SLSHT_E_ARG;
+  if (((uintptr_t)g_out) & 7) return SLSHT_E_ARG;
+  DeviceGuard g(ctx->device);
+  std::vector<int32_t> lm_host;
+  const int32_t* lmv = lm;
+  if (is_device_ptr(lm)) {
+    lm_host.resize(2 * (size_t)n_pairs);
+    CK(cudaMemcpy(lm_host.data(), lm, sizeof(int32_t) * 2 * (size_t)n_pairs, cudaMemcpyDeviceToHost));
+    lmv = lm_host.data();
+  }
+  CKS(check_pairs(desc, lmv, n_pairs));
+  const size_t nh = 2 * (size_t)desc->L_h * desc->L_h;                  // doubles per window
+  const size_t per_window = (size_t)n_pairs * desc->n_alpha * desc->n_beta * desc->n_gamma *
+                            (desc->prec == SLSHT_FP64 ? sizeof(double2) : sizeof(float2));
+  std::lock_guard<std::mutex> serial(ctx->sync_mu);
+  for (int32_t wi = 0; wi < n_windows; ++wi)
+    CKS(forward_impl(ctx, ctx->sync_ws, desc, f_lm, h_lms + nh * wi, lm, lmv, n_pairs,
+                     (char*)g_out + per_window * wi, (cudaStream_t)stream, wi > 0));
+  return SLSHT_OK;
 }
 
 // ---------------------------------------------------------------- inverse

@@ -356,3 +356,19 @@ def test_split_dft_alpha_stage(ctx, prec, Na):
     assert rel(split_mirror, ref) < tol
     assert rel(direct, ref) < tol
     assert rel(split, direct) < (1e-13 if prec == 0 else 2e-6)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_forward_windows_reuses_coupling(ctx, prec):
+    """slsht_forward_windows (Sec. IV-B, several windows over one signal):
+    equal to one slsht_forward per window, and to the oracle."""
+    Lf, Lh, grid = 16, 7, (61, 16, 13)
+    f = synth.signal_powerlaw(Lf, 301)
+    hs = np.stack([synth.window_cn(Lh, 302 + i, decay=1.0) for i in range(3)])
+    pairs = synth.pairs_bands([2, 11, 19])
+    g = ctx.forward_windows(Lf, Lh, grid, f, hs, pairs, prec=prec).cpu().numpy()
+    tol = TOL64 if prec == 0 else TOL32
+    for i in range(3):
+        single = _fw(ctx, Lf, Lh, grid, f, hs[i], pairs, prec)
+        assert np.array_equal(g[i], single)
+    assert rel(g[1], O.forward_coeff(f, hs[1], Lf, Lh, pairs, grid)) < tol
