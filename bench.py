@@ -514,6 +514,25 @@ def main():
         del gw
         return out
 
+    def window_leg():
+        """F3 of the scope table: the concentrated window of the 8 x 3 degree
+        ellipse (workload 5's region) generated on the device at L_h = 32 and
+        64, and by the host generator of the workloads at L_h = 32."""
+        from synth.window import ellipse_from_axes, window_ellipse
+        reg = ellipse_from_axes(8.0, 3.0)
+        out = {}
+        for L in (32, 64):
+            ctx.window_ellipse(L, *reg)                       # warm-up (cuBLAS, tables)
+            t0 = time.perf_counter()
+            _, lam = ctx.window_ellipse(L, *reg)
+            out["gpu_L%d_s" % L] = time.perf_counter() - t0
+            out["concentration_L%d" % L] = lam
+        t0 = time.perf_counter()
+        window_ellipse(32, *reg)
+        out["host_generator_L32_s"] = time.perf_counter() - t0
+        out["speedup_L32"] = out["host_generator_L32_s"] / out["gpu_L32_s"]
+        return out
+
     # ---------------- FP32_BULK headline
     g32 = torch.empty((npairs_map,) + grid, dtype=torch.complex64, device="cuda")
     ms32, st32, clk = timed(1, g32, args.steps, args.warmup, ClockSampler(local))
@@ -571,8 +590,10 @@ def main():
         fp64["real_fields_workload2"] = real_fields_leg()
     del a32
     torch.cuda.empty_cache()
+    win_gen = None
     if args.fp64_steps > 0:
         wins = windows_leg()
+        win_gen = window_leg()
 
     # ---------------- e2e through the C ABI with host buffers
     e2e = None
@@ -635,6 +656,7 @@ def main():
             "rel_l2_fp32_vs_fp64_sampled": rel32,
             "inverse_fp32": inv32,
             "multi_window": wins,
+            "window_generator": win_gen,
             "serve": serve,
         }
         print(json.dumps(line), flush=True)

@@ -117,6 +117,31 @@ int slsht_create(slsht_ctx** ctx, int device, size_t mem_budget_bytes);
  * NULL is a no-op. */
 void slsht_destroy(slsht_ctx* ctx);
 
+/* ---------------------------------------------------------------- window */
+
+/* The band-limited window of maximal energy concentration in the elliptical
+ * region R(theta_c, a) of Sec. III-D (Eq. region_def: points whose
+ * great-circle distances to the foci (theta_c, 0) and (theta_c, pi) add up
+ * to at most 2a), computed on the device: the concentration matrix over the
+ * real even harmonics (the region is symmetric under phi -> -phi) by
+ * quadrature ring by ring, then its top eigenpair by block subspace
+ * iteration.
+ *   L            exclusive band limit, 1..256
+ *   theta_c, a   focal colatitude and semi-major arc, radians,
+ *                0 <= theta_c <= a < pi/2
+ *   n_phi, n_theta  quadrature longitudes / Gauss-Legendre nodes per ring
+ *                (0: 8L+64 and 2L+24)
+ *   h_out        complex128 [L*L] (host or device), flat index l*l+l+m:
+ *                unit energy, real-valued, symmetric under phi -> -phi,
+ *                h_0^0 > 0
+ *   concentration  optional host double: the eigenvalue (fraction of the
+ *                window's energy inside R)
+ * Synchronous.  Errors: SLSHT_E_ARG, SLSHT_E_NOMEM (context budget: the
+ * quadrature matrix is n_phi*n_theta*L(L+1)/2 doubles), SLSHT_E_TIMEOUT (the
+ * iteration did not converge), SLSHT_E_CUDA. */
+int slsht_window_ellipse(slsht_ctx* ctx, int32_t L, double theta_c, double a, int32_t n_phi, int32_t n_theta,
+                         double* h_out, double* concentration, void* stream);
+
 /* ---------------------------------------------------------------- forward */
 
 /* g(rho; l, m) for every listed pair on the desc's grid (Definition 1,

@@ -16,6 +16,7 @@ from ._abi import (SLSHT_FP32_BULK, SLSHT_FP64, SLSHT_OPT_ALPHA_ENGINE,  # noqa:
 
 __all__ = ["Context", "make_desc", "SLSHT_FP64", "SLSHT_FP32_BULK", "SlshtError",
            "slsht_create", "slsht_destroy", "slsht_forward", "slsht_forward_noalloc", "slsht_forward_windows",
+           "slsht_window_ellipse",
            "slsht_inverse", "slsht_submit",
            "slsht_poll", "slsht_drain", "slsht_strerror", "slsht_check_args", "slsht_profile",
            "slsht_get_stats", "slsht_set_option", "slsht_mem_used", "slsht_version"]
@@ -58,6 +59,16 @@ def slsht_forward_windows(ctx, desc, f_lm, n_windows, h_lms, lm, n_pairs, g_out,
                                                         _abi.ptr(h_lms), _abi.ptr(lm), int(n_pairs),
                                                         _abi.ptr(g_out), _stream(stream)),
                       "slsht_forward_windows")
+
+
+def slsht_window_ellipse(ctx, L, theta_c, a, h_out, n_phi=0, n_theta=0, stream=None):
+    """Concentrated window of R(theta_c, a) into h_out (complex128 [L*L]);
+    returns the concentration."""
+    lam = ctypes.c_double()
+    _abi.check(_abi.load().slsht_window_ellipse(ctx, int(L), float(theta_c), float(a), int(n_phi), int(n_theta),
+                                                _abi.ptr(h_out), ctypes.byref(lam), _stream(stream)),
+               "slsht_window_ellipse")
+    return lam.value
 
 
 def slsht_inverse(ctx, desc, g_in, h00, lm, n_pairs, f_out, stream=None):
@@ -176,6 +187,14 @@ class Context:
             g_out = torch.empty((nw, n) + tuple(grid), dtype=dt, device="cuda:%d" % self.device)
         slsht_forward_windows(self.h, make_desc(L_f, L_h, grid, prec), _as_c128(f), nw, hs, lm, n, g_out, stream)
         return g_out
+
+    def window_ellipse(self, L, theta_c, a, n_phi=0, n_theta=0):
+        """(h, concentration): the most concentrated window of R(theta_c, a)
+        at band limit L, computed on the device (h: host complex128 [L*L])."""
+        import numpy as np
+        h = np.zeros(L * L, dtype=np.complex128)
+        lam = slsht_window_ellipse(self.h, L, theta_c, a, h, n_phi, n_theta)
+        return h, lam
 
     def inverse(self, L_f, L_h, grid, g, h00, lm, prec=SLSHT_FP64, f_out=None, stream=None):
         """f_lm for each pair from g (device tensor).  Returns a host numpy

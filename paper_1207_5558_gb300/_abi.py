@@ -64,6 +64,8 @@ def load(path=LIB_PATH):
         "slsht_inverse": (ctypes.c_int, [vp, ctypes.POINTER(slsht_desc), vp, vp, vp, i32, vp, vp]),
         "slsht_forward_noalloc": (ctypes.c_int, [ctypes.POINTER(slsht_desc), vp, vp, vp, i32, vp, vp]),
         "slsht_forward_windows": (ctypes.c_int, [vp, ctypes.POINTER(slsht_desc), vp, i32, vp, vp, i32, vp, vp]),
+        "slsht_window_ellipse": (ctypes.c_int, [vp, i32, ctypes.c_double, ctypes.c_double, i32, i32, vp,
+                                                ctypes.POINTER(ctypes.c_double), vp]),
         "slsht_submit": (ctypes.c_int, [vp, ctypes.POINTER(slsht_desc), vp, vp, vp, i32, vp,
                                         ctypes.POINTER(u64)]),
         "slsht_poll": (ctypes.c_int, [vp, u64]),

@@ -61,7 +61,7 @@ def build(verbose=False, force=False):
             if log.strip():
                 print(os.path.basename(o), "\n", log, file=sys.stderr)
     tmp = LIB + ".tmp"
-    cmd = [_nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"]
+    cmd = [_nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcublas", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))

@@ -916,6 +916,40 @@ extern "C" int slsht_forward_windows(slsht_ctx* ctx, const slsht_desc* desc, con
   return SLSHT_OK;
 }
 
+// ---------------------------------------------------------------- window generator
+int window_ellipse_run(int L, double theta_c, double a, int n_phi, int n_theta, void* (*alloc)(size_t, void*),
+                       void (*release)(void*, size_t, void*), void* actx, cudaStream_t st, std::vector<double>& h,
+                       double* lambda_out, char* errbuf, size_t errlen);
+
+static void* win_alloc(size_t bytes, void* c) {
+  void* p = nullptr;
+  return ctx_alloc((slsht_ctx*)c, bytes, &p) == SLSHT_OK ? p : nullptr;
+}
+static void win_release(void* p, size_t bytes, void* c) { ctx_free((slsht_ctx*)c, p, bytes); }
+
+extern "C" int slsht_window_ellipse(slsht_ctx* ctx, int32_t L, double theta_c, double a, int32_t n_phi,
+                                    int32_t n_theta, double* h_out, double* concentration, void* stream) {
+  if (!ctx || !h_out) return SLSHT_E_ARG;
+  DeviceGuard g(ctx->device);
+  std::lock_guard<std::mutex> serial(ctx->sync_mu);
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<double> h;
+  char err[160] = {0};
+  const int s = window_ellipse_run(L, theta_c, a, n_phi, n_theta, win_alloc, win_release, ctx, st, h, concentration,
+                                   err, sizeof(err));
+  if (s != SLSHT_OK) {
+    if (err[0]) slsht_record_error_text(err);
+    return s;
+  }
+  if (is_device_ptr(h_out)) {
+    CK(cudaMemcpyAsync(h_out, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+  } else {
+    std::memcpy(h_out, h.data(), sizeof(double) * h.size());
+  }
+  return SLSHT_OK;
+}
+
 // ---------------------------------------------------------------- inverse
 extern "C" int slsht_inverse(slsht_ctx* ctx, const slsht_desc* desc, const void* g_in,
                              const double h00[2], const int32_t* lm, int32_t n_pairs, double* f_out,
