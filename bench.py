@@ -533,6 +533,40 @@ def main():
         out["speedup_L32"] = out["host_generator_L32_s"] / out["gpu_L32_s"]
         return out
 
+    def coupling_leg():
+        """F1 of the scope table: time of the coupling stage (events on its
+        stream) by the 3j chains (Gaunt table off), the kept Gaunt table, and
+        the modulated-signal SHT of Appendix A, for map 0 of workload 3 and
+        for a wide window over a narrow signal (L_f = 32, L_h = 64)."""
+        out = {}
+        cases = [("workload3_map0", Lf, Lh, grid, dev_inputs[0][0], dev_inputs[0][1], dev_inputs[0][2])]
+        fw = synth.signal_powerlaw(32, 4101)
+        hw = synth.window_cn(64, 4102, decay=1.0)
+        pw = synth.pairs_bands([3, 17, 31])
+        cases.append(("Lf32_Lh64_3bands", 32, 64, (15, 8, 127), torch.from_numpy(fw).cuda(),
+                      torch.from_numpy(hw).cuda(), torch.from_numpy(pw).cuda()))
+        for name, lf, lh, gr, fd, hd, pd in cases:
+            n = pd.shape[0]
+            gb = torch.empty((n,) + gr, dtype=torch.complex64, device="cuda")
+            desc = pkg.make_desc(lf, lh, gr, 1)
+            res = {"pairs": int(n)}
+            for tag, gt, cp in (("gaunt_chains", 2, 0), ("gaunt_table", 0, 0), ("modulated_sht", 0, 2)):
+                ctx.set_option(pkg.SLSHT_OPT_GAUNT_TABLE, gt)
+                ctx.set_option(pkg.SLSHT_OPT_COUPLING, cp)
+                pkg.slsht_forward(ctx.h, desc, fd, hd, pd, n, gb, stream)
+                barrier()
+                ctx.stats(reset=True)
+                ctx.profile(True)
+                pkg.slsht_forward(ctx.h, desc, fd, hd, pd, n, gb, stream)
+                barrier()
+                ctx.profile(False)
+                res[tag + "_ms"] = ctx.stats(reset=True)["ms"]["couple"]
+            out[name] = res
+            del gb
+        ctx.set_option(pkg.SLSHT_OPT_GAUNT_TABLE, 0)
+        ctx.set_option(pkg.SLSHT_OPT_COUPLING, 0)
+        return out
+
     # ---------------- FP32_BULK headline
     g32 = torch.empty((npairs_map,) + grid, dtype=torch.complex64, device="cuda")
     ms32, st32, clk = timed(1, g32, args.steps, args.warmup, ClockSampler(local))
@@ -591,9 +625,11 @@ def main():
     del a32
     torch.cuda.empty_cache()
     win_gen = None
+    coup = None
     if args.fp64_steps > 0:
         wins = windows_leg()
         win_gen = window_leg()
+        coup = coupling_leg()
 
     # ---------------- e2e through the C ABI with host buffers
     e2e = None
@@ -657,6 +693,7 @@ def main():
             "inverse_fp32": inv32,
             "multi_window": wins,
             "window_generator": win_gen,
+            "coupling_routes": coup,
             "serve": serve,
         }
         print(json.dumps(line), flush=True)

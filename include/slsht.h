@@ -303,6 +303,14 @@ int slsht_get_stats(slsht_ctx* ctx, slsht_stats* out, int reset);
  *                            (l, -m) is also listed only one is computed:
  *                            the alpha stage stores both outputs (device g_out
  *                            only; host g_out is computed in full).  0: off.
+ *  SLSHT_OPT_COUPLING     1 (default 0 = 1): k by Gaunt coefficients (3j
+ *                            recurrences, Sec. III-B); 2: k by the spherical
+ *                            harmonic transform of the modulated signal
+ *                            (Appendix A: Gauss-Legendre quadrature of the
+ *                            band-limited triple products), cheaper when the
+ *                            window band is wide and the signal band narrow;
+ *                            rounding limits it to ~1e-11 relative near
+ *                            l = 255.
  * Returns SLSHT_OK or SLSHT_E_ARG. */
 #define SLSHT_OPT_BETA_ROUTE   1
 #define SLSHT_OPT_ALPHA_ENGINE 2
@@ -310,6 +318,7 @@ int slsht_get_stats(slsht_ctx* ctx, slsht_stats* out, int reset);
 #define SLSHT_OPT_GAUNT_TABLE  4
 #define SLSHT_OPT_WAIT_TEST    5
 #define SLSHT_OPT_REAL_FIELDS  6
+#define SLSHT_OPT_COUPLING     7
 int slsht_set_option(slsht_ctx* ctx, int option, int64_t value);
 
 /* Bytes of device memory the context currently holds. */

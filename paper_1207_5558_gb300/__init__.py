@@ -11,6 +11,7 @@ import ctypes
 from . import _abi
 from ._abi import (SLSHT_FP32_BULK, SLSHT_FP64, SLSHT_OPT_ALPHA_ENGINE,  # noqa: F401
                    SLSHT_OPT_BETA_ROUTE, SLSHT_OPT_CHUNK_PAIRS, SLSHT_OPT_GAUNT_TABLE, SLSHT_OPT_WAIT_TEST, SLSHT_OPT_REAL_FIELDS,
+                   SLSHT_OPT_COUPLING,
                    SlshtError, STAGE_NAMES,
                    slsht_desc, slsht_stats)
 

@@ -28,6 +28,7 @@ SLSHT_OPT_CHUNK_PAIRS = 3
 SLSHT_OPT_GAUNT_TABLE = 4
 SLSHT_OPT_WAIT_TEST = 5
 SLSHT_OPT_REAL_FIELDS = 6
+SLSHT_OPT_COUPLING = 7
 
 SLSHT_NSTAGES = 8
 SLSHT_NOALLOC_SCRATCH_BYTES = 32 << 20

@@ -124,6 +124,7 @@ struct Workspace {
   // until the next call: sources of the uploads) and the device slot map
   std::vector<int32_t> rf_lm, rf_slots;
   void* rfs = nullptr; size_t rfs_cap = 0;
+  void* ms = nullptr; size_t ms_cap = 0;     // modulated-SHT coupling scratch
   std::vector<int32_t> gt_work;              // host copy (source of the upload)
   bool gt_valid = false;
   int gt_Lf = 0, gt_Lh = 0;
@@ -172,6 +173,7 @@ struct slsht_ctx {
   std::map<std::tuple<int, int>, TableEntry> etab;                  // Na, Lh (tensor-core E blobs)
   Workspace sync_ws;
   int opt_beta_route = 0, opt_alpha_engine = 0, opt_gaunt_table = 0, opt_wait_test = 0, opt_real_fields = 0;
+  int opt_coupling = 0;
   int64_t opt_chunk = 0;
   bool profile = false;
   std::vector<ProfRec> prof;
@@ -292,6 +294,7 @@ static void ws_release(slsht_ctx* c, Workspace& w) {
   ctx_free(c, w.gt, w.gt_cap);
   ctx_free(c, w.gtw, w.gtw_cap);
   ctx_free(c, w.rfs, w.rfs_cap);
+  ctx_free(c, w.ms, w.ms_cap);
   w.gt_valid = false;
   for (int i = 0; i < 2; ++i) ctx_free(c, w.stage[i], w.stage_cap[i]);
   for (int i = 0; i < 2; ++i) {
@@ -532,6 +535,10 @@ extern "C" int slsht_set_option(slsht_ctx* c, int option, int64_t v) {
       if (v < 0 || v > 1) return SLSHT_E_ARG;
       c->opt_real_fields = (int)v;
       return SLSHT_OK;
+    case SLSHT_OPT_COUPLING:
+      if (v < 0 || v > 2) return SLSHT_E_ARG;
+      c->opt_coupling = (int)v;
+      return SLSHT_OK;
     default:
       return SLSHT_E_ARG;
   }
@@ -601,7 +608,7 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
   const bool host_out = !is_device_ptr(g_out);
   CK(cudaStreamWaitEvent(st, w.done, 0));
 
-  int route, tc, engine, gt_opt, wait_test;
+  int route, tc, engine, gt_opt, wait_test, coupling;
   int64_t chunk_opt;
   {
     std::lock_guard<std::mutex> g(ctx->mu);
@@ -611,6 +618,7 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
     chunk_opt = ctx->opt_chunk;
     gt_opt = ctx->opt_gaunt_table;
     wait_test = ctx->opt_wait_test;
+    coupling = ctx->opt_coupling;
   }
   // rotated-window route on the tensor cores: producer and alpha stage fused
   // into one kernel unless the separate producer kernel was asked for
@@ -685,6 +693,14 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
   const bool use_gt = gt_opt == 1 || (gt_opt == 0 && gt_bytes <= ((size_t)256 << 20));
   if (reuse_k) {
     // k of this signal and pair list is still in w.kc (multi-window calls)
+  } else if (coupling == 2) {
+    // Appendix A: quadrature of the modulated signal's transform
+    int lmax = 0;
+    for (int32_t i = 0; i < n_pairs; ++i) lmax = std::max(lmax, (int)lm_host[2 * i]);
+    CKS(ws_reserve(ctx, w, &w.ms, &w.ms_cap, msht_scratch_bytes(Lf, Lh, lmax, n_pairs)));
+    LAUNCH(SLSHT_STAGE_COUPLE, ax,
+           launch_couple_msht((const double2*)f_dev, Lf, Lh, (const int2*)lm_dev, n_pairs, lmax, w.ms,
+                              (double2*)w.kc, ax));
   } else if (use_gt) {
     const bool hit = w.gt_valid && w.gt_Lf == Lf && w.gt_Lh == Lh && w.gt_lm.size() == 2 * (size_t)n_pairs &&
                      std::memcmp(w.gt_lm.data(), lm_host, sizeof(int32_t) * 2 * (size_t)n_pairs) == 0;

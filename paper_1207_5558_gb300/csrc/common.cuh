@@ -57,6 +57,14 @@ cudaError_t launch_gaunt_table(int Lf, int Lh, const int2* lm, int npairs, const
 cudaError_t launch_couple_apply(const double2* f, int Lh, const int2* lm, int npairs, const void* table, double2* kc,
                                 cudaStream_t st);
 
+// k by the SHT of the modulated signal (Appendix A): Gauss-Legendre
+// quadrature of the band-limited triple products on msht_nodes(L_f, L_h, lmax)
+// nodes (lmax = the largest requested l); scratch of msht_scratch_bytes.
+int msht_nodes(int Lf, int Lh, int lmax);
+size_t msht_scratch_bytes(int Lf, int Lh, int lmax, int npairs);
+cudaError_t launch_couple_msht(const double2* f, int Lf, int Lh, const int2* lm, int npairs, int lmax, void* scratch,
+                               double2* kc, cudaStream_t st);
+
 // C_{q,q',q''}(l, m) (Eq. constant_alternative_formulation), [pair][q][q'][q''].
 cudaError_t launch_ctensor(const double2* kc, const double2* h, const double* D, int Lh,
                            int npairs, double2* C, cudaStream_t st);

@@ -90,7 +90,7 @@ __global__ void k_window_basis(const double* __restrict__ ct, const double* __re
 
 // ---------------------------------------------------------------- host helpers
 // Gauss-Legendre nodes and weights on [-1, 1] by Newton's method on P_n.
-static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
   x.assign(n, 0.0);
   w.assign(n, 0.0);
   const double pi = 3.14159265358979323846;

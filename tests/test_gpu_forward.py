@@ -372,3 +372,43 @@ def test_forward_windows_reuses_coupling(ctx, prec):
         single = _fw(ctx, Lf, Lh, grid, f, hs[i], pairs, prec)
         assert np.array_equal(g[i], single)
     assert rel(g[1], O.forward_coeff(f, hs[1], Lf, Lh, pairs, grid)) < tol
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_modulated_sht_coupling_route(ctx, prec):
+    """SLSHT_OPT_COUPLING 2: k by Gauss-Legendre quadrature of the modulated
+    signal's transform (Appendix A) instead of Gaunt coefficients; against the
+    oracle and the Gaunt route, including l > L_f - 1 and |m| = l."""
+    import paper_1207_5558_gb300 as pkg
+    Lf, Lh, grid = 20, 6, (45, 20, 11)
+    f = synth.signal_powerlaw(Lf, 401)
+    h = synth.window_cn(Lh, 402)
+    pairs = synth.subsample_pairs(synth.pairs_all(Lf + Lh - 1), 0.1, seed=403)
+    ref = O.forward_coeff(f, h, Lf, Lh, pairs, grid)
+    gaunt = _fw(ctx, Lf, Lh, grid, f, h, pairs, prec)
+    ctx.set_option(pkg.SLSHT_OPT_COUPLING, 2)
+    try:
+        msht = _fw(ctx, Lf, Lh, grid, f, h, pairs, prec)
+    finally:
+        ctx.set_option(pkg.SLSHT_OPT_COUPLING, 0)
+    tol = TOL64 if prec == 0 else TOL32
+    assert rel(msht, ref) < tol
+    assert rel(msht, gaunt) < (1e-12 if prec == 0 else 2e-6)
+
+
+def test_modulated_sht_coupling_workload2_size(ctx):
+    """Both coupling routes at workload 2's band limits (L_f = 64, L_h = 8),
+    FP64, on a seeded 5% of its pairs."""
+    import paper_1207_5558_gb300 as pkg
+    c = synth.CONFIGS[2]
+    f = synth.signal_powerlaw(c["Lf"], 404)
+    h = synth.window_cn(c["Lh"], 405, decay=1.0)
+    pairs = synth.subsample_pairs(synth.pairs_all(c["Lf"]), 0.05, seed=406)
+    grid = (c["grid"][0], 12, c["grid"][2])
+    gaunt = _fw(ctx, c["Lf"], c["Lh"], grid, f, h, pairs, 0)
+    ctx.set_option(pkg.SLSHT_OPT_COUPLING, 2)
+    try:
+        msht = _fw(ctx, c["Lf"], c["Lh"], grid, f, h, pairs, 0)
+    finally:
+        ctx.set_option(pkg.SLSHT_OPT_COUPLING, 0)
+    assert rel(msht, gaunt) < 1e-12
