@@ -412,3 +412,19 @@ def test_modulated_sht_coupling_workload2_size(ctx):
     finally:
         ctx.set_option(pkg.SLSHT_OPT_COUPLING, 0)
     assert rel(msht, gaunt) < 1e-12
+
+
+@pytest.mark.parametrize("Na", [135, 127])
+def test_fp64_widest_window_band(ctx, Na):
+    """FP64 at the largest window band limit, L_h = 64 (K = 127): the alpha
+    stage drops to 64-column CTAs to fit 127 staged coefficients; N_alpha =
+    135 takes the split DFT (P = 9), 127 the direct sum."""
+    import paper_1207_5558_gb300 as pkg
+    Lf, Lh = 6, 64
+    grid = (Na, 3, 131)
+    f = synth.signal_powerlaw(Lf, 500 + Na)
+    h = synth.window_cn(Lh, 600 + Na, decay=1.0)
+    pairs = np.array([[5, -2], [40, 7], [68, 68]], dtype=np.int32)
+    ref = O.forward_coeff(f, h, Lf, Lh, pairs, grid, kroute="recurrence")
+    g = _fw(ctx, Lf, Lh, grid, f, h, pairs, 0)
+    assert rel(g, ref) < TOL64
