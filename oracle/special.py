@@ -281,7 +281,7 @@ def wigner3j_m_family(j1, j2, j3, M, digits=100):
 
 def gaunt_exact(lp, mp, p, q, l, m):
     """T(l',m'; p,q; l,m) = int Y_l'^m' Y_p^q conj(Y_l^m) ds via the 3j route
-    (Sec. III-B: 'can be evaluated using Wigner-3j symbols'):
+    (Sec. III-B writes this triple integral through Wigner-3j symbols):
       T = (-1)^m sqrt((2l'+1)(2p+1)(2l+1)/(4 pi)) (l' p l; 0 0 0)(l' p l; m' q -m).
     """
     if mp + q != m:
