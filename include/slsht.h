@@ -222,6 +222,93 @@ int slsht_inverse(slsht_ctx* ctx, const slsht_desc* desc,
 int slsht_forward_noalloc(const slsht_desc* desc, const double* f_lm, const double* h_lm,
                           const int32_t* lm, int32_t n_pairs, void* g_out, void* stream);
 
+/* ---------------------------------------------------------------- batches */
+
+/* One analysis of a batch plan: a signal, a window, a pair list and a grid,
+ * each with its own band limits, sizes and precision.  f_lm, h_lm and g_out
+ * are DEVICE pointers bound to the plan: every slsht_batch_launch reads the
+ * coefficients they hold at that time and writes g_out (layout and size as for
+ * slsht_forward; g_out 16-byte aligned).  lm may be host or device memory and
+ * is copied when the plan is created. */
+typedef struct {
+  slsht_desc desc;
+  const double* f_lm;   /* device, L_f*L_f complex128 */
+  const double* h_lm;   /* device, L_h*L_h complex128 */
+  const int32_t* lm;    /* n_pairs x (l, m) */
+  int32_t n_pairs;      /* >= 1 */
+  void* g_out;          /* device */
+} slsht_batch_item;
+
+typedef struct slsht_batch slsht_batch;   /* opaque plan */
+
+/* Flags of slsht_batch_create. */
+#define SLSHT_BATCH_NO_GRAPH 1   /* enqueue the kernels one by one at each launch
+                                    instead of replaying a captured CUDA graph */
+#define SLSHT_BATCH_NO_TUNE  2   /* tile shapes from the built-in rule instead of
+                                    timing the candidates */
+#define SLSHT_BATCH_NO_TC    4   /* keep FP32_BULK items on CUDA cores */
+
+/* Plan many analyses (maps, windows, requests of uneven band limits and grids)
+ * as one unit.  Per launch the plan runs: the Gaunt gather-sum of every pair
+ * of every item (one kernel); every distinct rotated window (one kernel); the
+ * alpha stage of every CUDA-core item as ONE persistent kernel per precision,
+ * whose CTAs take (item, pair, column block) tiles from a shared counter; and
+ * one fused tensor-core launch per FP32_BULK item that the tuner gave to the
+ * tensor cores.  These launches are captured once into a CUDA graph that each
+ * slsht_batch_launch replays.
+ *  - Signal-independent work is done here, once: the Gaunt coefficient table
+ *    of every distinct (L_f, L_h, pair list) (Sec. III-B), the Delta and
+ *    d(beta) tables and the phase tables (shared with the context's cache).
+ *  - Tile shapes: for every distinct (precision, L_h, N_alpha, N_beta,
+ *    N_gamma) the autotuner times each candidate (columns per tile 32/64/128;
+ *    direct alpha sum or split DFT with each odd factor 3/5/7/9 of N_alpha;
+ *    for FP32_BULK the fused tensor-core kernel) on the item's own data into
+ *    plan scratch, and keeps the fastest per sample.  The choice is cached in
+ *    the context for later plans of the same shape.
+ *  - Memory: tables, k, the rotated windows and the tile lists are plan-owned
+ *    and counted against the context's budget.
+ *  - Creation is synchronous: it waits for `stream` (so f and h may be
+ *    written on it just before), builds the tables, tunes, runs the plan once
+ *    (so every g_out holds its result when the call returns) and captures the
+ *    graph, all on its own stream, and returns when they are complete.
+ * Errors: SLSHT_E_ARG (null ctx/items/out, n_items < 1, a bad descriptor or
+ * pair list, an f/h/g_out not in device memory, g_out misaligned),
+ * SLSHT_E_NOMEM, SLSHT_E_CUDA.  On error *out is NULL and nothing is kept. */
+int slsht_batch_create(slsht_ctx* ctx, int32_t n_items, const slsht_batch_item* items, int32_t flags,
+                       void* stream, slsht_batch** out);
+
+/* Enqueue one evaluation of every item of the plan on `stream`.  Launches of
+ * one plan share its scratch (k, rotated windows, tile counter): order them
+ * (one stream or events) and do not launch one plan from two threads at once. */
+int slsht_batch_launch(slsht_batch* batch, void* stream);
+
+/* Facts about a plan (item ignored where it says so):
+ *  SLSHT_BQ_TILE_COLS  item's columns per tile (0 on the tensor cores)
+ *  SLSHT_BQ_ALPHA_FORM item's alpha form: 0 direct sum, 3/5/7/9 split DFT with
+ *                      that factor, -1 fused tensor-core kernel
+ *  SLSHT_BQ_TUNED      item's shape: 1 timed by this plan, 2 taken from the
+ *                      context's cache, 0 built-in rule (SLSHT_BATCH_NO_TUNE)
+ *  SLSHT_BQ_TILES      CUDA-core tiles per launch (item ignored)
+ *  SLSHT_BQ_KERNELS    kernels per launch (item ignored)
+ *  SLSHT_BQ_GRAPH      1 if launches replay a CUDA graph (item ignored)
+ *  SLSHT_BQ_BYTES      device memory the plan holds (item ignored)
+ *  SLSHT_BQ_SAMPLES    g samples per launch (item ignored)
+ * Returns SLSHT_OK or SLSHT_E_ARG. */
+#define SLSHT_BQ_TILE_COLS  1
+#define SLSHT_BQ_ALPHA_FORM 2
+#define SLSHT_BQ_TUNED      3
+#define SLSHT_BQ_TILES      4
+#define SLSHT_BQ_KERNELS    5
+#define SLSHT_BQ_GRAPH      6
+#define SLSHT_BQ_BYTES      7
+#define SLSHT_BQ_SAMPLES    8
+int slsht_batch_query(const slsht_batch* batch, int32_t item, int32_t what, int64_t* value);
+
+/* Wait for the plan's last launch and free everything it holds.  NULL is a
+ * no-op.  slsht_destroy frees the plans of its context that are still alive;
+ * a plan must not be used (or destroyed) after its context. */
+void slsht_batch_destroy(slsht_batch* batch);
+
 /* ---------------------------------------------------------------- serving */
 
 /* Non-blocking forward request for a continuous-batching server.  The

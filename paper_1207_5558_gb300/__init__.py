@@ -12,12 +12,16 @@ from . import _abi
 from ._abi import (SLSHT_FP32_BULK, SLSHT_FP64, SLSHT_OPT_ALPHA_ENGINE,  # noqa: F401
                    SLSHT_OPT_BETA_ROUTE, SLSHT_OPT_CHUNK_PAIRS, SLSHT_OPT_GAUNT_TABLE, SLSHT_OPT_WAIT_TEST, SLSHT_OPT_REAL_FIELDS,
                    SLSHT_OPT_COUPLING,
+                   SLSHT_BATCH_NO_GRAPH, SLSHT_BATCH_NO_TUNE, SLSHT_BATCH_NO_TC,
+                   SLSHT_BQ_TILE_COLS, SLSHT_BQ_ALPHA_FORM, SLSHT_BQ_TUNED, SLSHT_BQ_TILES, SLSHT_BQ_KERNELS,
+                   SLSHT_BQ_GRAPH, SLSHT_BQ_BYTES, SLSHT_BQ_SAMPLES,
                    SlshtError, STAGE_NAMES,
-                   slsht_desc, slsht_stats)
+                   slsht_batch_item, slsht_desc, slsht_stats)
 
 __all__ = ["Context", "make_desc", "SLSHT_FP64", "SLSHT_FP32_BULK", "SlshtError",
            "slsht_create", "slsht_destroy", "slsht_forward", "slsht_forward_noalloc", "slsht_forward_windows",
-           "slsht_window_ellipse",
+           "slsht_window_ellipse", "slsht_batch_create", "slsht_batch_launch", "slsht_batch_query",
+           "slsht_batch_destroy", "Batch",
            "slsht_inverse", "slsht_submit",
            "slsht_poll", "slsht_drain", "slsht_strerror", "slsht_check_args", "slsht_profile",
            "slsht_get_stats", "slsht_set_option", "slsht_mem_used", "slsht_version"]
@@ -85,6 +89,28 @@ def slsht_forward_noalloc(desc, f_lm, h_lm, lm, n_pairs, g_out, stream=None):
     return _abi.check(_abi.load().slsht_forward_noalloc(ctypes.byref(desc), _abi.ptr(f_lm), _abi.ptr(h_lm),
                                                         _abi.ptr(lm), int(n_pairs), _abi.ptr(g_out),
                                                         _stream(stream)), "slsht_forward_noalloc")
+
+
+def slsht_batch_create(ctx, items, flags=0, stream=None):
+    """items: a ctypes array of slsht_batch_item.  Returns the plan handle."""
+    h = ctypes.c_void_p()
+    _abi.check(_abi.load().slsht_batch_create(ctx, len(items), items, int(flags), _stream(stream), ctypes.byref(h)),
+               "slsht_batch_create")
+    return h
+
+
+def slsht_batch_launch(batch, stream=None):
+    return _abi.check(_abi.load().slsht_batch_launch(batch, _stream(stream)), "slsht_batch_launch")
+
+
+def slsht_batch_query(batch, item, what):
+    v = ctypes.c_int64()
+    _abi.check(_abi.load().slsht_batch_query(batch, int(item), int(what), ctypes.byref(v)), "slsht_batch_query")
+    return v.value
+
+
+def slsht_batch_destroy(batch):
+    _abi.load().slsht_batch_destroy(batch)
 
 
 def slsht_submit(ctx, desc, f_lm, h_lm, lm, n_pairs, g_out):
@@ -231,6 +257,64 @@ class Context:
 
     def mem_used(self):
         return slsht_mem_used(self.h)
+
+    def batch(self, items, flags=0, stream=None):
+        """A Batch plan over `items` (see Batch)."""
+        return Batch(self, items, flags, stream)
+
+
+class Batch:
+    """A batch plan over several analyses of one context.
+
+    items: a list of dicts with keys L_f, L_h, grid (N_alpha, N_beta, N_gamma),
+    f and h (complex128 DEVICE tensors), lm ([n, 2] pairs) and optional prec
+    and g_out (a device tensor; allocated when absent).  The plan keeps
+    references to f, h and g_out: every launch() reads what f and h hold then
+    and writes g_out (see slsht_batch_create).  outputs: the g_out tensors."""
+
+    def __init__(self, ctx, items, flags=0, stream=None):
+        import torch
+        self.ctx = ctx
+        self.h = None
+        self.keep = []
+        self.outputs = []
+        arr = (slsht_batch_item * len(items))()
+        for i, it in enumerate(items):
+            prec = it.get("prec", SLSHT_FP64)
+            lm = _as_pairs(it["lm"])
+            n = int(lm.shape[0])
+            g = it.get("g_out")
+            if g is None:
+                dt = torch.complex128 if prec == SLSHT_FP64 else torch.complex64
+                g = torch.empty((n,) + tuple(it["grid"]), dtype=dt, device="cuda:%d" % ctx.device)
+            f, h = it["f"], it["h"]
+            self.keep += [f, h, lm, g]
+            self.outputs.append(g)
+            arr[i].desc = make_desc(it["L_f"], it["L_h"], it["grid"], prec)
+            arr[i].f_lm = f.data_ptr()
+            arr[i].h_lm = h.data_ptr()
+            arr[i].lm = _abi.ptr(lm).value
+            arr[i].n_pairs = n
+            arr[i].g_out = g.data_ptr()
+        self.h = slsht_batch_create(ctx.h, arr, flags, stream)
+
+    def launch(self, stream=None):
+        slsht_batch_launch(self.h, stream)
+
+    def query(self, what, item=0):
+        return slsht_batch_query(self.h, item, what)
+
+    def close(self):
+        # a plan dies with its context: after Context.close() only drop the handle
+        if self.h is not None and self.ctx.h is not None:
+            slsht_batch_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _as_pairs(lm):

@@ -30,6 +30,19 @@ SLSHT_OPT_WAIT_TEST = 5
 SLSHT_OPT_REAL_FIELDS = 6
 SLSHT_OPT_COUPLING = 7
 
+SLSHT_BATCH_NO_GRAPH = 1
+SLSHT_BATCH_NO_TUNE = 2
+SLSHT_BATCH_NO_TC = 4
+
+SLSHT_BQ_TILE_COLS = 1
+SLSHT_BQ_ALPHA_FORM = 2
+SLSHT_BQ_TUNED = 3
+SLSHT_BQ_TILES = 4
+SLSHT_BQ_KERNELS = 5
+SLSHT_BQ_GRAPH = 6
+SLSHT_BQ_BYTES = 7
+SLSHT_BQ_SAMPLES = 8
+
 SLSHT_NSTAGES = 8
 SLSHT_NOALLOC_SCRATCH_BYTES = 32 << 20
 STAGE_NAMES = ["tables", "couple", "ctensor", "beta_gamma", "alpha", "inverse", "copy", "other"]
@@ -38,6 +51,11 @@ STAGE_NAMES = ["tables", "couple", "ctensor", "beta_gamma", "alpha", "inverse", 
 class slsht_desc(ctypes.Structure):
     _fields_ = [("L_f", ctypes.c_int32), ("L_h", ctypes.c_int32), ("n_alpha", ctypes.c_int32),
                 ("n_beta", ctypes.c_int32), ("n_gamma", ctypes.c_int32), ("prec", ctypes.c_int32)]
+
+
+class slsht_batch_item(ctypes.Structure):
+    _fields_ = [("desc", slsht_desc), ("f_lm", ctypes.c_void_p), ("h_lm", ctypes.c_void_p),
+                ("lm", ctypes.c_void_p), ("n_pairs", ctypes.c_int32), ("g_out", ctypes.c_void_p)]
 
 
 class slsht_stats(ctypes.Structure):
@@ -67,6 +85,11 @@ def load(path=LIB_PATH):
         "slsht_forward_windows": (ctypes.c_int, [vp, ctypes.POINTER(slsht_desc), vp, i32, vp, vp, i32, vp, vp]),
         "slsht_window_ellipse": (ctypes.c_int, [vp, i32, ctypes.c_double, ctypes.c_double, i32, i32, vp,
                                                 ctypes.POINTER(ctypes.c_double), vp]),
+        "slsht_batch_create": (ctypes.c_int, [vp, i32, ctypes.POINTER(slsht_batch_item), i32, vp,
+                                              ctypes.POINTER(vp)]),
+        "slsht_batch_launch": (ctypes.c_int, [vp, vp]),
+        "slsht_batch_query": (ctypes.c_int, [vp, i32, i32, ctypes.POINTER(i64)]),
+        "slsht_batch_destroy": (None, [vp]),
         "slsht_submit": (ctypes.c_int, [vp, ctypes.POINTER(slsht_desc), vp, vp, vp, i32, vp,
                                         ctypes.POINTER(u64)]),
         "slsht_poll": (ctypes.c_int, [vp, u64]),

@@ -21,7 +21,9 @@
 #include <vector>
 
 #include "../../include/slsht.h"
+#include "batch.cuh"
 #include "common.cuh"
+#include "stages_dev.cuh"
 #include "tc.cuh"
 
 // ---------------------------------------------------------------- errors
@@ -160,6 +162,8 @@ struct Slot {
 #define SERVE_SLOTS 4
 #define SERVE_MAX_QUEUE 4096
 
+struct slsht_batch;
+
 struct slsht_ctx {
   int device = 0;
   size_t budget = 0;
@@ -171,6 +175,9 @@ struct slsht_ctx {
   std::map<std::tuple<int, int, int, int>, TableEntry> phase;       // N, R, r0, prec
   std::map<int, TableEntry> wbeta;                                  // Nb
   std::map<std::tuple<int, int>, TableEntry> etab;                  // Na, Lh (tensor-core E blobs)
+  // batch-plan autotuner: (prec, Lh, Na, Nb, Ng, tensor cores allowed) -> (columns per tile, alpha form)
+  std::map<std::tuple<int, int, int, int, int, int>, std::pair<int, int>> tune;
+  std::vector<slsht_batch*> plans;   // live batch plans (freed by slsht_destroy at the latest)
   Workspace sync_ws;
   int opt_beta_route = 0, opt_alpha_engine = 0, opt_gaunt_table = 0, opt_wait_test = 0, opt_real_fields = 0;
   int opt_coupling = 0;
@@ -481,9 +488,19 @@ static void free_entry(slsht_ctx* c, TableEntry& e) {
   if (e.ready) cudaEventDestroy(e.ready);
 }
 
+static void batch_free(slsht_batch* b);
+
 extern "C" void slsht_destroy(slsht_ctx* c) {
   if (!c) return;
   DeviceGuard g(c->device);
+  {
+    std::vector<slsht_batch*> plans;
+    {
+      std::lock_guard<std::mutex> l(c->mu);
+      plans.swap(c->plans);
+    }
+    for (slsht_batch* b : plans) batch_free(b);
+  }
   {
     std::unique_lock<std::mutex> l(c->smu);
     c->stop = true;
@@ -1026,6 +1043,545 @@ extern "C" int slsht_inverse(slsht_ctx* ctx, const slsht_desc* desc, const void*
   }
   CK(cudaEventRecord(w.done, st));
   return SLSHT_OK;
+}
+
+// ---------------------------------------------------------------- batch plans
+// A plan binds many analyses (items) and evaluates them with a fixed launch
+// sequence: k_batch_couple (k of every distinct (signal, pair list)),
+// k_batch_rotwin (every distinct rotated window), one persistent
+// k_batch_alpha per precision over the CUDA-core items' tiles, and one fused
+// tensor-core launch per item the tuner gave to the tensor cores.  The
+// sequence is captured once into a CUDA graph.
+struct BatchItemHost {
+  slsht_desc d{};
+  const double2* f = nullptr;
+  const double2* h = nullptr;
+  void* g = nullptr;
+  int npairs = 0;
+  int gaunt = -1, cpl = -1, rot = -1;
+  int nt = 0, form = 0, tuned = 0;     // form -1: fused tensor-core kernel
+  const void* etab = nullptr;
+};
+
+struct BatchGaunt {
+  int Lf = 0, Lh = 0;
+  std::vector<int32_t> lm;
+  void* lm_dev = nullptr;
+  void* table = nullptr;
+};
+
+struct slsht_batch {
+  slsht_ctx* ctx = nullptr;
+  int flags = 0;
+  std::mutex mu;
+  cudaStream_t cs = nullptr;            // creation, tuning and capture
+  cudaEvent_t done = nullptr;           // last launch
+  cudaEvent_t ta = nullptr, tb = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<std::pair<void*, size_t>> mem;
+  std::vector<BatchItemHost> items;
+  std::vector<BatchGaunt> gaunt;
+  std::vector<BCouple> cpl;
+  std::vector<BCplBlk> cblk;
+  std::vector<BRot> rot;
+  std::vector<BRotBlk> rblk;
+  std::vector<BItem> bitem;             // alpha view of every item (index = item)
+  std::vector<BTile> tiles[2];          // CUDA-core tiles per precision (0 FP64, 1 FP32)
+  std::vector<int> tc_items;
+  void *d_cpl = nullptr, *d_cblk = nullptr, *d_rot = nullptr, *d_rblk = nullptr, *d_bitem = nullptr;
+  void* d_tiles[2] = {nullptr, nullptr};
+  int* d_counter = nullptr;             // one tile counter per precision
+  size_t rot_smem = 0, alpha_smem[2] = {0, 0};
+  int alpha_grid[2] = {0, 0};
+  int kernels = 0, k_couple = 0, k_rot = 0, k_alpha = 0;
+  uint64_t samples = 0;
+  size_t bytes = 0;
+};
+
+static int batch_alloc(slsht_batch* b, size_t bytes, void** out) {
+  CKS(ctx_alloc(b->ctx, bytes, out));
+  b->mem.push_back({*out, bytes});
+  b->bytes += bytes;
+  return SLSHT_OK;
+}
+
+// Device copy of a host array that the plan keeps (stream-ordered on cs).
+static int batch_upload(slsht_batch* b, const void* src, size_t bytes, void** dev) {
+  *dev = nullptr;
+  if (bytes == 0) return SLSHT_OK;
+  CKS(batch_alloc(b, bytes, dev));
+  CK(cudaMemcpyAsync(*dev, src, bytes, cudaMemcpyHostToDevice, b->cs));
+  return SLSHT_OK;
+}
+
+static void batch_free(slsht_batch* b) {
+  if (!b) return;
+  if (b->cs) cudaStreamSynchronize(b->cs);
+  if (b->done) cudaEventSynchronize(b->done);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (auto& m : b->mem) ctx_free(b->ctx, m.first, m.second);
+  if (b->ta) cudaEventDestroy(b->ta);
+  if (b->tb) cudaEventDestroy(b->tb);
+  if (b->done) cudaEventDestroy(b->done);
+  if (b->cs) cudaStreamDestroy(b->cs);
+  delete b;
+}
+
+static size_t el2_of(int prec) { return prec == SLSHT_FP64 ? sizeof(double2) : sizeof(float2); }
+
+// Alpha-stage arithmetic per sample of a form (multiply-adds), for ordering tiles.
+static double alpha_form_cost(int Lh, int form) {
+  if (form <= 0) return 4.0 * (Lh - 1) + 2.0;
+  return 4.0 * (2 * Lh - 1) / form + form + 3.0;
+}
+
+// Columns per tile by rule: the smallest of 32/64/128 covering min(J, 128)
+// whose X tile fits the shared-memory limit.
+static int batch_rule_nt(int prec, int Lh, long long J) {
+  int nt = J <= 32 ? 32 : (J <= 64 ? 64 : 128);
+  while (nt > 32 && batch_alpha_smem(prec == SLSHT_FP64 ? 0 : 1, Lh, nt) > BA_SMEM_LIMIT) nt /= 2;
+  return nt;
+}
+
+static bool batch_tc_ok(const slsht_batch* b, const slsht_desc& d) {
+  return !(b->flags & SLSHT_BATCH_NO_TC) && d.prec == SLSHT_FP32_BULK && tc_supported(d.L_h, d.n_alpha) &&
+         d.L_h <= 16;
+}
+
+// Phase table of the alpha stage for a form: the direct sum's (cos, sin)(2 pi r a / Na)
+// or the split DFT's twiddles (cos, sin)(2 pi q t / Na).
+static int batch_alpha_table(slsht_batch* b, const slsht_desc& d, int form, const void** out) {
+  std::lock_guard<std::mutex> g(b->ctx->mu);
+  if (form > 0) return get_phase(b->ctx, d.n_alpha, 2 * d.L_h - 1, -(d.L_h - 1), d.prec, b->cs, out);
+  return get_phase(b->ctx, d.n_alpha, d.L_h, 0, d.prec, b->cs, out);
+}
+
+// Times one candidate on the first pairs of item `ii`, into scratch, as it
+// would run in the plan: a CUDA-core tile shape (nt, form) inside a
+// persistent launch that other items' tiles keep full (the sample pairs are
+// replicated `reps` times to fill the GPU), or the fused tensor-core kernel
+// (form -1) as a launch of its own over the item's pairs (np of them, no
+// replication).  Returns device milliseconds per sample in *cost.
+static int batch_time_candidate(slsht_batch* b, int ii, int nt, int form, int np, int reps, void* scratch,
+                                void* d_item, void* d_tiles, int* d_ctr, double* cost) {
+  slsht_ctx* ctx = b->ctx;
+  const BatchItemHost& it = b->items[ii];
+  const slsht_desc& d = it.d;
+  const int pi = d.prec == SLSHT_FP64 ? 0 : 1;
+  const long long J = (long long)d.n_beta * d.n_gamma;
+  if (form < 0) reps = 1;
+  const double samples = (double)np * reps * d.n_alpha * J;
+  std::vector<BTile> tl;
+  BItem bi{};
+  size_t smem = 0;
+  int grid = 0;
+  if (form >= 0) {
+    bi = b->bitem[ii];
+    bi.g = scratch;
+    bi.nt = nt;
+    bi.form = form;
+    CKS(batch_alpha_table(b, d, form, &bi.csa));
+    for (int r = 0; r < reps; ++r)
+      for (int p = 0; p < np; ++p)
+        for (long long j0 = 0; j0 < J; j0 += nt) tl.push_back({0, p, r * np + p, (int)j0});
+    CK(cudaMemcpyAsync(d_item, &bi, sizeof(BItem), cudaMemcpyHostToDevice, b->cs));
+    CK(cudaMemcpyAsync(d_tiles, tl.data(), sizeof(BTile) * tl.size(), cudaMemcpyHostToDevice, b->cs));
+    smem = batch_alpha_smem(pi, d.L_h, nt);
+    grid = (int)std::min<long long>((long long)ctx->num_sms * batch_alpha_occupancy(pi, smem), (long long)tl.size());
+  }
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {          // one warm-up, three timed
+    CK(cudaMemsetAsync(d_ctr, 0, sizeof(int), b->cs));
+    CK(cudaEventRecord(b->ta, b->cs));
+    cudaError_t e;
+    if (form >= 0)
+      e = launch_batch_alpha(pi, (const BItem*)d_item, (const BTile*)d_tiles, (int)tl.size(), d_ctr, grid, smem, b->cs);
+    else
+      e = launch_alpha_fused(b->cpl[it.cpl].kc, (const float2*)b->rot[it.rot].H, it.etab, d.L_h, d.n_alpha, d.n_beta,
+                             d.n_gamma, np * reps, (float2*)scratch, ctx->num_sms, 0, nullptr, b->cs);
+    if (e != cudaSuccess) { record_cuda_error("batch tuning launch", e); return SLSHT_E_CUDA; }
+    CK(cudaEventRecord(b->tb, b->cs));
+    CK(cudaEventSynchronize(b->tb));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, b->ta, b->tb));
+    if (rep > 0) best = std::min(best, ms);
+  }
+  *cost = best / samples;
+  return SLSHT_OK;
+}
+
+// Picks (columns per tile, alpha form) for item ii's shape: the context's
+// cache, the rule (SLSHT_BATCH_NO_TUNE), or by timing every candidate.
+static int batch_tune(slsht_batch* b, int ii) {
+  slsht_ctx* ctx = b->ctx;
+  BatchItemHost& it = b->items[ii];
+  const slsht_desc& d = it.d;
+  const int pi = d.prec == SLSHT_FP64 ? 0 : 1;
+  const int Lh = d.L_h, Na = d.n_alpha;
+  const long long J = (long long)d.n_beta * d.n_gamma;
+  const bool tc_ok = batch_tc_ok(b, d);
+  const auto key = std::make_tuple((int)d.prec, Lh, Na, d.n_beta, d.n_gamma, tc_ok ? 1 : 0);
+  if (b->flags & SLSHT_BATCH_NO_TUNE) {
+    it.nt = batch_rule_nt(d.prec, Lh, J);
+    it.form = tc_ok ? -1 : alpha_split_factor(Lh, Na);
+    it.tuned = 0;
+    return SLSHT_OK;
+  }
+  {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    auto f = ctx->tune.find(key);
+    if (f != ctx->tune.end()) {
+      it.nt = f->second.first;
+      it.form = f->second.second;
+      it.tuned = 2;
+      return SLSHT_OK;
+    }
+  }
+  // candidates
+  std::vector<std::pair<int, int>> cand;
+  std::vector<int> forms = {0};
+  for (int P : {3, 5, 7, 9})
+    if (Na % P == 0) forms.push_back(P);
+  for (int nt : {32, 64, 128}) {
+    if (nt > 32 && J <= nt / 2) continue;                 // more than half the tile idle
+    if (batch_alpha_smem(pi, Lh, nt) > BA_SMEM_LIMIT) continue;
+    for (int fm : forms) cand.push_back({nt, fm});
+  }
+  if (tc_ok) cand.push_back({0, -1});
+  if (cand.empty()) return SLSHT_E_ARG;
+  // sample: the first pairs (all of them up to 16M samples), replicated so
+  // the candidate with the widest tiles still has about eight tiles per SM;
+  // at most 16M samples
+  const double per_pair = (double)Na * J;
+  int np = (int)std::max<double>(1.0, std::min<double>(it.npairs, std::floor(1.6e7 / per_pair)));
+  const long long tiles_np = (long long)np * ((J + 127) / 128);
+  int reps = (int)std::max<long long>(1, (8LL * ctx->num_sms + tiles_np - 1) / tiles_np);
+  reps = (int)std::max<double>(1.0, std::min<double>(reps, std::floor(1.6e7 / (per_pair * np))));
+  const size_t out_bytes = (size_t)np * reps * Na * J * el2_of(d.prec);
+  const size_t max_tiles = (size_t)np * reps * ((J + 31) / 32);
+  void *scratch = nullptr, *d_item = nullptr, *d_tiles = nullptr, *d_ctr = nullptr;
+  int st = ctx_alloc(ctx, out_bytes, &scratch);
+  if (st == SLSHT_OK) st = ctx_alloc(ctx, sizeof(BItem), &d_item);
+  if (st == SLSHT_OK) st = ctx_alloc(ctx, sizeof(BTile) * max_tiles, &d_tiles);
+  if (st == SLSHT_OK) st = ctx_alloc(ctx, 16, &d_ctr);
+  double best = 1e300;
+  std::pair<int, int> pick = cand[0];
+  for (size_t c = 0; c < cand.size() && st == SLSHT_OK; ++c) {
+    double cost = 0.0;
+    st = batch_time_candidate(b, ii, cand[c].first, cand[c].second, np, reps, scratch, d_item, d_tiles,
+                              (int*)d_ctr, &cost);
+    if (st == SLSHT_OK && cost < best) { best = cost; pick = cand[c]; }
+  }
+  cudaStreamSynchronize(b->cs);
+  ctx_free(ctx, scratch, out_bytes);
+  ctx_free(ctx, d_item, sizeof(BItem));
+  ctx_free(ctx, d_tiles, sizeof(BTile) * max_tiles);
+  ctx_free(ctx, d_ctr, 16);
+  CKS(st);
+  it.nt = pick.second < 0 ? batch_rule_nt(d.prec, Lh, J) : pick.first;
+  it.form = pick.second;
+  it.tuned = 1;
+  std::lock_guard<std::mutex> g(ctx->mu);
+  ctx->tune[key] = {it.nt, it.form};
+  return SLSHT_OK;
+}
+
+// The launch sequence of a plan on `st` (also what the graph captures).
+static int batch_enqueue(slsht_batch* b, cudaStream_t st) {
+  slsht_ctx* ctx = b->ctx;
+  cudaError_t e;
+  CK(cudaMemsetAsync(b->d_counter, 0, 2 * sizeof(int), st));
+  e = launch_batch_couple((const BCouple*)b->d_cpl, (const BCplBlk*)b->d_cblk, (int)b->cblk.size(), st);
+  if (e != cudaSuccess) { record_cuda_error("launch_batch_couple", e); return SLSHT_E_CUDA; }
+  e = launch_batch_rotwin((const BRot*)b->d_rot, (const BRotBlk*)b->d_rblk, (int)b->rblk.size(), b->rot_smem, st);
+  if (e != cudaSuccess) { record_cuda_error("launch_batch_rotwin", e); return SLSHT_E_CUDA; }
+  for (int pi = 0; pi < 2; ++pi) {
+    e = launch_batch_alpha(pi, (const BItem*)b->d_bitem, (const BTile*)b->d_tiles[pi], (int)b->tiles[pi].size(),
+                           b->d_counter + pi, b->alpha_grid[pi], b->alpha_smem[pi], st);
+    if (e != cudaSuccess) { record_cuda_error("launch_batch_alpha", e); return SLSHT_E_CUDA; }
+  }
+  for (int ii : b->tc_items) {
+    const BatchItemHost& it = b->items[ii];
+    e = launch_alpha_fused(b->cpl[it.cpl].kc, (const float2*)b->rot[it.rot].H, it.etab, it.d.L_h, it.d.n_alpha,
+                           it.d.n_beta, it.d.n_gamma, it.npairs, (float2*)it.g, ctx->num_sms, 0, nullptr, st);
+    if (e != cudaSuccess) { record_cuda_error("launch_alpha_fused", e); return SLSHT_E_CUDA; }
+  }
+  return SLSHT_OK;
+}
+
+static void batch_count(slsht_batch* b) {
+  slsht_ctx* ctx = b->ctx;
+  std::lock_guard<std::mutex> g(ctx->mu);
+  ctx->launches[SLSHT_STAGE_COUPLE] += b->k_couple;
+  ctx->launches[SLSHT_STAGE_BETA] += b->k_rot;
+  ctx->launches[SLSHT_STAGE_ALPHA] += b->k_alpha;
+  ctx->samples += b->samples;
+}
+
+static int batch_build(slsht_batch* b, const slsht_batch_item* src, int32_t n, cudaStream_t ust,
+                       std::vector<std::vector<int32_t>>& lms) {
+  slsht_ctx* ctx = b->ctx;
+  CK(cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming));
+  CK(cudaEventCreate(&b->ta));
+  CK(cudaEventCreate(&b->tb));
+  CK(cudaEventRecord(b->done, ust));             // inputs written on the caller's stream
+  CK(cudaStreamWaitEvent(b->cs, b->done, 0));
+  b->items.resize(n);
+  std::map<std::tuple<int, int, std::vector<int32_t>>, int> gkey;
+  std::map<std::pair<const void*, int>, int> ckey;
+  std::map<std::tuple<const void*, int, int, int, int>, int> rkey;
+  for (int32_t i = 0; i < n; ++i) {
+    BatchItemHost& it = b->items[i];
+    const slsht_desc& d = src[i].desc;
+    it.d = d;
+    it.f = (const double2*)src[i].f_lm;
+    it.h = (const double2*)src[i].h_lm;
+    it.g = src[i].g_out;
+    it.npairs = src[i].n_pairs;
+    const int Lh = d.L_h, n2 = Lh * Lh, K = 2 * Lh - 1;
+    const long long J = (long long)d.n_beta * d.n_gamma;
+    b->samples += (uint64_t)it.npairs * d.n_alpha * J;
+    // Gaunt table of (L_f, L_h, pair list), signal independent (Sec. III-B)
+    auto gk = std::make_tuple(d.L_f, Lh, lms[i]);
+    auto gf = gkey.find(gk);
+    if (gf == gkey.end()) {
+      BatchGaunt bg;
+      bg.Lf = d.L_f;
+      bg.Lh = Lh;
+      bg.lm = lms[i];
+      CKS(batch_upload(b, bg.lm.data(), sizeof(int32_t) * bg.lm.size(), &bg.lm_dev));
+      std::vector<int32_t> work;
+      mirror_work(bg.lm.data(), it.npairs, &work);
+      void* wdev = nullptr;
+      CKS(batch_upload(b, work.data(), sizeof(int32_t) * work.size(), &wdev));
+      CKS(batch_alloc(b, gaunt_table_bytes(Lh, it.npairs), &bg.table));
+      cudaError_t e = launch_gaunt_table(d.L_f, Lh, (const int2*)bg.lm_dev, it.npairs, (const int2*)wdev,
+                                         (int)(work.size() / 2), bg.table, b->cs);
+      if (e != cudaSuccess) { record_cuda_error("launch_gaunt_table", e); return SLSHT_E_CUDA; }
+      CK(cudaStreamSynchronize(b->cs));          // `work` leaves scope
+      gf = gkey.emplace(gk, (int)b->gaunt.size()).first;
+      b->gaunt.push_back(std::move(bg));
+    }
+    it.gaunt = gf->second;
+    // k of (signal, Gaunt table)
+    auto ck = std::make_pair((const void*)it.f, it.gaunt);
+    auto cf = ckey.find(ck);
+    if (cf == ckey.end()) {
+      const BatchGaunt& bg = b->gaunt[it.gaunt];
+      BCouple c{};
+      c.f = it.f;
+      c.lm = (const int2*)bg.lm_dev;
+      c.coef = (const double*)bg.table;
+      c.meta = (const int2*)(c.coef + (size_t)it.npairs * Lh * n2);
+      void* kc = nullptr;
+      CKS(batch_alloc(b, sizeof(double2) * (size_t)it.npairs * n2, &kc));
+      c.kc = (double2*)kc;
+      c.Lh = Lh;
+      c.npairs = it.npairs;
+      const int ci = (int)b->cpl.size();
+      for (long long f0 = 0; f0 < (long long)it.npairs * n2; f0 += 256) b->cblk.push_back({ci, (int)f0});
+      cf = ckey.emplace(ck, ci).first;
+      b->cpl.push_back(c);
+    }
+    it.cpl = cf->second;
+    // rotated window of (h, L_h, grid rows, precision)
+    auto rk = std::make_tuple((const void*)it.h, Lh, d.n_beta, d.n_gamma, (int)d.prec);
+    auto rf = rkey.find(rk);
+    if (rf == rkey.end()) {
+      BRot r{};
+      r.h = it.h;
+      r.prec = d.prec == SLSHT_FP64 ? 0 : 1;
+      r.Lh = Lh;
+      r.Ng = d.n_gamma;
+      {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        CKS(get_dtab(ctx, Lh, d.n_beta, d.prec, b->cs, &r.dt));
+        CKS(get_phase(ctx, d.n_gamma, K, -(Lh - 1), d.prec, b->cs, &r.eg));
+      }
+      CKS(batch_alloc(b, el2_of(d.prec) * h_elems((size_t)J, n2), &r.H));
+      const size_t sm = rotwin_smem_bytes(Lh, d.n_gamma, el2_of(d.prec));
+      r.smem_ok = sm <= (size_t)BA_SMEM_LIMIT ? 1 : 0;
+      if (r.smem_ok) b->rot_smem = std::max(b->rot_smem, sm);
+      const int ri = (int)b->rot.size();
+      for (int bb = 0; bb < d.n_beta; ++bb)
+        for (int p = 0; p < Lh; ++p) b->rblk.push_back({ri, bb, p, 0});
+      rf = rkey.emplace(rk, ri).first;
+      b->rot.push_back(r);
+    }
+    it.rot = rf->second;
+    if (batch_tc_ok(b, d)) {
+      std::lock_guard<std::mutex> g(ctx->mu);
+      CKS(get_etab(ctx, d.n_alpha, Lh, b->cs, &it.etab));
+    }
+    BItem bi{};
+    bi.kc = b->cpl[it.cpl].kc;
+    bi.H = b->rot[it.rot].H;
+    bi.g = it.g;
+    bi.prec = d.prec == SLSHT_FP64 ? 0 : 1;
+    bi.Lh = Lh;
+    bi.Na = d.n_alpha;
+    bi.J = (int)J;
+    b->bitem.push_back(bi);
+  }
+  // k and H once, for the tuner
+  CKS(batch_upload(b, b->cpl.data(), sizeof(BCouple) * b->cpl.size(), &b->d_cpl));
+  CKS(batch_upload(b, b->cblk.data(), sizeof(BCplBlk) * b->cblk.size(), &b->d_cblk));
+  CKS(batch_upload(b, b->rot.data(), sizeof(BRot) * b->rot.size(), &b->d_rot));
+  CKS(batch_upload(b, b->rblk.data(), sizeof(BRotBlk) * b->rblk.size(), &b->d_rblk));
+  {
+    cudaError_t e = launch_batch_couple((const BCouple*)b->d_cpl, (const BCplBlk*)b->d_cblk, (int)b->cblk.size(),
+                                        b->cs);
+    if (e == cudaSuccess)
+      e = launch_batch_rotwin((const BRot*)b->d_rot, (const BRotBlk*)b->d_rblk, (int)b->rblk.size(), b->rot_smem,
+                              b->cs);
+    if (e != cudaSuccess) { record_cuda_error("batch k / H", e); return SLSHT_E_CUDA; }
+  }
+  // tile shapes
+  for (int32_t i = 0; i < n; ++i) {
+    BatchItemHost& it = b->items[i];
+    CKS(batch_tune(b, i));
+    BItem& bi = b->bitem[i];
+    bi.nt = it.nt;
+    bi.form = std::max(it.form, 0);
+    if (it.form >= 0) CKS(batch_alpha_table(b, it.d, it.form, &bi.csa));
+  }
+  // tiles, largest first
+  for (int pi = 0; pi < 2; ++pi) {
+    std::vector<std::pair<double, BTile>> tl;
+    for (int32_t i = 0; i < n; ++i) {
+      const BatchItemHost& it = b->items[i];
+      if (it.form < 0) continue;
+      if ((it.d.prec == SLSHT_FP64 ? 0 : 1) != pi) continue;
+      const long long J = (long long)it.d.n_beta * it.d.n_gamma;
+      const double cost = (double)it.nt * (4.0 * it.d.L_h * it.d.L_h + it.d.n_alpha * alpha_form_cost(it.d.L_h, it.form));
+      for (int p = 0; p < it.npairs; ++p)
+        for (long long j0 = 0; j0 < J; j0 += it.nt) tl.push_back({cost, BTile{i, p, p, (int)j0}});
+      b->alpha_smem[pi] = std::max(b->alpha_smem[pi], batch_alpha_smem(pi, it.d.L_h, it.nt));
+    }
+    std::stable_sort(tl.begin(), tl.end(), [](const std::pair<double, BTile>& x, const std::pair<double, BTile>& y) {
+      return x.first > y.first;
+    });
+    for (auto& t : tl) b->tiles[pi].push_back(t.second);
+    if (!b->tiles[pi].empty()) {
+      b->alpha_grid[pi] = (int)std::min<long long>(
+          (long long)ctx->num_sms * batch_alpha_occupancy(pi, b->alpha_smem[pi]), (long long)b->tiles[pi].size());
+      CKS(batch_upload(b, b->tiles[pi].data(), sizeof(BTile) * b->tiles[pi].size(), &b->d_tiles[pi]));
+      b->k_alpha++;
+    }
+  }
+  for (int32_t i = 0; i < n; ++i)
+    if (b->items[i].form < 0) { b->tc_items.push_back(i); b->k_alpha++; }
+  CKS(batch_upload(b, b->bitem.data(), sizeof(BItem) * b->bitem.size(), &b->d_bitem));
+  void* ctr = nullptr;
+  CKS(batch_alloc(b, 16, &ctr));
+  b->d_counter = (int*)ctr;
+  b->k_couple = b->cblk.empty() ? 0 : 1;
+  b->k_rot = b->rblk.empty() ? 0 : 1;
+  b->kernels = b->k_couple + b->k_rot + b->k_alpha;
+  // one direct run: every g_out holds its result, and every launch path
+  // (attributes, the tensor-core error word) is set up before the capture
+  CKS(batch_enqueue(b, b->cs));
+  CK(cudaStreamSynchronize(b->cs));
+  if (!(b->flags & SLSHT_BATCH_NO_GRAPH)) {
+    CK(cudaStreamBeginCapture(b->cs, cudaStreamCaptureModeThreadLocal));
+    const int s = batch_enqueue(b, b->cs);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(b->cs, &graph);
+    b->graph = graph;
+    CKS(s);
+    if (e != cudaSuccess) { record_cuda_error("cudaStreamEndCapture", e); return SLSHT_E_CUDA; }
+    CK(cudaGraphInstantiate(&b->exec, b->graph, 0));
+  }
+  CK(cudaEventRecord(b->done, b->cs));
+  CK(cudaStreamSynchronize(b->cs));
+  return SLSHT_OK;
+}
+
+extern "C" int slsht_batch_create(slsht_ctx* ctx, int32_t n_items, const slsht_batch_item* items, int32_t flags,
+                                  void* stream, slsht_batch** out) {
+  if (!out) return SLSHT_E_ARG;
+  *out = nullptr;
+  if (!ctx || !items || n_items < 1) return SLSHT_E_ARG;
+  if (flags & ~(SLSHT_BATCH_NO_GRAPH | SLSHT_BATCH_NO_TUNE | SLSHT_BATCH_NO_TC)) return SLSHT_E_ARG;
+  DeviceGuard g(ctx->device);
+  std::vector<std::vector<int32_t>> lms((size_t)n_items);
+  for (int32_t i = 0; i < n_items; ++i) {
+    const slsht_batch_item& it = items[i];
+    CKS(check_desc(&it.desc));
+    if (it.n_pairs < 1 || !it.lm) return SLSHT_E_ARG;
+    if (!is_device_ptr(it.f_lm) || !is_device_ptr(it.h_lm) || !is_device_ptr(it.g_out)) return SLSHT_E_ARG;
+    if (((uintptr_t)it.g_out) & 15) return SLSHT_E_ARG;
+    if ((long long)it.n_pairs * it.desc.L_h * it.desc.L_h > (1LL << 30)) return SLSHT_E_ARG;
+    lms[i].resize(2 * (size_t)it.n_pairs);
+    if (is_device_ptr(it.lm)) {
+      CK(cudaMemcpy(lms[i].data(), it.lm, sizeof(int32_t) * lms[i].size(), cudaMemcpyDeviceToHost));
+    } else {
+      std::memcpy(lms[i].data(), it.lm, sizeof(int32_t) * lms[i].size());
+    }
+    CKS(check_pairs(&it.desc, lms[i].data(), it.n_pairs));
+  }
+  slsht_batch* b = new slsht_batch();
+  b->ctx = ctx;
+  b->flags = flags;
+  const int s = batch_build(b, items, n_items, (cudaStream_t)stream, lms);
+  if (s != SLSHT_OK) {
+    batch_free(b);
+    return s;
+  }
+  {
+    std::lock_guard<std::mutex> l(ctx->mu);
+    ctx->plans.push_back(b);
+  }
+  *out = b;
+  return SLSHT_OK;
+}
+
+extern "C" int slsht_batch_launch(slsht_batch* b, void* stream) {
+  if (!b) return SLSHT_E_ARG;
+  DeviceGuard g(b->ctx->device);
+  std::lock_guard<std::mutex> l(b->mu);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (b->exec) {
+    CK(cudaGraphLaunch(b->exec, st));
+  } else {
+    CKS(batch_enqueue(b, st));
+  }
+  CK(cudaEventRecord(b->done, st));
+  batch_count(b);
+  return SLSHT_OK;
+}
+
+extern "C" int slsht_batch_query(const slsht_batch* b, int32_t item, int32_t what, int64_t* value) {
+  if (!b || !value) return SLSHT_E_ARG;
+  const bool per_item = what == SLSHT_BQ_TILE_COLS || what == SLSHT_BQ_ALPHA_FORM || what == SLSHT_BQ_TUNED;
+  if (per_item && (item < 0 || item >= (int32_t)b->items.size())) return SLSHT_E_ARG;
+  switch (what) {
+    case SLSHT_BQ_TILE_COLS: *value = b->items[item].form < 0 ? 0 : b->items[item].nt; return SLSHT_OK;
+    case SLSHT_BQ_ALPHA_FORM: *value = b->items[item].form; return SLSHT_OK;
+    case SLSHT_BQ_TUNED: *value = b->items[item].tuned; return SLSHT_OK;
+    case SLSHT_BQ_TILES: *value = (int64_t)(b->tiles[0].size() + b->tiles[1].size()); return SLSHT_OK;
+    case SLSHT_BQ_KERNELS: *value = b->kernels; return SLSHT_OK;
+    case SLSHT_BQ_GRAPH: *value = b->exec ? 1 : 0; return SLSHT_OK;
+    case SLSHT_BQ_BYTES: *value = (int64_t)b->bytes; return SLSHT_OK;
+    case SLSHT_BQ_SAMPLES: *value = (int64_t)b->samples; return SLSHT_OK;
+    default: return SLSHT_E_ARG;
+  }
+}
+
+extern "C" void slsht_batch_destroy(slsht_batch* b) {
+  if (!b) return;
+  slsht_ctx* ctx = b->ctx;
+  DeviceGuard g(ctx->device);
+  {
+    std::lock_guard<std::mutex> l(ctx->mu);
+    auto it = std::find(ctx->plans.begin(), ctx->plans.end(), b);
+    if (it == ctx->plans.end()) return;   // already freed with its context
+    ctx->plans.erase(it);
+  }
+  batch_free(b);
 }
 
 // ---------------------------------------------------------------- serving

@@ -1,0 +1,58 @@
+// Device descriptors and launchers of batch plans: many analyses (signal,
+// window, pair list, grid, precision) evaluated by three launches, each over
+// a host-built work list:
+//   k_batch_couple  the Gaunt gather-sum k_lm(p, q) of every pair of every item,
+//   k_batch_rotwin  every distinct rotated window H (one block per (beta row, degree)),
+//   k_batch_alpha   a persistent kernel (one per precision) whose CTAs take tiles (item, pair,
+//                   column block) from a shared counter: X_q for the tile's
+//                   columns from H and k, then the alpha sum, stored to g.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define BA_THREADS 128           // threads of a k_batch_alpha CTA (columns x row groups)
+#define BA_SMEM_LIMIT (200 * 1024)
+
+struct BCouple {                 // one coupling output (a signal with a pair list)
+  const double2* f;              // signal coefficients
+  const int2* lm;                // pair list (l, m)
+  const double* coef;            // Gaunt table rows [pair][i][t]
+  const int2* meta;              // (first l', count) per [pair][t]
+  double2* kc;                   // k [pair][t]
+  int Lh, npairs;
+};
+struct BCplBlk { int cpl, first; };        // 256 consecutive (pair, t) items of one BCouple
+
+struct BRot {                    // one rotated window H
+  const double2* h;
+  const void* dt;                // d^p(beta_b) table [b][blk_off(Lh)], T
+  const void* eg;                // gamma phases [c][2Lh-1], T2
+  void* H;                       // tiled H (h_index), T2
+  int prec, Lh, Ng, smem_ok;     // prec 0: FP64, 1: FP32
+};
+struct BRotBlk { int rot, b, p, pad; };
+
+struct BItem {                   // one analysis of the batch (alpha stage view)
+  const double2* kc;             // k [pair][Lh^2]
+  const void* H;                 // tiled H, T2
+  const void* csa;               // form 0: (cos, sin)(2 pi r a / Na) [a][Lh]; P: split twiddles [t][2Lh-1]
+  void* g;                       // output [pair][a][j], T2
+  int prec, Lh, Na, J;
+  int nt;                        // columns per tile: 32, 64 or 128 (BA_THREADS / nt row groups)
+  int form;                      // 0: direct sum, 3/5/7/9: split DFT with that factor
+};
+struct BTile { int item, pair, out, j0; };  // k of `pair`, output slot `out`, columns j0 .. j0+nt-1
+
+// Shared memory of a k_batch_alpha tile: X_q for nt columns.
+size_t batch_alpha_smem(int prec, int Lh, int nt);
+// Resident CTAs of k_batch_alpha (precision prec) per SM with `smem` bytes of
+// dynamic shared memory.
+int batch_alpha_occupancy(int prec, size_t smem);
+
+cudaError_t launch_batch_couple(const BCouple* cpl, const BCplBlk* blk, int nblk, cudaStream_t st);
+cudaError_t launch_batch_rotwin(const BRot* rot, const BRotBlk* blk, int nblk, size_t smem, cudaStream_t st);
+// Persistent: `grid` CTAs take tiles from *counter (reset to 0 before each
+// launch); every tile's item has precision prec.
+cudaError_t launch_batch_alpha(int prec, const BItem* items, const BTile* tiles, int ntiles, int* counter, int grid,
+                               size_t smem, cudaStream_t st);

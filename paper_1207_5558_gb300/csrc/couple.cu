@@ -3,7 +3,7 @@
 //   T(l',m';p,q;l,m) = (-1)^m sqrt((2l'+1)(2p+1)(2l+1)/(4 pi))
 //                      (l' p l; 0 0 0) (l' p l; m' q -m),
 // with both Wigner-3j families generated by recurrences in l' (= j1) in FP64.
-#include "common.cuh"
+#include "couple_dev.cuh"
 
 // 1/x for a positive integer-valued x: float reciprocal refined by two
 // Newton-Raphson steps, r <- r (2 - x r), to full double precision.
@@ -259,7 +259,8 @@ __global__ void __launch_bounds__(256) k_gaunt_table(int Lf, int Lh, const int2*
 }
 
 // k_lm(p, q) from the table: one thread per (pair, t), coefficient rows
-// read coalesced across t, f gathered (L2 resident).
+// read coalesced across t, f gathered (L2 resident); body couple_apply_one
+// (couple_dev.cuh).
 __global__ void __launch_bounds__(256) k_couple_apply(const double2* __restrict__ f, int Lh, const int2* __restrict__ lm,
                                                       const double* __restrict__ coef, const int2* __restrict__ meta,
                                                       int npairs, double2* __restrict__ kc) {
@@ -267,22 +268,7 @@ __global__ void __launch_bounds__(256) k_couple_apply(const double2* __restrict_
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)npairs * n2) return;
   const int pair = (int)(idx / n2), t = (int)(idx % n2);
-  int p = (int)sqrtf((float)t);
-  while (p * p > t) --p;
-  while ((p + 1) * (p + 1) <= t) ++p;
-  const int q = t - p * p - p;
-  const int mu = lm[pair].y - q;
-  const int2 md = meta[idx];
-  double2 acc = make_double2(0.0, 0.0);
-  const double* c = coef + (size_t)pair * Lh * n2 + t;
-  for (int i = 0; i < md.y; ++i) {
-    const int j1 = md.x + 2 * i;
-    const double ci = c[(size_t)i * n2];
-    const double2 fv = __ldg(f + j1 * j1 + j1 + mu);
-    acc.x = fma(ci, fv.x, acc.x);
-    acc.y = fma(ci, fv.y, acc.y);
-  }
-  kc[idx] = acc;
+  kc[idx] = couple_apply_one(f, Lh, lm[pair].y, coef + (size_t)pair * Lh * n2, meta[idx], t);
 }
 
 size_t gaunt_table_bytes(int Lh, int npairs) {

@@ -13,7 +13,7 @@
 // stage consumes.
 #include <algorithm>
 
-#include "common.cuh"
+#include "stages_dev.cuh"
 
 // ---------------------------------------------------------------------------
 // C_{q,q',q''} = i^{q-q'} sum_{p >= max(|q|,|q'|,|q''|)} Delta^p_{q''q} Delta^p_{q''q'} k(p,q) h_p^{q'}
@@ -264,45 +264,15 @@ __global__ void k_rotwin(const double2* __restrict__ h, const T* __restrict__ dt
   }
 }
 
-// The same H with one CTA per (beta row b, degree p): the (2p+1)^2 products
-// h_p^{q'} d^p_{q,q'}(beta_b) and the gamma phases of the orders |q'| <= p are
-// staged in shared memory once, then each output (q, c) is a (2p+1)-term dot
-// product read from shared memory (a warp shares q: broadcast rows of the
-// products, odd-stride phase rows without bank conflicts).
+// The same H with one CTA per (beta row b, degree p): rotwin_block_smem
+// (stages_dev.cuh).
 template <typename T>
 __global__ void __launch_bounds__(128) k_rotwin_smem(const double2* __restrict__ h, const T* __restrict__ dt,
                                                      const typename vec2<T>::t* __restrict__ eg, int Lh, int Nb,
                                                      int Ng, typename vec2<T>::t* __restrict__ H) {
-  typedef typename vec2<T>::t T2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int K = 2 * Lh - 1, S = blk_off(Lh), n2 = Lh * Lh;
-  const int b = blockIdx.x, p = blockIdx.y, w = 2 * p + 1;
-  T2* hd = reinterpret_cast<T2*>(smem_raw);   // [q + p][q' + p]
-  T2* ep = hd + w * w;                        // [c][q' + p]
-  const T* dblk = dt + (size_t)b * S + blk_off(p);
-  for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
-    const int qp = t % w;
-    const double2 hv = __ldg(h + p * p + qp);
-    const T d = __ldg(dblk + t);
-    hd[t] = mk2(d * (T)hv.x, d * (T)hv.y);
-  }
-  for (int t = threadIdx.x; t < Ng * w; t += blockDim.x) {
-    const int c = t / w, qp = t % w;
-    ep[t] = eg[(size_t)c * K + (Lh - 1) - p + qp];
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < w * Ng; t += blockDim.x) {
-    const int qi = t / Ng, c = t % Ng;
-    const T2* hr = hd + qi * w;
-    const T2* er = ep + c * w;
-    T re = 0, im = 0;
-    for (int u = 0; u < w; ++u) {                // h d (cos - i sin)
-      const T2 a = hr[u], E = er[u];
-      re = fma(a.x, E.x, re); re = fma(a.y, E.y, re);
-      im = fma(a.y, E.x, im); im = fma(-a.x, E.y, im);
-    }
-    H[h_index(p * p + qi, b * Ng + c, n2)] = mk2(re, im);
-  }
+  const int b = blockIdx.x, p = blockIdx.y;
+  rotwin_block_smem<T>(h, dt + (size_t)b * blk_off(Lh) + blk_off(p), eg, Lh, Ng, b, p, H, smem_raw);
 }
 
 template <typename T>
