@@ -157,18 +157,22 @@ def traffic_record(kernel):
     return d if d.get("source_sha256_16") == h else None
 
 
-def alpha_fp64_cost(Lh, Na):
+def alpha_fp64_cost(Lh, Na, P=None):
     """FP64 work of the CUDA-core alpha stage per output sample, for the form
-    the library picks (the same rule as alpha_split_factor in csrc/alpha.cu):
+    the library picks (the same rule as alpha_split_factor in csrc/alpha.cu),
+    or for split factor P (0: direct sum) when given:
     (P, FP64 instructions, flops, description)."""
     K = 2 * Lh - 1
     direct = 4.0 * (Lh - 1) + 2.0
     best, cost = 0, direct
-    for P in (9, 7, 5, 3):
-        if Na % P == 0:
-            c = 4.0 * K / P + P + 3.0
-            if c < cost:
-                best, cost = P, c
+    if P is not None:
+        best = P
+    else:
+        for P in (9, 7, 5, 3):
+            if Na % P == 0:
+                c = 4.0 * K / P + P + 3.0
+                if c < cost:
+                    best, cost = P, c
     if best == 0:
         return 0, direct, 2 * direct, "direct sum, +-q paired"
     H = (best - 1) // 2
@@ -567,6 +571,90 @@ def main():
         ctx.set_option(pkg.SLSHT_OPT_COUPLING, 0)
         return out
 
+    def batch_leg():
+        """Batch plans (slsht_batch_*): (a) the first 48 requests of the
+        serving workload (up to 40 GB of g) as one plan -- one persistent
+        alpha kernel per precision, a captured graph, tuned tile shapes --
+        against the same requests as slsht_forward calls on one stream, and
+        against a plan with the built-in tile rule; (b) the FP64 path of
+        workload 3 as one plan of the four maps (their outputs share one
+        map-sized buffer: every sample is still computed and stored)."""
+        def ev_ms(fn, reps):
+            fn()
+            barrier()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                fn()
+            b.record(stream)
+            b.synchronize()
+            return a.elapsed_time(b) / reps
+        out = {}
+        reqs = serve_requests(48, 4000)
+        items, tot = [], 0
+        for r in reqs:
+            by = len(r["pairs"]) * int(np.prod(r["grid"])) * (16 if r["prec"] == 0 else 8)
+            if tot + by > (40 << 30):
+                continue
+            tot += by
+            items.append({"L_f": r["Lf"], "L_h": r["Lh"], "grid": r["grid"], "prec": r["prec"],
+                          "f": torch.from_numpy(r["f"]).cuda(), "h": torch.from_numpy(r["h"]).cuda(),
+                          "lm": r["pairs"]})
+        t0 = time.perf_counter()
+        bp = ctx.batch(items, stream=stream)
+        create_s = time.perf_counter() - t0
+        for it, g in zip(items, bp.outputs):
+            it["g_out"] = g
+        smp = bp.query(pkg.SLSHT_BQ_SAMPLES)
+        ms_plan = ev_ms(lambda: bp.launch(stream), 3)
+
+        def per_call():
+            for it in items:
+                pkg.slsht_forward(ctx.h, pkg.make_desc(it["L_f"], it["L_h"], it["grid"], it["prec"]), it["f"],
+                                  it["h"], np.ascontiguousarray(it["lm"]), len(it["lm"]), it["g_out"], stream)
+        ms_call = ev_ms(per_call, 2)
+        br = ctx.batch(items, flags=pkg.SLSHT_BATCH_NO_TUNE, stream=stream)
+        ms_rule = ev_ms(lambda: br.launch(stream), 3)
+        forms = sorted({(it["L_h"], it["prec"], bp.query(pkg.SLSHT_BQ_TILE_COLS, i), bp.query(pkg.SLSHT_BQ_ALPHA_FORM, i))
+                        for i, it in enumerate(items)})
+        out["serving_mix"] = {
+            "requests": len(items), "samples": smp, "g_bytes": tot, "create_s": create_s,
+            "plan_ms": ms_plan, "per_call_ms": ms_call, "rule_plan_ms": ms_rule,
+            "value_plan": smp / (ms_plan / 1e3), "value_per_call": smp / (ms_call / 1e3),
+            "speedup_vs_per_call": ms_call / ms_plan, "tuner_gain_vs_rule": ms_rule / ms_plan,
+            "kernels_per_launch": bp.query(pkg.SLSHT_BQ_KERNELS), "tiles": bp.query(pkg.SLSHT_BQ_TILES),
+            "tile_choices": [{"L_h": a, "prec": "fp64" if b_ == 0 else "fp32", "cols": c_,
+                              "alpha": "tensor cores" if fm < 0 else ("direct" if fm == 0 else "split P=%d" % fm)}
+                             for a, b_, c_, fm in forms]}
+        bp.close()
+        br.close()
+        del items
+        torch.cuda.empty_cache()
+        # FP64 workload 3 as one plan
+        g64 = torch.empty((npairs_map,) + grid, dtype=torch.complex128, device="cuda")
+        items = [{"L_f": Lf, "L_h": Lh, "grid": grid, "prec": 0, "f": fd, "h": hd, "lm": pd.cpu().numpy(),
+                  "g_out": g64} for fd, hd, pd in dev_inputs]
+        t0 = time.perf_counter()
+        bp = ctx.batch(items, stream=stream)
+        create_s = time.perf_counter() - t0
+        smp = bp.query(pkg.SLSHT_BQ_SAMPLES)
+        ms = ev_ms(lambda: bp.launch(stream), 2)
+        fm = bp.query(pkg.SLSHT_BQ_ALPHA_FORM, 0)
+        P, instr, flops, form = alpha_fp64_cost(Lh, grid[0], fm if fm > 0 else 0)
+        x_instr = 4.0 * Lh * Lh / grid[0]
+        rate = smp / (ms / 1e3)
+        out["fp64_workload3"] = {
+            "value": rate, "unit": UNIT, "ms_per_step": ms, "create_s": create_s,
+            "tile_cols": bp.query(pkg.SLSHT_BQ_TILE_COLS, 0), "alpha_form": form,
+            "fp64_instructions_per_sample": instr + x_instr,
+            "fp64_pipe_frac": rate * (instr + x_instr) / 0.625e12,
+            "note": "X (4 L_h^2 / N_alpha FMA a sample) and the alpha sum in one persistent kernel; the "
+                    "fraction counts FP64 FMA/add instructions over the 0.625e12/s FMA pipe"}
+        bp.close()
+        del g64
+        torch.cuda.empty_cache()
+        return out
+
     # ---------------- FP32_BULK headline
     g32 = torch.empty((npairs_map,) + grid, dtype=torch.complex64, device="cuda")
     ms32, st32, clk = timed(1, g32, args.steps, args.warmup, ClockSampler(local))
@@ -626,10 +714,12 @@ def main():
     torch.cuda.empty_cache()
     win_gen = None
     coup = None
+    batch = None
     if args.fp64_steps > 0:
         wins = windows_leg()
         win_gen = window_leg()
         coup = coupling_leg()
+        batch = batch_leg()
 
     # ---------------- e2e through the C ABI with host buffers
     e2e = None
@@ -694,6 +784,7 @@ def main():
             "multi_window": wins,
             "window_generator": win_gen,
             "coupling_routes": coup,
+            "batch_plans": batch,
             "serve": serve,
         }
         print(json.dumps(line), flush=True)
