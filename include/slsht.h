@@ -72,7 +72,10 @@ extern "C" {
 typedef struct slsht_ctx slsht_ctx;   /* opaque; one device, owns tables */
 
 typedef enum {
-  SLSHT_FP64 = 0,       /* every stage in FP64; g is complex128            */
+  SLSHT_FP64 = 0,       /* FP64 accuracy (relative error <= 1e-12): 3j,
+                           Delta, coupling and rotated window in FP64, X and
+                           the alpha sum in FP64 or double-float arithmetic
+                           (SLSHT_OPT_FP64_ARITH); g is complex128           */
   SLSHT_FP32_BULK = 1   /* 3j, Delta, phases in FP64; coupling in FP64;
                            beta/gamma sums in FP32; alpha stage on tcgen05
                            tensor cores (split-FP16 operands, FP32
@@ -247,6 +250,8 @@ typedef struct slsht_batch slsht_batch;   /* opaque plan */
 #define SLSHT_BATCH_NO_TUNE  2   /* tile shapes from the built-in rule instead of
                                     timing the candidates */
 #define SLSHT_BATCH_NO_TC    4   /* keep FP32_BULK items on CUDA cores */
+#define SLSHT_BATCH_NO_DD    8   /* FP64 items in FP64 arithmetic only */
+#define SLSHT_BATCH_FP64_DD 16   /* FP64 items in double-float arithmetic only */
 
 /* Plan many analyses (maps, windows, requests of uneven band limits and grids)
  * as one unit.  Per launch the plan runs: the Gaunt gather-sum of every pair
@@ -262,9 +267,16 @@ typedef struct slsht_batch slsht_batch;   /* opaque plan */
  *  - Tile shapes: for every distinct (precision, L_h, N_alpha, N_beta,
  *    N_gamma) the autotuner times each candidate (columns per tile 32/64/128;
  *    direct alpha sum or split DFT with each odd factor 3/5/7/9 of N_alpha;
- *    for FP32_BULK the fused tensor-core kernel) on the item's own data into
+ *    for FP32_BULK the fused tensor-core kernel; for FP64 the X and alpha
+ *    sums in FP64 or in double-float arithmetic) on the item's own data into
  *    plan scratch, and keeps the fastest per sample.  The choice is cached in
  *    the context for later plans of the same shape.
+ *  - Double-float engine (FP64 items): X and the alpha sum carried as pairs of
+ *    floats (about 48 significant bits, from exact TwoProd/TwoSum steps on the
+ *    FP32 pipe, which GB300 issues at 64 times its FP64 rate), k and the
+ *    rotated window scaled by powers of two into the float range, every g
+ *    sample assembled as a double with its scale: relative L2 error about
+ *    1e-14, inside the FP64 path's 1e-12.
  *  - Memory: tables, k, the rotated windows and the tile lists are plan-owned
  *    and counted against the context's budget.
  *  - Creation is synchronous: it waits for `stream` (so f and h may be
@@ -293,6 +305,8 @@ int slsht_batch_launch(slsht_batch* batch, void* stream);
  *  SLSHT_BQ_GRAPH      1 if launches replay a CUDA graph (item ignored)
  *  SLSHT_BQ_BYTES      device memory the plan holds (item ignored)
  *  SLSHT_BQ_SAMPLES    g samples per launch (item ignored)
+ *  SLSHT_BQ_ENGINE     item's arithmetic: 0 its precision on CUDA cores, 1
+ *                      double-float on CUDA cores (FP64 items), 2 tensor cores
  * Returns SLSHT_OK or SLSHT_E_ARG. */
 #define SLSHT_BQ_TILE_COLS  1
 #define SLSHT_BQ_ALPHA_FORM 2
@@ -302,6 +316,7 @@ int slsht_batch_launch(slsht_batch* batch, void* stream);
 #define SLSHT_BQ_GRAPH      6
 #define SLSHT_BQ_BYTES      7
 #define SLSHT_BQ_SAMPLES    8
+#define SLSHT_BQ_ENGINE     9
 int slsht_batch_query(const slsht_batch* batch, int32_t item, int32_t what, int64_t* value);
 
 /* Wait for the plan's last launch and free everything it holds.  NULL is a
@@ -398,6 +413,13 @@ int slsht_get_stats(slsht_ctx* ctx, slsht_stats* out, int reset);
  *                            window band is wide and the signal band narrow;
  *                            rounding limits it to ~1e-11 relative near
  *                            l = 255.
+ *  SLSHT_OPT_FP64_ARITH   FP64 calls on the rotated-window route: 0 (default)
+ *                            X and the alpha sum in double-float arithmetic
+ *                            (pairs of floats from exact TwoProd/TwoSum steps
+ *                            on the FP32 pipe, about 48 significant bits;
+ *                            tables, 3j, coupling and the rotated window in
+ *                            FP64; relative error about 1e-14); 1: FP64
+ *                            arithmetic throughout.
  * Returns SLSHT_OK or SLSHT_E_ARG. */
 #define SLSHT_OPT_BETA_ROUTE   1
 #define SLSHT_OPT_ALPHA_ENGINE 2
@@ -406,6 +428,7 @@ int slsht_get_stats(slsht_ctx* ctx, slsht_stats* out, int reset);
 #define SLSHT_OPT_WAIT_TEST    5
 #define SLSHT_OPT_REAL_FIELDS  6
 #define SLSHT_OPT_COUPLING     7
+#define SLSHT_OPT_FP64_ARITH   8
 int slsht_set_option(slsht_ctx* ctx, int option, int64_t value);
 
 /* Bytes of device memory the context currently holds. */

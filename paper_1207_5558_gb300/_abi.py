@@ -29,10 +29,13 @@ SLSHT_OPT_GAUNT_TABLE = 4
 SLSHT_OPT_WAIT_TEST = 5
 SLSHT_OPT_REAL_FIELDS = 6
 SLSHT_OPT_COUPLING = 7
+SLSHT_OPT_FP64_ARITH = 8
 
 SLSHT_BATCH_NO_GRAPH = 1
 SLSHT_BATCH_NO_TUNE = 2
 SLSHT_BATCH_NO_TC = 4
+SLSHT_BATCH_NO_DD = 8
+SLSHT_BATCH_FP64_DD = 16
 
 SLSHT_BQ_TILE_COLS = 1
 SLSHT_BQ_ALPHA_FORM = 2
@@ -42,6 +45,7 @@ SLSHT_BQ_KERNELS = 5
 SLSHT_BQ_GRAPH = 6
 SLSHT_BQ_BYTES = 7
 SLSHT_BQ_SAMPLES = 8
+SLSHT_BQ_ENGINE = 9
 
 SLSHT_NSTAGES = 8
 SLSHT_NOALLOC_SCRATCH_BYTES = 32 << 20

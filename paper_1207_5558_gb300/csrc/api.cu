@@ -127,6 +127,11 @@ struct Workspace {
   std::vector<int32_t> rf_lm, rf_slots;
   void* rfs = nullptr; size_t rfs_cap = 0;
   void* ms = nullptr; size_t ms_cap = 0;     // modulated-SHT coupling scratch
+  // double-float FP64 engine: scaled k, its exponents, the scaled window, its exponent
+  void* kdd = nullptr; size_t kdd_cap = 0;
+  void* kexp = nullptr; size_t kexp_cap = 0;
+  void* Hdd = nullptr; size_t Hdd_cap = 0;
+  void* hexp = nullptr; size_t hexp_cap = 0;
   std::vector<int32_t> gt_work;              // host copy (source of the upload)
   bool gt_valid = false;
   int gt_Lf = 0, gt_Lh = 0;
@@ -175,12 +180,13 @@ struct slsht_ctx {
   std::map<std::tuple<int, int, int, int>, TableEntry> phase;       // N, R, r0, prec
   std::map<int, TableEntry> wbeta;                                  // Nb
   std::map<std::tuple<int, int>, TableEntry> etab;                  // Na, Lh (tensor-core E blobs)
-  // batch-plan autotuner: (prec, Lh, Na, Nb, Ng, tensor cores allowed) -> (columns per tile, alpha form)
-  std::map<std::tuple<int, int, int, int, int, int>, std::pair<int, int>> tune;
+  // batch-plan autotuner: (prec, Lh, Na, Nb, Ng, engines allowed) -> (columns per tile, alpha form, engine)
+  std::map<std::tuple<int, int, int, int, int, int>, std::tuple<int, int, int>> tune;
   std::vector<slsht_batch*> plans;   // live batch plans (freed by slsht_destroy at the latest)
   Workspace sync_ws;
   int opt_beta_route = 0, opt_alpha_engine = 0, opt_gaunt_table = 0, opt_wait_test = 0, opt_real_fields = 0;
   int opt_coupling = 0;
+  int opt_fp64_arith = 0;
   int64_t opt_chunk = 0;
   bool profile = false;
   std::vector<ProfRec> prof;
@@ -302,6 +308,10 @@ static void ws_release(slsht_ctx* c, Workspace& w) {
   ctx_free(c, w.gtw, w.gtw_cap);
   ctx_free(c, w.rfs, w.rfs_cap);
   ctx_free(c, w.ms, w.ms_cap);
+  ctx_free(c, w.kdd, w.kdd_cap);
+  ctx_free(c, w.kexp, w.kexp_cap);
+  ctx_free(c, w.Hdd, w.Hdd_cap);
+  ctx_free(c, w.hexp, w.hexp_cap);
   w.gt_valid = false;
   for (int i = 0; i < 2; ++i) ctx_free(c, w.stage[i], w.stage_cap[i]);
   for (int i = 0; i < 2; ++i) {
@@ -363,6 +373,8 @@ struct StageTimer {
   } while (0)
 
 // ---------------------------------------------------------------- tables
+#define PREC_DD 2   // internal table precision: double-float pairs (batch plans' FP64 engine)
+
 static int make_entry(slsht_ctx* c, TableEntry& e, size_t bytes) {
   CKS(ctx_alloc(c, bytes, &e.ptr));
   e.bytes = bytes;
@@ -416,11 +428,13 @@ static int get_phase(slsht_ctx* ctx, int N, int R, int r0, int prec, cudaStream_
   auto it = ctx->phase.find(key);
   if (it == ctx->phase.end()) {
     TableEntry e;
-    const size_t el = prec == SLSHT_FP64 ? sizeof(double2) : sizeof(float2);
+    // prec PREC_DD: double-float pairs {cos.h, sin.h, cos.l, sin.l}
+    const size_t el = prec == SLSHT_FP32_BULK ? sizeof(float2) : 16;
     CKS(make_entry(ctx, e, el * (size_t)N * R));
     ctx->launches[SLSHT_STAGE_TABLES]++;
     cudaError_t er = prec == SLSHT_FP64 ? launch_phase_f64((double2*)e.ptr, N, R, r0, st)
-                                        : launch_phase_f32((float2*)e.ptr, N, R, r0, st);
+                     : prec == SLSHT_FP32_BULK ? launch_phase_f32((float2*)e.ptr, N, R, r0, st)
+                                               : launch_phase_dd((float4*)e.ptr, N, R, r0, st);
     if (er != cudaSuccess) { record_cuda_error("launch_phase", er); return SLSHT_E_CUDA; }
     CK(cudaEventRecord(e.ready, st));
     it = ctx->phase.emplace(key, e).first;
@@ -556,6 +570,10 @@ extern "C" int slsht_set_option(slsht_ctx* c, int option, int64_t v) {
       if (v < 0 || v > 2) return SLSHT_E_ARG;
       c->opt_coupling = (int)v;
       return SLSHT_OK;
+    case SLSHT_OPT_FP64_ARITH:
+      if (v < 0 || v > 1) return SLSHT_E_ARG;
+      c->opt_fp64_arith = (int)v;
+      return SLSHT_OK;
     default:
       return SLSHT_E_ARG;
   }
@@ -611,6 +629,14 @@ static void mirror_work(const int32_t* lm, int32_t n, std::vector<int32_t>* out)
   }
 }
 
+// Columns per tile of the double-float alpha kernel by rule: the smallest of
+// 32/64/128 covering min(J, 128) whose X tile fits the shared-memory limit.
+static int dd_rule_cols(int Lh, long long J) {
+  int nt = J <= 32 ? 32 : (J <= 64 ? 64 : 128);
+  while (nt > 32 && batch_alpha_smem(2, Lh, nt) > BA_SMEM_LIMIT) nt /= 2;
+  return nt;
+}
+
 // The forward transform on workspace `w` and stream `st` (ctx->mu NOT held).
 // slots (device, nullable): per listed pair {output slot, mirror} (see
 // launch_alpha_tc); g_out must then be device memory.
@@ -625,8 +651,9 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
   const bool host_out = !is_device_ptr(g_out);
   CK(cudaStreamWaitEvent(st, w.done, 0));
 
-  int route, tc, engine, gt_opt, wait_test, coupling;
+  int route, tc, engine, gt_opt, wait_test, coupling, fp64_arith;
   int64_t chunk_opt;
+  int dd_nt = 0, dd_form = -1;
   {
     std::lock_guard<std::mutex> g(ctx->mu);
     route = ctx->opt_beta_route ? ctx->opt_beta_route : 1;
@@ -636,6 +663,13 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
     gt_opt = ctx->opt_gaunt_table;
     wait_test = ctx->opt_wait_test;
     coupling = ctx->opt_coupling;
+    fp64_arith = ctx->opt_fp64_arith;
+    // a tile shape the batch-plan tuner measured for this FP64 shape, if any
+    auto tf = ctx->tune.find(std::make_tuple((int)SLSHT_FP64, Lh, Na, Nb, Ng, 6));
+    if (tf != ctx->tune.end() && std::get<2>(tf->second) == 1) {
+      dd_nt = std::get<0>(tf->second);
+      dd_form = std::get<1>(tf->second);
+    }
   }
   // rotated-window route on the tensor cores: producer and alpha stage fused
   // into one kernel unless the separate producer kernel was asked for
@@ -643,6 +677,16 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
   // CUDA-core alpha stage: split DFT over the alpha index when Na has a small
   // odd factor that saves work (SLSHT_OPT_ALPHA_ENGINE 4 forces the direct sum)
   const bool split = !tc && engine != 4 && alpha_split_factor(Lh, Na) > 0;
+  // FP64, rotated-window route: X and the alpha sum in double-float
+  // arithmetic (one kernel over (pair, column block) tiles, no X scratch)
+  // unless SLSHT_OPT_FP64_ARITH asks for FP64 arithmetic
+  const bool ddx = f64 && route == 1 && fp64_arith == 0;
+  if (ddx) {
+    if (dd_form < 0 || (engine == 4 && dd_form != 0)) {
+      dd_nt = dd_rule_cols(Lh, (long long)J);
+      dd_form = engine == 4 ? 0 : alpha_split_factor(Lh, Na);
+    }
+  }
   // tables
   const double* D = nullptr;
   const void* dt = nullptr;
@@ -655,6 +699,8 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
     if (route == 1) CKS(get_dtab(ctx, Lh, Nb, d->prec, st, &dt));
     CKS(get_phase(ctx, Ng, K, -(Lh - 1), d->prec, st, &eg));
     if (tc) CKS(get_etab(ctx, Na, Lh, st, &etab));
+    else if (ddx && dd_form > 0) CKS(get_phase(ctx, Na, K, -(Lh - 1), PREC_DD, st, &csa));
+    else if (ddx) CKS(get_phase(ctx, Na, Lh, 0, PREC_DD, st, &csa));
     else if (split) CKS(get_phase(ctx, Na, K, -(Lh - 1), d->prec, st, &csa));   // twiddles of the split DFT
     else CKS(get_phase(ctx, Na, Lh, 0, d->prec, st, &csa));
   }
@@ -669,7 +715,7 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
   int P;
   if (chunk_opt > 0) {
     P = (int)std::min<int64_t>(chunk_opt, n_pairs);
-  } else if (fused) {
+  } else if (fused || ddx) {
     P = n_pairs;                 // no X scratch: one launch per call
   } else {
     const size_t target = (size_t)96 << 20;
@@ -682,12 +728,19 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
     P = (int)std::max<size_t>(1, std::min<size_t>((size_t)P, stage_limit / std::max<size_t>(1, per_pair_g)));
   }
   CKS(ws_reserve(ctx, w, &w.kc, &w.kc_cap, sizeof(double2) * (size_t)n_pairs * Lh * Lh));
-  if (!fused) {
+  if (!fused && !ddx) {
     CKS(ws_reserve(ctx, w, &w.X, &w.X_cap, x_per_pair * (size_t)P));
     CKS(ws_reserve(ctx, w, &w.X2, &w.X2_cap, x_per_pair * (size_t)P));
   }
   const size_t el2 = f64 ? sizeof(double2) : sizeof(float2);
-  if (route == 1) CKS(ws_reserve(ctx, w, &w.H, &w.H_cap, el2 * h_elems(J, Lh * Lh)));
+  if (ddx) {
+    CKS(ws_reserve(ctx, w, &w.kdd, &w.kdd_cap, sizeof(float4) * (size_t)n_pairs * Lh * Lh));
+    CKS(ws_reserve(ctx, w, &w.kexp, &w.kexp_cap, sizeof(int) * (size_t)n_pairs));
+    CKS(ws_reserve(ctx, w, &w.Hdd, &w.Hdd_cap, sizeof(float4) * h_elems(J, Lh * Lh)));
+    CKS(ws_reserve(ctx, w, &w.hexp, &w.hexp_cap, 16));
+  } else if (route == 1) {
+    CKS(ws_reserve(ctx, w, &w.H, &w.H_cap, el2 * h_elems(J, Lh * Lh)));
+  }
   if (route == 2) {
     CKS(ws_reserve(ctx, w, &w.C, &w.C_cap, sizeof(double2) * (size_t)P * K * K * K));
     CKS(ws_reserve(ctx, w, &w.Y, &w.Y_cap, sizeof(double2) * (size_t)P * Nb * K * K));
@@ -742,7 +795,13 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
            launch_couple((const double2*)f_dev, Lf, Lh, (const int2*)lm_dev, n_pairs, (double2*)w.kc, ax));
   }
   // route 1: the window rotated to every (beta, gamma) sample, once per call
-  if (route == 1) {
+  if (ddx) {
+    LAUNCH(SLSHT_STAGE_COUPLE, ax,
+           launch_kdd_pairs((const double2*)w.kc, Lh, n_pairs, (float4*)w.kdd, (int*)w.kexp, ax));
+    LAUNCH(SLSHT_STAGE_BETA, ax,
+           launch_rotwin_dd((const double2*)h_dev, (const double*)dt, (const double2*)eg, Lh, Nb, Ng,
+                            (float4*)w.Hdd, (int*)w.hexp, ax));
+  } else if (route == 1) {
     if (f64)
       LAUNCH(SLSHT_STAGE_BETA, ax,
              launch_rotwin_f64((const double2*)h_dev, (const double*)dt, (const double2*)eg, Lh, Nb, Ng,
@@ -758,7 +817,7 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
     const int np = std::min<int>(P, n_pairs - off);
     void* X = Xb[ci & 1];
     const double2* kcc = (const double2*)w.kc + (size_t)off * Lh * Lh;
-    if (fused) {
+    if (fused || ddx) {
       // every chunk reads the couplings and H that the aux stream produced once
       if (ci == 0) {
         CK(cudaEventRecord(w.x_ready[0], ax));
@@ -808,7 +867,23 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
       gdst = slots != nullptr ? g_out : (void*)((char*)g_out + per_pair_g * (size_t)off);
     }
     const int2* sl = slots != nullptr ? slots + off : nullptr;
-    if (fused) {
+    if (ddx) {
+      BItem item{};
+      item.H = w.Hdd;
+      item.csa = csa;
+      item.g = gdst;
+      item.kdd = (const float4*)w.kdd + (size_t)off * Lh * Lh;
+      item.kexp = (const int*)w.kexp + off;
+      item.hexp = (const int*)w.hexp;
+      item.slots = sl;
+      item.prec = 2;
+      item.Lh = Lh;
+      item.Na = Na;
+      item.J = (int)J;
+      item.nt = dd_nt;
+      item.form = dd_form;
+      LAUNCH(SLSHT_STAGE_ALPHA, st, launch_alpha_dd_call(item, np, ctx->num_sms, st));
+    } else if (fused) {
       LAUNCH(SLSHT_STAGE_ALPHA, st,
              launch_alpha_fused(kcc, (const float2*)w.H, etab, Lh, Na, Nb, Ng, np, (float2*)gdst, ctx->num_sms,
                                 ci == 0 ? wait_test : 0, sl, st));
@@ -832,7 +907,7 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
                    : launch_alpha_f32((const float2*)X, (const float2*)csa, Lh, Na, (int)J, np, (float2*)gdst, sl,
                                       st));
     }
-    if (!fused) CK(cudaEventRecord(w.x_free[ci & 1], st));
+    if (!fused && !ddx) CK(cudaEventRecord(w.x_free[ci & 1], st));
     if (host_out) {
       CK(cudaEventRecord(w.stage_ev[ci & 1], st));
       CK(cudaStreamWaitEvent(w.copy_stream, w.stage_ev[ci & 1], 0));
@@ -1060,8 +1135,13 @@ struct BatchItemHost {
   int npairs = 0;
   int gaunt = -1, cpl = -1, rot = -1;
   int nt = 0, form = 0, tuned = 0;     // form -1: fused tensor-core kernel
+  int engine = 0;                      // 0 CUDA cores in the item's precision, 1 double-float, 2 tensor cores
   const void* etab = nullptr;
 };
+
+#define ENG_NATIVE 0
+#define ENG_DD 1
+#define ENG_TC 2
 
 struct BatchGaunt {
   int Lf = 0, Lh = 0;
@@ -1086,14 +1166,16 @@ struct slsht_batch {
   std::vector<BCplBlk> cblk;
   std::vector<BRot> rot;
   std::vector<BRotBlk> rblk;
+  std::vector<BCplBlk> kblk;            // double-float k: {couple, pair}
   std::vector<BItem> bitem;             // alpha view of every item (index = item)
-  std::vector<BTile> tiles[2];          // CUDA-core tiles per precision (0 FP64, 1 FP32)
+  std::vector<BTile> tiles[3];          // CUDA-core tiles per kernel (0 FP64, 1 FP32, 2 double-float)
   std::vector<int> tc_items;
   void *d_cpl = nullptr, *d_cblk = nullptr, *d_rot = nullptr, *d_rblk = nullptr, *d_bitem = nullptr;
-  void* d_tiles[2] = {nullptr, nullptr};
-  int* d_counter = nullptr;             // one tile counter per precision
-  size_t rot_smem = 0, alpha_smem[2] = {0, 0};
-  int alpha_grid[2] = {0, 0};
+  void* d_kblk = nullptr;
+  void* d_tiles[3] = {nullptr, nullptr, nullptr};
+  int* d_counter = nullptr;             // one tile counter per kernel
+  size_t rot_smem = 0, alpha_smem[3] = {0, 0, 0};
+  int alpha_grid[3] = {0, 0, 0};
   int kernels = 0, k_couple = 0, k_rot = 0, k_alpha = 0;
   uint64_t samples = 0;
   size_t bytes = 0;
@@ -1138,10 +1220,11 @@ static double alpha_form_cost(int Lh, int form) {
 }
 
 // Columns per tile by rule: the smallest of 32/64/128 covering min(J, 128)
-// whose X tile fits the shared-memory limit.
-static int batch_rule_nt(int prec, int Lh, long long J) {
+// whose X tile fits the shared-memory limit (kp: alpha kernel 0 FP64, 1
+// FP32, 2 double-float).
+static int batch_rule_nt(int kp, int Lh, long long J) {
   int nt = J <= 32 ? 32 : (J <= 64 ? 64 : 128);
-  while (nt > 32 && batch_alpha_smem(prec == SLSHT_FP64 ? 0 : 1, Lh, nt) > BA_SMEM_LIMIT) nt /= 2;
+  while (nt > 32 && batch_alpha_smem(kp, Lh, nt) > BA_SMEM_LIMIT) nt /= 2;
   return nt;
 }
 
@@ -1151,56 +1234,76 @@ static bool batch_tc_ok(const slsht_batch* b, const slsht_desc& d) {
 }
 
 // Phase table of the alpha stage for a form: the direct sum's (cos, sin)(2 pi r a / Na)
-// or the split DFT's twiddles (cos, sin)(2 pi q t / Na).
-static int batch_alpha_table(slsht_batch* b, const slsht_desc& d, int form, const void** out) {
+// or the split DFT's twiddles (cos, sin)(2 pi q t / Na); double-float pairs for
+// the double-float engine.
+static int batch_alpha_table(slsht_batch* b, const slsht_desc& d, int form, int engine, const void** out) {
   std::lock_guard<std::mutex> g(b->ctx->mu);
-  if (form > 0) return get_phase(b->ctx, d.n_alpha, 2 * d.L_h - 1, -(d.L_h - 1), d.prec, b->cs, out);
-  return get_phase(b->ctx, d.n_alpha, d.L_h, 0, d.prec, b->cs, out);
+  const int prec = engine == ENG_DD ? PREC_DD : d.prec;
+  if (form > 0) return get_phase(b->ctx, d.n_alpha, 2 * d.L_h - 1, -(d.L_h - 1), prec, b->cs, out);
+  return get_phase(b->ctx, d.n_alpha, d.L_h, 0, prec, b->cs, out);
+}
+
+// The alpha view of item ii for a CUDA-core engine (its tables not set).
+static BItem batch_item_view(const slsht_batch* b, int ii, int engine) {
+  const BatchItemHost& it = b->items[ii];
+  BItem bi = b->bitem[ii];
+  if (engine == ENG_DD) {
+    bi.prec = 2;
+    bi.H = b->rot[it.rot].Hdd;
+    bi.kdd = b->cpl[it.cpl].kdd;
+    bi.kexp = b->cpl[it.cpl].kexp;
+    bi.hexp = b->rot[it.rot].hexp;
+  } else {
+    bi.prec = it.d.prec == SLSHT_FP64 ? 0 : 1;
+    bi.H = b->rot[it.rot].H;
+  }
+  return bi;
 }
 
 // Times one candidate on the first pairs of item `ii`, into scratch, as it
-// would run in the plan: a CUDA-core tile shape (nt, form) inside a
+// would run in the plan: a CUDA-core tile shape (nt, form, engine) inside a
 // persistent launch that other items' tiles keep full (the sample pairs are
 // replicated `reps` times to fill the GPU), or the fused tensor-core kernel
-// (form -1) as a launch of its own over the item's pairs (np of them, no
+// as a launch of its own over the item's pairs (np of them, no
 // replication).  Returns device milliseconds per sample in *cost.
-static int batch_time_candidate(slsht_batch* b, int ii, int nt, int form, int np, int reps, void* scratch,
+static int batch_time_candidate(slsht_batch* b, int ii, int nt, int form, int engine, int np, int reps, void* scratch,
                                 void* d_item, void* d_tiles, int* d_ctr, double* cost) {
   slsht_ctx* ctx = b->ctx;
   const BatchItemHost& it = b->items[ii];
   const slsht_desc& d = it.d;
-  const int pi = d.prec == SLSHT_FP64 ? 0 : 1;
   const long long J = (long long)d.n_beta * d.n_gamma;
-  if (form < 0) reps = 1;
+  if (engine == ENG_TC) reps = 1;
   const double samples = (double)np * reps * d.n_alpha * J;
   std::vector<BTile> tl;
   BItem bi{};
   size_t smem = 0;
   int grid = 0;
-  if (form >= 0) {
-    bi = b->bitem[ii];
+  if (engine != ENG_TC) {
+    bi = batch_item_view(b, ii, engine);
     bi.g = scratch;
     bi.nt = nt;
     bi.form = form;
-    CKS(batch_alpha_table(b, d, form, &bi.csa));
+    CKS(batch_alpha_table(b, d, form, engine, &bi.csa));
     for (int r = 0; r < reps; ++r)
       for (int p = 0; p < np; ++p)
         for (long long j0 = 0; j0 < J; j0 += nt) tl.push_back({0, p, r * np + p, (int)j0});
     CK(cudaMemcpyAsync(d_item, &bi, sizeof(BItem), cudaMemcpyHostToDevice, b->cs));
     CK(cudaMemcpyAsync(d_tiles, tl.data(), sizeof(BTile) * tl.size(), cudaMemcpyHostToDevice, b->cs));
-    smem = batch_alpha_smem(pi, d.L_h, nt);
-    grid = (int)std::min<long long>((long long)ctx->num_sms * batch_alpha_occupancy(pi, smem), (long long)tl.size());
+    smem = batch_alpha_smem(bi.prec, d.L_h, nt);
+    grid = (int)std::min<long long>((long long)ctx->num_sms * batch_alpha_occupancy(bi.prec, smem),
+                                    (long long)tl.size());
   }
   float best = 1e30f;
   for (int rep = 0; rep < 4; ++rep) {          // one warm-up, three timed
     CK(cudaMemsetAsync(d_ctr, 0, sizeof(int), b->cs));
     CK(cudaEventRecord(b->ta, b->cs));
     cudaError_t e;
-    if (form >= 0)
-      e = launch_batch_alpha(pi, (const BItem*)d_item, (const BTile*)d_tiles, (int)tl.size(), d_ctr, grid, smem, b->cs);
+    if (engine != ENG_TC)
+      e = launch_batch_alpha(bi.prec, (const BItem*)d_item, (const BTile*)d_tiles, (int)tl.size(), d_ctr, grid, smem,
+                             b->cs);
     else
-      e = launch_alpha_fused(b->cpl[it.cpl].kc, (const float2*)b->rot[it.rot].H, it.etab, d.L_h, d.n_alpha, d.n_beta,
-                             d.n_gamma, np * reps, (float2*)scratch, ctx->num_sms, 0, nullptr, b->cs);
+      e = launch_alpha_fused(b->cpl[it.cpl].kc, (const float2*)b->rot[it.rot].H, it.etab, d.L_h, d.n_alpha,
+                             d.n_beta, d.n_gamma, np * reps, (float2*)scratch, ctx->num_sms, 0, nullptr, b->cs);
     if (e != cudaSuccess) { record_cuda_error("batch tuning launch", e); return SLSHT_E_CUDA; }
     CK(cudaEventRecord(b->tb, b->cs));
     CK(cudaEventSynchronize(b->tb));
@@ -1212,20 +1315,31 @@ static int batch_time_candidate(slsht_batch* b, int ii, int nt, int form, int np
   return SLSHT_OK;
 }
 
-// Picks (columns per tile, alpha form) for item ii's shape: the context's
-// cache, the rule (SLSHT_BATCH_NO_TUNE), or by timing every candidate.
+// Engines an item may use under the plan's flags.
+static bool batch_dd_ok(const slsht_batch* b, const slsht_desc& d) {
+  return d.prec == SLSHT_FP64 && !(b->flags & SLSHT_BATCH_NO_DD);
+}
+static bool batch_native_ok(const slsht_batch* b, const slsht_desc& d) {
+  return !(d.prec == SLSHT_FP64 && (b->flags & SLSHT_BATCH_FP64_DD));
+}
+
+// Picks (columns per tile, alpha form, engine) for item ii's shape: the
+// context's cache, the rule (SLSHT_BATCH_NO_TUNE), or by timing every candidate.
 static int batch_tune(slsht_batch* b, int ii) {
   slsht_ctx* ctx = b->ctx;
   BatchItemHost& it = b->items[ii];
   const slsht_desc& d = it.d;
-  const int pi = d.prec == SLSHT_FP64 ? 0 : 1;
   const int Lh = d.L_h, Na = d.n_alpha;
   const long long J = (long long)d.n_beta * d.n_gamma;
-  const bool tc_ok = batch_tc_ok(b, d);
-  const auto key = std::make_tuple((int)d.prec, Lh, Na, d.n_beta, d.n_gamma, tc_ok ? 1 : 0);
+  const bool tc_ok = batch_tc_ok(b, d), dd_ok = batch_dd_ok(b, d), nat_ok = batch_native_ok(b, d);
+  const int allowed = (tc_ok ? 1 : 0) | (dd_ok ? 2 : 0) | (nat_ok ? 4 : 0);
+  const auto key = std::make_tuple((int)d.prec, Lh, Na, d.n_beta, d.n_gamma, allowed);
   if (b->flags & SLSHT_BATCH_NO_TUNE) {
-    it.nt = batch_rule_nt(d.prec, Lh, J);
-    it.form = tc_ok ? -1 : alpha_split_factor(Lh, Na);
+    // rule: the tensor cores where they apply; FP64 in double-float arithmetic
+    // unless excluded; the split factor of alpha_split_factor
+    it.engine = tc_ok ? ENG_TC : (dd_ok ? ENG_DD : ENG_NATIVE);
+    it.nt = batch_rule_nt(it.engine == ENG_DD ? 2 : (d.prec == SLSHT_FP64 ? 0 : 1), Lh, J);
+    it.form = it.engine == ENG_TC ? -1 : alpha_split_factor(Lh, Na);
     it.tuned = 0;
     return SLSHT_OK;
   }
@@ -1233,23 +1347,28 @@ static int batch_tune(slsht_batch* b, int ii) {
     std::lock_guard<std::mutex> g(ctx->mu);
     auto f = ctx->tune.find(key);
     if (f != ctx->tune.end()) {
-      it.nt = f->second.first;
-      it.form = f->second.second;
+      std::tie(it.nt, it.form, it.engine) = f->second;
       it.tuned = 2;
       return SLSHT_OK;
     }
   }
-  // candidates
-  std::vector<std::pair<int, int>> cand;
+  // candidates (nt, form, engine)
+  std::vector<std::tuple<int, int, int>> cand;
   std::vector<int> forms = {0};
   for (int P : {3, 5, 7, 9})
     if (Na % P == 0) forms.push_back(P);
-  for (int nt : {32, 64, 128}) {
-    if (nt > 32 && J <= nt / 2) continue;                 // more than half the tile idle
-    if (batch_alpha_smem(pi, Lh, nt) > BA_SMEM_LIMIT) continue;
-    for (int fm : forms) cand.push_back({nt, fm});
+  std::vector<int> engines;
+  if (nat_ok) engines.push_back(ENG_NATIVE);
+  if (dd_ok) engines.push_back(ENG_DD);
+  for (int eng : engines) {
+    const int kp = eng == ENG_DD ? 2 : (d.prec == SLSHT_FP64 ? 0 : 1);
+    for (int nt : {32, 64, 128}) {
+      if (nt > 32 && J <= nt / 2) continue;               // more than half the tile idle
+      if (batch_alpha_smem(kp, Lh, nt) > BA_SMEM_LIMIT) continue;
+      for (int fm : forms) cand.push_back(std::make_tuple(nt, fm, eng));
+    }
   }
-  if (tc_ok) cand.push_back({0, -1});
+  if (tc_ok) cand.push_back(std::make_tuple(0, -1, ENG_TC));
   if (cand.empty()) return SLSHT_E_ARG;
   // sample: the first pairs (all of them up to 16M samples), replicated so
   // the candidate with the widest tiles still has about eight tiles per SM;
@@ -1267,11 +1386,11 @@ static int batch_tune(slsht_batch* b, int ii) {
   if (st == SLSHT_OK) st = ctx_alloc(ctx, sizeof(BTile) * max_tiles, &d_tiles);
   if (st == SLSHT_OK) st = ctx_alloc(ctx, 16, &d_ctr);
   double best = 1e300;
-  std::pair<int, int> pick = cand[0];
+  std::tuple<int, int, int> pick = cand[0];
   for (size_t c = 0; c < cand.size() && st == SLSHT_OK; ++c) {
     double cost = 0.0;
-    st = batch_time_candidate(b, ii, cand[c].first, cand[c].second, np, reps, scratch, d_item, d_tiles,
-                              (int*)d_ctr, &cost);
+    st = batch_time_candidate(b, ii, std::get<0>(cand[c]), std::get<1>(cand[c]), std::get<2>(cand[c]), np, reps,
+                              scratch, d_item, d_tiles, (int*)d_ctr, &cost);
     if (st == SLSHT_OK && cost < best) { best = cost; pick = cand[c]; }
   }
   cudaStreamSynchronize(b->cs);
@@ -1280,11 +1399,11 @@ static int batch_tune(slsht_batch* b, int ii) {
   ctx_free(ctx, d_tiles, sizeof(BTile) * max_tiles);
   ctx_free(ctx, d_ctr, 16);
   CKS(st);
-  it.nt = pick.second < 0 ? batch_rule_nt(d.prec, Lh, J) : pick.first;
-  it.form = pick.second;
+  std::tie(it.nt, it.form, it.engine) = pick;
+  if (it.engine == ENG_TC) it.nt = batch_rule_nt(1, Lh, J);
   it.tuned = 1;
   std::lock_guard<std::mutex> g(ctx->mu);
-  ctx->tune[key] = {it.nt, it.form};
+  ctx->tune[key] = std::make_tuple(it.nt, it.form, it.engine);
   return SLSHT_OK;
 }
 
@@ -1292,12 +1411,14 @@ static int batch_tune(slsht_batch* b, int ii) {
 static int batch_enqueue(slsht_batch* b, cudaStream_t st) {
   slsht_ctx* ctx = b->ctx;
   cudaError_t e;
-  CK(cudaMemsetAsync(b->d_counter, 0, 2 * sizeof(int), st));
+  CK(cudaMemsetAsync(b->d_counter, 0, 4 * sizeof(int), st));
   e = launch_batch_couple((const BCouple*)b->d_cpl, (const BCplBlk*)b->d_cblk, (int)b->cblk.size(), st);
   if (e != cudaSuccess) { record_cuda_error("launch_batch_couple", e); return SLSHT_E_CUDA; }
+  e = launch_batch_kdd((const BCouple*)b->d_cpl, (const BCplBlk*)b->d_kblk, (int)b->kblk.size(), st);
+  if (e != cudaSuccess) { record_cuda_error("launch_batch_kdd", e); return SLSHT_E_CUDA; }
   e = launch_batch_rotwin((const BRot*)b->d_rot, (const BRotBlk*)b->d_rblk, (int)b->rblk.size(), b->rot_smem, st);
   if (e != cudaSuccess) { record_cuda_error("launch_batch_rotwin", e); return SLSHT_E_CUDA; }
-  for (int pi = 0; pi < 2; ++pi) {
+  for (int pi = 0; pi < 3; ++pi) {
     e = launch_batch_alpha(pi, (const BItem*)b->d_bitem, (const BTile*)b->d_tiles[pi], (int)b->tiles[pi].size(),
                            b->d_counter + pi, b->alpha_grid[pi], b->alpha_smem[pi], st);
     if (e != cudaSuccess) { record_cuda_error("launch_batch_alpha", e); return SLSHT_E_CUDA; }
@@ -1412,6 +1533,25 @@ static int batch_build(slsht_batch* b, const slsht_batch_item* src, int32_t n, c
       b->rot.push_back(r);
     }
     it.rot = rf->second;
+    if (batch_dd_ok(b, d)) {
+      // double-float k and H for the double-float engine
+      BCouple& c = b->cpl[it.cpl];
+      if (c.kdd == nullptr) {
+        void *kd = nullptr, *ke = nullptr;
+        CKS(batch_alloc(b, sizeof(float4) * (size_t)it.npairs * n2, &kd));
+        CKS(batch_alloc(b, sizeof(int) * (size_t)it.npairs, &ke));
+        c.kdd = (float4*)kd;
+        c.kexp = (int*)ke;
+      }
+      BRot& r = b->rot[it.rot];
+      if (r.Hdd == nullptr) {
+        void *hd = nullptr, *he = nullptr;
+        CKS(batch_alloc(b, sizeof(float4) * h_elems((size_t)J, n2), &hd));
+        CKS(batch_alloc(b, 16, &he));
+        r.Hdd = (float4*)hd;
+        r.hexp = (int*)he;
+      }
+    }
     if (batch_tc_ok(b, d)) {
       std::lock_guard<std::mutex> g(ctx->mu);
       CKS(get_etab(ctx, d.n_alpha, Lh, b->cs, &it.etab));
@@ -1426,35 +1566,61 @@ static int batch_build(slsht_batch* b, const slsht_batch_item* src, int32_t n, c
     bi.J = (int)J;
     b->bitem.push_back(bi);
   }
-  // k and H once, for the tuner
+  // k and H once (every engine's form), for the tuner
+  for (int ci = 0; ci < (int)b->cpl.size(); ++ci)
+    if (b->cpl[ci].kdd != nullptr)
+      for (int p = 0; p < b->cpl[ci].npairs; ++p) b->kblk.push_back({ci, p});
   CKS(batch_upload(b, b->cpl.data(), sizeof(BCouple) * b->cpl.size(), &b->d_cpl));
   CKS(batch_upload(b, b->cblk.data(), sizeof(BCplBlk) * b->cblk.size(), &b->d_cblk));
+  CKS(batch_upload(b, b->kblk.data(), sizeof(BCplBlk) * b->kblk.size(), &b->d_kblk));
   CKS(batch_upload(b, b->rot.data(), sizeof(BRot) * b->rot.size(), &b->d_rot));
   CKS(batch_upload(b, b->rblk.data(), sizeof(BRotBlk) * b->rblk.size(), &b->d_rblk));
   {
     cudaError_t e = launch_batch_couple((const BCouple*)b->d_cpl, (const BCplBlk*)b->d_cblk, (int)b->cblk.size(),
                                         b->cs);
     if (e == cudaSuccess)
+      e = launch_batch_kdd((const BCouple*)b->d_cpl, (const BCplBlk*)b->d_kblk, (int)b->kblk.size(), b->cs);
+    if (e == cudaSuccess)
       e = launch_batch_rotwin((const BRot*)b->d_rot, (const BRotBlk*)b->d_rblk, (int)b->rblk.size(), b->rot_smem,
                               b->cs);
     if (e != cudaSuccess) { record_cuda_error("batch k / H", e); return SLSHT_E_CUDA; }
   }
-  // tile shapes
+  // tile shapes and engines
   for (int32_t i = 0; i < n; ++i) {
     BatchItemHost& it = b->items[i];
     CKS(batch_tune(b, i));
     BItem& bi = b->bitem[i];
+    if (it.engine != ENG_TC) bi = batch_item_view(b, i, it.engine);
     bi.nt = it.nt;
     bi.form = std::max(it.form, 0);
-    if (it.form >= 0) CKS(batch_alpha_table(b, it.d, it.form, &bi.csa));
+    if (it.engine != ENG_TC) CKS(batch_alpha_table(b, it.d, it.form, it.engine, &bi.csa));
+  }
+  // only the forms of k and H that the chosen engines read are produced per launch
+  {
+    std::vector<char> rot_native(b->rot.size(), 0), rot_dd(b->rot.size(), 0), cpl_dd(b->cpl.size(), 0);
+    for (const BatchItemHost& it : b->items) {
+      if (it.engine == ENG_DD) { rot_dd[it.rot] = 1; cpl_dd[it.cpl] = 1; }
+      else rot_native[it.rot] = 1;
+    }
+    for (size_t r = 0; r < b->rot.size(); ++r) {
+      if (!rot_native[r]) b->rot[r].H = nullptr;
+      if (!rot_dd[r]) b->rot[r].Hdd = nullptr;
+    }
+    b->kblk.clear();
+    for (int ci = 0; ci < (int)b->cpl.size(); ++ci)
+      if (cpl_dd[ci])
+        for (int p = 0; p < b->cpl[ci].npairs; ++p) b->kblk.push_back({ci, p});
+    CK(cudaMemcpyAsync(b->d_rot, b->rot.data(), sizeof(BRot) * b->rot.size(), cudaMemcpyHostToDevice, b->cs));
+    if (!b->kblk.empty())
+      CK(cudaMemcpyAsync(b->d_kblk, b->kblk.data(), sizeof(BCplBlk) * b->kblk.size(), cudaMemcpyHostToDevice, b->cs));
   }
   // tiles, largest first
-  for (int pi = 0; pi < 2; ++pi) {
+  for (int pi = 0; pi < 3; ++pi) {
     std::vector<std::pair<double, BTile>> tl;
     for (int32_t i = 0; i < n; ++i) {
       const BatchItemHost& it = b->items[i];
-      if (it.form < 0) continue;
-      if ((it.d.prec == SLSHT_FP64 ? 0 : 1) != pi) continue;
+      if (it.engine == ENG_TC) continue;
+      if (b->bitem[i].prec != pi) continue;
       const long long J = (long long)it.d.n_beta * it.d.n_gamma;
       const double cost = (double)it.nt * (4.0 * it.d.L_h * it.d.L_h + it.d.n_alpha * alpha_form_cost(it.d.L_h, it.form));
       for (int p = 0; p < it.npairs; ++p)
@@ -1473,12 +1639,12 @@ static int batch_build(slsht_batch* b, const slsht_batch_item* src, int32_t n, c
     }
   }
   for (int32_t i = 0; i < n; ++i)
-    if (b->items[i].form < 0) { b->tc_items.push_back(i); b->k_alpha++; }
+    if (b->items[i].engine == ENG_TC) { b->tc_items.push_back(i); b->k_alpha++; }
   CKS(batch_upload(b, b->bitem.data(), sizeof(BItem) * b->bitem.size(), &b->d_bitem));
   void* ctr = nullptr;
   CKS(batch_alloc(b, 16, &ctr));
   b->d_counter = (int*)ctr;
-  b->k_couple = b->cblk.empty() ? 0 : 1;
+  b->k_couple = (b->cblk.empty() ? 0 : 1) + (b->kblk.empty() ? 0 : 1);
   b->k_rot = b->rblk.empty() ? 0 : 1;
   b->kernels = b->k_couple + b->k_rot + b->k_alpha;
   // one direct run: every g_out holds its result, and every launch path
@@ -1505,7 +1671,10 @@ extern "C" int slsht_batch_create(slsht_ctx* ctx, int32_t n_items, const slsht_b
   if (!out) return SLSHT_E_ARG;
   *out = nullptr;
   if (!ctx || !items || n_items < 1) return SLSHT_E_ARG;
-  if (flags & ~(SLSHT_BATCH_NO_GRAPH | SLSHT_BATCH_NO_TUNE | SLSHT_BATCH_NO_TC)) return SLSHT_E_ARG;
+  if (flags & ~(SLSHT_BATCH_NO_GRAPH | SLSHT_BATCH_NO_TUNE | SLSHT_BATCH_NO_TC | SLSHT_BATCH_NO_DD |
+                SLSHT_BATCH_FP64_DD))
+    return SLSHT_E_ARG;
+  if ((flags & SLSHT_BATCH_NO_DD) && (flags & SLSHT_BATCH_FP64_DD)) return SLSHT_E_ARG;
   DeviceGuard g(ctx->device);
   std::vector<std::vector<int32_t>> lms((size_t)n_items);
   for (int32_t i = 0; i < n_items; ++i) {
@@ -1556,13 +1725,15 @@ extern "C" int slsht_batch_launch(slsht_batch* b, void* stream) {
 
 extern "C" int slsht_batch_query(const slsht_batch* b, int32_t item, int32_t what, int64_t* value) {
   if (!b || !value) return SLSHT_E_ARG;
-  const bool per_item = what == SLSHT_BQ_TILE_COLS || what == SLSHT_BQ_ALPHA_FORM || what == SLSHT_BQ_TUNED;
+  const bool per_item = what == SLSHT_BQ_TILE_COLS || what == SLSHT_BQ_ALPHA_FORM || what == SLSHT_BQ_TUNED ||
+                        what == SLSHT_BQ_ENGINE;
   if (per_item && (item < 0 || item >= (int32_t)b->items.size())) return SLSHT_E_ARG;
   switch (what) {
     case SLSHT_BQ_TILE_COLS: *value = b->items[item].form < 0 ? 0 : b->items[item].nt; return SLSHT_OK;
     case SLSHT_BQ_ALPHA_FORM: *value = b->items[item].form; return SLSHT_OK;
     case SLSHT_BQ_TUNED: *value = b->items[item].tuned; return SLSHT_OK;
-    case SLSHT_BQ_TILES: *value = (int64_t)(b->tiles[0].size() + b->tiles[1].size()); return SLSHT_OK;
+    case SLSHT_BQ_ENGINE: *value = b->items[item].engine; return SLSHT_OK;
+    case SLSHT_BQ_TILES: *value = (int64_t)(b->tiles[0].size() + b->tiles[1].size() + b->tiles[2].size()); return SLSHT_OK;
     case SLSHT_BQ_KERNELS: *value = b->kernels; return SLSHT_OK;
     case SLSHT_BQ_GRAPH: *value = b->exec ? 1 : 0; return SLSHT_OK;
     case SLSHT_BQ_BYTES: *value = (int64_t)b->bytes; return SLSHT_OK;

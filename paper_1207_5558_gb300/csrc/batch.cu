@@ -11,8 +11,10 @@
 // either directly (+-q paired) or as the split DFT of alpha_dev.cuh, with
 // BA_THREADS / nt row groups per column.  Host code orders the tiles by
 // decreasing cost, so large tiles start first and small ones fill the tail.
+#include <algorithm>
 #include <mutex>
 
+#include "alpha_dd.cuh"
 #include "alpha_dev.cuh"
 #include "batch.cuh"
 #include "couple_dev.cuh"
@@ -36,26 +38,132 @@ cudaError_t launch_batch_couple(const BCouple* cpl, const BCplBlk* blk, int nblk
   return cudaGetLastError();
 }
 
+// Largest |value| over a block (every thread gets it).
+__device__ __forceinline__ double block_max(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double m = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+  __syncthreads();
+  return m;
+}
+
+// Exponent e with |x| * 2^-e in [0.5, 1) for the largest |x| (0 for x = 0).
+__device__ __forceinline__ int scale_exp(double mx) {
+  int e = 0;
+  if (mx > 0.0) frexp(mx, &e);
+  return e;
+}
+
+// k of one pair (n2 entries at kp) as double-floats at kd, scaled by a power
+// of two so its largest component lies in [0.5, 1); the exponent to *kexp.
+// Every thread of the block takes part.
+__device__ __forceinline__ void kdd_pair(const double2* __restrict__ kp, int n2, float4* __restrict__ kd,
+                                         int* __restrict__ kexp, double* red) {
+  double mx = 0.0;
+  for (int t = threadIdx.x; t < n2; t += blockDim.x) {
+    const double2 v = kp[t];
+    mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+  }
+  const int e = scale_exp(block_max(mx, red));
+  for (int t = threadIdx.x; t < n2; t += blockDim.x) {
+    const double2 v = kp[t];
+    float rh, rl, ih, il;
+    dd_split(ldexp(v.x, -e), &rh, &rl);
+    dd_split(ldexp(v.y, -e), &ih, &il);
+    kd[t] = make_float4(rh, ih, rl, il);
+  }
+  if (threadIdx.x == 0) *kexp = e;
+}
+
+// block {cpl, pair}
+__global__ void __launch_bounds__(256) k_batch_kdd(const BCouple* __restrict__ cpl, const BCplBlk* __restrict__ blk) {
+  __shared__ double red[8];
+  const BCplBlk b = blk[blockIdx.x];
+  const BCouple c = cpl[b.cpl];
+  const int n2 = c.Lh * c.Lh, pair = b.first;
+  kdd_pair(c.kc + (size_t)pair * n2, n2, c.kdd + (size_t)pair * n2, c.kexp + pair, red);
+}
+
+// one block per pair
+__global__ void __launch_bounds__(256) k_kdd_pairs(const double2* __restrict__ kc, int n2, float4* __restrict__ kdd,
+                                                   int* __restrict__ kexp) {
+  __shared__ double red[8];
+  const int pair = blockIdx.x;
+  kdd_pair(kc + (size_t)pair * n2, n2, kdd + (size_t)pair * n2, kexp + pair, red);
+}
+
+cudaError_t launch_kdd_pairs(const double2* kc, int Lh, int npairs, float4* kdd, int* kexp, cudaStream_t st) {
+  if (npairs <= 0) return cudaSuccess;
+  k_kdd_pairs<<<npairs, 256, 0, st>>>(kc, Lh * Lh, kdd, kexp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_kdd(const BCouple* cpl, const BCplBlk* blk, int nblk, cudaStream_t st) {
+  if (nblk <= 0) return cudaSuccess;
+  k_batch_kdd<<<nblk, 256, 0, st>>>(cpl, blk);
+  return cudaGetLastError();
+}
+
 static cudaError_t batch_attrs();
 
 // ---------------------------------------------------------------- rotated windows
+// FP64 outputs of a rotated window: the double H and/or its double-float copy
+// scaled by 2^-e (each pointer may be null).
+struct RotwinBoth {
+  double2* H;
+  float4* Hdd;
+  int e;
+  __device__ __forceinline__ void operator()(size_t i, double re, double im) const {
+    if (H != nullptr) H[i] = make_double2(re, im);
+    if (Hdd != nullptr) {
+      float rh, rl, ih, il;
+      dd_split(ldexp(re, -e), &rh, &rl);
+      dd_split(ldexp(im, -e), &ih, &il);
+      Hdd[i] = make_float4(rh, ih, rl, il);
+    }
+  }
+};
+// One (beta row, degree) block of an FP64 window: the double H and/or the
+// double-float copy scaled by 2^-e, e from the window's largest coefficient
+// (every block finds the same e; block (0, 0) records it in *hexp).
+__device__ __forceinline__ void rotwin_block_fp64(const double2* __restrict__ h, const double* __restrict__ dblk,
+                                                  const double2* __restrict__ eg, int Lh, int Ng, int b, int p,
+                                                  double2* H, float4* Hdd, int* hexp, int smem_ok,
+                                                  unsigned char* smem) {
+  __shared__ double red[4];
+  int e = 0;
+  if (Hdd != nullptr) {
+    double mx = 0.0;
+    for (int t = threadIdx.x; t < Lh * Lh; t += blockDim.x) {
+      const double2 v = h[t];
+      mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+    }
+    e = scale_exp(block_max(mx, red));
+    if (b == 0 && p == 0 && threadIdx.x == 0) *hexp = e;
+  }
+  const RotwinBoth st{H, Hdd, e};
+  if (smem_ok)
+    rotwin_block_smem_to<double>(h, dblk, eg, Lh, Ng, b, p, st, smem);
+  else
+    rotwin_block_direct_to<double>(h, dblk, eg, Lh, Ng, b, p, st);
+}
+
 __global__ void __launch_bounds__(128) k_batch_rotwin(const BRot* __restrict__ rot, const BRotBlk* __restrict__ blk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const BRotBlk bb = blk[blockIdx.x];
   const BRot r = rot[bb.rot];
   const size_t off = (size_t)bb.b * blk_off(r.Lh) + blk_off(bb.p);
   if (r.prec == 0) {
-    const double* d = (const double*)r.dt + off;
-    if (r.smem_ok)
-      rotwin_block_smem<double>(r.h, d, (const double2*)r.eg, r.Lh, r.Ng, bb.b, bb.p, (double2*)r.H, smem_raw);
-    else
-      rotwin_block_direct<double>(r.h, d, (const double2*)r.eg, r.Lh, r.Ng, bb.b, bb.p, (double2*)r.H);
+    rotwin_block_fp64(r.h, (const double*)r.dt + off, (const double2*)r.eg, r.Lh, r.Ng, bb.b, bb.p,
+                      (double2*)r.H, r.Hdd, r.hexp, r.smem_ok, smem_raw);
   } else {
     const float* d = (const float*)r.dt + off;
     if (r.smem_ok)
       rotwin_block_smem<float>(r.h, d, (const float2*)r.eg, r.Lh, r.Ng, bb.b, bb.p, (float2*)r.H, smem_raw);
     else
-      rotwin_block_direct<float>(r.h, d, (const float2*)r.eg, r.Lh, r.Ng, bb.b, bb.p, (float2*)r.H);
+      rotwin_block_direct_to<float>(r.h, d, (const float2*)r.eg, r.Lh, r.Ng, bb.b, bb.p, RotwinStore<float>{(float2*)r.H});
   }
 }
 
@@ -65,6 +173,27 @@ cudaError_t launch_batch_rotwin(const BRot* rot, const BRotBlk* blk, int nblk, s
   cudaError_t e = batch_attrs();
   if (e != cudaSuccess) return e;
   k_batch_rotwin<<<nblk, 128, smem, st>>>(rot, blk);
+  return cudaGetLastError();
+}
+
+// grid (Nb, Lh): the scaled double-float window of one call
+__global__ void __launch_bounds__(128) k_rotwin_dd(const double2* __restrict__ h, const double* __restrict__ dt,
+                                                   const double2* __restrict__ eg, int Lh, int Ng, float4* Hdd,
+                                                   int* hexp, int smem_ok) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int b = blockIdx.x, p = blockIdx.y;
+  rotwin_block_fp64(h, dt + (size_t)b * blk_off(Lh) + blk_off(p), eg, Lh, Ng, b, p, nullptr, Hdd, hexp, smem_ok,
+                    smem_raw);
+}
+
+cudaError_t launch_rotwin_dd(const double2* h, const double* dt, const double2* eg, int Lh, int Nb, int Ng,
+                             float4* Hdd, int* hexp, cudaStream_t st) {
+  const size_t sm = rotwin_smem_bytes(Lh, Ng, sizeof(double2));
+  const int ok = sm <= (size_t)BA_SMEM_LIMIT ? 1 : 0;
+  cudaError_t e = batch_attrs();
+  if (e != cudaSuccess) return e;
+  dim3 grid(Nb, Lh);
+  k_rotwin_dd<<<grid, 128, ok ? sm : 0, st>>>(h, dt, eg, Lh, Ng, Hdd, hexp, ok);
   return cudaGetLastError();
 }
 
@@ -167,6 +296,138 @@ __device__ __forceinline__ void ba_tile(const BItem& it, const BTile& tl, unsign
   }
 }
 
+// The tile of an FP64 item in double-float arithmetic: X_q from the scaled
+// double-float k and H, the alpha sum (direct or split) from double-float
+// tables, each output assembled as a double with the scale 2^(kexp + hexp).
+template <int P>
+__device__ __forceinline__ void ba_split_dd(const BItem& it, const float4* sx, const ddv* cst, const DdOut& out, int c,
+                                            int s) {
+  constexpr int H = (P - 1) / 2;
+  alpha_split_column_dd<P>(sx + c, it.nt, it.Lh, it.Na, it.J, reinterpret_cast<const float4*>(it.csa), cst,
+                           cst + (H + 1) * (H + 1), out, s, BA_THREADS / it.nt);
+}
+
+template <int P>
+__device__ __forceinline__ void ba_consts_dd(ddv* cst) {
+  constexpr int H = (P - 1) / 2;
+  const int t = threadIdx.x;
+  if (t < (H + 1) * (H + 1)) {
+    const int r = t / (H + 1), s = t % (H + 1);
+    double sv, cv;
+    sincospi(2.0 * r * s / P, &sv, &cv);
+    dd_split(cv, &cst[t].h, &cst[t].l);
+    dd_split(sv, &cst[(H + 1) * (H + 1) + t].h, &cst[(H + 1) * (H + 1) + t].l);
+  }
+}
+
+__device__ __forceinline__ void ba_tile_dd(const BItem& it, const BTile& tl, unsigned char* smem) {
+  const int Lh = it.Lh, K = 2 * Lh - 1, n2 = Lh * Lh, NT = it.nt, S = BA_THREADS / NT;
+  const int J = it.J, Na = it.Na, tid = threadIdx.x;
+  float4* sx = reinterpret_cast<float4*>(smem);                    // [q + Lh - 1][NT]
+  ddv* cst = reinterpret_cast<ddv*>(sx + (size_t)K * NT);          // split-DFT constants
+  const float4* kp = it.kdd + (size_t)tl.pair * n2;
+  const float4* H = reinterpret_cast<const float4*>(it.H);
+  for (int e = tid; e < K * NT; e += BA_THREADS) {
+    const int qi = e / NT, c = e - qi * NT;
+    const int q = qi - (Lh - 1), aq = q < 0 ? -q : q;
+    const int j = tl.j0 + c;
+    dd_acc xr = dd_acc_zero(), xi = dd_acc_zero();
+    if (j < J) {
+      for (int p0 = aq; p0 < Lh; p0 += 4) {
+        float4 hv[4], kv[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int p = p0 + v;
+          if (p < Lh) {
+            const int pq = p * p + p + q;
+            hv[v] = __ldg(H + h_index(pq, j, n2));
+            kv[v] = __ldg(kp + pq);
+          } else {
+            hv[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+            kv[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {      // k H: (kr hr - ki hi) + i (kr hi + ki hr)
+          dd_mac(xr, kv[v].x, kv[v].z, hv[v].x, hv[v].z);
+          dd_mac(xr, -kv[v].y, -kv[v].w, hv[v].y, hv[v].w);
+          dd_mac(xi, kv[v].x, kv[v].z, hv[v].y, hv[v].w);
+          dd_mac(xi, kv[v].y, kv[v].w, hv[v].x, hv[v].z);
+        }
+      }
+    }
+    const ddv vr = ddv_of(xr), vi = ddv_of(xi);
+    sx[e] = make_float4(vr.h, vi.h, vr.l, vi.l);
+  }
+  switch (it.form) {
+    case 3: ba_consts_dd<3>(cst); break;
+    case 5: ba_consts_dd<5>(cst); break;
+    case 7: ba_consts_dd<7>(cst); break;
+    case 9: ba_consts_dd<9>(cst); break;
+    default: break;
+  }
+  __syncthreads();
+  if (it.form == 0) {
+    for (int e = tid; e < (Lh - 1) * NT; e += BA_THREADS) {
+      const int r = e / NT + 1, c = e - (r - 1) * NT;
+      const ddc a = ddc_load_smem(sx + (Lh - 1 + r) * NT + c), b = ddc_load_smem(sx + (Lh - 1 - r) * NT + c);
+      sx[(Lh - 1 + r) * NT + c] = ddc_pack({ddv_add(a.re, b.re), ddv_add(a.im, b.im)});
+      sx[(Lh - 1 - r) * NT + c] = ddc_pack({ddv_sub(a.re, b.re), ddv_sub(a.im, b.im)});
+    }
+    __syncthreads();
+  }
+  const int c = tid % NT, s = tid / NT, j = tl.j0 + c;
+  if (j >= J) return;
+  // output slot and, for a mirrored pair, the slot of (l, -m) with (-1)^m
+  const int2 sl = it.slots != nullptr ? it.slots[tl.pair] : make_int2(tl.out, -1);
+  double2* g = reinterpret_cast<double2*>(it.g);
+  DdOut out;
+  out.dst = g + (size_t)sl.x * Na * J + j;
+  out.mdst = sl.y >= 0 ? g + (size_t)(sl.y >> 1) * Na * J + j : nullptr;
+  out.sgn = (sl.y & 1) ? -1.0 : 1.0;
+  out.sc = it.kexp[tl.pair] + *it.hexp;
+  switch (it.form) {
+    case 0:
+      alpha_direct_column_dd(sx + c, NT, Lh - 1, Lh - 1, 1, Lh - 1, -1, Lh, Na, J,
+                             reinterpret_cast<const float4*>(it.csa), out, s * ALPHA_ABLK, S * ALPHA_ABLK);
+      break;
+    case 3: ba_split_dd<3>(it, sx, cst, out, c, s); break;
+    case 5: ba_split_dd<5>(it, sx, cst, out, c, s); break;
+    case 7: ba_split_dd<7>(it, sx, cst, out, c, s); break;
+    case 9: ba_split_dd<9>(it, sx, cst, out, c, s); break;
+    default: break;
+  }
+}
+
+__global__ void __launch_bounds__(BA_THREADS) k_batch_alpha_dd(const BItem* __restrict__ items,
+                                                               const BTile* __restrict__ tiles, int ntiles,
+                                                               int* __restrict__ counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_tile;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1);
+    __syncthreads();
+    const int ti = s_tile;
+    if (ti >= ntiles) return;
+    const BTile tl = tiles[ti];
+    const BItem it = items[tl.item];
+    ba_tile_dd(it, tl, smem_raw);
+    __syncthreads();
+  }
+}
+
+// One item, every (pair, column block) tile in index order, CTAs striding
+// (equal tiles: no counter needed).
+__global__ void __launch_bounds__(BA_THREADS) k_alpha_dd_single(const BItem it, int ntiles) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ntj = (it.J + it.nt - 1) / it.nt;
+  for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+    const BTile tl{0, ti / ntj, ti / ntj, (ti % ntj) * it.nt};
+    ba_tile_dd(it, tl, smem_raw);
+    __syncthreads();
+  }
+}
+
 // One instantiation per precision: items of the other precision are never
 // in its tile list.
 template <typename T>
@@ -188,13 +449,15 @@ __global__ void __launch_bounds__(BA_THREADS) k_batch_alpha(const BItem* __restr
 }
 
 size_t batch_alpha_smem(int prec, int Lh, int nt) {
-  const size_t el = prec == 0 ? sizeof(double) : sizeof(float);
-  const size_t b = 2 * el * (size_t)(2 * Lh - 1) * nt + 2 * el * BA_CONST_ENTRIES;
+  const size_t el2 = prec == 1 ? sizeof(float2) : 16;     // double2, or float4 double-float pairs
+  const size_t cst = prec == 1 ? sizeof(float) : (prec == 0 ? sizeof(double) : sizeof(ddv));
+  const size_t b = el2 * (size_t)(2 * Lh - 1) * nt + 2 * cst * BA_CONST_ENTRIES;
   return (b + 15) / 16 * 16;
 }
 
 static const void* batch_alpha_fn(int prec) {
-  return prec == 0 ? (const void*)k_batch_alpha<double> : (const void*)k_batch_alpha<float>;
+  return prec == 0 ? (const void*)k_batch_alpha<double>
+                   : (prec == 1 ? (const void*)k_batch_alpha<float> : (const void*)k_batch_alpha_dd);
 }
 
 // The batch kernels' dynamic shared-memory ceiling is set once, to
@@ -210,6 +473,12 @@ static cudaError_t batch_attrs() {
                                          BA_SMEM_LIMIT);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_batch_alpha<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, BA_SMEM_LIMIT);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_batch_alpha_dd, cudaFuncAttributeMaxDynamicSharedMemorySize, BA_SMEM_LIMIT);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_alpha_dd_single, cudaFuncAttributeMaxDynamicSharedMemorySize, BA_SMEM_LIMIT);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_rotwin_dd, cudaFuncAttributeMaxDynamicSharedMemorySize, BA_SMEM_LIMIT);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_batch_rotwin, cudaFuncAttributeMaxDynamicSharedMemorySize, BA_SMEM_LIMIT);
     g_attr_status = e;
@@ -237,6 +506,25 @@ cudaError_t launch_batch_alpha(int prec, const BItem* items, const BTile* tiles,
   cudaError_t e = batch_attrs();
   if (e != cudaSuccess) return e;
   if (prec == 0) k_batch_alpha<double><<<grid, BA_THREADS, smem, st>>>(items, tiles, ntiles, counter);
-  else k_batch_alpha<float><<<grid, BA_THREADS, smem, st>>>(items, tiles, ntiles, counter);
+  else if (prec == 1) k_batch_alpha<float><<<grid, BA_THREADS, smem, st>>>(items, tiles, ntiles, counter);
+  else k_batch_alpha_dd<<<grid, BA_THREADS, smem, st>>>(items, tiles, ntiles, counter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_alpha_dd_call(const BItem& item, int npairs, int num_sms, cudaStream_t st) {
+  if (npairs <= 0 || item.J <= 0) return cudaSuccess;
+  const size_t smem = batch_alpha_smem(2, item.Lh, item.nt);
+  if (smem > BA_SMEM_LIMIT) return cudaErrorInvalidValue;
+  cudaError_t e = batch_attrs();
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_alpha_dd_single, BA_THREADS, smem) != cudaSuccess) {
+    cudaGetLastError();
+    occ = 1;
+  }
+  const long long ntiles = (long long)npairs * ((item.J + item.nt - 1) / item.nt);
+  if (ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+  const int grid = (int)std::min<long long>((long long)num_sms * std::max(occ, 1), ntiles);
+  k_alpha_dd_single<<<grid, BA_THREADS, smem, st>>>(item, (int)ntiles);
   return cudaGetLastError();
 }

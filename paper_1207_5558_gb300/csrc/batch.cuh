@@ -20,6 +20,8 @@ struct BCouple {                 // one coupling output (a signal with a pair li
   const double* coef;            // Gaunt table rows [pair][i][t]
   const int2* meta;              // (first l', count) per [pair][t]
   double2* kc;                   // k [pair][t]
+  float4* kdd;                   // double-float k scaled by 2^-kexp[pair] (null: not needed)
+  int* kexp;
   int Lh, npairs;
 };
 struct BCplBlk { int cpl, first; };        // 256 consecutive (pair, t) items of one BCouple
@@ -28,31 +30,50 @@ struct BRot {                    // one rotated window H
   const double2* h;
   const void* dt;                // d^p(beta_b) table [b][blk_off(Lh)], T
   const void* eg;                // gamma phases [c][2Lh-1], T2
-  void* H;                       // tiled H (h_index), T2
+  void* H;                       // tiled H (h_index), T2 (null: not needed)
+  float4* Hdd;                   // FP64 windows: double-float H scaled by 2^-hexp[0] (null: not needed)
+  int* hexp;
   int prec, Lh, Ng, smem_ok;     // prec 0: FP64, 1: FP32
 };
 struct BRotBlk { int rot, b, p, pad; };
 
 struct BItem {                   // one analysis of the batch (alpha stage view)
   const double2* kc;             // k [pair][Lh^2]
-  const void* H;                 // tiled H, T2
+  const void* H;                 // tiled H, T2 (double-float items: the scaled float4 H)
   const void* csa;               // form 0: (cos, sin)(2 pi r a / Na) [a][Lh]; P: split twiddles [t][2Lh-1]
+                                 // (double-float items: float4 {cos.h, sin.h, cos.l, sin.l})
   void* g;                       // output [pair][a][j], T2
-  int prec, Lh, Na, J;
+  const float4* kdd;             // double-float items: scaled k and its exponents
+  const int* kexp;
+  const int* hexp;
+  const int2* slots;             // double-float items (nullable): per pair {output slot, mirror}
+                                 // as for launch_alpha_tc; null: pair p -> tile's out slot
+  int prec, Lh, Na, J;           // prec 0: FP64, 1: FP32, 2: FP64 output from double-float arithmetic
   int nt;                        // columns per tile: 32, 64 or 128 (BA_THREADS / nt row groups)
   int form;                      // 0: direct sum, 3/5/7/9: split DFT with that factor
 };
 struct BTile { int item, pair, out, j0; };  // k of `pair`, output slot `out`, columns j0 .. j0+nt-1
 
-// Shared memory of a k_batch_alpha tile: X_q for nt columns.
+// Shared memory of a k_batch_alpha tile: X_q for nt columns (prec 0, 1 or 2).
 size_t batch_alpha_smem(int prec, int Lh, int nt);
 // Resident CTAs of k_batch_alpha (precision prec) per SM with `smem` bytes of
 // dynamic shared memory.
 int batch_alpha_occupancy(int prec, size_t smem);
 
 cudaError_t launch_batch_couple(const BCouple* cpl, const BCplBlk* blk, int nblk, cudaStream_t st);
+// Double-float k of the couplings that need it: block list {cpl, pair}.
+cudaError_t launch_batch_kdd(const BCouple* cpl, const BCplBlk* blk, int nblk, cudaStream_t st);
 cudaError_t launch_batch_rotwin(const BRot* rot, const BRotBlk* blk, int nblk, size_t smem, cudaStream_t st);
+// One call's double-float pieces (the per-call FP64 path): k of npairs pairs
+// scaled into kdd/kexp; the rotated window's scaled double-float copy; the
+// alpha stage of one item over all its (pair, column block) tiles, tiles
+// derived from the index (no list), CTAs striding over them.
+cudaError_t launch_kdd_pairs(const double2* kc, int Lh, int npairs, float4* kdd, int* kexp, cudaStream_t st);
+cudaError_t launch_rotwin_dd(const double2* h, const double* dt, const double2* eg, int Lh, int Nb, int Ng,
+                             float4* Hdd, int* hexp, cudaStream_t st);
+cudaError_t launch_alpha_dd_call(const BItem& item, int npairs, int num_sms, cudaStream_t st);
+
 // Persistent: `grid` CTAs take tiles from *counter (reset to 0 before each
-// launch); every tile's item has precision prec.
+// launch); every tile's item has precision prec (0 FP64, 1 FP32, 2 double-float).
 cudaError_t launch_batch_alpha(int prec, const BItem* items, const BTile* tiles, int ntiles, int* counter, int grid,
                                size_t smem, cudaStream_t st);

@@ -39,6 +39,8 @@ cudaError_t launch_dtable_f32(const double* D, float* dt, int Lh, int Nb, cudaSt
 // tab[i * R + r] = (cos, sin)(2 pi (r0 + r) i / N), i < N, r < R.
 cudaError_t launch_phase_f64(double2* tab, int N, int R, int r0, cudaStream_t st);
 cudaError_t launch_phase_f32(float2* tab, int N, int R, int r0, cudaStream_t st);
+// The same as double-float pairs {cos.h, sin.h, cos.l, sin.l}.
+cudaError_t launch_phase_dd(float4* tab, int N, int R, int r0, cudaStream_t st);
 // beta quadrature weights q_b, b < Nb (see the inverse).
 cudaError_t launch_beta_weights(double* w, int Nb, cudaStream_t st);
 

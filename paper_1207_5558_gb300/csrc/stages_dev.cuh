@@ -22,10 +22,11 @@ __host__ __device__ __forceinline__ size_t rotwin_smem_bytes(int Lh, int Ng, siz
 // odd-stride phase rows without bank conflicts).  dblk = the degree-p block
 // of d(beta_b); eg[c * (2Lh-1) + q' + Lh - 1] = (cos, sin)(q' gamma_c).  All
 // threads of the block take part (one __syncthreads).
-template <typename T>
-__device__ __forceinline__ void rotwin_block_smem(const double2* __restrict__ h, const T* __restrict__ dblk,
-                                                  const typename vec2<T>::t* __restrict__ eg, int Lh, int Ng, int b,
-                                                  int p, typename vec2<T>::t* __restrict__ H, unsigned char* smem) {
+// store(index, re, im) receives each output with its h_index position.
+template <typename T, typename Store>
+__device__ __forceinline__ void rotwin_block_smem_to(const double2* __restrict__ h, const T* __restrict__ dblk,
+                                                     const typename vec2<T>::t* __restrict__ eg, int Lh, int Ng,
+                                                     int b, int p, Store store, unsigned char* smem) {
   typedef typename vec2<T>::t T2;
   const int K = 2 * Lh - 1, n2 = Lh * Lh, w = 2 * p + 1;
   T2* hd = reinterpret_cast<T2*>(smem);       // [q + p][q' + p]
@@ -51,16 +52,29 @@ __device__ __forceinline__ void rotwin_block_smem(const double2* __restrict__ h,
       re = fma(a.x, E.x, re); re = fma(a.y, E.y, re);
       im = fma(a.y, E.x, im); im = fma(-a.x, E.y, im);
     }
-    H[h_index(p * p + qi, b * Ng + c, n2)] = mk2(re, im);
+    store(h_index(p * p + qi, b * Ng + c, n2), re, im);
   }
+}
+
+template <typename T>
+struct RotwinStore {
+  typename vec2<T>::t* H;
+  __device__ __forceinline__ void operator()(size_t i, T re, T im) const { H[i] = mk2(re, im); }
+};
+
+template <typename T>
+__device__ __forceinline__ void rotwin_block_smem(const double2* __restrict__ h, const T* __restrict__ dblk,
+                                                  const typename vec2<T>::t* __restrict__ eg, int Lh, int Ng, int b,
+                                                  int p, typename vec2<T>::t* __restrict__ H, unsigned char* smem) {
+  rotwin_block_smem_to<T>(h, dblk, eg, Lh, Ng, b, p, RotwinStore<T>{H}, smem);
 }
 
 // The same block without shared memory (windows whose staged products would
 // not fit): each output reads h, d and the phases through the cache.
-template <typename T>
-__device__ __forceinline__ void rotwin_block_direct(const double2* __restrict__ h, const T* __restrict__ dblk,
-                                                    const typename vec2<T>::t* __restrict__ eg, int Lh, int Ng,
-                                                    int b, int p, typename vec2<T>::t* __restrict__ H) {
+template <typename T, typename Store>
+__device__ __forceinline__ void rotwin_block_direct_to(const double2* __restrict__ h, const T* __restrict__ dblk,
+                                                       const typename vec2<T>::t* __restrict__ eg, int Lh, int Ng,
+                                                       int b, int p, Store store) {
   typedef typename vec2<T>::t T2;
   const int K = 2 * Lh - 1, n2 = Lh * Lh, w = 2 * p + 1;
   for (int t = threadIdx.x; t < w * Ng; t += blockDim.x) {
@@ -76,6 +90,6 @@ __device__ __forceinline__ void rotwin_block_direct(const double2* __restrict__ 
       re = fma(ar, E.x, re); re = fma(ai, E.y, re);
       im = fma(ai, E.x, im); im = fma(-ar, E.y, im);
     }
-    H[h_index(p * p + qi, b * Ng + c, n2)] = mk2(re, im);
+    store(h_index(p * p + qi, b * Ng + c, n2), re, im);
   }
 }

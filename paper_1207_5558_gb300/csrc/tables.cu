@@ -146,6 +146,27 @@ cudaError_t launch_phase_f32(float2* tab, int N, int R, int r0, cudaStream_t st)
   return cudaGetLastError();
 }
 
+// The same table as double-float pairs: tab[i * R + r] = {cos.h, sin.h,
+// cos.l, sin.l} with cos = cos.h + cos.l to about 2^-48.
+__global__ void k_phase_dd(float4* __restrict__ tab, int N, int R, int r0) {
+  const long long n = (long long)N * R;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t / R), r = (int)(t % R);
+    double s, c;
+    sincos_2pi_frac((long long)(r0 + r) * i, N, &s, &c);
+    const float ch = __double2float_rn(c), sh = __double2float_rn(s);
+    tab[t] = make_float4(ch, sh, __double2float_rn(c - (double)ch), __double2float_rn(s - (double)sh));
+  }
+}
+
+cudaError_t launch_phase_dd(float4* tab, int N, int R, int r0, cudaStream_t st) {
+  const long long n = (long long)N * R;
+  const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  k_phase_dd<<<blocks, 256, 0, st>>>(tab, N, R, r0);
+  return cudaGetLastError();
+}
+
 // q_b = (2/M) sum_{|k|<Nb} W(k) cos(k beta_b) (b >= 1), q_0 = (1/M) sum W(k),
 // M = 2Nb - 1, W(k) = 2/(1-k^2) for even k and 0 for odd k: the printed w(m)
 // of Sec. IV-A with the imaginary k = +-1 terms cancelling in the folded sum.

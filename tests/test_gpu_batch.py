@@ -185,14 +185,15 @@ def test_rule_and_cuda_core_plans(pkg, ctx, flags):
 
 def test_batch_matches_per_call_forward(pkg, ctx):
     """FP64: the plan and slsht_forward agree to rounding (the plan forms X per
-    tile, the per-call path in a separate kernel)."""
+    tile, the per-call path in a separate kernel; the plan's tuner may pick the
+    double-float engine, about 2^-48 per operation)."""
     Lf, Lh, grid = 16, 8, (63, 16, 15)
     f, h = synth.signal_powerlaw(Lf, 41), synth.window_cn(Lh, 42)
     pairs = synth.pairs_random(Lf + Lh - 1, 12, 43)
     b = ctx.batch([_item(Lf, Lh, grid, _dev(f), _dev(h), pairs, 0)])
     try:
         g = ctx.forward(Lf, Lh, grid, f, h, pairs, prec=0).cpu().numpy()
-        assert rel(b.outputs[0].cpu().numpy(), g) < 1e-14
+        assert rel(b.outputs[0].cpu().numpy(), g) < 1e-13
     finally:
         b.close()
 
@@ -213,3 +214,56 @@ def test_batch_argument_errors(pkg, ctx):
         it["g_out"] = g[1:]
         ctx.batch([it])
     assert ctx.mem_used() >= 0
+
+
+@pytest.mark.parametrize("flags", ["double_float", "fp64_only"])
+def test_fp64_engines_vs_oracle(pkg, ctx, flags):
+    """FP64 items in double-float arithmetic (pairs of floats on the FP32
+    pipe, forced) and in FP64 arithmetic (forced): both within the FP64 path's
+    1e-12 of the oracle."""
+    f = pkg.SLSHT_BATCH_FP64_DD if flags == "double_float" else pkg.SLSHT_BATCH_NO_DD
+    spec = _mix()
+    items, refs, _ = _build_items(spec)
+    b = ctx.batch(items, flags=f)
+    try:
+        for i, (it, ref) in enumerate(zip(items, refs)):
+            err = rel(b.outputs[i].cpu().numpy(), ref)
+            assert err < TOL[it["prec"]], (i, err)
+            if it["prec"] == 0:
+                assert b.query(pkg.SLSHT_BQ_ENGINE, i) == (1 if flags == "double_float" else 0)
+    finally:
+        b.close()
+
+
+def test_double_float_engine_extreme_scales(pkg, ctx):
+    """The double-float engine scales k and the rotated window by powers of two
+    into the float range: signals near 1e-35 and windows near 1e+30 (far
+    outside what unscaled float pairs could hold) keep FP64 accuracy."""
+    Lf, Lh, grid = 9, 5, (35, 9, 9)
+    f = synth.signal_powerlaw(Lf, 51) * 1e-35
+    h = synth.window_cn(Lh, 52) * 1e30
+    pairs = synth.pairs_random(Lf + Lh - 1, 10, 53)
+    ref = O.forward_coeff(f, h, Lf, Lh, pairs, grid)
+    b = ctx.batch([_item(Lf, Lh, grid, _dev(f), _dev(h), pairs, 0)], flags=pkg.SLSHT_BATCH_FP64_DD)
+    try:
+        assert b.query(pkg.SLSHT_BQ_ENGINE, 0) == 1
+        assert rel(b.outputs[0].cpu().numpy(), ref) < 1e-12
+    finally:
+        b.close()
+
+
+def test_double_float_matches_fp64_arithmetic(pkg, ctx):
+    """The two FP64 engines agree far inside the tolerance on a larger case
+    (workload-3 band limits, both alpha forms)."""
+    Lf, Lh = 64, 16
+    f, h = synth.signal_powerlaw(Lf, 61), synth.window_cn(Lh, 62, decay=1.0)
+    pairs = synth.pairs_bands([17, 63])
+    for grid in [(127, 20, 31), (105, 12, 31)]:            # direct (prime N_alpha) and split (3, 5, 7)
+        b1 = ctx.batch([_item(Lf, Lh, grid, _dev(f), _dev(h), pairs, 0)], flags=pkg.SLSHT_BATCH_FP64_DD)
+        b2 = ctx.batch([_item(Lf, Lh, grid, _dev(f), _dev(h), pairs, 0)], flags=pkg.SLSHT_BATCH_NO_DD)
+        try:
+            x, y = b1.outputs[0].cpu().numpy(), b2.outputs[0].cpu().numpy()
+            assert rel(x, y) < 1e-13, grid
+        finally:
+            b1.close()
+            b2.close()

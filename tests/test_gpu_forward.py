@@ -302,8 +302,8 @@ def test_bounded_wait_expiry_reports_and_context_recovers(ctx):
     assert rel(g, O.forward_coeff(f, h, Lf, Lh, pairs, grid)) < TOL32
 
 
-@pytest.mark.parametrize("prec,engine", [(0, 0), (1, 0), (1, 1), (1, 2)])
-def test_real_fields_mirror_pairs(ctx, prec, engine):
+@pytest.mark.parametrize("prec,engine,arith", [(0, 0, 0), (0, 0, 1), (1, 0, 0), (1, 1, 0), (1, 2, 0)])
+def test_real_fields_mirror_pairs(ctx, prec, engine, arith):
     """SLSHT_OPT_REAL_FIELDS: for real f and h, g(l, -m) = (-1)^m conj g(l, m)
     (Sec. IV-B; pin (iv) of the oracle tests), so only one of each mirrored
     pair is computed and the alpha stage writes both.  Against the full
@@ -315,6 +315,7 @@ def test_real_fields_mirror_pairs(ctx, prec, engine):
     pairs = np.concatenate([synth.pairs_bands([3, 13]), np.array([[9, 4], [18, -5]], dtype=np.int32)])
     ref = O.forward_coeff(f, h, Lf, Lh, pairs, grid)
     ctx.set_option(pkg.SLSHT_OPT_ALPHA_ENGINE, engine)
+    ctx.set_option(pkg.SLSHT_OPT_FP64_ARITH, arith)
     try:
         full = _fw(ctx, Lf, Lh, grid, f, h, pairs, prec)
         ctx.set_option(pkg.SLSHT_OPT_REAL_FIELDS, 1)
@@ -322,18 +323,21 @@ def test_real_fields_mirror_pairs(ctx, prec, engine):
     finally:
         ctx.set_option(pkg.SLSHT_OPT_REAL_FIELDS, 0)
         ctx.set_option(pkg.SLSHT_OPT_ALPHA_ENGINE, 0)
+        ctx.set_option(pkg.SLSHT_OPT_FP64_ARITH, 0)
     tol = TOL64 if prec == 0 else TOL32
     assert rel(half, ref) < tol
     assert rel(half, full) < (1e-13 if prec == 0 else 2e-6)
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec,arith", [(0, 0), (0, 1), (1, 0)])
 @pytest.mark.parametrize("Na", [15, 33, 45, 105, 511])
-def test_split_dft_alpha_stage(ctx, prec, Na):
+def test_split_dft_alpha_stage(ctx, prec, arith, Na):
     """The CUDA-core alpha stage as a split DFT over a = Q s + t (P = 3, 5, 7
     or 9 dividing N_alpha) against the direct sum (engine 4) and the oracle,
-    with mirrored pairs under the real-field option as well."""
+    with mirrored pairs under the real-field option as well; FP64 both in
+    double-float (arith 0) and in FP64 arithmetic (arith 1)."""
     import paper_1207_5558_gb300 as pkg
+    ctx.set_option(pkg.SLSHT_OPT_FP64_ARITH, arith)
     Lf, Lh = 12, 12
     grid = (Na, 7, 9)
     f = synth.signal_powerlaw(Lf, 100 + Na)
@@ -352,6 +356,7 @@ def test_split_dft_alpha_stage(ctx, prec, Na):
     finally:
         ctx.set_option(pkg.SLSHT_OPT_REAL_FIELDS, 0)
         ctx.set_option(pkg.SLSHT_OPT_ALPHA_ENGINE, 0)
+        ctx.set_option(pkg.SLSHT_OPT_FP64_ARITH, 0)
     assert rel(split, ref) < tol
     assert rel(split_mirror, ref) < tol
     assert rel(direct, ref) < tol
@@ -414,11 +419,13 @@ def test_modulated_sht_coupling_workload2_size(ctx):
     assert rel(msht, gaunt) < 1e-12
 
 
+@pytest.mark.parametrize("arith", [0, 1])
 @pytest.mark.parametrize("Na", [135, 127])
-def test_fp64_widest_window_band(ctx, Na):
-    """FP64 at the largest window band limit, L_h = 64 (K = 127): the alpha
-    stage drops to 64-column CTAs to fit 127 staged coefficients; N_alpha =
-    135 takes the split DFT (P = 9), 127 the direct sum."""
+def test_fp64_widest_window_band(ctx, Na, arith):
+    """FP64 at the largest window band limit, L_h = 64 (K = 127): the FP64
+    alpha stage drops to 64-column CTAs to fit 127 staged coefficients, the
+    double-float one to 32; N_alpha = 135 takes the split DFT (P = 9), 127
+    the direct sum."""
     import paper_1207_5558_gb300 as pkg
     Lf, Lh = 6, 64
     grid = (Na, 3, 131)
@@ -426,5 +433,9 @@ def test_fp64_widest_window_band(ctx, Na):
     h = synth.window_cn(Lh, 600 + Na, decay=1.0)
     pairs = np.array([[5, -2], [40, 7], [68, 68]], dtype=np.int32)
     ref = O.forward_coeff(f, h, Lf, Lh, pairs, grid, kroute="recurrence")
-    g = _fw(ctx, Lf, Lh, grid, f, h, pairs, 0)
+    ctx.set_option(pkg.SLSHT_OPT_FP64_ARITH, arith)
+    try:
+        g = _fw(ctx, Lf, Lh, grid, f, h, pairs, 0)
+    finally:
+        ctx.set_option(pkg.SLSHT_OPT_FP64_ARITH, 0)
     assert rel(g, ref) < TOL64
