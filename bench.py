@@ -40,6 +40,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--profile-prec", type=int, default=1, help="precision of --profile-pairs (1 FP32_BULK, 0 FP64)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=2000,
@@ -157,6 +158,13 @@ def traffic_record(kernel):
     return d if d.get("source_sha256_16") == h else None
 
 
+def alpha_split_factor_py(Lh, Na):
+    """The split factor the library picks for (Lh, Na) (alpha_split_factor in
+    csrc/alpha.cu): the odd P in {9, 7, 5, 3} dividing Na with the smallest
+    4K/P + P + 3 below the direct sum's 4(Lh-1) + 2, else 0."""
+    return alpha_fp64_cost(Lh, Na)[0]
+
+
 def alpha_fp64_cost(Lh, Na, P=None):
     """FP64 work of the CUDA-core alpha stage per output sample, for the form
     the library picks (the same rule as alpha_split_factor in csrc/alpha.cu),
@@ -179,6 +187,22 @@ def alpha_fp64_cost(Lh, Na, P=None):
     fma = 4 * K + 4 * H * H
     adds = 10 * H
     return best, (fma + adds) / best, (2 * fma + adds) / best, "split DFT, a = Q s + t with P = %d" % best
+
+
+def alpha_dd_ops(Lh, Na, P):
+    """Issue-slot model of the double-float X + alpha kernel per output sample
+    (FP32 and integer instructions, from the code of csrc/alpha_dd.cuh and
+    csrc/dd.cuh): a double-float multiply-add is 12 instructions (1 FMUL,
+    3 FFMA, a 6-add TwoSum, 2 adds), a renormalised add 11, the assembly of a
+    double about 15.  Returns (instructions a sample, description)."""
+    K = 2 * Lh - 1
+    x = 12.0 * 4 * Lh * Lh / Na + 6.0 * K / Na            # X: Lh^2 complex MACs a column
+    if P == 0:
+        a = 12.0 * (4 * (Lh - 1)) + 6.0 + 30.0             # direct: 4 (Lh-1) MACs, renormalise, assemble
+        return x + a, "direct sum, +-q paired"
+    H = (P - 1) // 2
+    per_t = 48.0 * K + 6.0 * P + 60.0 * H + H * (48.0 * H + 56.0) + 6.0
+    return x + per_t / P + 30.0, "split DFT, a = Q s + t with P = %d" % P
 
 
 def reduce_max(value, dist):
@@ -226,10 +250,12 @@ def serve_bench(pkg, device, n, rate, seed=4000, max_outstanding_bytes=48 << 30,
     rng = np.random.default_rng(seed + 1)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
     ctx = pkg.Context(device, mem_budget_bytes=(24 << 30))
-    # build the tables of every (L_h, native grid, precision) once, outside the measurement
+    # build the tables of every (L_h, native grid, precision) and measure the
+    # FP64 tile shapes once, outside the measurement
     for Lh in (4, 8, 16, 32):
+        grid = serve_native(Lh)
+        ctx.tune(128, Lh, grid, 0)
         for prec in (0, 1):
-            grid = serve_native(Lh)
             ctx.forward(32, Lh, grid, np.zeros(32 * 32, complex), np.ones(Lh * Lh, complex), [[1, 0]], prec=prec)
     torch.cuda.synchronize()
     done_at = np.full(n, np.nan)
@@ -278,10 +304,10 @@ def serve_bench(pkg, device, n, rate, seed=4000, max_outstanding_bytes=48 << 30,
                         "outstanding outputs capped at 48 GB, later arrivals wait (latency from arrival)"}
 
 
-def profile_case(pkg, n):
+def profile_case(pkg, n, prec=1):
     """A small case of workload 3 for kernel captures: one chunk of 48 pairs per
     launch, a few GB on the device, two forward passes, then two inverses of
-    the result."""
+    the result (prec 1: FP32_BULK, 0: FP64)."""
     import numpy as np
     import torch
     import synth
@@ -290,12 +316,14 @@ def profile_case(pkg, n):
     sub = np.ascontiguousarray(pairs[-n:])
     ctx = pkg.Context(0, 16 << 30)
     ctx.set_option(pkg.SLSHT_OPT_CHUNK_PAIRS, 48)
-    g = torch.empty((n,) + c["grid"], dtype=torch.complex64, device="cuda")
+    g = torch.empty((n,) + c["grid"], dtype=torch.complex64 if prec == 1 else torch.complex128, device="cuda")
+    if prec == 0:
+        ctx.tune(c["Lf"], c["Lh"], c["grid"], 0)
     for _ in range(2):
-        pkg.slsht_forward(ctx.h, pkg.make_desc(c["Lf"], c["Lh"], c["grid"], 1), f, h, sub, n, g)
+        pkg.slsht_forward(ctx.h, pkg.make_desc(c["Lf"], c["Lh"], c["grid"], prec), f, h, sub, n, g)
     fout = torch.empty(n, dtype=torch.complex128, device="cuda")
     for _ in range(2):
-        pkg.slsht_inverse(ctx.h, pkg.make_desc(c["Lf"], c["Lh"], c["grid"], 1), g, complex(h[0]), sub, n, fout)
+        pkg.slsht_inverse(ctx.h, pkg.make_desc(c["Lf"], c["Lh"], c["grid"], prec), g, complex(h[0]), sub, n, fout)
     torch.cuda.synchronize()
     print(json.dumps({"profile_pairs": n, "max_abs_g": float(g.abs().max())}))
     ctx.close()
@@ -373,7 +401,7 @@ def main():
 
     torch.cuda.set_device(local)
     if args.profile_pairs > 0:
-        profile_case(pkg, args.profile_pairs)
+        profile_case(pkg, args.profile_pairs, args.profile_prec)
         return
     dist = None
     if world > 1:
@@ -615,17 +643,22 @@ def main():
         ms_call = ev_ms(per_call, 2)
         br = ctx.batch(items, flags=pkg.SLSHT_BATCH_NO_TUNE, stream=stream)
         ms_rule = ev_ms(lambda: br.launch(stream), 3)
-        forms = sorted({(it["L_h"], it["prec"], bp.query(pkg.SLSHT_BQ_TILE_COLS, i), bp.query(pkg.SLSHT_BQ_ALPHA_FORM, i))
-                        for i, it in enumerate(items)})
+        bn = ctx.batch(items, flags=pkg.SLSHT_BATCH_NO_DD, stream=stream)
+        ms_nodd = ev_ms(lambda: bn.launch(stream), 2)
+        bn.close()
+        forms = sorted({(it["L_h"], it["prec"], bp.query(pkg.SLSHT_BQ_TILE_COLS, i), bp.query(pkg.SLSHT_BQ_ALPHA_FORM, i),
+                         bp.query(pkg.SLSHT_BQ_ENGINE, i)) for i, it in enumerate(items)})
         out["serving_mix"] = {
             "requests": len(items), "samples": smp, "g_bytes": tot, "create_s": create_s,
             "plan_ms": ms_plan, "per_call_ms": ms_call, "rule_plan_ms": ms_rule,
             "value_plan": smp / (ms_plan / 1e3), "value_per_call": smp / (ms_call / 1e3),
             "speedup_vs_per_call": ms_call / ms_plan, "tuner_gain_vs_rule": ms_rule / ms_plan,
+            "plan_fp64_arithmetic_ms": ms_nodd,
             "kernels_per_launch": bp.query(pkg.SLSHT_BQ_KERNELS), "tiles": bp.query(pkg.SLSHT_BQ_TILES),
             "tile_choices": [{"L_h": a, "prec": "fp64" if b_ == 0 else "fp32", "cols": c_,
-                              "alpha": "tensor cores" if fm < 0 else ("direct" if fm == 0 else "split P=%d" % fm)}
-                             for a, b_, c_, fm in forms]}
+                              "alpha": "tensor cores" if fm < 0 else ("direct" if fm == 0 else "split P=%d" % fm),
+                              "arithmetic": ["native", "double-float", "tensor cores"][en]}
+                             for a, b_, c_, fm, en in forms]}
         bp.close()
         br.close()
         del items
@@ -640,16 +673,28 @@ def main():
         smp = bp.query(pkg.SLSHT_BQ_SAMPLES)
         ms = ev_ms(lambda: bp.launch(stream), 2)
         fm = bp.query(pkg.SLSHT_BQ_ALPHA_FORM, 0)
-        P, instr, flops, form = alpha_fp64_cost(Lh, grid[0], fm if fm > 0 else 0)
-        x_instr = 4.0 * Lh * Lh / grid[0]
+        eng = bp.query(pkg.SLSHT_BQ_ENGINE, 0)
         rate = smp / (ms / 1e3)
         out["fp64_workload3"] = {
             "value": rate, "unit": UNIT, "ms_per_step": ms, "create_s": create_s,
-            "tile_cols": bp.query(pkg.SLSHT_BQ_TILE_COLS, 0), "alpha_form": form,
-            "fp64_instructions_per_sample": instr + x_instr,
-            "fp64_pipe_frac": rate * (instr + x_instr) / 0.625e12,
-            "note": "X (4 L_h^2 / N_alpha FMA a sample) and the alpha sum in one persistent kernel; the "
-                    "fraction counts FP64 FMA/add instructions over the 0.625e12/s FMA pipe"}
+            "tile_cols": bp.query(pkg.SLSHT_BQ_TILE_COLS, 0),
+            "engine": "double-float" if eng == 1 else "FP64 arithmetic"}
+        if eng == 1:
+            ops, form = alpha_dd_ops(Lh, grid[0], fm if fm > 0 else 0)
+            out["fp64_workload3"].update({
+                "alpha_form": form, "issue_slots_per_sample": ops,
+                "issue_frac": rate * ops / (128.0 * torch.cuda.get_device_properties(local).multi_processor_count *
+                                            2070e6),
+                "note": "X and the alpha sum in one persistent double-float kernel; modelled FP32/INT "
+                        "instructions a sample over 128 lanes x SMs x 2070 MHz"})
+        else:
+            P, instr, flops, form = alpha_fp64_cost(Lh, grid[0], fm if fm > 0 else 0)
+            x_instr = 4.0 * Lh * Lh / grid[0]
+            out["fp64_workload3"].update({
+                "alpha_form": form, "fp64_instructions_per_sample": instr + x_instr,
+                "fp64_pipe_frac": rate * (instr + x_instr) / 0.625e12,
+                "note": "X (4 L_h^2 / N_alpha FMA a sample) and the alpha sum in one persistent kernel; the "
+                        "fraction counts FP64 FMA/add instructions over the 0.625e12/s FMA pipe"})
         bp.close()
         del g64
         torch.cuda.empty_cache()
@@ -688,25 +733,50 @@ def main():
     rel32 = None
     if args.fp64_steps > 0:
         g64 = torch.empty((npairs_map,) + grid, dtype=torch.complex128, device="cuda")
-        ms64, st64, _ = timed(0, g64, args.fp64_steps, 1)
+        # the tile shape of this FP64 grid, measured once (untimed set-up)
+        t0 = time.perf_counter()
+        ctx.tune(Lf, Lh, grid, 0)
+        tune_s = time.perf_counter() - t0
+        # default FP64 path: X and alpha in double-float arithmetic
+        ms64, st64, clk64 = timed(0, g64, args.fp64_steps, 1, ClockSampler(local))
         value64 = samples_step * args.fp64_steps * world / (ms64 / 1e3)
         a64 = g64[sel]
         rel32 = float(torch.linalg.vector_norm(a32 - a64) / torch.linalg.vector_norm(a64))
         inv64 = inverse_leg(0, g64, 2)
         fp64_alpha_ms = st64["ms"]["alpha"]
-        P, instr, flops, form = alpha_fp64_cost(Lh, grid[0])
+        Pdd = alpha_split_factor_py(Lh, grid[0])
+        ops, form_dd = alpha_dd_ops(Lh, grid[0], Pdd)
         alpha_rate = samples_step * args.fp64_steps / (fp64_alpha_ms / 1e3)
+        sm_mhz = (clk64 or {}).get("sm_mhz") or 2070.0
+        issue_peak = 128.0 * torch.cuda.get_device_properties(local).multi_processor_count * sm_mhz * 1e6
+        # FP64 arithmetic throughout (SLSHT_OPT_FP64_ARITH = 1), one step
+        ctx.set_option(pkg.SLSHT_OPT_FP64_ARITH, 1)
+        msn, stn, _ = timed(0, g64, 1, 1)
+        ctx.set_option(pkg.SLSHT_OPT_FP64_ARITH, 0)
+        rel_dd = float(torch.linalg.vector_norm(g64[sel] - a64) / torch.linalg.vector_norm(g64[sel]))
+        P, instr, flops, form = alpha_fp64_cost(Lh, grid[0])
+        nat_rate = samples_step / (stn["ms"]["alpha"] / 1e3)
         fp64 = {"value": value64, "unit": UNIT, "steps": args.fp64_steps,
                 "ms_per_step": ms64 / args.fp64_steps,
                 "stage_ms_per_step": {k: v / args.fp64_steps for k, v in st64["ms"].items()},
-                "alpha_form": form,
-                "alpha_fp64_instructions_per_sample": instr,
-                "alpha_fp64_flops_per_sample": flops,
-                "alpha_fp64_tflops": alpha_rate * flops / 1e12,
-                "alpha_fp64_pipe_frac": alpha_rate * instr / 0.625e12,
-                "note": "FP64 alpha stage is FP64-pipe bound: the fraction is FP64 instructions (FMA or add) "
-                        "issued per second over the 0.625e12/s of a 1.25 TFLOP/s FMA pipe; stage times "
-                        "overlap (two streams)",
+                "arithmetic": "3j, Delta, coupling, rotated window in FP64; X and the alpha sum in double-float "
+                              "(float pairs, exact TwoProd/TwoSum on the FP32 pipe, ~2^-48), g assembled as "
+                              "complex128",
+                "alpha_form": form_dd,
+                "tune_s": tune_s,
+                "alpha_issue_slots_per_sample": ops,
+                "alpha_issue_frac": alpha_rate * ops / issue_peak,
+                "alpha_issue_note": "modelled FP32/INT instructions a sample (bench.alpha_dd_ops) times the "
+                                    "alpha kernel's sample rate over 128 lanes x SMs x the sampled SM clock",
+                "clocks": clk64,
+                "rel_l2_vs_fp64_arithmetic_sampled": rel_dd,
+                "fp64_arithmetic": {
+                    "value": samples_step / (msn / 1e3) * world, "ms_per_step": msn,
+                    "alpha_form": form, "alpha_fp64_instructions_per_sample": instr,
+                    "alpha_fp64_flops_per_sample": flops,
+                    "alpha_fp64_pipe_frac": nat_rate * instr / 0.625e12,
+                    "note": "SLSHT_OPT_FP64_ARITH = 1: the alpha stage is FP64-pipe bound; the fraction is FP64 "
+                            "instructions over the 0.625e12/s of a 1.25 TFLOP/s FMA pipe"},
                 "inverse": inv64}
         del g64, a64
         fp64["real_fields_workload2"] = real_fields_leg()

@@ -319,6 +319,15 @@ int slsht_batch_launch(slsht_batch* batch, void* stream);
 #define SLSHT_BQ_ENGINE     9
 int slsht_batch_query(const slsht_batch* batch, int32_t item, int32_t what, int64_t* value);
 
+/* Measure the tile shapes of one grid shape now: the same autotuner as
+ * slsht_batch_create (every candidate timed on seeded synthetic
+ * coefficients of that shape, a few pairs of degree L_f - 1), its choice
+ * cached in the context.  slsht_forward and slsht_submit read the cache for
+ * the CUDA-core alpha kernels of FP64 calls (double-float engine); without
+ * an entry they use a built-in rule.  Synchronous; returns SLSHT_OK,
+ * SLSHT_E_ARG, SLSHT_E_NOMEM or SLSHT_E_CUDA. */
+int slsht_tune(slsht_ctx* ctx, const slsht_desc* desc);
+
 /* Wait for the plan's last launch and free everything it holds.  NULL is a
  * no-op.  slsht_destroy frees the plans of its context that are still alive;
  * a plan must not be used (or destroyed) after its context. */

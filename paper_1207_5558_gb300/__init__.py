@@ -22,7 +22,7 @@ from ._abi import (SLSHT_FP32_BULK, SLSHT_FP64, SLSHT_OPT_ALPHA_ENGINE,  # noqa:
 __all__ = ["Context", "make_desc", "SLSHT_FP64", "SLSHT_FP32_BULK", "SlshtError",
            "slsht_create", "slsht_destroy", "slsht_forward", "slsht_forward_noalloc", "slsht_forward_windows",
            "slsht_window_ellipse", "slsht_batch_create", "slsht_batch_launch", "slsht_batch_query",
-           "slsht_batch_destroy", "Batch",
+           "slsht_batch_destroy", "slsht_tune", "Batch",
            "slsht_inverse", "slsht_submit",
            "slsht_poll", "slsht_drain", "slsht_strerror", "slsht_check_args", "slsht_profile",
            "slsht_get_stats", "slsht_set_option", "slsht_mem_used", "slsht_version"]
@@ -112,6 +112,10 @@ def slsht_batch_query(batch, item, what):
 
 def slsht_batch_destroy(batch):
     _abi.load().slsht_batch_destroy(batch)
+
+
+def slsht_tune(ctx, desc):
+    return _abi.check(_abi.load().slsht_tune(ctx, ctypes.byref(desc)), "slsht_tune")
 
 
 def slsht_submit(ctx, desc, f_lm, h_lm, lm, n_pairs, g_out):
@@ -258,6 +262,10 @@ class Context:
 
     def mem_used(self):
         return slsht_mem_used(self.h)
+
+    def tune(self, L_f, L_h, grid, prec=SLSHT_FP64):
+        """Measure and cache the tile shapes of one grid shape (slsht_tune)."""
+        slsht_tune(self.h, make_desc(L_f, L_h, grid, prec))
 
     def batch(self, items, flags=0, stream=None):
         """A Batch plan over `items` (see Batch)."""

@@ -92,6 +92,7 @@ def load(path=LIB_PATH):
         "slsht_batch_create": (ctypes.c_int, [vp, i32, ctypes.POINTER(slsht_batch_item), i32, vp,
                                               ctypes.POINTER(vp)]),
         "slsht_batch_launch": (ctypes.c_int, [vp, vp]),
+        "slsht_tune": (ctypes.c_int, [vp, ctypes.POINTER(slsht_desc)]),
         "slsht_batch_query": (ctypes.c_int, [vp, i32, i32, ctypes.POINTER(i64)]),
         "slsht_batch_destroy": (None, [vp]),
         "slsht_submit": (ctypes.c_int, [vp, ctypes.POINTER(slsht_desc), vp, vp, vp, i32, vp,

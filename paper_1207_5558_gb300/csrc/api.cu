@@ -629,10 +629,10 @@ static void mirror_work(const int32_t* lm, int32_t n, std::vector<int32_t>* out)
   }
 }
 
-// Columns per tile of the double-float alpha kernel by rule: the smallest of
-// 32/64/128 covering min(J, 128) whose X tile fits the shared-memory limit.
+// Columns per tile of the double-float alpha kernel by rule: 32 for at most
+// 32 columns, else 64 (two row groups a column), within the shared-memory limit.
 static int dd_rule_cols(int Lh, long long J) {
-  int nt = J <= 32 ? 32 : (J <= 64 ? 64 : 128);
+  int nt = J <= 32 ? 32 : 64;
   while (nt > 32 && batch_alpha_smem(2, Lh, nt) > BA_SMEM_LIMIT) nt /= 2;
   return nt;
 }
@@ -653,7 +653,7 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
 
   int route, tc, engine, gt_opt, wait_test, coupling, fp64_arith;
   int64_t chunk_opt;
-  int dd_nt = 0, dd_form = -1;
+  int dd_nt = 0, dd_form = -1, tuned_engine = -1;
   {
     std::lock_guard<std::mutex> g(ctx->mu);
     route = ctx->opt_beta_route ? ctx->opt_beta_route : 1;
@@ -666,9 +666,12 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
     fp64_arith = ctx->opt_fp64_arith;
     // a tile shape the batch-plan tuner measured for this FP64 shape, if any
     auto tf = ctx->tune.find(std::make_tuple((int)SLSHT_FP64, Lh, Na, Nb, Ng, 6));
-    if (tf != ctx->tune.end() && std::get<2>(tf->second) == 1) {
-      dd_nt = std::get<0>(tf->second);
-      dd_form = std::get<1>(tf->second);
+    if (tf != ctx->tune.end()) {
+      tuned_engine = std::get<2>(tf->second);
+      if (tuned_engine == 1) {
+        dd_nt = std::get<0>(tf->second);
+        dd_form = std::get<1>(tf->second);
+      }
     }
   }
   // rotated-window route on the tensor cores: producer and alpha stage fused
@@ -679,8 +682,9 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
   const bool split = !tc && engine != 4 && alpha_split_factor(Lh, Na) > 0;
   // FP64, rotated-window route: X and the alpha sum in double-float
   // arithmetic (one kernel over (pair, column block) tiles, no X scratch)
-  // unless SLSHT_OPT_FP64_ARITH asks for FP64 arithmetic
-  const bool ddx = f64 && route == 1 && fp64_arith == 0;
+  // unless SLSHT_OPT_FP64_ARITH asks for FP64 arithmetic or the tuner found
+  // FP64 arithmetic faster for this shape
+  const bool ddx = f64 && route == 1 && fp64_arith == 0 && tuned_engine != 0;
   if (ddx) {
     if (dd_form < 0 || (engine == 4 && dd_form != 0)) {
       dd_nt = dd_rule_cols(Lh, (long long)J);
@@ -1338,7 +1342,7 @@ static int batch_tune(slsht_batch* b, int ii) {
     // rule: the tensor cores where they apply; FP64 in double-float arithmetic
     // unless excluded; the split factor of alpha_split_factor
     it.engine = tc_ok ? ENG_TC : (dd_ok ? ENG_DD : ENG_NATIVE);
-    it.nt = batch_rule_nt(it.engine == ENG_DD ? 2 : (d.prec == SLSHT_FP64 ? 0 : 1), Lh, J);
+    it.nt = it.engine == ENG_DD ? dd_rule_cols(Lh, J) : batch_rule_nt(d.prec == SLSHT_FP64 ? 0 : 1, Lh, J);
     it.form = it.engine == ENG_TC ? -1 : alpha_split_factor(Lh, Na);
     it.tuned = 0;
     return SLSHT_OK;
@@ -1706,6 +1710,59 @@ extern "C" int slsht_batch_create(slsht_ctx* ctx, int32_t n_items, const slsht_b
   }
   *out = b;
   return SLSHT_OK;
+}
+
+extern "C" int slsht_tune(slsht_ctx* ctx, const slsht_desc* desc) {
+  if (!ctx) return SLSHT_E_ARG;
+  CKS(check_desc(desc));
+  DeviceGuard g(ctx->device);
+  // seeded synthetic coefficients: f_lm = (cos(0.7 i), sin(1.3 i)) / (l + 1),
+  // h the same at the window's band; pairs (L_f - 1, m) for |m| <= min(l, 7)
+  const int Lf = desc->L_f, Lh = desc->L_h;
+  std::vector<double> f(2 * (size_t)Lf * Lf), h(2 * (size_t)Lh * Lh);
+  for (int l = 0; l < Lf; ++l)
+    for (int m = -l; m <= l; ++m) {
+      const size_t i = (size_t)l * l + l + m;
+      f[2 * i] = std::cos(0.7 * i) / (l + 1);
+      f[2 * i + 1] = std::sin(1.3 * i) / (l + 1);
+    }
+  for (int l = 0; l < Lh; ++l)
+    for (int m = -l; m <= l; ++m) {
+      const size_t i = (size_t)l * l + l + m;
+      h[2 * i] = std::cos(0.9 * i + 0.3) / (l + 1);
+      h[2 * i + 1] = std::sin(1.1 * i + 0.2) / (l + 1);
+    }
+  std::vector<int32_t> lm;
+  const int l = Lf - 1;
+  for (int m = -std::min(l, 7); m <= std::min(l, 7); ++m) { lm.push_back(l); lm.push_back(m); }
+  const int np = (int)(lm.size() / 2);
+  const size_t gbytes = (size_t)np * desc->n_alpha * desc->n_beta * desc->n_gamma *
+                        (desc->prec == SLSHT_FP64 ? sizeof(double2) : sizeof(float2));
+  void *fd = nullptr, *hd = nullptr, *gd = nullptr;
+  int st = ctx_alloc(ctx, sizeof(double) * f.size(), &fd);
+  if (st == SLSHT_OK) st = ctx_alloc(ctx, sizeof(double) * h.size(), &hd);
+  if (st == SLSHT_OK) st = ctx_alloc(ctx, gbytes, &gd);
+  if (st == SLSHT_OK && (cudaMemcpy(fd, f.data(), sizeof(double) * f.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+                         cudaMemcpy(hd, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess)) {
+    cudaGetLastError();
+    st = SLSHT_E_CUDA;
+  }
+  if (st == SLSHT_OK) {
+    slsht_batch_item it{};
+    it.desc = *desc;
+    it.f_lm = (const double*)fd;
+    it.h_lm = (const double*)hd;
+    it.lm = lm.data();
+    it.n_pairs = np;
+    it.g_out = gd;
+    slsht_batch* b = nullptr;
+    st = slsht_batch_create(ctx, 1, &it, SLSHT_BATCH_NO_GRAPH, nullptr, &b);
+    if (st == SLSHT_OK) slsht_batch_destroy(b);
+  }
+  ctx_free(ctx, gd, gbytes);
+  ctx_free(ctx, hd, sizeof(double) * h.size());
+  ctx_free(ctx, fd, sizeof(double) * f.size());
+  return st;
 }
 
 extern "C" int slsht_batch_launch(slsht_batch* b, void* stream) {

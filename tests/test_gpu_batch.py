@@ -267,3 +267,19 @@ def test_double_float_matches_fp64_arithmetic(pkg, ctx):
         finally:
             b1.close()
             b2.close()
+
+
+def test_tune_feeds_per_call_fp64(pkg, ctx):
+    """slsht_tune measures one FP64 grid shape; the per-call forward then uses
+    the cached tile shape and stays within the FP64 tolerance, equal to the
+    untuned call to rounding."""
+    Lf, Lh, grid = 20, 9, (45, 20, 17)
+    f, h = synth.signal_powerlaw(Lf, 71), synth.window_cn(Lh, 72)
+    pairs = synth.pairs_random(Lf + Lh - 1, 9, 73)
+    ref = O.forward_coeff(f, h, Lf, Lh, pairs, grid)
+    before = ctx.forward(Lf, Lh, grid, f, h, pairs, prec=0).cpu().numpy()
+    ctx.tune(Lf, Lh, grid, 0)
+    after = ctx.forward(Lf, Lh, grid, f, h, pairs, prec=0).cpu().numpy()
+    assert rel(before, ref) < 1e-12
+    assert rel(after, ref) < 1e-12
+    assert rel(after, before) < 1e-13
