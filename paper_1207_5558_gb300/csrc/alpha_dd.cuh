@@ -50,12 +50,16 @@ __device__ __forceinline__ float4 ddc_pack(ddc a) { return make_float4(a.re.h, a
 struct DdOut {
   double2* dst;
   double2* mdst;
-  double sgn;
+  unsigned long long sgn;   // sign bit of (-1)^m: 0 or 1 << 63
   int sc;
   __device__ __forceinline__ void put(size_t off, ddv re, ddv im) const {
     const double r = dd_to_double(re.h, re.l, sc), i = dd_to_double(im.h, im.l, sc);
     dst[off] = make_double2(r, i);
-    if (mdst != nullptr) mdst[off] = make_double2(sgn * r, -sgn * i);
+    if (mdst != nullptr) {   // (-1)^m conj(g): sign flips on the bit patterns, no FP64 multiply
+      const unsigned long long br = (unsigned long long)__double_as_longlong(r) ^ sgn;
+      const unsigned long long bi = (unsigned long long)__double_as_longlong(i) ^ sgn ^ (1ull << 63);
+      mdst[off] = make_double2(__longlong_as_double((long long)br), __longlong_as_double((long long)bi));
+    }
   }
 };
 

@@ -384,7 +384,7 @@ __device__ __forceinline__ void ba_tile_dd(const BItem& it, const BTile& tl, uns
   DdOut out;
   out.dst = g + (size_t)sl.x * Na * J + j;
   out.mdst = sl.y >= 0 ? g + (size_t)(sl.y >> 1) * Na * J + j : nullptr;
-  out.sgn = (sl.y & 1) ? -1.0 : 1.0;
+  out.sgn = (sl.y & 1) ? (1ull << 63) : 0ull;
   out.sc = it.kexp[tl.pair] + *it.hexp;
   switch (it.form) {
     case 0:

@@ -72,13 +72,19 @@ __device__ __forceinline__ void dd_acc_get(const dd_acc& a, float* h, float* l) 
 // The 53-bit significand is M = m_h 2^29 + round(l / 2^(e_h - 52)), shifted
 // once if l moved it out of [2^52, 2^53).  Zero, FP32-subnormal h, h below
 // 2^-74 and results outside the double's normal range take the FP64 route.
+// The rare cases of dd_to_double in FP64 arithmetic, kept out of line so
+// the compiler does not evaluate them speculatively beside the common path.
+__device__ __noinline__ double dd_to_double_slow(float h, float l, int sc) {
+  return ldexp((double)h + (double)l, sc);
+}
+
 __device__ __forceinline__ double dd_to_double(float h, float l, int sc) {
   const uint32_t bh = __float_as_uint(h);
   const int eh = (int)((bh >> 23) & 0xffu);          // biased exponent of h
   const int e = eh - 127 + sc;                        // unbiased exponent of the result
   if (eh < 53 || eh == 255 || e < -1000 || e > 1000) {
     // rare: h = 0 (then l = 0), tiny h, or an extreme scale
-    return ldexp((double)h + (double)l, sc);
+    return dd_to_double_slow(h, l, sc);
   }
   const int64_t m = (int64_t)((bh & 0x7fffffu) | 0x800000u) << 29;
   // l in units of 2^(eh - 127 - 52): an exact power-of-two scaling (|l| <= 2^(eh - 127 - 23)
