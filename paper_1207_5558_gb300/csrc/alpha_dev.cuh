@@ -99,20 +99,25 @@ __device__ __forceinline__ void alpha_split_column(const typename vec2<T>::t* __
     q += (((r - q) % P) + P) % P;
     qfirst[r] = q;
   }
+  const int nq = (K + P - 1) / P;          // most orders in one residue class
   for (int tt = t_first; tt < Q; tt += t_step) {
     const T2* w = tw + (size_t)tt * K + (Lh - 1);
+    // the P residue classes advance together, one order of each per step:
+    // 2P independent multiply-add chains
     T zr[P], zi[P];
 #pragma unroll
-    for (int r = 0; r < P; ++r) {
-      T ar = 0, ai = 0;
-      for (int q = qfirst[r]; q < Lh; q += P) {       // X_q e^{-i theta} = X_q (cos - i sin)
-        const T2 x = sx[(q + Lh - 1) * ld];
-        const T2 e = __ldg(w + q);
-        ar = fma(x.x, e.x, ar); ar = fma(x.y, e.y, ar);
-        ai = fma(x.y, e.x, ai); ai = fma(-x.x, e.y, ai);
+    for (int r = 0; r < P; ++r) zr[r] = zi[r] = (T)0;
+    for (int jj = 0; jj < nq; ++jj) {
+#pragma unroll
+      for (int r = 0; r < P; ++r) {
+        const int q = qfirst[r] + jj * P;
+        if (q < Lh) {                                  // X_q e^{-i theta} = X_q (cos - i sin)
+          const T2 x = sx[(q + Lh - 1) * ld];
+          const T2 e = __ldg(w + q);
+          zr[r] = fma(x.x, e.x, zr[r]); zr[r] = fma(x.y, e.y, zr[r]);
+          zi[r] = fma(x.y, e.x, zi[r]); zi[r] = fma(-x.x, e.y, zi[r]);
+        }
       }
-      zr[r] = ar;
-      zi[r] = ai;
     }
     // folded pairs Z_r +- Z_{P-r}, once per t
     T sr[H + 1], si[H + 1], dr[H + 1], di[H + 1];

@@ -629,6 +629,8 @@ static void mirror_work(const int32_t* lm, int32_t n, std::vector<int32_t>* out)
   }
 }
 
+static int batch_rule_nt(int kp, int Lh, long long J);
+
 // Columns per tile of the double-float alpha kernel by rule: 32 for at most
 // 32 columns, else 64 (two row groups a column), within the shared-memory limit.
 static int dd_rule_cols(int Lh, long long J) {
@@ -654,6 +656,7 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
   int route, tc, engine, gt_opt, wait_test, coupling, fp64_arith;
   int64_t chunk_opt;
   int dd_nt = 0, dd_form = -1, tuned_engine = -1;
+  int cc_nt = 0, cc_form = -1;
   {
     std::lock_guard<std::mutex> g(ctx->mu);
     route = ctx->opt_beta_route ? ctx->opt_beta_route : 1;
@@ -664,13 +667,18 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
     wait_test = ctx->opt_wait_test;
     coupling = ctx->opt_coupling;
     fp64_arith = ctx->opt_fp64_arith;
-    // a tile shape the batch-plan tuner measured for this FP64 shape, if any
-    auto tf = ctx->tune.find(std::make_tuple((int)SLSHT_FP64, Lh, Na, Nb, Ng, 6));
+    // a tile shape the batch-plan tuner measured for this shape, if any
+    // (FP64: both arithmetics allowed; FP32: the tensor cores where they apply)
+    const int allowed = f64 ? 6 : ((tc_supported(Lh, Na) && Lh <= 16) ? 5 : 4);
+    auto tf = ctx->tune.find(std::make_tuple((int)d->prec, Lh, Na, Nb, Ng, allowed));
     if (tf != ctx->tune.end()) {
       tuned_engine = std::get<2>(tf->second);
       if (tuned_engine == 1) {
         dd_nt = std::get<0>(tf->second);
         dd_form = std::get<1>(tf->second);
+      } else if (tuned_engine == 0) {
+        cc_nt = std::get<0>(tf->second);
+        cc_form = std::get<1>(tf->second);
       }
     }
   }
@@ -691,6 +699,15 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
       dd_form = engine == 4 ? 0 : alpha_split_factor(Lh, Na);
     }
   }
+  // other CUDA-core calls on the rotated-window route: the same tile kernel
+  // in the call's own precision (X in shared memory, no X scratch)
+  const bool cc1 = !tc && route == 1 && !ddx;
+  if (cc1) {
+    if (cc_form < 0 || (engine == 4 && cc_form != 0)) {
+      cc_nt = batch_rule_nt(f64 ? 0 : 1, Lh, (long long)J);
+      cc_form = engine == 4 ? 0 : alpha_split_factor(Lh, Na);
+    }
+  }
   // tables
   const double* D = nullptr;
   const void* dt = nullptr;
@@ -705,6 +722,8 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
     if (tc) CKS(get_etab(ctx, Na, Lh, st, &etab));
     else if (ddx && dd_form > 0) CKS(get_phase(ctx, Na, K, -(Lh - 1), PREC_DD, st, &csa));
     else if (ddx) CKS(get_phase(ctx, Na, Lh, 0, PREC_DD, st, &csa));
+    else if (cc1 && cc_form > 0) CKS(get_phase(ctx, Na, K, -(Lh - 1), d->prec, st, &csa));
+    else if (cc1) CKS(get_phase(ctx, Na, Lh, 0, d->prec, st, &csa));
     else if (split) CKS(get_phase(ctx, Na, K, -(Lh - 1), d->prec, st, &csa));   // twiddles of the split DFT
     else CKS(get_phase(ctx, Na, Lh, 0, d->prec, st, &csa));
   }
@@ -719,7 +738,7 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
   int P;
   if (chunk_opt > 0) {
     P = (int)std::min<int64_t>(chunk_opt, n_pairs);
-  } else if (fused || ddx) {
+  } else if (fused || ddx || cc1) {
     P = n_pairs;                 // no X scratch: one launch per call
   } else {
     const size_t target = (size_t)96 << 20;
@@ -732,7 +751,7 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
     P = (int)std::max<size_t>(1, std::min<size_t>((size_t)P, stage_limit / std::max<size_t>(1, per_pair_g)));
   }
   CKS(ws_reserve(ctx, w, &w.kc, &w.kc_cap, sizeof(double2) * (size_t)n_pairs * Lh * Lh));
-  if (!fused && !ddx) {
+  if (!fused && !ddx && !cc1) {
     CKS(ws_reserve(ctx, w, &w.X, &w.X_cap, x_per_pair * (size_t)P));
     CKS(ws_reserve(ctx, w, &w.X2, &w.X2_cap, x_per_pair * (size_t)P));
   }
@@ -821,7 +840,7 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
     const int np = std::min<int>(P, n_pairs - off);
     void* X = Xb[ci & 1];
     const double2* kcc = (const double2*)w.kc + (size_t)off * Lh * Lh;
-    if (fused || ddx) {
+    if (fused || ddx || cc1) {
       // every chunk reads the couplings and H that the aux stream produced once
       if (ci == 0) {
         CK(cudaEventRecord(w.x_ready[0], ax));
@@ -837,16 +856,8 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
       }
       const double2* Ysrc = route == 2 ? (const double2*)w.Y : nullptr;
       if (route == 1) {
-        if (tc) {
-          LAUNCH(SLSHT_STAGE_BETA, ax,
-                 launch_xa_from_h(kcc, (const float2*)w.H, Lh, Nb, Ng, np, X, ax));
-        } else if (f64) {
-          LAUNCH(SLSHT_STAGE_BETA, ax,
-                 launch_x_from_h_f64(kcc, (const double2*)w.H, Lh, (int)J, np, (double2*)X, ax));
-        } else {
-          LAUNCH(SLSHT_STAGE_BETA, ax,
-                 launch_x_from_h_f32(kcc, (const float2*)w.H, Lh, (int)J, np, (float2*)X, ax));
-        }
+        // (route 1 on CUDA cores forms X inside the alpha tile kernel)
+        LAUNCH(SLSHT_STAGE_BETA, ax, launch_xa_from_h(kcc, (const float2*)w.H, Lh, Nb, Ng, np, X, ax));
       } else if (tc) {
         LAUNCH(SLSHT_STAGE_BETA, ax,
                launch_betagamma_tc(kcc, (const double2*)h_dev, nullptr, Ysrc, (const float2*)eg, Lh, Nb, Ng, np, X, ax));
@@ -886,7 +897,21 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
       item.J = (int)J;
       item.nt = dd_nt;
       item.form = dd_form;
-      LAUNCH(SLSHT_STAGE_ALPHA, st, launch_alpha_dd_call(item, np, ctx->num_sms, st));
+      LAUNCH(SLSHT_STAGE_ALPHA, st, launch_alpha_call(item, np, ctx->num_sms, st));
+    } else if (cc1) {
+      BItem item{};
+      item.kc = kcc;
+      item.H = w.H;
+      item.csa = csa;
+      item.g = gdst;
+      item.slots = sl;
+      item.prec = f64 ? 0 : 1;
+      item.Lh = Lh;
+      item.Na = Na;
+      item.J = (int)J;
+      item.nt = cc_nt;
+      item.form = cc_form;
+      LAUNCH(SLSHT_STAGE_ALPHA, st, launch_alpha_call(item, np, ctx->num_sms, st));
     } else if (fused) {
       LAUNCH(SLSHT_STAGE_ALPHA, st,
              launch_alpha_fused(kcc, (const float2*)w.H, etab, Lh, Na, Nb, Ng, np, (float2*)gdst, ctx->num_sms,
@@ -911,7 +936,7 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
                    : launch_alpha_f32((const float2*)X, (const float2*)csa, Lh, Na, (int)J, np, (float2*)gdst, sl,
                                       st));
     }
-    if (!fused && !ddx) CK(cudaEventRecord(w.x_free[ci & 1], st));
+    if (!fused && !ddx && !cc1) CK(cudaEventRecord(w.x_free[ci & 1], st));
     if (host_out) {
       CK(cudaEventRecord(w.stage_ev[ci & 1], st));
       CK(cudaStreamWaitEvent(w.copy_stream, w.stage_ev[ci & 1], 0));
@@ -1223,12 +1248,12 @@ static double alpha_form_cost(int Lh, int form) {
   return 4.0 * (2 * Lh - 1) / form + form + 3.0;
 }
 
-// Columns per tile by rule: the smallest of 32/64/128 covering min(J, 128)
-// whose X tile fits the shared-memory limit (kp: alpha kernel 0 FP64, 1
-// FP32, 2 double-float).
+// Columns per tile by rule: the smallest of 32/64/128 covering min(J, 128),
+// halved while its X tile exceeds 48 KB (so that four CTAs fit an SM; kp:
+// alpha kernel 0 FP64, 1 FP32, 2 double-float).
 static int batch_rule_nt(int kp, int Lh, long long J) {
   int nt = J <= 32 ? 32 : (J <= 64 ? 64 : 128);
-  while (nt > 32 && batch_alpha_smem(kp, Lh, nt) > BA_SMEM_LIMIT) nt /= 2;
+  while (nt > 32 && batch_alpha_smem(kp, Lh, nt) > (size_t)48 * 1024) nt /= 2;
   return nt;
 }
 
@@ -1527,12 +1552,14 @@ static int batch_build(slsht_batch* b, const slsht_batch_item* src, int32_t n, c
         CKS(get_phase(ctx, d.n_gamma, K, -(Lh - 1), d.prec, b->cs, &r.eg));
       }
       CKS(batch_alloc(b, el2_of(d.prec) * h_elems((size_t)J, n2), &r.H));
-      const size_t sm = rotwin_smem_bytes(Lh, d.n_gamma, el2_of(d.prec));
-      r.smem_ok = sm <= (size_t)BA_SMEM_LIMIT ? 1 : 0;
-      if (r.smem_ok) b->rot_smem = std::max(b->rot_smem, sm);
+      const RotChunks ch = rot_chunks(Lh, d.n_gamma, el2_of(d.prec));
+      r.QC = ch.QC; r.CC = ch.CC; r.nq = ch.nq; r.nc = ch.nc;
+      b->rot_smem = std::max(b->rot_smem, ch.smem(Lh, el2_of(d.prec)));
       const int ri = (int)b->rot.size();
       for (int bb = 0; bb < d.n_beta; ++bb)
-        for (int p = 0; p < Lh; ++p) b->rblk.push_back({ri, bb, p, 0});
+        for (int p = 0; p < Lh; ++p)
+          for (int z = 0; z < ch.nq * ch.nc; ++z)
+            if ((z / ch.nc) * ch.QC < 2 * p + 1) b->rblk.push_back({ri, bb, p, z});
       rf = rkey.emplace(rk, ri).first;
       b->rot.push_back(r);
     }

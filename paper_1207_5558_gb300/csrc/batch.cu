@@ -130,7 +130,7 @@ struct RotwinBoth {
 // (every block finds the same e; block (0, 0) records it in *hexp).
 __device__ __forceinline__ void rotwin_block_fp64(const double2* __restrict__ h, const double* __restrict__ dblk,
                                                   const double2* __restrict__ eg, int Lh, int Ng, int b, int p,
-                                                  double2* H, float4* Hdd, int* hexp, int smem_ok,
+                                                  const RotChunks& ch, int z, double2* H, float4* Hdd, int* hexp,
                                                   unsigned char* smem) {
   __shared__ double red[4];
   int e = 0;
@@ -141,13 +141,9 @@ __device__ __forceinline__ void rotwin_block_fp64(const double2* __restrict__ h,
       mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
     }
     e = scale_exp(block_max(mx, red));
-    if (b == 0 && p == 0 && threadIdx.x == 0) *hexp = e;
+    if (b == 0 && p == 0 && z == 0 && threadIdx.x == 0) *hexp = e;
   }
-  const RotwinBoth st{H, Hdd, e};
-  if (smem_ok)
-    rotwin_block_smem_to<double>(h, dblk, eg, Lh, Ng, b, p, st, smem);
-  else
-    rotwin_block_direct_to<double>(h, dblk, eg, Lh, Ng, b, p, st);
+  rotwin_block_smem_to<double>(h, dblk, eg, Lh, Ng, b, p, ch, z, RotwinBoth{H, Hdd, e}, smem);
 }
 
 __global__ void __launch_bounds__(128) k_batch_rotwin(const BRot* __restrict__ rot, const BRotBlk* __restrict__ blk) {
@@ -155,45 +151,43 @@ __global__ void __launch_bounds__(128) k_batch_rotwin(const BRot* __restrict__ r
   const BRotBlk bb = blk[blockIdx.x];
   const BRot r = rot[bb.rot];
   const size_t off = (size_t)bb.b * blk_off(r.Lh) + blk_off(bb.p);
+  RotChunks ch;
+  ch.QC = r.QC; ch.CC = r.CC; ch.nq = r.nq; ch.nc = r.nc;
   if (r.prec == 0) {
-    rotwin_block_fp64(r.h, (const double*)r.dt + off, (const double2*)r.eg, r.Lh, r.Ng, bb.b, bb.p,
-                      (double2*)r.H, r.Hdd, r.hexp, r.smem_ok, smem_raw);
+    rotwin_block_fp64(r.h, (const double*)r.dt + off, (const double2*)r.eg, r.Lh, r.Ng, bb.b, bb.p, ch, bb.z,
+                      (double2*)r.H, r.Hdd, r.hexp, smem_raw);
   } else {
-    const float* d = (const float*)r.dt + off;
-    if (r.smem_ok)
-      rotwin_block_smem<float>(r.h, d, (const float2*)r.eg, r.Lh, r.Ng, bb.b, bb.p, (float2*)r.H, smem_raw);
-    else
-      rotwin_block_direct_to<float>(r.h, d, (const float2*)r.eg, r.Lh, r.Ng, bb.b, bb.p, RotwinStore<float>{(float2*)r.H});
+    rotwin_block_smem_to<float>(r.h, (const float*)r.dt + off, (const float2*)r.eg, r.Lh, r.Ng, bb.b, bb.p, ch,
+                                bb.z, RotwinStore<float>{(float2*)r.H}, smem_raw);
   }
 }
 
 cudaError_t launch_batch_rotwin(const BRot* rot, const BRotBlk* blk, int nblk, size_t smem, cudaStream_t st) {
   if (nblk <= 0) return cudaSuccess;
-  if (smem > BA_SMEM_LIMIT) return cudaErrorInvalidValue;
+  if (smem > ROTWIN_SMEM_LIMIT) return cudaErrorInvalidValue;
   cudaError_t e = batch_attrs();
   if (e != cudaSuccess) return e;
   k_batch_rotwin<<<nblk, 128, smem, st>>>(rot, blk);
   return cudaGetLastError();
 }
 
-// grid (Nb, Lh): the scaled double-float window of one call
+// grid (Nb, Lh, chunks): the scaled double-float window of one call
 __global__ void __launch_bounds__(128) k_rotwin_dd(const double2* __restrict__ h, const double* __restrict__ dt,
-                                                   const double2* __restrict__ eg, int Lh, int Ng, float4* Hdd,
-                                                   int* hexp, int smem_ok) {
+                                                   const double2* __restrict__ eg, int Lh, int Ng, RotChunks ch,
+                                                   float4* Hdd, int* hexp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b = blockIdx.x, p = blockIdx.y;
-  rotwin_block_fp64(h, dt + (size_t)b * blk_off(Lh) + blk_off(p), eg, Lh, Ng, b, p, nullptr, Hdd, hexp, smem_ok,
-                    smem_raw);
+  rotwin_block_fp64(h, dt + (size_t)b * blk_off(Lh) + blk_off(p), eg, Lh, Ng, b, p, ch, blockIdx.z, nullptr, Hdd,
+                    hexp, smem_raw);
 }
 
 cudaError_t launch_rotwin_dd(const double2* h, const double* dt, const double2* eg, int Lh, int Nb, int Ng,
                              float4* Hdd, int* hexp, cudaStream_t st) {
-  const size_t sm = rotwin_smem_bytes(Lh, Ng, sizeof(double2));
-  const int ok = sm <= (size_t)BA_SMEM_LIMIT ? 1 : 0;
+  const RotChunks ch = rot_chunks(Lh, Ng, sizeof(double2));
   cudaError_t e = batch_attrs();
   if (e != cudaSuccess) return e;
-  dim3 grid(Nb, Lh);
-  k_rotwin_dd<<<grid, 128, ok ? sm : 0, st>>>(h, dt, eg, Lh, Ng, Hdd, hexp, ok);
+  dim3 grid(Nb, Lh, ch.nq * ch.nc);
+  k_rotwin_dd<<<grid, 128, ch.smem(Lh, sizeof(double2)), st>>>(h, dt, eg, Lh, Ng, ch, Hdd, hexp);
   return cudaGetLastError();
 }
 
@@ -204,13 +198,13 @@ cudaError_t launch_rotwin_dd(const double2* h, const double* dt, const double2* 
 
 template <typename T, int P>
 __device__ __forceinline__ void ba_split(const BItem& it, const BTile& tl, const typename vec2<T>::t* sx, const T* cst,
-                                         typename vec2<T>::t* dst, int c, int s) {
+                                         typename vec2<T>::t* dst, typename vec2<T>::t* mdst, T sgn, int c, int s) {
   constexpr int H = (P - 1) / 2;
   const int S = BA_THREADS / it.nt;
   const T(*cpr)[H + 1] = reinterpret_cast<const T(*)[H + 1]>(cst);
   const T(*spr)[H + 1] = reinterpret_cast<const T(*)[H + 1]>(cst + BA_CONST_ENTRIES);
   alpha_split_column<T, P>(sx + c, it.nt, it.Lh, it.Na, it.J, reinterpret_cast<const typename vec2<T>::t*>(it.csa),
-                           cpr, spr, dst, nullptr, (T)1, s, S);
+                           cpr, spr, dst, mdst, sgn, s, S);
 }
 
 template <typename T, int P>
@@ -281,17 +275,21 @@ __device__ __forceinline__ void ba_tile(const BItem& it, const BTile& tl, unsign
   }
   const int c = tid % NT, s = tid / NT, j = tl.j0 + c;
   if (j >= J) return;
-  T2* dst = reinterpret_cast<T2*>(it.g) + (size_t)tl.out * Na * J + j;
+  // output slot and, for a mirrored pair, the slot of (l, -m) with (-1)^m
+  const int2 sl = it.slots != nullptr ? it.slots[tl.pair] : make_int2(tl.out, -1);
+  T2* g = reinterpret_cast<T2*>(it.g);
+  T2* dst = g + (size_t)sl.x * Na * J + j;
+  T2* mdst = sl.y >= 0 ? g + (size_t)(sl.y >> 1) * Na * J + j : nullptr;
+  const T sgn = (sl.y & 1) ? (T)-1 : (T)1;
   switch (it.form) {
     case 0:
       alpha_direct_column<T>(sx + c, NT, Lh - 1, Lh - 1, 1, Lh - 1, -1, Lh, Na, J,
-                             reinterpret_cast<const T2*>(it.csa), dst, nullptr, (T)1, s * ALPHA_ABLK,
-                             S * ALPHA_ABLK);
+                             reinterpret_cast<const T2*>(it.csa), dst, mdst, sgn, s * ALPHA_ABLK, S * ALPHA_ABLK);
       break;
-    case 3: ba_split<T, 3>(it, tl, sx, cst, dst, c, s); break;
-    case 5: ba_split<T, 5>(it, tl, sx, cst, dst, c, s); break;
-    case 7: ba_split<T, 7>(it, tl, sx, cst, dst, c, s); break;
-    case 9: ba_split<T, 9>(it, tl, sx, cst, dst, c, s); break;
+    case 3: ba_split<T, 3>(it, tl, sx, cst, dst, mdst, sgn, c, s); break;
+    case 5: ba_split<T, 5>(it, tl, sx, cst, dst, mdst, sgn, c, s); break;
+    case 7: ba_split<T, 7>(it, tl, sx, cst, dst, mdst, sgn, c, s); break;
+    case 9: ba_split<T, 9>(it, tl, sx, cst, dst, mdst, sgn, c, s); break;
     default: break;
   }
 }
@@ -416,8 +414,20 @@ __global__ void __launch_bounds__(BA_THREADS) k_batch_alpha_dd(const BItem* __re
   }
 }
 
-// One item, every (pair, column block) tile in index order, CTAs striding
-// (equal tiles: no counter needed).
+// One item in FP64 or FP32 arithmetic, every (pair, column block) tile in
+// index order, CTAs striding (equal tiles: no counter needed).
+template <typename T>
+__global__ void __launch_bounds__(BA_THREADS) k_alpha_single(const BItem it, int ntiles) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ntj = (it.J + it.nt - 1) / it.nt;
+  for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+    const BTile tl{0, ti / ntj, ti / ntj, (ti % ntj) * it.nt};
+    ba_tile<T>(it, tl, smem_raw);
+    __syncthreads();
+  }
+}
+
+// The same for the double-float engine.
 __global__ void __launch_bounds__(BA_THREADS) k_alpha_dd_single(const BItem it, int ntiles) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int ntj = (it.J + it.nt - 1) / it.nt;
@@ -478,6 +488,10 @@ static cudaError_t batch_attrs() {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_alpha_dd_single, cudaFuncAttributeMaxDynamicSharedMemorySize, BA_SMEM_LIMIT);
     if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_alpha_single<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, BA_SMEM_LIMIT);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_alpha_single<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, BA_SMEM_LIMIT);
+    if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_rotwin_dd, cudaFuncAttributeMaxDynamicSharedMemorySize, BA_SMEM_LIMIT);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_batch_rotwin, cudaFuncAttributeMaxDynamicSharedMemorySize, BA_SMEM_LIMIT);
@@ -512,19 +526,27 @@ cudaError_t launch_batch_alpha(int prec, const BItem* items, const BTile* tiles,
 }
 
 cudaError_t launch_alpha_dd_call(const BItem& item, int npairs, int num_sms, cudaStream_t st) {
+  return launch_alpha_call(item, npairs, num_sms, st);
+}
+
+cudaError_t launch_alpha_call(const BItem& item, int npairs, int num_sms, cudaStream_t st) {
   if (npairs <= 0 || item.J <= 0) return cudaSuccess;
-  const size_t smem = batch_alpha_smem(2, item.Lh, item.nt);
+  const size_t smem = batch_alpha_smem(item.prec, item.Lh, item.nt);
   if (smem > BA_SMEM_LIMIT) return cudaErrorInvalidValue;
   cudaError_t e = batch_attrs();
   if (e != cudaSuccess) return e;
+  const void* fn = item.prec == 2 ? (const void*)k_alpha_dd_single
+                   : (item.prec == 0 ? (const void*)k_alpha_single<double> : (const void*)k_alpha_single<float>);
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_alpha_dd_single, BA_THREADS, smem) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, BA_THREADS, smem) != cudaSuccess) {
     cudaGetLastError();
     occ = 1;
   }
   const long long ntiles = (long long)npairs * ((item.J + item.nt - 1) / item.nt);
   if (ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
   const int grid = (int)std::min<long long>((long long)num_sms * std::max(occ, 1), ntiles);
-  k_alpha_dd_single<<<grid, BA_THREADS, smem, st>>>(item, (int)ntiles);
+  if (item.prec == 2) k_alpha_dd_single<<<grid, BA_THREADS, smem, st>>>(item, (int)ntiles);
+  else if (item.prec == 0) k_alpha_single<double><<<grid, BA_THREADS, smem, st>>>(item, (int)ntiles);
+  else k_alpha_single<float><<<grid, BA_THREADS, smem, st>>>(item, (int)ntiles);
   return cudaGetLastError();
 }

@@ -33,9 +33,10 @@ struct BRot {                    // one rotated window H
   void* H;                       // tiled H (h_index), T2 (null: not needed)
   float4* Hdd;                   // FP64 windows: double-float H scaled by 2^-hexp[0] (null: not needed)
   int* hexp;
-  int prec, Lh, Ng, smem_ok;     // prec 0: FP64, 1: FP32
+  int prec, Lh, Ng;              // prec 0: FP64, 1: FP32
+  int QC, CC, nq, nc;            // shared-memory chunking (rot_chunks)
 };
-struct BRotBlk { int rot, b, p, pad; };
+struct BRotBlk { int rot, b, p, z; };      // z: chunk of (q rows, gamma columns)
 
 struct BItem {                   // one analysis of the batch (alpha stage view)
   const double2* kc;             // k [pair][Lh^2]
@@ -64,14 +65,16 @@ cudaError_t launch_batch_couple(const BCouple* cpl, const BCplBlk* blk, int nblk
 // Double-float k of the couplings that need it: block list {cpl, pair}.
 cudaError_t launch_batch_kdd(const BCouple* cpl, const BCplBlk* blk, int nblk, cudaStream_t st);
 cudaError_t launch_batch_rotwin(const BRot* rot, const BRotBlk* blk, int nblk, size_t smem, cudaStream_t st);
-// One call's double-float pieces (the per-call FP64 path): k of npairs pairs
-// scaled into kdd/kexp; the rotated window's scaled double-float copy; the
-// alpha stage of one item over all its (pair, column block) tiles, tiles
-// derived from the index (no list), CTAs striding over them.
+// One call's pieces (the per-call path): k of npairs pairs scaled into
+// kdd/kexp; the rotated window's scaled double-float copy; the alpha stage
+// of one item over all its (pair, column block) tiles, tiles derived from
+// the index (no list), CTAs striding over them.
 cudaError_t launch_kdd_pairs(const double2* kc, int Lh, int npairs, float4* kdd, int* kexp, cudaStream_t st);
 cudaError_t launch_rotwin_dd(const double2* h, const double* dt, const double2* eg, int Lh, int Nb, int Ng,
                              float4* Hdd, int* hexp, cudaStream_t st);
 cudaError_t launch_alpha_dd_call(const BItem& item, int npairs, int num_sms, cudaStream_t st);
+// The same for an item of any precision (item.prec 0 FP64, 1 FP32, 2 double-float).
+cudaError_t launch_alpha_call(const BItem& item, int npairs, int num_sms, cudaStream_t st);
 
 // Persistent: `grid` CTAs take tiles from *counter (reset to 0 before each
 // launch); every tile's item has precision prec (0 FP64, 1 FP32, 2 double-float).

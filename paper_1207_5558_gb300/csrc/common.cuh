@@ -102,13 +102,6 @@ cudaError_t launch_rotwin_f64(const double2* h, const double* dt, const double2*
                               double2* H, cudaStream_t st);
 cudaError_t launch_rotwin_f32(const double2* h, const float* dt, const float2* eg, int Lh, int Nb, int Ng,
                               float2* H, cudaStream_t st);
-// X_q(j) = sum_{p>=|q|} k(p,q) H^p_q(j), written in the paired form of
-// launch_betagamma_* for the CUDA-core alpha stage.
-cudaError_t launch_x_from_h_f64(const double2* kc, const double2* H, int Lh, int J, int npairs, double2* Xs,
-                                cudaStream_t st);
-cudaError_t launch_x_from_h_f32(const double2* kc, const float2* H, int Lh, int J, int npairs, float2* Xs,
-                                cudaStream_t st);
-
 // g[pair][a][j] = X_0 + sum_r (P_r cos(r alpha_a) - i M_r sin(r alpha_a)).
 // slots (nullable): per pair {output slot, mirror} as for launch_alpha_tc.
 cudaError_t launch_alpha_f64(const double2* Xs, const double2* csa, int Lh, int Na, int J,

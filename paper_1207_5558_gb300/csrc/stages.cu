@@ -235,64 +235,30 @@ cudaError_t launch_betagamma_f32(const double2* kc, const double2* h, const floa
 // H is the window's coefficients rotated by (0, beta_b, gamma_c) (Eq. rotation_non_symm
 // with Eq. Dlm): it does not depend on the pair (l, m), so it is built once per call and
 // every pair costs only Lh^2 multiply-adds per column.
-// H in the tiled layout of h_index.
-template <typename T>
-__global__ void k_rotwin(const double2* __restrict__ h, const T* __restrict__ dt,
-                         const typename vec2<T>::t* __restrict__ eg, int Lh, int Nb, int Ng,
-                         typename vec2<T>::t* __restrict__ H) {
-  typedef typename vec2<T>::t T2;
-  const int K = 2 * Lh - 1, S = blk_off(Lh), n2 = Lh * Lh;
-  const int b = blockIdx.x;
-  for (int t = blockIdx.y * blockDim.x + threadIdx.x; t < n2 * Ng; t += gridDim.y * blockDim.x) {
-    const int pq = t / Ng, c = t % Ng;
-    int p = (int)sqrt((double)pq);
-    while (p * p > pq) --p;
-    while ((p + 1) * (p + 1) <= pq) ++p;
-    const int q = pq - p * p - p;
-    const T* drow = dt + (size_t)b * S + blk_off(p) + (q + p) * (2 * p + 1);
-    const T2* erow = eg + (size_t)c * K + (Lh - 1);
-    T re = 0, im = 0;
-    for (int qp = -p; qp <= p; ++qp) {           // h d (cos - i sin)
-      const double2 hv = __ldg(h + p * p + p + qp);
-      const T d = __ldg(drow + qp + p);
-      const T2 E = erow[qp];
-      const T ar = d * (T)hv.x, ai = d * (T)hv.y;
-      re = fma(ar, E.x, re); re = fma(ai, E.y, re);
-      im = fma(ai, E.x, im); im = fma(-ar, E.y, im);
-    }
-    H[h_index(pq, b * Ng + c, n2)] = mk2(re, im);
-  }
-}
-
-// The same H with one CTA per (beta row b, degree p): rotwin_block_smem
-// (stages_dev.cuh).
+// H in the tiled layout of h_index.  One CTA per (beta row b, degree p,
+// chunk): rotwin_block_smem_to (stages_dev.cuh).
 template <typename T>
 __global__ void __launch_bounds__(128) k_rotwin_smem(const double2* __restrict__ h, const T* __restrict__ dt,
                                                      const typename vec2<T>::t* __restrict__ eg, int Lh, int Nb,
-                                                     int Ng, typename vec2<T>::t* __restrict__ H) {
+                                                     int Ng, RotChunks ch, typename vec2<T>::t* __restrict__ H) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b = blockIdx.x, p = blockIdx.y;
-  rotwin_block_smem<T>(h, dt + (size_t)b * blk_off(Lh) + blk_off(p), eg, Lh, Ng, b, p, H, smem_raw);
+  rotwin_block_smem_to<T>(h, dt + (size_t)b * blk_off(Lh) + blk_off(p), eg, Lh, Ng, b, p, ch, blockIdx.z,
+                          RotwinStore<T>{H}, smem_raw);
 }
 
 template <typename T>
 static cudaError_t launch_rotwin_t(const double2* h, const T* dt, const typename vec2<T>::t* eg, int Lh,
                                    int Nb, int Ng, typename vec2<T>::t* H, cudaStream_t st) {
   typedef typename vec2<T>::t T2;
-  const int K = 2 * Lh - 1;
-  const size_t smem = sizeof(T2) * ((size_t)K * K + (size_t)Ng * K);
-  if (smem <= 200 * 1024) {
-    if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(k_rotwin_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-    }
-    dim3 grid(Nb, Lh);
-    k_rotwin_smem<T><<<grid, 128, smem, st>>>(h, dt, eg, Lh, Nb, Ng, H);
-    return cudaGetLastError();
+  const RotChunks ch = rot_chunks(Lh, Ng, sizeof(T2));
+  const size_t smem = ch.smem(Lh, sizeof(T2));
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_rotwin_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
   }
-  const long long items = (long long)Lh * Lh * Ng;
-  dim3 grid(Nb, (unsigned)std::min<long long>((items + 255) / 256, 64));
-  k_rotwin<T><<<grid, 256, 0, st>>>(h, dt, eg, Lh, Nb, Ng, H);
+  dim3 grid(Nb, Lh, ch.nq * ch.nc);
+  k_rotwin_smem<T><<<grid, 128, smem, st>>>(h, dt, eg, Lh, Nb, Ng, ch, H);
   return cudaGetLastError();
 }
 
@@ -303,76 +269,4 @@ cudaError_t launch_rotwin_f64(const double2* h, const double* dt, const double2*
 cudaError_t launch_rotwin_f32(const double2* h, const float* dt, const float2* eg, int Lh, int Nb, int Ng,
                               float2* H, cudaStream_t st) {
   return launch_rotwin_t<float>(h, dt, eg, Lh, Nb, Ng, H, st);
-}
-
-// X from H for the CUDA-core alpha stage (paired output as k_betagamma):
-//   X_q(j) = sum_{p>=|q|} k(p,q) H^p_q(j); Xs[0] = X_0, Xs[2r-1] = X_r + X_-r, Xs[2r] = X_r - X_-r.
-// One thread per column j, loads of H coalesced across the warp.
-template <typename T>
-__global__ void __launch_bounds__(128) k_x_from_h(const double2* __restrict__ kc, const typename vec2<T>::t* __restrict__ H,
-                                                  int Lh, int J, typename vec2<T>::t* __restrict__ Xs) {
-  typedef typename vec2<T>::t T2;
-  extern __shared__ unsigned char smem_raw[];
-  T2* sk = reinterpret_cast<T2*>(smem_raw);      // [Lh*Lh]
-  const int pair = blockIdx.y, n2 = Lh * Lh, K = 2 * Lh - 1;
-  for (int t = threadIdx.x; t < n2; t += blockDim.x) {
-    const double2 v = kc[(size_t)pair * n2 + t];
-    sk[t] = mk2((T)v.x, (T)v.y);
-  }
-  __syncthreads();
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= J) return;
-  T2* out = Xs + (size_t)pair * K * J;
-  for (int r = 0; r < Lh; ++r) {
-    T xr = 0, xi = 0, yr = 0, yi = 0;             // X_r and X_-r
-    for (int p0 = r; p0 < Lh; p0 += 8) {          // eight degrees' loads in flight at once
-      T2 ha[8], hb[8];
-#pragma unroll
-      for (int v = 0; v < 8; ++v) {
-        const int p = p0 + v;
-        ha[v] = p < Lh ? H[h_index(p * p + p + r, j, n2)] : mk2((T)0, (T)0);
-        hb[v] = (p < Lh && r > 0) ? H[h_index(p * p + p - r, j, n2)] : mk2((T)0, (T)0);
-      }
-#pragma unroll
-      for (int v = 0; v < 8; ++v) {
-        const int p = p0 + v;
-        if (p < Lh) {
-          const T2 ka = sk[p * p + p + r], kb = sk[p * p + p - r];
-          xr = fma(ka.x, ha[v].x, xr); xr = fma(-ka.y, ha[v].y, xr);
-          xi = fma(ka.x, ha[v].y, xi); xi = fma(ka.y, ha[v].x, xi);
-          yr = fma(kb.x, hb[v].x, yr); yr = fma(-kb.y, hb[v].y, yr);
-          yi = fma(kb.x, hb[v].y, yi); yi = fma(kb.y, hb[v].x, yi);
-        }
-      }
-    }
-    if (r == 0) {
-      out[j] = mk2(xr, xi);
-    } else {
-      out[(size_t)(2 * r - 1) * J + j] = mk2(xr + yr, xi + yi);
-      out[(size_t)(2 * r) * J + j] = mk2(xr - yr, xi - yi);
-    }
-  }
-}
-
-template <typename T>
-static cudaError_t launch_x_from_h_t(const double2* kc, const typename vec2<T>::t* H, int Lh, int J, int npairs,
-                                     typename vec2<T>::t* Xs, cudaStream_t st) {
-  if (npairs <= 0 || J <= 0) return cudaSuccess;
-  typedef typename vec2<T>::t T2;
-  const size_t smem = sizeof(T2) * (size_t)Lh * Lh;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_x_from_h<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  dim3 grid((J + 127) / 128, npairs);
-  k_x_from_h<T><<<grid, 128, smem, st>>>(kc, H, Lh, J, Xs);
-  return cudaGetLastError();
-}
-cudaError_t launch_x_from_h_f64(const double2* kc, const double2* H, int Lh, int J, int npairs, double2* Xs,
-                                cudaStream_t st) {
-  return launch_x_from_h_t<double>(kc, H, Lh, J, npairs, Xs, st);
-}
-cudaError_t launch_x_from_h_f32(const double2* kc, const float2* H, int Lh, int J, int npairs, float2* Xs,
-                                cudaStream_t st) {
-  return launch_x_from_h_t<float>(kc, H, Lh, J, npairs, Xs, st);
 }

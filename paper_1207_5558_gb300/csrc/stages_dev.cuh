@@ -8,51 +8,88 @@
 
 #include "common.cuh"
 
-// Shared memory of rotwin_block_smem: the (2p+1)^2 products and the Ng x
-// (2p+1) gamma phases of the largest degree p = Lh - 1.
-__host__ __device__ __forceinline__ size_t rotwin_smem_bytes(int Lh, int Ng, size_t el2) {
-  const size_t K = 2 * (size_t)Lh - 1;
-  return el2 * (K * K + (size_t)Ng * K);
+// Shared-memory chunking of a rotated-window block: a block (beta row b,
+// degree p, chunk z) forms the outputs (q, c) with q + p in [q0, q0 + QC) and
+// c in [c0, c0 + CC), staging QC rows of the (2p+1)^2 products h d and CC
+// rows of gamma phases.  Whole blocks (QC = 2Lh-1, CC = Ng, one chunk) when
+// they fit ROTWIN_SMEM_TARGET (four blocks an SM); otherwise CC <= 32 gamma
+// columns and as many q rows as fit beside them.  ROTWIN_SMEM_LIMIT bounds
+// the launches' dynamic shared memory.
+#define ROTWIN_SMEM_LIMIT (200 * 1024)
+#define ROTWIN_SMEM_TARGET (48 * 1024)
+struct RotChunks {
+  int QC, CC, nq, nc;
+  __host__ __device__ size_t smem(int Lh, size_t el2) const { return el2 * (size_t)(QC + CC) * (2 * Lh - 1); }
+};
+__host__ __device__ inline RotChunks rot_chunks(int Lh, int Ng, size_t el2) {
+  const int K = 2 * Lh - 1;
+  RotChunks r;
+  const long long rows = (long long)ROTWIN_SMEM_TARGET / ((long long)K * (long long)el2);   // QC + CC that fit
+  if ((long long)K + Ng <= rows) {
+    r.QC = K;
+    r.CC = Ng;
+  } else {
+    r.CC = Ng < 32 ? Ng : 32;
+    if (r.CC > rows - 1) r.CC = (int)(rows > 2 ? rows / 2 : 1);
+    long long qc = rows - r.CC;
+    r.QC = (int)(qc < 1 ? 1 : (qc > K ? K : qc));
+  }
+  r.nq = (K + r.QC - 1) / r.QC;
+  r.nc = (Ng + r.CC - 1) / r.CC;
+  return r;
 }
 
-// One (beta row b, degree p) block: the (2p+1)^2 products h_p^{q'}
-// d^p_{q,q'}(beta_b) and the gamma phases of the orders |q'| <= p are staged
-// in shared memory once, then each output (q, c) is a (2p+1)-term dot product
-// read from shared memory (a warp shares q: broadcast rows of the products,
-// odd-stride phase rows without bank conflicts).  dblk = the degree-p block
-// of d(beta_b); eg[c * (2Lh-1) + q' + Lh - 1] = (cos, sin)(q' gamma_c).  All
-// threads of the block take part (one __syncthreads).
+// One (beta row b, degree p, chunk z) block: the products h_p^{q'}
+// d^p_{q,q'}(beta_b) of its q rows and the gamma phases of its columns are
+// staged in shared memory once, then each output (q, c) is a (2p+1)-term dot
+// product read from shared memory (a warp shares q: broadcast rows of the
+// products, odd-stride phase rows without bank conflicts).  dblk = the
+// degree-p block of d(beta_b); eg[c * (2Lh-1) + q' + Lh - 1] = (cos, sin)(q'
+// gamma_c).  All threads of the block take part (one __syncthreads); a chunk
+// wholly beyond degree p returns at once (the same for the whole block).
 // store(index, re, im) receives each output with its h_index position.
 template <typename T, typename Store>
 __device__ __forceinline__ void rotwin_block_smem_to(const double2* __restrict__ h, const T* __restrict__ dblk,
                                                      const typename vec2<T>::t* __restrict__ eg, int Lh, int Ng,
-                                                     int b, int p, Store store, unsigned char* smem) {
+                                                     int b, int p, const RotChunks& ch, int z, Store store,
+                                                     unsigned char* smem) {
   typedef typename vec2<T>::t T2;
   const int K = 2 * Lh - 1, n2 = Lh * Lh, w = 2 * p + 1;
-  T2* hd = reinterpret_cast<T2*>(smem);       // [q + p][q' + p]
-  T2* ep = hd + w * w;                        // [c][q' + p]
-  for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
+  const int q0 = (z / ch.nc) * ch.QC, c0 = (z % ch.nc) * ch.CC;
+  if (q0 >= w) return;
+  const int nqr = min(ch.QC, w - q0), ncr = min(ch.CC, Ng - c0);
+  T2* hd = reinterpret_cast<T2*>(smem);       // [q + p - q0][q' + p]
+  T2* ep = hd + (size_t)nqr * w;              // [c - c0][q' + p]
+  for (int t = threadIdx.x; t < nqr * w; t += blockDim.x) {
     const int qp = t % w;
     const double2 hv = __ldg(h + p * p + qp);
-    const T d = __ldg(dblk + t);
+    const T d = __ldg(dblk + (size_t)q0 * w + t);
     hd[t] = mk2(d * (T)hv.x, d * (T)hv.y);
   }
-  for (int t = threadIdx.x; t < Ng * w; t += blockDim.x) {
+  for (int t = threadIdx.x; t < ncr * w; t += blockDim.x) {
     const int c = t / w, qp = t % w;
-    ep[t] = eg[(size_t)c * K + (Lh - 1) - p + qp];
+    ep[t] = eg[(size_t)(c0 + c) * K + (Lh - 1) - p + qp];
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < w * Ng; t += blockDim.x) {
-    const int qi = t / Ng, c = t % Ng;
+  for (int t = threadIdx.x; t < nqr * ncr; t += blockDim.x) {
+    const int qi = t / ncr, c = t % ncr;
     const T2* hr = hd + qi * w;
     const T2* er = ep + c * w;
-    T re = 0, im = 0;
-    for (int u = 0; u < w; ++u) {                // h d (cos - i sin)
+    T re = 0, im = 0, re2 = 0, im2 = 0;          // two chains: even and odd q'
+    int u = 0;
+    for (; u + 1 < w; u += 2) {                  // h d (cos - i sin)
+      const T2 a = hr[u], E = er[u], a2 = hr[u + 1], E2 = er[u + 1];
+      re = fma(a.x, E.x, re); re = fma(a.y, E.y, re);
+      im = fma(a.y, E.x, im); im = fma(-a.x, E.y, im);
+      re2 = fma(a2.x, E2.x, re2); re2 = fma(a2.y, E2.y, re2);
+      im2 = fma(a2.y, E2.x, im2); im2 = fma(-a2.x, E2.y, im2);
+    }
+    if (u < w) {
       const T2 a = hr[u], E = er[u];
       re = fma(a.x, E.x, re); re = fma(a.y, E.y, re);
       im = fma(a.y, E.x, im); im = fma(-a.x, E.y, im);
     }
-    store(h_index(p * p + qi, b * Ng + c, n2), re, im);
+    store(h_index(p * p + q0 + qi, b * Ng + c0 + c, n2), re + re2, im + im2);
   }
 }
 
@@ -61,35 +98,3 @@ struct RotwinStore {
   typename vec2<T>::t* H;
   __device__ __forceinline__ void operator()(size_t i, T re, T im) const { H[i] = mk2(re, im); }
 };
-
-template <typename T>
-__device__ __forceinline__ void rotwin_block_smem(const double2* __restrict__ h, const T* __restrict__ dblk,
-                                                  const typename vec2<T>::t* __restrict__ eg, int Lh, int Ng, int b,
-                                                  int p, typename vec2<T>::t* __restrict__ H, unsigned char* smem) {
-  rotwin_block_smem_to<T>(h, dblk, eg, Lh, Ng, b, p, RotwinStore<T>{H}, smem);
-}
-
-// The same block without shared memory (windows whose staged products would
-// not fit): each output reads h, d and the phases through the cache.
-template <typename T, typename Store>
-__device__ __forceinline__ void rotwin_block_direct_to(const double2* __restrict__ h, const T* __restrict__ dblk,
-                                                       const typename vec2<T>::t* __restrict__ eg, int Lh, int Ng,
-                                                       int b, int p, Store store) {
-  typedef typename vec2<T>::t T2;
-  const int K = 2 * Lh - 1, n2 = Lh * Lh, w = 2 * p + 1;
-  for (int t = threadIdx.x; t < w * Ng; t += blockDim.x) {
-    const int qi = t / Ng, c = t % Ng;
-    const T* drow = dblk + qi * w;
-    const T2* erow = eg + (size_t)c * K + (Lh - 1) - p;
-    T re = 0, im = 0;
-    for (int u = 0; u < w; ++u) {
-      const double2 hv = __ldg(h + p * p + u);
-      const T d = __ldg(drow + u);
-      const T2 E = erow[u];
-      const T ar = d * (T)hv.x, ai = d * (T)hv.y;
-      re = fma(ar, E.x, re); re = fma(ai, E.y, re);
-      im = fma(ai, E.x, im); im = fma(-ar, E.y, im);
-    }
-    store(h_index(p * p + qi, b * Ng + c, n2), re, im);
-  }
-}

@@ -78,12 +78,21 @@ __device__ __forceinline__ int degree_of(int idx, int Lh) {
 
 // d^p_{q,q'}(beta_b) = Re[ i^{q-q'} sum_{q''} Delta^p_{q''q} Delta^p_{q''q'} e^{-i q'' beta_b} ]
 // (Eq. WignerD_expansion_new at alpha = gamma = 0), beta_b = 2 pi b / (2 Nb - 1).
-// Layout [b][S].
+// Layout [b][S].  A block serves one beta row: the 2Lh-1 phases e^{-i q'' beta_b}
+// are computed once into shared memory, so an entry costs 2(2p+1) FP64
+// multiply-adds.
 template <typename T>
 __global__ void k_dtable(const double* __restrict__ D, T* __restrict__ dt, int Lh, int Nb) {
+  extern __shared__ double2 ph[];                 // [q'' + Lh - 1] = (cos, sin)(q'' beta_b)
   const int S = blk_off(Lh);
   const int b = blockIdx.y;
   const long long M = 2LL * Nb - 1;
+  for (int t = threadIdx.x; t < 2 * Lh - 1; t += blockDim.x) {
+    double s, c;
+    sincos_2pi_frac((long long)(t - (Lh - 1)) * b, M, &s, &c);
+    ph[t] = make_double2(c, s);
+  }
+  __syncthreads();
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < S; idx += gridDim.x * blockDim.x) {
     const int p = degree_of(idx, Lh);
     const int W = 2 * p + 1;
@@ -93,10 +102,9 @@ __global__ void k_dtable(const double* __restrict__ D, T* __restrict__ dt, int L
     double sr = 0.0, si = 0.0;
     for (int qpp = -p; qpp <= p; ++qpp) {
       const double w = blk[(qpp + p) * W + (q + p)] * blk[(qpp + p) * W + (qp + p)];
-      double s, c;
-      sincos_2pi_frac((long long)qpp * b, M, &s, &c);
-      sr = fma(w, c, sr);
-      si = fma(-w, s, si);
+      const double2 e = ph[qpp + Lh - 1];
+      sr = fma(w, e.x, sr);
+      si = fma(-w, e.y, si);
     }
     double v;
     switch ((((q - qp) % 4) + 4) % 4) {
@@ -112,13 +120,13 @@ __global__ void k_dtable(const double* __restrict__ D, T* __restrict__ dt, int L
 cudaError_t launch_dtable_f64(const double* D, double* dt, int Lh, int Nb, cudaStream_t st) {
   const int S = blk_off(Lh);
   dim3 grid((S + 255) / 256, Nb);
-  k_dtable<double><<<grid, 256, 0, st>>>(D, dt, Lh, Nb);
+  k_dtable<double><<<grid, 256, sizeof(double2) * (2 * Lh - 1), st>>>(D, dt, Lh, Nb);
   return cudaGetLastError();
 }
 cudaError_t launch_dtable_f32(const double* D, float* dt, int Lh, int Nb, cudaStream_t st) {
   const int S = blk_off(Lh);
   dim3 grid((S + 255) / 256, Nb);
-  k_dtable<float><<<grid, 256, 0, st>>>(D, dt, Lh, Nb);
+  k_dtable<float><<<grid, 256, sizeof(double2) * (2 * Lh - 1), st>>>(D, dt, Lh, Nb);
   return cudaGetLastError();
 }
 template <typename T2>
