@@ -700,6 +700,71 @@ def main():
         torch.cuda.empty_cache()
         return out
 
+    def workload5_leg():
+        """Workload 5 (L_f = 2048, L_h = 64, the 8 x 3 degree elliptical
+        window from the device generator, 16 seeded pairs, each on the full
+        4095 x 2048 x 127 grid, FP32_BULK): 4 calls of 4 pairs into one 34 GB
+        buffer, and one batch plan of the 4 pair groups (same buffer), events
+        on the stream.  The alpha stage runs on CUDA cores (L_h > 16)."""
+        from synth.window import ellipse_from_axes
+        c5 = synth.CONFIGS[5]
+        L5f, L5h, g5 = c5["Lf"], c5["Lh"], c5["grid"]
+        h5, _ = ctx.window_ellipse(L5h, *ellipse_from_axes(8.0, 3.0))
+        f5, _, p5 = synth.config_inputs(5, window_cache=h5)
+        f5d, h5d = torch.from_numpy(f5).cuda(), torch.from_numpy(h5).cuda()
+        p5d = torch.from_numpy(np.ascontiguousarray(p5)).cuda()
+        npb = 4
+        gb = torch.empty((npb,) + g5, dtype=torch.complex64, device="cuda")
+        desc = pkg.make_desc(L5f, L5h, g5, 1)
+        smp = len(p5) * synth.samples_per_pair(g5)
+
+        def step():
+            for i in range(0, len(p5), npb):
+                pkg.slsht_forward(ctx.h, desc, f5d, h5d, p5d[i:i + npb], npb, gb, stream)
+        step()
+        barrier()
+        ctx.stats(reset=True)
+        ctx.profile(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        barrier()
+        ctx.profile(False)
+        ms = e0.elapsed_time(e1)
+        st = ctx.stats(reset=True)
+        items = [{"L_f": L5f, "L_h": L5h, "grid": g5, "prec": 1, "f": f5d, "h": h5d, "lm": p5[i:i + npb],
+                  "g_out": gb} for i in range(0, len(p5), npb)]
+        bp = ctx.batch(items, stream=stream)
+        bp.launch(stream)
+        barrier()
+        e0.record(stream)
+        bp.launch(stream)
+        e1.record(stream)
+        barrier()
+        ms_plan = e0.elapsed_time(e1)
+        P5 = bp.query(pkg.SLSHT_BQ_ALPHA_FORM, 0)
+        K5 = 2 * L5h - 1
+        H5 = (P5 - 1) // 2 if P5 > 0 else 0
+        fma = (4.0 * K5 + 4 * H5 * H5 + 10 * H5) / P5 if P5 > 0 else 4.0 * (L5h - 1) + 2
+        fma += 4.0 * L5h * L5h / g5[0]
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        out = {"workload": "workload 5: L_f=2048, L_h=64 ellipse 8x3 deg, 16 pairs, grid 4095x2048x127, FP32_BULK",
+               "samples": smp, "per_call_ms": ms, "value_per_call": smp / (ms / 1e3),
+               "stage_ms_per_call_step": st["ms"], "plan_ms": ms_plan, "value_plan": smp / (ms_plan / 1e3),
+               "alpha_form": "split P=%d" % P5 if P5 > 0 else "direct",
+               "tile_cols": bp.query(pkg.SLSHT_BQ_TILE_COLS, 0),
+               "alpha_fp32_fma_per_sample": fma,
+               "plan_fp32_fma_frac": smp / (ms_plan / 1e3) * fma / (128.0 * sms * 2070e6),
+               "plan_hbm_frac": smp / (ms_plan / 1e3) * 8.0 / (peaks()[0]["hbm_gbs"] * 1e9),
+               "note": "the per-call figure rebuilds the rotated window in each of the 4 calls; the plan "
+                       "forms it once; fractions against 128 FP32 lanes x SMs x 2070 MHz and the measured copy "
+                       "bandwidth"}
+        bp.close()
+        del gb
+        torch.cuda.empty_cache()
+        return out
+
     # ---------------- FP32_BULK headline
     g32 = torch.empty((npairs_map,) + grid, dtype=torch.complex64, device="cuda")
     ms32, st32, clk = timed(1, g32, args.steps, args.warmup, ClockSampler(local))
@@ -785,11 +850,13 @@ def main():
     win_gen = None
     coup = None
     batch = None
+    w5 = None
     if args.fp64_steps > 0:
         wins = windows_leg()
         win_gen = window_leg()
         coup = coupling_leg()
         batch = batch_leg()
+        w5 = workload5_leg()
 
     # ---------------- e2e through the C ABI with host buffers
     e2e = None
@@ -855,6 +922,7 @@ def main():
             "window_generator": win_gen,
             "coupling_routes": coup,
             "batch_plans": batch,
+            "workload5": w5,
             "serve": serve,
         }
         print(json.dumps(line), flush=True)

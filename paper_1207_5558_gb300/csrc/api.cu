@@ -1295,12 +1295,14 @@ static BItem batch_item_view(const slsht_batch* b, int ii, int engine) {
 // replicated `reps` times to fill the GPU), or the fused tensor-core kernel
 // as a launch of its own over the item's pairs (np of them, no
 // replication).  Returns device milliseconds per sample in *cost.
-static int batch_time_candidate(slsht_batch* b, int ii, int nt, int form, int engine, int np, int reps, void* scratch,
-                                void* d_item, void* d_tiles, int* d_ctr, double* cost) {
+static int batch_time_candidate(slsht_batch* b, int ii, int nt, int form, int engine, int np, int reps, int nbs,
+                                void* scratch, void* d_item, void* d_tiles, int* d_ctr, double* cost) {
   slsht_ctx* ctx = b->ctx;
   const BatchItemHost& it = b->items[ii];
   const slsht_desc& d = it.d;
-  const long long J = (long long)d.n_beta * d.n_gamma;
+  // the first nbs beta rows of each sampled pair (the tiled H and the row
+  // stride of the scratch output both allow a prefix of the columns)
+  const long long J = (long long)nbs * d.n_gamma;
   if (engine == ENG_TC) reps = 1;
   const double samples = (double)np * reps * d.n_alpha * J;
   std::vector<BTile> tl;
@@ -1310,6 +1312,7 @@ static int batch_time_candidate(slsht_batch* b, int ii, int nt, int form, int en
   if (engine != ENG_TC) {
     bi = batch_item_view(b, ii, engine);
     bi.g = scratch;
+    bi.J = (int)J;
     bi.nt = nt;
     bi.form = form;
     CKS(batch_alpha_table(b, d, form, engine, &bi.csa));
@@ -1332,7 +1335,7 @@ static int batch_time_candidate(slsht_batch* b, int ii, int nt, int form, int en
                              b->cs);
     else
       e = launch_alpha_fused(b->cpl[it.cpl].kc, (const float2*)b->rot[it.rot].H, it.etab, d.L_h, d.n_alpha,
-                             d.n_beta, d.n_gamma, np * reps, (float2*)scratch, ctx->num_sms, 0, nullptr, b->cs);
+                             nbs, d.n_gamma, np * reps, (float2*)scratch, ctx->num_sms, 0, nullptr, b->cs);
     if (e != cudaSuccess) { record_cuda_error("batch tuning launch", e); return SLSHT_E_CUDA; }
     CK(cudaEventRecord(b->tb, b->cs));
     CK(cudaEventSynchronize(b->tb));
@@ -1401,14 +1404,21 @@ static int batch_tune(slsht_batch* b, int ii) {
   if (cand.empty()) return SLSHT_E_ARG;
   // sample: the first pairs (all of them up to 16M samples), replicated so
   // the candidate with the widest tiles still has about eight tiles per SM;
-  // at most 16M samples
-  const double per_pair = (double)Na * J;
+  // at most 16M samples; of a pair larger than that, the first beta rows
+  // (whole 128-column tiles, at least eight per SM)
+  int nbs = d.n_beta;
+  if ((double)Na * J > 1.6e7) {
+    const long long cols = std::max<long long>((long long)std::ceil(1.6e7 / Na), 8LL * ctx->num_sms * 128);
+    nbs = (int)std::min<long long>(d.n_beta, (cols + d.n_gamma - 1) / d.n_gamma);
+  }
+  const long long Js = (long long)nbs * d.n_gamma;
+  const double per_pair = (double)Na * Js;
   int np = (int)std::max<double>(1.0, std::min<double>(it.npairs, std::floor(1.6e7 / per_pair)));
-  const long long tiles_np = (long long)np * ((J + 127) / 128);
+  const long long tiles_np = (long long)np * ((Js + 127) / 128);
   int reps = (int)std::max<long long>(1, (8LL * ctx->num_sms + tiles_np - 1) / tiles_np);
   reps = (int)std::max<double>(1.0, std::min<double>(reps, std::floor(1.6e7 / (per_pair * np))));
-  const size_t out_bytes = (size_t)np * reps * Na * J * el2_of(d.prec);
-  const size_t max_tiles = (size_t)np * reps * ((J + 31) / 32);
+  const size_t out_bytes = (size_t)np * reps * Na * Js * el2_of(d.prec);
+  const size_t max_tiles = (size_t)np * reps * ((Js + 31) / 32);
   void *scratch = nullptr, *d_item = nullptr, *d_tiles = nullptr, *d_ctr = nullptr;
   int st = ctx_alloc(ctx, out_bytes, &scratch);
   if (st == SLSHT_OK) st = ctx_alloc(ctx, sizeof(BItem), &d_item);
@@ -1419,7 +1429,7 @@ static int batch_tune(slsht_batch* b, int ii) {
   for (size_t c = 0; c < cand.size() && st == SLSHT_OK; ++c) {
     double cost = 0.0;
     st = batch_time_candidate(b, ii, std::get<0>(cand[c]), std::get<1>(cand[c]), std::get<2>(cand[c]), np, reps,
-                              scratch, d_item, d_tiles, (int*)d_ctr, &cost);
+                              nbs, scratch, d_item, d_tiles, (int*)d_ctr, &cost);
     if (st == SLSHT_OK && cost < best) { best = cost; pick = cand[c]; }
   }
   cudaStreamSynchronize(b->cs);
