@@ -1,0 +1,436 @@
+// FP32_BULK alpha stage on tcgen05 for wide windows, 16 < L_h <= 64: the
+// contraction g[a][j] = sum_q X_q[j] e^{-i q alpha_a} of depth 2(2L_h - 1) real
+// terms, split into NK = 2 (L_h <= 32) or 4 (L_h <= 64) K-chunks of 64.
+//
+// The real GEMM D[j][n] = sum_k A[j][k] B[n][k] (M = 128 columns, N = 128 =
+// Re and Im of 64 alpha rows, K = 64 NK) uses the slot map of NK:
+//   half = 32 NK, centre = 16 NK - 1,
+//   A[j][centre + q] = Re X_q[j],  A[j][half + centre + q] = Im X_q[j]   (|q| < L_h),
+//   B[n][centre + q] = cos(q alpha_a), B[n][half + centre + q] = sin(q alpha_a)   (n < 64: Re g),
+//   B[64+n][centre + q] = -sin(q alpha_a), B[64+n][half + centre + q] = cos(q alpha_a)   (Im g),
+// every other slot zero; K-chunk kc holds slots [64 kc, 64 kc + 64).  As in
+// the narrow engine both operands are split into FP16 hi + lo (A after a
+// per-column power-of-two scale that puts its largest entry in [2^14, 2^15))
+// and D = A_hi B_hi + A_hi B_lo + A_lo B_hi accumulates in FP32.
+//
+// Two kernels: k_xaw_from_h (CUDA cores) forms X of one pair and one
+// 128-column tile from the rotated window H, scales, splits and writes the
+// swizzled A operand (NK x 32 KB) and the column scales to a blob in global
+// memory; k_alpha_tcw (persistent, one CTA per SM, work item = (pair, tile))
+// keeps the item's whole A operand in shared memory, streams the E-table
+// K-chunks (32 KB each) through a ring of 3 or 4 stages with cp.async.bulk, issues
+// the MMAs from one thread into two TMEM accumulators (2 x 128 columns), and
+// eight epilogue warps drain them and store g.  Every mbarrier wait is
+// bounded; on expiry the CTA raises its abort flag, waits (bounded) for its
+// copies and MMAs in flight, frees TMEM and exits, and the host reads the
+// shared error word.
+#include <cuda_fp16.h>
+
+#include "common.cuh"
+#include "tc.cuh"
+#include "tc_ptx.cuh"
+
+static inline int tcw_nk(int Lh) { return Lh <= 32 ? 2 : 4; }
+static inline int tcw_tiles(int Nb, int Ng) { return (Nb * Ng + TC_M - 1) / TC_M; }
+static inline int tcw_chunks(int Na) { return (Na + TC_NC - 1) / TC_NC; }
+
+bool tcw_supported(int Lh, int Na) { return Lh > 16 && Lh <= 64 && Na >= 1; }
+
+size_t tcw_etab_bytes(int Na, int Lh) { return (size_t)tcw_chunks(Na) * tcw_nk(Lh) * TC_B_BYTES; }
+
+// per pair: tiles x NK x 32 KB of A, then one float scale per padded column
+size_t tcw_xblob_bytes(int Nb, int Ng, int Lh) {
+  const size_t t = (size_t)tcw_tiles(Nb, Ng);
+  const size_t sc = ((t * TC_M * sizeof(float)) + 1023) / 1024 * 1024;
+  return t * (size_t)tcw_nk(Lh) * TC_A_BYTES + sc;
+}
+
+// ---------------------------------------------------------------- E tables
+// chunk (c, kc) at (c NK + kc) 32 KB: [hi: 128 rows x 64][lo], rows n < 64 ->
+// alpha a = 64 c + n (cos in the Re slots | sin in the Im slots), rows 64 + n
+// -> (-sin | cos); zeros beyond Na and outside |q| < Lh.
+__global__ void k_tcw_etab(unsigned char* __restrict__ etab, int Na, int Lh, int nk) {
+  const int c = blockIdx.x / nk, kc = blockIdx.x % nk;
+  const int half = 32 * nk, centre = 16 * nk - 1;
+  unsigned char* base = etab + (size_t)blockIdx.x * TC_B_BYTES;
+  for (int t = threadIdx.x; t < TC_N * TC_KB; t += blockDim.x) {
+    const int r = t / TC_KB, kl = t % TC_KB;
+    const int slot = kc * TC_KB + kl;
+    const bool im_part = slot >= half;
+    const int q = (im_part ? slot - half : slot) - centre;
+    const int n = r % TC_NC;
+    const int a = c * TC_NC + n;
+    double v = 0.0;
+    if (a < Na && q > -Lh && q < Lh) {
+      double s, co;
+      sincos_2pi_frac((long long)q * a, Na, &s, &co);
+      if (r < TC_NC) v = im_part ? s : co;
+      else v = im_part ? co : -s;
+    }
+    const __half hi = __double2half(v);
+    const __half lo = __double2half(v - (double)__half2float(hi));
+    *reinterpret_cast<__half*>(base + sw128_off(r, kl)) = hi;
+    *reinterpret_cast<__half*>(base + TC_B_HALF + sw128_off(r, kl)) = lo;
+  }
+}
+
+cudaError_t launch_tcw_etab(void* etab, int Na, int Lh, cudaStream_t st) {
+  if (!tcw_supported(Lh, Na)) return cudaErrorInvalidValue;
+  const int nk = tcw_nk(Lh);
+  k_tcw_etab<<<tcw_chunks(Na) * nk, 256, 0, st>>>((unsigned char*)etab, Na, Lh, nk);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- A operand from H
+// X_q(j) = sum_{p>=|q|} k(p,q) H^p_q(j) for one pair and one 128-column tile:
+// A block serves half a tile (64 columns); the blocks of one tile for every
+// pair of the launch are adjacent, so each H tile is read from HBM about once.
+//   phase 1: one item per (q, column), its degrees p >= |q| (H loads coalesced
+//            across columns, k broadcast through the cache) into the shared
+//            tile sX[slot][column] (unused slots zero);
+//   phase 2: per column, the largest |entry| -> scale 2^e into [2^14, 2^15);
+//   phase 3: per (column, 16-byte chunk): scale, split into FP16 hi/lo, store
+//            swizzled into its K-chunk.  Columns beyond J are zero.
+#define XW_COLS 64                      // columns per producer block (half a tile)
+
+__global__ void __launch_bounds__(256)
+k_xaw_from_h(const double2* __restrict__ kc, const float2* __restrict__ H, int Lh, int J, int nk,
+             unsigned char* __restrict__ xblob, size_t blob_stride, int tiles) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int half = 32 * nk, centre = 16 * nk - 1, KS = 2 * half;
+  float* sX = reinterpret_cast<float*>(smem_raw);                 // [KS][XW_COLS]
+  int* sEx = reinterpret_cast<int*>(sX + (size_t)KS * XW_COLS);   // [XW_COLS]
+  // pairs vary fastest: the blocks of one H tile run together and share it in L2
+  const int pair = blockIdx.x, tile = blockIdx.y >> 1, r0 = (blockIdx.y & 1) * XW_COLS;
+  const int n2 = Lh * Lh, K = 2 * Lh - 1;
+  const double2* kp = kc + (size_t)pair * n2;
+  for (int t = threadIdx.x; t < KS * XW_COLS; t += blockDim.x) sX[t] = 0.f;
+  __syncthreads();
+  const int jt = tile * TC_M + r0;
+  for (int it = threadIdx.x; it < K * XW_COLS; it += blockDim.x) {
+    const int u = it / XW_COLS, r = it % XW_COLS;
+    const int q = u - (Lh - 1), aq = q < 0 ? -q : q;
+    const int j = jt + r;
+    float ar = 0.f, ai = 0.f;
+    if (j < J) {
+      const float2* hp = H + h_index(0, j, n2);      // row pq at hp + pq * 128
+      int p = aq;
+      for (; p + 3 < Lh; p += 4) {                  // four loads in flight per step
+        float2 hv[4];
+        double2 kv[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int pq = (p + v) * (p + v) + (p + v) + q;
+          hv[v] = __ldg(hp + (size_t)pq * 128);
+          kv[v] = __ldg(kp + pq);
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const float kr = (float)kv[v].x, ki = (float)kv[v].y;
+          ar = fmaf(kr, hv[v].x, ar); ar = fmaf(-ki, hv[v].y, ar);
+          ai = fmaf(kr, hv[v].y, ai); ai = fmaf(ki, hv[v].x, ai);
+        }
+      }
+      for (; p < Lh; ++p) {
+        const int pq = p * p + p + q;
+        const float2 hv = __ldg(hp + (size_t)pq * 128);
+        const double2 kd = __ldg(kp + pq);
+        const float kr = (float)kd.x, ki = (float)kd.y;
+        ar = fmaf(kr, hv.x, ar); ar = fmaf(-ki, hv.y, ar);
+        ai = fmaf(kr, hv.y, ai); ai = fmaf(ki, hv.x, ai);
+      }
+    }
+    sX[(size_t)(centre + q) * XW_COLS + r] = ar;
+    sX[(size_t)(half + centre + q) * XW_COLS + r] = ai;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < XW_COLS; r += blockDim.x) {
+    float mx = 0.f;
+    for (int k = 0; k < KS; ++k) mx = fmaxf(mx, fabsf(sX[(size_t)k * XW_COLS + r]));
+    int ex = 0;
+    if (mx > 0.f) frexpf(mx, &ex);
+    sEx[r] = mx > 0.f ? min(125, max(-125, 15 - ex)) : 0;
+  }
+  __syncthreads();
+  unsigned char* blob = xblob + (size_t)pair * blob_stride;
+  unsigned char* tb = blob + (size_t)tile * nk * TC_A_BYTES;
+  float* scales = reinterpret_cast<float*>(blob + (size_t)tiles * nk * TC_A_BYTES);
+  for (int it = threadIdx.x; it < XW_COLS * (KS / 8); it += blockDim.x) {
+    const int r = it % XW_COLS, k0 = (it / XW_COLS) * 8;
+    const int e = sEx[r];
+    const float sc = __int_as_float((127 + e) << 23);
+    __align__(16) __half hi[8], lo[8];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      const float x = sX[(size_t)(k0 + v) * XW_COLS + r] * sc;
+      hi[v] = __float2half_rn(x);
+      lo[v] = __float2half_rn(x - __half2float(hi[v]));
+    }
+    unsigned char* cb = tb + (size_t)(k0 / TC_KB) * TC_A_BYTES;
+    *reinterpret_cast<uint4*>(cb + sw128_off(r0 + r, k0 % TC_KB)) = *reinterpret_cast<uint4*>(hi);
+    *reinterpret_cast<uint4*>(cb + TC_A_HALF + sw128_off(r0 + r, k0 % TC_KB)) = *reinterpret_cast<uint4*>(lo);
+    if (k0 == 0) scales[jt + r] = jt + r < J ? __int_as_float((127 - e) << 23) : 0.f;
+  }
+}
+
+cudaError_t launch_xaw_from_h(const double2* kc, const float2* H, int Lh, int Nb, int Ng, int npairs, void* xblob,
+                              cudaStream_t st) {
+  if (npairs <= 0) return cudaSuccess;
+  if (Lh <= 16 || Lh > 64) return cudaErrorInvalidValue;
+  const int nk = tcw_nk(Lh), tiles = tcw_tiles(Nb, Ng);
+  const size_t smem = sizeof(float) * (size_t)64 * nk * XW_COLS + sizeof(int) * XW_COLS;
+  if (npairs > 65535 || 2LL * tiles > 65535) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_xaw_from_h, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(npairs, 2 * tiles);
+  k_xaw_from_h<<<grid, 256, smem, st>>>(kc, H, Lh, Nb * Ng, nk, (unsigned char*)xblob, tcw_xblob_bytes(Nb, Ng, Lh),
+                                        tiles);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- the kernel
+#define TCW_MAX_BS 4
+struct TcwBars {
+  uint64_t a_full, a_empty, b_full[TCW_MAX_BS], b_empty[TCW_MAX_BS], acc_full[2], acc_empty[2], drain;
+  uint32_t tmem_base;
+  int abort_flag;
+};
+
+// E-table ring depth: what fits beside the A operand (3 stages at NK = 4, 4 at NK = 2).
+#define TCW_BS(NK) ((NK) == 4 ? 3 : 4)
+#define TCW_SMEM(NK) ((NK) * TC_A_BYTES + TCW_BS(NK) * TC_B_BYTES + 1024 + 256)
+
+template <int NK>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+k_alpha_tcw(const unsigned char* __restrict__ xblob, size_t blob_stride, int tiles,
+            const unsigned char* __restrict__ etab, int Na, int J, int npairs, float2* __restrict__ g,
+            int* __restrict__ err, const int2* __restrict__ slots) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  constexpr int BS = TCW_BS(NK);
+  unsigned char* sA = sm;                               // NK x 32 KB: the item's A operand
+  unsigned char* sB = sm + NK * TC_A_BYTES;             // BS x 32 KB: ring of E-table K-chunks
+  TcwBars* bars = reinterpret_cast<TcwBars*>(sB + BS * TC_B_BYTES);
+  volatile int* abort_flag = &bars->abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nch = (Na + TC_NC - 1) / TC_NC;
+  const long long nitems = (long long)npairs * tiles;
+
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bars->a_full), 1);
+    mbar_init(smem_u32(&bars->a_empty), 1);
+    for (int i = 0; i < BS; ++i) {
+      mbar_init(smem_u32(&bars->b_full[i]), 1);
+      mbar_init(smem_u32(&bars->b_empty[i]), 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(smem_u32(&bars->acc_full[i]), 1);
+      mbar_init(smem_u32(&bars->acc_empty[i]), 32 * TC_EPI_WARPS);
+    }
+    mbar_init(smem_u32(&bars->drain), 1);
+    bars->abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {   // TMEM: two 128 x TC_N FP32 accumulators
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
+                     smem_u32(&bars->tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = bars->tmem_base;
+
+  if (warp == 0) {
+    // ---------------- loader: the item's A operand, then its E K-chunks in order
+    if (lane == 0) {
+      int a_armed = -1, b_armed[BS];
+#pragma unroll
+      for (int i = 0; i < BS; ++i) b_armed[i] = -1;
+      long long bc = 0;
+      int li = 0;
+      bool ok = true;
+      for (long long it = blockIdx.x; it < nitems && ok; it += gridDim.x, ++li) {
+        const int pair = (int)(it / tiles), tile = (int)(it % tiles);
+        const uint32_t pa = (uint32_t)(li & 1);
+        if (!(ok = mbar_wait(smem_u32(&bars->a_empty), pa ^ 1u, abort_flag))) break;
+        const uint32_t fa = smem_u32(&bars->a_full);
+        mbar_expect_tx(fa, NK * TC_A_BYTES);
+        const unsigned char* src = xblob + (size_t)pair * blob_stride + (size_t)tile * NK * TC_A_BYTES;
+        for (int o = 0; o < NK * TC_A_BYTES; o += 16384) bulk_g2s(smem_u32(sA + o), src + o, 16384, fa);
+        a_armed = (int)pa;
+        for (int c = 0; c < nch && ok; ++c) {
+          for (int kc = 0; kc < NK; ++kc, ++bc) {
+            const int sb = (int)(bc % BS);
+            const uint32_t pb = (uint32_t)((bc / BS) & 1);
+            if (!(ok = mbar_wait(smem_u32(&bars->b_empty[sb]), pb ^ 1u, abort_flag))) break;
+            const uint32_t fb = smem_u32(&bars->b_full[sb]);
+            mbar_expect_tx(fb, TC_B_BYTES);
+            const unsigned char* bsrc = etab + ((size_t)c * NK + kc) * TC_B_BYTES;
+            for (int o = 0; o < TC_B_BYTES; o += 16384)
+              bulk_g2s(smem_u32(sB + sb * TC_B_BYTES + o), bsrc + o, 16384, fb);
+#pragma unroll
+            for (int i = 0; i < BS; ++i)
+              if (i == sb) b_armed[i] = (int)pb;
+          }
+        }
+      }
+      if (!ok) *abort_flag = 1;
+      // copies in flight must land before the CTA may exit
+      if (a_armed >= 0) {
+        uint32_t n = 0;
+        while (!mbar_test(smem_u32(&bars->a_full), (uint32_t)a_armed) && ++n < TC_WAIT_LIMIT) {}
+      }
+#pragma unroll
+      for (int i = 0; i < BS; ++i) {
+        if (b_armed[i] >= 0) {
+          uint32_t n = 0;
+          while (!mbar_test(smem_u32(&bars->b_full[i]), (uint32_t)b_armed[i]) && ++n < TC_WAIT_LIMIT) {}
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = umma_idesc_f16(TC_M, TC_N);
+      long long bc = 0, ac = 0;
+      int li = 0;
+      bool ok = true;
+      for (long long it = blockIdx.x; it < nitems && ok; it += gridDim.x, ++li) {
+        if (!(ok = mbar_wait(smem_u32(&bars->a_full), (uint32_t)(li & 1), abort_flag))) break;
+        for (int c = 0; c < nch && ok; ++c, ++ac) {
+          const int acc = (int)(ac & 1);
+          if (!(ok = mbar_wait(smem_u32(&bars->acc_empty[acc]), (uint32_t)(((ac >> 1) & 1) ^ 1), abort_flag)))
+            break;
+          const uint32_t d = tmem + (uint32_t)(acc * TC_N);
+          for (int kc = 0; kc < NK; ++kc, ++bc) {
+            const int sb = (int)(bc % BS);
+            if (!(ok = mbar_wait(smem_u32(&bars->b_full[sb]), (uint32_t)((bc / BS) & 1), abort_flag))) break;
+            tc_fence_after();
+            const uint32_t a_hi = smem_u32(sA + kc * TC_A_BYTES), a_lo = a_hi + TC_A_HALF;
+            const uint32_t b_hi = smem_u32(sB + sb * TC_B_BYTES), b_lo = b_hi + TC_B_HALF;
+            const uint32_t as[3] = {a_hi, a_hi, a_lo};
+            const uint32_t bs[3] = {b_hi, b_lo, b_hi};
+#pragma unroll
+            for (int pr = 0; pr < 3; ++pr) {
+              const uint64_t ad = sw128_desc(as[pr]), bd = sw128_desc(bs[pr]);
+#pragma unroll
+              for (int s = 0; s < TC_KB / 16; ++s)       // K = 16 per MMA: +32 bytes
+                umma_f16(d, ad + (uint64_t)(2 * s), bd + (uint64_t)(2 * s), idesc, (kc | pr | s) != 0);
+            }
+            umma_commit(smem_u32(&bars->b_empty[sb]));
+          }
+          if (!ok) break;
+          umma_commit(smem_u32(&bars->acc_full[acc]));
+        }
+        if (!ok) break;
+        umma_commit(smem_u32(&bars->a_empty));
+      }
+      if (!ok) *abort_flag = 1;
+      // every MMA issued by this thread completes before TMEM is released
+      umma_commit(smem_u32(&bars->drain));
+      uint32_t n = 0;
+      while (!mbar_test(smem_u32(&bars->drain), 0u) && ++n < TC_WAIT_LIMIT) {}
+    }
+  } else {
+    // ---------------- epilogue: warps 2..9; TMEM lane quadrant = warp % 4,
+    // half = which 32 of the chunk's 64 alpha rows
+    const int quad = warp & 3;
+    const int half = (warp - 2) >> 2;
+    const int row = quad * 32 + lane;
+    long long ac = 0;
+    bool ok = true;
+    for (long long it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
+      const int pair = (int)(it / tiles), tile = (int)(it % tiles);
+      const int j = tile * TC_M + row;
+      const bool jin = j < J;
+      const float* scales = reinterpret_cast<const float*>(xblob + (size_t)pair * blob_stride +
+                                                           (size_t)tiles * NK * TC_A_BYTES);
+      const float sc = jin ? scales[j] : 0.f;
+      const int2 sl = slots != nullptr ? slots[pair] : make_int2(pair, -1);
+      float2* gp = g + (size_t)sl.x * Na * J + (jin ? j : 0);
+      float2* gm = sl.y >= 0 ? g + (size_t)(sl.y >> 1) * Na * J + (jin ? j : 0) : nullptr;
+      const float msc = (sl.y & 1) ? -sc : sc;
+      for (int c = 0; c < nch; ++c, ++ac) {
+        const int acc = (int)(ac & 1);
+        // one lane waits, the warp follows: tcgen05.ld needs a converged warp
+        int got = 0;
+        if (lane == 0) got = mbar_wait(smem_u32(&bars->acc_full[acc]), (uint32_t)((ac >> 1) & 1), abort_flag);
+        got = __shfl_sync(0xffffffffu, got, 0);
+        __syncwarp();
+        if (!(ok = got != 0)) break;
+        tc_fence_after();
+        const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * TC_N);
+        const int cb = half * (TC_NC / 2);
+        uint32_t vr[32], vi[32];
+        TMEM_LD32(tbase + (uint32_t)cb, vr);
+        TMEM_LD32(tbase + (uint32_t)(TC_NC + cb), vi);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int a0 = c * TC_NC + cb;
+        if (jin) {
+          float2* p = gp + (size_t)a0 * J;
+          if (a0 + 32 <= Na) {
+#pragma unroll
+            for (int u = 0; u < 32; ++u) {
+              __stcs(p, make_float2(__uint_as_float(vr[u]) * sc, __uint_as_float(vi[u]) * sc));
+              p += J;
+            }
+          } else {
+#pragma unroll
+            for (int u = 0; u < 32; ++u) {
+              if (a0 + u < Na) __stcs(p, make_float2(__uint_as_float(vr[u]) * sc, __uint_as_float(vi[u]) * sc));
+              p += J;
+            }
+          }
+        }
+        if (jin && gm != nullptr) {     // (l, -m): (-1)^m conj g (real f and h)
+          float2* p = gm + (size_t)a0 * J;
+#pragma unroll
+          for (int u = 0; u < 32; ++u) {
+            if (a0 + u < Na)
+              __stcs(p, make_float2(__uint_as_float(vr[u]) * msc, -__uint_as_float(vi[u]) * msc));
+            p += J;
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(smem_u32(&bars->acc_empty[acc]));
+      }
+    }
+    if (!ok) *abort_flag = 1;
+  }
+  __syncthreads();
+  if (*abort_flag && threadIdx.x == 0) atomicExch(err, 1);
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
+  }
+}
+
+template <int NK>
+static cudaError_t launch_tcw_t(const void* xblob, const void* etab, int Lh, int Na, int Nb, int Ng, int npairs,
+                                float2* g, int num_sms, const int2* slots, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_alpha_tcw<NK>, cudaFuncAttributeMaxDynamicSharedMemorySize, TCW_SMEM(NK));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  int* err = tc_error_word();
+  if (!err) return cudaErrorMemoryAllocation;
+  const int tiles = tcw_tiles(Nb, Ng);
+  const long long items = (long long)npairs * tiles;
+  const int grid = (int)(items < num_sms ? items : num_sms);
+  k_alpha_tcw<NK><<<grid, TC_THREADS, TCW_SMEM(NK), st>>>((const unsigned char*)xblob, tcw_xblob_bytes(Nb, Ng, Lh),
+                                                          tiles, (const unsigned char*)etab, Na, Nb * Ng, npairs, g,
+                                                          err, slots);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_alpha_tcw(const void* xblob, const void* etab, int Lh, int Na, int Nb, int Ng, int npairs,
+                             float2* g, int num_sms, const int2* slots, cudaStream_t st) {
+  if (npairs <= 0) return cudaSuccess;
+  if (!tcw_supported(Lh, Na)) return cudaErrorInvalidValue;
+  if (tcw_nk(Lh) == 2) return launch_tcw_t<2>(xblob, etab, Lh, Na, Nb, Ng, npairs, g, num_sms, slots, st);
+  return launch_tcw_t<4>(xblob, etab, Lh, Na, Nb, Ng, npairs, g, num_sms, slots, st);
+}

@@ -465,9 +465,11 @@ static int get_etab(slsht_ctx* ctx, int Na, int Lh, cudaStream_t st, const void*
   auto it = ctx->etab.find(key);
   if (it == ctx->etab.end()) {
     TableEntry e;
-    CKS(make_entry(ctx, e, tc_etab_bytes(Na, Lh)));
+    // narrow windows (L_h <= 16): one K-chunk; wide ones: 2 or 4
+    const bool wide = Lh > 16;
+    CKS(make_entry(ctx, e, wide ? tcw_etab_bytes(Na, Lh) : tc_etab_bytes(Na, Lh)));
     ctx->launches[SLSHT_STAGE_TABLES]++;
-    cudaError_t er = launch_tc_etab(e.ptr, Na, Lh, st);
+    cudaError_t er = wide ? launch_tcw_etab(e.ptr, Na, Lh, st) : launch_tc_etab(e.ptr, Na, Lh, st);
     if (er != cudaSuccess) { record_cuda_error("launch_tc_etab", er); return SLSHT_E_CUDA; }
     CK(cudaEventRecord(e.ready, st));
     it = ctx->etab.emplace(key, e).first;
@@ -598,7 +600,7 @@ static int stage_input(slsht_ctx* ctx, Workspace& w, void** buf, size_t* cap, co
 
 static bool use_tensor_cores(slsht_ctx* ctx, const slsht_desc* d) {
   if (d->prec != SLSHT_FP32_BULK) return false;
-  if (!tc_supported(d->L_h, d->n_alpha)) return false;
+  if (!tc_supported(d->L_h, d->n_alpha) && !tcw_supported(d->L_h, d->n_alpha)) return false;
   if (ctx->opt_alpha_engine == 1 || ctx->opt_alpha_engine == 4) return false;
   return true;   // default for FP32_BULK when supported
 }
@@ -684,7 +686,10 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
   }
   // rotated-window route on the tensor cores: producer and alpha stage fused
   // into one kernel unless the separate producer kernel was asked for
+  // the factoring route's tensor-core producer serves narrow windows only
+  if (tc && route == 2 && Lh > 16) tc = 0;
   const bool fused = tc && route == 1 && Lh <= 16 && engine != 2;
+  const bool wide = tc && Lh > 16;      // K-chunked two-kernel tensor-core engine
   // CUDA-core alpha stage: split DFT over the alpha index when Na has a small
   // odd factor that saves work (SLSHT_OPT_ALPHA_ENGINE 4 forces the direct sum)
   const bool split = !tc && engine != 4 && alpha_split_factor(Lh, Na) > 0;
@@ -734,7 +739,8 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
   CKS(stage_input(ctx, w, &w.lm, &w.lm_cap, lm, sizeof(int2) * (size_t)n_pairs, st, &lm_dev));
 
   // chunking: X scratch of the chunk kept near L2 size
-  const size_t x_per_pair = tc ? tc_xblob_bytes(Nb, Ng, Lh) : (size_t)K * J * (f64 ? sizeof(double2) : sizeof(float2));
+  const size_t x_per_pair = wide ? tcw_xblob_bytes(Nb, Ng, Lh)
+                            : tc ? tc_xblob_bytes(Nb, Ng, Lh) : (size_t)K * J * (f64 ? sizeof(double2) : sizeof(float2));
   int P;
   if (chunk_opt > 0) {
     P = (int)std::min<int64_t>(chunk_opt, n_pairs);
@@ -744,6 +750,9 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
     const size_t target = (size_t)96 << 20;
     P = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_pairs, target / std::max<size_t>(1, x_per_pair)));
     P = std::min(P, 256);
+    // the wide engine's producer shares each H tile in L2 across the pairs of
+    // a chunk: at least four pairs a chunk
+    if (wide) P = std::max(P, std::min<int>(n_pairs, 4));
   }
   if (host_out) {
     // staging buffers for the chunk outputs (double-buffered, D2H on the copy stream)
@@ -857,7 +866,10 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
       const double2* Ysrc = route == 2 ? (const double2*)w.Y : nullptr;
       if (route == 1) {
         // (route 1 on CUDA cores forms X inside the alpha tile kernel)
-        LAUNCH(SLSHT_STAGE_BETA, ax, launch_xa_from_h(kcc, (const float2*)w.H, Lh, Nb, Ng, np, X, ax));
+        if (wide)
+          LAUNCH(SLSHT_STAGE_BETA, ax, launch_xaw_from_h(kcc, (const float2*)w.H, Lh, Nb, Ng, np, X, ax));
+        else
+          LAUNCH(SLSHT_STAGE_BETA, ax, launch_xa_from_h(kcc, (const float2*)w.H, Lh, Nb, Ng, np, X, ax));
       } else if (tc) {
         LAUNCH(SLSHT_STAGE_BETA, ax,
                launch_betagamma_tc(kcc, (const double2*)h_dev, nullptr, Ysrc, (const float2*)eg, Lh, Nb, Ng, np, X, ax));
@@ -920,6 +932,9 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
         std::lock_guard<std::mutex> g(ctx->mu);
         ctx->opt_wait_test = 0;
       }
+    } else if (wide) {
+      LAUNCH(SLSHT_STAGE_ALPHA, st,
+             launch_alpha_tcw(X, etab, Lh, Na, Nb, Ng, np, (float2*)gdst, ctx->num_sms, sl, st));
     } else if (tc) {
       LAUNCH(SLSHT_STAGE_ALPHA, st,
              launch_alpha_tc(X, etab, Lh, Na, Nb, Ng, np, (float2*)gdst, ctx->num_sms, sl, st));

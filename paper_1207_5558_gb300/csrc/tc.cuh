@@ -35,6 +35,16 @@ cudaError_t launch_alpha_tc(const void* xblob, const void* etab, int Lh, int Na,
 cudaError_t launch_alpha_fused(const double2* kc, const float2* H, const void* etab, int Lh, int Na, int Nb,
                                int Ng, int npairs, float2* g, int num_sms, int wait_test, const int2* slots,
                                cudaStream_t st);
+// Wide windows, 16 < Lh <= 64 (alpha_tcw.cu): K split into 2 or 4 chunks of
+// 64; the same E-table / A-blob / alpha-stage roles as the narrow engine.
+bool tcw_supported(int Lh, int Na);
+size_t tcw_etab_bytes(int Na, int Lh);
+cudaError_t launch_tcw_etab(void* etab, int Na, int Lh, cudaStream_t st);
+size_t tcw_xblob_bytes(int Nb, int Ng, int Lh);
+cudaError_t launch_xaw_from_h(const double2* kc, const float2* H, int Lh, int Nb, int Ng, int npairs, void* xblob,
+                              cudaStream_t st);
+cudaError_t launch_alpha_tcw(const void* xblob, const void* etab, int Lh, int Na, int Nb, int Ng, int npairs,
+                             float2* g, int num_sms, const int2* slots, cudaStream_t st);
 // Device error word shared by the tensor-core kernels (allocated on first use).
 int* tc_error_word();
 // Non-zero (and cleared) if a tensor-core kernel gave up on a bounded wait

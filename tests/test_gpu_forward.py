@@ -439,3 +439,47 @@ def test_fp64_widest_window_band(ctx, Na, arith):
     finally:
         ctx.set_option(pkg.SLSHT_OPT_FP64_ARITH, 0)
     assert rel(g, ref) < TOL64
+
+
+@pytest.mark.parametrize("Lf,Lh,grid", [
+    (20, 17, (70, 9, 33)),      # two K-chunks; a ragged alpha chunk (70 = 64 + 6), 297 columns
+    (12, 32, (130, 5, 63)),     # two K-chunks at their limit
+    (8, 33, (65, 4, 65)),       # four K-chunks from here on
+    (6, 64, (127, 3, 131)),     # four K-chunks at the largest window band
+])
+def test_wide_tensor_core_engine(ctx, Lf, Lh, grid):
+    """FP32_BULK with L_h > 16 on the tensor cores (K split into 2 or 4 chunks
+    of 64) against the oracle and against the CUDA-core path."""
+    import paper_1207_5558_gb300 as pkg
+    f = synth.signal_powerlaw(Lf, 700 + Lh)
+    h = synth.window_cn(Lh, 800 + Lh, decay=1.0)
+    pairs = synth.pairs_random(Lf + Lh - 1, 6, 900 + Lh)
+    ref = O.forward_coeff(f, h, Lf, Lh, pairs, grid, kroute="recurrence" if Lh > 40 else "exact")
+    g = _fw(ctx, Lf, Lh, grid, f, h, pairs, 1)
+    ctx.set_option(pkg.SLSHT_OPT_ALPHA_ENGINE, 1)
+    try:
+        gc = _fw(ctx, Lf, Lh, grid, f, h, pairs, 1)
+    finally:
+        ctx.set_option(pkg.SLSHT_OPT_ALPHA_ENGINE, 0)
+    assert rel(g, ref) < TOL32
+    assert rel(gc, ref) < TOL32
+    assert rel(g, gc) < 2e-6
+
+
+def test_wide_tensor_core_real_fields(ctx):
+    """The wide engine's mirror stores: real f and h, SLSHT_OPT_REAL_FIELDS,
+    equal to the full computation and the oracle."""
+    import paper_1207_5558_gb300 as pkg
+    Lf, Lh, grid = 10, 24, (67, 5, 47)
+    f = synth.signal_powerlaw(Lf, 951)
+    h = synth.signal_cn_real(Lh, 952)
+    pairs = np.concatenate([synth.pairs_bands([5, 20]), np.array([[7, 3]], dtype=np.int32)])
+    ref = O.forward_coeff(f, h, Lf, Lh, pairs, grid)
+    full = _fw(ctx, Lf, Lh, grid, f, h, pairs, 1)
+    ctx.set_option(pkg.SLSHT_OPT_REAL_FIELDS, 1)
+    try:
+        half = _fw(ctx, Lf, Lh, grid, f, h, pairs, 1)
+    finally:
+        ctx.set_option(pkg.SLSHT_OPT_REAL_FIELDS, 0)
+    assert rel(half, ref) < TOL32
+    assert rel(half, full) < 2e-6
