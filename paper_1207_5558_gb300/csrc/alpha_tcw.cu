@@ -180,8 +180,14 @@ cudaError_t launch_xaw_from_h(const double2* kc, const float2* H, int Lh, int Nb
   const int nk = tcw_nk(Lh), tiles = tcw_tiles(Nb, Ng);
   const size_t smem = sizeof(float) * (size_t)64 * nk * XW_COLS + sizeof(int) * XW_COLS;
   if (npairs > 65535 || 2LL * tiles > 65535) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_xaw_from_h, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  // the ceiling of the largest case (four K-chunks), set once (never inside a stream capture)
+  static bool attr = false;
+  if (!attr) {
+    const size_t smax = sizeof(float) * (size_t)64 * 4 * XW_COLS + sizeof(int) * XW_COLS;
+    cudaError_t e = cudaFuncSetAttribute(k_xaw_from_h, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
   dim3 grid(npairs, 2 * tiles);
   k_xaw_from_h<<<grid, 256, smem, st>>>(kc, H, Lh, Nb * Ng, nk, (unsigned char*)xblob, tcw_xblob_bytes(Nb, Ng, Lh),
                                         tiles);

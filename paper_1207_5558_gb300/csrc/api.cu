@@ -1181,7 +1181,13 @@ struct BatchItemHost {
   int nt = 0, form = 0, tuned = 0;     // form -1: fused tensor-core kernel
   int engine = 0;                      // 0 CUDA cores in the item's precision, 1 double-float, 2 tensor cores
   const void* etab = nullptr;
+  void* xw = nullptr;                  // wide tensor-core items: A-operand scratch of xw_pairs pairs
+  int xw_pairs = 0;
 };
+
+// Pairs a chunk of a wide tensor-core item (the producer shares each H tile
+// in L2 across a chunk's pairs).
+#define XW_CHUNK 4
 
 #define ENG_NATIVE 0
 #define ENG_DD 1
@@ -1273,8 +1279,30 @@ static int batch_rule_nt(int kp, int Lh, long long J) {
 }
 
 static bool batch_tc_ok(const slsht_batch* b, const slsht_desc& d) {
-  return !(b->flags & SLSHT_BATCH_NO_TC) && d.prec == SLSHT_FP32_BULK && tc_supported(d.L_h, d.n_alpha) &&
-         d.L_h <= 16;
+  return !(b->flags & SLSHT_BATCH_NO_TC) && d.prec == SLSHT_FP32_BULK &&
+         ((tc_supported(d.L_h, d.n_alpha) && d.L_h <= 16) || tcw_supported(d.L_h, d.n_alpha));
+}
+
+// The tensor-core launches of one item, chunk by chunk: the fused kernel
+// (L_h <= 16), or the wide engine's producer and alpha kernels.
+static cudaError_t batch_tc_launch(const slsht_batch* b, const BatchItemHost& it, int npairs, int nb, void* xw,
+                                   int xw_pairs, void* g, cudaStream_t st) {
+  const slsht_desc& d = it.d;
+  const double2* kc = b->cpl[it.cpl].kc;
+  const float2* H = (const float2*)b->rot[it.rot].H;
+  if (d.L_h <= 16)
+    return launch_alpha_fused(kc, H, it.etab, d.L_h, d.n_alpha, nb, d.n_gamma, npairs, (float2*)g, b->ctx->num_sms,
+                              0, nullptr, st);
+  const size_t n2 = (size_t)d.L_h * d.L_h, per_pair = (size_t)d.n_alpha * nb * d.n_gamma;
+  for (int off = 0; off < npairs; off += xw_pairs) {
+    const int np = std::min(xw_pairs, npairs - off);
+    cudaError_t e = launch_xaw_from_h(kc + off * n2, H, d.L_h, nb, d.n_gamma, np, xw, st);
+    if (e == cudaSuccess)
+      e = launch_alpha_tcw(xw, it.etab, d.L_h, d.n_alpha, nb, d.n_gamma, np, (float2*)g + off * per_pair,
+                           b->ctx->num_sms, nullptr, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 // Phase table of the alpha stage for a form: the direct sum's (cos, sin)(2 pi r a / Na)
@@ -1311,7 +1339,7 @@ static BItem batch_item_view(const slsht_batch* b, int ii, int engine) {
 // as a launch of its own over the item's pairs (np of them, no
 // replication).  Returns device milliseconds per sample in *cost.
 static int batch_time_candidate(slsht_batch* b, int ii, int nt, int form, int engine, int np, int reps, int nbs,
-                                void* scratch, void* d_item, void* d_tiles, int* d_ctr, double* cost) {
+                                void* scratch, void* xw, void* d_item, void* d_tiles, int* d_ctr, double* cost) {
   slsht_ctx* ctx = b->ctx;
   const BatchItemHost& it = b->items[ii];
   const slsht_desc& d = it.d;
@@ -1349,8 +1377,7 @@ static int batch_time_candidate(slsht_batch* b, int ii, int nt, int form, int en
       e = launch_batch_alpha(bi.prec, (const BItem*)d_item, (const BTile*)d_tiles, (int)tl.size(), d_ctr, grid, smem,
                              b->cs);
     else
-      e = launch_alpha_fused(b->cpl[it.cpl].kc, (const float2*)b->rot[it.rot].H, it.etab, d.L_h, d.n_alpha,
-                             nbs, d.n_gamma, np * reps, (float2*)scratch, ctx->num_sms, 0, nullptr, b->cs);
+      e = batch_tc_launch(b, it, np * reps, nbs, xw, XW_CHUNK, scratch, b->cs);
     if (e != cudaSuccess) { record_cuda_error("batch tuning launch", e); return SLSHT_E_CUDA; }
     CK(cudaEventRecord(b->tb, b->cs));
     CK(cudaEventSynchronize(b->tb));
@@ -1434,8 +1461,10 @@ static int batch_tune(slsht_batch* b, int ii) {
   reps = (int)std::max<double>(1.0, std::min<double>(reps, std::floor(1.6e7 / (per_pair * np))));
   const size_t out_bytes = (size_t)np * reps * Na * Js * el2_of(d.prec);
   const size_t max_tiles = (size_t)np * reps * ((Js + 31) / 32);
-  void *scratch = nullptr, *d_item = nullptr, *d_tiles = nullptr, *d_ctr = nullptr;
+  void *scratch = nullptr, *d_item = nullptr, *d_tiles = nullptr, *d_ctr = nullptr, *xw = nullptr;
+  const size_t xw_bytes = (tc_ok && Lh > 16) ? tcw_xblob_bytes(nbs, d.n_gamma, Lh) * XW_CHUNK : 0;
   int st = ctx_alloc(ctx, out_bytes, &scratch);
+  if (st == SLSHT_OK && xw_bytes) st = ctx_alloc(ctx, xw_bytes, &xw);
   if (st == SLSHT_OK) st = ctx_alloc(ctx, sizeof(BItem), &d_item);
   if (st == SLSHT_OK) st = ctx_alloc(ctx, sizeof(BTile) * max_tiles, &d_tiles);
   if (st == SLSHT_OK) st = ctx_alloc(ctx, 16, &d_ctr);
@@ -1444,11 +1473,12 @@ static int batch_tune(slsht_batch* b, int ii) {
   for (size_t c = 0; c < cand.size() && st == SLSHT_OK; ++c) {
     double cost = 0.0;
     st = batch_time_candidate(b, ii, std::get<0>(cand[c]), std::get<1>(cand[c]), std::get<2>(cand[c]), np, reps,
-                              nbs, scratch, d_item, d_tiles, (int*)d_ctr, &cost);
+                              nbs, scratch, xw, d_item, d_tiles, (int*)d_ctr, &cost);
     if (st == SLSHT_OK && cost < best) { best = cost; pick = cand[c]; }
   }
   cudaStreamSynchronize(b->cs);
   ctx_free(ctx, scratch, out_bytes);
+  ctx_free(ctx, xw, xw_bytes);
   ctx_free(ctx, d_item, sizeof(BItem));
   ctx_free(ctx, d_tiles, sizeof(BTile) * max_tiles);
   ctx_free(ctx, d_ctr, 16);
@@ -1479,9 +1509,8 @@ static int batch_enqueue(slsht_batch* b, cudaStream_t st) {
   }
   for (int ii : b->tc_items) {
     const BatchItemHost& it = b->items[ii];
-    e = launch_alpha_fused(b->cpl[it.cpl].kc, (const float2*)b->rot[it.rot].H, it.etab, it.d.L_h, it.d.n_alpha,
-                           it.d.n_beta, it.d.n_gamma, it.npairs, (float2*)it.g, ctx->num_sms, 0, nullptr, st);
-    if (e != cudaSuccess) { record_cuda_error("launch_alpha_fused", e); return SLSHT_E_CUDA; }
+    e = batch_tc_launch(b, it, it.npairs, it.d.n_beta, it.xw, it.xw_pairs, it.g, st);
+    if (e != cudaSuccess) { record_cuda_error("batch tensor-core launch", e); return SLSHT_E_CUDA; }
   }
   return SLSHT_OK;
 }
@@ -1694,8 +1723,18 @@ static int batch_build(slsht_batch* b, const slsht_batch_item* src, int32_t n, c
       b->k_alpha++;
     }
   }
-  for (int32_t i = 0; i < n; ++i)
-    if (b->items[i].engine == ENG_TC) { b->tc_items.push_back(i); b->k_alpha++; }
+  for (int32_t i = 0; i < n; ++i) {
+    BatchItemHost& it = b->items[i];
+    if (it.engine != ENG_TC) continue;
+    b->tc_items.push_back(i);
+    if (it.d.L_h <= 16) {
+      b->k_alpha++;
+    } else {   // wide: producer + alpha kernel per chunk of XW_CHUNK pairs
+      it.xw_pairs = std::min(it.npairs, XW_CHUNK);
+      CKS(batch_alloc(b, tcw_xblob_bytes(it.d.n_beta, it.d.n_gamma, it.d.L_h) * it.xw_pairs, &it.xw));
+      b->k_alpha += 2 * ((it.npairs + it.xw_pairs - 1) / it.xw_pairs);
+    }
+  }
   CKS(batch_upload(b, b->bitem.data(), sizeof(BItem) * b->bitem.size(), &b->d_bitem));
   void* ctr = nullptr;
   CKS(batch_alloc(b, 16, &ctr));

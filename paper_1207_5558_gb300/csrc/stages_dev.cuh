@@ -71,25 +71,25 @@ __device__ __forceinline__ void rotwin_block_smem_to(const double2* __restrict__
     ep[t] = eg[(size_t)(c0 + c) * K + (Lh - 1) - p + qp];
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < nqr * ncr; t += blockDim.x) {
-    const int qi = t / ncr, c = t % ncr;
-    const T2* hr = hd + qi * w;
+  // each thread: rows qa and qa + nqh of one gamma column (the phase row read
+  // once for both; four independent multiply-add chains)
+  const int nqh = (nqr + 1) / 2;
+  for (int t = threadIdx.x; t < nqh * ncr; t += blockDim.x) {
+    const int qa = t / ncr, c = t % ncr, qb = qa + nqh;
+    const bool has_b = qb < nqr;
+    const T2* ha = hd + qa * w;
+    const T2* hb = hd + (has_b ? qb : qa) * w;
     const T2* er = ep + c * w;
-    T re = 0, im = 0, re2 = 0, im2 = 0;          // two chains: even and odd q'
-    int u = 0;
-    for (; u + 1 < w; u += 2) {                  // h d (cos - i sin)
-      const T2 a = hr[u], E = er[u], a2 = hr[u + 1], E2 = er[u + 1];
-      re = fma(a.x, E.x, re); re = fma(a.y, E.y, re);
-      im = fma(a.y, E.x, im); im = fma(-a.x, E.y, im);
-      re2 = fma(a2.x, E2.x, re2); re2 = fma(a2.y, E2.y, re2);
-      im2 = fma(a2.y, E2.x, im2); im2 = fma(-a2.x, E2.y, im2);
+    T ra = 0, ia = 0, rb = 0, ib = 0;
+    for (int u = 0; u < w; ++u) {                // h d (cos - i sin)
+      const T2 E = er[u], a = ha[u], b2 = hb[u];
+      ra = fma(a.x, E.x, ra); ra = fma(a.y, E.y, ra);
+      ia = fma(a.y, E.x, ia); ia = fma(-a.x, E.y, ia);
+      rb = fma(b2.x, E.x, rb); rb = fma(b2.y, E.y, rb);
+      ib = fma(b2.y, E.x, ib); ib = fma(-b2.x, E.y, ib);
     }
-    if (u < w) {
-      const T2 a = hr[u], E = er[u];
-      re = fma(a.x, E.x, re); re = fma(a.y, E.y, re);
-      im = fma(a.y, E.x, im); im = fma(-a.x, E.y, im);
-    }
-    store(h_index(p * p + q0 + qi, b * Ng + c0 + c, n2), re + re2, im + im2);
+    store(h_index(p * p + q0 + qa, b * Ng + c0 + c, n2), ra, ia);
+    if (has_b) store(h_index(p * p + q0 + qb, b * Ng + c0 + c, n2), rb, ib);
   }
 }
 

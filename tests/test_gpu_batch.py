@@ -47,10 +47,10 @@ def _item(Lf, Lh, grid, f, h, pairs, prec):
 
 
 def _mix():
-    """Eight analyses: both precisions, L_h from 1 to 16, prime and composite
+    """Nine analyses: both precisions, L_h from 1 to 20, prime and composite
     N_alpha (direct sum and split DFT), ragged column counts, a shared signal
-    (one coupling for two windows), a shared window over two grids, and an
-    FP32 item the tensor cores can take."""
+    (one coupling for two windows), a shared window over two grids, and FP32
+    items the tensor cores can take (narrow and wide windows)."""
     fA = synth.signal_powerlaw(8, 11)
     hA = synth.window_cn(4, 12)
     hF = synth.window_cn(4, 13)
@@ -65,6 +65,8 @@ def _mix():
         (8, 4, (15, 8, 7), fA, hF, synth.pairs_random(11, 9, 21), 0),       # same f and pairs as item 0
         (8, 4, (45, 6, 11), fA, hA, synth.pairs_random(11, 4, 25), 0),      # same window as item 0, other grid
         (9, 8, (63, 9, 15), synth.signal_powerlaw(9, 22), synth.window_cn(8, 23), synth.pairs_random(16, 6, 26), 1),
+        (7, 20, (40, 7, 39), synth.signal_powerlaw(7, 24), synth.window_cn(20, 25, decay=1.0),
+         synth.pairs_random(26, 5, 27), 1),                                   # wide window: K in two chunks
     ]
     return spec
 
