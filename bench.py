@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--profile-prec", type=int, default=1, help="precision of --profile-pairs (1 FP32_BULK, 0 FP64)")
+    ap.add_argument("--profile-workload", type=int, default=3, choices=(3, 5),
+                    help="workload of --profile-pairs (5: its band limits on 256 beta rows)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=2000,
@@ -304,17 +306,27 @@ def serve_bench(pkg, device, n, rate, seed=4000, max_outstanding_bytes=48 << 30,
                         "outstanding outputs capped at 48 GB, later arrivals wait (latency from arrival)"}
 
 
-def profile_case(pkg, n, prec=1):
-    """A small case of workload 3 for kernel captures: one chunk of 48 pairs per
-    launch, a few GB on the device, two forward passes, then two inverses of
-    the result (prec 1: FP32_BULK, 0: FP64)."""
+def profile_case(pkg, n, prec=1, wl=3):
+    """A small case for kernel captures: one chunk of 48 pairs per launch, a
+    few GB on the device, two forward passes, then two inverses of the result
+    (prec 1: FP32_BULK, 0: FP64).  wl 3: the last n pairs of workload 3; wl 5:
+    the first n pairs of workload 5 (its band limits, window and N_alpha,
+    N_gamma) on 256 of its beta rows."""
     import numpy as np
     import torch
     import synth
-    c = synth.CONFIGS[3]
-    f, h, pairs = synth.config_inputs(3, 0)
-    sub = np.ascontiguousarray(pairs[-n:])
     ctx = pkg.Context(0, 16 << 30)
+    if wl == 5:
+        from synth.window import ellipse_from_axes
+        c5 = synth.CONFIGS[5]
+        h, _ = ctx.window_ellipse(c5["Lh"], *ellipse_from_axes(8.0, 3.0))
+        f, _, pairs = synth.config_inputs(5, window_cache=h)
+        c = dict(c5, grid=(c5["grid"][0], 256, c5["grid"][2]))
+        sub = np.ascontiguousarray(pairs[:n])
+    else:
+        c = synth.CONFIGS[3]
+        f, h, pairs = synth.config_inputs(3, 0)
+        sub = np.ascontiguousarray(pairs[-n:])
     ctx.set_option(pkg.SLSHT_OPT_CHUNK_PAIRS, 48)
     g = torch.empty((n,) + c["grid"], dtype=torch.complex64 if prec == 1 else torch.complex128, device="cuda")
     if prec == 0:
@@ -401,7 +413,7 @@ def main():
 
     torch.cuda.set_device(local)
     if args.profile_pairs > 0:
-        profile_case(pkg, args.profile_pairs, args.profile_prec)
+        profile_case(pkg, args.profile_pairs, args.profile_prec, args.profile_workload)
         return
     dist = None
     if world > 1:
@@ -703,9 +715,10 @@ def main():
     def workload5_leg():
         """Workload 5 (L_f = 2048, L_h = 64, the 8 x 3 degree elliptical
         window from the device generator, 16 seeded pairs, each on the full
-        4095 x 2048 x 127 grid, FP32_BULK): 4 calls of 4 pairs into one 34 GB
-        buffer, and one batch plan of the 4 pair groups (same buffer), events
-        on the stream.  The alpha stage runs on CUDA cores (L_h > 16)."""
+        4095 x 2048 x 127 grid, FP32_BULK, 136 GB of g): one call, and one
+        batch plan of the same pairs (same buffer), events on the stream.
+        The alpha stage runs on the wide tensor-core engine (K in four
+        chunks of 64)."""
         from synth.window import ellipse_from_axes
         c5 = synth.CONFIGS[5]
         L5f, L5h, g5 = c5["Lf"], c5["Lh"], c5["grid"]
@@ -713,7 +726,7 @@ def main():
         f5, _, p5 = synth.config_inputs(5, window_cache=h5)
         f5d, h5d = torch.from_numpy(f5).cuda(), torch.from_numpy(h5).cuda()
         p5d = torch.from_numpy(np.ascontiguousarray(p5)).cuda()
-        npb = 4
+        npb = len(p5)
         gb = torch.empty((npb,) + g5, dtype=torch.complex64, device="cuda")
         desc = pkg.make_desc(L5f, L5h, g5, 1)
         smp = len(p5) * synth.samples_per_pair(g5)
@@ -733,8 +746,7 @@ def main():
         ctx.profile(False)
         ms = e0.elapsed_time(e1)
         st = ctx.stats(reset=True)
-        items = [{"L_f": L5f, "L_h": L5h, "grid": g5, "prec": 1, "f": f5d, "h": h5d, "lm": p5[i:i + npb],
-                  "g_out": gb} for i in range(0, len(p5), npb)]
+        items = [{"L_f": L5f, "L_h": L5h, "grid": g5, "prec": 1, "f": f5d, "h": h5d, "lm": p5, "g_out": gb}]
         bp = ctx.batch(items, stream=stream)
         bp.launch(stream)
         barrier()
@@ -743,23 +755,16 @@ def main():
         e1.record(stream)
         barrier()
         ms_plan = e0.elapsed_time(e1)
-        P5 = bp.query(pkg.SLSHT_BQ_ALPHA_FORM, 0)
-        K5 = 2 * L5h - 1
-        H5 = (P5 - 1) // 2 if P5 > 0 else 0
-        fma = (4.0 * K5 + 4 * H5 * H5 + 10 * H5) / P5 if P5 > 0 else 4.0 * (L5h - 1) + 2
-        fma += 4.0 * L5h * L5h / g5[0]
-        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        eng = bp.query(pkg.SLSHT_BQ_ENGINE, 0)
+        hbm = peaks()[0]["hbm_gbs"] * 1e9
         out = {"workload": "workload 5: L_f=2048, L_h=64 ellipse 8x3 deg, 16 pairs, grid 4095x2048x127, FP32_BULK",
                "samples": smp, "per_call_ms": ms, "value_per_call": smp / (ms / 1e3),
-               "stage_ms_per_call_step": st["ms"], "plan_ms": ms_plan, "value_plan": smp / (ms_plan / 1e3),
-               "alpha_form": "split P=%d" % P5 if P5 > 0 else "direct",
-               "tile_cols": bp.query(pkg.SLSHT_BQ_TILE_COLS, 0),
-               "alpha_fp32_fma_per_sample": fma,
-               "plan_fp32_fma_frac": smp / (ms_plan / 1e3) * fma / (128.0 * sms * 2070e6),
-               "plan_hbm_frac": smp / (ms_plan / 1e3) * 8.0 / (peaks()[0]["hbm_gbs"] * 1e9),
-               "note": "the per-call figure rebuilds the rotated window in each of the 4 calls; the plan "
-                       "forms it once; fractions against 128 FP32 lanes x SMs x 2070 MHz and the measured copy "
-                       "bandwidth"}
+               "stage_ms_per_call": st["ms"], "plan_ms": ms_plan, "value_plan": smp / (ms_plan / 1e3),
+               "plan_engine": ["CUDA cores", "double-float", "tensor cores"][eng],
+               "alpha_stage_hbm_frac": smp * 8.0 / (st["ms"]["alpha"] / 1e3) / hbm if st["ms"]["alpha"] else None,
+               "per_call_hbm_frac": smp / (ms / 1e3) * 8.0 / hbm,
+               "note": "stage times overlap (two streams); the alpha fraction is the g bytes over the alpha "
+                       "kernels' summed time against the measured copy bandwidth"}
         bp.close()
         del gb
         torch.cuda.empty_cache()

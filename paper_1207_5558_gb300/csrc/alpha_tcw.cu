@@ -19,7 +19,7 @@
 // memory; k_alpha_tcw (persistent, one CTA per SM, work item = (pair, tile))
 // keeps the item's whole A operand in shared memory, streams the E-table
 // K-chunks (32 KB each) through a ring of 3 or 4 stages with cp.async.bulk, issues
-// the MMAs from one thread into two TMEM accumulators (2 x 128 columns), and
+// the MMAs from one thread into four TMEM accumulators (4 x 128 columns), and
 // eight epilogue warps drain them and store g.  Every mbarrier wait is
 // bounded; on expiry the CTA raises its abort flag, waits (bounded) for its
 // copies and MMAs in flight, frees TMEM and exits, and the host reads the
@@ -196,8 +196,9 @@ cudaError_t launch_xaw_from_h(const double2* kc, const float2* H, int Lh, int Nb
 
 // ---------------------------------------------------------------- the kernel
 #define TCW_MAX_BS 4
+#define TCW_ACC 4                       // TMEM accumulators (4 x 128 columns: all 512)
 struct TcwBars {
-  uint64_t a_full, a_empty, b_full[TCW_MAX_BS], b_empty[TCW_MAX_BS], acc_full[2], acc_empty[2], drain;
+  uint64_t a_full, a_empty, b_full[TCW_MAX_BS], b_empty[TCW_MAX_BS], acc_full[TCW_ACC], acc_empty[TCW_ACC], drain;
   uint32_t tmem_base;
   int abort_flag;
 };
@@ -229,7 +230,7 @@ k_alpha_tcw(const unsigned char* __restrict__ xblob, size_t blob_stride, int til
       mbar_init(smem_u32(&bars->b_full[i]), 1);
       mbar_init(smem_u32(&bars->b_empty[i]), 1);
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < TCW_ACC; ++i) {
       mbar_init(smem_u32(&bars->acc_full[i]), 1);
       mbar_init(smem_u32(&bars->acc_empty[i]), 32 * TC_EPI_WARPS);
     }
@@ -237,8 +238,8 @@ k_alpha_tcw(const unsigned char* __restrict__ xblob, size_t blob_stride, int til
     bars->abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 1) {   // TMEM: two 128 x TC_N FP32 accumulators
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
+  if (warp == 1) {   // TMEM: TCW_ACC accumulators of 128 x TC_N FP32
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
                      smem_u32(&bars->tmem_base)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
@@ -305,8 +306,9 @@ k_alpha_tcw(const unsigned char* __restrict__ xblob, size_t blob_stride, int til
       for (long long it = blockIdx.x; it < nitems && ok; it += gridDim.x, ++li) {
         if (!(ok = mbar_wait(smem_u32(&bars->a_full), (uint32_t)(li & 1), abort_flag))) break;
         for (int c = 0; c < nch && ok; ++c, ++ac) {
-          const int acc = (int)(ac & 1);
-          if (!(ok = mbar_wait(smem_u32(&bars->acc_empty[acc]), (uint32_t)(((ac >> 1) & 1) ^ 1), abort_flag)))
+          const int acc = (int)(ac % TCW_ACC);
+          if (!(ok = mbar_wait(smem_u32(&bars->acc_empty[acc]), (uint32_t)(((ac / TCW_ACC) & 1) ^ 1),
+                               abort_flag)))
             break;
           const uint32_t d = tmem + (uint32_t)(acc * TC_N);
           for (int kc = 0; kc < NK; ++kc, ++bc) {
@@ -358,10 +360,11 @@ k_alpha_tcw(const unsigned char* __restrict__ xblob, size_t blob_stride, int til
       float2* gm = sl.y >= 0 ? g + (size_t)(sl.y >> 1) * Na * J + (jin ? j : 0) : nullptr;
       const float msc = (sl.y & 1) ? -sc : sc;
       for (int c = 0; c < nch; ++c, ++ac) {
-        const int acc = (int)(ac & 1);
+        const int acc = (int)(ac % TCW_ACC);
         // one lane waits, the warp follows: tcgen05.ld needs a converged warp
         int got = 0;
-        if (lane == 0) got = mbar_wait(smem_u32(&bars->acc_full[acc]), (uint32_t)((ac >> 1) & 1), abort_flag);
+        if (lane == 0)
+          got = mbar_wait(smem_u32(&bars->acc_full[acc]), (uint32_t)((ac / TCW_ACC) & 1), abort_flag);
         got = __shfl_sync(0xffffffffu, got, 0);
         __syncwarp();
         if (!(ok = got != 0)) break;
@@ -408,7 +411,7 @@ k_alpha_tcw(const unsigned char* __restrict__ xblob, size_t blob_stride, int til
   if (*abort_flag && threadIdx.x == 0) atomicExch(err, 1);
   tc_fence_after();
   if (warp == 1) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
   }
 }
 
