@@ -71,25 +71,30 @@ __device__ __forceinline__ void rotwin_block_smem_to(const double2* __restrict__
     ep[t] = eg[(size_t)(c0 + c) * K + (Lh - 1) - p + qp];
   }
   __syncthreads();
-  // each thread: rows qa and qa + nqh of one gamma column (the phase row read
-  // once for both; four independent multiply-add chains)
-  const int nqh = (nqr + 1) / 2;
-  for (int t = threadIdx.x; t < nqh * ncr; t += blockDim.x) {
-    const int qa = t / ncr, c = t % ncr, qb = qa + nqh;
-    const bool has_b = qb < nqr;
+  // each thread: rows qa, qa + nqh and columns ca, ca + nch of the chunk (a
+  // 2 x 2 block: two product rows and two phase rows read per step for four
+  // multiply-adds, eight independent chains); a warp shares two q rows
+  const int nqh = (nqr + 1) / 2, nch = (ncr + 1) / 2;
+  for (int t = threadIdx.x; t < nqh * nch; t += blockDim.x) {
+    const int qa = t / nch, ca = t % nch, qb = qa + nqh, cb = ca + nch;
+    const bool has_q = qb < nqr, has_c = cb < ncr;
     const T2* ha = hd + qa * w;
-    const T2* hb = hd + (has_b ? qb : qa) * w;
-    const T2* er = ep + c * w;
-    T ra = 0, ia = 0, rb = 0, ib = 0;
+    const T2* hb = hd + (has_q ? qb : qa) * w;
+    const T2* ea = ep + ca * w;
+    const T2* eb = ep + (has_c ? cb : ca) * w;
+    T r00 = 0, i00 = 0, r01 = 0, i01 = 0, r10 = 0, i10 = 0, r11 = 0, i11 = 0;
     for (int u = 0; u < w; ++u) {                // h d (cos - i sin)
-      const T2 E = er[u], a = ha[u], b2 = hb[u];
-      ra = fma(a.x, E.x, ra); ra = fma(a.y, E.y, ra);
-      ia = fma(a.y, E.x, ia); ia = fma(-a.x, E.y, ia);
-      rb = fma(b2.x, E.x, rb); rb = fma(b2.y, E.y, rb);
-      ib = fma(b2.y, E.x, ib); ib = fma(-b2.x, E.y, ib);
+      const T2 a = ha[u], b2 = hb[u], E = ea[u], F = eb[u];
+      r00 = fma(a.x, E.x, r00); r00 = fma(a.y, E.y, r00); i00 = fma(a.y, E.x, i00); i00 = fma(-a.x, E.y, i00);
+      r01 = fma(a.x, F.x, r01); r01 = fma(a.y, F.y, r01); i01 = fma(a.y, F.x, i01); i01 = fma(-a.x, F.y, i01);
+      r10 = fma(b2.x, E.x, r10); r10 = fma(b2.y, E.y, r10); i10 = fma(b2.y, E.x, i10); i10 = fma(-b2.x, E.y, i10);
+      r11 = fma(b2.x, F.x, r11); r11 = fma(b2.y, F.y, r11); i11 = fma(b2.y, F.x, i11); i11 = fma(-b2.x, F.y, i11);
     }
-    store(h_index(p * p + q0 + qa, b * Ng + c0 + c, n2), ra, ia);
-    if (has_b) store(h_index(p * p + q0 + qb, b * Ng + c0 + c, n2), rb, ib);
+    const int ja = b * Ng + c0 + ca, jb = b * Ng + c0 + cb;
+    store(h_index(p * p + q0 + qa, ja, n2), r00, i00);
+    if (has_c) store(h_index(p * p + q0 + qa, jb, n2), r01, i01);
+    if (has_q) store(h_index(p * p + q0 + qb, ja, n2), r10, i10);
+    if (has_q && has_c) store(h_index(p * p + q0 + qb, jb, n2), r11, i11);
   }
 }
 
