@@ -38,11 +38,26 @@ bool tcw_supported(int Lh, int Na) { return Lh > 16 && Lh <= 64 && Na >= 1; }
 
 size_t tcw_etab_bytes(int Na, int Lh) { return (size_t)tcw_chunks(Na) * tcw_nk(Lh) * TC_B_BYTES; }
 
-// per pair: tiles x NK x 32 KB of A, then one float scale per padded column
+// per pair: tiles x NK x 32 KB of A, one float scale per padded column, then
+// the pair's coupling row as floats (the producer's operand)
+static inline size_t tcw_scales_bytes(size_t tiles) { return ((tiles * TC_M * sizeof(float)) + 1023) / 1024 * 1024; }
 size_t tcw_xblob_bytes(int Nb, int Ng, int Lh) {
   const size_t t = (size_t)tcw_tiles(Nb, Ng);
-  const size_t sc = ((t * TC_M * sizeof(float)) + 1023) / 1024 * 1024;
-  return t * (size_t)tcw_nk(Lh) * TC_A_BYTES + sc;
+  const size_t kf = ((size_t)Lh * Lh * sizeof(float2) + 1023) / 1024 * 1024;
+  return t * (size_t)tcw_nk(Lh) * TC_A_BYTES + tcw_scales_bytes(t) + kf;
+}
+
+// The coupling rows of the launch's pairs as floats, into each pair's blob:
+// one conversion per coefficient (float/double conversions share the slow
+// FP64 pipe on this GPU; the producer then reads floats).
+__global__ void k_kf_from_kc(const double2* __restrict__ kc, int n2, unsigned char* __restrict__ xblob,
+                             size_t blob_stride, size_t kf_off) {
+  const int pair = blockIdx.y;
+  float2* kf = reinterpret_cast<float2*>(xblob + (size_t)pair * blob_stride + kf_off);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n2; t += gridDim.x * blockDim.x) {
+    const double2 v = kc[(size_t)pair * n2 + t];
+    kf[t] = make_float2((float)v.x, (float)v.y);
+  }
 }
 
 // ---------------------------------------------------------------- E tables
@@ -83,7 +98,7 @@ cudaError_t launch_tcw_etab(void* etab, int Na, int Lh, cudaStream_t st) {
 
 // ---------------------------------------------------------------- A operand from H
 // X_q(j) = sum_{p>=|q|} k(p,q) H^p_q(j) for one pair and one 128-column tile:
-// A block serves half a tile (64 columns); the blocks of one tile for every
+// A block serves a quarter tile (32 columns); the blocks of one tile for every
 // pair of the launch are adjacent, so each H tile is read from HBM about once.
 //   phase 1: one item per (q, column), its degrees p >= |q| (H loads coalesced
 //            across columns, k broadcast through the cache) into the shared
@@ -91,19 +106,20 @@ cudaError_t launch_tcw_etab(void* etab, int Na, int Lh, cudaStream_t st) {
 //   phase 2: per column, the largest |entry| -> scale 2^e into [2^14, 2^15);
 //   phase 3: per (column, 16-byte chunk): scale, split into FP16 hi/lo, store
 //            swizzled into its K-chunk.  Columns beyond J are zero.
-#define XW_COLS 64                      // columns per producer block (half a tile)
+#define XW_COLS 32                      // columns per producer block (a quarter tile)
+#define XW_PARTS (TC_M / XW_COLS)
 
 __global__ void __launch_bounds__(256)
-k_xaw_from_h(const double2* __restrict__ kc, const float2* __restrict__ H, int Lh, int J, int nk,
-             unsigned char* __restrict__ xblob, size_t blob_stride, int tiles) {
+k_xaw_from_h(const float2* __restrict__ H, int Lh, int J, int nk, unsigned char* __restrict__ xblob,
+             size_t blob_stride, int tiles, size_t kf_off) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int half = 32 * nk, centre = 16 * nk - 1, KS = 2 * half;
   float* sX = reinterpret_cast<float*>(smem_raw);                 // [KS][XW_COLS]
   int* sEx = reinterpret_cast<int*>(sX + (size_t)KS * XW_COLS);   // [XW_COLS]
   // pairs vary fastest: the blocks of one H tile run together and share it in L2
-  const int pair = blockIdx.x, tile = blockIdx.y >> 1, r0 = (blockIdx.y & 1) * XW_COLS;
+  const int pair = blockIdx.x, tile = blockIdx.y / XW_PARTS, r0 = (blockIdx.y % XW_PARTS) * XW_COLS;
   const int n2 = Lh * Lh, K = 2 * Lh - 1;
-  const double2* kp = kc + (size_t)pair * n2;
+  const float2* kp = reinterpret_cast<const float2*>(xblob + (size_t)pair * blob_stride + kf_off);
   for (int t = threadIdx.x; t < KS * XW_COLS; t += blockDim.x) sX[t] = 0.f;
   __syncthreads();
   const int jt = tile * TC_M + r0;
@@ -115,27 +131,31 @@ k_xaw_from_h(const double2* __restrict__ kc, const float2* __restrict__ H, int L
     if (j < J) {
       const float2* hp = H + h_index(0, j, n2);      // row pq at hp + pq * 128
       int p = aq;
-      for (; p + 3 < Lh; p += 4) {                  // four loads in flight per step
-        float2 hv[4];
-        double2 kv[4];
+      float br = 0.f, bi = 0.f;                     // second chain (odd steps)
+      for (; p + 7 < Lh; p += 8) {                  // eight degrees' loads in flight per step
+        float2 hv[8], kv[8];
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
+        for (int v = 0; v < 8; ++v) {
           const int pq = (p + v) * (p + v) + (p + v) + q;
           hv[v] = __ldg(hp + (size_t)pq * 128);
           kv[v] = __ldg(kp + pq);
         }
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          const float kr = (float)kv[v].x, ki = (float)kv[v].y;
-          ar = fmaf(kr, hv[v].x, ar); ar = fmaf(-ki, hv[v].y, ar);
-          ai = fmaf(kr, hv[v].y, ai); ai = fmaf(ki, hv[v].x, ai);
+        for (int v = 0; v < 8; ++v) {
+          const float kr = kv[v].x, ki = kv[v].y;
+          float& xr = (v & 1) ? br : ar;
+          float& xi = (v & 1) ? bi : ai;
+          xr = fmaf(kr, hv[v].x, xr); xr = fmaf(-ki, hv[v].y, xr);
+          xi = fmaf(kr, hv[v].y, xi); xi = fmaf(ki, hv[v].x, xi);
         }
       }
+      ar += br;
+      ai += bi;
       for (; p < Lh; ++p) {
         const int pq = p * p + p + q;
         const float2 hv = __ldg(hp + (size_t)pq * 128);
-        const double2 kd = __ldg(kp + pq);
-        const float kr = (float)kd.x, ki = (float)kd.y;
+        const float2 kd = __ldg(kp + pq);
+        const float kr = kd.x, ki = kd.y;
         ar = fmaf(kr, hv.x, ar); ar = fmaf(-ki, hv.y, ar);
         ai = fmaf(kr, hv.y, ai); ai = fmaf(ki, hv.x, ai);
       }
@@ -179,7 +199,7 @@ cudaError_t launch_xaw_from_h(const double2* kc, const float2* H, int Lh, int Nb
   if (Lh <= 16 || Lh > 64) return cudaErrorInvalidValue;
   const int nk = tcw_nk(Lh), tiles = tcw_tiles(Nb, Ng);
   const size_t smem = sizeof(float) * (size_t)64 * nk * XW_COLS + sizeof(int) * XW_COLS;
-  if (npairs > 65535 || 2LL * tiles > 65535) return cudaErrorInvalidValue;
+  if (npairs > 65535 || (long long)XW_PARTS * tiles > 65535) return cudaErrorInvalidValue;
   // the ceiling of the largest case (four K-chunks), set once (never inside a stream capture)
   static bool attr = false;
   if (!attr) {
@@ -188,9 +208,12 @@ cudaError_t launch_xaw_from_h(const double2* kc, const float2* H, int Lh, int Nb
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  dim3 grid(npairs, 2 * tiles);
-  k_xaw_from_h<<<grid, 256, smem, st>>>(kc, H, Lh, Nb * Ng, nk, (unsigned char*)xblob, tcw_xblob_bytes(Nb, Ng, Lh),
-                                        tiles);
+  const size_t stride = tcw_xblob_bytes(Nb, Ng, Lh);
+  const size_t kf_off = (size_t)tiles * nk * TC_A_BYTES + tcw_scales_bytes(tiles);
+  k_kf_from_kc<<<dim3((Lh * Lh + 255) / 256, npairs), 256, 0, st>>>(kc, Lh * Lh, (unsigned char*)xblob, stride,
+                                                                   kf_off);
+  dim3 grid(npairs, XW_PARTS * tiles);
+  k_xaw_from_h<<<grid, 256, smem, st>>>(H, Lh, Nb * Ng, nk, (unsigned char*)xblob, stride, tiles, kf_off);
   return cudaGetLastError();
 }
 

@@ -221,7 +221,23 @@ __device__ __forceinline__ void ba_tile(const BItem& it, const BTile& tl, unsign
   const int J = it.J, Na = it.Na, tid = threadIdx.x;
   T2* sx = reinterpret_cast<T2*>(smem);                      // [q + Lh - 1][NT]
   T* cst = reinterpret_cast<T*>(sx + (size_t)K * NT);       // split-DFT constants
-  const double2* kp = it.kc + (size_t)tl.pair * n2;
+  // the pair's k in T: FP32 tiles with L_h <= 32 convert it once into shared
+  // memory (a float/double conversion runs on the slow FP64 pipe); wider
+  // windows (the row would cost occupancy) and FP64 tiles read it as stored
+  const double2* kd = it.kc + (size_t)tl.pair * n2;
+  const bool staged = sizeof(T) == sizeof(float) && Lh <= 32;
+  const T2* kp;
+  if (staged) {
+    T2* sk = reinterpret_cast<T2*>(cst + 2 * BA_CONST_ENTRIES);
+    for (int t = tid; t < n2; t += BA_THREADS) {
+      const double2 v = kd[t];
+      sk[t] = mk2((T)v.x, (T)v.y);
+    }
+    __syncthreads();
+    kp = sk;
+  } else {
+    kp = nullptr;
+  }
   const T2* H = reinterpret_cast<const T2*>(it.H);
   // X_q for the tile's columns: four degrees' loads in flight per step
   for (int e = tid; e < K * NT; e += BA_THREADS) {
@@ -231,23 +247,27 @@ __device__ __forceinline__ void ba_tile(const BItem& it, const BTile& tl, unsign
     T xr = 0, xi = 0;
     if (j < J) {
       for (int p0 = aq; p0 < Lh; p0 += 4) {
-        T2 hv[4];
-        double2 kv[4];
+        T2 hv[4], kv[4];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           const int p = p0 + v;
           if (p < Lh) {
             const int pq = p * p + p + q;
             hv[v] = H[h_index(pq, j, n2)];
-            kv[v] = __ldg(kp + pq);
+            if (staged) {
+              kv[v] = kp[pq];
+            } else {
+              const double2 k2 = __ldg(kd + pq);
+              kv[v] = mk2((T)k2.x, (T)k2.y);
+            }
           } else {
             hv[v] = mk2((T)0, (T)0);
-            kv[v] = make_double2(0.0, 0.0);
+            kv[v] = mk2((T)0, (T)0);
           }
         }
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-          const T kr = (T)kv[v].x, ki = (T)kv[v].y;
+          const T kr = kv[v].x, ki = kv[v].y;
           xr = fma(kr, hv[v].x, xr); xr = fma(-ki, hv[v].y, xr);
           xi = fma(kr, hv[v].y, xi); xi = fma(ki, hv[v].x, xi);
         }
@@ -461,7 +481,9 @@ __global__ void __launch_bounds__(BA_THREADS) k_batch_alpha(const BItem* __restr
 size_t batch_alpha_smem(int prec, int Lh, int nt) {
   const size_t el2 = prec == 1 ? sizeof(float2) : 16;     // double2, or float4 double-float pairs
   const size_t cst = prec == 1 ? sizeof(float) : (prec == 0 ? sizeof(double) : sizeof(ddv));
-  const size_t b = el2 * (size_t)(2 * Lh - 1) * nt + 2 * cst * BA_CONST_ENTRIES;
+  // X tile, split-DFT constants, and (FP32 kernel, L_h <= 32) the pair's k row as floats
+  const size_t krow = (prec == 1 && Lh <= 32) ? sizeof(float2) * (size_t)Lh * Lh : 0;
+  const size_t b = el2 * (size_t)(2 * Lh - 1) * nt + 2 * cst * BA_CONST_ENTRIES + krow;
   return (b + 15) / 16 * 16;
 }
 
