@@ -1599,6 +1599,7 @@ static int batch_build(slsht_batch* b, const slsht_batch_item* src, int32_t n, c
       r.h = it.h;
       r.prec = d.prec == SLSHT_FP64 ? 0 : 1;
       r.Lh = Lh;
+      r.Nb = d.n_beta;
       r.Ng = d.n_gamma;
       {
         std::lock_guard<std::mutex> g(ctx->mu);
@@ -1610,7 +1611,7 @@ static int batch_build(slsht_batch* b, const slsht_batch_item* src, int32_t n, c
       r.QC = ch.QC; r.CC = ch.CC; r.nq = ch.nq; r.nc = ch.nc;
       b->rot_smem = std::max(b->rot_smem, ch.smem(Lh, el2_of(d.prec)));
       const int ri = (int)b->rot.size();
-      for (int bb = 0; bb < d.n_beta; ++bb)
+      for (int bb = 0; bb < d.n_beta; bb += ROTWIN_NB)
         for (int p = 0; p < Lh; ++p)
           for (int z = 0; z < ch.nq * ch.nc; ++z)
             if ((z / ch.nc) * ch.QC < 2 * p + 1) b->rblk.push_back({ri, bb, p, z});

@@ -129,9 +129,9 @@ struct RotwinBoth {
 // double-float copy scaled by 2^-e, e from the window's largest coefficient
 // (every block finds the same e; block (0, 0) records it in *hexp).
 __device__ __forceinline__ void rotwin_block_fp64(const double2* __restrict__ h, const double* __restrict__ dblk,
-                                                  const double2* __restrict__ eg, int Lh, int Ng, int b, int p,
-                                                  const RotChunks& ch, int z, double2* H, float4* Hdd, int* hexp,
-                                                  unsigned char* smem) {
+                                                  size_t dstride, int nb, const double2* __restrict__ eg, int Lh,
+                                                  int Ng, int b, int p, const RotChunks& ch, int z, double2* H,
+                                                  float4* Hdd, int* hexp, unsigned char* smem) {
   __shared__ double red[4];
   int e = 0;
   if (Hdd != nullptr) {
@@ -143,22 +143,24 @@ __device__ __forceinline__ void rotwin_block_fp64(const double2* __restrict__ h,
     e = scale_exp(block_max(mx, red));
     if (b == 0 && p == 0 && z == 0 && threadIdx.x == 0) *hexp = e;
   }
-  rotwin_block_smem_to<double>(h, dblk, eg, Lh, Ng, b, p, ch, z, RotwinBoth{H, Hdd, e}, smem);
+  rotwin_block_smem_to<double>(h, dblk, dstride, nb, eg, Lh, Ng, b, p, ch, z, RotwinBoth{H, Hdd, e}, smem);
 }
 
 __global__ void __launch_bounds__(128) k_batch_rotwin(const BRot* __restrict__ rot, const BRotBlk* __restrict__ blk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const BRotBlk bb = blk[blockIdx.x];
   const BRot r = rot[bb.rot];
-  const size_t off = (size_t)bb.b * blk_off(r.Lh) + blk_off(bb.p);
+  const size_t S = blk_off(r.Lh);
+  const size_t off = (size_t)bb.b * S + blk_off(bb.p);
+  const int nb = min(ROTWIN_NB, r.Nb - bb.b);
   RotChunks ch;
   ch.QC = r.QC; ch.CC = r.CC; ch.nq = r.nq; ch.nc = r.nc;
   if (r.prec == 0) {
-    rotwin_block_fp64(r.h, (const double*)r.dt + off, (const double2*)r.eg, r.Lh, r.Ng, bb.b, bb.p, ch, bb.z,
+    rotwin_block_fp64(r.h, (const double*)r.dt + off, S, nb, (const double2*)r.eg, r.Lh, r.Ng, bb.b, bb.p, ch, bb.z,
                       (double2*)r.H, r.Hdd, r.hexp, smem_raw);
   } else {
-    rotwin_block_smem_to<float>(r.h, (const float*)r.dt + off, (const float2*)r.eg, r.Lh, r.Ng, bb.b, bb.p, ch,
-                                bb.z, RotwinStore<float>{(float2*)r.H}, smem_raw);
+    rotwin_block_smem_to<float>(r.h, (const float*)r.dt + off, S, nb, (const float2*)r.eg, r.Lh, r.Ng, bb.b, bb.p,
+                                ch, bb.z, RotwinStore<float>{(float2*)r.H}, smem_raw);
   }
 }
 
@@ -173,12 +175,13 @@ cudaError_t launch_batch_rotwin(const BRot* rot, const BRotBlk* blk, int nblk, s
 
 // grid (Nb, Lh, chunks): the scaled double-float window of one call
 __global__ void __launch_bounds__(128) k_rotwin_dd(const double2* __restrict__ h, const double* __restrict__ dt,
-                                                   const double2* __restrict__ eg, int Lh, int Ng, RotChunks ch,
-                                                   float4* Hdd, int* hexp) {
+                                                   const double2* __restrict__ eg, int Lh, int Nb, int Ng,
+                                                   RotChunks ch, float4* Hdd, int* hexp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int b = blockIdx.x, p = blockIdx.y;
-  rotwin_block_fp64(h, dt + (size_t)b * blk_off(Lh) + blk_off(p), eg, Lh, Ng, b, p, ch, blockIdx.z, nullptr, Hdd,
-                    hexp, smem_raw);
+  const int b0 = blockIdx.x * ROTWIN_NB, p = blockIdx.y;
+  const size_t S = blk_off(Lh);
+  rotwin_block_fp64(h, dt + (size_t)b0 * S + blk_off(p), S, min(ROTWIN_NB, Nb - b0), eg, Lh, Ng, b0, p, ch,
+                    blockIdx.z, nullptr, Hdd, hexp, smem_raw);
 }
 
 cudaError_t launch_rotwin_dd(const double2* h, const double* dt, const double2* eg, int Lh, int Nb, int Ng,
@@ -186,8 +189,8 @@ cudaError_t launch_rotwin_dd(const double2* h, const double* dt, const double2* 
   const RotChunks ch = rot_chunks(Lh, Ng, sizeof(double2));
   cudaError_t e = batch_attrs();
   if (e != cudaSuccess) return e;
-  dim3 grid(Nb, Lh, ch.nq * ch.nc);
-  k_rotwin_dd<<<grid, 128, ch.smem(Lh, sizeof(double2)), st>>>(h, dt, eg, Lh, Ng, ch, Hdd, hexp);
+  dim3 grid((Nb + ROTWIN_NB - 1) / ROTWIN_NB, Lh, ch.nq * ch.nc);
+  k_rotwin_dd<<<grid, 128, ch.smem(Lh, sizeof(double2)), st>>>(h, dt, eg, Lh, Nb, Ng, ch, Hdd, hexp);
   return cudaGetLastError();
 }
 

@@ -33,10 +33,10 @@ struct BRot {                    // one rotated window H
   void* H;                       // tiled H (h_index), T2 (null: not needed)
   float4* Hdd;                   // FP64 windows: double-float H scaled by 2^-hexp[0] (null: not needed)
   int* hexp;
-  int prec, Lh, Ng;              // prec 0: FP64, 1: FP32
+  int prec, Lh, Nb, Ng;          // prec 0: FP64, 1: FP32
   int QC, CC, nq, nc;            // shared-memory chunking (rot_chunks)
 };
-struct BRotBlk { int rot, b, p, z; };      // z: chunk of (q rows, gamma columns)
+struct BRotBlk { int rot, b, p, z; };      // beta rows b .. b + ROTWIN_NB - 1; z: chunk of (q rows, gamma columns)
 
 struct BItem {                   // one analysis of the batch (alpha stage view)
   const double2* kc;             // k [pair][Lh^2]

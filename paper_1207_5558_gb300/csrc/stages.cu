@@ -235,16 +235,17 @@ cudaError_t launch_betagamma_f32(const double2* kc, const double2* h, const floa
 // H is the window's coefficients rotated by (0, beta_b, gamma_c) (Eq. rotation_non_symm
 // with Eq. Dlm): it does not depend on the pair (l, m), so it is built once per call and
 // every pair costs only Lh^2 multiply-adds per column.
-// H in the tiled layout of h_index.  One CTA per (beta row b, degree p,
-// chunk): rotwin_block_smem_to (stages_dev.cuh).
+// H in the tiled layout of h_index.  One CTA per (ROTWIN_NB beta rows,
+// degree p, chunk): rotwin_block_smem_to (stages_dev.cuh).
 template <typename T>
 __global__ void __launch_bounds__(128) k_rotwin_smem(const double2* __restrict__ h, const T* __restrict__ dt,
                                                      const typename vec2<T>::t* __restrict__ eg, int Lh, int Nb,
                                                      int Ng, RotChunks ch, typename vec2<T>::t* __restrict__ H) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int b = blockIdx.x, p = blockIdx.y;
-  rotwin_block_smem_to<T>(h, dt + (size_t)b * blk_off(Lh) + blk_off(p), eg, Lh, Ng, b, p, ch, blockIdx.z,
-                          RotwinStore<T>{H}, smem_raw);
+  const int b0 = blockIdx.x * ROTWIN_NB, p = blockIdx.y;
+  const int S = blk_off(Lh);
+  rotwin_block_smem_to<T>(h, dt + (size_t)b0 * S + blk_off(p), (size_t)S, min(ROTWIN_NB, Nb - b0), eg, Lh, Ng, b0,
+                          p, ch, blockIdx.z, RotwinStore<T>{H}, smem_raw);
 }
 
 template <typename T>
@@ -257,7 +258,7 @@ static cudaError_t launch_rotwin_t(const double2* h, const T* dt, const typename
     cudaError_t e = cudaFuncSetAttribute(k_rotwin_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  dim3 grid(Nb, Lh, ch.nq * ch.nc);
+  dim3 grid((Nb + ROTWIN_NB - 1) / ROTWIN_NB, Lh, ch.nq * ch.nc);
   k_rotwin_smem<T><<<grid, 128, smem, st>>>(h, dt, eg, Lh, Nb, Ng, ch, H);
   return cudaGetLastError();
 }
