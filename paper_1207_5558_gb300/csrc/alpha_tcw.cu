@@ -97,114 +97,141 @@ cudaError_t launch_tcw_etab(void* etab, int Na, int Lh, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------- A operand from H
-// X_q(j) = sum_{p>=|q|} k(p,q) H^p_q(j) for one pair and one 128-column tile:
-// A block serves a quarter tile (32 columns); the blocks of one tile for every
-// pair of the launch are adjacent, so each H tile is read from HBM about once.
+// X_q(j) = sum_{p>=|q|} k(p,q) H^p_q(j) for up to XW_PP pairs and one eighth
+// of a 128-column tile: a block serves XW_COLS columns of XW_PP pairs, so every
+// H value it loads feeds the multiply-adds of all its pairs (H is read from L2
+// once per group of XW_PP pairs); the groups of one tile are adjacent blocks,
+// so each H tile is read from HBM about once.
 //   phase 1: one item per (q, column), its degrees p >= |q| (H loads coalesced
 //            across columns, k broadcast through the cache) into the shared
-//            tile sX[slot][column] (unused slots zero);
-//   phase 2: per column, the largest |entry| -> scale 2^e into [2^14, 2^15);
-//   phase 3: per (column, 16-byte chunk): scale, split into FP16 hi/lo, store
-//            swizzled into its K-chunk.  Columns beyond J are zero.
-#define XW_COLS 32                      // columns per producer block (a quarter tile)
+//            tiles sX[pair][slot][column] (unused slots zero);
+//   phase 2: per (pair, column), the largest |entry| -> scale 2^e into
+//            [2^14, 2^15);
+//   phase 3: per (pair, column, 16-byte chunk): scale, split into FP16 hi/lo,
+//            store swizzled into its K-chunk.  Columns beyond J are zero.
+#define XW_COLS 16                      // columns per producer block
 #define XW_PARTS (TC_M / XW_COLS)
+#define XW_PP 4                         // pairs per producer block
+#define XW_THREADS 256
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(XW_THREADS, 3)
 k_xaw_from_h(const float2* __restrict__ H, int Lh, int J, int nk, unsigned char* __restrict__ xblob,
-             size_t blob_stride, int tiles, size_t kf_off) {
+             size_t blob_stride, int tiles, size_t kf_off, int npairs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int half = 32 * nk, centre = 16 * nk - 1, KS = 2 * half;
-  float* sX = reinterpret_cast<float*>(smem_raw);                 // [KS][XW_COLS]
-  int* sEx = reinterpret_cast<int*>(sX + (size_t)KS * XW_COLS);   // [XW_COLS]
-  // pairs vary fastest: the blocks of one H tile run together and share it in L2
-  const int pair = blockIdx.x, tile = blockIdx.y / XW_PARTS, r0 = (blockIdx.y % XW_PARTS) * XW_COLS;
+  float* sX = reinterpret_cast<float*>(smem_raw);                      // [XW_PP][KS][XW_COLS]
+  int* sEx = reinterpret_cast<int*>(sX + (size_t)XW_PP * KS * XW_COLS);   // [XW_PP][XW_COLS]
+  // pair groups vary fastest: the blocks of one H tile run together and share it in L2
+  const int groups = (npairs + XW_PP - 1) / XW_PP;
+  const int pb = (int)(blockIdx.x % groups) * XW_PP, part = (int)(blockIdx.x / groups);
+  const int tile = part / XW_PARTS, r0 = (part % XW_PARTS) * XW_COLS;
+  const int npp = min(XW_PP, npairs - pb);
   const int n2 = Lh * Lh, K = 2 * Lh - 1;
-  const float2* kp = reinterpret_cast<const float2*>(xblob + (size_t)pair * blob_stride + kf_off);
-  for (int t = threadIdx.x; t < KS * XW_COLS; t += blockDim.x) sX[t] = 0.f;
-  __syncthreads();
+  const float2* kp[XW_PP];
+#pragma unroll
+  for (int v = 0; v < XW_PP; ++v)   // a short group repeats its last pair (results not stored)
+    kp[v] = reinterpret_cast<const float2*>(xblob + (size_t)(pb + min(v, npp - 1)) * blob_stride + kf_off);
+  // zero the slots outside |q| < Lh (per half: below centre - (Lh-1) and above centre + (Lh-1))
+  const int lowu = centre - (Lh - 1), nun = half - K;
+  for (int t = threadIdx.x; t < XW_PP * 2 * nun * XW_COLS; t += XW_THREADS) {
+    const int r = t % XW_COLS, u = (t / XW_COLS) % nun, hh = (t / (XW_COLS * nun)) % 2, v = t / (XW_COLS * nun * 2);
+    const int slot = hh * half + (u < lowu ? u : u + K);
+    sX[((size_t)v * KS + slot) * XW_COLS + r] = 0.f;
+  }
   const int jt = tile * TC_M + r0;
-  for (int it = threadIdx.x; it < K * XW_COLS; it += blockDim.x) {
+  for (int it = threadIdx.x; it < K * XW_COLS; it += XW_THREADS) {
     const int u = it / XW_COLS, r = it % XW_COLS;
     const int q = u - (Lh - 1), aq = q < 0 ? -q : q;
     const int j = jt + r;
-    float ar = 0.f, ai = 0.f;
+    float ar[XW_PP], ai[XW_PP];
+#pragma unroll
+    for (int v = 0; v < XW_PP; ++v) ar[v] = ai[v] = 0.f;
     if (j < J) {
       const float2* hp = H + h_index(0, j, n2);      // row pq at hp + pq * 128
       int p = aq;
-      float br = 0.f, bi = 0.f;                     // second chain (odd steps)
-      for (; p + 7 < Lh; p += 8) {                  // eight degrees' loads in flight per step
-        float2 hv[8], kv[8];
+      for (; p + 3 < Lh; p += 4) {                  // four degrees' loads in flight per step
+        float2 hv[4];
 #pragma unroll
-        for (int v = 0; v < 8; ++v) {
-          const int pq = (p + v) * (p + v) + (p + v) + q;
-          hv[v] = __ldg(hp + (size_t)pq * 128);
-          kv[v] = __ldg(kp + pq);
-        }
+        for (int w = 0; w < 4; ++w) hv[w] = __ldg(hp + (size_t)((p + w) * (p + w) + (p + w) + q) * 128);
 #pragma unroll
-        for (int v = 0; v < 8; ++v) {
-          const float kr = kv[v].x, ki = kv[v].y;
-          float& xr = (v & 1) ? br : ar;
-          float& xi = (v & 1) ? bi : ai;
-          xr = fmaf(kr, hv[v].x, xr); xr = fmaf(-ki, hv[v].y, xr);
-          xi = fmaf(kr, hv[v].y, xi); xi = fmaf(ki, hv[v].x, xi);
+        for (int w = 0; w < 4; ++w) {
+          const int pq = (p + w) * (p + w) + (p + w) + q;
+#pragma unroll
+          for (int v = 0; v < XW_PP; ++v) {
+            const float2 kd = __ldg(kp[v] + pq);
+            ar[v] = fmaf(kd.x, hv[w].x, ar[v]); ar[v] = fmaf(-kd.y, hv[w].y, ar[v]);
+            ai[v] = fmaf(kd.x, hv[w].y, ai[v]); ai[v] = fmaf(kd.y, hv[w].x, ai[v]);
+          }
         }
       }
-      ar += br;
-      ai += bi;
       for (; p < Lh; ++p) {
         const int pq = p * p + p + q;
         const float2 hv = __ldg(hp + (size_t)pq * 128);
-        const float2 kd = __ldg(kp + pq);
-        const float kr = kd.x, ki = kd.y;
-        ar = fmaf(kr, hv.x, ar); ar = fmaf(-ki, hv.y, ar);
-        ai = fmaf(kr, hv.y, ai); ai = fmaf(ki, hv.x, ai);
+#pragma unroll
+        for (int v = 0; v < XW_PP; ++v) {
+          const float2 kd = __ldg(kp[v] + pq);
+          ar[v] = fmaf(kd.x, hv.x, ar[v]); ar[v] = fmaf(-kd.y, hv.y, ar[v]);
+          ai[v] = fmaf(kd.x, hv.y, ai[v]); ai[v] = fmaf(kd.y, hv.x, ai[v]);
+        }
       }
     }
-    sX[(size_t)(centre + q) * XW_COLS + r] = ar;
-    sX[(size_t)(half + centre + q) * XW_COLS + r] = ai;
+#pragma unroll
+    for (int v = 0; v < XW_PP; ++v) {
+      sX[((size_t)v * KS + centre + q) * XW_COLS + r] = ar[v];
+      sX[((size_t)v * KS + half + centre + q) * XW_COLS + r] = ai[v];
+    }
   }
   __syncthreads();
-  for (int r = threadIdx.x; r < XW_COLS; r += blockDim.x) {
+  {   // four threads per (pair, column), then a shuffle across the four
+    const int col = threadIdx.x / 4, sub = threadIdx.x % 4;      // col < XW_PP * XW_COLS = 64
+    const float* xs = sX + (size_t)(col / XW_COLS) * KS * XW_COLS + (col % XW_COLS);
     float mx = 0.f;
-    for (int k = 0; k < KS; ++k) mx = fmaxf(mx, fabsf(sX[(size_t)k * XW_COLS + r]));
-    int ex = 0;
-    if (mx > 0.f) frexpf(mx, &ex);
-    sEx[r] = mx > 0.f ? min(125, max(-125, 15 - ex)) : 0;
+    for (int k = sub; k < KS; k += 4) mx = fmaxf(mx, fabsf(xs[(size_t)k * XW_COLS]));
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+    if (sub == 0) {
+      int ex = 0;
+      if (mx > 0.f) frexpf(mx, &ex);
+      sEx[col] = mx > 0.f ? min(125, max(-125, 15 - ex)) : 0;
+    }
   }
   __syncthreads();
-  unsigned char* blob = xblob + (size_t)pair * blob_stride;
-  unsigned char* tb = blob + (size_t)tile * nk * TC_A_BYTES;
-  float* scales = reinterpret_cast<float*>(blob + (size_t)tiles * nk * TC_A_BYTES);
-  for (int it = threadIdx.x; it < XW_COLS * (KS / 8); it += blockDim.x) {
-    const int r = it % XW_COLS, k0 = (it / XW_COLS) * 8;
-    const int e = sEx[r];
+  for (int it = threadIdx.x; it < npp * XW_COLS * (KS / 8); it += XW_THREADS) {
+    const int r = it % XW_COLS, k0 = ((it / XW_COLS) % (KS / 8)) * 8, v = it / (XW_COLS * (KS / 8));
+    const int e = sEx[v * XW_COLS + r];
     const float sc = __int_as_float((127 + e) << 23);
+    const float* xs = sX + (size_t)v * KS * XW_COLS + r;
     __align__(16) __half hi[8], lo[8];
 #pragma unroll
-    for (int v = 0; v < 8; ++v) {
-      const float x = sX[(size_t)(k0 + v) * XW_COLS + r] * sc;
-      hi[v] = __float2half_rn(x);
-      lo[v] = __float2half_rn(x - __half2float(hi[v]));
+    for (int w = 0; w < 8; ++w) {
+      const float x = xs[(size_t)(k0 + w) * XW_COLS] * sc;
+      hi[w] = __float2half_rn(x);
+      lo[w] = __float2half_rn(x - __half2float(hi[w]));
     }
-    unsigned char* cb = tb + (size_t)(k0 / TC_KB) * TC_A_BYTES;
+    unsigned char* blob = xblob + (size_t)(pb + v) * blob_stride;
+    unsigned char* cb = blob + ((size_t)tile * nk + k0 / TC_KB) * TC_A_BYTES;
     *reinterpret_cast<uint4*>(cb + sw128_off(r0 + r, k0 % TC_KB)) = *reinterpret_cast<uint4*>(hi);
     *reinterpret_cast<uint4*>(cb + TC_A_HALF + sw128_off(r0 + r, k0 % TC_KB)) = *reinterpret_cast<uint4*>(lo);
-    if (k0 == 0) scales[jt + r] = jt + r < J ? __int_as_float((127 - e) << 23) : 0.f;
+    if (k0 == 0) {
+      float* scales = reinterpret_cast<float*>(blob + (size_t)tiles * nk * TC_A_BYTES);
+      scales[jt + r] = jt + r < J ? __int_as_float((127 - e) << 23) : 0.f;
+    }
   }
 }
+
+static size_t xaw_smem(int nk) { return sizeof(float) * (size_t)XW_PP * 64 * nk * XW_COLS + sizeof(int) * XW_PP * XW_COLS; }
 
 cudaError_t launch_xaw_from_h(const double2* kc, const float2* H, int Lh, int Nb, int Ng, int npairs, void* xblob,
                               cudaStream_t st) {
   if (npairs <= 0) return cudaSuccess;
   if (Lh <= 16 || Lh > 64) return cudaErrorInvalidValue;
   const int nk = tcw_nk(Lh), tiles = tcw_tiles(Nb, Ng);
-  const size_t smem = sizeof(float) * (size_t)64 * nk * XW_COLS + sizeof(int) * XW_COLS;
-  if (npairs > 65535 || (long long)XW_PARTS * tiles > 65535) return cudaErrorInvalidValue;
+  const long long blocks = (long long)((npairs + XW_PP - 1) / XW_PP) * XW_PARTS * tiles;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
   // the ceiling of the largest case (four K-chunks), set once (never inside a stream capture)
   static bool attr = false;
   if (!attr) {
-    const size_t smax = sizeof(float) * (size_t)64 * 4 * XW_COLS + sizeof(int) * XW_COLS;
-    cudaError_t e = cudaFuncSetAttribute(k_xaw_from_h, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
+    cudaError_t e = cudaFuncSetAttribute(k_xaw_from_h, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xaw_smem(4));
     if (e != cudaSuccess) return e;
     attr = true;
   }
@@ -212,8 +239,8 @@ cudaError_t launch_xaw_from_h(const double2* kc, const float2* H, int Lh, int Nb
   const size_t kf_off = (size_t)tiles * nk * TC_A_BYTES + tcw_scales_bytes(tiles);
   k_kf_from_kc<<<dim3((Lh * Lh + 255) / 256, npairs), 256, 0, st>>>(kc, Lh * Lh, (unsigned char*)xblob, stride,
                                                                    kf_off);
-  dim3 grid(npairs, XW_PARTS * tiles);
-  k_xaw_from_h<<<grid, 256, smem, st>>>(H, Lh, Nb * Ng, nk, (unsigned char*)xblob, stride, tiles, kf_off);
+  k_xaw_from_h<<<(unsigned)blocks, XW_THREADS, xaw_smem(nk), st>>>(H, Lh, Nb * Ng, nk, (unsigned char*)xblob, stride, tiles,
+                                                       kf_off, npairs);
   return cudaGetLastError();
 }
 
