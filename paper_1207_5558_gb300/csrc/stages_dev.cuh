@@ -6,113 +6,128 @@
 // with Eq. Dlm), stored at H[h_index(p*p + p + q, j, Lh*Lh)].
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
-// Shared-memory chunking of a rotated-window block: a block (beta row b,
-// degree p, chunk z) forms the outputs (q, c) with q + p in [q0, q0 + QC) and
-// c in [c0, c0 + CC), staging QC rows of the (2p+1)^2 products h d and CC
-// rows of gamma phases.  Whole blocks (QC = 2Lh-1, CC = Ng, one chunk) when
-// they fit ROTWIN_SMEM_TARGET (four blocks an SM); otherwise CC <= 32 gamma
-// columns and as many q rows as fit beside them.  ROTWIN_SMEM_LIMIT bounds
-// the launches' dynamic shared memory.
+// Shared-memory chunking of a rotated-window block.  With the window folded
+// into the gamma phases,
+//   H^p_q(b, c) = sum_{q'} d^p_{q,q'}(beta_b) B_p(q', c),
+//   B_p(q', c)  = h_p^{q'} e^{-i q' gamma_c},
+// each (degree p) slice is a real-by-complex matrix product whose rows are the
+// (beta row, q) pairs.  A block (beta rows b .. b + ROTWIN_NB - 1, degree p,
+// column chunk z) stages B_p for CC <= 32 gamma columns once, then passes over
+// its ROTWIN_NB (2p+1) rows QC at a time, staging their d rows (transposed)
+// for each pass.  nq = 1 (kept for the batch block lists).
 #define ROTWIN_SMEM_LIMIT (200 * 1024)
-#define ROTWIN_SMEM_TARGET (48 * 1024)
+#define ROTWIN_NB 4          // beta rows a block serves
+#define ROTWIN_CC 32         // gamma columns of a chunk
+#define ROTWIN_THREADS 128   // 16 row groups x 8 column groups
 struct RotChunks {
   int QC, CC, nq, nc;
-  // QC product rows, CC phase rows and the window's degree-p row
-  __host__ __device__ size_t smem(int Lh, size_t el2) const { return el2 * (size_t)(QC + CC + 1) * (2 * Lh - 1); }
-};
-__host__ __device__ inline RotChunks rot_chunks(int Lh, int Ng, size_t el2) {
-  const int K = 2 * Lh - 1;
-  RotChunks r;
-  const long long rows = (long long)ROTWIN_SMEM_TARGET / ((long long)K * (long long)el2) - 1;   // QC + CC that fit
-  if ((long long)K + Ng <= rows) {
-    r.QC = K;
-    r.CC = Ng;
-  } else {
-    r.CC = Ng < 32 ? Ng : 32;
-    if (r.CC > rows - 1) r.CC = (int)(rows > 2 ? rows / 2 : 1);
-    long long qc = rows - r.CC;
-    r.QC = (int)(qc < 1 ? 1 : (qc > K ? K : qc));
+  // d rows of one pass ([2Lh-1][QC] reals) and B ([2Lh-1][CC] complex)
+  __host__ __device__ size_t smem(int Lh, size_t el2) const {
+    return (el2 / 2) * (size_t)QC * (2 * Lh - 1) + el2 * (size_t)CC * (2 * Lh - 1);
   }
-  r.nq = (K + r.QC - 1) / r.QC;
+};
+// Rows a thread holds: four (float, one 16-byte load of d) or two (double).
+__host__ __device__ inline int rot_tq(size_t el2) { return el2 == 8 ? 4 : 2; }
+__host__ __device__ inline RotChunks rot_chunks(int Lh, int Ng, size_t el2) {
+  (void)Lh;
+  RotChunks r;
+  r.QC = 16 * rot_tq(el2);
+  r.CC = ROTWIN_CC;
+  r.nq = 1;
   r.nc = (Ng + r.CC - 1) / r.CC;
   return r;
 }
 
-// Beta rows a rotated-window block serves (the gamma phases and the
-// window's degree-p row are staged once for all of them).
-#define ROTWIN_NB 4
+__device__ __forceinline__ void rot_unpack(const float4 v, float* d) { d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w; }
+__device__ __forceinline__ void rot_unpack(const double2 v, double* d) { d[0] = v.x; d[1] = v.y; }
 
-// One (beta rows b0 .. b0 + nb - 1, degree p, chunk z) block: the gamma
-// phases of its columns and the window's degree-p row are staged in shared
-// memory once; then for each beta row the products h_p^{q'} d^p_{q,q'}(beta_b)
-// of its q rows are staged and each output (q, c) is a (2p+1)-term dot
-// product read from shared memory (2 x 2 output blocks per thread: two
-// product rows and two phase rows per step for four multiply-adds).  dblk0 =
-// the degree-p block of d(beta_b0), consecutive rows dstride apart;
-// eg[c * (2Lh-1) + q' + Lh - 1] = (cos, sin)(q' gamma_c).  All threads of the
-// block take part; a chunk wholly beyond degree p returns at once (the same
-// for the whole block).  store(index, re, im) receives each output with its
-// h_index position.
+// One (beta rows b0 .. b0 + nb - 1, degree p, column chunk z) block of the
+// rotated window (see RotChunks).  dblk0 = the degree-p block of d(beta_b0),
+// consecutive beta rows dstride apart, row-major [q + p][q' + p];
+// eg[c * (2Lh-1) + q' + Lh - 1] = (cos, sin)(q' gamma_c).  The d rows are read
+// through the symmetry d^p_{q,q'} = (-1)^{q-q'} d^p_{q',q}, so that the
+// staging loads run along q (coalesced) and land in [q'][row] order.  A thread
+// holds TQ consecutive rows x 4 columns (c0 + cg + 8 k), 2 multiply-adds a term.
+// All threads of the block take part.  store(index, re, im) receives each
+// output with its h_index position.
 template <typename T, typename Store>
 __device__ __forceinline__ void rotwin_block_smem_to(const double2* __restrict__ h, const T* __restrict__ dblk0,
                                                      size_t dstride, int nb, const typename vec2<T>::t* __restrict__ eg,
                                                      int Lh, int Ng, int b0, int p, const RotChunks& ch, int z,
                                                      Store store, unsigned char* smem) {
   typedef typename vec2<T>::t T2;
+  constexpr int TQ = sizeof(T) == 4 ? 4 : 2;
+  typedef typename std::conditional<sizeof(T) == 4, float4, double2>::type TV;   // TQ values of T
   const int K = 2 * Lh - 1, n2 = Lh * Lh, w = 2 * p + 1;
-  const int q0 = (z / ch.nc) * ch.QC, c0 = (z % ch.nc) * ch.CC;
-  if (q0 >= w) return;
-  const int nqr = min(ch.QC, w - q0), ncr = min(ch.CC, Ng - c0);
-  T2* hd = reinterpret_cast<T2*>(smem);       // [q + p - q0][q' + p]
-  T2* ep = hd + (size_t)nqr * w;              // [c - c0][q' + p]
-  T2* hr = ep + (size_t)ncr * w;              // [q' + p]: h_p^{q'} in T
-  // the window's degree-p row, converted once (a float/double conversion runs
-  // on the FP64 pipe), and the gamma phases of the chunk's columns
-  for (int t = threadIdx.x; t < w; t += blockDim.x) {
-    const double2 hv = __ldg(h + p * p + t);
-    hr[t] = mk2((T)hv.x, (T)hv.y);
+  const int QC = ch.QC, CC = ch.CC;
+  if (QC != 16 * TQ || CC != ROTWIN_CC) return;   // the tiling below assumes rot_chunks' shape
+  const int c0 = z * CC, ncr = min(CC, Ng - c0);
+  T* sd = reinterpret_cast<T*>(smem);                          // [q' + p][row of the pass]
+  T2* sB = reinterpret_cast<T2*>(sd + (size_t)QC * K);         // [q' + p][c - c0]
+  // B_p(q', c) = h_p^{q'} (cos - i sin)(q' gamma_c); zero beyond the chunk
+  for (int t = threadIdx.x; t < w * CC; t += ROTWIN_THREADS) {
+    const int u = t / CC, c = t - u * CC;
+    T2 v = mk2((T)0, (T)0);
+    if (c < ncr) {
+      const double2 hv = __ldg(h + p * p + u);
+      const T2 e = eg[(size_t)(c0 + c) * K + (Lh - 1) - p + u];
+      const T hx = (T)hv.x, hy = (T)hv.y;
+      v = mk2(hx * e.x + hy * e.y, hy * e.x - hx * e.y);
+    }
+    sB[t] = v;
   }
-#pragma unroll 4
-  for (int t = threadIdx.x; t < ncr * w; t += blockDim.x) {
-    const int c = t / w, qp = t - c * w;
-    ep[t] = eg[(size_t)(c0 + c) * K + (Lh - 1) - p + qp];
-  }
-  const int nqh = (nqr + 1) / 2, nch = (ncr + 1) / 2;
-  for (int bi = 0; bi < nb; ++bi) {
-    const int b = b0 + bi;
-    const T* dblk = dblk0 + (size_t)bi * dstride;
-    __syncthreads();                          // hr / ep ready; the previous row's products read
-#pragma unroll 4
-    for (int t = threadIdx.x; t < nqr * w; t += blockDim.x) {
-      const int qp = t % w;
-      const T2 hv = hr[qp];
-      const T d = __ldg(dblk + (size_t)q0 * w + t);
-      hd[t] = mk2(d * hv.x, d * hv.y);
+  const int rows = nb * w;
+  const int rg = threadIdx.x >> 3, cg = threadIdx.x & 7;
+  for (int r0 = 0; r0 < rows; r0 += QC) {
+    __syncthreads();                          // sB ready; the previous pass's d rows read
+    // d rows of the pass, transposed: sd[u][rr] = d^p_{q,u-p}(beta_b) for row
+    // r0 + rr = (b - b0) w + q + p, read as (-1)^{q+u} d[u][q + p]
+    for (int t = threadIdx.x; t < w * QC; t += ROTWIN_THREADS) {
+      const int u = t / QC, rr = t - u * QC, r = r0 + rr;
+      T v = (T)0;
+      if (r < rows) {
+        const int bi = r / w, qi = r - bi * w;
+        v = __ldg(dblk0 + (size_t)bi * dstride + (size_t)u * w + qi);
+        if ((qi ^ u) & 1) v = -v;
+      }
+      sd[t] = v;
     }
     __syncthreads();
-    // each thread: rows qa, qa + nqh and columns ca, ca + nch of the chunk
-    for (int t = threadIdx.x; t < nqh * nch; t += blockDim.x) {
-      const int qa = t / nch, ca = t % nch, qb = qa + nqh, cb = ca + nch;
-      const bool has_q = qb < nqr, has_c = cb < ncr;
-      const T2* ha = hd + qa * w;
-      const T2* hb = hd + (has_q ? qb : qa) * w;
-      const T2* ea = ep + ca * w;
-      const T2* eb = ep + (has_c ? cb : ca) * w;
-      T r00 = 0, i00 = 0, r01 = 0, i01 = 0, r10 = 0, i10 = 0, r11 = 0, i11 = 0;
-      for (int u = 0; u < w; ++u) {              // h d (cos - i sin)
-        const T2 a = ha[u], b2 = hb[u], E = ea[u], F = eb[u];
-        r00 = fma(a.x, E.x, r00); r00 = fma(a.y, E.y, r00); i00 = fma(a.y, E.x, i00); i00 = fma(-a.x, E.y, i00);
-        r01 = fma(a.x, F.x, r01); r01 = fma(a.y, F.y, r01); i01 = fma(a.y, F.x, i01); i01 = fma(-a.x, F.y, i01);
-        r10 = fma(b2.x, E.x, r10); r10 = fma(b2.y, E.y, r10); i10 = fma(b2.y, E.x, i10); i10 = fma(-b2.x, E.y, i10);
-        r11 = fma(b2.x, F.x, r11); r11 = fma(b2.y, F.y, r11); i11 = fma(b2.y, F.x, i11); i11 = fma(-b2.x, F.y, i11);
+    T re[TQ][4], im[TQ][4];
+#pragma unroll
+    for (int a = 0; a < TQ; ++a)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) re[a][k] = im[a][k] = (T)0;
+    const T* dp = sd + rg * TQ;
+    const T2* bp = sB + cg;
+    for (int u = 0; u < w; ++u) {
+      T dq[TQ];
+      rot_unpack(*reinterpret_cast<const TV*>(dp + (size_t)u * QC), dq);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const T2 bv = bp[(size_t)u * CC + 8 * k];
+#pragma unroll
+        for (int a = 0; a < TQ; ++a) {
+          re[a][k] = fma(dq[a], bv.x, re[a][k]);
+          im[a][k] = fma(dq[a], bv.y, im[a][k]);
+        }
       }
-      const int ja = b * Ng + c0 + ca, jb = b * Ng + c0 + cb;
-      store(h_index(p * p + q0 + qa, ja, n2), r00, i00);
-      if (has_c) store(h_index(p * p + q0 + qa, jb, n2), r01, i01);
-      if (has_q) store(h_index(p * p + q0 + qb, ja, n2), r10, i10);
-      if (has_q && has_c) store(h_index(p * p + q0 + qb, jb, n2), r11, i11);
+    }
+#pragma unroll
+    for (int a = 0; a < TQ; ++a) {
+      const int r = r0 + rg * TQ + a;
+      if (r >= rows) continue;
+      const int bi = r / w, qi = r - bi * w;
+      const int jb = (b0 + bi) * Ng + c0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int c = cg + 8 * k;
+        if (c < ncr) store(h_index(p * p + qi, jb + c, n2), re[a][k], im[a][k]);
+      }
     }
   }
 }
