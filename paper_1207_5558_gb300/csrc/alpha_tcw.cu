@@ -30,6 +30,11 @@
 #include "tc.cuh"
 #include "tc_ptx.cuh"
 
+#define XW_COLS 16                      // columns per producer block
+#define XW_PARTS (TC_M / XW_COLS)
+#define XW_PP 4                         // pairs per producer block
+#define XW_THREADS 256
+
 static inline int tcw_nk(int Lh) { return Lh <= 32 ? 2 : 4; }
 static inline int tcw_tiles(int Nb, int Ng) { return (Nb * Ng + TC_M - 1) / TC_M; }
 static inline int tcw_chunks(int Na) { return (Na + TC_NC - 1) / TC_NC; }
@@ -39,24 +44,30 @@ bool tcw_supported(int Lh, int Na) { return Lh > 16 && Lh <= 64 && Na >= 1; }
 size_t tcw_etab_bytes(int Na, int Lh) { return (size_t)tcw_chunks(Na) * tcw_nk(Lh) * TC_B_BYTES; }
 
 // per pair: tiles x NK x 32 KB of A, one float scale per padded column, then
-// the pair's coupling row as floats (the producer's operand)
+// room for the coupling rows of a producer group as floats, interleaved
+// [pq][XW_PP] (the producer's operand; used in the group's first pair)
 static inline size_t tcw_scales_bytes(size_t tiles) { return ((tiles * TC_M * sizeof(float)) + 1023) / 1024 * 1024; }
 size_t tcw_xblob_bytes(int Nb, int Ng, int Lh) {
   const size_t t = (size_t)tcw_tiles(Nb, Ng);
-  const size_t kf = ((size_t)Lh * Lh * sizeof(float2) + 1023) / 1024 * 1024;
+  const size_t kf = ((size_t)Lh * Lh * XW_PP * sizeof(float2) + 1023) / 1024 * 1024;
   return t * (size_t)tcw_nk(Lh) * TC_A_BYTES + tcw_scales_bytes(t) + kf;
 }
 
-// The coupling rows of the launch's pairs as floats, into each pair's blob:
-// one conversion per coefficient (float/double conversions share the slow
-// FP64 pipe on this GPU; the producer then reads floats).
-__global__ void k_kf_from_kc(const double2* __restrict__ kc, int n2, unsigned char* __restrict__ xblob,
+// The coupling rows of the launch's pairs as floats: one conversion per
+// coefficient (float/double conversions share the slow FP64 pipe on this
+// GPU; the producer then reads floats), pair i at [pq][i % XW_PP] of its
+// group's first blob; the slots of a short last group are zero.
+__global__ void k_kf_from_kc(const double2* __restrict__ kc, int n2, int npairs, unsigned char* __restrict__ xblob,
                              size_t blob_stride, size_t kf_off) {
-  const int pair = blockIdx.y;
-  float2* kf = reinterpret_cast<float2*>(xblob + (size_t)pair * blob_stride + kf_off);
+  const int pair = blockIdx.y, g0 = pair - pair % XW_PP;
+  float2* kf = reinterpret_cast<float2*>(xblob + (size_t)g0 * blob_stride + kf_off);
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n2; t += gridDim.x * blockDim.x) {
-    const double2 v = kc[(size_t)pair * n2 + t];
-    kf[t] = make_float2((float)v.x, (float)v.y);
+    float2 o = make_float2(0.f, 0.f);
+    if (pair < npairs) {
+      const double2 v = kc[(size_t)pair * n2 + t];
+      o = make_float2((float)v.x, (float)v.y);
+    }
+    kf[(size_t)t * XW_PP + pair % XW_PP] = o;
   }
 }
 
@@ -109,10 +120,16 @@ cudaError_t launch_tcw_etab(void* etab, int Na, int Lh, cudaStream_t st) {
 //            [2^14, 2^15);
 //   phase 3: per (pair, column, 16-byte chunk): scale, split into FP16 hi/lo,
 //            store swizzled into its K-chunk.  Columns beyond J are zero.
-#define XW_COLS 16                      // columns per producer block
-#define XW_PARTS (TC_M / XW_COLS)
-#define XW_PP 4                         // pairs per producer block
-#define XW_THREADS 256
+
+// x_v += k_v h for the four pairs v of a group, k01 = (k_0, k_1), k23 = (k_2, k_3)
+__device__ __forceinline__ void xw_mac(float* ar, float* ai, float4 k01, float4 k23, float2 h) {
+  const float kr[XW_PP] = {k01.x, k01.z, k23.x, k23.z}, ki[XW_PP] = {k01.y, k01.w, k23.y, k23.w};
+#pragma unroll
+  for (int v = 0; v < XW_PP; ++v) {
+    ar[v] = fmaf(kr[v], h.x, ar[v]); ar[v] = fmaf(-ki[v], h.y, ar[v]);
+    ai[v] = fmaf(kr[v], h.y, ai[v]); ai[v] = fmaf(ki[v], h.x, ai[v]);
+  }
+}
 
 __global__ void __launch_bounds__(XW_THREADS, 3)
 k_xaw_from_h(const float2* __restrict__ H, int Lh, int J, int nk, unsigned char* __restrict__ xblob,
@@ -127,10 +144,8 @@ k_xaw_from_h(const float2* __restrict__ H, int Lh, int J, int nk, unsigned char*
   const int tile = part / XW_PARTS, r0 = (part % XW_PARTS) * XW_COLS;
   const int npp = min(XW_PP, npairs - pb);
   const int n2 = Lh * Lh, K = 2 * Lh - 1;
-  const float2* kp[XW_PP];
-#pragma unroll
-  for (int v = 0; v < XW_PP; ++v)   // a short group repeats its last pair (results not stored)
-    kp[v] = reinterpret_cast<const float2*>(xblob + (size_t)(pb + min(v, npp - 1)) * blob_stride + kf_off);
+  // k(p,q) of the group's pairs: two 16-byte loads per pq
+  const float4* kp = reinterpret_cast<const float4*>(xblob + (size_t)pb * blob_stride + kf_off);
   // zero the slots outside |q| < Lh (per half: below centre - (Lh-1) and above centre + (Lh-1))
   const int lowu = centre - (Lh - 1), nun = half - K;
   for (int t = threadIdx.x; t < XW_PP * 2 * nun * XW_COLS; t += XW_THREADS) {
@@ -156,23 +171,13 @@ k_xaw_from_h(const float2* __restrict__ H, int Lh, int J, int nk, unsigned char*
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
           const int pq = (p + w) * (p + w) + (p + w) + q;
-#pragma unroll
-          for (int v = 0; v < XW_PP; ++v) {
-            const float2 kd = __ldg(kp[v] + pq);
-            ar[v] = fmaf(kd.x, hv[w].x, ar[v]); ar[v] = fmaf(-kd.y, hv[w].y, ar[v]);
-            ai[v] = fmaf(kd.x, hv[w].y, ai[v]); ai[v] = fmaf(kd.y, hv[w].x, ai[v]);
-          }
+          xw_mac(ar, ai, __ldg(kp + 2 * pq), __ldg(kp + 2 * pq + 1), hv[w]);
         }
       }
       for (; p < Lh; ++p) {
         const int pq = p * p + p + q;
         const float2 hv = __ldg(hp + (size_t)pq * 128);
-#pragma unroll
-        for (int v = 0; v < XW_PP; ++v) {
-          const float2 kd = __ldg(kp[v] + pq);
-          ar[v] = fmaf(kd.x, hv.x, ar[v]); ar[v] = fmaf(-kd.y, hv.y, ar[v]);
-          ai[v] = fmaf(kd.x, hv.y, ai[v]); ai[v] = fmaf(kd.y, hv.x, ai[v]);
-        }
+        xw_mac(ar, ai, __ldg(kp + 2 * pq), __ldg(kp + 2 * pq + 1), hv);
       }
     }
 #pragma unroll
@@ -227,6 +232,7 @@ cudaError_t launch_xaw_from_h(const double2* kc, const float2* H, int Lh, int Nb
   if (Lh <= 16 || Lh > 64) return cudaErrorInvalidValue;
   const int nk = tcw_nk(Lh), tiles = tcw_tiles(Nb, Ng);
   const long long blocks = (long long)((npairs + XW_PP - 1) / XW_PP) * XW_PARTS * tiles;
+  static_assert(XW_PP == 4, "xw_mac takes the coupling rows of four pairs");
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
   // the ceiling of the largest case (four K-chunks), set once (never inside a stream capture)
   static bool attr = false;
@@ -237,8 +243,9 @@ cudaError_t launch_xaw_from_h(const double2* kc, const float2* H, int Lh, int Nb
   }
   const size_t stride = tcw_xblob_bytes(Nb, Ng, Lh);
   const size_t kf_off = (size_t)tiles * nk * TC_A_BYTES + tcw_scales_bytes(tiles);
-  k_kf_from_kc<<<dim3((Lh * Lh + 255) / 256, npairs), 256, 0, st>>>(kc, Lh * Lh, (unsigned char*)xblob, stride,
-                                                                   kf_off);
+  const int groups = (npairs + XW_PP - 1) / XW_PP;
+  k_kf_from_kc<<<dim3((Lh * Lh + 255) / 256, groups * XW_PP), 256, 0, st>>>(kc, Lh * Lh, npairs,
+                                                                           (unsigned char*)xblob, stride, kf_off);
   k_xaw_from_h<<<(unsigned)blocks, XW_THREADS, xaw_smem(nk), st>>>(H, Lh, Nb * Ng, nk, (unsigned char*)xblob, stride, tiles,
                                                        kf_off, npairs);
   return cudaGetLastError();

@@ -82,19 +82,32 @@ __device__ __forceinline__ void rotwin_block_smem_to(const double2* __restrict__
   }
   const int rows = nb * w;
   const int rg = threadIdx.x >> 3, cg = threadIdx.x & 7;
-  for (int r0 = 0; r0 < rows; r0 += QC) {
+  // staging: a thread always fills row rr of the pass, every ustep-th u
+  constexpr int QCc = 16 * TQ, ustep = ROTWIN_THREADS / QCc;
+  const int rr = threadIdx.x % QCc, u0 = threadIdx.x / QCc;
+  for (int r0 = 0; r0 < rows; r0 += QCc) {
     __syncthreads();                          // sB ready; the previous pass's d rows read
     // d rows of the pass, transposed: sd[u][rr] = d^p_{q,u-p}(beta_b) for row
-    // r0 + rr = (b - b0) w + q + p, read as (-1)^{q+u} d[u][q + p]
-    for (int t = threadIdx.x; t < w * QC; t += ROTWIN_THREADS) {
-      const int u = t / QC, rr = t - u * QC, r = r0 + rr;
-      T v = (T)0;
-      if (r < rows) {
-        const int bi = r / w, qi = r - bi * w;
-        v = __ldg(dblk0 + (size_t)bi * dstride + (size_t)u * w + qi);
-        if ((qi ^ u) & 1) v = -v;
+    // r0 + rr = (b - b0) w + q + p, read as (-1)^{q+u} d[u][q + p]; eight
+    // loads in flight per thread
+    {
+      const int r = r0 + rr;
+      const bool live = r < rows;
+      const int bi = live ? r / w : 0, qi = live ? r - bi * w : 0;
+      const T* src = dblk0 + (size_t)bi * dstride + qi;
+      for (int ub = u0; ub < w; ub += 8 * ustep) {
+        T v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int u = ub + k * ustep;
+          v[k] = (live && u < w) ? __ldg(src + (size_t)u * w) : (T)0;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int u = ub + k * ustep;
+          if (u < w) sd[(size_t)u * QCc + rr] = ((qi ^ u) & 1) ? -v[k] : v[k];
+        }
       }
-      sd[t] = v;
     }
     __syncthreads();
     T re[TQ][4], im[TQ][4];
@@ -106,7 +119,7 @@ __device__ __forceinline__ void rotwin_block_smem_to(const double2* __restrict__
     const T2* bp = sB + cg;
     for (int u = 0; u < w; ++u) {
       T dq[TQ];
-      rot_unpack(*reinterpret_cast<const TV*>(dp + (size_t)u * QC), dq);
+      rot_unpack(*reinterpret_cast<const TV*>(dp + (size_t)u * QCc), dq);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const T2 bv = bp[(size_t)u * CC + 8 * k];
