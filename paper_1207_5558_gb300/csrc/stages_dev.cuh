@@ -42,6 +42,22 @@ __host__ __device__ inline RotChunks rot_chunks(int Lh, int Ng, size_t el2) {
   return r;
 }
 
+// Asynchronous 4- or 8-byte global -> shared copy (cp.async), and the wait
+// for all of this thread's copies.
+template <typename T>
+__device__ __forceinline__ void cp_async_el(T* dst, const T* src) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "cp.async element");
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 __device__ __forceinline__ void rot_unpack(const float4 v, float* d) { d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w; }
 __device__ __forceinline__ void rot_unpack(const double2 v, double* d) { d[0] = v.x; d[1] = v.y; }
 
@@ -50,8 +66,10 @@ __device__ __forceinline__ void rot_unpack(const double2 v, double* d) { d[0] = 
 // consecutive beta rows dstride apart, row-major [q + p][q' + p];
 // eg[c * (2Lh-1) + q' + Lh - 1] = (cos, sin)(q' gamma_c).  The d rows are read
 // through the symmetry d^p_{q,q'} = (-1)^{q-q'} d^p_{q',q}, so that the
-// staging loads run along q (coalesced) and land in [q'][row] order.  A thread
-// holds TQ consecutive rows x 4 columns (c0 + cg + 8 k), 2 multiply-adds a term.
+// staging copies run along q (coalesced, cp.async: a pass's loads all in
+// flight) and land in [q'][row] order; the sign (-1)^{q'+p} is folded into
+// the staged B rows and (-1)^{q+p} into the outputs.  A thread holds TQ consecutive
+// rows x 4 columns (c0 + cg + 8 k), 2 multiply-adds a term.
 // All threads of the block take part.  store(index, re, im) receives each
 // output with its h_index position.
 template <typename T, typename Store>
@@ -68,14 +86,14 @@ __device__ __forceinline__ void rotwin_block_smem_to(const double2* __restrict__
   const int c0 = z * CC, ncr = min(CC, Ng - c0);
   T* sd = reinterpret_cast<T*>(smem);                          // [q' + p][row of the pass]
   T2* sB = reinterpret_cast<T2*>(sd + (size_t)QC * K);         // [q' + p][c - c0]
-  // B_p(q', c) = h_p^{q'} (cos - i sin)(q' gamma_c); zero beyond the chunk
+  // (-1)^{q'+p} B_p(q', c) = (-1)^{q'+p} h_p^{q'} (cos - i sin)(q' gamma_c); zero beyond the chunk
   for (int t = threadIdx.x; t < w * CC; t += ROTWIN_THREADS) {
     const int u = t / CC, c = t - u * CC;
     T2 v = mk2((T)0, (T)0);
     if (c < ncr) {
       const double2 hv = __ldg(h + p * p + u);
       const T2 e = eg[(size_t)(c0 + c) * K + (Lh - 1) - p + u];
-      const T hx = (T)hv.x, hy = (T)hv.y;
+      const T hx = (u & 1) ? -(T)hv.x : (T)hv.x, hy = (u & 1) ? -(T)hv.y : (T)hv.y;
       v = mk2(hx * e.x + hy * e.y, hy * e.x - hx * e.y);
     }
     sB[t] = v;
@@ -87,27 +105,17 @@ __device__ __forceinline__ void rotwin_block_smem_to(const double2* __restrict__
   const int rr = threadIdx.x % QCc, u0 = threadIdx.x / QCc;
   for (int r0 = 0; r0 < rows; r0 += QCc) {
     __syncthreads();                          // sB ready; the previous pass's d rows read
-    // d rows of the pass, transposed: sd[u][rr] = d^p_{q,u-p}(beta_b) for row
-    // r0 + rr = (b - b0) w + q + p, read as (-1)^{q+u} d[u][q + p]; eight
-    // loads in flight per thread
+    // d rows of the pass, transposed: sd[u][rr] = d[u][q + p] = (-1)^{q+u}
+    // d^p_{q,u-p}(beta_b) for row r0 + rr = (b - b0) w + q + p (rows past the
+    // end are left as they are: they feed only outputs that are not stored)
     {
       const int r = r0 + rr;
-      const bool live = r < rows;
-      const int bi = live ? r / w : 0, qi = live ? r - bi * w : 0;
-      const T* src = dblk0 + (size_t)bi * dstride + qi;
-      for (int ub = u0; ub < w; ub += 8 * ustep) {
-        T v[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int u = ub + k * ustep;
-          v[k] = (live && u < w) ? __ldg(src + (size_t)u * w) : (T)0;
-        }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int u = ub + k * ustep;
-          if (u < w) sd[(size_t)u * QCc + rr] = ((qi ^ u) & 1) ? -v[k] : v[k];
-        }
+      if (r < rows) {
+        const int bi = r / w, qi = r - bi * w;
+        const T* src = dblk0 + (size_t)bi * dstride + qi;
+        for (int u = u0; u < w; u += ustep) cp_async_el(sd + (size_t)u * QCc + rr, src + (size_t)u * w);
       }
+      cp_async_wait_all();
     }
     __syncthreads();
     T re[TQ][4], im[TQ][4];
@@ -136,10 +144,11 @@ __device__ __forceinline__ void rotwin_block_smem_to(const double2* __restrict__
       if (r >= rows) continue;
       const int bi = r / w, qi = r - bi * w;
       const int jb = (b0 + bi) * Ng + c0;
+      const T sg = (qi & 1) ? (T)-1 : (T)1;             // (-1)^{q+p}
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const int c = cg + 8 * k;
-        if (c < ncr) store(h_index(p * p + qi, jb + c, n2), re[a][k], im[a][k]);
+        if (c < ncr) store(h_index(p * p + qi, jb + c, n2), sg * re[a][k], sg * im[a][k]);
       }
     }
   }
