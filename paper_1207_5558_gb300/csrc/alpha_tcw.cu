@@ -119,22 +119,31 @@ cudaError_t launch_tcw_etab(void* etab, int Na, int Lh, cudaStream_t st) {
 // H value it loads feeds the multiply-adds of all its pairs (H is read from L2
 // once per group of XW_PP pairs); the groups of one tile are adjacent blocks,
 // so each H tile is read from HBM about once.
-//   phase 1: one item per (q, column), its degrees p >= |q| (H loads coalesced
-//            across columns, k broadcast through the cache) into the shared
-//            tiles sX[pair][q + Lh - 1][column] (complex);
+//   phase 1: one item per (q, two adjacent columns), its degrees p >= |q| (H
+//            loads coalesced across columns, k broadcast through the cache)
+//            into the shared tiles sX[pair][q + Lh - 1][column] (complex);
 //   phase 2: per (pair, column), the largest |entry| of A_re and A_im (from
 //            P_r and M_r) -> scale 2^e into [2^14, 2^15);
 //   phase 3: per (pair, column, operand, 8 slots): P_r / M_r, scale, split
 //            into FP16 hi/lo, store swizzled into its K-chunk.  Columns
 //            beyond J are zero.
 
-// x_v += k_v h for the four pairs v of a group, k01 = (k_0, k_1), k23 = (k_2, k_3)
-__device__ __forceinline__ void xw_mac(float* ar, float* ai, float4 k01, float4 k23, float2 h) {
+// H values of columns j, j + 1 (the second zero when two is false)
+__device__ __forceinline__ float4 xw_ld2(const float2* p, bool two) {
+  if (two) return __ldg(reinterpret_cast<const float4*>(p));
+  const float2 a = __ldg(p);
+  return make_float4(a.x, a.y, 0.f, 0.f);
+}
+// x_v += k_v h for the four pairs v of a group and two columns: acc[v] =
+// (re, im) of both columns, h = (H of column 0, H of column 1)
+__device__ __forceinline__ void xw_mac2(float4* acc, float4 k01, float4 k23, float4 h) {
   const float kr[XW_PP] = {k01.x, k01.z, k23.x, k23.z}, ki[XW_PP] = {k01.y, k01.w, k23.y, k23.w};
 #pragma unroll
   for (int v = 0; v < XW_PP; ++v) {
-    ar[v] = fmaf(kr[v], h.x, ar[v]); ar[v] = fmaf(-ki[v], h.y, ar[v]);
-    ai[v] = fmaf(kr[v], h.y, ai[v]); ai[v] = fmaf(ki[v], h.x, ai[v]);
+    acc[v].x = fmaf(kr[v], h.x, acc[v].x); acc[v].x = fmaf(-ki[v], h.y, acc[v].x);
+    acc[v].y = fmaf(kr[v], h.y, acc[v].y); acc[v].y = fmaf(ki[v], h.x, acc[v].y);
+    acc[v].z = fmaf(kr[v], h.z, acc[v].z); acc[v].z = fmaf(-ki[v], h.w, acc[v].z);
+    acc[v].w = fmaf(kr[v], h.w, acc[v].w); acc[v].w = fmaf(ki[v], h.z, acc[v].w);
   }
 }
 
@@ -170,34 +179,36 @@ k_xaw_from_h(const float2* __restrict__ H, int Lh, int J, int nkf, unsigned char
   // k(p,q) of the group's pairs: two 16-byte loads per pq
   const float4* kp = reinterpret_cast<const float4*>(xblob + (size_t)pb * blob_stride + kf_off);
   const int jt = tile * TC_M + r0;
-  for (int it = threadIdx.x; it < K * XW_COLS; it += XW_THREADS) {
-    const int u = it / XW_COLS, r = it % XW_COLS;
+  // items (q, column pair): one 16-byte H load serves two adjacent columns
+  for (int it = threadIdx.x; it < K * (XW_COLS / 2); it += XW_THREADS) {
+    const int u = it / (XW_COLS / 2), r = 2 * (it % (XW_COLS / 2));
     const int q = u - (Lh - 1), aq = q < 0 ? -q : q;
     const int j = jt + r;
-    float ar[XW_PP], ai[XW_PP];
+    float4 acc[XW_PP];                              // (re, im) of columns r and r + 1
 #pragma unroll
-    for (int v = 0; v < XW_PP; ++v) ar[v] = ai[v] = 0.f;
+    for (int v = 0; v < XW_PP; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (j < J) {
+      // j is even, so (j, j + 1) share a 128-column tile and a 16-byte H word
       const float2* hp = H + h_index(0, j, n2);      // row pq at hp + pq * 128
+      const bool two = j + 1 < J;
       int p = aq;
       for (; p + 3 < Lh; p += 4) {                  // four degrees' loads in flight per step
-        float2 hv[4];
+        float4 hv[4];
 #pragma unroll
-        for (int w = 0; w < 4; ++w) hv[w] = __ldg(hp + (size_t)((p + w) * (p + w) + (p + w) + q) * 128);
+        for (int w = 0; w < 4; ++w) hv[w] = xw_ld2(hp + (size_t)((p + w) * (p + w) + (p + w) + q) * 128, two);
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
           const int pq = (p + w) * (p + w) + (p + w) + q;
-          xw_mac(ar, ai, __ldg(kp + 2 * pq), __ldg(kp + 2 * pq + 1), hv[w]);
+          xw_mac2(acc, __ldg(kp + 2 * pq), __ldg(kp + 2 * pq + 1), hv[w]);
         }
       }
       for (; p < Lh; ++p) {
         const int pq = p * p + p + q;
-        const float2 hv = __ldg(hp + (size_t)pq * 128);
-        xw_mac(ar, ai, __ldg(kp + 2 * pq), __ldg(kp + 2 * pq + 1), hv);
+        xw_mac2(acc, __ldg(kp + 2 * pq), __ldg(kp + 2 * pq + 1), xw_ld2(hp + (size_t)pq * 128, two));
       }
     }
 #pragma unroll
-    for (int v = 0; v < XW_PP; ++v) sX[((size_t)v * K + u) * XW_COLS + r] = make_float2(ar[v], ai[v]);
+    for (int v = 0; v < XW_PP; ++v) *reinterpret_cast<float4*>(sX + ((size_t)v * K + u) * XW_COLS + r) = acc[v];
   }
   __syncthreads();
   {   // four threads per (pair, column), then a shuffle across the four
@@ -250,7 +261,7 @@ cudaError_t launch_xaw_from_h(const double2* kc, const float2* H, int Lh, int Nb
   if (Lh <= 16 || Lh > 64) return cudaErrorInvalidValue;
   const int nkf = tcw_nk(Lh) / 2, tiles = tcw_tiles(Nb, Ng);
   const long long blocks = (long long)((npairs + XW_PP - 1) / XW_PP) * XW_PARTS * tiles;
-  static_assert(XW_PP == 4, "xw_mac takes the coupling rows of four pairs");
+  static_assert(XW_PP == 4, "xw_mac2 takes the coupling rows of four pairs");
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
   // the ceiling of the largest case (L_h = 64), set once (never inside a stream capture)
   static bool attr = false;

@@ -750,9 +750,8 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
     const size_t target = (size_t)96 << 20;
     P = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_pairs, target / std::max<size_t>(1, x_per_pair)));
     P = std::min(P, 256);
-    // the wide engine's producer shares each H tile in L2 across the pairs of
-    // a chunk: at least four pairs a chunk
-    if (wide) P = std::max(P, std::min<int>(n_pairs, 4));
+    // the wide engine's producer reads H once per chunk: up to 16 pairs a chunk
+    if (wide) P = std::max(P, std::min<int>(n_pairs, 16));
   }
   if (host_out) {
     // staging buffers for the chunk outputs (double-buffered, D2H on the copy stream)
@@ -1185,9 +1184,11 @@ struct BatchItemHost {
   int xw_pairs = 0;
 };
 
-// Pairs a chunk of a wide tensor-core item (the producer shares each H tile
-// in L2 across a chunk's pairs).
-#define XW_CHUNK 4
+// Pairs a chunk of a wide tensor-core item: the producer reads H once per
+// chunk (from HBM once, from L2 once per group of four pairs); the producer
+// and the alpha kernel do not share SMs (the alpha kernel holds a whole SM's
+// shared memory), so a chunk's only cost is the X scratch.
+#define XW_CHUNK 16
 
 #define ENG_NATIVE 0
 #define ENG_DD 1
