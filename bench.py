@@ -717,10 +717,15 @@ def main():
         window from the device generator, 16 seeded pairs, each on the full
         4095 x 2048 x 127 grid, FP32_BULK, 136 GB of g): one call, and one
         batch plan of the same pairs (same buffer), events on the stream.
-        The alpha stage runs on the wide tensor-core engine (K in four
-        chunks of 64)."""
+        The alpha stage runs on the wide tensor-core engine (orders +-q
+        paired: two real GEMMs of K = 128 against one cos|sin operand)."""
         from synth.window import ellipse_from_axes
         c5 = synth.CONFIGS[5]
+        # contexts of their own, one for the call (H, 8.5 GB; X scratch of a
+        # 16-pair chunk, 4.3 GB each) and, after it is closed, one for the
+        # plan; the 136 GB of g leave no room for the earlier legs' cached blocks
+        torch.cuda.empty_cache()
+        ctx = pkg.Context(local, mem_budget_bytes=(96 << 30))
         L5f, L5h, g5 = c5["Lf"], c5["Lh"], c5["grid"]
         h5, _ = ctx.window_ellipse(L5h, *ellipse_from_axes(8.0, 3.0))
         f5, _, p5 = synth.config_inputs(5, window_cache=h5)
@@ -746,6 +751,8 @@ def main():
         ctx.profile(False)
         ms = e0.elapsed_time(e1)
         st = ctx.stats(reset=True)
+        ctx.close()
+        ctx = pkg.Context(local, mem_budget_bytes=(96 << 30))
         items = [{"L_f": L5f, "L_h": L5h, "grid": g5, "prec": 1, "f": f5d, "h": h5d, "lm": p5, "g_out": gb}]
         bp = ctx.batch(items, stream=stream)
         bp.launch(stream)
@@ -763,9 +770,10 @@ def main():
                "plan_engine": ["CUDA cores", "double-float", "tensor cores"][eng],
                "alpha_stage_hbm_frac": smp * 8.0 / (st["ms"]["alpha"] / 1e3) / hbm if st["ms"]["alpha"] else None,
                "per_call_hbm_frac": smp / (ms / 1e3) * 8.0 / hbm,
-               "note": "stage times overlap (two streams); the alpha fraction is the g bytes over the alpha "
-                       "kernels' summed time against the measured copy bandwidth"}
+               "note": "stage times from events around each launch; the alpha fraction is the g bytes over the "
+                       "alpha kernels' summed time against the measured copy bandwidth"}
         bp.close()
+        ctx.close()
         del gb
         torch.cuda.empty_cache()
         return out
