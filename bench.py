@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--profile-prec", type=int, default=1, help="precision of --profile-pairs (1 FP32_BULK, 0 FP64)")
+    ap.add_argument("--profile-fp64-arith", type=int, default=0, choices=(0, 1, 2),
+                    help="SLSHT_OPT_FP64_ARITH of an FP64 --profile-pairs case")
     ap.add_argument("--profile-workload", type=int, default=3, choices=(3, 5),
                     help="workload of --profile-pairs (5: its band limits on 256 beta rows)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -306,12 +308,12 @@ def serve_bench(pkg, device, n, rate, seed=4000, max_outstanding_bytes=48 << 30,
                         "outstanding outputs capped at 48 GB, later arrivals wait (latency from arrival)"}
 
 
-def profile_case(pkg, n, prec=1, wl=3):
+def profile_case(pkg, n, prec=1, wl=3, fp64_arith=0):
     """A small case for kernel captures: one chunk of 48 pairs per launch, a
     few GB on the device, two forward passes, then two inverses of the result
     (prec 1: FP32_BULK, 0: FP64).  wl 3: the last n pairs of workload 3; wl 5:
     the first n pairs of workload 5 (its band limits, window and N_alpha,
-    N_gamma) on 256 of its beta rows."""
+    N_gamma) on 256 of its beta rows.  fp64_arith: SLSHT_OPT_FP64_ARITH."""
     import numpy as np
     import torch
     import synth
@@ -328,8 +330,9 @@ def profile_case(pkg, n, prec=1, wl=3):
         f, h, pairs = synth.config_inputs(3, 0)
         sub = np.ascontiguousarray(pairs[-n:])
     ctx.set_option(pkg.SLSHT_OPT_CHUNK_PAIRS, 48)
+    ctx.set_option(pkg.SLSHT_OPT_FP64_ARITH, fp64_arith)
     g = torch.empty((n,) + c["grid"], dtype=torch.complex64 if prec == 1 else torch.complex128, device="cuda")
-    if prec == 0:
+    if prec == 0 and fp64_arith == 0:
         ctx.tune(c["Lf"], c["Lh"], c["grid"], 0)
     for _ in range(2):
         pkg.slsht_forward(ctx.h, pkg.make_desc(c["Lf"], c["Lh"], c["grid"], prec), f, h, sub, n, g)
@@ -413,7 +416,7 @@ def main():
 
     torch.cuda.set_device(local)
     if args.profile_pairs > 0:
-        profile_case(pkg, args.profile_pairs, args.profile_prec, args.profile_workload)
+        profile_case(pkg, args.profile_pairs, args.profile_prec, args.profile_workload, args.profile_fp64_arith)
         return
     dist = None
     if world > 1:

@@ -74,7 +74,8 @@ typedef struct slsht_ctx slsht_ctx;   /* opaque; one device, owns tables */
 typedef enum {
   SLSHT_FP64 = 0,       /* FP64 accuracy (relative error <= 1e-12): 3j,
                            Delta, coupling and rotated window in FP64, X and
-                           the alpha sum in FP64 or double-float arithmetic
+                           the alpha sum in FP64, double-float or exact
+                           digit-product tensor-core arithmetic
                            (SLSHT_OPT_FP64_ARITH); g is complex128           */
   SLSHT_FP32_BULK = 1   /* 3j, Delta, phases in FP64; coupling in FP64;
                            beta/gamma sums in FP32; alpha stage on tcgen05
@@ -428,7 +429,14 @@ int slsht_get_stats(slsht_ctx* ctx, slsht_stats* out, int reset);
  *                            on the FP32 pipe, about 48 significant bits;
  *                            tables, 3j, coupling and the rotated window in
  *                            FP64; relative error about 1e-14); 1: FP64
- *                            arithmetic throughout.
+ *                            arithmetic throughout; 2 (L_h <= 16): X in
+ *                            double-float, the alpha sum on the tensor
+ *                            cores from base-256 digits of X and of the
+ *                            cos/sin tables (7 digits each, 28 digit
+ *                            products whose FP32 sums are exact), combined
+ *                            by TwoSum into a double-float and assembled as
+ *                            a double (relative error about 1e-14); other
+ *                            window bands fall back to 0.
  * Returns SLSHT_OK or SLSHT_E_ARG. */
 #define SLSHT_OPT_BETA_ROUTE   1
 #define SLSHT_OPT_ALPHA_ENGINE 2

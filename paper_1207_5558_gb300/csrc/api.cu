@@ -479,6 +479,25 @@ static int get_etab(slsht_ctx* ctx, int Na, int Lh, cudaStream_t st, const void*
   return SLSHT_OK;
 }
 
+// The base-256 digit tables of the FP64 tensor-core alpha stage (all |q| <= 15),
+// cached per N_alpha beside the FP32 E tables (key (Na, -1)).
+static int get_etab64(slsht_ctx* ctx, int Na, cudaStream_t st, const void** out) {
+  auto key = std::make_tuple(Na, -1);
+  auto it = ctx->etab.find(key);
+  if (it == ctx->etab.end()) {
+    TableEntry e;
+    CKS(make_entry(ctx, e, tc64_etab_bytes(Na)));
+    ctx->launches[SLSHT_STAGE_TABLES]++;
+    cudaError_t er = launch_tc64_etab(e.ptr, Na, st);
+    if (er != cudaSuccess) { record_cuda_error("launch_tc64_etab", er); return SLSHT_E_CUDA; }
+    CK(cudaEventRecord(e.ready, st));
+    it = ctx->etab.emplace(key, e).first;
+  }
+  CK(cudaStreamWaitEvent(st, it->second.ready, 0));
+  *out = it->second.ptr;
+  return SLSHT_OK;
+}
+
 // ---------------------------------------------------------------- create/destroy
 extern "C" int slsht_create(slsht_ctx** out, int device, size_t budget) {
   if (!out) return SLSHT_E_ARG;
@@ -573,7 +592,7 @@ extern "C" int slsht_set_option(slsht_ctx* c, int option, int64_t v) {
       c->opt_coupling = (int)v;
       return SLSHT_OK;
     case SLSHT_OPT_FP64_ARITH:
-      if (v < 0 || v > 1) return SLSHT_E_ARG;
+      if (v < 0 || v > 2) return SLSHT_E_ARG;
       c->opt_fp64_arith = (int)v;
       return SLSHT_OK;
     default:
@@ -697,7 +716,11 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
   // arithmetic (one kernel over (pair, column block) tiles, no X scratch)
   // unless SLSHT_OPT_FP64_ARITH asks for FP64 arithmetic or the tuner found
   // FP64 arithmetic faster for this shape
-  const bool ddx = f64 && route == 1 && fp64_arith == 0 && tuned_engine != 0;
+  // FP64 on the tensor cores (SLSHT_OPT_FP64_ARITH = 2, L_h <= 16): X in
+  // double-float, the alpha sum from exact base-256 digit products (producer
+  // + alpha kernel per chunk of pairs); wider windows take double-float
+  const bool t64 = f64 && route == 1 && fp64_arith == 2 && tc64_supported(Lh, Na);
+  const bool ddx = f64 && route == 1 && !t64 && fp64_arith != 1 && tuned_engine != 0;
   if (ddx) {
     if (dd_form < 0 || (engine == 4 && dd_form != 0)) {
       dd_nt = dd_rule_cols(Lh, (long long)J);
@@ -706,7 +729,7 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
   }
   // other CUDA-core calls on the rotated-window route: the same tile kernel
   // in the call's own precision (X in shared memory, no X scratch)
-  const bool cc1 = !tc && route == 1 && !ddx;
+  const bool cc1 = !tc && route == 1 && !ddx && !t64;
   if (cc1) {
     if (cc_form < 0 || (engine == 4 && cc_form != 0)) {
       cc_nt = batch_rule_nt(f64 ? 0 : 1, Lh, (long long)J);
@@ -725,6 +748,7 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
     if (route == 1) CKS(get_dtab(ctx, Lh, Nb, d->prec, st, &dt));
     CKS(get_phase(ctx, Ng, K, -(Lh - 1), d->prec, st, &eg));
     if (tc) CKS(get_etab(ctx, Na, Lh, st, &etab));
+    else if (t64) CKS(get_etab64(ctx, Na, st, &etab));
     else if (ddx && dd_form > 0) CKS(get_phase(ctx, Na, K, -(Lh - 1), PREC_DD, st, &csa));
     else if (ddx) CKS(get_phase(ctx, Na, Lh, 0, PREC_DD, st, &csa));
     else if (cc1 && cc_form > 0) CKS(get_phase(ctx, Na, K, -(Lh - 1), d->prec, st, &csa));
@@ -739,8 +763,10 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
   CKS(stage_input(ctx, w, &w.lm, &w.lm_cap, lm, sizeof(int2) * (size_t)n_pairs, st, &lm_dev));
 
   // chunking: X scratch of the chunk kept near L2 size
-  const size_t x_per_pair = wide ? tcw_xblob_bytes(Nb, Ng, Lh)
-                            : tc ? tc_xblob_bytes(Nb, Ng, Lh) : (size_t)K * J * (f64 ? sizeof(double2) : sizeof(float2));
+  const size_t x_per_pair = wide  ? tcw_xblob_bytes(Nb, Ng, Lh)
+                            : tc  ? tc_xblob_bytes(Nb, Ng, Lh)
+                            : t64 ? tc64_xblob_bytes(Nb, Ng)
+                                  : (size_t)K * J * (f64 ? sizeof(double2) : sizeof(float2));
   int P;
   if (chunk_opt > 0) {
     P = (int)std::min<int64_t>(chunk_opt, n_pairs);
@@ -764,7 +790,7 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
     CKS(ws_reserve(ctx, w, &w.X2, &w.X2_cap, x_per_pair * (size_t)P));
   }
   const size_t el2 = f64 ? sizeof(double2) : sizeof(float2);
-  if (ddx) {
+  if (ddx || t64) {
     CKS(ws_reserve(ctx, w, &w.kdd, &w.kdd_cap, sizeof(float4) * (size_t)n_pairs * Lh * Lh));
     CKS(ws_reserve(ctx, w, &w.kexp, &w.kexp_cap, sizeof(int) * (size_t)n_pairs));
     CKS(ws_reserve(ctx, w, &w.Hdd, &w.Hdd_cap, sizeof(float4) * h_elems(J, Lh * Lh)));
@@ -826,7 +852,7 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
            launch_couple((const double2*)f_dev, Lf, Lh, (const int2*)lm_dev, n_pairs, (double2*)w.kc, ax));
   }
   // route 1: the window rotated to every (beta, gamma) sample, once per call
-  if (ddx) {
+  if (ddx || t64) {
     LAUNCH(SLSHT_STAGE_COUPLE, ax,
            launch_kdd_pairs((const double2*)w.kc, Lh, n_pairs, (float4*)w.kdd, (int*)w.kexp, ax));
     LAUNCH(SLSHT_STAGE_BETA, ax,
@@ -865,7 +891,11 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
       const double2* Ysrc = route == 2 ? (const double2*)w.Y : nullptr;
       if (route == 1) {
         // (route 1 on CUDA cores forms X inside the alpha tile kernel)
-        if (wide)
+        if (t64)
+          LAUNCH(SLSHT_STAGE_BETA, ax,
+                 launch_xa64((const float4*)w.kdd + (size_t)off * Lh * Lh, (const int*)w.kexp + off,
+                             (const float4*)w.Hdd, (const int*)w.hexp, Lh, Nb, Ng, np, X, ax));
+        else if (wide)
           LAUNCH(SLSHT_STAGE_BETA, ax, launch_xaw_from_h(kcc, (const float2*)w.H, Lh, Nb, Ng, np, X, ax));
         else
           LAUNCH(SLSHT_STAGE_BETA, ax, launch_xa_from_h(kcc, (const float2*)w.H, Lh, Nb, Ng, np, X, ax));
@@ -937,6 +967,9 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
     } else if (tc) {
       LAUNCH(SLSHT_STAGE_ALPHA, st,
              launch_alpha_tc(X, etab, Lh, Na, Nb, Ng, np, (float2*)gdst, ctx->num_sms, sl, st));
+    } else if (t64) {
+      LAUNCH(SLSHT_STAGE_ALPHA, st,
+             launch_alpha_tc64(X, etab, Lh, Na, Nb, Ng, np, (double2*)gdst, ctx->num_sms, sl, st));
     } else if (f64) {
       LAUNCH(SLSHT_STAGE_ALPHA, st,
              split ? launch_alpha_split_f64((const double2*)X, (const double2*)csa, Lh, Na, (int)J, np,

@@ -74,7 +74,7 @@ __device__ __forceinline__ void dd_acc_get(const dd_acc& a, float* h, float* l) 
 // 2^-74 and results outside the double's normal range take the FP64 route.
 // The rare cases of dd_to_double in FP64 arithmetic, kept out of line so
 // the compiler does not evaluate them speculatively beside the common path.
-__device__ __noinline__ double dd_to_double_slow(float h, float l, int sc) {
+static __device__ __noinline__ double dd_to_double_slow(float h, float l, int sc) {
   return ldexp((double)h + (double)l, sc);
 }
 

@@ -45,6 +45,19 @@ cudaError_t launch_xaw_from_h(const double2* kc, const float2* H, int Lh, int Nb
                               cudaStream_t st);
 cudaError_t launch_alpha_tcw(const void* xblob, const void* etab, int Lh, int Na, int Nb, int Ng, int npairs,
                              float2* g, int num_sms, const int2* slots, cudaStream_t st);
+// FP64 alpha stage on the tensor cores, Lh <= 16 (alpha_tc64.cu): base-256
+// digit products, exact in FP32, into seven accumulators per output.
+bool tc64_supported(int Lh, int Na);
+size_t tc64_etab_bytes(int Na);
+cudaError_t launch_tc64_etab(void* etab, int Na, cudaStream_t st);
+size_t tc64_xblob_bytes(int Nb, int Ng);
+// A digits from the double-float window Hdd (tiled layout of h_index, scaled
+// by 2^-*hexp) and couplings kdd (per pair, scaled by 2^-kexp[pair])
+cudaError_t launch_xa64(const float4* kdd, const int* kexp, const float4* Hdd, const int* hexp, int Lh, int Nb,
+                        int Ng, int npairs, void* xblob, cudaStream_t st);
+// g[pair][a][j] complex128; slots as launch_alpha_tc
+cudaError_t launch_alpha_tc64(const void* xblob, const void* etab, int Lh, int Na, int Nb, int Ng, int npairs,
+                              double2* g, int num_sms, const int2* slots, cudaStream_t st);
 // Device error word shared by the tensor-core kernels (allocated on first use).
 int* tc_error_word();
 // Non-zero (and cleared) if a tensor-core kernel gave up on a bounded wait
