@@ -818,17 +818,23 @@ def main():
         t0 = time.perf_counter()
         ctx.tune(Lf, Lh, grid, 0)
         tune_s = time.perf_counter() - t0
-        # default FP64 path: X and alpha in double-float arithmetic
+        # default FP64 path: X in double-float, the alpha sum on the tensor
+        # cores from exact base-256 digit products
         ms64, st64, clk64 = timed(0, g64, args.fp64_steps, 1, ClockSampler(local))
         value64 = samples_step * args.fp64_steps * world / (ms64 / 1e3)
-        a64 = g64[sel]
+        a64 = g64[sel].clone()
         rel32 = float(torch.linalg.vector_norm(a32 - a64) / torch.linalg.vector_norm(a64))
         inv64 = inverse_leg(0, g64, 2)
         fp64_alpha_ms = st64["ms"]["alpha"]
+        hbm = peaks()[0]["hbm_gbs"] * 1e9
+        # the double-float engine on CUDA cores (SLSHT_OPT_FP64_ARITH = 3)
+        ctx.set_option(pkg.SLSHT_OPT_FP64_ARITH, 3)
+        msd, std_, clkd = timed(0, g64, args.fp64_steps, 1, ClockSampler(local))
+        rel_tc_dd = float(torch.linalg.vector_norm(a64 - g64[sel]) / torch.linalg.vector_norm(g64[sel]))
         Pdd = alpha_split_factor_py(Lh, grid[0])
         ops, form_dd = alpha_dd_ops(Lh, grid[0], Pdd)
-        alpha_rate = samples_step * args.fp64_steps / (fp64_alpha_ms / 1e3)
-        sm_mhz = (clk64 or {}).get("sm_mhz") or 2070.0
+        alpha_rate = samples_step * args.fp64_steps / (std_["ms"]["alpha"] / 1e3)
+        sm_mhz = (clkd or {}).get("sm_mhz") or 2070.0
         issue_peak = 128.0 * torch.cuda.get_device_properties(local).multi_processor_count * sm_mhz * 1e6
         # FP64 arithmetic throughout (SLSHT_OPT_FP64_ARITH = 1), one step
         ctx.set_option(pkg.SLSHT_OPT_FP64_ARITH, 1)
@@ -840,17 +846,26 @@ def main():
         fp64 = {"value": value64, "unit": UNIT, "steps": args.fp64_steps,
                 "ms_per_step": ms64 / args.fp64_steps,
                 "stage_ms_per_step": {k: v / args.fp64_steps for k, v in st64["ms"].items()},
-                "arithmetic": "3j, Delta, coupling, rotated window in FP64; X and the alpha sum in double-float "
-                              "(float pairs, exact TwoProd/TwoSum on the FP32 pipe, ~2^-48), g assembled as "
-                              "complex128",
-                "alpha_form": form_dd,
-                "tune_s": tune_s,
-                "alpha_issue_slots_per_sample": ops,
-                "alpha_issue_frac": alpha_rate * ops / issue_peak,
-                "alpha_issue_note": "modelled FP32/INT instructions a sample (bench.alpha_dd_ops) times the "
-                                    "alpha kernel's sample rate over 128 lanes x SMs x the sampled SM clock",
+                "arithmetic": "3j, Delta, coupling, rotated window in FP64; X in double-float (float pairs, "
+                              "exact TwoProd/TwoSum, ~2^-48); the alpha sum on the tensor cores from base-256 "
+                              "digits of X and of the cos/sin tables (28 digit products, exact FP32 sums per "
+                              "weight), combined by TwoSum, g assembled as complex128",
+                "engine": "tensor cores (exact digit products)",
+                "alpha_g_bytes_frac_of_copy": samples_step * args.fp64_steps * 16.0 / (fp64_alpha_ms / 1e3) / hbm
+                if fp64_alpha_ms else None,
+                "alpha_note": "complex128 bytes of g over the alpha kernels' summed time (producer separate) "
+                              "against the measured copy bandwidth",
                 "clocks": clk64,
                 "rel_l2_vs_fp64_arithmetic_sampled": rel_dd,
+                "double_float": {
+                    "value": samples_step * args.fp64_steps * world / (msd / 1e3),
+                    "ms_per_step": msd / args.fp64_steps, "alpha_form": form_dd, "tune_s": tune_s,
+                    "rel_l2_vs_tensor_cores_sampled": rel_tc_dd,
+                    "alpha_issue_slots_per_sample": ops,
+                    "alpha_issue_frac": alpha_rate * ops / issue_peak,
+                    "alpha_issue_note": "SLSHT_OPT_FP64_ARITH = 3: modelled FP32/INT instructions a sample "
+                                        "(bench.alpha_dd_ops) times the alpha kernel's sample rate over 128 lanes "
+                                        "x SMs x the sampled SM clock"},
                 "fp64_arithmetic": {
                     "value": samples_step / (msn / 1e3) * world, "ms_per_step": msn,
                     "alpha_form": form, "alpha_fp64_instructions_per_sample": instr,

@@ -423,20 +423,21 @@ int slsht_get_stats(slsht_ctx* ctx, slsht_stats* out, int reset);
  *                            window band is wide and the signal band narrow;
  *                            rounding limits it to ~1e-11 relative near
  *                            l = 255.
- *  SLSHT_OPT_FP64_ARITH   FP64 calls on the rotated-window route: 0 (default)
- *                            X and the alpha sum in double-float arithmetic
- *                            (pairs of floats from exact TwoProd/TwoSum steps
- *                            on the FP32 pipe, about 48 significant bits;
- *                            tables, 3j, coupling and the rotated window in
- *                            FP64; relative error about 1e-14); 1: FP64
- *                            arithmetic throughout; 2 (L_h <= 16): X in
- *                            double-float, the alpha sum on the tensor
- *                            cores from base-256 digits of X and of the
- *                            cos/sin tables (7 digits each, 28 digit
- *                            products whose FP32 sums are exact), combined
- *                            by TwoSum into a double-float and assembled as
- *                            a double (relative error about 1e-14); other
- *                            window bands fall back to 0.
+ *  SLSHT_OPT_FP64_ARITH   FP64 calls on the rotated-window route (tables,
+ *                            3j, coupling and the rotated window in FP64
+ *                            throughout): 0 (default) = 2 where it applies,
+ *                            else 3; 1: X and the alpha sum in FP64
+ *                            arithmetic; 2 (L_h <= 16, alpha engine not held
+ *                            to CUDA cores): X in double-float, the alpha
+ *                            sum on the tensor cores from base-256 digits of
+ *                            X and of the cos/sin tables (7 digits each, 28
+ *                            digit products whose FP32 sums are exact),
+ *                            combined by TwoSum into a double-float and
+ *                            assembled as a double; 3: X and the alpha sum
+ *                            in double-float arithmetic on CUDA cores (pairs
+ *                            of floats from exact TwoProd/TwoSum steps, about
+ *                            48 significant bits).  Relative error about
+ *                            1e-14 for 0, 2 and 3.
  * Returns SLSHT_OK or SLSHT_E_ARG. */
 #define SLSHT_OPT_BETA_ROUTE   1
 #define SLSHT_OPT_ALPHA_ENGINE 2

@@ -211,6 +211,7 @@ cudaError_t launch_xa64(const float4* kdd, const int* kexp, const float4* Hdd, c
                         int Ng, int npairs, void* xblob, cudaStream_t st) {
   if (npairs <= 0) return cudaSuccess;
   if (Lh < 1 || Lh > 16 || npairs > 65535) return cudaErrorInvalidValue;
+  if (!kdd || !kexp || !Hdd || !hexp || !xblob) return cudaErrorInvalidValue;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_xa64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xa64_smem());
@@ -456,6 +457,7 @@ cudaError_t launch_alpha_tc64(const void* xblob, const void* etab, int Lh, int N
                               double2* g, int num_sms, const int2* slots, cudaStream_t st) {
   if (npairs <= 0) return cudaSuccess;
   if (!tc64_supported(Lh, Na)) return cudaErrorInvalidValue;
+  if (!xblob || !etab || !g) return cudaErrorInvalidValue;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_alpha_tc64, cudaFuncAttributeMaxDynamicSharedMemorySize, T64_SMEM);

@@ -592,7 +592,7 @@ extern "C" int slsht_set_option(slsht_ctx* c, int option, int64_t v) {
       c->opt_coupling = (int)v;
       return SLSHT_OK;
     case SLSHT_OPT_FP64_ARITH:
-      if (v < 0 || v > 2) return SLSHT_E_ARG;
+      if (v < 0 || v > 3) return SLSHT_E_ARG;
       c->opt_fp64_arith = (int)v;
       return SLSHT_OK;
     default:
@@ -716,11 +716,14 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
   // arithmetic (one kernel over (pair, column block) tiles, no X scratch)
   // unless SLSHT_OPT_FP64_ARITH asks for FP64 arithmetic or the tuner found
   // FP64 arithmetic faster for this shape
-  // FP64 on the tensor cores (SLSHT_OPT_FP64_ARITH = 2, L_h <= 16): X in
+  // FP64 on the tensor cores (the default, and SLSHT_OPT_FP64_ARITH = 2, for
+  // L_h <= 16 unless the alpha engine is held to CUDA cores): X in
   // double-float, the alpha sum from exact base-256 digit products (producer
-  // + alpha kernel per chunk of pairs); wider windows take double-float
-  const bool t64 = f64 && route == 1 && fp64_arith == 2 && tc64_supported(Lh, Na);
-  const bool ddx = f64 && route == 1 && !t64 && fp64_arith != 1 && tuned_engine != 0;
+  // + alpha kernel per chunk of pairs).  Elsewhere double-float (= 3, or the
+  // default where the tuner did not find FP64 arithmetic faster).
+  const bool t64 = f64 && route == 1 && (fp64_arith == 0 || fp64_arith == 2) && tc64_supported(Lh, Na) &&
+                   engine != 1 && engine != 4;
+  const bool ddx = f64 && route == 1 && !t64 && (fp64_arith == 3 || (fp64_arith != 1 && tuned_engine != 0));
   if (ddx) {
     if (dd_form < 0 || (engine == 4 && dd_form != 0)) {
       dd_nt = dd_rule_cols(Lh, (long long)J);
@@ -1313,15 +1316,33 @@ static int batch_rule_nt(int kp, int Lh, long long J) {
 }
 
 static bool batch_tc_ok(const slsht_batch* b, const slsht_desc& d) {
-  return !(b->flags & SLSHT_BATCH_NO_TC) && d.prec == SLSHT_FP32_BULK &&
-         ((tc_supported(d.L_h, d.n_alpha) && d.L_h <= 16) || tcw_supported(d.L_h, d.n_alpha));
+  if (b->flags & SLSHT_BATCH_NO_TC) return false;
+  if (d.prec == SLSHT_FP64)   // exact digit products from the double-float X (needs its k and H)
+    return tc64_supported(d.L_h, d.n_alpha) && !(b->flags & (SLSHT_BATCH_NO_DD | SLSHT_BATCH_FP64_DD));
+  return (tc_supported(d.L_h, d.n_alpha) && d.L_h <= 16) || tcw_supported(d.L_h, d.n_alpha);
 }
 
 // The tensor-core launches of one item, chunk by chunk: the fused kernel
-// (L_h <= 16), or the wide engine's producer and alpha kernels.
+// (L_h <= 16), or the wide engine's producer and alpha kernels; FP64 items:
+// the digit producer and the FP64 alpha kernel.
 static cudaError_t batch_tc_launch(const slsht_batch* b, const BatchItemHost& it, int npairs, int nb, void* xw,
                                    int xw_pairs, void* g, cudaStream_t st) {
   const slsht_desc& d = it.d;
+  if (d.prec == SLSHT_FP64) {
+    const BCouple& c = b->cpl[it.cpl];
+    const BRot& r = b->rot[it.rot];
+    if (c.kdd == nullptr || c.kexp == nullptr || r.Hdd == nullptr || r.hexp == nullptr) return cudaErrorInvalidValue;
+    const size_t n2 = (size_t)d.L_h * d.L_h, per_pair = (size_t)d.n_alpha * nb * d.n_gamma;
+    for (int off = 0; off < npairs; off += xw_pairs) {
+      const int np = std::min(xw_pairs, npairs - off);
+      cudaError_t e = launch_xa64(c.kdd + off * n2, c.kexp + off, r.Hdd, r.hexp, d.L_h, nb, d.n_gamma, np, xw, st);
+      if (e == cudaSuccess)
+        e = launch_alpha_tc64(xw, it.etab, d.L_h, d.n_alpha, nb, d.n_gamma, np, (double2*)g + off * per_pair,
+                              b->ctx->num_sms, nullptr, st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
   const double2* kc = b->cpl[it.cpl].kc;
   const float2* H = (const float2*)b->rot[it.rot].H;
   if (d.L_h <= 16)
@@ -1496,7 +1517,10 @@ static int batch_tune(slsht_batch* b, int ii) {
   const size_t out_bytes = (size_t)np * reps * Na * Js * el2_of(d.prec);
   const size_t max_tiles = (size_t)np * reps * ((Js + 31) / 32);
   void *scratch = nullptr, *d_item = nullptr, *d_tiles = nullptr, *d_ctr = nullptr, *xw = nullptr;
-  const size_t xw_bytes = (tc_ok && Lh > 16) ? tcw_xblob_bytes(nbs, d.n_gamma, Lh) * XW_CHUNK : 0;
+  const size_t xw_bytes = !tc_ok                    ? 0
+                          : d.prec == SLSHT_FP64    ? tc64_xblob_bytes(nbs, d.n_gamma) * XW_CHUNK
+                          : Lh > 16                 ? tcw_xblob_bytes(nbs, d.n_gamma, Lh) * XW_CHUNK
+                                                    : 0;
   int st = ctx_alloc(ctx, out_bytes, &scratch);
   if (st == SLSHT_OK && xw_bytes) st = ctx_alloc(ctx, xw_bytes, &xw);
   if (st == SLSHT_OK) st = ctx_alloc(ctx, sizeof(BItem), &d_item);
@@ -1674,7 +1698,10 @@ static int batch_build(slsht_batch* b, const slsht_batch_item* src, int32_t n, c
     }
     if (batch_tc_ok(b, d)) {
       std::lock_guard<std::mutex> g(ctx->mu);
-      CKS(get_etab(ctx, d.n_alpha, Lh, b->cs, &it.etab));
+      if (d.prec == SLSHT_FP64)
+        CKS(get_etab64(ctx, d.n_alpha, b->cs, &it.etab));
+      else
+        CKS(get_etab(ctx, d.n_alpha, Lh, b->cs, &it.etab));
     }
     BItem bi{};
     bi.kc = b->cpl[it.cpl].kc;
@@ -1719,8 +1746,14 @@ static int batch_build(slsht_batch* b, const slsht_batch_item* src, int32_t n, c
   {
     std::vector<char> rot_native(b->rot.size(), 0), rot_dd(b->rot.size(), 0), cpl_dd(b->cpl.size(), 0);
     for (const BatchItemHost& it : b->items) {
-      if (it.engine == ENG_DD) { rot_dd[it.rot] = 1; cpl_dd[it.cpl] = 1; }
-      else rot_native[it.rot] = 1;
+      // the double-float engine and the FP64 tensor-core engine read the
+      // double-float k and H
+      if (it.engine == ENG_DD || (it.engine == ENG_TC && it.d.prec == SLSHT_FP64)) {
+        rot_dd[it.rot] = 1;
+        cpl_dd[it.cpl] = 1;
+      } else {
+        rot_native[it.rot] = 1;
+      }
     }
     for (size_t r = 0; r < b->rot.size(); ++r) {
       if (!rot_native[r]) b->rot[r].H = nullptr;
@@ -1762,7 +1795,11 @@ static int batch_build(slsht_batch* b, const slsht_batch_item* src, int32_t n, c
     BatchItemHost& it = b->items[i];
     if (it.engine != ENG_TC) continue;
     b->tc_items.push_back(i);
-    if (it.d.L_h <= 16) {
+    if (it.d.prec == SLSHT_FP64) {   // digit producer + FP64 alpha kernel per chunk of XW_CHUNK pairs
+      it.xw_pairs = std::min(it.npairs, XW_CHUNK);
+      CKS(batch_alloc(b, tc64_xblob_bytes(it.d.n_beta, it.d.n_gamma) * it.xw_pairs, &it.xw));
+      b->k_alpha += 2 * ((it.npairs + it.xw_pairs - 1) / it.xw_pairs);
+    } else if (it.d.L_h <= 16) {
       b->k_alpha++;
     } else {   // wide: producer + alpha kernel per chunk of XW_CHUNK pairs
       it.xw_pairs = std::min(it.npairs, XW_CHUNK);
@@ -1882,7 +1919,10 @@ extern "C" int slsht_tune(slsht_ctx* ctx, const slsht_desc* desc) {
     it.n_pairs = np;
     it.g_out = gd;
     slsht_batch* b = nullptr;
-    st = slsht_batch_create(ctx, 1, &it, SLSHT_BATCH_NO_GRAPH, nullptr, &b);
+    // the per-call CUDA-core engines' shapes (FP64: double-float or FP64
+    // arithmetic; the tensor-core FP64 engine has no tile shape to tune)
+    const int fl = SLSHT_BATCH_NO_GRAPH | (desc->prec == SLSHT_FP64 ? SLSHT_BATCH_NO_TC : 0);
+    st = slsht_batch_create(ctx, 1, &it, fl, nullptr, &b);
     if (st == SLSHT_OK) slsht_batch_destroy(b);
   }
   ctx_free(ctx, gd, gbytes);

@@ -302,7 +302,7 @@ def test_bounded_wait_expiry_reports_and_context_recovers(ctx):
     assert rel(g, O.forward_coeff(f, h, Lf, Lh, pairs, grid)) < TOL32
 
 
-@pytest.mark.parametrize("prec,engine,arith", [(0, 0, 0), (0, 0, 1), (0, 0, 2), (1, 0, 0), (1, 1, 0), (1, 2, 0)])
+@pytest.mark.parametrize("prec,engine,arith", [(0, 0, 0), (0, 0, 1), (0, 0, 3), (1, 0, 0), (1, 1, 0), (1, 2, 0)])
 def test_real_fields_mirror_pairs(ctx, prec, engine, arith):
     """SLSHT_OPT_REAL_FIELDS: for real f and h, g(l, -m) = (-1)^m conj g(l, m)
     (Sec. IV-B; pin (iv) of the oracle tests), so only one of each mirrored
@@ -426,17 +426,20 @@ def test_modulated_sht_coupling_workload2_size(ctx):
     (20, 16, (511, 8, 31)),     # the widest narrow window at workload 3's N_alpha, 248 columns
 ])
 def test_fp64_tensor_core_engine(ctx, Lf, Lh, grid):
-    """SLSHT_OPT_FP64_ARITH = 2: the FP64 alpha stage from exact base-256
-    digit products on the tensor cores, against the oracle (FP64 bound), the
-    double-float engine, and itself in chunks of two pairs."""
+    """The FP64 alpha stage from exact base-256 digit products on the tensor
+    cores (the FP64 default for L_h <= 16, SLSHT_OPT_FP64_ARITH 0 or 2),
+    against the oracle (FP64 bound), the double-float engine (3), and itself
+    in chunks of two pairs."""
     import paper_1207_5558_gb300 as pkg
     f = synth.signal_powerlaw(Lf, 810 + Lh)
     h = synth.window_cn(Lh, 820 + Lh, decay=1.0)
     pairs = synth.pairs_random(Lf + Lh - 1, 7, 830 + Lh)
     ref = O.forward_coeff(f, h, Lf, Lh, pairs, grid)
-    dd = _fw(ctx, Lf, Lh, grid, f, h, pairs, 0)
-    ctx.set_option(pkg.SLSHT_OPT_FP64_ARITH, 2)
+    g0 = _fw(ctx, Lf, Lh, grid, f, h, pairs, 0)
+    ctx.set_option(pkg.SLSHT_OPT_FP64_ARITH, 3)
     try:
+        dd = _fw(ctx, Lf, Lh, grid, f, h, pairs, 0)
+        ctx.set_option(pkg.SLSHT_OPT_FP64_ARITH, 2)
         g = _fw(ctx, Lf, Lh, grid, f, h, pairs, 0)
         ctx.set_option(pkg.SLSHT_OPT_CHUNK_PAIRS, 2)
         gc = _fw(ctx, Lf, Lh, grid, f, h, pairs, 0)
@@ -445,6 +448,7 @@ def test_fp64_tensor_core_engine(ctx, Lf, Lh, grid):
         ctx.set_option(pkg.SLSHT_OPT_FP64_ARITH, 0)
     assert rel(g, ref) < TOL64
     assert rel(g, dd) < 1e-13
+    assert np.array_equal(g, g0)           # the default
     if Lh > 1:                             # (L_h = 1: g = X_0 exactly, both ways)
         assert not np.array_equal(g, dd)   # a different arithmetic ran
     assert np.array_equal(g, gc)
