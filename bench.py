@@ -693,8 +693,14 @@ def main():
         out["fp64_workload3"] = {
             "value": rate, "unit": UNIT, "ms_per_step": ms, "create_s": create_s,
             "tile_cols": bp.query(pkg.SLSHT_BQ_TILE_COLS, 0),
-            "engine": "double-float" if eng == 1 else "FP64 arithmetic"}
-        if eng == 1:
+            "engine": ["FP64 arithmetic", "double-float", "tensor cores (exact digit products)"][eng]}
+        if eng == 2:
+            out["fp64_workload3"].update({
+                "g_bytes_per_s_frac_of_copy": rate * 16.0 / (peaks()[0]["hbm_gbs"] * 1e9),
+                "note": "per chunk of 16 pairs: the digit producer (X in double-float) and the FP64 alpha "
+                        "kernel on the tensor cores; the fraction is the complex128 bytes of g over the plan's "
+                        "time against the measured copy bandwidth"})
+        elif eng == 1:
             ops, form = alpha_dd_ops(Lh, grid[0], fm if fm > 0 else 0)
             out["fp64_workload3"].update({
                 "alpha_form": form, "issue_slots_per_sample": ops,
