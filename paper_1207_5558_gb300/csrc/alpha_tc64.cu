@@ -53,7 +53,10 @@
 #define T64_BS 3                        // B ring stages
 #define T64_SET (T64_NW * T64_N)        // TMEM columns of one accumulator set (224)
 #define T64_SMEM (T64_A_BYTES + T64_BS * T64_B_BYTES + 1024 + 256)
-#define T64_EPI_WARPS 16                // four per TMEM lane quadrant, 4 alpha rows each
+#ifndef T64_EPI_WARPS
+#define T64_EPI_WARPS 16                // four per TMEM lane quadrant, 4 alpha rows each (8: two, 8 rows)
+#endif
+#define T64_RPW (4 * T64_NA / T64_EPI_WARPS)   // alpha rows per epilogue warp and chunk
 #define T64_THREADS (64 + 32 * T64_EPI_WARPS)
 
 static inline int t64_tiles(int Nb, int Ng) { return (Nb * Ng + TC_M - 1) / TC_M; }
@@ -230,6 +233,11 @@ cudaError_t launch_xa64(const float4* kdd, const int* kexp, const float4* Hdd, c
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"                         \
                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])                                     \
                : "r"(taddr))
+#define TMEM_LD8(taddr, v)                                                                          \
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"             \
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), \
+                 "=r"(v[7])                                                                         \
+               : "r"(taddr))
 
 struct T64Bars {
   uint64_t a_full, a_empty, b_full[T64_BS], b_empty[T64_BS], acc_full[2], acc_empty[2], drain;
@@ -382,8 +390,8 @@ k_alpha_tc64(const unsigned char* __restrict__ xblob, size_t blob_stride, int ti
       while (!mbar_test(smem_u32(&bars->drain), 0u) && ++n < TC_WAIT_LIMIT) {}
     }
   } else {
-    // ---------------- epilogue: warps 2..17; TMEM lane quadrant = warp % 4,
-    // part = which 4 of the chunk's 16 alpha rows
+    // ---------------- epilogue: warps 2 .. 1 + T64_EPI_WARPS; TMEM lane
+    // quadrant = warp % 4, part = which T64_RPW of the chunk's 16 alpha rows
     const int quad = warp & 3;
     const int part = (warp - 2) >> 2;
     const int row = quad * 32 + lane;
@@ -409,19 +417,24 @@ k_alpha_tc64(const unsigned char* __restrict__ xblob, size_t blob_stride, int ti
         __syncwarp();
         if (!(ok = got != 0)) break;
         tc_fence_after();
-        const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(set * T64_SET + part * 4);
-        uint32_t vr[T64_NW][4], vi[T64_NW][4];
+        const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(set * T64_SET + part * T64_RPW);
+        uint32_t vr[T64_NW][T64_RPW], vi[T64_NW][T64_RPW];
 #pragma unroll
         for (int w = 0; w < T64_NW; ++w) {
+#if T64_RPW == 4
           TMEM_LD4(tbase + (uint32_t)(w * T64_N), vr[w]);
           TMEM_LD4(tbase + (uint32_t)(w * T64_N + T64_NA), vi[w]);
+#else
+          TMEM_LD8(tbase + (uint32_t)(w * T64_N), vr[w]);
+          TMEM_LD8(tbase + (uint32_t)(w * T64_N + T64_NA), vi[w]);
+#endif
         }
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         tc_fence_before();
         mbar_arrive(smem_u32(&bars->acc_empty[set]));   // the registers hold the chunk
-        const int a0 = c * T64_NA + part * 4;
+        const int a0 = c * T64_NA + part * T64_RPW;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < T64_RPW; ++u) {
           float ar[T64_NW], ai[T64_NW];
 #pragma unroll
           for (int w = 0; w < T64_NW; ++w) {
