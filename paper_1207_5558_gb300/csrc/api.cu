@@ -660,6 +660,10 @@ static int dd_rule_cols(int Lh, long long J) {
   return nt;
 }
 
+// Pairs a chunk of an FP64 tensor-core call or plan item (digit producer +
+// alpha kernel).
+#define T64_CHUNK 48
+
 // The forward transform on workspace `w` and stream `st` (ctx->mu NOT held).
 // slots (device, nullable): per listed pair {output slot, mirror} (see
 // launch_alpha_tc); g_out must then be device memory.
@@ -781,6 +785,10 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
     P = std::min(P, 256);
     // the wide engine's producer reads H once per chunk: up to 16 pairs a chunk
     if (wide) P = std::max(P, std::min<int>(n_pairs, 16));
+    // the FP64 tensor-core kernel is persistent over (pair, tile) items: up to
+    // 48 pairs a chunk keep its last wave short (about 20 items a CTA at
+    // workload 3's 62 tiles a pair)
+    if (t64) P = std::max(P, std::min<int>(n_pairs, T64_CHUNK));
   }
   if (host_out) {
     // staging buffers for the chunk outputs (double-buffered, D2H on the copy stream)
@@ -1795,8 +1803,8 @@ static int batch_build(slsht_batch* b, const slsht_batch_item* src, int32_t n, c
     BatchItemHost& it = b->items[i];
     if (it.engine != ENG_TC) continue;
     b->tc_items.push_back(i);
-    if (it.d.prec == SLSHT_FP64) {   // digit producer + FP64 alpha kernel per chunk of XW_CHUNK pairs
-      it.xw_pairs = std::min(it.npairs, XW_CHUNK);
+    if (it.d.prec == SLSHT_FP64) {   // digit producer + FP64 alpha kernel per chunk of T64_CHUNK pairs
+      it.xw_pairs = std::min(it.npairs, T64_CHUNK);
       CKS(batch_alloc(b, tc64_xblob_bytes(it.d.n_beta, it.d.n_gamma) * it.xw_pairs, &it.xw));
       b->k_alpha += 2 * ((it.npairs + it.xw_pairs - 1) / it.xw_pairs);
     } else if (it.d.L_h <= 16) {
