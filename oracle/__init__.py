@@ -18,11 +18,16 @@ Modules
            the definition (Eq. stft_spatial) and by the convolution form
            (Eq. alternative_harmonic_formulation_wigner), the SO(3) quadrature
            weights and the inverse (Eq. inversion_1, inversion_2,
-           sig_reconstruction_discrete).
+           sig_reconstruction_discrete), and the inverse without h_0^0 of the
+           remark after Eq. inversion_2 (projection on conj(D^p_{q,q'}) and
+           the Wigner-3j orthogonality).
+  window   the elliptical concentration window of Sec. III-D (Eq. region_def
+           and the concentration matrix), the reference of the device window
+           generator and the source of the stored windows of workloads 2, 5.
 
 Parity status of every function is stated in its docstring: each one is pinned
 by a ``-m "not gpu"`` test against something other than itself (closed forms,
 exact rationals, library routines, invariants the paper states).
 """
 
-from . import special, slsht  # noqa: F401
+from . import special, slsht, window  # noqa: F401

@@ -1,9 +1,11 @@
 """Seeded synthetic inputs for the directional SLSHT.
 
 The one module that both the oracle tests and the CUDA path use.  It holds
-none of the transform's arithmetic: it only draws coefficient vectors, lists
-of (l, m) pairs and grid sizes, and designs the elliptical concentration
-window (an input of the transform, Sec. III-D of the paper).
+none of the method's arithmetic: it only draws coefficient vectors, lists of
+(l, m) pairs and grid sizes, and reads the two stored elliptical
+concentration windows of workloads 2 and 5 (inputs of the transform,
+Sec. III-D of the paper), which tests/golden/make_windows.py wrote with the
+oracle's window generator.
 
 Layouts: coefficient vectors are complex128 with flat index l*l + l + m and
 EXCLUSIVE band limits (f_lm = 0 for l >= Lf).  Pair lists are int32 [n, 2]
@@ -19,16 +21,36 @@ windows, Sec. V):
                          C_l = (l+1)^-2 (topography-like).
   * ``window_cn``        h_pq ~ CN(0,1) / (p+1)^decay for every order (no
                          symmetry, azimuthally asymmetric), unit energy.
-  * ``window_ellipse``   the most concentrated band-limited function in the
+  * ``stored_window``    the most concentrated band-limited function in the
                          elliptical region R_(theta_c, a) at the north pole
-                         (Eq. region_def), real-valued, unit energy, h00 > 0.
+                         (Eq. region_def), real-valued, unit energy, h00 > 0:
+                         L_h = 8 in the 20 x 10 degree ellipse (workload 2),
+                         L_h = 64 in the 8 x 3 degree ellipse (workload 5).
 """
 
+import json
+import os
 from math import pi
 
 import numpy as np
 
-from .window import ellipse_from_axes, window_ellipse  # noqa: F401
+_GOLDEN = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "tests", "golden")
+
+
+def ellipse_from_axes(a_deg, b_deg):
+    """(theta_c, a) in radians from the semi-major and semi-minor arcs of an
+    ellipse centred on the pole: the foci lie on the major axis at colatitude
+    theta_c, and cos(a) = cos(theta_c) cos(b) (spherical Pythagoras)."""
+    a = np.deg2rad(a_deg)
+    b = np.deg2rad(b_deg)
+    return float(np.arccos(np.cos(a) / np.cos(b))), float(a)
+
+
+def stored_window(workload):
+    """(h, concentration) of the stored elliptical window of workload 2 or 5
+    (complex128 [L_h*L_h], flat index p*p+p+q)."""
+    d = json.load(open(os.path.join(_GOLDEN, "workload%d_window.json" % workload)))
+    return np.array(d["re"]) + 1j * np.array(d["im"]), float(d["concentration"])
 
 
 def _cn(rng, size):
@@ -133,12 +155,12 @@ def config_inputs(cfg, map_index=0, window_cache=None):
     if cfg == 1:
         return signal_cn_real(Lf, seed), window_cn(Lh, seed + 500), pairs_all(Lf)
     if cfg == 2:
-        h = window_cache if window_cache is not None else window_ellipse(Lh, *ellipse_from_axes(20.0, 10.0))[0]
+        h = window_cache if window_cache is not None else stored_window(2)[0]
         return signal_powerlaw(Lf, seed), h, pairs_all(Lf)
     if cfg == 3:
         return signal_powerlaw(Lf, seed), window_cn(Lh, seed + 500, decay=1.0), pairs_bands(c["bands"])
     if cfg == 5:
-        h = window_cache if window_cache is not None else window_ellipse(Lh, *ellipse_from_axes(8.0, 3.0))[0]
+        h = window_cache if window_cache is not None else stored_window(5)[0]
         return signal_powerlaw(Lf, seed), h, pairs_random(Lf, c["npairs"], seed)
     raise KeyError(cfg)
 
@@ -155,7 +177,7 @@ def grid_native(Lh):
 
 __all__ = [
     "signal_real_symmetric", "signal_cn_real", "signal_powerlaw", "signal_uniform",
-    "window_cn", "window_ellipse", "ellipse_from_axes", "pairs_all", "pairs_bands",
+    "window_cn", "stored_window", "ellipse_from_axes", "pairs_all", "pairs_bands",
     "pairs_random", "subsample_pairs", "CONFIGS", "config_inputs", "samples_per_pair",
     "grid_native", "pi",
 ]

@@ -1,18 +1,14 @@
 """The concentrated-window generator on the device (slsht_window_ellipse,
-Sec. III-D) against the host generator of the workloads (synth/window.py,
-pinned in test_window.py): the same eigenfunction and concentration."""
-import json
-import os
-
+Sec. III-D) against the oracle's generator (oracle/window.py, pinned in
+test_window.py): the same eigenfunction and concentration."""
 import numpy as np
 import pytest
 
 import synth
-from synth.window import ellipse_from_axes, window_ellipse
+from oracle.window import window_ellipse
+from synth import ellipse_from_axes
 
 pytestmark = pytest.mark.gpu
-
-HERE = os.path.dirname(os.path.abspath(__file__))
 
 
 @pytest.fixture(scope="module")
@@ -42,9 +38,9 @@ def test_window_matches_host_generator(ctx, L, region):
 
 
 def test_window_workload5(ctx):
-    """L = 64, 8 x 3 degrees (workload 5) against the stored host result."""
-    d = json.load(open(os.path.join(HERE, "golden", "workload5_window.json")))
-    h_ref = np.array(d["re"]) + 1j * np.array(d["im"])
+    """L = 64, 8 x 3 degrees (workload 5) against the oracle's stored result
+    (tests/golden/make_windows.py)."""
+    h_ref, lam_ref = synth.stored_window(5)
     h, lam = ctx.window_ellipse(64, *ellipse_from_axes(8.0, 3.0))
     assert np.linalg.norm(h - h_ref) < 1e-8
-    assert 0.0 < lam <= 1.0
+    assert abs(lam - lam_ref) < 1e-12

@@ -8,9 +8,6 @@ against the oracle's coefficient-domain route with its coupling from the
 order-recursion 3j families (Racah's rational sum is too slow for a whole
 pair at l ~ 2000; the families are pinned against it in the oracle tests),
 and the inversion round trip of all 16 f_lm (Sec. III-C)."""
-import json
-import os
-
 import numpy as np
 import pytest
 
@@ -19,16 +16,10 @@ from oracle import slsht as O
 
 pytestmark = pytest.mark.gpu
 
-HERE = os.path.dirname(os.path.abspath(__file__))
-
 
 def _window():
-    path = os.path.join(HERE, "golden", "workload5_window.json")
-    if os.path.exists(path):
-        d = json.load(open(path))
-        return np.array(d["re"]) + 1j * np.array(d["im"])
-    from synth.window import ellipse_from_axes, window_ellipse
-    return window_ellipse(64, *ellipse_from_axes(8.0, 3.0))[0]
+    """The stored L_h = 64 window, written by the oracle (make_windows.py)."""
+    return synth.stored_window(5)[0]
 
 
 def test_workload5_full_grid():

@@ -1,4 +1,6 @@
-"""Pins for the elliptical concentration window generator (Sec. III-D)."""
+"""Pins for the oracle's elliptical concentration window generator
+(oracle/window.py, Sec. III-D), and for the stored windows of workloads 2
+and 5 that the seeded-input module hands to both sides."""
 import json
 import os
 from math import pi
@@ -6,7 +8,7 @@ from math import pi
 import numpy as np
 
 import synth
-from synth import window as W
+from oracle import window as W
 
 GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
 
@@ -66,3 +68,17 @@ def test_window_is_real_unit_energy_positive_dc():
         for m in range(-l, l + 1):
             assert abs(h[l * l + l - m] - (-1) ** (m % 2) * np.conj(h[l * l + l + m])) < 1e-13
     assert 0.3 < lam < 1.0
+
+
+def test_stored_windows_are_the_oracle_windows():
+    """The stored workload-2 window is the oracle's eigenfunction (recomputed
+    here); both stored windows are unit-energy real fields with h00 > 0 and
+    the concentration the file records lies in (0, 1]."""
+    h2, lam2 = synth.stored_window(2)
+    h, lam = W.window_ellipse(8, *synth.ellipse_from_axes(20.0, 10.0))
+    assert np.linalg.norm(h2 - h) < 1e-13 and abs(lam2 - lam) < 1e-14
+    for w, L in ((2, 8), (5, 64)):
+        hw, lw = synth.stored_window(w)
+        assert hw.shape == (L * L,) and abs(np.linalg.norm(hw) - 1) < 1e-13 and hw[0].real > 0
+        assert np.max(np.abs(hw - W.mirror(hw, L))) < 1e-12
+        assert 0.0 < lw <= 1.0
