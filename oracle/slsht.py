@@ -107,7 +107,7 @@ class GauntCoefficients:
 class GauntRecurrence:
     """The same k_{lm}(p, q) as GauntCoefficients, with the 3j symbols of T
     from their order families (special.wigner3j_m_family: the J^2
-    eigen-equation in the coupled basis, run in 60-digit decimal arithmetic)
+    eigen-equation in the coupled basis, run in 100-digit decimal arithmetic)
     instead of Racah's rational sum, which costs milliseconds a symbol at the
     degrees of workload 5 (l ~ 2000).  Pinned against GauntCoefficients at
     small and at large degree."""
@@ -341,3 +341,65 @@ def inverse(g, h00, grid):
     if h00 == 0:
         raise ValueError("h_0^0 must be non-zero for the inverse (Eq. inversion_2)")
     return so3_integral(g, grid) / (sqrt(16.0 * pi ** 3) * h00)
+
+
+# --------------------------------------------------------------------------
+# inverse without h_0^0 (the remark after Eq. inversion_2)
+# --------------------------------------------------------------------------
+
+def d_projection(g, grid, p):
+    """P[i, q, q'] = int_SO(3) g(rho; pair i) conj(D^p_{q,q'}(rho)) d rho for
+    |q|, |q'| <= p, by the same SO(3) quadrature as the inverse, with
+    D^p_{q,q'} = e^{-i q alpha} d^p_{q,q'}(beta) e^{-i q' gamma} (Eq. Dlm).
+    Exact when every grid size is at least Lh + p (the integrand is then
+    band-limited within the rule's reach in every angle).
+    g: [npairs, Na, Nb, Ng] -> [npairs, 2p+1, 2p+1] (index q + p, q' + p)."""
+    Na, Nb, Ng = grid
+    a, b, c = grid_angles(Na, Nb, Ng)
+    qs = np.arange(-p, p + 1)
+    Ea = np.exp(1j * np.outer(qs, a))             # conj(e^{-i q alpha})   [2p+1, Na]
+    Eg = np.exp(1j * np.outer(qs, c))             # conj(e^{-i q' gamma})  [2p+1, Ng]
+    d = special.wigner_d_table(p + 1, b)[p]       # d^p_{q,q'}(beta_b), [K, K, Nb] with K = 2p + 1
+    wq = beta_weights(Nb)
+    out = np.einsum('iabc,qa,qrb,rc,b->iqr', g, Ea, d, Eg, wq)
+    return (2.0 * pi / Na) * (2.0 * pi / Ng) * out
+
+
+def inverse_alt(g, h, Lh, pairs, grid, p, out_pairs):
+    """f_{L,M} from g without the condition h_0^0 != 0, by the reconstruction of
+    the remark after Eq. inversion_2, taken in its steps:
+      1. project g on conj(D^p_{q,q'}) (d_projection): by the orthogonality of
+         the Wigner D functions (Eq. WignerD_ortho) the projection of
+         g(.; l, m) is 8 pi^2 / (2p+1) k_lm(p, q) h_p^{q'};
+      2. decouple the window with its coefficients at degree p: summing
+         conj(h_p^{q'}) times the projection over q' leaves
+         8 pi^2 / (2p+1) E_p k_lm(p, q), E_p = sum_q' |h_p^q'|^2 the window's
+         energy at degree p (non-zero: the condition that replaces h_0^0 != 0);
+      3. decouple the signal with the orthogonality of the Wigner-3j symbols:
+         with k_lm(p, q) = sum_l' f_{l', m-q} T(l', m-q; p, q; l, m) and T
+         through 3j symbols (Sec. III-B),
+           sum_q (L p l; M q -(M+q)) (l' p l; M q -(M+q)) = delta_{L l'} / (2L+1),
+         so f_{L,M} = (2L+1) / c^2 sum_q T(L, M; p, q; l, M+q) k_{l, M+q}(p, q),
+         c^2 = (2L+1)(2p+1)(2l+1)/(4 pi) (L p l; 0 0 0)^2, for any degree l with
+         (L p l; 0 0 0) != 0.  Here l = L + p, which always qualifies.
+    pairs: the (l, m) of g's rows; every (L + p, M + q), |q| <= p, of each
+    requested (L, M) must be among them.  out_pairs: the (L, M) to recover.
+    Returns complex128 [len(out_pairs)]."""
+    pairs = [tuple(int(v) for v in pr) for pr in pairs]
+    row = {pr: i for i, pr in enumerate(pairs)}
+    hp = np.array([h[p * p + p + q] for q in range(-p, p + 1)])
+    Ep = float(np.sum(np.abs(hp) ** 2))
+    if Ep == 0.0:
+        raise ValueError("the window has no energy at degree p")
+    out = np.zeros(len(out_pairs), dtype=np.complex128)
+    need = sorted({row[(L + p, M + q)] for L, M in out_pairs for q in range(-p, p + 1)})
+    proj = d_projection(g[need], grid, p)                       # [n, 2p+1, 2p+1]
+    khat = {need[i]: (2 * p + 1) / (8.0 * pi ** 2 * Ep) * (proj[i] @ np.conj(hp)) for i in range(len(need))}
+    for o, (L, M) in enumerate(out_pairs):
+        l = L + p
+        c2 = (2 * L + 1) * (2 * p + 1) * (2 * l + 1) / (4.0 * pi) * special.wigner3j_exact(L, p, l, 0, 0, 0) ** 2
+        acc = 0.0
+        for q in range(-p, p + 1):
+            acc += special.gaunt_exact(L, M, p, q, l, M + q) * khat[row[(l, M + q)]][q + p]
+        out[o] = (2 * L + 1) / c2 * acc
+    return out

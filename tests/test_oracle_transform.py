@@ -301,3 +301,72 @@ def test_gaunt_recurrence_route_matches_exact():
     for l, m in [(1800, 1200), (1850, 7)]:
         ke = O.modulated_coeffs_gaunt(f, Lf, Lh, l, m)
         assert np.linalg.norm(gr.coeffs(l, m) - ke) / np.linalg.norm(ke) < 1e-13
+
+
+def test_d_projection_equals_coupling_times_window():
+    """d_projection against the identity of the remark after Eq. inversion_2,
+    its right side from the Appendix A route to k (independent of the 3j
+    symbols and of the projection's own code): the grid here is the smallest
+    the oracle's docstring allows (every size Lh + p)."""
+    Lf, Lh, p = 7, 4, 2
+    f = synth.signal_cn_real(Lf, 23)
+    h = synth.window_cn(Lh, 24)
+    grid = (Lh + p, Lh + p, Lh + p)
+    pairs = [(3, 1), (6, -4), (8, 2)]
+    g = O.forward_coeff(f, h, Lf, Lh, pairs, grid)
+    P = O.d_projection(g, grid, p)
+    ms = O.ModulatedSHT(f, Lf, Lh, 8)
+    for i, (l, m) in enumerate(pairs):
+        k = ms.coeffs(l, m)
+        for q in range(-p, p + 1):
+            for qp in range(-p, p + 1):
+                rhs = 8 * pi ** 2 / (2 * p + 1) * k[p, q + Lh - 1] * h[p * p + p + qp]
+                assert abs(P[i, q + p, qp + p] - rhs) < 1e-13
+
+
+def test_threej_orthogonality_over_the_window_order():
+    """The 3j orthogonality the alternative inversion rests on, in exact
+    rationals: for fixed (p, l) and M, sum over q of (L p l; M q -(M+q))
+    (L' p l; M q -(M+q)) = delta_{L L'} / (2L+1)."""
+    from fractions import Fraction
+    p, l = 2, 5
+    for M in (-3, 0, 2):
+        for L in range(abs(l - p), l + p + 1):
+            for L2 in range(abs(l - p), l + p + 1):
+                if abs(M) > min(L, L2):
+                    continue
+                s = Fraction(0)
+                for q in range(-p, p + 1):
+                    if abs(M + q) > l:
+                        continue
+                    a = S.wigner3j_exact(L, p, l, M, q, -(M + q))
+                    b = S.wigner3j_exact(L2, p, l, M, q, -(M + q))
+                    s += Fraction(a) * Fraction(b)
+                want = Fraction(1, 2 * L + 1) if L == L2 else Fraction(0)
+                assert abs(float(s - want)) < 1e-15, (M, L, L2)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_inverse_alt_recovers_signal_without_dc(p):
+    """The inverse of the remark after Eq. inversion_2 on a window with
+    h_0^0 = 0 (where Eq. inversion_2 cannot be used): f recovered to rounding
+    from the distribution at degrees L + p, for each degree p of the window,
+    on the smallest grid its quadrature allows; one size smaller in beta the
+    rule is no longer exact and the recovery fails."""
+    Lf, Lh = 8, 4
+    f = synth.signal_cn_real(Lf, 3)
+    h = synth.window_cn(Lh, 4)
+    h[0] = 0.0
+    outs = synth.pairs_all(Lf)
+    pairs = sorted({(L + p, M + q) for L, M in outs for q in range(-p, p + 1)})
+    ft = f[outs[:, 0] ** 2 + outs[:, 0] + outs[:, 1]]
+    grid = (Lh + p, Lh + p, Lh + p)
+    g = O.forward_coeff(f, h, Lf, Lh, pairs, grid)
+    fr = O.inverse_alt(g, h, Lh, pairs, grid, p, outs)
+    assert np.max(np.abs(fr - ft)) < 1e-13 * np.max(np.abs(ft))
+    with pytest.raises(ValueError):
+        O.inverse(g[:1], h[0], grid)
+    small = (Lh + p, Lh + p - 1, Lh + p)
+    gs = O.forward_coeff(f, h, Lf, Lh, pairs, small)
+    fs = O.inverse_alt(gs, h, Lh, pairs, small, p, outs)
+    assert np.max(np.abs(fs - ft)) > 1e-6 * np.max(np.abs(ft))
