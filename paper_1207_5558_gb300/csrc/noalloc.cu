@@ -1,11 +1,12 @@
 // slsht_forward_noalloc: the forward transform without any device allocation.
 //
 // Some callers cannot allocate device memory at the moment they need the
-// transform: code running inside a host callback or a real-time section where
-// cudaMalloc's implicit device synchronisation is not allowed, plug-ins whose
-// host application owns the allocator (and forbids a second one from growing
-// behind its back), and processes that have already handed the whole device to
-// a fixed memory pool.  For them this entry point works out of one scratch
+// transform: real-time sections where cudaMalloc's implicit device
+// synchronisation is not allowed, plug-ins whose host application owns the
+// allocator (and forbids a second one from growing behind its back), and
+// processes that have already handed the whole device to a fixed memory pool.
+// The call is made from ordinary host code (it calls the CUDA runtime, which a
+// function queued with cudaLaunchHostFunc may not do).  For them this entry point works out of one scratch
 // array of SLSHT_NOALLOC_SCRATCH_BYTES declared at file scope in device memory:
 // it is created when the library is loaded and stays on every GPU that loads
 // the library until the process exits.
@@ -76,7 +77,11 @@ extern "C" int slsht_forward_noalloc(const slsht_desc* desc, const double* f_lm,
   if (!f_lm || !h_lm || !lm || !g_out || (((uintptr_t)g_out) & 7)) return SLSHT_E_ARG;
   if (!on_device(g_out)) return SLSHT_E_ARG;
   cudaStream_t st = (cudaStream_t)stream;
-  // validate the pairs through a fixed host buffer (no allocation)
+  // Validate the pairs through a fixed host buffer (no allocation).  A device
+  // pair list is read on the caller's stream, after the work queued there
+  // before this call (which may be what wrote it), and the stream is then
+  // synchronised: the kernels below read the same, validated list, provided
+  // the caller leaves it unchanged until the call's work is done.
   const bool lm_dev = on_device(lm);
   {
     int32_t buf[1024];
@@ -84,8 +89,10 @@ extern "C" int slsht_forward_noalloc(const slsht_desc* desc, const double* f_lm,
       const int32_t n = n_pairs - off < 512 ? n_pairs - off : 512;
       const int32_t* src = lm + 2 * (size_t)off;
       if (lm_dev) {
-        if (cudaMemcpy(buf, src, sizeof(int32_t) * 2 * (size_t)n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        if (cudaMemcpyAsync(buf, src, sizeof(int32_t) * 2 * (size_t)n, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
           cudaGetLastError();
+          slsht_record_error_text("slsht_forward_noalloc: reading the device pair list on the stream failed");
           return SLSHT_E_CUDA;
         }
         src = buf;
