@@ -369,13 +369,14 @@ struct TcBars {
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_alpha_tc(const unsigned char* __restrict__ xblob, size_t blob_stride, int tiles,
            const unsigned char* __restrict__ etab, int Na, int J, int npairs, float2* __restrict__ g,
-           int* __restrict__ err, const int2* __restrict__ slots) {
+           int* __restrict__ err, const int2* __restrict__ slots, int wait_test) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = sm;                               // 2 x 32 KB
   unsigned char* sB = sm + 2 * TC_A_BYTES;              // 64 KB
   TcBars* bars = reinterpret_cast<TcBars*>(sB + TC_B_BYTES);
   volatile int* abort_flag = &bars->abort_flag;
+  const uint32_t wlim = wait_test ? (1u << 14) : TC_WAIT_LIMIT;   // short limit for the timeout test
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nch = (Na + TC_NC - 1) / TC_NC;
   const long long nitems = (long long)npairs * tiles;
@@ -413,16 +414,18 @@ k_alpha_tc(const unsigned char* __restrict__ xblob, size_t blob_stride, int tile
         const int pair = (int)(it / tiles), tile = (int)(it % tiles);
         const int sa = li & 1;
         const uint32_t pa = (uint32_t)((li >> 1) & 1);
-        if (!mbar_wait(smem_u32(&bars->a_empty[sa]), pa ^ 1u, abort_flag)) { *abort_flag = 1; break; }
-        const uint32_t fa = smem_u32(&bars->a_full[sa]);
-        mbar_expect_tx(fa, TC_A_BYTES);
-        const unsigned char* src = xblob + (size_t)pair * blob_stride + (size_t)tile * TC_A_BYTES;
-        for (int o = 0; o < TC_A_BYTES; o += 16384)
-          bulk_g2s(smem_u32(sA + sa * TC_A_BYTES + o), src + o, 16384, fa);
-        a_armed[sa] = (int)pa;
+        if (!mbar_wait_n(smem_u32(&bars->a_empty[sa]), pa ^ 1u, abort_flag, wlim)) { *abort_flag = 1; break; }
+        if (!(wait_test && li == 0)) {   // wait_test: the first A operand is never fetched
+          const uint32_t fa = smem_u32(&bars->a_full[sa]);
+          mbar_expect_tx(fa, TC_A_BYTES);
+          const unsigned char* src = xblob + (size_t)pair * blob_stride + (size_t)tile * TC_A_BYTES;
+          for (int o = 0; o < TC_A_BYTES; o += 16384)
+            bulk_g2s(smem_u32(sA + sa * TC_A_BYTES + o), src + o, 16384, fa);
+          a_armed[sa] = (int)pa;
+        }
         for (int c = 0; c < nch; ++c, ++bc) {
           const uint32_t pb = (uint32_t)(bc & 1);
-          if (!mbar_wait(smem_u32(&bars->b_empty), pb ^ 1u, abort_flag)) { *abort_flag = 1; break; }
+          if (!mbar_wait_n(smem_u32(&bars->b_empty), pb ^ 1u, abort_flag, wlim)) { *abort_flag = 1; break; }
           const uint32_t fb = smem_u32(&bars->b_full);
           mbar_expect_tx(fb, TC_B_BYTES);
           const unsigned char* bsrc = etab + (size_t)c * TC_B_BYTES;
@@ -452,12 +455,12 @@ k_alpha_tc(const unsigned char* __restrict__ xblob, size_t blob_stride, int tile
       bool ok = true;
       for (long long it = blockIdx.x; it < nitems && ok; it += gridDim.x, ++li) {
         const int sa = li & 1;
-        if (!(ok = mbar_wait(smem_u32(&bars->a_full[sa]), (uint32_t)((li >> 1) & 1), abort_flag))) break;
+        if (!(ok = mbar_wait_n(smem_u32(&bars->a_full[sa]), (uint32_t)((li >> 1) & 1), abort_flag, wlim))) break;
         const uint32_t a_hi = smem_u32(sA + sa * TC_A_BYTES), a_lo = a_hi + TC_A_HALF;
         for (int c = 0; c < nch; ++c, ++bc, ++ac) {
           const int acc = (int)(ac & 1);
-          if (!(ok = mbar_wait(smem_u32(&bars->b_full), (uint32_t)(bc & 1), abort_flag))) break;
-          if (!(ok = mbar_wait(smem_u32(&bars->acc_empty[acc]), (uint32_t)(((ac >> 1) & 1) ^ 1), abort_flag))) break;
+          if (!(ok = mbar_wait_n(smem_u32(&bars->b_full), (uint32_t)(bc & 1), abort_flag, wlim))) break;
+          if (!(ok = mbar_wait_n(smem_u32(&bars->acc_empty[acc]), (uint32_t)(((ac >> 1) & 1) ^ 1), abort_flag, wlim))) break;
           tc_fence_after();
           const uint32_t b_hi = smem_u32(sB), b_lo = b_hi + TC_B_HALF;
           const uint32_t d = tmem + (uint32_t)(acc * TC_N);
@@ -505,7 +508,7 @@ k_alpha_tc(const unsigned char* __restrict__ xblob, size_t blob_stride, int tile
         const int acc = (int)(ac & 1);
         // one lane waits, the warp follows: tcgen05.ld needs a converged warp
         int got = 0;
-        if (lane == 0) got = mbar_wait(smem_u32(&bars->acc_full[acc]), (uint32_t)((ac >> 1) & 1), abort_flag);
+        if (lane == 0) got = mbar_wait_n(smem_u32(&bars->acc_full[acc]), (uint32_t)((ac >> 1) & 1), abort_flag, wlim);
         got = __shfl_sync(0xffffffffu, got, 0);
         __syncwarp();
         if (!(ok = got != 0)) break;
@@ -558,6 +561,14 @@ k_alpha_tc(const unsigned char* __restrict__ xblob, size_t blob_stride, int tile
   }
 }
 
+static thread_local int t_wait_test = 0;
+void tc_arm_wait_test() { t_wait_test = 1; }
+int tc_take_wait_test() {
+  const int v = t_wait_test;
+  t_wait_test = 0;
+  return v;
+}
+
 // Device word a tensor-core kernel sets when it gives up on a bounded wait.
 int* tc_error_word() {
   static int* p = nullptr;
@@ -598,6 +609,7 @@ cudaError_t launch_alpha_tc(const void* xblob, const void* etab, int Lh, int Na,
   const long long items = (long long)npairs * tiles;
   const int grid = (int)(items < num_sms ? items : num_sms);
   k_alpha_tc<<<grid, TC_THREADS, TC_SMEM, st>>>((const unsigned char*)xblob, tc_xblob_bytes(Nb, Ng, Lh), tiles,
-                                               (const unsigned char*)etab, Na, Nb * Ng, npairs, g, err, slots);
+                                               (const unsigned char*)etab, Na, Nb * Ng, npairs, g, err, slots,
+                                               tc_take_wait_test());
   return cudaGetLastError();
 }

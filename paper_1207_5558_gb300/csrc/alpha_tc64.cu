@@ -263,13 +263,14 @@ __device__ __forceinline__ void t64_combine(const float* a, float* h, float* l) 
 __global__ void __launch_bounds__(T64_THREADS, 1)
 k_alpha_tc64(const unsigned char* __restrict__ xblob, size_t blob_stride, int tiles,
              const unsigned char* __restrict__ etab, int Na, int J, int npairs, double2* __restrict__ g,
-             int* __restrict__ err, const int2* __restrict__ slots) {
+             int* __restrict__ err, const int2* __restrict__ slots, int wait_test) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = sm;                               // 7 x 16 KB: the item's A digits
   unsigned char* sB = sm + T64_A_BYTES;                 // T64_BS x 28 KB: ring of B digit chunks
   T64Bars* bars = reinterpret_cast<T64Bars*>(sB + T64_BS * T64_B_BYTES);
   volatile int* abort_flag = &bars->abort_flag;
+  const uint32_t wlim = wait_test ? (1u << 14) : TC_WAIT_LIMIT;   // short limit for the timeout test
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nch = (Na + T64_NA - 1) / T64_NA;
   const long long nitems = (long long)npairs * tiles;
@@ -311,16 +312,18 @@ k_alpha_tc64(const unsigned char* __restrict__ xblob, size_t blob_stride, int ti
       for (long long it = blockIdx.x; it < nitems && ok; it += gridDim.x, ++li) {
         const int pair = (int)(it / tiles), tile = (int)(it % tiles);
         const uint32_t pa = (uint32_t)(li & 1);
-        if (!(ok = mbar_wait(smem_u32(&bars->a_empty), pa ^ 1u, abort_flag))) break;
-        const uint32_t fa = smem_u32(&bars->a_full);
-        mbar_expect_tx(fa, T64_A_BYTES);
-        const unsigned char* src = xblob + (size_t)pair * blob_stride + (size_t)tile * T64_A_BYTES;
-        for (int o = 0; o < T64_A_BYTES; o += 16384) bulk_g2s(smem_u32(sA + o), src + o, 16384, fa);
-        a_armed = (int)pa;
+        if (!(ok = mbar_wait_n(smem_u32(&bars->a_empty), pa ^ 1u, abort_flag, wlim))) break;
+        if (!(wait_test && li == 0)) {   // wait_test: the first A digits are never fetched
+          const uint32_t fa = smem_u32(&bars->a_full);
+          mbar_expect_tx(fa, T64_A_BYTES);
+          const unsigned char* src = xblob + (size_t)pair * blob_stride + (size_t)tile * T64_A_BYTES;
+          for (int o = 0; o < T64_A_BYTES; o += 16384) bulk_g2s(smem_u32(sA + o), src + o, 16384, fa);
+          a_armed = (int)pa;
+        }
         for (int c = 0; c < nch && ok; ++c, ++bc) {
           const int sb = (int)(bc % T64_BS);
           const uint32_t pb = (uint32_t)((bc / T64_BS) & 1);
-          if (!(ok = mbar_wait(smem_u32(&bars->b_empty[sb]), pb ^ 1u, abort_flag))) break;
+          if (!(ok = mbar_wait_n(smem_u32(&bars->b_empty[sb]), pb ^ 1u, abort_flag, wlim))) break;
           const uint32_t fb = smem_u32(&bars->b_full[sb]);
           mbar_expect_tx(fb, T64_B_BYTES);
           const unsigned char* bsrc = etab + (size_t)c * T64_B_BYTES;
@@ -353,11 +356,11 @@ k_alpha_tc64(const unsigned char* __restrict__ xblob, size_t blob_stride, int ti
       int li = 0;
       bool ok = true;
       for (long long it = blockIdx.x; it < nitems && ok; it += gridDim.x, ++li) {
-        if (!(ok = mbar_wait(smem_u32(&bars->a_full), (uint32_t)(li & 1), abort_flag))) break;
+        if (!(ok = mbar_wait_n(smem_u32(&bars->a_full), (uint32_t)(li & 1), abort_flag, wlim))) break;
         for (int c = 0; c < nch && ok; ++c, ++bc, ++ac) {
           const int set = (int)(ac & 1), sb = (int)(bc % T64_BS);
-          if (!(ok = mbar_wait(smem_u32(&bars->b_full[sb]), (uint32_t)((bc / T64_BS) & 1), abort_flag))) break;
-          if (!(ok = mbar_wait(smem_u32(&bars->acc_empty[set]), (uint32_t)(((ac >> 1) & 1) ^ 1), abort_flag)))
+          if (!(ok = mbar_wait_n(smem_u32(&bars->b_full[sb]), (uint32_t)((bc / T64_BS) & 1), abort_flag, wlim))) break;
+          if (!(ok = mbar_wait_n(smem_u32(&bars->acc_empty[set]), (uint32_t)(((ac >> 1) & 1) ^ 1), abort_flag, wlim)))
             break;
           tc_fence_after();
           const uint32_t d0 = tmem + (uint32_t)(set * T64_SET);
@@ -412,7 +415,7 @@ k_alpha_tc64(const unsigned char* __restrict__ xblob, size_t blob_stride, int ti
         const int set = (int)(ac & 1);
         // one lane waits, the warp follows: tcgen05.ld needs a converged warp
         int got = 0;
-        if (lane == 0) got = mbar_wait(smem_u32(&bars->acc_full[set]), (uint32_t)((ac >> 1) & 1), abort_flag);
+        if (lane == 0) got = mbar_wait_n(smem_u32(&bars->acc_full[set]), (uint32_t)((ac >> 1) & 1), abort_flag, wlim);
         got = __shfl_sync(0xffffffffu, got, 0);
         __syncwarp();
         if (!(ok = got != 0)) break;
@@ -483,6 +486,7 @@ cudaError_t launch_alpha_tc64(const void* xblob, const void* etab, int Lh, int N
   const long long items = (long long)npairs * tiles;
   const int grid = (int)(items < num_sms ? items : num_sms);
   k_alpha_tc64<<<grid, T64_THREADS, T64_SMEM, st>>>((const unsigned char*)xblob, tc64_xblob_bytes(Nb, Ng), tiles,
-                                                   (const unsigned char*)etab, Na, Nb * Ng, npairs, g, err, slots);
+                                                   (const unsigned char*)etab, Na, Nb * Ng, npairs, g, err, slots,
+                                                   tc_take_wait_test());
   return cudaGetLastError();
 }

@@ -297,7 +297,7 @@ template <int NKF>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_alpha_tcw(const unsigned char* __restrict__ xblob, size_t blob_stride, int tiles,
             const unsigned char* __restrict__ etab, int Na, int J, int npairs, float2* __restrict__ g,
-            int* __restrict__ err, const int2* __restrict__ slots) {
+            int* __restrict__ err, const int2* __restrict__ slots, int wait_test) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   constexpr int BS = TCW_BS(NKF), NK = 2 * NKF;
@@ -305,6 +305,7 @@ k_alpha_tcw(const unsigned char* __restrict__ xblob, size_t blob_stride, int til
   unsigned char* sB = sm + NK * TC_A_BYTES;             // BS x 32 KB: ring of E-table K-chunks
   TcwBars* bars = reinterpret_cast<TcwBars*>(sB + BS * TC_B_BYTES);
   volatile int* abort_flag = &bars->abort_flag;
+  const uint32_t wlim = wait_test ? (1u << 14) : TC_WAIT_LIMIT;   // short limit for the timeout test
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nch = (Na + TCW_NA - 1) / TCW_NA;
   const long long nitems = (long long)npairs * tiles;
@@ -346,17 +347,19 @@ k_alpha_tcw(const unsigned char* __restrict__ xblob, size_t blob_stride, int til
       for (long long it = blockIdx.x; it < nitems && ok; it += gridDim.x, ++li) {
         const int pair = (int)(it / tiles), tile = (int)(it % tiles);
         const uint32_t pa = (uint32_t)(li & 1);
-        if (!(ok = mbar_wait(smem_u32(&bars->a_empty), pa ^ 1u, abort_flag))) break;
-        const uint32_t fa = smem_u32(&bars->a_full);
-        mbar_expect_tx(fa, NK * TC_A_BYTES);
-        const unsigned char* src = xblob + (size_t)pair * blob_stride + (size_t)tile * NK * TC_A_BYTES;
-        for (int o = 0; o < NK * TC_A_BYTES; o += 16384) bulk_g2s(smem_u32(sA + o), src + o, 16384, fa);
-        a_armed = (int)pa;
+        if (!(ok = mbar_wait_n(smem_u32(&bars->a_empty), pa ^ 1u, abort_flag, wlim))) break;
+        if (!(wait_test && li == 0)) {   // wait_test: the first A operand is never fetched
+          const uint32_t fa = smem_u32(&bars->a_full);
+          mbar_expect_tx(fa, NK * TC_A_BYTES);
+          const unsigned char* src = xblob + (size_t)pair * blob_stride + (size_t)tile * NK * TC_A_BYTES;
+          for (int o = 0; o < NK * TC_A_BYTES; o += 16384) bulk_g2s(smem_u32(sA + o), src + o, 16384, fa);
+          a_armed = (int)pa;
+        }
         for (int c = 0; c < nch && ok; ++c) {
           for (int kc = 0; kc < NKF; ++kc, ++bc) {
             const int sb = (int)(bc % BS);
             const uint32_t pb = (uint32_t)((bc / BS) & 1);
-            if (!(ok = mbar_wait(smem_u32(&bars->b_empty[sb]), pb ^ 1u, abort_flag))) break;
+            if (!(ok = mbar_wait_n(smem_u32(&bars->b_empty[sb]), pb ^ 1u, abort_flag, wlim))) break;
             const uint32_t fb = smem_u32(&bars->b_full[sb]);
             mbar_expect_tx(fb, TC_B_BYTES);
             const unsigned char* bsrc = etab + ((size_t)c * NKF + kc) * TC_B_BYTES;
@@ -390,16 +393,16 @@ k_alpha_tcw(const unsigned char* __restrict__ xblob, size_t blob_stride, int til
       int li = 0;
       bool ok = true;
       for (long long it = blockIdx.x; it < nitems && ok; it += gridDim.x, ++li) {
-        if (!(ok = mbar_wait(smem_u32(&bars->a_full), (uint32_t)(li & 1), abort_flag))) break;
+        if (!(ok = mbar_wait_n(smem_u32(&bars->a_full), (uint32_t)(li & 1), abort_flag, wlim))) break;
         for (int c = 0; c < nch && ok; ++c, ++ac) {
           const int acc = (int)(ac % TCW_ACC);
-          if (!(ok = mbar_wait(smem_u32(&bars->acc_empty[acc]), (uint32_t)(((ac / TCW_ACC) & 1) ^ 1),
-                               abort_flag)))
+          if (!(ok = mbar_wait_n(smem_u32(&bars->acc_empty[acc]), (uint32_t)(((ac / TCW_ACC) & 1) ^ 1),
+                                 abort_flag, wlim)))
             break;
           const uint32_t d = tmem + (uint32_t)(acc * 2 * TC_N);     // D_re, then D_im 128 columns on
           for (int kc = 0; kc < NKF; ++kc, ++bc) {
             const int sb = (int)(bc % BS);
-            if (!(ok = mbar_wait(smem_u32(&bars->b_full[sb]), (uint32_t)((bc / BS) & 1), abort_flag))) break;
+            if (!(ok = mbar_wait_n(smem_u32(&bars->b_full[sb]), (uint32_t)((bc / BS) & 1), abort_flag, wlim))) break;
             tc_fence_after();
             const uint32_t b_hi = smem_u32(sB + sb * TC_B_BYTES), b_lo = b_hi + TC_B_HALF;
 #pragma unroll
@@ -454,7 +457,7 @@ k_alpha_tcw(const unsigned char* __restrict__ xblob, size_t blob_stride, int til
         // one lane waits, the warp follows: tcgen05.ld needs a converged warp
         int got = 0;
         if (lane == 0)
-          got = mbar_wait(smem_u32(&bars->acc_full[acc]), (uint32_t)((ac / TCW_ACC) & 1), abort_flag);
+          got = mbar_wait_n(smem_u32(&bars->acc_full[acc]), (uint32_t)((ac / TCW_ACC) & 1), abort_flag, wlim);
         got = __shfl_sync(0xffffffffu, got, 0);
         __syncwarp();
         if (!(ok = got != 0)) break;
@@ -525,7 +528,7 @@ static cudaError_t launch_tcw_t(const void* xblob, const void* etab, int Lh, int
   const int grid = (int)(items < num_sms ? items : num_sms);
   k_alpha_tcw<NKF><<<grid, TC_THREADS, TCW_SMEM(NKF), st>>>((const unsigned char*)xblob, tcw_xblob_bytes(Nb, Ng, Lh),
                                                           tiles, (const unsigned char*)etab, Na, Nb * Ng, npairs, g,
-                                                          err, slots);
+                                                          err, slots, tc_take_wait_test());
   return cudaGetLastError();
 }
 

@@ -58,6 +58,14 @@ cudaError_t launch_xa64(const float4* kdd, const int* kexp, const float4* Hdd, c
 // g[pair][a][j] complex128; slots as launch_alpha_tc
 cudaError_t launch_alpha_tc64(const void* xblob, const void* etab, int Lh, int Na, int Nb, int Ng, int npairs,
                               double2* g, int num_sms, const int2* slots, cudaStream_t st);
+// Timeout-path test of the separate-producer tensor-core kernels
+// (launch_alpha_tc, launch_alpha_tcw, launch_alpha_tc64): after
+// tc_arm_wait_test() the next such launch from the same host thread withholds
+// the first A operand of every CTA (the copy is never issued), so the
+// issuer's and the epilogue's bounded waits expire, the kernel leaves cleanly
+// and reports through the error word; that launch's output is not computed.
+void tc_arm_wait_test();
+int tc_take_wait_test();
 // Device error word shared by the tensor-core kernels (allocated on first use).
 int* tc_error_word();
 // Non-zero (and cleared) if a tensor-core kernel gave up on a bounded wait

@@ -278,28 +278,41 @@ def test_gaunt_table_mirror_pairs_with_duplicates(ctx):
     assert rel(g, O.forward_coeff(f, h, Lf, Lh, pairs, grid)) < TOL64
 
 
-def test_bounded_wait_expiry_reports_and_context_recovers(ctx):
-    """The timeout path of the fused tensor-core kernel: with one internal
-    hand-off withheld (SLSHT_OPT_WAIT_TEST) every bounded wait expires, the
-    kernel leaves cleanly, slsht_get_stats reports SLSHT_E_TIMEOUT, and the
-    next call on the same context is correct."""
+@pytest.mark.parametrize("name,prec,Lh,engine", [
+    ("fused", 1, 5, 0),              # k_alpha_fused: producer warps in the alpha kernel
+    ("two_kernel", 1, 5, 2),         # k_alpha_tc fed by k_xa_from_h
+    ("wide", 1, 20, 0),              # k_alpha_tcw (16 < L_h <= 64)
+    ("fp64_digits", 0, 5, 0),        # k_alpha_tc64 (FP64 from exact digit products)
+])
+def test_bounded_wait_expiry_reports_and_context_recovers(ctx, name, prec, Lh, engine):
+    """The timeout path of every tensor-core alpha kernel: with one internal
+    hand-off withheld (SLSHT_OPT_WAIT_TEST: the fused kernel's first A tile is
+    never handed to the issuer; the other kernels' first A operand is never
+    fetched) the bounded waits expire, the kernel leaves cleanly,
+    slsht_get_stats reports SLSHT_E_TIMEOUT, and the next call on the same
+    context is correct."""
     import torch
     import paper_1207_5558_gb300 as pkg
     from paper_1207_5558_gb300 import _abi
-    Lf, Lh, grid = 10, 5, (130, 10, 13)
+    Lf, grid = 10, (130, 10, 2 * Lh + 3)
     f = synth.signal_powerlaw(Lf, 81)
     h = synth.window_cn(Lh, 82)
     pairs = synth.pairs_bands([2, 9])
-    ctx.stats(reset=True)
-    ctx.set_option(pkg.SLSHT_OPT_WAIT_TEST, 1)
-    ctx.forward(Lf, Lh, grid, f, h, pairs, prec=1)
-    torch.cuda.synchronize()
-    with pytest.raises(pkg.SlshtError) as e:
-        ctx.stats()
-    assert e.value.code == _abi.SLSHT_E_TIMEOUT
-    ctx.stats()                                    # the error word was cleared
-    g = _fw(ctx, Lf, Lh, grid, f, h, pairs, 1)
-    assert rel(g, O.forward_coeff(f, h, Lf, Lh, pairs, grid)) < TOL32
+    ctx.set_option(pkg.SLSHT_OPT_ALPHA_ENGINE, engine)
+    try:
+        ctx.stats(reset=True)
+        ctx.set_option(pkg.SLSHT_OPT_WAIT_TEST, 1)
+        ctx.forward(Lf, Lh, grid, f, h, pairs, prec=prec)
+        torch.cuda.synchronize()
+        with pytest.raises(pkg.SlshtError) as e:
+            ctx.stats()
+        assert e.value.code == _abi.SLSHT_E_TIMEOUT
+        ctx.stats()                                    # the error word was cleared
+        g = _fw(ctx, Lf, Lh, grid, f, h, pairs, prec)
+        assert rel(g, O.forward_coeff(f, h, Lf, Lh, pairs, grid)) < (TOL32 if prec else TOL64)
+    finally:
+        ctx.set_option(pkg.SLSHT_OPT_WAIT_TEST, 0)
+        ctx.set_option(pkg.SLSHT_OPT_ALPHA_ENGINE, 0)
 
 
 @pytest.mark.parametrize("prec,engine,arith", [(0, 0, 0), (0, 0, 1), (0, 0, 3), (1, 0, 0), (1, 1, 0), (1, 2, 0)])
