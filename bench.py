@@ -256,13 +256,30 @@ def serve_bench(pkg, device, n, rate, seed=4000, max_outstanding_bytes=48 << 30,
     ctx = pkg.Context(device, mem_budget_bytes=(24 << 30))
     # build the tables of every (L_h, native grid, precision) and measure the
     # FP64 tile shapes once, outside the measurement
+    warm = []
     for Lh in (4, 8, 16, 32):
         grid = serve_native(Lh)
-        ctx.tune(128, Lh, grid, 0)
         for prec in (0, 1):
-            ctx.forward(32, Lh, grid, np.zeros(32 * 32, complex), np.ones(Lh * Lh, complex), [[1, 0]], prec=prec)
+            ctx.tune(128, Lh, grid, prec)
+            g = torch.empty((1,) + grid, dtype=torch.complex128 if prec == 0 else torch.complex64,
+                            device="cuda:%d" % device)
+            warm.append((g, ctx.submit(32, Lh, grid, np.zeros(32 * 32, complex), np.ones(Lh * Lh, complex),
+                                       [[1, 0]], g, prec=prec)))
+    ctx.drain(600000)          # tables built, graphs captured at the workload's shared-memory sizes
+    for _, tk in warm:
+        ctx.poll(tk)
     torch.cuda.synchronize()
     done_at = np.full(n, np.nan)
+    parts = np.full((n, 4), np.nan)            # queue, host issue, device, total (library clock), ms
+    # a seeded sample of requests whose results are kept for the oracle check
+    # of the CPU leg: both precisions, the widest window and the largest signal
+    picks = set(np.random.default_rng(seed + 2).choice(n, size=min(n, 6), replace=False).tolist())
+    for want in (lambda r: r["Lh"] == 32, lambda r: r["Lf"] == 512):
+        for k in range(n):
+            if want(reqs[k]):
+                picks.add(k)
+                break
+    kept = []
     outstanding = {}
     out_bytes = 0
     samples = 0
@@ -283,13 +300,17 @@ def serve_bench(pkg, device, n, rate, seed=4000, max_outstanding_bytes=48 << 30,
             samples += g.numel()
             i += 1
         for tk in list(outstanding):
-            st = ctx.poll(tk)
+            st, tm = ctx.poll_times(tk)
             if st != 1:
                 if st != 0:
                     raise RuntimeError("serving request failed: %d" % st)
-                k, _, nb = outstanding.pop(tk)
+                k, g, nb = outstanding.pop(tk)
                 done_at[k] = time.perf_counter() - t0
+                parts[k] = tm
                 out_bytes -= nb
+                if k in picks:         # one seeded pair of the request, on the host
+                    j = int(np.random.default_rng(seed + 3 + k).integers(len(reqs[k]["pairs"])))
+                    kept.append(dict(reqs[k], pairs=reqs[k]["pairs"][j:j + 1], g=g[j:j + 1].cpu().numpy()))
         time.sleep(0.0002)
     ctx.drain(600000)
     ok = ~np.isnan(done_at)
@@ -297,12 +318,29 @@ def serve_bench(pkg, device, n, rate, seed=4000, max_outstanding_bytes=48 << 30,
     span = np.nanmax(done_at) - arrivals[0]
     done_samples = sum(len(reqs[k]["pairs"]) * int(np.prod(reqs[k]["grid"])) for k in np.nonzero(ok)[0])
     ctx.close()
+    pt = parts[ok]
+
+    def pct(col):
+        v = pt[:, col]
+        return {"p50": float(np.percentile(v, 50)), "p99": float(np.percentile(v, 99)), "mean": float(v.mean())}
+    slow = np.argsort(lat)[-max(1, len(lat) // 100):]          # the slowest 1 %
     return {"requests": n, "completed": int(ok.sum()), "offered_rate_per_s": rate,
             "achieved_rate_per_s": float(ok.sum() / span), "sustained": bool(ok.sum() / span >= 0.95 * rate),
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
             "g_samples_per_s": done_samples / span, "span_s": float(span),
             "mean_samples_per_request": done_samples / max(1, ok.sum()),
+            "breakdown_ms": {"queue": pct(0), "host_issue": pct(1), "device": pct(2), "library_total": pct(3),
+                             "slowest_1pct_mean": {"queue": float(pt[slow, 0].mean()),
+                                                   "device": float(pt[slow, 2].mean()),
+                                                   "samples": float(np.mean([len(reqs[k]["pairs"]) * np.prod(
+                                                       reqs[k]["grid"]) for k in np.nonzero(ok)[0][slow]]))},
+                             "note": "per request from slsht_poll_times: queue = submission to its first tick, "
+                                     "host issue = building + launching its first tick, device = start of its "
+                                     "first tick to the end of its last (device clock); latency above is from "
+                                     "arrival (includes the wait behind the output cap)"},
+            "engine": "ticks of persistent batched kernels replayed from a captured graph (two lanes)",
+            "kept_for_oracle": kept,
             "workload": "L_f in {32..512}, L_h in {4,8,16,32}, 1-8 degrees x all m, native grid "
                         "2L_h-1 x L_h x 2L_h-1, FP64/FP32_BULK 50/50, Poisson arrivals (seed 4000); "
                         "outstanding outputs capped at 48 GB, later arrivals wait (latency from arrival)"}
@@ -319,9 +357,8 @@ def profile_case(pkg, n, prec=1, wl=3, fp64_arith=0):
     import synth
     ctx = pkg.Context(0, 16 << 30)
     if wl == 5:
-        from synth.window import ellipse_from_axes
         c5 = synth.CONFIGS[5]
-        h, _ = ctx.window_ellipse(c5["Lh"], *ellipse_from_axes(8.0, 3.0))
+        h, _ = ctx.window_ellipse(c5["Lh"], *synth.ellipse_from_axes(8.0, 3.0))
         f, _, pairs = synth.config_inputs(5, window_cache=h)
         c = dict(c5, grid=(c5["grid"][0], 256, c5["grid"][2]))
         sub = np.ascontiguousarray(pairs[:n])
@@ -383,24 +420,57 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------- our arm
-def cpu_baseline_sample(budget_s=20.0):
-    """Time the oracle as it stands on a bounded sample of the workload."""
+def cpu_baseline_sample(budget_s=12.0):
+    """Time the oracle as it stands on a bounded sample of the workload: pairs
+    of map 0 drawn from a seeded permutation, each on the full grid, until
+    about budget_s seconds have passed."""
+    import numpy as np
     import synth
     from oracle import slsht as O
     c, maps = workload(0)
     f, h, pairs = maps[0]
-    sample = [pairs[i] for i in (3, 100, 300, 700, 929)]
-    n, t0 = 0, time.perf_counter()
-    for pr in sample:
-        O.forward_coeff(f, h, c["Lf"], c["Lh"], [pr], c["grid"])
+    order = np.random.default_rng(3).permutation(len(pairs))
+    n, t0, c0 = 0, time.perf_counter(), time.process_time()
+    for i in order:
+        O.forward_coeff(f, h, c["Lf"], c["Lh"], [pairs[i]], c["grid"])
         n += 1
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
+    busy = (time.process_time() - c0) / dt          # cores the oracle kept busy on average
     v = n * synth.samples_per_pair(c["grid"]) / dt
-    return {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "%d pairs of map 0 (l in 16..255) on the full grid, %.1f s; numpy BLAS threads for the "
-                      "sums, exact-3j coupling single-threaded" % (n, dt)}
+    # the oracle's concentration-window generator (Sec. III-D) at L_h = 32,
+    # the 8 x 3 degree ellipse: the baseline of the device generator
+    from oracle.window import window_ellipse
+    t1 = time.perf_counter()
+    window_ellipse(32, *synth.ellipse_from_axes(8.0, 3.0))
+    tw = time.perf_counter() - t1
+    return {"value": v, "unit": UNIT, "cores": round(busy, 2), "kind": "oracle",
+            "sample": "%d seeded pairs of map 0 (l in 16..255) on the full grid, %.1f s; cores = process CPU time "
+                      "over wall time (the exact-3j coupling runs on one core, the numpy sums may use BLAS "
+                      "threads; %d host cores)" % (n, dt, os.cpu_count()),
+            "window_generator_L32_s": tw}
+
+
+def serve_oracle_check(kept):
+    """Part of the CPU leg: the oracle on the seeded sample of served results
+    that the serving run kept (one pair of each sampled request, full native
+    grid); the worst relative L2 per precision."""
+    import numpy as np
+    from oracle import slsht as O
+    worst = {0: 0.0, 1: 0.0}
+    cnt = {0: 0, 1: 0}
+    t0 = time.perf_counter()
+    for r in kept:
+        ref = O.forward_coeff(r["f"], r["h"], r["Lf"], r["Lh"], r["pairs"], r["grid"])
+        e = float(np.linalg.norm(r["g"] - ref) / np.linalg.norm(ref))
+        worst[r["prec"]] = max(worst[r["prec"]], e)
+        cnt[r["prec"]] += 1
+    return {"max_rel_l2_fp64": worst[0], "max_rel_l2_fp32": worst[1], "oracle_checked": {
+        "fp64_requests": cnt[0], "fp32_requests": cnt[1], "seconds": time.perf_counter() - t0,
+        "sample": "one seeded pair of each of 6 seeded requests plus the first with L_h = 32 and the first with "
+                  "L_f = 512, full native grid, against the FP64 oracle (tolerances 1e-12 FP64, 1e-5 FP32_BULK)",
+        "lh32_and_lf512_included": bool(any(r["Lh"] == 32 for r in kept) and any(r["Lf"] == 512 for r in kept))}}
 
 
 def main():
@@ -564,20 +634,15 @@ def main():
     def window_leg():
         """F3 of the scope table: the concentrated window of the 8 x 3 degree
         ellipse (workload 5's region) generated on the device at L_h = 32 and
-        64, and by the host generator of the workloads at L_h = 32."""
-        from synth.window import ellipse_from_axes, window_ellipse
-        reg = ellipse_from_axes(8.0, 3.0)
+        64 (the oracle's generator is timed in the CPU-baseline leg)."""
+        reg = synth.ellipse_from_axes(8.0, 3.0)
         out = {}
         for L in (32, 64):
-            ctx.window_ellipse(L, *reg)                       # warm-up (cuBLAS, tables)
+            ctx.window_ellipse(L, *reg)                       # warm-up (tables)
             t0 = time.perf_counter()
             _, lam = ctx.window_ellipse(L, *reg)
             out["gpu_L%d_s" % L] = time.perf_counter() - t0
             out["concentration_L%d" % L] = lam
-        t0 = time.perf_counter()
-        window_ellipse(32, *reg)
-        out["host_generator_L32_s"] = time.perf_counter() - t0
-        out["speedup_L32"] = out["host_generator_L32_s"] / out["gpu_L32_s"]
         return out
 
     def coupling_leg():
@@ -613,6 +678,40 @@ def main():
         ctx.set_option(pkg.SLSHT_OPT_GAUNT_TABLE, 0)
         ctx.set_option(pkg.SLSHT_OPT_COUPLING, 0)
         return out
+
+    def inverse_alt_leg(p=2):
+        """The inverse without h_0^0 (remark after Eq. inversion_2) at workload-2
+        band limits: the window of workload 2 with its h_0^0 removed, g at every
+        pair (L + p, M + q) the outputs L < 64 need, complex64 on 127 x 64 x 15;
+        time of slsht_inverse_alt and the recovered f against the signal."""
+        c2 = synth.CONFIGS[2]
+        L2f, L2h, gr = c2["Lf"], c2["Lh"], c2["grid"]
+        f2 = synth.signal_powerlaw(L2f, 2000)
+        h2 = synth.stored_window(2)[0].copy()
+        h2[0] = 0.0
+        outs = synth.pairs_all(L2f)
+        pin = np.array(sorted({(int(L) + p, int(M) + q) for L, M in outs for q in range(-p, p + 1)}), dtype=np.int32)
+        g2 = torch.empty((len(pin),) + gr, dtype=torch.complex64, device="cuda")
+        ctx.forward(L2f, L2h, gr, f2, h2, pin, prec=1, g_out=g2)
+        hd, ind, outd = torch.from_numpy(h2).cuda(), torch.from_numpy(pin).cuda(), torch.from_numpy(outs).cuda()
+        fd = torch.zeros(len(outs), dtype=torch.complex128, device="cuda")
+        desc = pkg.make_desc(L2f, L2h, gr, 1)
+        pkg.slsht_inverse_alt(ctx.h, desc, g2, hd, ind, len(pin), p, outd, len(outs), fd, stream)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            pkg.slsht_inverse_alt(ctx.h, desc, g2, hd, ind, len(pin), p, outd, len(outs), fd, stream)
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1) / 3
+        ft = f2[outs[:, 0] ** 2 + outs[:, 0] + outs[:, 1]]
+        rel = float(np.linalg.norm(fd.cpu().numpy() - ft) / np.linalg.norm(ft))
+        nbytes = g2.numel() * 8
+        del g2
+        return {"p": p, "pairs_in": int(len(pin)), "outputs": int(len(outs)), "ms_per_call": ms,
+                "read_GB_per_s": nbytes / (ms / 1e3) / 1e9, "rel_l2_recovered_f": rel,
+                "workload": "L_f=64, L_h=8 workload-2 window with h_0^0 = 0, grid 127x64x15, complex64 g"}
 
     def batch_leg():
         """Batch plans (slsht_batch_*): (a) the first 48 requests of the
@@ -728,7 +827,6 @@ def main():
         batch plan of the same pairs (same buffer), events on the stream.
         The alpha stage runs on the wide tensor-core engine (orders +-q
         paired: two real GEMMs of K = 128 against one cos|sin operand)."""
-        from synth.window import ellipse_from_axes
         c5 = synth.CONFIGS[5]
         # contexts of their own, one for the call (H, 8.5 GB; X scratch of a
         # 16-pair chunk, 4.3 GB each) and, after it is closed, one for the
@@ -736,7 +834,7 @@ def main():
         torch.cuda.empty_cache()
         ctx = pkg.Context(local, mem_budget_bytes=(96 << 30))
         L5f, L5h, g5 = c5["Lf"], c5["Lh"], c5["grid"]
-        h5, _ = ctx.window_ellipse(L5h, *ellipse_from_axes(8.0, 3.0))
+        h5, _ = ctx.window_ellipse(L5h, *synth.ellipse_from_axes(8.0, 3.0))
         f5, _, p5 = synth.config_inputs(5, window_cache=h5)
         f5d, h5d = torch.from_numpy(f5).cuda(), torch.from_numpy(h5).cuda()
         p5d = torch.from_numpy(np.ascontiguousarray(p5)).cuda()
@@ -760,6 +858,23 @@ def main():
         ctx.profile(False)
         ms = e0.elapsed_time(e1)
         st = ctx.stats(reset=True)
+        # the rotated window over the window's active orders only
+        # (SLSHT_OPT_WINDOW_ORDERS = 2: the ellipse window's odd orders are rounding noise)
+        ref_rows = gb[0, :, :8, :].clone()
+        ctx.set_option(pkg.SLSHT_OPT_WINDOW_ORDERS, 2)
+        step()
+        barrier()
+        ctx.profile(True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        barrier()
+        ctx.profile(False)
+        ms_orders = e0.elapsed_time(e1)
+        st_orders = ctx.stats(reset=True)
+        rel_orders = float(torch.linalg.vector_norm(gb[0, :, :8, :] - ref_rows) / torch.linalg.vector_norm(ref_rows))
+        ctx.set_option(pkg.SLSHT_OPT_WINDOW_ORDERS, 0)
+        del ref_rows
         ctx.close()
         ctx = pkg.Context(local, mem_budget_bytes=(96 << 30))
         items = [{"L_f": L5f, "L_h": L5h, "grid": g5, "prec": 1, "f": f5d, "h": h5d, "lm": p5, "g_out": gb}]
@@ -779,6 +894,11 @@ def main():
                "plan_engine": ["CUDA cores", "double-float", "tensor cores"][eng],
                "alpha_stage_hbm_frac": smp * 8.0 / (st["ms"]["alpha"] / 1e3) / hbm if st["ms"]["alpha"] else None,
                "per_call_hbm_frac": smp / (ms / 1e3) * 8.0 / hbm,
+               "window_orders": {"per_call_ms": ms_orders, "value_per_call": smp / (ms_orders / 1e3),
+                                 "beta_gamma_ms": st_orders["ms"]["beta_gamma"],
+                                 "rel_l2_vs_all_orders_pair0_8rows": rel_orders,
+                                 "note": "SLSHT_OPT_WINDOW_ORDERS = 2: the rotated window sums over the window's "
+                                         "even orders only (its odd orders are at the rounding level)"},
                "note": "stage times from events around each launch; the alpha fraction is the g bytes over the "
                        "alpha kernels' summed time against the measured copy bandwidth"}
         bp.close()
@@ -885,11 +1005,13 @@ def main():
     del a32
     torch.cuda.empty_cache()
     win_gen = None
+    inv_alt = None
     coup = None
     batch = None
     w5 = None
     if args.fp64_steps > 0:
         wins = windows_leg()
+        inv_alt = inverse_alt_leg()
         win_gen = window_leg()
         coup = coupling_leg()
         batch = batch_leg()
@@ -935,6 +1057,11 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline_sample()
+        if serve is not None:
+            serve.update(serve_oracle_check(serve.pop("kept_for_oracle")))
+    for rec in (serve, (serve or {}).get("at_80pct_of_saturation")):
+        if rec is not None:
+            rec.pop("kept_for_oracle", None)
 
     if rank == 0:
         line = {
@@ -961,7 +1088,20 @@ def main():
             "batch_plans": batch,
             "workload5": w5,
             "serve": serve,
+            "inverse_alt": inv_alt,
         }
+        # the headline figures again, last on the line (a compact record for tails)
+        line["summary"] = {
+            "fp32_bulk": value, "roofline_frac": roof.get("frac"),
+            "fp64": fp64["value"] if fp64 else None,
+            "fp64_plan": ((batch or {}).get("fp64_workload3") or {}).get("value"),
+            "fp32_over_fp64": line["fp32_over_fp64_speedup"],
+            "workload5_per_call": (w5 or {}).get("value_per_call"),
+            "serve_p50_ms": (serve or {}).get("p50_ms"), "serve_p99_ms": (serve or {}).get("p99_ms"),
+            "serve_rate": (serve or {}).get("achieved_rate_per_s"),
+            "serve_max_rel_l2_fp64": (serve or {}).get("max_rel_l2_fp64"),
+            "serve_max_rel_l2_fp32": (serve or {}).get("max_rel_l2_fp32"),
+            "e2e": (e2e or {}).get("value")}
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist is not None:

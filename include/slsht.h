@@ -199,16 +199,46 @@ int slsht_inverse(slsht_ctx* ctx, const slsht_desc* desc,
                   const int32_t* lm, int32_t n_pairs,
                   double* f_out, void* stream);
 
+/* f_lm without the condition h_0^0 != 0: the reconstruction of the remark
+ * after Eq. inversion_2 (Sec. III-C).  The projection of g(.; l, m) on
+ * conj(D^p_{q,q'}) over SO(3) is 8 pi^2/(2p+1) k_lm(p, q) h_p^q'
+ * (Eq. WignerD_ortho); summing it against conj(h_p^q') leaves the window's
+ * energy at degree p, E_p = sum_q' |h_p^q'|^2, times k_lm(p, q); and the
+ * Wigner-3j orthogonality over q decouples the signal:
+ *   f_LM = (2L+1)/c^2 sum_q T(L, M; p, q; L+p, M+q) khat_{L+p, M+q}(q),
+ * c^2 = (2L+1)(2p+1)(2L+2p+1)/(4 pi) (L p L+p; 0 0 0)^2.
+ *   g_in   device buffer laid out as slsht_forward's g_out for the pairs
+ *          lm_in (desc->prec selects complex128 / complex64)
+ *   h_lm   complex128 [L_h*L_h] (host or device): the window of g_in
+ *   lm_in  int32 [n_in][2] (host or device): the pairs of g_in's rows
+ *   p      the window degree used, 0 <= p < L_h, with E_p > 0; the
+ *          distribution must hold, for each output (L, M), every pair
+ *          (L + p, M + q) with |q| <= p
+ *   lm_out int32 [n_out][2] (host or device): the (L, M) to recover,
+ *          0 <= L < L_f, |M| <= L
+ *   f_out  complex128 [n_out] (host or device)
+ * Exact (to rounding) when n_alpha, n_beta, n_gamma >= L_h + p.  Device
+ * argument arrays are read on `stream` after the work queued there; the call
+ * returns when its work is done.  Errors: SLSHT_E_ARG (as slsht_inverse,
+ * plus p out of range, a grid size < L_h + p, an output outside the signal
+ * band, or a missing pair), SLSHT_E_H00 (E_p == 0), SLSHT_E_NOMEM,
+ * SLSHT_E_CUDA.  Fixed reduction order: bitwise reproducible. */
+int slsht_inverse_alt(slsht_ctx* ctx, const slsht_desc* desc, const void* g_in, const double* h_lm,
+                      const int32_t* lm_in, int32_t n_in, int32_t p, const int32_t* lm_out, int32_t n_out,
+                      double* f_out, void* stream);
+
 /* ---------------------------------------------------------------- no-alloc */
 
 /* Size of the static device scratch array behind slsht_forward_noalloc. */
 #define SLSHT_NOALLOC_SCRATCH_BYTES (32u << 20)
 
 /* The forward transform for callers that cannot allocate device memory when
- * they need it: code in host callbacks or real-time sections where
- * cudaMalloc's implicit synchronisation is not allowed, plug-ins whose host
- * application owns the device allocator, and processes that have given the
- * whole device to a fixed pool.  The paper has no counterpart to this call.
+ * they need it: real-time sections where cudaMalloc's implicit
+ * synchronisation is not allowed, plug-ins whose host application owns the
+ * device allocator, and processes that have given the whole device to a
+ * fixed pool.  Call it from ordinary host code: it calls the CUDA runtime,
+ * which a function queued with cudaLaunchHostFunc (or a stream callback) may
+ * not do.  The paper has no counterpart to this call.
  * It needs no context and allocates nothing: it works in one static device
  * array of SLSHT_NOALLOC_SCRATCH_BYTES that every GPU loading this library
  * holds until the process exits.  Arguments, layouts and results are those of
@@ -217,6 +247,12 @@ int slsht_inverse(slsht_ctx* ctx, const slsht_desc* desc,
  * processed in chunks that fit the array.
  *  - Requests whose tables plus one pair exceed the array are rejected with
  *    SLSHT_E_NOMEM before anything is enqueued (slsht_last_error explains).
+ *  - A pair list in device memory is validated by reading it on `stream`
+ *    (after the work queued there before the call) and synchronising that
+ *    stream, so such a call blocks until the stream's earlier work is done;
+ *    pass lm in host memory for a call that must not block.  The kernels read
+ *    the device list again later in stream order: leave it unchanged until
+ *    the call's work has completed.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current: make that first call
  *    before any stream capture.
@@ -323,9 +359,10 @@ int slsht_batch_query(const slsht_batch* batch, int32_t item, int32_t what, int6
 /* Measure the tile shapes of one grid shape now: the same autotuner as
  * slsht_batch_create (every candidate timed on seeded synthetic
  * coefficients of that shape, a few pairs of degree L_f - 1), its choice
- * cached in the context.  slsht_forward and slsht_submit read the cache for
- * the CUDA-core alpha kernels of FP64 calls (double-float engine); without
- * an entry they use a built-in rule.  Synchronous; returns SLSHT_OK,
+ * cached in the context (for FP32_BULK also the shape on CUDA cores alone).
+ * slsht_forward reads the cache for the CUDA-core alpha kernels of FP64 calls
+ * (double-float engine) and slsht_submit for every request's alpha tiles;
+ * without an entry they use a built-in rule.  Synchronous; returns SLSHT_OK,
  * SLSHT_E_ARG, SLSHT_E_NOMEM or SLSHT_E_CUDA. */
 int slsht_tune(slsht_ctx* ctx, const slsht_desc* desc);
 
@@ -339,11 +376,21 @@ void slsht_batch_destroy(slsht_batch* batch);
 /* Non-blocking forward request for a continuous-batching server.  The
  * library copies f_lm, h_lm and lm before returning (host or device input);
  * g_out must be DEVICE memory and stay valid until the request completes.
- * Requests run on the context's own pool of streams, so requests that arrive
- * while others are on the GPU overlap with them; each is admitted when its
- * scratch fits the context's memory budget.  *ticket receives the request
- * id.  Returns SLSHT_OK, SLSHT_E_BUSY (queue full), or the errors of
- * slsht_forward (validation is synchronous). */
+ * A worker thread evaluates the requests in ticks: each tick takes a chunk of
+ * pairs from every started request (oldest first; a large request is spread
+ * over several ticks, so requests that arrive behind it are not held up) and
+ * from newly arrived ones while its arena has room (admission by memory), and
+ * runs them as ONE set of persistent batched kernels -- the 3j-chain
+ * coupling, the rotated windows, and one alpha kernel per arithmetic whose
+ * blocks take tiles from a counter -- replayed from a captured CUDA graph.
+ * Two ticks can be on the device at once.  The alpha stage runs on CUDA
+ * cores (FP64 requests in double-float arithmetic unless the tuner cache of
+ * the context says otherwise; slsht_tune fills it), with the tile shape of
+ * the request's grid shape, so a request's g does not depend on the requests
+ * it shares ticks with.  *ticket receives the request id.  Returns SLSHT_OK,
+ * SLSHT_E_BUSY (more than 4096 requests unfinished), SLSHT_E_NOMEM (one pair
+ * exceeds a tick's arena), or the errors of slsht_forward (validation is
+ * synchronous). */
 int slsht_submit(slsht_ctx* ctx, const slsht_desc* desc,
                  const double* f_lm, const double* h_lm,
                  const int32_t* lm, int32_t n_pairs,
@@ -354,6 +401,13 @@ int slsht_submit(slsht_ctx* ctx, const slsht_desc* desc,
  * polled until it has returned a final status once; then it is forgotten
  * (SLSHT_E_STATE afterwards). */
 int slsht_poll(slsht_ctx* ctx, uint64_t ticket);
+
+/* slsht_poll that also reports, once the request has finished, its times
+ * in milliseconds: times[0] queue (submission to its first tick), times[1]
+ * host issue (building and launching its first tick), times[2] device (start
+ * of its first tick to the end of its last, device clock), times[3] total
+ * (submission to the completion seen by the worker).  times may be NULL. */
+int slsht_poll_times(slsht_ctx* ctx, uint64_t ticket, double* times);
 
 /* Block until every submitted request has finished (bounded by timeout_ms;
  * SLSHT_E_TIMEOUT if it expires). */
@@ -401,13 +455,15 @@ int slsht_get_stats(slsht_ctx* ctx, slsht_stats* out, int reset);
  *                            fits in 256 MB, and a call with the same list
  *                            only gathers k = sum T f; 1: always keep it;
  *                            2: never (3j chains recomputed in every call).
- *  SLSHT_OPT_WAIT_TEST    1: the next forward call that runs the fused
- *                            tensor-core kernel withholds one internal
- *                            hand-off, so the kernel's bounded waits expire
- *                            (short limit), it exits cleanly and the next
- *                            slsht_get_stats returns SLSHT_E_TIMEOUT; that
- *                            call's g is not computed.  Resets itself.  For
- *                            testing the timeout path; the context stays usable.
+ *  SLSHT_OPT_WAIT_TEST    1: the next forward call that runs a tensor-core
+ *                            alpha kernel (fused, two-kernel, wide or FP64
+ *                            digit-product engine) withholds one internal
+ *                            hand-off in its first launch, so the kernel's
+ *                            bounded waits expire, it exits cleanly and the
+ *                            next slsht_get_stats returns SLSHT_E_TIMEOUT;
+ *                            that call's g is not computed.  Resets itself.
+ *                            For testing the timeout path; the context stays
+ *                            usable.
  *  SLSHT_OPT_REAL_FIELDS  1: the caller guarantees that f and h are real
  *                            fields (f_{l,-m} = (-1)^m conj f_lm, and the same
  *                            for h).  Then g(rho; l, -m) = (-1)^m conj
@@ -438,6 +494,22 @@ int slsht_get_stats(slsht_ctx* ctx, slsht_stats* out, int reset);
  *                            of floats from exact TwoProd/TwoSum steps, about
  *                            48 significant bits).  Relative error about
  *                            1e-14 for 0, 2 and 3.
+ *  SLSHT_OPT_WINDOW_ORDERS 1: the rotated window (the window turned to every
+ *                            (beta, gamma) sample) sums only over the orders
+ *                            q' at which the window has a non-zero
+ *                            coefficient at some degree (found on the device
+ *                            from h in every call).  A steerable window --
+ *                            azimuthally band-limited, h_p^q' = 0 for
+ *                            |q'| >= N < L_h (Sec. IV-B) -- then costs
+ *                            (2N-1)/(2p+1) of the full sum at degree p; the
+ *                            terms left out are zero, so g is unchanged.
+ *                            2: as 1, also leaving out orders whose
+ *                            coefficients are at most 2^-40 (FP32_BULK) or
+ *                            2^-52 (FP64) of the largest one: windows whose
+ *                            vanishing orders carry rounding noise only (the
+ *                            concentration window of an ellipse centred on
+ *                            the pole has its odd orders at that level).
+ *                            0 (default): every order.
  * Returns SLSHT_OK or SLSHT_E_ARG. */
 #define SLSHT_OPT_BETA_ROUTE   1
 #define SLSHT_OPT_ALPHA_ENGINE 2
@@ -447,6 +519,7 @@ int slsht_get_stats(slsht_ctx* ctx, slsht_stats* out, int reset);
 #define SLSHT_OPT_REAL_FIELDS  6
 #define SLSHT_OPT_COUPLING     7
 #define SLSHT_OPT_FP64_ARITH   8
+#define SLSHT_OPT_WINDOW_ORDERS 9
 int slsht_set_option(slsht_ctx* ctx, int option, int64_t value);
 
 /* Bytes of device memory the context currently holds. */

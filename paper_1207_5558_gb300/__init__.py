@@ -11,7 +11,7 @@ import ctypes
 from . import _abi
 from ._abi import (SLSHT_FP32_BULK, SLSHT_FP64, SLSHT_OPT_ALPHA_ENGINE,  # noqa: F401
                    SLSHT_OPT_BETA_ROUTE, SLSHT_OPT_CHUNK_PAIRS, SLSHT_OPT_GAUNT_TABLE, SLSHT_OPT_WAIT_TEST, SLSHT_OPT_REAL_FIELDS,
-                   SLSHT_OPT_COUPLING, SLSHT_OPT_FP64_ARITH,
+                   SLSHT_OPT_COUPLING, SLSHT_OPT_FP64_ARITH, SLSHT_OPT_WINDOW_ORDERS,
                    SLSHT_BATCH_NO_GRAPH, SLSHT_BATCH_NO_TUNE, SLSHT_BATCH_NO_TC, SLSHT_BATCH_NO_DD,
                    SLSHT_BATCH_FP64_DD,
                    SLSHT_BQ_TILE_COLS, SLSHT_BQ_ALPHA_FORM, SLSHT_BQ_TUNED, SLSHT_BQ_TILES, SLSHT_BQ_KERNELS,
@@ -23,8 +23,8 @@ __all__ = ["Context", "make_desc", "SLSHT_FP64", "SLSHT_FP32_BULK", "SlshtError"
            "slsht_create", "slsht_destroy", "slsht_forward", "slsht_forward_noalloc", "slsht_forward_windows",
            "slsht_window_ellipse", "slsht_batch_create", "slsht_batch_launch", "slsht_batch_query",
            "slsht_batch_destroy", "slsht_tune", "Batch",
-           "slsht_inverse", "slsht_submit",
-           "slsht_poll", "slsht_drain", "slsht_strerror", "slsht_check_args", "slsht_profile",
+           "slsht_inverse", "slsht_inverse_alt", "slsht_submit",
+           "slsht_poll", "slsht_poll_times", "slsht_drain", "slsht_strerror", "slsht_check_args", "slsht_profile",
            "slsht_get_stats", "slsht_set_option", "slsht_mem_used", "slsht_version"]
 
 
@@ -84,6 +84,13 @@ def slsht_inverse(ctx, desc, g_in, h00, lm, n_pairs, f_out, stream=None):
                       "slsht_inverse")
 
 
+def slsht_inverse_alt(ctx, desc, g_in, h_lm, lm_in, n_in, p, lm_out, n_out, f_out, stream=None):
+    return _abi.check(_abi.load().slsht_inverse_alt(ctx, ctypes.byref(desc), _abi.ptr(g_in), _abi.ptr(h_lm),
+                                                    _abi.ptr(lm_in), int(n_in), int(p), _abi.ptr(lm_out),
+                                                    int(n_out), _abi.ptr(f_out), _stream(stream)),
+                      "slsht_inverse_alt")
+
+
 def slsht_forward_noalloc(desc, f_lm, h_lm, lm, n_pairs, g_out, stream=None):
     """slsht_forward without a context and without device allocation (static
     scratch of SLSHT_NOALLOC_SCRATCH_BYTES); g_out must be device memory."""
@@ -128,6 +135,14 @@ def slsht_submit(ctx, desc, f_lm, h_lm, lm, n_pairs, g_out):
 
 def slsht_poll(ctx, ticket):
     return _abi.load().slsht_poll(ctx, ctypes.c_uint64(ticket))
+
+
+def slsht_poll_times(ctx, ticket):
+    """(status, times): times = [queue, host issue, device, total] in ms once
+    the request has finished, else None."""
+    t = (ctypes.c_double * 4)()
+    s = _abi.load().slsht_poll_times(ctx, ctypes.c_uint64(ticket), ctypes.cast(t, ctypes.c_void_p))
+    return s, (list(t) if s != 1 else None)
 
 
 def slsht_drain(ctx, timeout_ms=60000):
@@ -243,6 +258,17 @@ class Context:
             torch.cuda.synchronize(self.device)
         return f_out
 
+    def inverse_alt(self, L_f, L_h, grid, g, h, lm_in, p, lm_out, prec=SLSHT_FP64, stream=None):
+        """f_lm for the pairs lm_out from g (device tensor, rows lm_in) without
+        h_0^0 (slsht_inverse_alt, window degree p).  Returns host complex128."""
+        import numpy as np
+        lm_in = _as_pairs(lm_in)
+        lm_out = _as_pairs(lm_out)
+        f_out = np.zeros(int(lm_out.shape[0]), dtype=np.complex128)
+        slsht_inverse_alt(self.h, make_desc(L_f, L_h, grid, prec), g, _as_c128(h), lm_in, int(lm_in.shape[0]), p,
+                          lm_out, int(lm_out.shape[0]), f_out, stream)
+        return f_out
+
     def submit(self, L_f, L_h, grid, f, h, lm, g_out, prec=SLSHT_FP64):
         lm = _as_pairs(lm)
         return slsht_submit(self.h, make_desc(L_f, L_h, grid, prec), _as_c128(f), _as_c128(h), lm,
@@ -250,6 +276,10 @@ class Context:
 
     def poll(self, ticket):
         return slsht_poll(self.h, ticket)
+
+    def poll_times(self, ticket):
+        """(status, [queue, host issue, device, total] ms or None)."""
+        return slsht_poll_times(self.h, ticket)
 
     def drain(self, timeout_ms=60000):
         return slsht_drain(self.h, timeout_ms)

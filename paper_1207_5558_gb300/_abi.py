@@ -30,6 +30,7 @@ SLSHT_OPT_WAIT_TEST = 5
 SLSHT_OPT_REAL_FIELDS = 6
 SLSHT_OPT_COUPLING = 7
 SLSHT_OPT_FP64_ARITH = 8
+SLSHT_OPT_WINDOW_ORDERS = 9
 
 SLSHT_BATCH_NO_GRAPH = 1
 SLSHT_BATCH_NO_TUNE = 2
@@ -85,6 +86,8 @@ def load(path=LIB_PATH):
         "slsht_destroy": (None, [vp]),
         "slsht_forward": (ctypes.c_int, [vp, ctypes.POINTER(slsht_desc), vp, vp, vp, i32, vp, vp]),
         "slsht_inverse": (ctypes.c_int, [vp, ctypes.POINTER(slsht_desc), vp, vp, vp, i32, vp, vp]),
+        "slsht_inverse_alt": (ctypes.c_int, [vp, ctypes.POINTER(slsht_desc), vp, vp, vp, i32, i32, vp, i32, vp,
+                                             vp]),
         "slsht_forward_noalloc": (ctypes.c_int, [ctypes.POINTER(slsht_desc), vp, vp, vp, i32, vp, vp]),
         "slsht_forward_windows": (ctypes.c_int, [vp, ctypes.POINTER(slsht_desc), vp, i32, vp, vp, i32, vp, vp]),
         "slsht_window_ellipse": (ctypes.c_int, [vp, i32, ctypes.c_double, ctypes.c_double, i32, i32, vp,
@@ -98,6 +101,7 @@ def load(path=LIB_PATH):
         "slsht_submit": (ctypes.c_int, [vp, ctypes.POINTER(slsht_desc), vp, vp, vp, i32, vp,
                                         ctypes.POINTER(u64)]),
         "slsht_poll": (ctypes.c_int, [vp, u64]),
+        "slsht_poll_times": (ctypes.c_int, [vp, u64, vp]),
         "slsht_drain": (ctypes.c_int, [vp, i64]),
         "slsht_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "slsht_last_error": (ctypes.c_char_p, []),

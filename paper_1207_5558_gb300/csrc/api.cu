@@ -132,6 +132,7 @@ struct Workspace {
   void* kexp = nullptr; size_t kexp_cap = 0;
   void* Hdd = nullptr; size_t Hdd_cap = 0;
   void* hexp = nullptr; size_t hexp_cap = 0;
+  void* qmask = nullptr; size_t qmask_cap = 0;   // the window's active orders (SLSHT_OPT_WINDOW_ORDERS)
   std::vector<int32_t> gt_work;              // host copy (source of the upload)
   bool gt_valid = false;
   int gt_Lf = 0, gt_Lh = 0;
@@ -154,18 +155,76 @@ struct Request {
   std::vector<double> f, h;
   std::vector<int32_t> lm;
   void* g_out = nullptr;
+  int n_pairs = 0;
+  int next = 0;                        // first pair not yet issued to a tick
+  int done = 0;                        // pairs whose tick has completed
+  int nt = 0, form = 0, engine = -1;   // alpha tile shape (engine -1: not chosen yet)
+  double t_submit = 0, t_admit = -1, t_issue = -1;   // host clock, ms
+  double dev_first = 1e300, dev_last = -1e300;       // device clock of its ticks, ms
+  int status = SLSHT_OK;
 };
 
-struct Slot {
-  cudaStream_t stream = nullptr;
-  Workspace ws;
-  std::unique_ptr<Request> req;
-  cudaEvent_t fin = nullptr;
+// A chunk of consecutive pairs of one request, evaluated in one serving tick.
+struct SvChunk {
+  Request* r;
+  int p0, np;
+};
+
+// One serving lane: a stream, a device arena with fixed list regions (the
+// addresses the captured graph reads) and a data region, its pinned host
+// staging copy, and the graph.  One tick in flight per lane.
+struct SvLane {
+  cudaStream_t st = nullptr;
+  cudaStream_t side[3] = {nullptr, nullptr, nullptr};   // branches of the captured graph
+  cudaEvent_t fork[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+  unsigned char* arena = nullptr;
+  unsigned char* stage = nullptr;
   bool busy = false;
+  std::vector<SvChunk> chunks;
+  double t_assemble = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  size_t g_rot_smem = 0, g_alpha_smem[3] = {0, 0, 0};
 };
 
-#define SERVE_SLOTS 4
+#define SERVE_LANES 3
 #define SERVE_MAX_QUEUE 4096
+
+// Serving arena (per lane): list capacities, sizes of the staged-input and
+// device-only data regions, and the tick budget.
+#define SV_ITEMS 1024                         // request chunks per tick
+#define SV_PAIRS (1 << 17)                    // pairs per tick (coupling lists)
+#define SV_RBLK (1 << 18)                     // rotated-window blocks per tick
+#define SV_TILES (1 << 20)                    // alpha tiles per tick and precision
+#define SV_STAGE_IN ((size_t)64 << 20)        // staged f, h and pair lists per tick
+#define SV_DEV_BYTES ((size_t)896 << 20)      // k, H and their double-float forms per tick
+#define SV_TICK_SAMPLES (32ll << 20)          // samples per tick (bounds a tick's duration)
+#define SV_CHUNK_SAMPLES (8ll << 20)          // first share of one request in a tick
+
+// Byte offsets of a serving arena's regions (the same in the pinned stage,
+// which mirrors the lists and the staged inputs).
+struct SvLayout {
+  size_t hdr, cpl, rot, item, cplp[3], kblk, rblk, tiles[3], in, dev, total, stage;
+};
+static size_t sv_up(size_t n) { return (n + 255) & ~(size_t)255; }
+static SvLayout sv_layout() {
+  SvLayout L{};
+  size_t o = 0;
+  L.hdr = o; o += 256;                                   // int counts[8], counters[4]
+  L.cpl = o; o += sv_up(sizeof(BCouple) * SV_ITEMS);
+  L.rot = o; o += sv_up(sizeof(BRot) * SV_ITEMS);
+  L.item = o; o += sv_up(sizeof(BItem) * SV_ITEMS);
+  for (int c = 0; c < 3; ++c) { L.cplp[c] = o; o += sv_up(sizeof(int2) * SV_PAIRS); }
+  L.kblk = o; o += sv_up(sizeof(BCplBlk) * SV_PAIRS);
+  L.rblk = o; o += sv_up(sizeof(BRotBlk) * SV_RBLK);
+  for (int c = 0; c < 3; ++c) { L.tiles[c] = o; o += sv_up(sizeof(BTile) * SV_TILES); }
+  L.in = o; o += SV_STAGE_IN;
+  L.stage = o;
+  L.dev = o; o += SV_DEV_BYTES;
+  L.total = o;
+  return L;
+}
 
 struct slsht_batch;
 
@@ -187,6 +246,7 @@ struct slsht_ctx {
   int opt_beta_route = 0, opt_alpha_engine = 0, opt_gaunt_table = 0, opt_wait_test = 0, opt_real_fields = 0;
   int opt_coupling = 0;
   int opt_fp64_arith = 0;
+  int opt_window_orders = 0;
   int64_t opt_chunk = 0;
   bool profile = false;
   std::vector<ProfRec> prof;
@@ -198,13 +258,18 @@ struct slsht_ctx {
   // serving
   std::mutex smu;
   std::condition_variable scv;
-  std::deque<std::unique_ptr<Request>> queue;
-  std::map<uint64_t, int> status;      // final or pending status per ticket
-  Slot slots[SERVE_SLOTS];
+  std::deque<std::unique_ptr<Request>> queue;        // submitted, not started
+  std::vector<std::unique_ptr<Request>> active;      // started, not finished (arrival order)
+  struct Final { int st; double t[4]; };
+  std::map<uint64_t, Final> status;                  // pending (SLSHT_PENDING) or final, per ticket
+  SvLane lanes[SERVE_LANES];
+  cudaEvent_t sv_ref = nullptr;                      // device-clock origin of the serving ticks
+  bool sv_ready = false;
   std::thread worker;
   bool stop = false, worker_started = false;
   uint64_t next_id = 1;
-  int inflight = 0;
+  int inflight = 0;                                  // requests in queue or active
+  uint64_t sv_ticks = 0, sv_graphs = 0;
 };
 
 struct DeviceGuard {
@@ -312,6 +377,7 @@ static void ws_release(slsht_ctx* c, Workspace& w) {
   ctx_free(c, w.kexp, w.kexp_cap);
   ctx_free(c, w.Hdd, w.Hdd_cap);
   ctx_free(c, w.hexp, w.hexp_cap);
+  ctx_free(c, w.qmask, w.qmask_cap);
   w.gt_valid = false;
   for (int i = 0; i < 2; ++i) ctx_free(c, w.stage[i], w.stage_cap[i]);
   for (int i = 0; i < 2; ++i) {
@@ -542,12 +608,21 @@ extern "C" void slsht_destroy(slsht_ctx* c) {
   }
   c->scv.notify_all();
   if (c->worker.joinable()) c->worker.join();
-  for (auto& s : c->slots) {
-    if (s.stream) cudaStreamSynchronize(s.stream);
-    ws_release(c, s.ws);
-    if (s.fin) cudaEventDestroy(s.fin);
-    if (s.stream) cudaStreamDestroy(s.stream);
+  for (auto& ln : c->lanes) {
+    if (ln.st) cudaStreamSynchronize(ln.st);
+    if (ln.exec) cudaGraphExecDestroy(ln.exec);
+    if (ln.graph) cudaGraphDestroy(ln.graph);
+    if (ln.ev_a) cudaEventDestroy(ln.ev_a);
+    if (ln.ev_b) cudaEventDestroy(ln.ev_b);
+    for (auto& sd : ln.side)
+      if (sd) cudaStreamDestroy(sd);
+    for (auto& ev : ln.fork)
+      if (ev) cudaEventDestroy(ev);
+    if (ln.st) cudaStreamDestroy(ln.st);
+    if (ln.stage) cudaFreeHost(ln.stage);
+    ctx_free(c, ln.arena, sv_layout().total);
   }
+  if (c->sv_ref) cudaEventDestroy(c->sv_ref);
   ws_release(c, c->sync_ws);
   for (auto& kv : c->delta) free_entry(c, kv.second);
   for (auto& kv : c->dtab) free_entry(c, kv.second);
@@ -594,6 +669,10 @@ extern "C" int slsht_set_option(slsht_ctx* c, int option, int64_t v) {
     case SLSHT_OPT_FP64_ARITH:
       if (v < 0 || v > 3) return SLSHT_E_ARG;
       c->opt_fp64_arith = (int)v;
+      return SLSHT_OK;
+    case SLSHT_OPT_WINDOW_ORDERS:
+      if (v < 0 || v > 2) return SLSHT_E_ARG;
+      c->opt_window_orders = (int)v;
       return SLSHT_OK;
     default:
       return SLSHT_E_ARG;
@@ -678,7 +757,7 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
   const bool host_out = !is_device_ptr(g_out);
   CK(cudaStreamWaitEvent(st, w.done, 0));
 
-  int route, tc, engine, gt_opt, wait_test, coupling, fp64_arith;
+  int route, tc, engine, gt_opt, wait_test, coupling, fp64_arith, win_orders;
   int64_t chunk_opt;
   int dd_nt = 0, dd_form = -1, tuned_engine = -1;
   int cc_nt = 0, cc_form = -1;
@@ -692,6 +771,7 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
     wait_test = ctx->opt_wait_test;
     coupling = ctx->opt_coupling;
     fp64_arith = ctx->opt_fp64_arith;
+    win_orders = ctx->opt_window_orders;
     // a tile shape the batch-plan tuner measured for this shape, if any
     // (FP64: both arithmetics allowed; FP32: the tensor cores where they apply)
     const int allowed = f64 ? 6 : ((tc_supported(Lh, Na) && Lh <= 16) ? 5 : 4);
@@ -863,21 +943,31 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
            launch_couple((const double2*)f_dev, Lf, Lh, (const int2*)lm_dev, n_pairs, (double2*)w.kc, ax));
   }
   // route 1: the window rotated to every (beta, gamma) sample, once per call
+  // (SLSHT_OPT_WINDOW_ORDERS: over the window's active orders only)
+  const uint32_t* qmask = nullptr;
+  if (win_orders && (ddx || t64 || route == 1)) {
+    CKS(ws_reserve(ctx, w, &w.qmask, &w.qmask_cap, 16));
+    // 1: exact zeros; 2: also orders at the rounding level (2^-40 of the
+    // largest coefficient for FP32_BULK, 2^-52 for FP64)
+    const int rel_exp = win_orders == 1 ? 0 : (f64 ? 52 : 40);
+    LAUNCH(SLSHT_STAGE_BETA, ax, launch_order_mask((const double2*)h_dev, Lh, rel_exp, (uint32_t*)w.qmask, ax));
+    qmask = (const uint32_t*)w.qmask;
+  }
   if (ddx || t64) {
     LAUNCH(SLSHT_STAGE_COUPLE, ax,
            launch_kdd_pairs((const double2*)w.kc, Lh, n_pairs, (float4*)w.kdd, (int*)w.kexp, ax));
     LAUNCH(SLSHT_STAGE_BETA, ax,
            launch_rotwin_dd((const double2*)h_dev, (const double*)dt, (const double2*)eg, Lh, Nb, Ng,
-                            (float4*)w.Hdd, (int*)w.hexp, ax));
+                            (float4*)w.Hdd, (int*)w.hexp, ax, qmask));
   } else if (route == 1) {
     if (f64)
       LAUNCH(SLSHT_STAGE_BETA, ax,
              launch_rotwin_f64((const double2*)h_dev, (const double*)dt, (const double2*)eg, Lh, Nb, Ng,
-                               (double2*)w.H, ax));
+                               (double2*)w.H, ax, qmask));
     else
       LAUNCH(SLSHT_STAGE_BETA, ax,
              launch_rotwin_f32((const double2*)h_dev, (const float*)dt, (const float2*)eg, Lh, Nb, Ng,
-                               (float2*)w.H, ax));
+                               (float2*)w.H, ax, qmask));
   }
   void* Xb[2] = {w.X, w.X2};
   int ci = 0;
@@ -972,15 +1062,23 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
         std::lock_guard<std::mutex> g(ctx->mu);
         ctx->opt_wait_test = 0;
       }
-    } else if (wide) {
-      LAUNCH(SLSHT_STAGE_ALPHA, st,
-             launch_alpha_tcw(X, etab, Lh, Na, Nb, Ng, np, (float2*)gdst, ctx->num_sms, sl, st));
-    } else if (tc) {
-      LAUNCH(SLSHT_STAGE_ALPHA, st,
-             launch_alpha_tc(X, etab, Lh, Na, Nb, Ng, np, (float2*)gdst, ctx->num_sms, sl, st));
-    } else if (t64) {
-      LAUNCH(SLSHT_STAGE_ALPHA, st,
-             launch_alpha_tc64(X, etab, Lh, Na, Nb, Ng, np, (double2*)gdst, ctx->num_sms, sl, st));
+    } else if (wide || tc || t64) {
+      // the separate-producer tensor-core kernels; SLSHT_OPT_WAIT_TEST arms
+      // the first launch's withheld operand (thread-local, consumed by it)
+      if (ci == 0 && wait_test) {
+        tc_arm_wait_test();
+        std::lock_guard<std::mutex> g(ctx->mu);
+        ctx->opt_wait_test = 0;
+      }
+      if (wide)
+        LAUNCH(SLSHT_STAGE_ALPHA, st,
+               launch_alpha_tcw(X, etab, Lh, Na, Nb, Ng, np, (float2*)gdst, ctx->num_sms, sl, st));
+      else if (tc)
+        LAUNCH(SLSHT_STAGE_ALPHA, st,
+               launch_alpha_tc(X, etab, Lh, Na, Nb, Ng, np, (float2*)gdst, ctx->num_sms, sl, st));
+      else
+        LAUNCH(SLSHT_STAGE_ALPHA, st,
+               launch_alpha_tc64(X, etab, Lh, Na, Nb, Ng, np, (double2*)gdst, ctx->num_sms, sl, st));
     } else if (f64) {
       LAUNCH(SLSHT_STAGE_ALPHA, st,
              split ? launch_alpha_split_f64((const double2*)X, (const double2*)csa, Lh, Na, (int)J, np,
@@ -1073,9 +1171,11 @@ extern "C" int slsht_forward(slsht_ctx* ctx, const slsht_desc* desc, const doubl
   // pair validation needs host-visible indices
   std::vector<int32_t> lm_host;
   const int32_t* lmv = lm;
-  if (is_device_ptr(lm)) {
+  if (is_device_ptr(lm)) {            // read on the caller's stream, after the work queued there
     lm_host.resize(2 * (size_t)n_pairs);
-    CK(cudaMemcpy(lm_host.data(), lm, sizeof(int32_t) * 2 * (size_t)n_pairs, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpyAsync(lm_host.data(), lm, sizeof(int32_t) * 2 * (size_t)n_pairs, cudaMemcpyDeviceToHost,
+                       (cudaStream_t)stream));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
     lmv = lm_host.data();
   }
   CKS(check_pairs(desc, lmv, n_pairs));
@@ -1095,9 +1195,11 @@ extern "C" int slsht_forward_windows(slsht_ctx* ctx, const slsht_desc* desc, con
   DeviceGuard g(ctx->device);
   std::vector<int32_t> lm_host;
   const int32_t* lmv = lm;
-  if (is_device_ptr(lm)) {
+  if (is_device_ptr(lm)) {            // read on the caller's stream, after the work queued there
     lm_host.resize(2 * (size_t)n_pairs);
-    CK(cudaMemcpy(lm_host.data(), lm, sizeof(int32_t) * 2 * (size_t)n_pairs, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpyAsync(lm_host.data(), lm, sizeof(int32_t) * 2 * (size_t)n_pairs, cudaMemcpyDeviceToHost,
+                       (cudaStream_t)stream));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
     lmv = lm_host.data();
   }
   CKS(check_pairs(desc, lmv, n_pairs));
@@ -1161,9 +1263,11 @@ extern "C" int slsht_inverse(slsht_ctx* ctx, const slsht_desc* desc, const void*
   if (!is_device_ptr(g_in)) return SLSHT_E_ARG;
   std::vector<int32_t> lm_host;
   const int32_t* lmv = lm;
-  if (is_device_ptr(lm)) {
+  if (is_device_ptr(lm)) {            // read on the caller's stream, after the work queued there
     lm_host.resize(2 * (size_t)n_pairs);
-    CK(cudaMemcpy(lm_host.data(), lm, sizeof(int32_t) * 2 * (size_t)n_pairs, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpyAsync(lm_host.data(), lm, sizeof(int32_t) * 2 * (size_t)n_pairs, cudaMemcpyDeviceToHost,
+                       (cudaStream_t)stream));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
     lmv = lm_host.data();
   }
   CKS(check_pairs(desc, lmv, n_pairs));
@@ -1204,6 +1308,115 @@ extern "C" int slsht_inverse(slsht_ctx* ctx, const slsht_desc* desc, const void*
     CK(cudaMemcpyAsync(f_out, fdev, sizeof(double2) * (size_t)n_pairs, cudaMemcpyDeviceToHost, st));
   }
   CK(cudaEventRecord(w.done, st));
+  return SLSHT_OK;
+}
+
+// Host copy of a small argument array on the caller's stream (after the
+// work queued there) into out; host memory is copied directly.
+static int read_arg(const void* src, size_t bytes, cudaStream_t st, void* out) {
+  if (is_device_ptr(src)) {
+    CK(cudaMemcpyAsync(out, src, bytes, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  } else {
+    std::memcpy(out, src, bytes);
+  }
+  return SLSHT_OK;
+}
+
+extern "C" int slsht_inverse_alt(slsht_ctx* ctx, const slsht_desc* desc, const void* g_in, const double* h_lm,
+                                 const int32_t* lm_in, int32_t n_in, int32_t p, const int32_t* lm_out,
+                                 int32_t n_out, double* f_out, void* stream) {
+  if (!ctx) return SLSHT_E_ARG;
+  CKS(check_desc(desc));
+  if (n_in < 0 || n_out < 0) return SLSHT_E_ARG;
+  if (n_out == 0) return SLSHT_OK;
+  if (!g_in || !h_lm || !lm_in || !lm_out || !f_out || n_in == 0) return SLSHT_E_ARG;
+  const int Lf = desc->L_f, Lh = desc->L_h, Na = desc->n_alpha, Nb = desc->n_beta, Ng = desc->n_gamma;
+  if (p < 0 || p >= Lh) return SLSHT_E_ARG;
+  if (Na < Lh + p || Nb < Lh + p || Ng < Lh + p) return SLSHT_E_ARG;
+  DeviceGuard g(ctx->device);
+  if (!is_device_ptr(g_in)) return SLSHT_E_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int K = 2 * p + 1;
+  std::vector<int32_t> lin(2 * (size_t)n_in), lout(2 * (size_t)n_out);
+  std::vector<double> h(2 * (size_t)Lh * Lh);
+  CKS(read_arg(lm_in, sizeof(int32_t) * lin.size(), st, lin.data()));
+  CKS(read_arg(lm_out, sizeof(int32_t) * lout.size(), st, lout.data()));
+  CKS(read_arg(h_lm, sizeof(double) * h.size(), st, h.data()));
+  CKS(check_pairs(desc, lin.data(), n_in));
+  // the window's degree-p coefficients and energy (the condition replacing h_0^0 != 0)
+  std::vector<double2> hp(K);
+  double Ep = 0.0;
+  for (int q = -p; q <= p; ++q) {
+    const size_t i = (size_t)p * p + p + q;
+    hp[q + p] = make_double2(h[2 * i], h[2 * i + 1]);
+    Ep += h[2 * i] * h[2 * i] + h[2 * i + 1] * h[2 * i + 1];
+  }
+  if (!(Ep > 0.0)) {
+    slsht_record_error_text("slsht_inverse_alt: the window has no energy at degree p");
+    return SLSHT_E_H00;
+  }
+  // every output needs the rows of (L + p, M + q), |q| <= p
+  std::map<std::pair<int, int>, int> row;
+  for (int32_t i = 0; i < n_in; ++i) row.emplace(std::make_pair(lin[2 * i], lin[2 * i + 1]), i);
+  std::vector<int> rows((size_t)n_out * K);
+  for (int32_t o = 0; o < n_out; ++o) {
+    const int L = lout[2 * o], M = lout[2 * o + 1];
+    if (L < 0 || L >= Lf || M < -L || M > L) return SLSHT_E_ARG;
+    for (int q = -p; q <= p; ++q) {
+      auto it = row.find(std::make_pair(L + p, M + q));
+      if (it == row.end()) {
+        slsht_record_error_text("slsht_inverse_alt: g lacks a pair (L + p, M + q) that an output needs");
+        return SLSHT_E_ARG;
+      }
+      rows[(size_t)o * K + q + p] = it->second;
+    }
+  }
+  std::lock_guard<std::mutex> serial(ctx->sync_mu);
+  Workspace& w = ctx->sync_ws;
+  CK(cudaStreamWaitEvent(st, w.done, 0));
+  const double *wb, *dt;
+  const void *ea, *eg;
+  {
+    std::lock_guard<std::mutex> gl(ctx->mu);
+    CKS(get_wbeta(ctx, Nb, st, &wb));
+    const void* d = nullptr;
+    CKS(get_dtab(ctx, Lh, Nb, SLSHT_FP64, st, &d));
+    dt = (const double*)d;
+    CKS(get_phase(ctx, Na, K, -p, desc->prec == SLSHT_FP64 ? SLSHT_FP64 : SLSHT_FP32_BULK, st, &ea));
+    CKS(get_phase(ctx, Ng, K, -p, SLSHT_FP64, st, &eg));
+  }
+  // scratch in the synchronous workspace: partial sums, khat, f (device),
+  // then the host-built arrays (window row, outputs, row map)
+  const size_t ncb = (size_t)ialt_col_blocks(Nb, Ng);
+  const size_t n_part = (size_t)n_in * ncb * K, n_khat = (size_t)n_in * K;
+  CKS(ws_reserve(ctx, w, &w.kc, &w.kc_cap, sizeof(double2) * (n_part + n_khat + (size_t)n_out)));
+  double2* partial = (double2*)w.kc;
+  double2* khat = partial + n_part;
+  double2* fdev = is_device_ptr(f_out) ? (double2*)f_out : khat + n_khat;
+  const size_t up_bytes = sizeof(double2) * K + sizeof(int32_t) * lout.size() + sizeof(int) * rows.size();
+  CKS(ws_reserve(ctx, w, &w.lm, &w.lm_cap, up_bytes));
+  double2* hp_d = (double2*)w.lm;
+  int2* lout_d = (int2*)(hp_d + K);
+  int* rows_d = (int*)(lout_d + n_out);
+  {
+    StageTimer t(ctx, SLSHT_STAGE_COPY, st);
+    CK(cudaMemcpyAsync(hp_d, hp.data(), sizeof(double2) * K, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(lout_d, lout.data(), sizeof(int32_t) * lout.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(rows_d, rows.data(), sizeof(int) * rows.size(), cudaMemcpyHostToDevice, st));
+  }
+  const double pi = 3.14159265358979323846;
+  const double scale = (2.0 * pi / Na) * (2.0 * pi / Ng) * (2.0 * p + 1.0) / (8.0 * pi * pi * Ep);
+  LAUNCH(SLSHT_STAGE_INVERSE, st,
+         launch_inverse_alt(g_in, desc->prec == SLSHT_FP64 ? 0 : 1, wb, dt, Lh, hp_d, ea, (const double2*)eg, Na, Nb,
+                            Ng, p, n_in, partial, scale, khat, lout_d, rows_d, n_out, fdev, st));
+  if ((void*)fdev != (void*)f_out) {
+    StageTimer t(ctx, SLSHT_STAGE_COPY, st);
+    CK(cudaMemcpyAsync(f_out, fdev, sizeof(double2) * (size_t)n_out, cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaEventRecord(w.done, st));
+  // the host arrays above are read by the stream's copies: wait for them
+  CK(cudaStreamSynchronize(st));
   return SLSHT_OK;
 }
 
@@ -1932,6 +2145,12 @@ extern "C" int slsht_tune(slsht_ctx* ctx, const slsht_desc* desc) {
     const int fl = SLSHT_BATCH_NO_GRAPH | (desc->prec == SLSHT_FP64 ? SLSHT_BATCH_NO_TC : 0);
     st = slsht_batch_create(ctx, 1, &it, fl, nullptr, &b);
     if (st == SLSHT_OK) slsht_batch_destroy(b);
+    // FP32_BULK: also the CUDA-core shapes alone (the serving path's engines)
+    if (st == SLSHT_OK && desc->prec != SLSHT_FP64) {
+      b = nullptr;
+      st = slsht_batch_create(ctx, 1, &it, SLSHT_BATCH_NO_GRAPH | SLSHT_BATCH_NO_TC, nullptr, &b);
+      if (st == SLSHT_OK) slsht_batch_destroy(b);
+    }
   }
   ctx_free(ctx, gd, gbytes);
   ctx_free(ctx, hd, sizeof(double) * h.size());
@@ -1987,78 +2206,454 @@ extern "C" void slsht_batch_destroy(slsht_batch* b) {
 }
 
 // ---------------------------------------------------------------- serving
-// Continuous batching: requests wait in a FIFO; the worker admits the head
-// request as soon as a stream slot is free and its scratch fits the memory
-// budget, launches it on that slot's stream (so it overlaps with requests
-// already on the GPU) and retires slots whose completion event has fired.
-static size_t request_scratch_estimate(const slsht_desc* d, int32_t n_pairs) {
-  const int Lh = d->L_h, K = 2 * Lh - 1;
-  const size_t J = (size_t)d->n_beta * d->n_gamma;
-  const size_t x = (d->prec == SLSHT_FP64 ? sizeof(double2) : sizeof(float2)) * (size_t)K * J;
-  const size_t P = std::max<size_t>(1, std::min<size_t>((size_t)n_pairs, ((size_t)96 << 20) / std::max<size_t>(1, x)));
-  return P * (x + sizeof(double2) * Lh * Lh) + sizeof(double2) * ((size_t)d->L_f * d->L_f + Lh * Lh) +
-         sizeof(int2) * (size_t)n_pairs;
+// Continuous batching on persistent batched kernels under a captured graph.
+// A worker thread turns the admitted requests into ticks: each tick takes a
+// chunk of pairs from every started request (oldest first, at most
+// SV_CHUNK_SAMPLES a request, SV_TICK_SAMPLES a tick) and from new requests
+// as space allows, so a large request is spread over several ticks and small
+// requests that arrive behind it enter the next tick.  A tick's work lists
+// (couplings, rotated windows, alpha tiles) are built on the host in a
+// pinned stage, copied into the lane's device arena, and evaluated by one
+// replay of the lane's captured graph:
+//   k_serve_couple x3 (3j chains by window band), k_batch_kdd, k_batch_rotwin,
+//   k_batch_alpha x3 (FP64, FP32, double-float; persistent, tiles from a counter),
+// whose launch configurations are fixed and whose work counts are read from
+// the arena's header.  The graph is captured again only when a tick needs more
+// shared memory than the captured configuration holds.  Two lanes alternate,
+// so the host builds one tick while the other runs, and their kernels overlap
+// on the device.  Admission is by memory: a chunk joins a tick only while its
+// inputs, couplings and rotated window fit the lane's arena.  The alpha tile
+// shape of a request's grid shape comes from the context's tuner cache
+// (CUDA-core engines), else the built-in rule, so that a request's result does
+// not depend on the requests it shares ticks with.
+static double sv_now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+static int sv_init(slsht_ctx* c) {
+  if (c->sv_ready) return SLSHT_OK;
+  const SvLayout L = sv_layout();
+  for (auto& ln : c->lanes) {
+    CK(cudaStreamCreateWithFlags(&ln.st, cudaStreamNonBlocking));
+    for (auto& sd : ln.side) CK(cudaStreamCreateWithFlags(&sd, cudaStreamNonBlocking));
+    for (auto& ev : ln.fork) CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CK(cudaEventCreate(&ln.ev_a));
+    CK(cudaEventCreate(&ln.ev_b));
+    void* a = nullptr;
+    CKS(ctx_alloc(c, L.total, &a));
+    ln.arena = (unsigned char*)a;
+    CK(cudaHostAlloc((void**)&ln.stage, L.stage, cudaHostAllocDefault));
+  }
+  CK(cudaEventCreate(&c->sv_ref));
+  CK(cudaEventRecord(c->sv_ref, c->lanes[0].st));
+  CK(cudaEventSynchronize(c->sv_ref));
+  c->sv_ready = true;
+  return SLSHT_OK;
+}
+
+// Bytes a chunk of np pairs needs in the device-only region, and its staged inputs.
+static size_t sv_dev_bytes(const Request& r, int np) {
+  const slsht_desc& d = r.desc;
+  const size_t n2 = (size_t)d.L_h * d.L_h, J = (size_t)d.n_beta * d.n_gamma;
+  size_t b = sv_up(sizeof(double2) * np * n2);
+  if (r.engine == ENG_DD)
+    b += sv_up(sizeof(float4) * np * n2) + sv_up(sizeof(int) * np) + sv_up(sizeof(float4) * h_elems(J, (int)n2)) + 256;
+  else
+    b += sv_up(el2_of(d.prec) * h_elems(J, (int)n2));
+  return b;
+}
+static size_t sv_in_bytes(const Request& r, int np) {
+  return sv_up(sizeof(double2) * (size_t)r.desc.L_f * r.desc.L_f) + sv_up(sizeof(double2) * (size_t)r.desc.L_h * r.desc.L_h) +
+         sv_up(sizeof(int2) * (size_t)np);
+}
+static long long sv_tiles_per_pair(const Request& r) {
+  const long long J = (long long)r.desc.n_beta * r.desc.n_gamma;
+  return (J + r.nt - 1) / r.nt;
+}
+static int sv_rblk_count(const Request& r) {
+  const RotChunks ch = rot_chunks(r.desc.L_h, r.desc.n_gamma, r.engine == ENG_NATIVE && r.desc.prec != SLSHT_FP64
+                                                                 ? sizeof(float2) : sizeof(double2));
+  return ((r.desc.n_beta + ROTWIN_NB - 1) / ROTWIN_NB) * r.desc.L_h * ch.nq * ch.nc;
+}
+
+// The alpha tile shape of a request: the tuner's cache for its grid shape on
+// CUDA cores, else the rule of SLSHT_BATCH_NO_TUNE.
+static void sv_choose(slsht_ctx* c, Request& r) {
+  const slsht_desc& d = r.desc;
+  const long long J = (long long)d.n_beta * d.n_gamma;
+  const int allowed = d.prec == SLSHT_FP64 ? 6 : 4;
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    auto f = c->tune.find(std::make_tuple((int)d.prec, d.L_h, d.n_alpha, d.n_beta, d.n_gamma, allowed));
+    if (f != c->tune.end()) {
+      std::tie(r.nt, r.form, r.engine) = f->second;
+      return;
+    }
+  }
+  r.engine = d.prec == SLSHT_FP64 ? ENG_DD : ENG_NATIVE;
+  r.nt = r.engine == ENG_DD ? dd_rule_cols(d.L_h, J) : batch_rule_nt(1, d.L_h, J);
+  r.form = alpha_split_factor(d.L_h, d.n_alpha);
+}
+
+// Captures the lane's launch sequence with shared-memory sizes rot_smem and
+// alpha_smem[3] (the graph reads the arena's fixed list addresses).
+static int sv_capture(slsht_ctx* c, SvLane& ln, size_t rot_smem, const size_t* alpha_smem) {
+  const SvLayout L = sv_layout();
+  unsigned char* A = ln.arena;
+  const int* hdr = (const int*)(A + L.hdr);
+  int* ctr = (int*)(A + L.hdr) + 8;
+  const int sms = c->num_sms;
+  int agrid[3];
+  for (int pi = 0; pi < 3; ++pi) agrid[pi] = sms * batch_alpha_occupancy(pi, alpha_smem[pi]);
+  const int rgrid = sms * batch_rotwin_occupancy(rot_smem);
+  if (ln.exec) { cudaGraphExecDestroy(ln.exec); ln.exec = nullptr; }
+  if (ln.graph) { cudaGraphDestroy(ln.graph); ln.graph = nullptr; }
+  // branches: {couplings, double-float k} || {rotated windows}, then the
+  // three alpha kernels side by side (each takes tiles of its own list)
+  CK(cudaStreamBeginCapture(ln.st, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaMemsetAsync(ctr, 0, 4 * sizeof(int), ln.st);
+  if (e == cudaSuccess) e = cudaEventRecord(ln.fork[0], ln.st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ln.side[0], ln.fork[0], 0);
+  if (e == cudaSuccess)
+    e = launch_batch_rotwin_n((const BRot*)(A + L.rot), (const BRotBlk*)(A + L.rblk), hdr + 4, rgrid, rot_smem,
+                              ln.side[0]);
+  for (int cls = 0; cls < 3 && e == cudaSuccess; ++cls)
+    e = launch_serve_couple(cls, (const BCouple*)(A + L.cpl), (const int2*)(A + L.cplp[cls]), hdr + cls, sms * 4,
+                            ln.st);
+  if (e == cudaSuccess)
+    e = launch_batch_kdd_n((const BCouple*)(A + L.cpl), (const BCplBlk*)(A + L.kblk), hdr + 3, sms * 4, ln.st);
+  if (e == cudaSuccess) e = cudaEventRecord(ln.fork[1], ln.side[0]);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ln.st, ln.fork[1], 0);
+  if (e == cudaSuccess) e = cudaEventRecord(ln.fork[0], ln.st);
+  for (int pi = 0; pi < 3 && e == cudaSuccess; ++pi) {
+    cudaStream_t bs = pi == 0 ? ln.st : ln.side[pi];
+    if (pi > 0) e = cudaStreamWaitEvent(bs, ln.fork[0], 0);
+    if (e == cudaSuccess)
+      e = launch_batch_alpha_n(pi, (const BItem*)(A + L.item), (const BTile*)(A + L.tiles[pi]), hdr + 5 + pi,
+                               ctr + pi, agrid[pi], alpha_smem[pi], bs);
+    if (e == cudaSuccess && pi > 0) e = cudaEventRecord(ln.fork[1 + pi], bs);
+  }
+  for (int pi = 1; pi < 3 && e == cudaSuccess; ++pi) e = cudaStreamWaitEvent(ln.st, ln.fork[1 + pi], 0);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(ln.st, &graph);
+  ln.graph = graph;
+  if (e != cudaSuccess) { record_cuda_error("serving graph launch", e); return SLSHT_E_CUDA; }
+  if (e2 != cudaSuccess) { record_cuda_error("cudaStreamEndCapture", e2); return SLSHT_E_CUDA; }
+  CK(cudaGraphInstantiate(&ln.exec, ln.graph, 0));
+  ln.g_rot_smem = rot_smem;
+  for (int pi = 0; pi < 3; ++pi) ln.g_alpha_smem[pi] = alpha_smem[pi];
+  c->sv_graphs++;
+  return SLSHT_OK;
+}
+
+// Builds one tick on a free lane from the started and queued requests
+// (c->smu held by the caller, released around the CUDA calls).  Returns the
+// number of chunks issued (0: nothing to do), or a negative status.
+static int sv_tick(slsht_ctx* c, SvLane& ln, std::unique_lock<std::mutex>& lk) {
+  const SvLayout L = sv_layout();
+  // requests that may join: started ones first (arrival order), then the queue
+  while (!c->queue.empty() && c->active.size() < SV_ITEMS) {
+    c->active.push_back(std::move(c->queue.front()));
+    c->queue.pop_front();
+    sv_choose(c, *c->active.back());
+  }
+  std::vector<SvChunk> ch;
+  long long samples = 0, tiles[3] = {0, 0, 0};
+  size_t dev = 0, in = 0;
+  int npairs[3] = {0, 0, 0}, nkblk = 0, nrblk = 0;
+  for (auto& up : c->active) {
+    Request& r = *up;
+    if (r.next >= r.n_pairs) continue;
+    if (samples >= SV_TICK_SAMPLES || (int)ch.size() >= SV_ITEMS) break;
+    const slsht_desc& d = r.desc;
+    const long long spp = (long long)d.n_alpha * d.n_beta * d.n_gamma;
+    int np = (int)std::min<long long>(r.n_pairs - r.next, std::max<long long>(1, SV_CHUNK_SAMPLES / spp));
+    np = (int)std::min<long long>(np, std::max<long long>(1, (SV_TICK_SAMPLES - samples) / spp));
+    const int cls = d.L_h <= 16 ? 0 : (d.L_h <= 32 ? 1 : 2);
+    const int kp = r.engine == ENG_DD ? 2 : (d.prec == SLSHT_FP64 ? 0 : 1);
+    const int rb = sv_rblk_count(r);
+    const long long tpp = sv_tiles_per_pair(r);
+    // the largest np that fits every region and list
+    auto fits = [&](int n) {
+      return dev + sv_dev_bytes(r, n) <= SV_DEV_BYTES && in + sv_in_bytes(r, n) <= SV_STAGE_IN &&
+             npairs[cls] + n <= SV_PAIRS && (r.engine != ENG_DD || nkblk + n <= SV_PAIRS) && nrblk + rb <= SV_RBLK &&
+             tiles[kp] + tpp * n <= SV_TILES;
+    };
+    while (np > 0 && !fits(np)) np /= 2;
+    if (np == 0) break;
+    ch.push_back({&r, r.next, np});
+    dev += sv_dev_bytes(r, np);
+    in += sv_in_bytes(r, np);
+    npairs[cls] += np;
+    if (r.engine == ENG_DD) nkblk += np;
+    nrblk += rb;
+    tiles[kp] += tpp * np;
+    samples += spp * np;
+    if (r.t_admit < 0) r.t_admit = sv_now_ms();
+    r.next += np;
+  }
+  // a tick with room left grows its chunks (oldest request first) up to
+  // the tick's budget: a request alone on the GPU is not held to one share
+  for (SvChunk& k : ch) {
+    Request& r = *k.r;
+    const slsht_desc& d = r.desc;
+    const long long spp = (long long)d.n_alpha * d.n_beta * d.n_gamma;
+    if (samples >= SV_TICK_SAMPLES || r.next >= r.n_pairs) continue;
+    int extra = (int)std::min<long long>(r.n_pairs - r.next, (SV_TICK_SAMPLES - samples) / spp);
+    const int cls = d.L_h <= 16 ? 0 : (d.L_h <= 32 ? 1 : 2);
+    const int kp = r.engine == ENG_DD ? 2 : (d.prec == SLSHT_FP64 ? 0 : 1);
+    const long long tpp = sv_tiles_per_pair(r);
+    auto fits = [&](int n) {
+      return dev - sv_dev_bytes(r, k.np) + sv_dev_bytes(r, k.np + n) <= SV_DEV_BYTES &&
+             in - sv_in_bytes(r, k.np) + sv_in_bytes(r, k.np + n) <= SV_STAGE_IN && npairs[cls] + n <= SV_PAIRS &&
+             (r.engine != ENG_DD || nkblk + n <= SV_PAIRS) && tiles[kp] + tpp * n <= SV_TILES;
+    };
+    while (extra > 0 && !fits(extra)) extra /= 2;
+    if (extra == 0) continue;
+    dev += sv_dev_bytes(r, k.np + extra) - sv_dev_bytes(r, k.np);
+    in += sv_in_bytes(r, k.np + extra) - sv_in_bytes(r, k.np);
+    npairs[cls] += extra;
+    if (r.engine == ENG_DD) nkblk += extra;
+    tiles[kp] += tpp * extra;
+    samples += spp * extra;
+    k.np += extra;
+    r.next += extra;
+  }
+  if (ch.empty()) return 0;
+  const double t0 = sv_now_ms();
+  lk.unlock();
+  // ---- fill the stage: lists and staged inputs; device addresses in the arena
+  unsigned char* S = ln.stage;
+  unsigned char* A = ln.arena;
+  int* hdr = (int*)(S + L.hdr);
+  std::memset(hdr, 0, 64);
+  BCouple* cpl = (BCouple*)(S + L.cpl);
+  BRot* rot = (BRot*)(S + L.rot);
+  BItem* item = (BItem*)(S + L.item);
+  int2* cplp[3] = {(int2*)(S + L.cplp[0]), (int2*)(S + L.cplp[1]), (int2*)(S + L.cplp[2])};
+  BCplBlk* kblk = (BCplBlk*)(S + L.kblk);
+  BRotBlk* rblk = (BRotBlk*)(S + L.rblk);
+  BTile* tl[3] = {(BTile*)(S + L.tiles[0]), (BTile*)(S + L.tiles[1]), (BTile*)(S + L.tiles[2])};
+  size_t in_off = 0, dev_off = 0;
+  size_t rot_smem = ln.g_rot_smem, asmem[3] = {ln.g_alpha_smem[0], ln.g_alpha_smem[1], ln.g_alpha_smem[2]};
+  int st = SLSHT_OK;
+  CK(cudaEventRecord(ln.ev_a, ln.st));
+  // items in decreasing tile cost, so the large tiles start first
+  std::vector<int> order(ch.size());
+  for (size_t i = 0; i < ch.size(); ++i) order[i] = (int)i;
+  auto cost = [&](const SvChunk& k) {
+    const slsht_desc& d = k.r->desc;
+    return (double)k.r->nt * (4.0 * d.L_h * d.L_h + d.n_alpha * alpha_form_cost(d.L_h, k.r->form));
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(ch[a]) > cost(ch[b]); });
+  for (size_t ii = 0; ii < ch.size() && st == SLSHT_OK; ++ii) {
+    const SvChunk& k = ch[ii];
+    const Request& r = *k.r;
+    const slsht_desc& d = r.desc;
+    const int Lh = d.L_h, n2 = Lh * Lh, K = 2 * Lh - 1, np = k.np;
+    const size_t J = (size_t)d.n_beta * d.n_gamma;
+    const bool dd = r.engine == ENG_DD;
+    const int rprec = (dd || d.prec == SLSHT_FP64) ? SLSHT_FP64 : SLSHT_FP32_BULK;   // rotated window's
+    // staged inputs
+    const size_t fo = in_off, fb = sizeof(double2) * (size_t)d.L_f * d.L_f;
+    std::memcpy(S + L.in + fo, r.f.data(), fb);
+    in_off += sv_up(fb);
+    const size_t ho = in_off, hb = sizeof(double2) * (size_t)n2;
+    std::memcpy(S + L.in + ho, r.h.data(), hb);
+    in_off += sv_up(hb);
+    const size_t lo = in_off, lb = sizeof(int2) * (size_t)np;
+    std::memcpy(S + L.in + lo, r.lm.data() + 2 * (size_t)k.p0, lb);
+    in_off += sv_up(lb);
+    // device-only data
+    auto dalloc = [&](size_t bytes) { unsigned char* p = A + L.dev + dev_off; dev_off += sv_up(bytes); return p; };
+    BCouple cc{};
+    cc.f = (const double2*)(A + L.in + fo);
+    cc.lm = (const int2*)(A + L.in + lo);
+    cc.kc = (double2*)dalloc(sizeof(double2) * (size_t)np * n2);
+    cc.Lh = Lh;
+    cc.npairs = np;
+    cc.Lf = d.L_f;
+    BRot rr{};
+    rr.h = (const double2*)(A + L.in + ho);
+    rr.prec = rprec == SLSHT_FP64 ? 0 : 1;
+    rr.Lh = Lh;
+    rr.Nb = d.n_beta;
+    rr.Ng = d.n_gamma;
+    const RotChunks rc = rot_chunks(Lh, d.n_gamma, el2_of(rprec));
+    rr.QC = rc.QC; rr.CC = rc.CC; rr.nq = rc.nq; rr.nc = rc.nc;
+    rot_smem = std::max(rot_smem, rc.smem(Lh, el2_of(rprec)));
+    if (dd) {
+      cc.kdd = (float4*)dalloc(sizeof(float4) * (size_t)np * n2);
+      cc.kexp = (int*)dalloc(sizeof(int) * (size_t)np);
+      rr.Hdd = (float4*)dalloc(sizeof(float4) * h_elems(J, n2));
+      rr.hexp = (int*)dalloc(16);
+    } else {
+      rr.H = dalloc(el2_of(d.prec) * h_elems(J, n2));
+    }
+    BItem bi{};
+    {
+      std::lock_guard<std::mutex> g(c->mu);
+      const void *dt = nullptr, *eg = nullptr, *csa = nullptr;
+      st = get_dtab(c, Lh, d.n_beta, rprec, ln.st, &dt);
+      if (st == SLSHT_OK) st = get_phase(c, d.n_gamma, K, -(Lh - 1), rprec, ln.st, &eg);
+      const int aprec = dd ? PREC_DD : d.prec;
+      if (st == SLSHT_OK)
+        st = r.form > 0 ? get_phase(c, d.n_alpha, K, -(Lh - 1), aprec, ln.st, &csa)
+                        : get_phase(c, d.n_alpha, Lh, 0, aprec, ln.st, &csa);
+      rr.dt = dt;
+      rr.eg = eg;
+      bi.csa = csa;
+    }
+    const int idx = (int)ii;
+    const int cls = Lh <= 16 ? 0 : (Lh <= 32 ? 1 : 2);
+    for (int pr = 0; pr < np; ++pr) cplp[cls][hdr[cls]++] = make_int2(idx, pr);
+    if (dd)
+      for (int pr = 0; pr < np; ++pr) kblk[hdr[3]++] = BCplBlk{idx, pr};
+    for (int bb = 0; bb < d.n_beta; bb += ROTWIN_NB)
+      for (int pp = 0; pp < Lh; ++pp)
+        for (int z = 0; z < rc.nq * rc.nc; ++z) rblk[hdr[4]++] = BRotBlk{idx, bb, pp, z};
+    bi.kc = cc.kc;
+    bi.H = dd ? (const void*)rr.Hdd : (const void*)rr.H;
+    const size_t per_pair_g = (size_t)d.n_alpha * J * el2_of(d.prec);
+    bi.g = (unsigned char*)r.g_out + per_pair_g * (size_t)k.p0;
+    bi.kdd = cc.kdd;
+    bi.kexp = cc.kexp;
+    bi.hexp = rr.hexp;
+    bi.prec = dd ? 2 : (d.prec == SLSHT_FP64 ? 0 : 1);
+    bi.Lh = Lh;
+    bi.Na = d.n_alpha;
+    bi.J = (int)J;
+    bi.nt = r.nt;
+    bi.form = std::max(r.form, 0);
+    cpl[idx] = cc;
+    rot[idx] = rr;
+    item[idx] = bi;
+    asmem[bi.prec] = std::max(asmem[bi.prec], batch_alpha_smem(bi.prec, Lh, r.nt));
+  }
+  for (int oi : order) {          // tiles in decreasing cost
+    const SvChunk& k = ch[oi];
+    const BItem& bi = item[oi];
+    for (int pr = 0; pr < k.np; ++pr)
+      for (int j0 = 0; j0 < bi.J; j0 += bi.nt) tl[bi.prec][hdr[5 + bi.prec]++] = BTile{oi, pr, pr, j0};
+  }
+  // the graph's launch configuration must hold this tick's shared memory
+  if (st == SLSHT_OK && (!ln.exec || rot_smem > ln.g_rot_smem || asmem[0] > ln.g_alpha_smem[0] ||
+                         asmem[1] > ln.g_alpha_smem[1] || asmem[2] > ln.g_alpha_smem[2])) {
+    for (int pi = 0; pi < 3; ++pi)
+      if (asmem[pi] == 0) asmem[pi] = batch_alpha_smem(pi, 1, 32);
+    if (rot_smem == 0) rot_smem = rot_chunks(1, 1, sizeof(double2)).smem(1, sizeof(double2));
+    st = sv_capture(c, ln, rot_smem, asmem);
+  }
+  // copies of the used parts of the stage, then the graph
+  auto put = [&](size_t off, size_t bytes) -> int {
+    if (bytes == 0) return SLSHT_OK;
+    CK(cudaMemcpyAsync(A + off, S + off, bytes, cudaMemcpyHostToDevice, ln.st));
+    return SLSHT_OK;
+  };
+  const int n = (int)ch.size();
+  if (st == SLSHT_OK) st = put(L.hdr, 64);
+  if (st == SLSHT_OK) st = put(L.cpl, sizeof(BCouple) * n);
+  if (st == SLSHT_OK) st = put(L.rot, sizeof(BRot) * n);
+  if (st == SLSHT_OK) st = put(L.item, sizeof(BItem) * n);
+  for (int cl = 0; cl < 3 && st == SLSHT_OK; ++cl) st = put(L.cplp[cl], sizeof(int2) * hdr[cl]);
+  if (st == SLSHT_OK) st = put(L.kblk, sizeof(BCplBlk) * hdr[3]);
+  if (st == SLSHT_OK) st = put(L.rblk, sizeof(BRotBlk) * hdr[4]);
+  for (int pi = 0; pi < 3 && st == SLSHT_OK; ++pi) st = put(L.tiles[pi], sizeof(BTile) * hdr[5 + pi]);
+  if (st == SLSHT_OK) st = put(L.in, in_off);
+  if (st == SLSHT_OK && cudaGraphLaunch(ln.exec, ln.st) != cudaSuccess) {
+    cudaGetLastError();
+    st = SLSHT_E_CUDA;
+  }
+  if (st == SLSHT_OK && cudaEventRecord(ln.ev_b, ln.st) != cudaSuccess) st = SLSHT_E_CUDA;
+  const double t1 = sv_now_ms();
+  lk.lock();
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    c->launches[SLSHT_STAGE_COUPLE] += 4;
+    c->launches[SLSHT_STAGE_BETA] += 1;
+    c->launches[SLSHT_STAGE_ALPHA] += 3;
+    c->samples += (uint64_t)samples;
+  }
+  c->sv_ticks++;
+  for (const SvChunk& k : ch)
+    if (k.r->t_issue < 0) k.r->t_issue = t1 - t0;
+  if (st != SLSHT_OK) {
+    for (const SvChunk& k : ch) k.r->status = st;
+    // the lane's stream is left as it is; its chunks fail with the tick
+  }
+  ln.chunks = std::move(ch);
+  ln.busy = true;
+  ln.t_assemble = t0;
+  return st == SLSHT_OK ? (int)ln.chunks.size() : st;
+}
+
+// Retires a lane whose tick has completed (c->smu held).
+static void sv_retire(slsht_ctx* c, SvLane& ln) {
+  const cudaError_t q = cudaEventQuery(ln.ev_b);
+  if (q == cudaErrorNotReady) return;
+  float a = 0.f, b = 0.f;
+  int st = SLSHT_OK;
+  if (q != cudaSuccess || cudaEventElapsedTime(&a, c->sv_ref, ln.ev_a) != cudaSuccess ||
+      cudaEventElapsedTime(&b, c->sv_ref, ln.ev_b) != cudaSuccess) {
+    cudaGetLastError();
+    record_cuda_error("serving tick", q != cudaSuccess ? q : cudaErrorUnknown);
+    st = SLSHT_E_CUDA;
+  }
+  const double now = sv_now_ms();
+  for (const SvChunk& k : ln.chunks) {
+    Request& r = *k.r;
+    r.done += k.np;
+    r.dev_first = std::min(r.dev_first, (double)a);
+    r.dev_last = std::max(r.dev_last, (double)b);
+    if (st != SLSHT_OK) r.status = st;
+  }
+  ln.chunks.clear();
+  ln.busy = false;
+  // finished requests leave the active list with their times
+  for (size_t i = 0; i < c->active.size();) {
+    Request& r = *c->active[i];
+    if (r.done >= r.n_pairs || (r.status != SLSHT_OK && r.next >= r.n_pairs && r.done >= r.next)) {
+      slsht_ctx::Final fin{r.status, {r.t_admit - r.t_submit, r.t_issue, r.dev_last - r.dev_first, now - r.t_submit}};
+      c->status[r.id] = fin;
+      c->active.erase(c->active.begin() + (long)i);
+      c->inflight--;
+      c->scv.notify_all();
+    } else {
+      ++i;
+    }
+  }
 }
 
 static void worker_loop(slsht_ctx* c) {
   DeviceGuard g(c->device);
   std::unique_lock<std::mutex> l(c->smu);
+  int init = sv_init(c);
   while (true) {
-    // retire finished slots
-    for (auto& s : c->slots) {
-      if (!s.busy) continue;
-      cudaError_t q = cudaEventQuery(s.fin);
-      if (q == cudaErrorNotReady) continue;
-      int st = SLSHT_OK;
-      if (q != cudaSuccess) { record_cuda_error("request", q); st = SLSHT_E_CUDA; }
-      c->status[s.req->id] = st;
-      s.req.reset();
-      s.busy = false;
-      c->inflight--;
+    for (auto& ln : c->lanes)
+      if (ln.busy) sv_retire(c, ln);
+    if (init != SLSHT_OK) {          // fail every request: the serving lanes could not be set up
+      while (!c->queue.empty()) {
+        c->status[c->queue.front()->id] = slsht_ctx::Final{init, {0, 0, 0, 0}};
+        c->queue.pop_front();
+        c->inflight--;
+      }
       c->scv.notify_all();
     }
-    // admit
-    while (!c->queue.empty()) {
-      Slot* free_slot = nullptr;
-      for (auto& s : c->slots) if (!s.busy) { free_slot = &s; break; }
-      if (!free_slot) break;
-      Request* r = c->queue.front().get();
-      const size_t need = request_scratch_estimate(&r->desc, (int32_t)(r->lm.size() / 2));
-      const size_t avail = c->budget > c->used.load() ? c->budget - c->used.load() : 0;
-      if (need > avail + free_slot->ws.bytes && c->inflight > 0) break;   // wait for memory
-      std::unique_ptr<Request> req = std::move(c->queue.front());
-      c->queue.pop_front();
-      Slot& s = *free_slot;
-      s.busy = true;          // counted in flight before the lock is released
-      c->inflight++;
-      int st = SLSHT_OK;
-      if (!s.stream) {
-        if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&s.fin, cudaEventDisableTiming) != cudaSuccess) {
-          cudaGetLastError();
-          st = SLSHT_E_CUDA;
-        } else {
-          st = ws_init(s.ws);
-        }
+    bool issued = false;
+    if (init == SLSHT_OK) {
+      for (auto& ln : c->lanes) {
+        if (ln.busy) continue;
+        const int n = sv_tick(c, ln, l);
+        if (n > 0) issued = true;
+        break;                       // one tick per pass: completions are seen between ticks
       }
-      if (st == SLSHT_OK) {
-        l.unlock();
-        st = forward_impl(c, s.ws, &req->desc, req->f.data(), req->h.data(), req->lm.data(), req->lm.data(),
-                          (int32_t)(req->lm.size() / 2), req->g_out, s.stream);
-        if (st == SLSHT_OK && cudaEventRecord(s.fin, s.stream) != cudaSuccess) st = SLSHT_E_CUDA;
-        l.lock();
-      }
-      if (st != SLSHT_OK) {
-        c->status[req->id] = st;
-        s.busy = false;
-        c->inflight--;
-        c->scv.notify_all();
-        continue;
-      }
-      s.req = std::move(req);
     }
-    if (c->stop && c->queue.empty() && c->inflight == 0) break;
-    if (c->inflight > 0) {
+    bool busy = false;
+    for (auto& ln : c->lanes) busy = busy || ln.busy;
+    if (c->stop && c->queue.empty() && c->active.empty() && !busy) break;
+    if (issued) continue;
+    if (busy) {
       c->scv.wait_for(l, std::chrono::microseconds(50));
     } else {
       c->scv.wait(l, [c] { return c->stop || !c->queue.empty(); });
@@ -2087,6 +2682,8 @@ extern "C" int slsht_submit(slsht_ctx* c, const slsht_desc* desc, const double* 
   std::unique_ptr<Request> r(new Request());
   r->desc = *desc;
   r->g_out = g_out;
+  r->n_pairs = n_pairs;
+  r->t_submit = sv_now_ms();
   CKS(copy_in(f_lm, 2 * (size_t)desc->L_f * desc->L_f, r->f));
   CKS(copy_in(h_lm, 2 * (size_t)desc->L_h * desc->L_h, r->h));
   r->lm.resize(2 * (size_t)n_pairs);
@@ -2096,38 +2693,56 @@ extern "C" int slsht_submit(slsht_ctx* c, const slsht_desc* desc, const double* 
     std::memcpy(r->lm.data(), lm, sizeof(int32_t) * 2 * (size_t)n_pairs);
   }
   CKS(check_pairs(desc, r->lm.data(), n_pairs));
+  // one pair must fit an empty tick (the double-float form is the larger)
+  {
+    Request probe = Request();
+    probe.desc = *desc;
+    probe.engine = ENG_DD;
+    probe.nt = 32;
+    const long long J = (long long)desc->n_beta * desc->n_gamma;
+    if (sv_dev_bytes(probe, 1) > SV_DEV_BYTES || sv_in_bytes(probe, 1) > SV_STAGE_IN ||
+        sv_rblk_count(probe) > SV_RBLK || (J + 31) / 32 > SV_TILES) {
+      slsht_record_error_text("slsht_submit: one pair of this request exceeds a serving tick's arena");
+      return SLSHT_E_NOMEM;
+    }
+  }
   std::unique_lock<std::mutex> l(c->smu);
-  if (c->queue.size() >= SERVE_MAX_QUEUE) return SLSHT_E_BUSY;
+  if (c->inflight >= SERVE_MAX_QUEUE) return SLSHT_E_BUSY;
   if (!c->worker_started) {
     c->worker = std::thread(worker_loop, c);
     c->worker_started = true;
   }
   r->id = c->next_id++;
   *ticket = r->id;
-  c->status[r->id] = SLSHT_PENDING;
+  c->status[r->id] = slsht_ctx::Final{SLSHT_PENDING, {0, 0, 0, 0}};
   c->queue.push_back(std::move(r));
+  c->inflight++;
   c->scv.notify_all();
   return SLSHT_OK;
 }
 
-extern "C" int slsht_poll(slsht_ctx* c, uint64_t ticket) {
+extern "C" int slsht_poll_times(slsht_ctx* c, uint64_t ticket, double* times) {
   if (!c) return SLSHT_E_ARG;
   std::lock_guard<std::mutex> l(c->smu);
   auto it = c->status.find(ticket);
   if (it == c->status.end()) return SLSHT_E_STATE;
-  const int s = it->second;
-  if (s != SLSHT_PENDING) c->status.erase(it);
+  const int s = it->second.st;
+  if (s != SLSHT_PENDING) {
+    if (times)
+      for (int i = 0; i < 4; ++i) times[i] = it->second.t[i];
+    c->status.erase(it);
+  }
   return s;
 }
+
+extern "C" int slsht_poll(slsht_ctx* c, uint64_t ticket) { return slsht_poll_times(c, ticket, nullptr); }
 
 extern "C" int slsht_drain(slsht_ctx* c, int64_t timeout_ms) {
   if (!c) return SLSHT_E_ARG;
   std::unique_lock<std::mutex> l(c->smu);
   const auto until = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms);
-  while (!c->queue.empty() || c->inflight > 0) {
-    if (c->scv.wait_until(l, until) == std::cv_status::timeout &&
-        (!c->queue.empty() || c->inflight > 0))
-      return SLSHT_E_TIMEOUT;
+  while (c->inflight > 0) {
+    if (c->scv.wait_until(l, until) == std::cv_status::timeout && c->inflight > 0) return SLSHT_E_TIMEOUT;
   }
   return SLSHT_OK;
 }

@@ -77,13 +77,17 @@ __device__ __forceinline__ void kdd_pair(const double2* __restrict__ kp, int n2,
   if (threadIdx.x == 0) *kexp = e;
 }
 
-// block {cpl, pair}
-__global__ void __launch_bounds__(256) k_batch_kdd(const BCouple* __restrict__ cpl, const BCplBlk* __restrict__ blk) {
+// block {cpl, pair}; blocks stride over the list (count nblk, or *n_dev)
+__global__ void __launch_bounds__(256) k_batch_kdd(const BCouple* __restrict__ cpl, const BCplBlk* __restrict__ blk,
+                                                   int nblk, const int* __restrict__ n_dev) {
   __shared__ double red[8];
-  const BCplBlk b = blk[blockIdx.x];
-  const BCouple c = cpl[b.cpl];
-  const int n2 = c.Lh * c.Lh, pair = b.first;
-  kdd_pair(c.kc + (size_t)pair * n2, n2, c.kdd + (size_t)pair * n2, c.kexp + pair, red);
+  const int cnt = n_dev != nullptr ? *n_dev : nblk;
+  for (int i = blockIdx.x; i < cnt; i += gridDim.x) {
+    const BCplBlk b = blk[i];
+    const BCouple c = cpl[b.cpl];
+    const int n2 = c.Lh * c.Lh, pair = b.first;
+    kdd_pair(c.kc + (size_t)pair * n2, n2, c.kdd + (size_t)pair * n2, c.kexp + pair, red);
+  }
 }
 
 // one block per pair
@@ -102,7 +106,12 @@ cudaError_t launch_kdd_pairs(const double2* kc, int Lh, int npairs, float4* kdd,
 
 cudaError_t launch_batch_kdd(const BCouple* cpl, const BCplBlk* blk, int nblk, cudaStream_t st) {
   if (nblk <= 0) return cudaSuccess;
-  k_batch_kdd<<<nblk, 256, 0, st>>>(cpl, blk);
+  k_batch_kdd<<<nblk, 256, 0, st>>>(cpl, blk, nblk, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_kdd_n(const BCouple* cpl, const BCplBlk* blk, const int* n, int grid, cudaStream_t st) {
+  k_batch_kdd<<<grid, 256, 0, st>>>(cpl, blk, 0, n);
   return cudaGetLastError();
 }
 
@@ -131,7 +140,8 @@ struct RotwinBoth {
 __device__ __forceinline__ void rotwin_block_fp64(const double2* __restrict__ h, const double* __restrict__ dblk,
                                                   size_t dstride, int nb, const double2* __restrict__ eg, int Lh,
                                                   int Ng, int b, int p, const RotChunks& ch, int z, double2* H,
-                                                  float4* Hdd, int* hexp, unsigned char* smem) {
+                                                  float4* Hdd, int* hexp, unsigned char* smem,
+                                                  const uint32_t* qmask) {
   __shared__ double red[4];
   int e = 0;
   if (Hdd != nullptr) {
@@ -143,24 +153,29 @@ __device__ __forceinline__ void rotwin_block_fp64(const double2* __restrict__ h,
     e = scale_exp(block_max(mx, red));
     if (b == 0 && p == 0 && z == 0 && threadIdx.x == 0) *hexp = e;
   }
-  rotwin_block_smem_to<double>(h, dblk, dstride, nb, eg, Lh, Ng, b, p, ch, z, RotwinBoth{H, Hdd, e}, smem);
+  rotwin_block_smem_to<double>(h, dblk, dstride, nb, eg, Lh, Ng, b, p, ch, z, RotwinBoth{H, Hdd, e}, smem, qmask);
 }
 
-__global__ void __launch_bounds__(128) k_batch_rotwin(const BRot* __restrict__ rot, const BRotBlk* __restrict__ blk) {
+__global__ void __launch_bounds__(128) k_batch_rotwin(const BRot* __restrict__ rot, const BRotBlk* __restrict__ blk,
+                                                      int nblk, const int* __restrict__ n_dev) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const BRotBlk bb = blk[blockIdx.x];
-  const BRot r = rot[bb.rot];
-  const size_t S = blk_off(r.Lh);
-  const size_t off = (size_t)bb.b * S + blk_off(bb.p);
-  const int nb = min(ROTWIN_NB, r.Nb - bb.b);
-  RotChunks ch;
-  ch.QC = r.QC; ch.CC = r.CC; ch.nq = r.nq; ch.nc = r.nc;
-  if (r.prec == 0) {
-    rotwin_block_fp64(r.h, (const double*)r.dt + off, S, nb, (const double2*)r.eg, r.Lh, r.Ng, bb.b, bb.p, ch, bb.z,
-                      (double2*)r.H, r.Hdd, r.hexp, smem_raw);
-  } else {
-    rotwin_block_smem_to<float>(r.h, (const float*)r.dt + off, S, nb, (const float2*)r.eg, r.Lh, r.Ng, bb.b, bb.p,
-                                ch, bb.z, RotwinStore<float>{(float2*)r.H}, smem_raw);
+  const int cnt = n_dev != nullptr ? *n_dev : nblk;
+  for (int i = blockIdx.x; i < cnt; i += gridDim.x) {
+    const BRotBlk bb = blk[i];
+    const BRot r = rot[bb.rot];
+    const size_t S = blk_off(r.Lh);
+    const size_t off = (size_t)bb.b * S + blk_off(bb.p);
+    const int nb = min(ROTWIN_NB, r.Nb - bb.b);
+    RotChunks ch;
+    ch.QC = r.QC; ch.CC = r.CC; ch.nq = r.nq; ch.nc = r.nc;
+    if (r.prec == 0) {
+      rotwin_block_fp64(r.h, (const double*)r.dt + off, S, nb, (const double2*)r.eg, r.Lh, r.Ng, bb.b, bb.p, ch,
+                        bb.z, (double2*)r.H, r.Hdd, r.hexp, smem_raw, r.qmask);
+    } else {
+      rotwin_block_smem_to<float>(r.h, (const float*)r.dt + off, S, nb, (const float2*)r.eg, r.Lh, r.Ng, bb.b, bb.p,
+                                  ch, bb.z, RotwinStore<float>{(float2*)r.H}, smem_raw, r.qmask);
+    }
+    __syncthreads();               // the block's shared memory is reused by its next entry
   }
 }
 
@@ -169,28 +184,38 @@ cudaError_t launch_batch_rotwin(const BRot* rot, const BRotBlk* blk, int nblk, s
   if (smem > ROTWIN_SMEM_LIMIT) return cudaErrorInvalidValue;
   cudaError_t e = batch_attrs();
   if (e != cudaSuccess) return e;
-  k_batch_rotwin<<<nblk, 128, smem, st>>>(rot, blk);
+  k_batch_rotwin<<<nblk, 128, smem, st>>>(rot, blk, nblk, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_rotwin_n(const BRot* rot, const BRotBlk* blk, const int* n, int grid, size_t smem,
+                                  cudaStream_t st) {
+  if (smem > ROTWIN_SMEM_LIMIT) return cudaErrorInvalidValue;
+  cudaError_t e = batch_attrs();
+  if (e != cudaSuccess) return e;
+  k_batch_rotwin<<<grid, 128, smem, st>>>(rot, blk, 0, n);
   return cudaGetLastError();
 }
 
 // grid (Nb, Lh, chunks): the scaled double-float window of one call
 __global__ void __launch_bounds__(128) k_rotwin_dd(const double2* __restrict__ h, const double* __restrict__ dt,
                                                    const double2* __restrict__ eg, int Lh, int Nb, int Ng,
-                                                   RotChunks ch, float4* Hdd, int* hexp) {
+                                                   RotChunks ch, float4* Hdd, int* hexp,
+                                                   const uint32_t* __restrict__ qmask) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b0 = blockIdx.x * ROTWIN_NB, p = blockIdx.y;
   const size_t S = blk_off(Lh);
   rotwin_block_fp64(h, dt + (size_t)b0 * S + blk_off(p), S, min(ROTWIN_NB, Nb - b0), eg, Lh, Ng, b0, p, ch,
-                    blockIdx.z, nullptr, Hdd, hexp, smem_raw);
+                    blockIdx.z, nullptr, Hdd, hexp, smem_raw, qmask);
 }
 
 cudaError_t launch_rotwin_dd(const double2* h, const double* dt, const double2* eg, int Lh, int Nb, int Ng,
-                             float4* Hdd, int* hexp, cudaStream_t st) {
+                             float4* Hdd, int* hexp, cudaStream_t st, const uint32_t* qmask) {
   const RotChunks ch = rot_chunks(Lh, Ng, sizeof(double2));
   cudaError_t e = batch_attrs();
   if (e != cudaSuccess) return e;
   dim3 grid((Nb + ROTWIN_NB - 1) / ROTWIN_NB, Lh, ch.nq * ch.nc);
-  k_rotwin_dd<<<grid, 128, ch.smem(Lh, sizeof(double2)), st>>>(h, dt, eg, Lh, Nb, Ng, ch, Hdd, hexp);
+  k_rotwin_dd<<<grid, 128, ch.smem(Lh, sizeof(double2)), st>>>(h, dt, eg, Lh, Nb, Ng, ch, Hdd, hexp, qmask);
   return cudaGetLastError();
 }
 
@@ -422,9 +447,11 @@ __device__ __forceinline__ void ba_tile_dd(const BItem& it, const BTile& tl, uns
 
 __global__ void __launch_bounds__(BA_THREADS) k_batch_alpha_dd(const BItem* __restrict__ items,
                                                                const BTile* __restrict__ tiles, int ntiles,
-                                                               int* __restrict__ counter) {
+                                                               int* __restrict__ counter,
+                                                               const int* __restrict__ n_dev) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_tile;
+  if (n_dev != nullptr) ntiles = *n_dev;
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1);
     __syncthreads();
@@ -466,9 +493,10 @@ __global__ void __launch_bounds__(BA_THREADS) k_alpha_dd_single(const BItem it, 
 template <typename T>
 __global__ void __launch_bounds__(BA_THREADS) k_batch_alpha(const BItem* __restrict__ items,
                                                             const BTile* __restrict__ tiles, int ntiles,
-                                                            int* __restrict__ counter) {
+                                                            int* __restrict__ counter, const int* __restrict__ n_dev) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_tile;
+  if (n_dev != nullptr) ntiles = *n_dev;
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1);
     __syncthreads();
@@ -544,10 +572,34 @@ cudaError_t launch_batch_alpha(int prec, const BItem* items, const BTile* tiles,
   if (smem > BA_SMEM_LIMIT) return cudaErrorInvalidValue;
   cudaError_t e = batch_attrs();
   if (e != cudaSuccess) return e;
-  if (prec == 0) k_batch_alpha<double><<<grid, BA_THREADS, smem, st>>>(items, tiles, ntiles, counter);
-  else if (prec == 1) k_batch_alpha<float><<<grid, BA_THREADS, smem, st>>>(items, tiles, ntiles, counter);
-  else k_batch_alpha_dd<<<grid, BA_THREADS, smem, st>>>(items, tiles, ntiles, counter);
+  if (prec == 0) k_batch_alpha<double><<<grid, BA_THREADS, smem, st>>>(items, tiles, ntiles, counter, nullptr);
+  else if (prec == 1) k_batch_alpha<float><<<grid, BA_THREADS, smem, st>>>(items, tiles, ntiles, counter, nullptr);
+  else k_batch_alpha_dd<<<grid, BA_THREADS, smem, st>>>(items, tiles, ntiles, counter, nullptr);
   return cudaGetLastError();
+}
+
+cudaError_t launch_batch_alpha_n(int prec, const BItem* items, const BTile* tiles, const int* n, int* counter,
+                                 int grid, size_t smem, cudaStream_t st) {
+  if (smem > BA_SMEM_LIMIT) return cudaErrorInvalidValue;
+  cudaError_t e = batch_attrs();
+  if (e != cudaSuccess) return e;
+  if (prec == 0) k_batch_alpha<double><<<grid, BA_THREADS, smem, st>>>(items, tiles, 0, counter, n);
+  else if (prec == 1) k_batch_alpha<float><<<grid, BA_THREADS, smem, st>>>(items, tiles, 0, counter, n);
+  else k_batch_alpha_dd<<<grid, BA_THREADS, smem, st>>>(items, tiles, 0, counter, n);
+  return cudaGetLastError();
+}
+
+int batch_rotwin_occupancy(size_t smem) {
+  if (batch_attrs() != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_rotwin, 128, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return n > 0 ? n : 1;
 }
 
 cudaError_t launch_alpha_dd_call(const BItem& item, int npairs, int num_sms, cudaStream_t st) {

@@ -23,6 +23,7 @@ struct BCouple {                 // one coupling output (a signal with a pair li
   float4* kdd;                   // double-float k scaled by 2^-kexp[pair] (null: not needed)
   int* kexp;
   int Lh, npairs;
+  int Lf;                        // signal band limit (the serving path's 3j chains)
 };
 struct BCplBlk { int cpl, first; };        // 256 consecutive (pair, t) items of one BCouple
 
@@ -33,6 +34,7 @@ struct BRot {                    // one rotated window H
   void* H;                       // tiled H (h_index), T2 (null: not needed)
   float4* Hdd;                   // FP64 windows: double-float H scaled by 2^-hexp[0] (null: not needed)
   int* hexp;
+  const uint32_t* qmask;         // active orders of the window (null: all; launch_order_mask)
   int prec, Lh, Nb, Ng;          // prec 0: FP64, 1: FP32
   int QC, CC, nq, nc;            // shared-memory chunking (rot_chunks)
 };
@@ -71,7 +73,7 @@ cudaError_t launch_batch_rotwin(const BRot* rot, const BRotBlk* blk, int nblk, s
 // the index (no list), CTAs striding over them.
 cudaError_t launch_kdd_pairs(const double2* kc, int Lh, int npairs, float4* kdd, int* kexp, cudaStream_t st);
 cudaError_t launch_rotwin_dd(const double2* h, const double* dt, const double2* eg, int Lh, int Nb, int Ng,
-                             float4* Hdd, int* hexp, cudaStream_t st);
+                             float4* Hdd, int* hexp, cudaStream_t st, const uint32_t* qmask = nullptr);
 cudaError_t launch_alpha_dd_call(const BItem& item, int npairs, int num_sms, cudaStream_t st);
 // The same for an item of any precision (item.prec 0 FP64, 1 FP32, 2 double-float).
 cudaError_t launch_alpha_call(const BItem& item, int npairs, int num_sms, cudaStream_t st);
@@ -80,3 +82,19 @@ cudaError_t launch_alpha_call(const BItem& item, int npairs, int num_sms, cudaSt
 // launch); every tile's item has precision prec (0 FP64, 1 FP32, 2 double-float).
 cudaError_t launch_batch_alpha(int prec, const BItem* items, const BTile* tiles, int ntiles, int* counter, int grid,
                                size_t smem, cudaStream_t st);
+
+// The serving path's launches (fixed grids, work counts read from device
+// memory, so that one captured graph serves ticks of any composition):
+//   launch_serve_couple  k of the {coupling, pair} list by 3j chains in the
+//                        call (cls 0: L_h <= 16, 1: <= 32, 2: <= 64)
+//   launch_batch_kdd_n, launch_batch_rotwin_n, launch_batch_alpha_n
+//                        as above with the block / tile count *n.
+cudaError_t launch_serve_couple(int cls, const BCouple* cpl, const int2* list, const int* n, int grid,
+                                cudaStream_t st);
+cudaError_t launch_batch_kdd_n(const BCouple* cpl, const BCplBlk* blk, const int* n, int grid, cudaStream_t st);
+cudaError_t launch_batch_rotwin_n(const BRot* rot, const BRotBlk* blk, const int* n, int grid, size_t smem,
+                                  cudaStream_t st);
+cudaError_t launch_batch_alpha_n(int prec, const BItem* items, const BTile* tiles, const int* n, int* counter,
+                                 int grid, size_t smem, cudaStream_t st);
+// Resident CTAs per SM of the rotated-window kernel with `smem` bytes.
+int batch_rotwin_occupancy(size_t smem);

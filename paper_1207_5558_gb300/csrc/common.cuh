@@ -99,9 +99,14 @@ __host__ __device__ __forceinline__ size_t h_elems(size_t J, int n2) { return (J
 // Rotated window H^p_q(j) = sum_q' h_p^q' d^p_{q,q'}(beta_b) e^{-i q' gamma_c},
 // at H[h_index(p*p+p+q, j, Lh*Lh)], j = b*Ng + c; dt in the [b][S] layout.
 cudaError_t launch_rotwin_f64(const double2* h, const double* dt, const double2* eg, int Lh, int Nb, int Ng,
-                              double2* H, cudaStream_t st);
+                              double2* H, cudaStream_t st, const uint32_t* qmask = nullptr);
 cudaError_t launch_rotwin_f32(const double2* h, const float* dt, const float2* eg, int Lh, int Nb, int Ng,
-                              float2* H, cudaStream_t st);
+                              float2* H, cudaStream_t st, const uint32_t* qmask = nullptr);
+// The window's active orders for the rotated-window sums (qmask of
+// rotwin_block_smem_to): bit q' + 63 of mask[0..3] is set when some degree
+// has |Re h_p^q'| or |Im h_p^q'| above 2^-rel_exp of the window's largest
+// component (rel_exp = 0: above zero).  One block.
+cudaError_t launch_order_mask(const double2* h, int Lh, int rel_exp, uint32_t* mask, cudaStream_t st);
 // g[pair][a][j] = X_0 + sum_r (P_r cos(r alpha_a) - i M_r sin(r alpha_a)).
 // slots (nullable): per pair {output slot, mirror} as for launch_alpha_tc.
 cudaError_t launch_alpha_f64(const double2* Xs, const double2* csa, int Lh, int Na, int J,
@@ -121,6 +126,17 @@ cudaError_t launch_alpha_split_f32(const float2* Xs, const float2* tw, int Lh, i
 // Inverse: partial sums then final scaling (deterministic order).  The
 // partial sums of one pair are nslab * inverse_col_blocks(Nb, Ng) entries.
 int inverse_col_blocks(int Nb, int Ng);
+// Inverse without h_0^0 (inverse_alt.cu): column blocks of the projection
+// kernel, and the whole launch sequence.  prec 0: g complex128 and ea the
+// FP64 table (cos, sin)(q alpha_a), q = -p..p; 1: complex64 g, FP32 ea.
+// eg: (cos, sin)(q' gamma_c), q' = -p..p, FP64.  hp: h_p^q', q' = -p..p.
+// partial: n_in * ialt_col_blocks * (2p+1); khat: n_in * (2p+1);
+// rows[o * (2p+1) + q + p]: the g row of (L + p, M + q) for output o.
+int ialt_col_blocks(int Nb, int Ng);
+cudaError_t launch_inverse_alt(const void* g, int prec, const double* wb, const double* dt, int Lh,
+                               const double2* hp, const void* ea, const double2* eg, int Na, int Nb, int Ng, int p,
+                               int n_in, double2* partial, double scale, double2* khat, const int2* lm_out,
+                               const int* rows, int n_out, double2* f, cudaStream_t st);
 cudaError_t launch_inverse_f64(const double2* g, const double* wb, int Na, int Nb, int Ng,
                                int npairs, double2* partial, int nslab, cudaStream_t st);
 cudaError_t launch_inverse_f32(const float2* g, const double* wb, int Na, int Nb, int Ng,

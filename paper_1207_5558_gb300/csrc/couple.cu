@@ -3,6 +3,7 @@
 //   T(l',m';p,q;l,m) = (-1)^m sqrt((2l'+1)(2p+1)(2l+1)/(4 pi))
 //                      (l' p l; 0 0 0) (l' p l; m' q -m),
 // with both Wigner-3j families generated by recurrences in l' (= j1) in FP64.
+#include "batch.cuh"
 #include "couple_dev.cuh"
 
 // 1/x for a positive integer-valued x: float reciprocal refined by two
@@ -107,19 +108,18 @@ __device__ int threej_chain(int j2, int j3, int m2, int m3, double* f, double* b
   return n;
 }
 
-// One CTA per pair.  First the CTA builds, in shared memory, the
-// (l' p l; 0 0 0) family for every p < Lh: the two-term relation
+// One pair's k_lm(p, q), every item t = p*p + p + q, by one CTA.  First the
+// CTA builds, in shared memory (w0s), the (l' p l; 0 0 0) family for every
+// p < Lh: the two-term relation
 //   f(j1+1) = -sqrt((j1^2-d^2)(S^2-j1^2) / (((j1+1)^2-d^2)(S^2-(j1+1)^2))) f(j1-1),
 // d = p - l, S = p + l + 1, over the even j1 + p + l, normalised by
-// sum (2 j1 + 1) f^2 = 1 with sgn f(p + l) = (-1)^{p-l}.  Then item
-// t = p*p + p + q (the window's flat index) runs the (l' p l; m-q q -m) chain
-// and accumulates k_lm(p, q).
+// sum (2 j1 + 1) f^2 = 1 with sgn f(p + l) = (-1)^{p-l}.  Then item t runs
+// the (l' p l; m-q q -m) chain and accumulates k_lm(p, q) into kc[t].  Every
+// thread of the block takes part (the block may call it again after it).
 template <int CMAX>
-__global__ void __launch_bounds__(256) k_couple(const double2* __restrict__ f, int Lf, int Lh,
-                                                const int2* __restrict__ lm, double2* __restrict__ kc) {
-  __shared__ double w0s[SLSHT_MAX_LH * (SLSHT_MAX_LH + 1) / 2];
-  const int pair = blockIdx.x;
-  const int l = lm[pair].x, m = lm[pair].y;
+__device__ __forceinline__ void couple_pair_chains(const double2* __restrict__ f, int Lf, int Lh, int l, int m,
+                                                   double2* __restrict__ kc, double* w0s) {
+  __syncthreads();                              // w0s of a previous call is read
   for (int p = threadIdx.x; p < Lh; p += blockDim.x) {
     double* w = w0s + p * (p + 1) / 2;
     const int j0 = abs(p - l), cnt = min(p, l) + 1;
@@ -167,8 +167,40 @@ __global__ void __launch_bounds__(256) k_couple(const double2* __restrict__ f, i
       acc.x *= pre;
       acc.y *= pre;
     }
-    kc[(size_t)pair * nitems + t] = acc;
+    kc[t] = acc;
   }
+}
+
+// One CTA per pair.
+template <int CMAX>
+__global__ void __launch_bounds__(256) k_couple(const double2* __restrict__ f, int Lf, int Lh,
+                                                const int2* __restrict__ lm, double2* __restrict__ kc) {
+  __shared__ double w0s[SLSHT_MAX_LH * (SLSHT_MAX_LH + 1) / 2];
+  const int pair = blockIdx.x;
+  couple_pair_chains<CMAX>(f, Lf, Lh, lm[pair].x, lm[pair].y, kc + (size_t)pair * Lh * Lh, w0s);
+}
+
+// The same for the pairs of many couplings (serving ticks): blocks stride
+// over the list {coupling, pair} of *n entries.
+template <int CMAX>
+__global__ void __launch_bounds__(256) k_serve_couple(const BCouple* __restrict__ cpl, const int2* __restrict__ list,
+                                                      const int* __restrict__ n) {
+  __shared__ double w0s[SLSHT_MAX_LH * (SLSHT_MAX_LH + 1) / 2];
+  const int cnt = *n;
+  for (int i = blockIdx.x; i < cnt; i += gridDim.x) {
+    const int2 e = list[i];
+    const BCouple c = cpl[e.x];
+    const int2 pr = c.lm[e.y];
+    couple_pair_chains<CMAX>(c.f, c.Lf, c.Lh, pr.x, pr.y, c.kc + (size_t)e.y * c.Lh * c.Lh, w0s);
+  }
+}
+
+cudaError_t launch_serve_couple(int cls, const BCouple* cpl, const int2* list, const int* n, int grid,
+                                cudaStream_t st) {
+  if (cls == 0) k_serve_couple<32><<<grid, 256, 0, st>>>(cpl, list, n);
+  else if (cls == 1) k_serve_couple<64><<<grid, 256, 0, st>>>(cpl, list, n);
+  else k_serve_couple<128><<<grid, 256, 0, st>>>(cpl, list, n);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_couple(const double2* f, int Lf, int Lh, const int2* lm, int npairs,

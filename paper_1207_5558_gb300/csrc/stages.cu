@@ -240,17 +240,55 @@ cudaError_t launch_betagamma_f32(const double2* kc, const double2* h, const floa
 template <typename T>
 __global__ void __launch_bounds__(128) k_rotwin_smem(const double2* __restrict__ h, const T* __restrict__ dt,
                                                      const typename vec2<T>::t* __restrict__ eg, int Lh, int Nb,
-                                                     int Ng, RotChunks ch, typename vec2<T>::t* __restrict__ H) {
+                                                     int Ng, RotChunks ch, typename vec2<T>::t* __restrict__ H,
+                                                     const uint32_t* __restrict__ qmask) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b0 = blockIdx.x * ROTWIN_NB, p = blockIdx.y;
   const int S = blk_off(Lh);
   rotwin_block_smem_to<T>(h, dt + (size_t)b0 * S + blk_off(p), (size_t)S, min(ROTWIN_NB, Nb - b0), eg, Lh, Ng, b0,
-                          p, ch, blockIdx.z, RotwinStore<T>{H}, smem_raw);
+                          p, ch, blockIdx.z, RotwinStore<T>{H}, smem_raw, qmask);
+}
+
+// Active orders of a window (launch_order_mask): one block of 128 threads.
+__global__ void __launch_bounds__(128) k_order_mask(const double2* __restrict__ h, int Lh, int rel_exp,
+                                                    uint32_t* __restrict__ mask) {
+  __shared__ double red[4];
+  __shared__ uint32_t sm[4];
+  const int n2 = Lh * Lh;
+  double mx = 0.0;
+  for (int t = threadIdx.x; t < n2; t += blockDim.x) {
+    const double2 v = h[t];
+    mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  if (threadIdx.x < 4) sm[threadIdx.x] = 0u;
+  __syncthreads();
+  mx = fmax(fmax(red[0], red[1]), fmax(red[2], red[3]));
+  const double eps = rel_exp > 0 ? ldexp(mx, -rel_exp) : 0.0;
+  for (int t = threadIdx.x; t < n2; t += blockDim.x) {
+    int p = (int)sqrtf((float)t);
+    while (p * p > t) --p;
+    while ((p + 1) * (p + 1) <= t) ++p;
+    const int q = t - p * p - p;
+    const double2 v = h[t];
+    if (fabs(v.x) > eps || fabs(v.y) > eps) {
+      const int bit = q + 63;
+      atomicOr(&sm[bit >> 5], 1u << (bit & 31));
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) mask[threadIdx.x] = sm[threadIdx.x];
+}
+
+cudaError_t launch_order_mask(const double2* h, int Lh, int rel_exp, uint32_t* mask, cudaStream_t st) {
+  k_order_mask<<<1, 128, 0, st>>>(h, Lh, rel_exp, mask);
+  return cudaGetLastError();
 }
 
 template <typename T>
 static cudaError_t launch_rotwin_t(const double2* h, const T* dt, const typename vec2<T>::t* eg, int Lh,
-                                   int Nb, int Ng, typename vec2<T>::t* H, cudaStream_t st) {
+                                   int Nb, int Ng, typename vec2<T>::t* H, cudaStream_t st, const uint32_t* qmask) {
   typedef typename vec2<T>::t T2;
   const RotChunks ch = rot_chunks(Lh, Ng, sizeof(T2));
   const size_t smem = ch.smem(Lh, sizeof(T2));
@@ -259,15 +297,15 @@ static cudaError_t launch_rotwin_t(const double2* h, const T* dt, const typename
     if (e != cudaSuccess) return e;
   }
   dim3 grid((Nb + ROTWIN_NB - 1) / ROTWIN_NB, Lh, ch.nq * ch.nc);
-  k_rotwin_smem<T><<<grid, 128, smem, st>>>(h, dt, eg, Lh, Nb, Ng, ch, H);
+  k_rotwin_smem<T><<<grid, 128, smem, st>>>(h, dt, eg, Lh, Nb, Ng, ch, H, qmask);
   return cudaGetLastError();
 }
 
 cudaError_t launch_rotwin_f64(const double2* h, const double* dt, const double2* eg, int Lh, int Nb, int Ng,
-                              double2* H, cudaStream_t st) {
-  return launch_rotwin_t<double>(h, dt, eg, Lh, Nb, Ng, H, st);
+                              double2* H, cudaStream_t st, const uint32_t* qmask) {
+  return launch_rotwin_t<double>(h, dt, eg, Lh, Nb, Ng, H, st, qmask);
 }
 cudaError_t launch_rotwin_f32(const double2* h, const float* dt, const float2* eg, int Lh, int Nb, int Ng,
-                              float2* H, cudaStream_t st) {
-  return launch_rotwin_t<float>(h, dt, eg, Lh, Nb, Ng, H, st);
+                              float2* H, cudaStream_t st, const uint32_t* qmask) {
+  return launch_rotwin_t<float>(h, dt, eg, Lh, Nb, Ng, H, st, qmask);
 }

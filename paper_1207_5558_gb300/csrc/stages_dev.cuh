@@ -61,6 +61,17 @@ __device__ __forceinline__ void cp_async_wait_all() {
 __device__ __forceinline__ void rot_unpack(const float4 v, float* d) { d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w; }
 __device__ __forceinline__ void rot_unpack(const double2 v, double* d) { d[0] = v.x; d[1] = v.y; }
 
+// Orders q' of the window that take part in the sums: bit q' + 63 of the four
+// words of qmask (null: every order).  A window whose coefficients vanish at
+// some orders for every degree -- a steerable window, azimuthally band-limited
+// (|q'| < N < L_h), or a window with only even orders -- then costs only its
+// active orders: the sums over q' skip terms that are zero.
+__device__ __forceinline__ bool rot_order_on(const uint32_t* qmask, int qp) {
+  if (qmask == nullptr) return true;
+  const int bit = qp + 63;
+  return (__ldg(qmask + (bit >> 5)) >> (bit & 31)) & 1u;
+}
+
 // One (beta rows b0 .. b0 + nb - 1, degree p, column chunk z) block of the
 // rotated window (see RotChunks).  dblk0 = the degree-p block of d(beta_b0),
 // consecutive beta rows dstride apart, row-major [q + p][q' + p];
@@ -69,14 +80,17 @@ __device__ __forceinline__ void rot_unpack(const double2 v, double* d) { d[0] = 
 // staging copies run along q (coalesced, cp.async: a pass's loads all in
 // flight) and land in [q'][row] order; the sign (-1)^{q'+p} is folded into
 // the staged B rows and (-1)^{q+p} into the outputs.  A thread holds TQ consecutive
-// rows x 4 columns (c0 + cg + 8 k), 2 multiply-adds a term.
+// rows x 4 columns (c0 + cg + 8 k), 2 multiply-adds a term.  Only the orders
+// that qmask marks active are staged and summed (in increasing q', so with
+// every order active the sums are those of the full window).
 // All threads of the block take part.  store(index, re, im) receives each
 // output with its h_index position.
 template <typename T, typename Store>
 __device__ __forceinline__ void rotwin_block_smem_to(const double2* __restrict__ h, const T* __restrict__ dblk0,
                                                      size_t dstride, int nb, const typename vec2<T>::t* __restrict__ eg,
                                                      int Lh, int Ng, int b0, int p, const RotChunks& ch, int z,
-                                                     Store store, unsigned char* smem) {
+                                                     Store store, unsigned char* smem,
+                                                     const uint32_t* qmask = nullptr) {
   typedef typename vec2<T>::t T2;
   constexpr int TQ = sizeof(T) == 4 ? 4 : 2;
   typedef typename std::conditional<sizeof(T) == 4, float4, double2>::type TV;   // TQ values of T
@@ -84,11 +98,23 @@ __device__ __forceinline__ void rotwin_block_smem_to(const double2* __restrict__
   const int QC = ch.QC, CC = ch.CC;
   if (QC != 16 * TQ || CC != ROTWIN_CC) return;   // the tiling below assumes rot_chunks' shape
   const int c0 = z * CC, ncr = min(CC, Ng - c0);
-  T* sd = reinterpret_cast<T*>(smem);                          // [q' + p][row of the pass]
-  T2* sB = reinterpret_cast<T2*>(sd + (size_t)QC * K);         // [q' + p][c - c0]
+  T* sd = reinterpret_cast<T*>(smem);                          // [active order][row of the pass]
+  T2* sB = reinterpret_cast<T2*>(sd + (size_t)QC * K);         // [active order][c - c0]
+  // the active orders of degree p as u = q' + p, increasing
+  __shared__ int s_ul[2 * SLSHT_MAX_LH - 1];
+  __shared__ int s_nu;
+  __syncthreads();                            // s_ul of a previous block of this CTA is read
+  if (threadIdx.x == 0) {
+    int n = 0;
+    for (int u = 0; u < w; ++u)
+      if (rot_order_on(qmask, u - p)) s_ul[n++] = u;
+    s_nu = n;
+  }
+  __syncthreads();
+  const int nu = s_nu;
   // (-1)^{q'+p} B_p(q', c) = (-1)^{q'+p} h_p^{q'} (cos - i sin)(q' gamma_c); zero beyond the chunk
-  for (int t = threadIdx.x; t < w * CC; t += ROTWIN_THREADS) {
-    const int u = t / CC, c = t - u * CC;
+  for (int t = threadIdx.x; t < nu * CC; t += ROTWIN_THREADS) {
+    const int i = t / CC, c = t - i * CC, u = s_ul[i];
     T2 v = mk2((T)0, (T)0);
     if (c < ncr) {
       const double2 hv = __ldg(h + p * p + u);
@@ -105,15 +131,15 @@ __device__ __forceinline__ void rotwin_block_smem_to(const double2* __restrict__
   const int rr = threadIdx.x % QCc, u0 = threadIdx.x / QCc;
   for (int r0 = 0; r0 < rows; r0 += QCc) {
     __syncthreads();                          // sB ready; the previous pass's d rows read
-    // d rows of the pass, transposed: sd[u][rr] = d[u][q + p] = (-1)^{q+u}
-    // d^p_{q,u-p}(beta_b) for row r0 + rr = (b - b0) w + q + p (rows past the
+    // d rows of the pass, transposed: sd[i][rr] = d[u][q + p] = (-1)^{q+u}
+    // d^p_{q,u-p}(beta_b), u = s_ul[i], for row r0 + rr = (b - b0) w + q + p (rows past the
     // end are left as they are: they feed only outputs that are not stored)
     {
       const int r = r0 + rr;
       if (r < rows) {
         const int bi = r / w, qi = r - bi * w;
         const T* src = dblk0 + (size_t)bi * dstride + qi;
-        for (int u = u0; u < w; u += ustep) cp_async_el(sd + (size_t)u * QCc + rr, src + (size_t)u * w);
+        for (int i = u0; i < nu; i += ustep) cp_async_el(sd + (size_t)i * QCc + rr, src + (size_t)s_ul[i] * w);
       }
       cp_async_wait_all();
     }
@@ -125,12 +151,12 @@ __device__ __forceinline__ void rotwin_block_smem_to(const double2* __restrict__
       for (int k = 0; k < 4; ++k) re[a][k] = im[a][k] = (T)0;
     const T* dp = sd + rg * TQ;
     const T2* bp = sB + cg;
-    for (int u = 0; u < w; ++u) {
+    for (int i = 0; i < nu; ++i) {
       T dq[TQ];
-      rot_unpack(*reinterpret_cast<const TV*>(dp + (size_t)u * QCc), dq);
+      rot_unpack(*reinterpret_cast<const TV*>(dp + (size_t)i * QCc), dq);
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const T2 bv = bp[(size_t)u * CC + 8 * k];
+        const T2 bv = bp[(size_t)i * CC + 8 * k];
 #pragma unroll
         for (int a = 0; a < TQ; ++a) {
           re[a][k] = fma(dq[a], bv.x, re[a][k]);
