@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="Poisson-arriving requests of the serving run (0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--profile-case", default="", choices=("", "window", "inverse_alt", "serve"),
+                    help="small case for kernel captures, then exit: the L_h = 64 window generator (8 x 3 "
+                         "degree ellipse), the inverse without h_0^0 at workload-2 sizes, or 300 served requests")
     ap.add_argument("--profile-pairs", type=int, default=0,
                     help="profiling case: two forwards (FP32_BULK) over the last N pairs of map 0, "
                          "48 pairs per chunk, then exit")
@@ -381,6 +384,41 @@ def profile_case(pkg, n, prec=1, wl=3, fp64_arith=0):
     ctx.close()
 
 
+def profile_case_other(pkg, case):
+    """Small cases of the other kernels for captures (one GPU, a few GB)."""
+    import numpy as np
+    import torch
+    import synth
+    ctx = pkg.Context(0, 16 << 30)
+    if case == "window":
+        for _ in range(2):
+            _, lam = ctx.window_ellipse(64, *synth.ellipse_from_axes(8.0, 3.0))
+        print(json.dumps({"profile_case": case, "concentration": lam}))
+    elif case == "inverse_alt":
+        c2 = synth.CONFIGS[2]
+        Lf, Lh, gr, p = c2["Lf"], c2["Lh"], c2["grid"], 2
+        f, h = synth.signal_powerlaw(Lf, 2000), synth.stored_window(2)[0].copy()
+        h[0] = 0.0
+        outs = synth.pairs_all(Lf)
+        pin = np.array(sorted({(int(L) + p, int(M) + q) for L, M in outs for q in range(-p, p + 1)}), dtype=np.int32)
+        g = ctx.forward(Lf, Lh, gr, f, h, pin, prec=1)
+        for _ in range(2):
+            fr = ctx.inverse_alt(Lf, Lh, gr, g, h, pin, p, outs, prec=1)
+        ft = f[outs[:, 0] ** 2 + outs[:, 0] + outs[:, 1]]
+        print(json.dumps({"profile_case": case, "rel_l2": float(np.linalg.norm(fr - ft) / np.linalg.norm(ft))}))
+    else:
+        reqs = serve_requests(300, 4000)
+        outs = []
+        for r in reqs:
+            dt = torch.complex128 if r["prec"] == 0 else torch.complex64
+            g = torch.empty((len(r["pairs"]),) + tuple(r["grid"]), dtype=dt, device="cuda")
+            outs.append((g, ctx.submit(r["Lf"], r["Lh"], r["grid"], r["f"], r["h"], r["pairs"], g, prec=r["prec"])))
+        ctx.drain(600000)
+        print(json.dumps({"profile_case": case, "completed": sum(ctx.poll(t) == 0 for _, t in outs)}))
+    torch.cuda.synchronize()
+    ctx.close()
+
+
 def serve_native(Lh):
     return (2 * Lh - 1, Lh, 2 * Lh - 1)
 
@@ -485,6 +523,9 @@ def main():
     import synth
 
     torch.cuda.set_device(local)
+    if args.profile_case:
+        profile_case_other(pkg, args.profile_case)
+        return
     if args.profile_pairs > 0:
         profile_case(pkg, args.profile_pairs, args.profile_prec, args.profile_workload, args.profile_fp64_arith)
         return

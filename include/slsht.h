@@ -227,6 +227,24 @@ int slsht_inverse_alt(slsht_ctx* ctx, const slsht_desc* desc, const void* g_in, 
                       const int32_t* lm_in, int32_t n_in, int32_t p, const int32_t* lm_out, int32_t n_out,
                       double* f_out, void* stream);
 
+/* g at arbitrary orientations gamma from the grid's gamma samples (Sec. IV-B,
+ * the remark on steerable windows: by linearity the distribution at any
+ * gamma follows from a few basis orientations).  g depends on gamma only
+ * through e^{-i q' gamma} for the window's orders |q'| <= Q, so with
+ * n_gamma >= 2Q + 1 samples it is recovered exactly at any gamma by the
+ * trigonometric interpolation of that band:
+ *   g(gamma) = sum_c g(gamma_c) (1 + 2 sum_{q'=1..Q} cos(q' (gamma - gamma_c))) / n_gamma.
+ * Q = L_h - 1 serves any window; a steerable window (h_p^q' = 0 for |q'| >= N)
+ * needs only Q = N - 1, i.e. 2N - 1 basis orientations.
+ *   g_in    device, laid out as slsht_forward's g_out for n_pairs pairs
+ *   gammas  double [n_g] angles in radians (host or device)
+ *   g_out   device [n_pairs][n_alpha][n_beta][n_g], same precision as g_in
+ * Errors: SLSHT_E_ARG (bad desc, Q outside [0, L_h - 1], n_gamma < 2Q + 1,
+ * g_in or g_out not in device memory), SLSHT_E_NOMEM, SLSHT_E_CUDA.  The
+ * weights and sums are FP64. */
+int slsht_steer_gamma(slsht_ctx* ctx, const slsht_desc* desc, const void* g_in, int32_t n_pairs,
+                      const double* gammas, int32_t n_g, int32_t Q, void* g_out, void* stream);
+
 /* ---------------------------------------------------------------- no-alloc */
 
 /* Size of the static device scratch array behind slsht_forward_noalloc. */

@@ -23,7 +23,7 @@ __all__ = ["Context", "make_desc", "SLSHT_FP64", "SLSHT_FP32_BULK", "SlshtError"
            "slsht_create", "slsht_destroy", "slsht_forward", "slsht_forward_noalloc", "slsht_forward_windows",
            "slsht_window_ellipse", "slsht_batch_create", "slsht_batch_launch", "slsht_batch_query",
            "slsht_batch_destroy", "slsht_tune", "Batch",
-           "slsht_inverse", "slsht_inverse_alt", "slsht_submit",
+           "slsht_inverse", "slsht_inverse_alt", "slsht_steer_gamma", "slsht_submit",
            "slsht_poll", "slsht_poll_times", "slsht_drain", "slsht_strerror", "slsht_check_args", "slsht_profile",
            "slsht_get_stats", "slsht_set_option", "slsht_mem_used", "slsht_version"]
 
@@ -89,6 +89,12 @@ def slsht_inverse_alt(ctx, desc, g_in, h_lm, lm_in, n_in, p, lm_out, n_out, f_ou
                                                     _abi.ptr(lm_in), int(n_in), int(p), _abi.ptr(lm_out),
                                                     int(n_out), _abi.ptr(f_out), _stream(stream)),
                       "slsht_inverse_alt")
+
+
+def slsht_steer_gamma(ctx, desc, g_in, n_pairs, gammas, n_g, Q, g_out, stream=None):
+    return _abi.check(_abi.load().slsht_steer_gamma(ctx, ctypes.byref(desc), _abi.ptr(g_in), int(n_pairs),
+                                                    _abi.ptr(gammas), int(n_g), int(Q), _abi.ptr(g_out),
+                                                    _stream(stream)), "slsht_steer_gamma")
 
 
 def slsht_forward_noalloc(desc, f_lm, h_lm, lm, n_pairs, g_out, stream=None):

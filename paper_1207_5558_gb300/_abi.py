@@ -88,6 +88,7 @@ def load(path=LIB_PATH):
         "slsht_inverse": (ctypes.c_int, [vp, ctypes.POINTER(slsht_desc), vp, vp, vp, i32, vp, vp]),
         "slsht_inverse_alt": (ctypes.c_int, [vp, ctypes.POINTER(slsht_desc), vp, vp, vp, i32, i32, vp, i32, vp,
                                              vp]),
+        "slsht_steer_gamma": (ctypes.c_int, [vp, ctypes.POINTER(slsht_desc), vp, i32, vp, i32, i32, vp, vp]),
         "slsht_forward_noalloc": (ctypes.c_int, [ctypes.POINTER(slsht_desc), vp, vp, vp, i32, vp, vp]),
         "slsht_forward_windows": (ctypes.c_int, [vp, ctypes.POINTER(slsht_desc), vp, i32, vp, vp, i32, vp, vp]),
         "slsht_window_ellipse": (ctypes.c_int, [vp, i32, ctypes.c_double, ctypes.c_double, i32, i32, vp,
@@ -145,7 +146,7 @@ class SlshtError(RuntimeError):
     def __init__(self, code, where):
         lib = load()
         msg = "%s: %s (%d)" % (where, lib.slsht_strerror(code).decode(), code)
-        if code == SLSHT_E_CUDA:
+        if code in (SLSHT_E_CUDA, SLSHT_E_TIMEOUT, SLSHT_E_NOMEM):
             msg += ": " + lib.slsht_last_error().decode()
         super().__init__(msg)
         self.code = code

@@ -2,7 +2,7 @@
 
 Every CUDA translation unit under csrc/ is compiled in parallel to an object
 file in _build/, then linked into lib/libslsht.so (CUDA runtime linked
-statically).  ``python -m paper_1207_5558_gb300.build`` or ``build()``.
+statically; no CUDA library beyond the runtime).  ``python -m paper_1207_5558_gb300.build`` or ``build()``.
 """
 import concurrent.futures as cf
 import os
@@ -61,7 +61,7 @@ def build(verbose=False, force=False):
             if log.strip():
                 print(os.path.basename(o), "\n", log, file=sys.stderr)
     tmp = LIB + ".tmp"
-    cmd = [_nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcublas", "-lpthread"]
+    cmd = [_nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))

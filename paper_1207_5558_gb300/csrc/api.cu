@@ -162,12 +162,18 @@ struct Request {
   double t_submit = 0, t_admit = -1, t_issue = -1;   // host clock, ms
   double dev_first = 1e300, dev_last = -1e300;       // device clock of its ticks, ms
   int status = SLSHT_OK;
+  // its rotated window (once per request, in the context's window pool)
+  size_t h_off = 0, h_len = 0;
+  bool h_have = false;
+  int h_lane = -1;                     // lane of the tick that computes it
+  uint64_t h_tick = 0;                 // that lane's tick number
 };
 
 // A chunk of consecutive pairs of one request, evaluated in one serving tick.
 struct SvChunk {
   Request* r;
   int p0, np;
+  bool comp_h;                         // the tick computes the request's rotated window
 };
 
 // One serving lane: a stream, a device arena with fixed list regions (the
@@ -181,6 +187,7 @@ struct SvLane {
   unsigned char* arena = nullptr;
   unsigned char* stage = nullptr;
   bool busy = false;
+  uint64_t tick = 0;                   // ticks issued on this lane
   std::vector<SvChunk> chunks;
   double t_assemble = 0;
   cudaGraph_t graph = nullptr;
@@ -201,6 +208,8 @@ struct SvLane {
 #define SV_DEV_BYTES ((size_t)896 << 20)      // k, H and their double-float forms per tick
 #define SV_TICK_SAMPLES (32ll << 20)          // samples per tick (bounds a tick's duration)
 #define SV_CHUNK_SAMPLES (8ll << 20)          // first share of one request in a tick
+#define SV_HPOOL_BYTES ((size_t)4 << 30)      // rotated windows of the started requests
+#define SV_EXPRESS_SAMPLES (4ll << 20)        // requests this small run on the express lane
 
 // Byte offsets of a serving arena's regions (the same in the pinned stage,
 // which mirrors the lists and the staged inputs).
@@ -263,6 +272,8 @@ struct slsht_ctx {
   struct Final { int st; double t[4]; };
   std::map<uint64_t, Final> status;                  // pending (SLSHT_PENDING) or final, per ticket
   SvLane lanes[SERVE_LANES];
+  unsigned char* sv_hpool = nullptr;                 // rotated windows of the started requests
+  std::map<size_t, size_t> sv_hfree;                 // free blocks of the pool: offset -> length
   cudaEvent_t sv_ref = nullptr;                      // device-clock origin of the serving ticks
   bool sv_ready = false;
   std::thread worker;
@@ -622,6 +633,7 @@ extern "C" void slsht_destroy(slsht_ctx* c) {
     if (ln.stage) cudaFreeHost(ln.stage);
     ctx_free(c, ln.arena, sv_layout().total);
   }
+  ctx_free(c, c->sv_hpool, SV_HPOOL_BYTES);
   if (c->sv_ref) cudaEventDestroy(c->sv_ref);
   ws_release(c, c->sync_ws);
   for (auto& kv : c->delta) free_entry(c, kv.second);
@@ -1417,6 +1429,37 @@ extern "C" int slsht_inverse_alt(slsht_ctx* ctx, const slsht_desc* desc, const v
   CK(cudaEventRecord(w.done, st));
   // the host arrays above are read by the stream's copies: wait for them
   CK(cudaStreamSynchronize(st));
+  return SLSHT_OK;
+}
+
+extern "C" int slsht_steer_gamma(slsht_ctx* ctx, const slsht_desc* desc, const void* g_in, int32_t n_pairs,
+                                 const double* gammas, int32_t n_g, int32_t Q, void* g_out, void* stream) {
+  if (!ctx) return SLSHT_E_ARG;
+  CKS(check_desc(desc));
+  if (n_pairs < 0 || n_g < 0) return SLSHT_E_ARG;
+  if (n_pairs == 0 || n_g == 0) return SLSHT_OK;
+  if (!g_in || !gammas || !g_out) return SLSHT_E_ARG;
+  if (Q < 0 || Q >= desc->L_h || desc->n_gamma < 2 * Q + 1) return SLSHT_E_ARG;
+  DeviceGuard g(ctx->device);
+  if (!is_device_ptr(g_in) || !is_device_ptr(g_out)) return SLSHT_E_ARG;
+  std::lock_guard<std::mutex> serial(ctx->sync_mu);
+  Workspace& w = ctx->sync_ws;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaStreamWaitEvent(st, w.done, 0));
+  const size_t wbytes = sizeof(double) * ((size_t)n_g * desc->n_gamma + (size_t)n_g);
+  CKS(ws_reserve(ctx, w, &w.ms, &w.ms_cap, wbytes));
+  double* W = (double*)w.ms;
+  double* gam = W + (size_t)n_g * desc->n_gamma;
+  {
+    StageTimer t(ctx, SLSHT_STAGE_COPY, st);
+    CK(cudaMemcpyAsync(gam, gammas, sizeof(double) * (size_t)n_g,
+                       is_device_ptr(gammas) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  }
+  const long long rows = (long long)n_pairs * desc->n_alpha * desc->n_beta;
+  LAUNCH(SLSHT_STAGE_OTHER, st,
+         launch_steer_gamma(g_in, desc->prec == SLSHT_FP64 ? 0 : 1, rows, desc->n_gamma, gam, n_g, Q, W, g_out, st));
+  CK(cudaEventRecord(w.done, st));
+  if (!is_device_ptr(gammas)) CK(cudaStreamSynchronize(st));   // the host angles are read by the copy
   return SLSHT_OK;
 }
 
@@ -2234,9 +2277,13 @@ static double sv_now_ms() {
 static int sv_init(slsht_ctx* c) {
   if (c->sv_ready) return SLSHT_OK;
   const SvLayout L = sv_layout();
+  int prio_low = 0, prio_high = 0;
+  CK(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
   for (auto& ln : c->lanes) {
-    CK(cudaStreamCreateWithFlags(&ln.st, cudaStreamNonBlocking));
-    for (auto& sd : ln.side) CK(cudaStreamCreateWithFlags(&sd, cudaStreamNonBlocking));
+    // lane 0 is the express lane (small requests, high priority)
+    const int prio = &ln == &c->lanes[0] ? prio_high : prio_low;
+    CK(cudaStreamCreateWithPriority(&ln.st, cudaStreamNonBlocking, prio));
+    for (auto& sd : ln.side) CK(cudaStreamCreateWithPriority(&sd, cudaStreamNonBlocking, prio));
     for (auto& ev : ln.fork) CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     CK(cudaEventCreate(&ln.ev_a));
     CK(cudaEventCreate(&ln.ev_b));
@@ -2244,6 +2291,13 @@ static int sv_init(slsht_ctx* c) {
     CKS(ctx_alloc(c, L.total, &a));
     ln.arena = (unsigned char*)a;
     CK(cudaHostAlloc((void**)&ln.stage, L.stage, cudaHostAllocDefault));
+  }
+  {
+    void* hp = nullptr;
+    CKS(ctx_alloc(c, SV_HPOOL_BYTES, &hp));
+    c->sv_hpool = (unsigned char*)hp;
+    c->sv_hfree.clear();
+    c->sv_hfree[0] = SV_HPOOL_BYTES;
   }
   CK(cudaEventCreate(&c->sv_ref));
   CK(cudaEventRecord(c->sv_ref, c->lanes[0].st));
@@ -2253,36 +2307,91 @@ static int sv_init(slsht_ctx* c) {
 }
 
 // Bytes a chunk of np pairs needs in the device-only region, and its staged inputs.
-static size_t sv_dev_bytes(const Request& r, int np) {
+// Whether a request reads the double-float forms of k and H (the
+// double-float engine, and the FP64 tensor-core engine's digit producer).
+static bool sv_ddform(const Request& r) {
+  return r.engine == ENG_DD || (r.engine == ENG_TC && r.desc.prec == SLSHT_FP64);
+}
+// The tensor-core engines' operand scratch of a chunk of np pairs (the FP64
+// digits of up to T64_CHUNK pairs, the wide FP32 engine's operand of up to
+// XW_CHUNK pairs; none for the fused FP32 kernel).
+static size_t sv_xw_bytes(const Request& r, int np) {
+  const slsht_desc& d = r.desc;
+  if (r.engine != ENG_TC) return 0;
+  if (d.prec == SLSHT_FP64) return sv_up(tc64_xblob_bytes(d.n_beta, d.n_gamma) * (size_t)std::min(np, T64_CHUNK));
+  if (d.L_h > 16) return sv_up(tcw_xblob_bytes(d.n_beta, d.n_gamma, d.L_h) * (size_t)std::min(np, XW_CHUNK));
+  return 0;
+}
+// Bytes of a request's rotated window in the pool (with the double-float
+// form's scale exponent).
+static size_t sv_h_bytes(const Request& r) {
   const slsht_desc& d = r.desc;
   const size_t n2 = (size_t)d.L_h * d.L_h, J = (size_t)d.n_beta * d.n_gamma;
+  return sv_ddform(r) ? sv_up(sizeof(float4) * h_elems(J, (int)n2)) + 256
+                      : sv_up(el2_of(d.prec) * h_elems(J, (int)n2));
+}
+static size_t sv_dev_bytes(const Request& r, int np) {
+  const size_t n2 = (size_t)r.desc.L_h * r.desc.L_h;
   size_t b = sv_up(sizeof(double2) * np * n2);
-  if (r.engine == ENG_DD)
-    b += sv_up(sizeof(float4) * np * n2) + sv_up(sizeof(int) * np) + sv_up(sizeof(float4) * h_elems(J, (int)n2)) + 256;
-  else
-    b += sv_up(el2_of(d.prec) * h_elems(J, (int)n2));
-  return b;
+  if (sv_ddform(r)) b += sv_up(sizeof(float4) * np * n2) + sv_up(sizeof(int) * np);
+  return b + sv_xw_bytes(r, np);
+}
+// First-fit allocation from the window pool; false when nothing fits.
+static bool sv_halloc(slsht_ctx* c, size_t len, size_t* off) {
+  for (auto it = c->sv_hfree.begin(); it != c->sv_hfree.end(); ++it) {
+    if (it->second < len) continue;
+    *off = it->first;
+    const size_t rest = it->second - len;
+    const size_t at = it->first + len;
+    c->sv_hfree.erase(it);
+    if (rest) c->sv_hfree[at] = rest;
+    return true;
+  }
+  return false;
+}
+static void sv_hrelease(slsht_ctx* c, size_t off, size_t len) {
+  auto it = c->sv_hfree.emplace(off, len).first;
+  auto nx = std::next(it);
+  if (nx != c->sv_hfree.end() && it->first + it->second == nx->first) {
+    it->second += nx->second;
+    c->sv_hfree.erase(nx);
+  }
+  if (it != c->sv_hfree.begin()) {
+    auto pv = std::prev(it);
+    if (pv->first + pv->second == it->first) {
+      pv->second += it->second;
+      c->sv_hfree.erase(it);
+    }
+  }
 }
 static size_t sv_in_bytes(const Request& r, int np) {
   return sv_up(sizeof(double2) * (size_t)r.desc.L_f * r.desc.L_f) + sv_up(sizeof(double2) * (size_t)r.desc.L_h * r.desc.L_h) +
          sv_up(sizeof(int2) * (size_t)np);
 }
 static long long sv_tiles_per_pair(const Request& r) {
+  if (r.engine == ENG_TC) return 0;                  // the tensor-core kernels take no tiles
   const long long J = (long long)r.desc.n_beta * r.desc.n_gamma;
   return (J + r.nt - 1) / r.nt;
 }
 static int sv_rblk_count(const Request& r) {
-  const RotChunks ch = rot_chunks(r.desc.L_h, r.desc.n_gamma, r.engine == ENG_NATIVE && r.desc.prec != SLSHT_FP64
-                                                                 ? sizeof(float2) : sizeof(double2));
+  const RotChunks ch = rot_chunks(r.desc.L_h, r.desc.n_gamma, sv_ddform(r) || r.desc.prec == SLSHT_FP64
+                                                                 ? sizeof(double2) : sizeof(float2));
   return ((r.desc.n_beta + ROTWIN_NB - 1) / ROTWIN_NB) * r.desc.L_h * ch.nq * ch.nc;
 }
 
 // The alpha tile shape of a request: the tuner's cache for its grid shape on
 // CUDA cores, else the rule of SLSHT_BATCH_NO_TUNE.
+static bool sv_tc_ok(const slsht_desc& d) {
+  if (d.prec == SLSHT_FP64) return tc64_supported(d.L_h, d.n_alpha);
+  return (tc_supported(d.L_h, d.n_alpha) && d.L_h <= 16) || tcw_supported(d.L_h, d.n_alpha);
+}
 static void sv_choose(slsht_ctx* c, Request& r) {
   const slsht_desc& d = r.desc;
   const long long J = (long long)d.n_beta * d.n_gamma;
-  const int allowed = d.prec == SLSHT_FP64 ? 6 : 4;
+  const bool tc = sv_tc_ok(d);
+  // engines allowed: the tensor cores where they apply, double-float and FP64
+  // for FP64 requests, FP32 CUDA cores for FP32_BULK (the tuner cache's key)
+  const int allowed = (tc ? 1 : 0) | (d.prec == SLSHT_FP64 ? 6 : 4);
   {
     std::lock_guard<std::mutex> g(c->mu);
     auto f = c->tune.find(std::make_tuple((int)d.prec, d.L_h, d.n_alpha, d.n_beta, d.n_gamma, allowed));
@@ -2291,22 +2400,72 @@ static void sv_choose(slsht_ctx* c, Request& r) {
       return;
     }
   }
-  r.engine = d.prec == SLSHT_FP64 ? ENG_DD : ENG_NATIVE;
+  r.engine = tc ? ENG_TC : (d.prec == SLSHT_FP64 ? ENG_DD : ENG_NATIVE);
   r.nt = r.engine == ENG_DD ? dd_rule_cols(d.L_h, J) : batch_rule_nt(1, d.L_h, J);
-  r.form = alpha_split_factor(d.L_h, d.n_alpha);
+  r.form = r.engine == ENG_TC ? -1 : alpha_split_factor(d.L_h, d.n_alpha);
+}
+
+// The tensor-core launches of one chunk (after the graph's coupling and
+// rotated window): the fused FP32 kernel (L_h <= 16), the wide engine's
+// producer and alpha kernel per XW_CHUNK pairs, or the FP64 digit producer and
+// alpha kernel per T64_CHUNK pairs.
+struct SvTc {
+  const double2* kc;
+  const float4* kdd;
+  const int* kexp;
+  const void* H;
+  const int* hexp;
+  const void* etab;
+  void* xw;
+  int prec, Lh, Na, Nb, Ng, np;
+  void* g;
+};
+static cudaError_t sv_tc_launch(slsht_ctx* c, const SvTc& t, cudaStream_t st) {
+  const int n2 = t.Lh * t.Lh;
+  const size_t per_pair = (size_t)t.Na * t.Nb * t.Ng;
+  if (t.prec == SLSHT_FP64) {
+    for (int off = 0; off < t.np; off += T64_CHUNK) {
+      const int n = std::min(T64_CHUNK, t.np - off);
+      cudaError_t e = launch_xa64(t.kdd + (size_t)off * n2, t.kexp + off, (const float4*)t.H, t.hexp, t.Lh, t.Nb,
+                                  t.Ng, n, t.xw, st);
+      if (e == cudaSuccess)
+        e = launch_alpha_tc64(t.xw, t.etab, t.Lh, t.Na, t.Nb, t.Ng, n, (double2*)t.g + per_pair * off, c->num_sms,
+                              nullptr, st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  if (t.Lh <= 16)
+    return launch_alpha_fused(t.kc, (const float2*)t.H, t.etab, t.Lh, t.Na, t.Nb, t.Ng, t.np, (float2*)t.g,
+                              c->num_sms, 0, nullptr, st);
+  for (int off = 0; off < t.np; off += XW_CHUNK) {
+    const int n = std::min(XW_CHUNK, t.np - off);
+    cudaError_t e = launch_xaw_from_h(t.kc + (size_t)off * n2, (const float2*)t.H, t.Lh, t.Nb, t.Ng, n, t.xw, st);
+    if (e == cudaSuccess)
+      e = launch_alpha_tcw(t.xw, t.etab, t.Lh, t.Na, t.Nb, t.Ng, n, (float2*)t.g + per_pair * off, c->num_sms, nullptr,
+                           st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 // Captures the lane's launch sequence with shared-memory sizes rot_smem and
 // alpha_smem[3] (the graph reads the arena's fixed list addresses).
 static int sv_capture(slsht_ctx* c, SvLane& ln, size_t rot_smem, const size_t* alpha_smem) {
+  // the bulk lanes' persistent kernels leave one block slot per SM free, so
+  // that the express lane's blocks start without waiting for them to finish
+  const bool express = &ln == &c->lanes[0];
   const SvLayout L = sv_layout();
   unsigned char* A = ln.arena;
   const int* hdr = (const int*)(A + L.hdr);
   int* ctr = (int*)(A + L.hdr) + 8;
   const int sms = c->num_sms;
   int agrid[3];
-  for (int pi = 0; pi < 3; ++pi) agrid[pi] = sms * batch_alpha_occupancy(pi, alpha_smem[pi]);
-  const int rgrid = sms * batch_rotwin_occupancy(rot_smem);
+  // (when at least three fit: below that the slot costs the bulk too much)
+  auto keep = [&](int occ) { return express || occ < 3 ? occ : occ - 1; };
+  for (int pi = 0; pi < 3; ++pi) agrid[pi] = sms * keep(batch_alpha_occupancy(pi, alpha_smem[pi]));
+  const int rgrid = sms * keep(batch_rotwin_occupancy(rot_smem));
+  const int cgrid = sms * (express ? 4 : 2);
   if (ln.exec) { cudaGraphExecDestroy(ln.exec); ln.exec = nullptr; }
   if (ln.graph) { cudaGraphDestroy(ln.graph); ln.graph = nullptr; }
   // branches: {couplings, double-float k} || {rotated windows}, then the
@@ -2319,10 +2478,10 @@ static int sv_capture(slsht_ctx* c, SvLane& ln, size_t rot_smem, const size_t* a
     e = launch_batch_rotwin_n((const BRot*)(A + L.rot), (const BRotBlk*)(A + L.rblk), hdr + 4, rgrid, rot_smem,
                               ln.side[0]);
   for (int cls = 0; cls < 3 && e == cudaSuccess; ++cls)
-    e = launch_serve_couple(cls, (const BCouple*)(A + L.cpl), (const int2*)(A + L.cplp[cls]), hdr + cls, sms * 4,
+    e = launch_serve_couple(cls, (const BCouple*)(A + L.cpl), (const int2*)(A + L.cplp[cls]), hdr + cls, cgrid,
                             ln.st);
   if (e == cudaSuccess)
-    e = launch_batch_kdd_n((const BCouple*)(A + L.cpl), (const BCplBlk*)(A + L.kblk), hdr + 3, sms * 4, ln.st);
+    e = launch_batch_kdd_n((const BCouple*)(A + L.cpl), (const BCplBlk*)(A + L.kblk), hdr + 3, cgrid, ln.st);
   if (e == cudaSuccess) e = cudaEventRecord(ln.fork[1], ln.side[0]);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(ln.st, ln.fork[1], 0);
   if (e == cudaSuccess) e = cudaEventRecord(ln.fork[0], ln.st);
@@ -2362,31 +2521,47 @@ static int sv_tick(slsht_ctx* c, SvLane& ln, std::unique_lock<std::mutex>& lk) {
   long long samples = 0, tiles[3] = {0, 0, 0};
   size_t dev = 0, in = 0;
   int npairs[3] = {0, 0, 0}, nkblk = 0, nrblk = 0;
+  const bool express = &ln == &c->lanes[0];
   for (auto& up : c->active) {
     Request& r = *up;
     if (r.next >= r.n_pairs) continue;
     if (samples >= SV_TICK_SAMPLES || (int)ch.size() >= SV_ITEMS) break;
     const slsht_desc& d = r.desc;
     const long long spp = (long long)d.n_alpha * d.n_beta * d.n_gamma;
-    int np = (int)std::min<long long>(r.n_pairs - r.next, std::max<long long>(1, SV_CHUNK_SAMPLES / spp));
+    if (((long long)r.n_pairs * spp <= SV_EXPRESS_SAMPLES) != express) continue;   // the other lanes' request
+    // express ticks share among their small requests; bulk ticks serve the
+    // oldest request first, as much of it as the tick holds (first come,
+    // first served: the large requests are not time-sliced against each other)
+    int np = (int)std::min<long long>(r.n_pairs - r.next,
+                                      std::max<long long>(1, express ? SV_CHUNK_SAMPLES / spp : SV_TICK_SAMPLES / spp));
     np = (int)std::min<long long>(np, std::max<long long>(1, (SV_TICK_SAMPLES - samples) / spp));
     const int cls = d.L_h <= 16 ? 0 : (d.L_h <= 32 ? 1 : 2);
     const int kp = r.engine == ENG_DD ? 2 : (d.prec == SLSHT_FP64 ? 0 : 1);
-    const int rb = sv_rblk_count(r);
+    // the request's rotated window lives in the window pool from its first
+    // tick to its completion (admission by memory: wait for room)
+    if (!r.h_have) {
+      const size_t hb = sv_h_bytes(r);
+      if (!sv_halloc(c, hb, &r.h_off)) continue;
+      r.h_len = hb;
+      r.h_have = true;
+      r.h_lane = -1;
+    }
+    const bool comp_h = r.h_lane < 0;
+    const int rb = comp_h ? sv_rblk_count(r) : 0;
     const long long tpp = sv_tiles_per_pair(r);
     // the largest np that fits every region and list
     auto fits = [&](int n) {
       return dev + sv_dev_bytes(r, n) <= SV_DEV_BYTES && in + sv_in_bytes(r, n) <= SV_STAGE_IN &&
-             npairs[cls] + n <= SV_PAIRS && (r.engine != ENG_DD || nkblk + n <= SV_PAIRS) && nrblk + rb <= SV_RBLK &&
+             npairs[cls] + n <= SV_PAIRS && (!sv_ddform(r) || nkblk + n <= SV_PAIRS) && nrblk + rb <= SV_RBLK &&
              tiles[kp] + tpp * n <= SV_TILES;
     };
     while (np > 0 && !fits(np)) np /= 2;
     if (np == 0) break;
-    ch.push_back({&r, r.next, np});
+    ch.push_back({&r, r.next, np, comp_h});
     dev += sv_dev_bytes(r, np);
     in += sv_in_bytes(r, np);
     npairs[cls] += np;
-    if (r.engine == ENG_DD) nkblk += np;
+    if (sv_ddform(r)) nkblk += np;
     nrblk += rb;
     tiles[kp] += tpp * np;
     samples += spp * np;
@@ -2407,14 +2582,14 @@ static int sv_tick(slsht_ctx* c, SvLane& ln, std::unique_lock<std::mutex>& lk) {
     auto fits = [&](int n) {
       return dev - sv_dev_bytes(r, k.np) + sv_dev_bytes(r, k.np + n) <= SV_DEV_BYTES &&
              in - sv_in_bytes(r, k.np) + sv_in_bytes(r, k.np + n) <= SV_STAGE_IN && npairs[cls] + n <= SV_PAIRS &&
-             (r.engine != ENG_DD || nkblk + n <= SV_PAIRS) && tiles[kp] + tpp * n <= SV_TILES;
+             (!sv_ddform(r) || nkblk + n <= SV_PAIRS) && tiles[kp] + tpp * n <= SV_TILES;
     };
     while (extra > 0 && !fits(extra)) extra /= 2;
     if (extra == 0) continue;
     dev += sv_dev_bytes(r, k.np + extra) - sv_dev_bytes(r, k.np);
     in += sv_in_bytes(r, k.np + extra) - sv_in_bytes(r, k.np);
     npairs[cls] += extra;
-    if (r.engine == ENG_DD) nkblk += extra;
+    if (sv_ddform(r)) nkblk += extra;
     tiles[kp] += tpp * extra;
     samples += spp * extra;
     k.np += extra;
@@ -2438,6 +2613,11 @@ static int sv_tick(slsht_ctx* c, SvLane& ln, std::unique_lock<std::mutex>& lk) {
   size_t in_off = 0, dev_off = 0;
   size_t rot_smem = ln.g_rot_smem, asmem[3] = {ln.g_alpha_smem[0], ln.g_alpha_smem[1], ln.g_alpha_smem[2]};
   int st = SLSHT_OK;
+  const int lane_ix = (int)(&ln - c->lanes);
+  const uint64_t tick_no = ln.tick + 1;
+  int nrot = 0;
+  bool wait_lane[SERVE_LANES] = {false};
+  std::vector<SvTc> tcs;
   CK(cudaEventRecord(ln.ev_a, ln.st));
   // items in decreasing tile cost, so the large tiles start first
   std::vector<int> order(ch.size());
@@ -2449,11 +2629,12 @@ static int sv_tick(slsht_ctx* c, SvLane& ln, std::unique_lock<std::mutex>& lk) {
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(ch[a]) > cost(ch[b]); });
   for (size_t ii = 0; ii < ch.size() && st == SLSHT_OK; ++ii) {
     const SvChunk& k = ch[ii];
-    const Request& r = *k.r;
+    Request& r = *k.r;
     const slsht_desc& d = r.desc;
     const int Lh = d.L_h, n2 = Lh * Lh, K = 2 * Lh - 1, np = k.np;
     const size_t J = (size_t)d.n_beta * d.n_gamma;
-    const bool dd = r.engine == ENG_DD;
+    const bool dd = sv_ddform(r);                       // double-float k and H
+    const bool tcx = r.engine == ENG_TC;
     const int rprec = (dd || d.prec == SLSHT_FP64) ? SLSHT_FP64 : SLSHT_FP32_BULK;   // rotated window's
     // staged inputs
     const size_t fo = in_off, fb = sizeof(double2) * (size_t)d.L_f * d.L_f;
@@ -2483,22 +2664,28 @@ static int sv_tick(slsht_ctx* c, SvLane& ln, std::unique_lock<std::mutex>& lk) {
     const RotChunks rc = rot_chunks(Lh, d.n_gamma, el2_of(rprec));
     rr.QC = rc.QC; rr.CC = rc.CC; rr.nq = rc.nq; rr.nc = rc.nc;
     rot_smem = std::max(rot_smem, rc.smem(Lh, el2_of(rprec)));
+    unsigned char* hbase = c->sv_hpool + r.h_off;      // the request's rotated window
     if (dd) {
       cc.kdd = (float4*)dalloc(sizeof(float4) * (size_t)np * n2);
       cc.kexp = (int*)dalloc(sizeof(int) * (size_t)np);
-      rr.Hdd = (float4*)dalloc(sizeof(float4) * h_elems(J, n2));
-      rr.hexp = (int*)dalloc(16);
+      rr.Hdd = (float4*)hbase;
+      rr.hexp = (int*)(hbase + r.h_len - 256);
     } else {
-      rr.H = dalloc(el2_of(d.prec) * h_elems(J, n2));
+      rr.H = hbase;
     }
+    if (!k.comp_h && r.h_lane != lane_ix && c->lanes[r.h_lane].busy && c->lanes[r.h_lane].tick == r.h_tick)
+      wait_lane[r.h_lane] = true;                        // computed by a tick still on another lane
     BItem bi{};
+    const void* etab = nullptr;
     {
       std::lock_guard<std::mutex> g(c->mu);
       const void *dt = nullptr, *eg = nullptr, *csa = nullptr;
       st = get_dtab(c, Lh, d.n_beta, rprec, ln.st, &dt);
       if (st == SLSHT_OK) st = get_phase(c, d.n_gamma, K, -(Lh - 1), rprec, ln.st, &eg);
       const int aprec = dd ? PREC_DD : d.prec;
-      if (st == SLSHT_OK)
+      if (st == SLSHT_OK && tcx)
+        st = d.prec == SLSHT_FP64 ? get_etab64(c, d.n_alpha, ln.st, &etab) : get_etab(c, d.n_alpha, Lh, ln.st, &etab);
+      else if (st == SLSHT_OK)
         st = r.form > 0 ? get_phase(c, d.n_alpha, K, -(Lh - 1), aprec, ln.st, &csa)
                         : get_phase(c, d.n_alpha, Lh, 0, aprec, ln.st, &csa);
       rr.dt = dt;
@@ -2510,9 +2697,15 @@ static int sv_tick(slsht_ctx* c, SvLane& ln, std::unique_lock<std::mutex>& lk) {
     for (int pr = 0; pr < np; ++pr) cplp[cls][hdr[cls]++] = make_int2(idx, pr);
     if (dd)
       for (int pr = 0; pr < np; ++pr) kblk[hdr[3]++] = BCplBlk{idx, pr};
-    for (int bb = 0; bb < d.n_beta; bb += ROTWIN_NB)
-      for (int pp = 0; pp < Lh; ++pp)
-        for (int z = 0; z < rc.nq * rc.nc; ++z) rblk[hdr[4]++] = BRotBlk{idx, bb, pp, z};
+    if (k.comp_h) {                                      // the window, once per request
+      const int ri = nrot++;
+      rot[ri] = rr;
+      for (int bb = 0; bb < d.n_beta; bb += ROTWIN_NB)
+        for (int pp = 0; pp < Lh; ++pp)
+          for (int z = 0; z < rc.nq * rc.nc; ++z) rblk[hdr[4]++] = BRotBlk{ri, bb, pp, z};
+      r.h_lane = lane_ix;
+      r.h_tick = tick_no;
+    }
     bi.kc = cc.kc;
     bi.H = dd ? (const void*)rr.Hdd : (const void*)rr.H;
     const size_t per_pair_g = (size_t)d.n_alpha * J * el2_of(d.prec);
@@ -2527,12 +2720,31 @@ static int sv_tick(slsht_ctx* c, SvLane& ln, std::unique_lock<std::mutex>& lk) {
     bi.nt = r.nt;
     bi.form = std::max(r.form, 0);
     cpl[idx] = cc;
-    rot[idx] = rr;
     item[idx] = bi;
-    asmem[bi.prec] = std::max(asmem[bi.prec], batch_alpha_smem(bi.prec, Lh, r.nt));
+    if (tcx) {                       // a tensor-core engine, launched after the graph
+      SvTc t{};
+      t.kc = cc.kc;
+      t.kdd = cc.kdd;
+      t.kexp = cc.kexp;
+      t.H = dd ? (const void*)rr.Hdd : (const void*)rr.H;
+      t.hexp = rr.hexp;
+      t.etab = etab;
+      t.xw = sv_xw_bytes(r, np) ? (void*)dalloc(sv_xw_bytes(r, np)) : nullptr;
+      t.prec = d.prec;
+      t.Lh = Lh;
+      t.Na = d.n_alpha;
+      t.Nb = d.n_beta;
+      t.Ng = d.n_gamma;
+      t.np = np;
+      t.g = bi.g;
+      tcs.push_back(t);
+    } else {
+      asmem[bi.prec] = std::max(asmem[bi.prec], batch_alpha_smem(bi.prec, Lh, r.nt));
+    }
   }
   for (int oi : order) {          // tiles in decreasing cost
     const SvChunk& k = ch[oi];
+    if (k.r->engine == ENG_TC) continue;
     const BItem& bi = item[oi];
     for (int pr = 0; pr < k.np; ++pr)
       for (int j0 = 0; j0 < bi.J; j0 += bi.nt) tl[bi.prec][hdr[5 + bi.prec]++] = BTile{oi, pr, pr, j0};
@@ -2554,7 +2766,9 @@ static int sv_tick(slsht_ctx* c, SvLane& ln, std::unique_lock<std::mutex>& lk) {
   const int n = (int)ch.size();
   if (st == SLSHT_OK) st = put(L.hdr, 64);
   if (st == SLSHT_OK) st = put(L.cpl, sizeof(BCouple) * n);
-  if (st == SLSHT_OK) st = put(L.rot, sizeof(BRot) * n);
+  if (st == SLSHT_OK) st = put(L.rot, sizeof(BRot) * nrot);
+  for (int li = 0; li < SERVE_LANES && st == SLSHT_OK; ++li)
+    if (wait_lane[li] && cudaStreamWaitEvent(ln.st, c->lanes[li].ev_b, 0) != cudaSuccess) st = SLSHT_E_CUDA;
   if (st == SLSHT_OK) st = put(L.item, sizeof(BItem) * n);
   for (int cl = 0; cl < 3 && st == SLSHT_OK; ++cl) st = put(L.cplp[cl], sizeof(int2) * hdr[cl]);
   if (st == SLSHT_OK) st = put(L.kblk, sizeof(BCplBlk) * hdr[3]);
@@ -2564,6 +2778,13 @@ static int sv_tick(slsht_ctx* c, SvLane& ln, std::unique_lock<std::mutex>& lk) {
   if (st == SLSHT_OK && cudaGraphLaunch(ln.exec, ln.st) != cudaSuccess) {
     cudaGetLastError();
     st = SLSHT_E_CUDA;
+  }
+  for (const SvTc& t : tcs) {
+    if (st != SLSHT_OK) break;
+    if (sv_tc_launch(c, t, ln.st) != cudaSuccess) {
+      cudaGetLastError();
+      st = SLSHT_E_CUDA;
+    }
   }
   if (st == SLSHT_OK && cudaEventRecord(ln.ev_b, ln.st) != cudaSuccess) st = SLSHT_E_CUDA;
   const double t1 = sv_now_ms();
@@ -2584,6 +2805,7 @@ static int sv_tick(slsht_ctx* c, SvLane& ln, std::unique_lock<std::mutex>& lk) {
   }
   ln.chunks = std::move(ch);
   ln.busy = true;
+  ln.tick = tick_no;
   ln.t_assemble = t0;
   return st == SLSHT_OK ? (int)ln.chunks.size() : st;
 }
@@ -2614,6 +2836,7 @@ static void sv_retire(slsht_ctx* c, SvLane& ln) {
   for (size_t i = 0; i < c->active.size();) {
     Request& r = *c->active[i];
     if (r.done >= r.n_pairs || (r.status != SLSHT_OK && r.next >= r.n_pairs && r.done >= r.next)) {
+      if (r.h_have) sv_hrelease(c, r.h_off, r.h_len);
       slsht_ctx::Final fin{r.status, {r.t_admit - r.t_submit, r.t_issue, r.dev_last - r.dev_first, now - r.t_submit}};
       c->status[r.id] = fin;
       c->active.erase(c->active.begin() + (long)i);
@@ -2642,11 +2865,11 @@ static void worker_loop(slsht_ctx* c) {
     }
     bool issued = false;
     if (init == SLSHT_OK) {
-      for (auto& ln : c->lanes) {
+      for (auto& ln : c->lanes) {    // every free lane, the express lane first
         if (ln.busy) continue;
         const int n = sv_tick(c, ln, l);
         if (n > 0) issued = true;
-        break;                       // one tick per pass: completions are seen between ticks
+        if (n != 0 && &ln != &c->lanes[0]) break;   // one bulk tick per pass: completions are seen between
       }
     }
     bool busy = false;
@@ -2701,6 +2924,7 @@ extern "C" int slsht_submit(slsht_ctx* c, const slsht_desc* desc, const double* 
     probe.nt = 32;
     const long long J = (long long)desc->n_beta * desc->n_gamma;
     if (sv_dev_bytes(probe, 1) > SV_DEV_BYTES || sv_in_bytes(probe, 1) > SV_STAGE_IN ||
+        sv_h_bytes(probe) > SV_HPOOL_BYTES ||
         sv_rblk_count(probe) > SV_RBLK || (J + 31) / 32 > SV_TILES) {
       slsht_record_error_text("slsht_submit: one pair of this request exceeds a serving tick's arena");
       return SLSHT_E_NOMEM;

@@ -132,6 +132,11 @@ int inverse_col_blocks(int Nb, int Ng);
 // eg: (cos, sin)(q' gamma_c), q' = -p..p, FP64.  hp: h_p^q', q' = -p..p.
 // partial: n_in * ialt_col_blocks * (2p+1); khat: n_in * (2p+1);
 // rows[o * (2p+1) + q + p]: the g row of (L + p, M + q) for output o.
+// g at arbitrary gamma (steer.cu): out[row][k] = sum_c w_c(gam[k]) g[row][c]
+// over rows = pairs * n_alpha * n_beta rows of Ngam samples, the Dirichlet
+// weights of the band |q'| <= Q written to W (ng * Ngam doubles).
+cudaError_t launch_steer_gamma(const void* g, int prec, long long rows, int Ngam, const double* gam, int ng, int Q,
+                               double* W, void* out, cudaStream_t st);
 int ialt_col_blocks(int Nb, int Ng);
 cudaError_t launch_inverse_alt(const void* g, int prec, const double* wb, const double* dt, int Lh,
                                const double2* hp, const void* ea, const double2* eg, int Na, int Nb, int Ng, int p,

@@ -33,6 +33,48 @@ __device__ __forceinline__ float two_sum(float a, float b, float* e) {
   return s;
 }
 
+// Two floats in one 64-bit register pair for the packed FP32x2 instructions
+// of sm_100 and later: one instruction computes both halves, each rounded
+// exactly as the scalar instruction would (IEEE round to nearest, never
+// contracted), so code on pairs gives the bits of the scalar code at half the
+// issue slots.
+typedef unsigned long long f2p;
+__device__ __forceinline__ f2p pk2(float a, float b) {
+  f2p r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void up2(f2p v, float* a, float* b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(*a), "=f"(*b) : "l"(v));
+}
+__device__ __forceinline__ f2p add2(f2p a, f2p b) {
+  f2p r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2p sub2(f2p a, f2p b) {
+  f2p r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2p mul2(f2p a, f2p b) {
+  f2p r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2p fma2(f2p a, f2p b, f2p c) {
+  f2p r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+// two_sum on both halves
+__device__ __forceinline__ f2p two_sum2(f2p a, f2p b, f2p* e) {
+  const f2p s = add2(a, b);
+  const f2p v = sub2(s, a);
+  *e = add2(sub2(a, sub2(s, v)), sub2(b, v));
+  return s;
+}
+
 // Accumulator of a sum of products: (sh, sl) with sh the running float sum
 // and sl the collected rounding errors and low-order product terms; the pair
 // is renormalised only when read (dd_acc_get).

@@ -12,13 +12,16 @@
 // L(L+1)/2.  Quadrature over R, ring by ring: for each of n_phi longitudes the
 // boundary colatitude theta_b(phi) by bisection on the focal-distance sum,
 // Gauss-Legendre in theta on [0, theta_b], trapezoid in phi.  With
-// A[pt][a] = sqrt(w_pt) u_a(pt), K = A^T A (one symmetric rank-k update on
-// the tensor-core-free FP64 path of cuBLAS: a plain library product).  The top
-// eigenpair by block subspace iteration (block larger than the Shannon number
-// trace(K), where the eigenvalues cluster near 1) with a Rayleigh-Ritz step
-// on the host; the block products K V run on the device.
-#include <cublas_v2.h>
-
+// A[pt][a] = sqrt(w_pt) u_a(pt), K = A^T A.  The top eigenpair by block
+// subspace iteration (block larger than the Shannon number trace(K), where the
+// eigenvalues cluster near 1): W = K V, V <- an orthonormal basis of W by
+// shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa, Yamamoto and Yanagisawa,
+// "Shifted Cholesky QR for computing the QR factorization of ill-conditioned
+// matrices", SIAM J. Sci. Comput. 2020: a shifted Cholesky QR, then Cholesky
+// QR twice), and every few steps a Rayleigh-Ritz step (T = V^T W and its
+// eigenpairs by cyclic Jacobi rotations).  Everything runs on the device in
+// this file's FP64 kernels; the host only reads the Ritz value and residual
+// norm of each Rayleigh-Ritz step and the final vector.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -88,6 +91,256 @@ __global__ void k_window_basis(const double* __restrict__ ct, const double* __re
   }
 }
 
+// ---------------------------------------------------------------- dense FP64 kernels
+// C_s = op(A) B over the s-th of ksplit slices of the inner dimension (s =
+// blockIdx.z), column-major: C_s[i + j ldc] = sum_k opA(i, k) B[k + j ldb],
+// opA(i, k) = A[k + i lda] (TA) or A[i + k lda].  64 x 64 output tiles, 256
+// threads of 4 x 4 outputs (rows ty + 16 r, columns tx + 16 c), the inner
+// dimension staged 16 at a time in shared memory; FP64 fused multiply-adds
+// in a fixed order.  sym: C is symmetric (op(A) B = B^T A): only the tiles on
+// and below the diagonal run, each output written to both halves.
+#define WG_T 64
+#define WG_KC 16
+template <bool TA>
+__global__ void __launch_bounds__(256) k_wgemm(int m, int n, int kdim, int ksplit, const double* __restrict__ A,
+                                               int lda, const double* __restrict__ B, int ldb, double* __restrict__ C,
+                                               int ldc, size_t cstride, int sym) {
+  if (sym && blockIdx.x < blockIdx.y) return;
+  __shared__ double As[WG_KC][WG_T + 1];
+  __shared__ double Bs[WG_KC][WG_T + 1];
+  const int i0 = blockIdx.x * WG_T, j0 = blockIdx.y * WG_T;
+  const int kper = (kdim + ksplit - 1) / ksplit;
+  const int kb = blockIdx.z * kper, ke = min(kdim, kb + kper);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
+  for (int k0 = kb; k0 < ke; k0 += WG_KC) {
+    for (int e = threadIdx.x; e < WG_KC * WG_T; e += 256) {
+      int kk, ii;
+      if (TA) { kk = e & 15; ii = e >> 4; } else { ii = e & 63; kk = e >> 6; }
+      const int k = k0 + kk, i = i0 + ii;
+      double v = 0.0;
+      if (k < ke && i < m) v = TA ? A[k + (size_t)i * lda] : A[i + (size_t)k * lda];
+      As[kk][ii] = v;
+    }
+    for (int e = threadIdx.x; e < WG_KC * WG_T; e += 256) {
+      const int kk = e & 15, jj = e >> 4;
+      const int k = k0 + kk, j = j0 + jj;
+      Bs[kk][jj] = (k < ke && j < n) ? B[k + (size_t)j * ldb] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < WG_KC; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+    }
+    __syncthreads();
+  }
+  double* Cs = C + (size_t)blockIdx.z * cstride;
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int i = i0 + ty + 16 * r, j = j0 + tx + 16 * c;
+      if (i < m && j < n) {
+        Cs[i + (size_t)j * ldc] = acc[r][c];
+        if (sym && i != j) Cs[j + (size_t)i * ldc] = acc[r][c];
+      }
+    }
+}
+
+// C[i] = sum_s P[i + s stride], s in order (the split-K partials)
+__global__ void k_wsum(const double* __restrict__ P, int ns, size_t stride, size_t n, double* __restrict__ C) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double v = 0.0;
+  for (int s = 0; s < ns; ++s) v += P[i + (size_t)s * stride];
+  C[i] = v;
+}
+
+// Upper Cholesky factor R (R^T R = G + shift I) of the b x b symmetric G
+// (column-major, in place as R's storage), one block.  shift_on: shift =
+// 11 (m b + b (b + 1)) 2^-53 trace(G), the shift of the shifted Cholesky QR
+// (trace(G) = ||X||_F^2 bounds ||X||_2^2).  A non-positive pivot (columns
+// dependent to working precision) is replaced by 2^-52 trace(G) and counted
+// in *bad; the basis is then not quite orthonormal, which the caller's
+// convergence test (the residual of a Ritz pair, valid for any basis) sees.
+__global__ void k_wchol(double* __restrict__ G, int b, int m, int shift_on, int* __restrict__ bad) {
+  extern __shared__ double sg[];          // b x b, column-major
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) sg[e] = G[e];
+  __syncthreads();
+  if (shift_on) {
+    __shared__ double s_shift;
+    if (threadIdx.x == 0) {
+      double tr = 0.0;
+      for (int i = 0; i < b; ++i) tr += sg[i + i * b];
+      s_shift = 11.0 * ((double)m * b + (double)b * (b + 1)) * ldexp(1.0, -53) * tr;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < b; i += blockDim.x) sg[i + i * b] += s_shift;
+    __syncthreads();
+  }
+  __shared__ double s_piv, s_floor;
+  if (threadIdx.x == 0) {
+    double tr = 0.0;
+    for (int i = 0; i < b; ++i) tr += sg[i + i * b];
+    s_floor = ldexp(fmax(tr, 1e-300), -52);
+  }
+  __syncthreads();
+  for (int j = 0; j < b; ++j) {
+    if (threadIdx.x == 0) {
+      const double d = sg[j + j * b];
+      if (!(d > s_floor)) { atomicAdd(bad, 1); s_piv = sqrt(s_floor); } else { s_piv = sqrt(d); }
+      sg[j + j * b] = s_piv;
+    }
+    __syncthreads();
+    for (int k = j + 1 + threadIdx.x; k < b; k += blockDim.x) sg[j + k * b] /= s_piv;   // row j of R
+    __syncthreads();
+    for (int e = threadIdx.x; e < (b - j - 1) * (b - j - 1); e += blockDim.x) {      // trailing update
+      const int i = j + 1 + e % (b - j - 1), k = j + 1 + e / (b - j - 1);
+      if (i <= k) sg[i + k * b] -= sg[j + i * b] * sg[j + k * b];
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int i = e % b, k = e / b;
+    G[e] = i <= k ? sg[e] : 0.0;
+  }
+}
+
+// X <- X R^-1 (R upper b x b), one thread per row of X (m x b, ld m).
+__global__ void k_wtrsm(double* __restrict__ X, int m, int b, const double* __restrict__ R) {
+  extern __shared__ double sr[];
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) sr[e] = R[e];
+  __syncthreads();
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= m) return;
+  for (int j = 0; j < b; ++j) {
+    double v = X[row + (size_t)j * m];
+    for (int i = 0; i < j; ++i) v -= X[row + (size_t)i * m] * sr[i + j * b];
+    X[row + (size_t)j * m] = v / sr[j + j * b];
+  }
+}
+
+// Eigenpairs of the symmetric b x b T (column-major) by cyclic Jacobi
+// rotations, one block: each rotation zeroes one off-diagonal pair and is
+// applied to the columns, the rows and the accumulated Q by all threads;
+// sweeps until the squared off-diagonal mass is below 1e-30 (T is a
+// Rayleigh quotient of K, whose eigenvalues lie in [0, 1]).  Out: ev[i] and
+// Q[:, i]; top[0] = the index of the largest eigenvalue.
+__global__ void k_wjacobi(const double* __restrict__ Tin, int b, double* __restrict__ Qout, double* __restrict__ ev,
+                          int* __restrict__ top) {
+  extern __shared__ double sm[];
+  double* T = sm;               // b x b
+  double* Q = sm + b * b;       // b x b
+  __shared__ double s_c, s_s, s_off;
+  __shared__ int s_go;
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int i = e % b, k = e / b;
+    T[e] = 0.5 * (Tin[e] + Tin[k + i * b]);   // symmetrised
+    Q[e] = i == k ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    if (threadIdx.x == 0) {
+      double off = 0.0;
+      for (int p = 0; p < b; ++p)
+        for (int q = p + 1; q < b; ++q) off += T[p + q * b] * T[p + q * b];
+      s_off = off;
+    }
+    __syncthreads();
+    if (s_off < 1e-30) break;
+    for (int p = 0; p < b; ++p) {
+      for (int q = p + 1; q < b; ++q) {
+        if (threadIdx.x == 0) {
+          const double apq = T[p + q * b];
+          s_go = fabs(apq) >= 1e-300;
+          if (s_go) {
+            const double app = T[p + p * b], aqq = T[q + q * b];
+            const double th = 0.5 * (aqq - app) / apq;
+            const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+            s_c = 1.0 / sqrt(t * t + 1.0);
+            s_s = t * s_c;
+          }
+        }
+        __syncthreads();
+        if (s_go) {
+          const double c = s_c, sn = s_s;
+          for (int k = threadIdx.x; k < b; k += blockDim.x) {     // columns p, q
+            const double tkp = T[k + p * b], tkq = T[k + q * b];
+            T[k + p * b] = c * tkp - sn * tkq;
+            T[k + q * b] = sn * tkp + c * tkq;
+            const double qkp = Q[k + p * b], qkq = Q[k + q * b];
+            Q[k + p * b] = c * qkp - sn * qkq;
+            Q[k + q * b] = sn * qkp + c * qkq;
+          }
+          __syncthreads();
+          for (int k = threadIdx.x; k < b; k += blockDim.x) {     // rows p, q
+            const double tpk = T[p + k * b], tqk = T[q + k * b];
+            T[p + k * b] = c * tpk - sn * tqk;
+            T[q + k * b] = sn * tpk + c * tqk;
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) Qout[e] = Q[e];
+  for (int i = threadIdx.x; i < b; i += blockDim.x) ev[i] = T[i + i * b];
+  if (threadIdx.x == 0) {
+    int im = 0;
+    for (int i = 1; i < b; ++i)
+      if (T[i + i * b] > T[im + im * b]) im = i;
+    *top = im;
+  }
+}
+
+// The top Ritz pair's vector x = V q and residual r = W q - lam x (q = column
+// *top of Q, lam = ev[*top]); per block the partial sums of |x|^2 and |r|^2.
+__global__ void k_writz(const double* __restrict__ V, const double* __restrict__ W, int m, int b,
+                        const double* __restrict__ Q, const double* __restrict__ ev, const int* __restrict__ top,
+                        double* __restrict__ x, double* __restrict__ part) {
+  __shared__ double sx[256], sr[256];
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = *top;
+  const double lam = ev[t];
+  double xv = 0.0, rv = 0.0;
+  if (row < m) {
+    double wq = 0.0;
+    for (int i = 0; i < b; ++i) {
+      const double qi = Q[i + (size_t)t * b];
+      xv = fma(V[row + (size_t)i * m], qi, xv);
+      wq = fma(W[row + (size_t)i * m], qi, wq);
+    }
+    x[row] = xv;
+    rv = wq - lam * xv;
+  }
+  sx[threadIdx.x] = xv * xv;
+  sr[threadIdx.x] = rv * rv;
+  __syncthreads();
+  for (int s2 = 128; s2 > 0; s2 >>= 1) {
+    if (threadIdx.x < s2) {
+      sx[threadIdx.x] += sx[threadIdx.x + s2];
+      sr[threadIdx.x] += sr[threadIdx.x + s2];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = sx[0];
+    part[2 * blockIdx.x + 1] = sr[0];
+  }
+}
+
 // ---------------------------------------------------------------- host helpers
 // Gauss-Legendre nodes and weights on [-1, 1] by Newton's method on P_n.
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
@@ -115,67 +368,43 @@ void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
   }
 }
 
-// Modified Gram-Schmidt on the columns of V (m x b, column-major), twice.
-static void orthonormalise(std::vector<double>& V, int m, int b) {
-  for (int pass = 0; pass < 2; ++pass) {
-    for (int j = 0; j < b; ++j) {
-      double* vj = &V[(size_t)j * m];
-      for (int k = 0; k < j; ++k) {
-        const double* vk = &V[(size_t)k * m];
-        double d = 0.0;
-        for (int i = 0; i < m; ++i) d += vk[i] * vj[i];
-        for (int i = 0; i < m; ++i) vj[i] -= d * vk[i];
-      }
-      double nrm = 0.0;
-      for (int i = 0; i < m; ++i) nrm += vj[i] * vj[i];
-      nrm = std::sqrt(nrm);
-      if (nrm > 0.0)
-        for (int i = 0; i < m; ++i) vj[i] /= nrm;
-    }
-  }
-}
-
-// Cyclic Jacobi eigen-decomposition of the symmetric b x b matrix T
-// (column-major); eigenvalues to ev, eigenvectors (columns) to Q.
-static void jacobi_eig(std::vector<double> T, int b, std::vector<double>& ev, std::vector<double>& Q) {
-  Q.assign((size_t)b * b, 0.0);
-  for (int i = 0; i < b; ++i) Q[(size_t)i * b + i] = 1.0;
-  for (int sweep = 0; sweep < 100; ++sweep) {
-    double off = 0.0;
-    for (int p = 0; p < b; ++p)
-      for (int q = p + 1; q < b; ++q) off += T[(size_t)q * b + p] * T[(size_t)q * b + p];
-    if (off < 1e-30) break;
-    for (int p = 0; p < b; ++p) {
-      for (int q = p + 1; q < b; ++q) {
-        const double apq = T[(size_t)q * b + p];
-        if (std::fabs(apq) < 1e-300) continue;
-        const double app = T[(size_t)p * b + p], aqq = T[(size_t)q * b + q];
-        const double th = 0.5 * (aqq - app) / apq;
-        const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
-        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
-        for (int k = 0; k < b; ++k) {            // T <- J^T T J
-          const double tkp = T[(size_t)p * b + k], tkq = T[(size_t)q * b + k];
-          T[(size_t)p * b + k] = c * tkp - s * tkq;
-          T[(size_t)q * b + k] = s * tkp + c * tkq;
-        }
-        for (int k = 0; k < b; ++k) {
-          const double tpk = T[(size_t)k * b + p], tqk = T[(size_t)k * b + q];
-          T[(size_t)k * b + p] = c * tpk - s * tqk;
-          T[(size_t)k * b + q] = s * tpk + c * tqk;
-        }
-        for (int k = 0; k < b; ++k) {
-          const double qkp = Q[(size_t)p * b + k], qkq = Q[(size_t)q * b + k];
-          Q[(size_t)p * b + k] = c * qkp - s * qkq;
-          Q[(size_t)q * b + k] = s * qkp + c * qkq;
-        }
-      }
-    }
-  }
-  ev.resize(b);
-  for (int i = 0; i < b; ++i) ev[i] = T[(size_t)i * b + i];
-}
-
 // ---------------------------------------------------------------- driver
+// Launch helpers of the dense kernels: C = op(A) B with the inner dimension
+// split so that the GPU holds at least ~4 blocks per SM (partials in P, then
+// summed in a fixed order), or straight into C.
+static cudaError_t wgemm(bool ta, int m, int n, int kdim, const double* A, int lda, const double* B, int ldb,
+                         double* C, int ldc, bool sym, double* P, size_t pcap, int sms, cudaStream_t st) {
+  const int tm = (m + WG_T - 1) / WG_T, tn = (n + WG_T - 1) / WG_T;
+  const long long tiles = sym ? (long long)tm * (tm + 1) / 2 : (long long)tm * tn;
+  int ks = (int)std::max<long long>(1, (4LL * sms + tiles - 1) / tiles);
+  ks = std::min(ks, std::max(1, kdim / WG_KC));
+  const size_t cn = (size_t)ldc * n;
+  if ((size_t)ks * cn > pcap) ks = (int)std::max<size_t>(1, pcap / cn);
+  dim3 grid(tm, tn, ks);
+  double* out = ks > 1 ? P : C;
+  if (ta)
+    k_wgemm<true><<<grid, 256, 0, st>>>(m, n, kdim, ks, A, lda, B, ldb, out, ldc, cn, sym ? 1 : 0);
+  else
+    k_wgemm<false><<<grid, 256, 0, st>>>(m, n, kdim, ks, A, lda, B, ldb, out, ldc, cn, sym ? 1 : 0);
+  if (ks > 1) k_wsum<<<(unsigned)((cn + 255) / 256), 256, 0, st>>>(P, ks, cn, cn, C);
+  return cudaGetLastError();
+}
+
+// Shifted CholeskyQR3: X (m x b) <- an orthonormal basis of its columns.
+static cudaError_t wortho(double* X, int m, int b, double* G, double* P, size_t pcap, int* bad, int sms,
+                          cudaStream_t st) {
+  const size_t smem = sizeof(double) * (size_t)b * b;
+  for (int pass = 0; pass < 3; ++pass) {
+    cudaError_t e = wgemm(true, b, b, m, X, m, X, m, G, b, true, P, pcap, sms, st);
+    if (e != cudaSuccess) return e;
+    k_wchol<<<1, 256, smem, st>>>(G, b, m, pass == 0 ? 1 : 0, bad);
+    k_wtrsm<<<(m + 127) / 128, 128, smem, st>>>(X, m, b, G);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 // Status codes follow slsht.h (0 ok, -1 argument, -3 memory, -5 no
 // convergence, -6 CUDA); the caller supplies device scratch allocation.
 int window_ellipse_run(int L, double theta_c, double a, int n_phi, int n_theta, void* (*alloc)(size_t, void*),
@@ -187,19 +416,23 @@ int window_ellipse_run(int L, double theta_c, double a, int n_phi, int n_theta, 
   if (n_theta <= 0) n_theta = 2 * L + 24;
   const int M = L * (L + 1) / 2;
   const size_t npts = (size_t)n_phi * n_theta;
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   std::vector<double> glx, glw;
   gauss_legendre(n_theta, glx, glw);
+  const int bmax = std::min(M, 96);
   const size_t bytes_nodes = sizeof(double) * (3 * npts + 2 * (size_t)n_theta);
   const size_t bytes_A = sizeof(double) * npts * M;
   const size_t bytes_K = sizeof(double) * (size_t)M * M;
-  int bmax = std::min(M, 96);
-  const size_t bytes_V = sizeof(double) * (size_t)M * bmax * 2;
+  // V, W (M x bmax); G, Q (bmax^2); ev, x, partial norms; split-K partials
+  const size_t pcap = std::max<size_t>((size_t)8 * M * bmax, (size_t)64 * bmax * bmax);
+  const size_t n_small = 2 * (size_t)M * bmax + 2 * (size_t)bmax * bmax + bmax + M + 2 * 4096;
+  const size_t bytes_V = sizeof(double) * (n_small + pcap) + 256;
   double* nodes = (double*)alloc(bytes_nodes, actx);
   double* A = (double*)alloc(bytes_A, actx);
   double* K = (double*)alloc(bytes_K, actx);
   double* Vd = (double*)alloc(bytes_V, actx);
   int status = 0;
-  cublasHandle_t hb = nullptr;
   auto fail = [&](int code, const char* what) {
     if (errbuf && errlen) snprintf(errbuf, errlen, "%s", what);
     status = code;
@@ -220,30 +453,35 @@ int window_ellipse_run(int L, double theta_c, double a, int n_phi, int n_theta, 
     dim3 grid((unsigned)((npts + 255) / 256), L);
     k_window_basis<<<grid, 256, 0, st>>>(ct, ph, sw, (int)npts, L, A);
     if (cudaGetLastError() != cudaSuccess) { fail(-6, "window generator: node / basis kernels"); break; }
-    if (cublasCreate(&hb) != CUBLAS_STATUS_SUCCESS || cublasSetStream(hb, st) != CUBLAS_STATUS_SUCCESS) {
-      fail(-6, "window generator: cuBLAS handle");
-      break;
-    }
-    const double one = 1.0, zero = 0.0;
-    // K = A^T A (lower triangle), A: npts x M column-major
-    if (cublasDsyrk(hb, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T, M, (int)npts, &one, A, (int)npts, &zero, K, M) !=
-        CUBLAS_STATUS_SUCCESS) {
-      fail(-6, "window generator: cublasDsyrk");
+    double* V = Vd;
+    double* W = V + (size_t)M * bmax;
+    double* G = W + (size_t)M * bmax;
+    double* Q = G + (size_t)bmax * bmax;
+    double* ev = Q + (size_t)bmax * bmax;
+    double* x = ev + bmax;
+    double* part = x + M;
+    double* P = part + 2 * 4096;
+    int* flags = (int*)(P + pcap);                 // [0] bad pivot, [1] top index
+    // K = A^T A (A: npts x M, column-major)
+    if (wgemm(true, M, M, (int)npts, A, (int)npts, A, (int)npts, K, M, true, P, pcap, sms, st) != cudaSuccess) {
+      fail(-6, "window generator: Gram matrix");
       break;
     }
     // Shannon number trace(K): the count of eigenvalues near 1
     std::vector<double> Kdiag(M);
-    if (cublasGetVector(M, sizeof(double), K, M + 1, Kdiag.data(), 1) != CUBLAS_STATUS_SUCCESS) {
+    if (cudaMemcpy2DAsync(Kdiag.data(), sizeof(double), K, sizeof(double) * (M + 1), sizeof(double), M,
+                          cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
       fail(-6, "window generator: trace");
       break;
     }
     double shannon = 0.0;
     for (double v : Kdiag) shannon += v;
     const int b = std::min(M, std::max(16, std::min(bmax, (int)std::ceil(2.0 * shannon) + 8)));
-    // block subspace iteration with Rayleigh-Ritz
-    std::vector<double> V((size_t)M * b), W((size_t)M * b), ev, Q, T((size_t)b * b);
+    // seeded start block (splitmix64 -> [-1, 1)), orthonormalised on the device
+    std::vector<double> V0((size_t)M * b);
     uint64_t seed = 0x9E3779B97F4A7C15ull;
-    for (auto& v : V) {                        // splitmix64 -> [-1, 1)
+    for (auto& v : V0) {
       seed += 0x9E3779B97F4A7C15ull;
       uint64_t z = seed;
       z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -251,59 +489,90 @@ int window_ellipse_run(int L, double theta_c, double a, int n_phi, int n_theta, 
       z ^= z >> 31;
       v = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
     }
-    orthonormalise(V, M, b);
-    double* Vdev = Vd;
-    double* Wdev = Vd + (size_t)M * bmax;
-    double prev = -1.0, lam = 0.0;
+    const size_t smem2 = 2 * sizeof(double) * (size_t)b * b;
+    if (cudaFuncSetAttribute(k_wjacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2) != cudaSuccess ||
+        cudaFuncSetAttribute(k_wchol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(smem2 / 2)) != cudaSuccess ||
+        cudaFuncSetAttribute(k_wtrsm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(smem2 / 2)) != cudaSuccess ||
+        cudaMemsetAsync(flags, 0, 2 * sizeof(int), st) != cudaSuccess ||
+        cudaMemcpyAsync(V, V0.data(), sizeof(double) * V0.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        wortho(V, M, b, G, P, pcap, flags, sms, st) != cudaSuccess) {
+      fail(-6, "window generator: start block");
+      break;
+    }
+    const int nblk = (M + 255) / 256;
+    double prev = -1.0, lam = 0.0, last_res = -1.0, last_change = -1.0;
     bool converged = false;
-    std::vector<double> top(M);
-    for (int it = 0; it < 400; ++it) {
-      if (cudaMemcpyAsync(Vdev, V.data(), sizeof(double) * V.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-          cublasDsymm(hb, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, M, b, &one, K, M, Vdev, M, &zero, Wdev, M) !=
-              CUBLAS_STATUS_SUCCESS ||
-          cudaMemcpyAsync(W.data(), Wdev, sizeof(double) * W.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-          cudaStreamSynchronize(st) != cudaSuccess) {
+    std::vector<double> pn(2 * (size_t)nblk);
+    if (b == M) {
+      // the block spans the whole space: K's own eigenpairs (Jacobi on K)
+      int top = 0;
+      k_wjacobi<<<1, 128, smem2, st>>>(K, M, Q, ev, flags + 1);
+      if (cudaGetLastError() != cudaSuccess ||
+          cudaMemcpyAsync(&top, flags + 1, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess ||
+          cudaMemcpyAsync(&lam, ev + top, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaMemcpyAsync(x, Q + (size_t)top * M, sizeof(double) * M, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+        fail(-6, "window generator: eigenpairs of K");
+        break;
+      }
+      converged = true;
+    }
+    for (int it = 0; it < 400 && !status && !converged; ++it) {
+      // W = K V
+      if (wgemm(false, M, b, M, K, M, V, M, W, M, false, P, pcap, sms, st) != cudaSuccess) {
         fail(-6, "window generator: block product");
         break;
       }
-      // Rayleigh-Ritz: T = V^T K V
-      for (int j = 0; j < b; ++j)
-        for (int i = 0; i < b; ++i) {
-          double d = 0.0;
-          const double* vi = &V[(size_t)i * M];
-          const double* wj = &W[(size_t)j * M];
-          for (int k = 0; k < M; ++k) d += vi[k] * wj[k];
-          T[(size_t)j * b + i] = d;
+      if (it % 3 == 2) {
+        // Rayleigh-Ritz: T = V^T W, its eigenpairs, the top Ritz pair's residual
+        int top = 0;
+        if (wgemm(true, b, b, M, V, M, W, M, G, b, false, P, pcap, sms, st) != cudaSuccess) {
+          fail(-6, "window generator: Rayleigh quotient");
+          break;
         }
-      for (int j = 0; j < b; ++j)              // symmetrise
-        for (int i = j + 1; i < b; ++i) {
-          const double s = 0.5 * (T[(size_t)j * b + i] + T[(size_t)i * b + j]);
-          T[(size_t)j * b + i] = T[(size_t)i * b + j] = s;
+        k_wjacobi<<<1, 128, smem2, st>>>(G, b, Q, ev, flags + 1);
+        k_writz<<<nblk, 256, 0, st>>>(V, W, M, b, Q, ev, flags + 1, x, part);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(pn.data(), part, sizeof(double) * pn.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(&top, flags + 1, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess ||
+            cudaMemcpyAsync(&lam, ev + top, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+          fail(-6, "window generator: Rayleigh-Ritz");
+          break;
         }
-      jacobi_eig(T, b, ev, Q);
-      int imax = 0;
-      for (int i = 1; i < b; ++i)
-        if (ev[i] > ev[imax]) imax = i;
-      lam = ev[imax];
-      // residual of the top Ritz pair: r = W q - lam V q
-      double rn = 0.0, vn = 0.0;
-      for (int k = 0; k < M; ++k) {
-        double wv = 0.0, vv = 0.0;
-        for (int i = 0; i < b; ++i) {
-          wv += W[(size_t)i * M + k] * Q[(size_t)imax * b + i];
-          vv += V[(size_t)i * M + k] * Q[(size_t)imax * b + i];
-        }
-        top[k] = vv;
-        rn += (wv - lam * vv) * (wv - lam * vv);
-        vn += vv * vv;
+        double xn = 0.0, rn = 0.0;
+        for (int i = 0; i < nblk; ++i) { xn += pn[2 * i]; rn += pn[2 * i + 1]; }
+        last_res = std::sqrt(rn / xn);
+        last_change = std::fabs(lam - prev);
+        // the Ritz value settled to a few units in the last place of lambda <= 1
+        if (last_res < 1e-13 && last_change < 4e-15) { converged = true; break; }
+        prev = lam;
       }
-      if (std::sqrt(rn / vn) < 1e-13 && std::fabs(lam - prev) < 1e-15) { converged = true; break; }
-      prev = lam;
-      V = W;                                   // next block: orth(K V)
-      orthonormalise(V, M, b);
+      // the next block: an orthonormal basis of K V
+      std::swap(V, W);
+      if (wortho(V, M, b, G, P, pcap, flags, sms, st) != cudaSuccess) {
+        fail(-6, "window generator: orthonormalisation");
+        break;
+      }
     }
     if (status) break;
-    if (!converged) { fail(-5, "window generator: subspace iteration did not converge"); break; }
+    int bad = 0;
+    std::vector<double> top(M);
+    if (cudaMemcpyAsync(&bad, flags, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(top.data(), x, sizeof(double) * M, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      fail(-6, "window generator: result");
+      break;
+    }
+    (void)bad;                       // pivots replaced along the way; the convergence test decides
+    if (!converged) {
+      if (errbuf && errlen)
+        snprintf(errbuf, errlen, "window generator: subspace iteration did not converge (residual %.3g, change %.3g)",
+                 last_res, last_change);
+      status = -5;
+      break;
+    }
     // real even basis -> complex coefficients, unit energy, h_0^0 > 0
     double nrm = 0.0;
     for (double v : top) nrm += v * v;
@@ -321,7 +590,6 @@ int window_ellipse_run(int L, double theta_c, double a, int n_phi, int n_theta, 
     }
     if (lambda_out) *lambda_out = lam;
   } while (0);
-  if (hb) cublasDestroy(hb);
   cudaStreamSynchronize(st);
   if (nodes) release(nodes, bytes_nodes, actx);
   if (A) release(A, bytes_A, actx);

@@ -84,3 +84,31 @@ def test_even_order_window(ctx, prec):
     finally:
         ctx.set_option(pkg.SLSHT_OPT_WINDOW_ORDERS, 0)
     assert _rel(g, O.forward_coeff(f, h, Lf, Lh, pairs, grid)) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("N", [3, None])
+def test_steer_gamma_from_basis_orientations(ctx, prec, N):
+    """g at orientations between the grid's gamma samples (Sec. IV-B, the
+    linearity remark): a steerable window (|q'| < N) evaluated on 2N - 1 basis
+    orientations, and a general window on 2 L_h - 1, interpolated to 13
+    orientations and compared with the oracle's g computed there directly."""
+    import torch
+    import paper_1207_5558_gb300 as pkg
+    Lf, Lh = 14, 10
+    f = synth.signal_powerlaw(Lf, 321)
+    h = steerable_window(Lh, N, 322) if N else synth.window_cn(Lh, 322, decay=1.0)
+    Q = (N - 1) if N else Lh - 1
+    coarse = (2 * Lf - 1, Lf, 2 * Q + 1)
+    fine = (2 * Lf - 1, Lf, 13 if N else 29)
+    pairs = synth.pairs_bands([2, 9, 13, 20])
+    g = ctx.forward(Lf, Lh, coarse, f, h, pairs, prec=prec)
+    gam = 2 * np.pi * np.arange(fine[2]) / fine[2]
+    dt = torch.complex128 if prec == 0 else torch.complex64
+    out = torch.empty((len(pairs), coarse[0], coarse[1], fine[2]), dtype=dt, device="cuda")
+    pkg.slsht_steer_gamma(ctx.h, pkg.make_desc(Lf, Lh, coarse, prec), g, len(pairs), gam, len(gam), Q, out)
+    torch.cuda.synchronize()
+    ref = O.forward_coeff(f, h, Lf, Lh, pairs, fine)
+    assert _rel(out.cpu().numpy(), ref) < TOL[prec]
+    with pytest.raises(pkg.SlshtError):            # too few orientations for the band
+        pkg.slsht_steer_gamma(ctx.h, pkg.make_desc(Lf, Lh, coarse, prec), g, len(pairs), gam, len(gam), Q + 1, out)
