@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--profile-prec", type=int, default=1, help="precision of --profile-pairs (1 FP32_BULK, 0 FP64)")
     ap.add_argument("--profile-fp64-arith", type=int, default=0, choices=(0, 1, 2),
                     help="SLSHT_OPT_FP64_ARITH of an FP64 --profile-pairs case")
+    ap.add_argument("--profile-rotwin-engine", type=int, default=0, choices=(0, 1, 2),
+                    help="SLSHT_OPT_ROTWIN_ENGINE of a --profile-pairs case (2: the tensor cores)")
     ap.add_argument("--profile-workload", type=int, default=3, choices=(3, 5),
                     help="workload of --profile-pairs (5: its band limits on 256 beta rows)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -349,7 +351,7 @@ def serve_bench(pkg, device, n, rate, seed=4000, max_outstanding_bytes=48 << 30,
                         "outstanding outputs capped at 48 GB, later arrivals wait (latency from arrival)"}
 
 
-def profile_case(pkg, n, prec=1, wl=3, fp64_arith=0):
+def profile_case(pkg, n, prec=1, wl=3, fp64_arith=0, rotwin_engine=0):
     """A small case for kernel captures: one chunk of 48 pairs per launch, a
     few GB on the device, two forward passes, then two inverses of the result
     (prec 1: FP32_BULK, 0: FP64).  wl 3: the last n pairs of workload 3; wl 5:
@@ -371,6 +373,7 @@ def profile_case(pkg, n, prec=1, wl=3, fp64_arith=0):
         sub = np.ascontiguousarray(pairs[-n:])
     ctx.set_option(pkg.SLSHT_OPT_CHUNK_PAIRS, 48)
     ctx.set_option(pkg.SLSHT_OPT_FP64_ARITH, fp64_arith)
+    ctx.set_option(pkg.SLSHT_OPT_ROTWIN_ENGINE, rotwin_engine)
     g = torch.empty((n,) + c["grid"], dtype=torch.complex64 if prec == 1 else torch.complex128, device="cuda")
     if prec == 0 and fp64_arith == 0:
         ctx.tune(c["Lf"], c["Lh"], c["grid"], 0)
@@ -527,7 +530,8 @@ def main():
         profile_case_other(pkg, args.profile_case)
         return
     if args.profile_pairs > 0:
-        profile_case(pkg, args.profile_pairs, args.profile_prec, args.profile_workload, args.profile_fp64_arith)
+        profile_case(pkg, args.profile_pairs, args.profile_prec, args.profile_workload, args.profile_fp64_arith,
+                     args.profile_rotwin_engine)
         return
     dist = None
     if world > 1:
@@ -899,21 +903,29 @@ def main():
         ctx.profile(False)
         ms = e0.elapsed_time(e1)
         st = ctx.stats(reset=True)
-        # the rotated window over the window's active orders only
-        # (SLSHT_OPT_WINDOW_ORDERS = 2: the ellipse window's odd orders are rounding noise)
+        # the rotated window on the CUDA cores (SLSHT_OPT_ROTWIN_ENGINE = 1), over
+        # all orders and over the window's active orders only (SLSHT_OPT_WINDOW_ORDERS
+        # = 2: the ellipse window's odd orders are at the rounding level)
         ref_rows = gb[0, :, :8, :].clone()
-        ctx.set_option(pkg.SLSHT_OPT_WINDOW_ORDERS, 2)
-        step()
-        barrier()
-        ctx.profile(True)
-        e0.record(stream)
-        step()
-        e1.record(stream)
-        barrier()
-        ctx.profile(False)
-        ms_orders = e0.elapsed_time(e1)
-        st_orders = ctx.stats(reset=True)
-        rel_orders = float(torch.linalg.vector_norm(gb[0, :, :8, :] - ref_rows) / torch.linalg.vector_norm(ref_rows))
+        cuda_cores = {}
+        for tag, orders in (("all_orders", 0), ("window_orders", 2)):
+            ctx.set_option(pkg.SLSHT_OPT_ROTWIN_ENGINE, 1)
+            ctx.set_option(pkg.SLSHT_OPT_WINDOW_ORDERS, orders)
+            step()
+            barrier()
+            ctx.profile(True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            barrier()
+            ctx.profile(False)
+            stt = ctx.stats(reset=True)
+            cuda_cores[tag] = {"per_call_ms": e0.elapsed_time(e1), "value_per_call": smp / (e0.elapsed_time(e1) / 1e3),
+                               "beta_gamma_ms": stt["ms"]["beta_gamma"],
+                               "rel_l2_vs_default_pair0_8rows": float(
+                                   torch.linalg.vector_norm(gb[0, :, :8, :] - ref_rows)
+                                   / torch.linalg.vector_norm(ref_rows))}
+        ctx.set_option(pkg.SLSHT_OPT_ROTWIN_ENGINE, 0)
         ctx.set_option(pkg.SLSHT_OPT_WINDOW_ORDERS, 0)
         del ref_rows
         ctx.close()
@@ -935,13 +947,14 @@ def main():
                "plan_engine": ["CUDA cores", "double-float", "tensor cores"][eng],
                "alpha_stage_hbm_frac": smp * 8.0 / (st["ms"]["alpha"] / 1e3) / hbm if st["ms"]["alpha"] else None,
                "per_call_hbm_frac": smp / (ms / 1e3) * 8.0 / hbm,
-               "window_orders": {"per_call_ms": ms_orders, "value_per_call": smp / (ms_orders / 1e3),
-                                 "beta_gamma_ms": st_orders["ms"]["beta_gamma"],
-                                 "rel_l2_vs_all_orders_pair0_8rows": rel_orders,
-                                 "note": "SLSHT_OPT_WINDOW_ORDERS = 2: the rotated window sums over the window's "
-                                         "even orders only (its odd orders are at the rounding level)"},
-               "note": "stage times from events around each launch; the alpha fraction is the g bytes over the "
-                       "alpha kernels' summed time against the measured copy bandwidth"}
+               "rotated_window": "tensor cores (the default for L_h > 16): split-FP16 products, the d(beta) "
+                                 "operand's split parts built once per context",
+               "rotated_window_cuda_cores": cuda_cores,
+               "note": "stage times from events around each launch (beta_gamma: the rotated window and the alpha "
+                       "operand producer); the alpha fraction is the g bytes over the alpha kernels' summed time "
+                       "against the measured copy bandwidth; rotated_window_cuda_cores: the same call with "
+                       "SLSHT_OPT_ROTWIN_ENGINE = 1, all orders and the window's even orders only "
+                       "(SLSHT_OPT_WINDOW_ORDERS = 2, its odd orders are at the rounding level)"}
         bp.close()
         ctx.close()
         del gb
@@ -1022,6 +1035,13 @@ def main():
                 if fp64_alpha_ms else None,
                 "alpha_note": "complex128 bytes of g over the alpha kernels' summed time (producer separate) "
                               "against the measured copy bandwidth",
+                "step_g_bytes_frac_of_copy": value64 * 16.0 / hbm,
+                "vs_fp64_pipe_roof": value64 / (1.25e12 / 49.0),
+                "fp64_pipe_roof_note": "the FP64-pipe roofline of the FFT-count FP64 path (about 49 flop a sample "
+                                       "at the nominal 1.25 TFLOP/s: 2.55e10 g-samples/s); this path keeps the alpha "
+                                       "stage off the FP64 pipe (double-float X, exact digit products on the "
+                                       "tensor cores), so it runs above that roof; its own bound is the epilogue's "
+                                       "instruction issue",
                 "clocks": clk64,
                 "rel_l2_vs_fp64_arithmetic_sampled": rel_dd,
                 "double_float": {

@@ -474,8 +474,10 @@ int slsht_get_stats(slsht_ctx* ctx, slsht_stats* out, int reset);
  *                            only gathers k = sum T f; 1: always keep it;
  *                            2: never (3j chains recomputed in every call).
  *  SLSHT_OPT_WAIT_TEST    1: the next forward call that runs a tensor-core
- *                            alpha kernel (fused, two-kernel, wide or FP64
- *                            digit-product engine) withholds one internal
+ *                            kernel (the fused, two-kernel, wide or FP64
+ *                            digit-product alpha engine, or the rotated window
+ *                            of SLSHT_OPT_ROTWIN_ENGINE 2, which takes it
+ *                            first) withholds one internal
  *                            hand-off in its first launch, so the kernel's
  *                            bounded waits expire, it exits cleanly and the
  *                            next slsht_get_stats returns SLSHT_E_TIMEOUT;
@@ -528,6 +530,18 @@ int slsht_get_stats(slsht_ctx* ctx, slsht_stats* out, int reset);
  *                            concentration window of an ellipse centred on
  *                            the pole has its odd orders at that level).
  *                            0 (default): every order.
+ *  SLSHT_OPT_ROTWIN_ENGINE FP32_BULK calls: the rotated window on 1 the
+ *                            CUDA cores, or 2 the tensor cores where they
+ *                            apply (n_gamma <= 128); 0, the default: the
+ *                            tensor cores for L_h > 16 where they apply, else
+ *                            the CUDA cores.  On the tensor cores: split-FP16
+ *                            products with FP32 accumulation, each MMA tile
+ *                            the gamma samples (128 rows) by 128 (beta, q)
+ *                            rows of one degree, Re and Im in two
+ *                            accumulators.  The d(beta) operand's split parts
+ *                            are built once per (L_h, n_beta) and kept by the
+ *                            context: about 4 bytes per element of the d(beta)
+ *                            table (3.8 GB at L_h = 64, n_beta = 2048).
  * Returns SLSHT_OK or SLSHT_E_ARG. */
 #define SLSHT_OPT_BETA_ROUTE   1
 #define SLSHT_OPT_ALPHA_ENGINE 2
@@ -538,6 +552,7 @@ int slsht_get_stats(slsht_ctx* ctx, slsht_stats* out, int reset);
 #define SLSHT_OPT_COUPLING     7
 #define SLSHT_OPT_FP64_ARITH   8
 #define SLSHT_OPT_WINDOW_ORDERS 9
+#define SLSHT_OPT_ROTWIN_ENGINE 10
 int slsht_set_option(slsht_ctx* ctx, int option, int64_t value);
 
 /* Bytes of device memory the context currently holds. */

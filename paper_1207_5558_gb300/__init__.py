@@ -11,7 +11,7 @@ import ctypes
 from . import _abi
 from ._abi import (SLSHT_FP32_BULK, SLSHT_FP64, SLSHT_OPT_ALPHA_ENGINE,  # noqa: F401
                    SLSHT_OPT_BETA_ROUTE, SLSHT_OPT_CHUNK_PAIRS, SLSHT_OPT_GAUNT_TABLE, SLSHT_OPT_WAIT_TEST, SLSHT_OPT_REAL_FIELDS,
-                   SLSHT_OPT_COUPLING, SLSHT_OPT_FP64_ARITH, SLSHT_OPT_WINDOW_ORDERS,
+                   SLSHT_OPT_COUPLING, SLSHT_OPT_FP64_ARITH, SLSHT_OPT_WINDOW_ORDERS, SLSHT_OPT_ROTWIN_ENGINE,
                    SLSHT_BATCH_NO_GRAPH, SLSHT_BATCH_NO_TUNE, SLSHT_BATCH_NO_TC, SLSHT_BATCH_NO_DD,
                    SLSHT_BATCH_FP64_DD,
                    SLSHT_BQ_TILE_COLS, SLSHT_BQ_ALPHA_FORM, SLSHT_BQ_TUNED, SLSHT_BQ_TILES, SLSHT_BQ_KERNELS,

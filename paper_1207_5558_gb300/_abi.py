@@ -31,6 +31,7 @@ SLSHT_OPT_REAL_FIELDS = 6
 SLSHT_OPT_COUPLING = 7
 SLSHT_OPT_FP64_ARITH = 8
 SLSHT_OPT_WINDOW_ORDERS = 9
+SLSHT_OPT_ROTWIN_ENGINE = 10
 
 SLSHT_BATCH_NO_GRAPH = 1
 SLSHT_BATCH_NO_TUNE = 2

@@ -133,6 +133,7 @@ struct Workspace {
   void* Hdd = nullptr; size_t Hdd_cap = 0;
   void* hexp = nullptr; size_t hexp_cap = 0;
   void* qmask = nullptr; size_t qmask_cap = 0;   // the window's active orders (SLSHT_OPT_WINDOW_ORDERS)
+  void* rtw = nullptr; size_t rtw_cap = 0;       // window operand images of the tensor-core rotated window
   std::vector<int32_t> gt_work;              // host copy (source of the upload)
   bool gt_valid = false;
   int gt_Lf = 0, gt_Lh = 0;
@@ -245,6 +246,7 @@ struct slsht_ctx {
   std::mutex sync_mu;                  // serialises users of sync_ws
   std::map<int, TableEntry> delta;                                  // Lh
   std::map<std::tuple<int, int, int>, TableEntry> dtab;             // Lh, Nb, prec
+  std::map<std::tuple<int, int>, TableEntry> rtab;                  // Lh, Nb (split-FP16 d images)
   std::map<std::tuple<int, int, int, int>, TableEntry> phase;       // N, R, r0, prec
   std::map<int, TableEntry> wbeta;                                  // Nb
   std::map<std::tuple<int, int>, TableEntry> etab;                  // Na, Lh (tensor-core E blobs)
@@ -256,6 +258,7 @@ struct slsht_ctx {
   int opt_coupling = 0;
   int opt_fp64_arith = 0;
   int opt_window_orders = 0;
+  int opt_rotwin_engine = 0;
   int64_t opt_chunk = 0;
   bool profile = false;
   std::vector<ProfRec> prof;
@@ -389,6 +392,7 @@ static void ws_release(slsht_ctx* c, Workspace& w) {
   ctx_free(c, w.Hdd, w.Hdd_cap);
   ctx_free(c, w.hexp, w.hexp_cap);
   ctx_free(c, w.qmask, w.qmask_cap);
+  ctx_free(c, w.rtw, w.rtw_cap);
   w.gt_valid = false;
   for (int i = 0; i < 2; ++i) ctx_free(c, w.stage[i], w.stage_cap[i]);
   for (int i = 0; i < 2; ++i) {
@@ -494,6 +498,27 @@ static int get_dtab(slsht_ctx* ctx, int Lh, int Nb, int prec, cudaStream_t st, c
     if (er != cudaSuccess) { record_cuda_error("launch_dtable", er); return SLSHT_E_CUDA; }
     CK(cudaEventRecord(e.ready, st));
     it = ctx->dtab.emplace(key, e).first;
+  }
+  CK(cudaStreamWaitEvent(st, it->second.ready, 0));
+  *out = it->second.ptr;
+  return SLSHT_OK;
+}
+
+// The tensor-core rotated window's split-FP16 d(beta) images (from the FP32
+// d table; once per (Lh, Nb)).
+static int get_rtab(slsht_ctx* ctx, int Lh, int Nb, cudaStream_t st, const void** out) {
+  auto key = std::make_tuple(Lh, Nb);
+  auto it = ctx->rtab.find(key);
+  if (it == ctx->rtab.end()) {
+    const void* dt;
+    CKS(get_dtab(ctx, Lh, Nb, SLSHT_FP32_BULK, st, &dt));
+    TableEntry e;
+    CKS(make_entry(ctx, e, rotwin_tc_table_bytes(Lh, Nb)));
+    ctx->launches[SLSHT_STAGE_TABLES]++;
+    cudaError_t er = launch_rotwin_tc_table((const float*)dt, Lh, Nb, e.ptr, st);
+    if (er != cudaSuccess) { record_cuda_error("launch_rotwin_tc_table", er); return SLSHT_E_CUDA; }
+    CK(cudaEventRecord(e.ready, st));
+    it = ctx->rtab.emplace(key, e).first;
   }
   CK(cudaStreamWaitEvent(st, it->second.ready, 0));
   *out = it->second.ptr;
@@ -638,6 +663,7 @@ extern "C" void slsht_destroy(slsht_ctx* c) {
   ws_release(c, c->sync_ws);
   for (auto& kv : c->delta) free_entry(c, kv.second);
   for (auto& kv : c->dtab) free_entry(c, kv.second);
+  for (auto& kv : c->rtab) free_entry(c, kv.second);
   for (auto& kv : c->phase) free_entry(c, kv.second);
   for (auto& kv : c->wbeta) free_entry(c, kv.second);
   for (auto& kv : c->etab) free_entry(c, kv.second);
@@ -681,6 +707,10 @@ extern "C" int slsht_set_option(slsht_ctx* c, int option, int64_t v) {
     case SLSHT_OPT_FP64_ARITH:
       if (v < 0 || v > 3) return SLSHT_E_ARG;
       c->opt_fp64_arith = (int)v;
+      return SLSHT_OK;
+    case SLSHT_OPT_ROTWIN_ENGINE:
+      if (v < 0 || v > 2) return SLSHT_E_ARG;
+      c->opt_rotwin_engine = (int)v;
       return SLSHT_OK;
     case SLSHT_OPT_WINDOW_ORDERS:
       if (v < 0 || v > 2) return SLSHT_E_ARG;
@@ -769,7 +799,7 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
   const bool host_out = !is_device_ptr(g_out);
   CK(cudaStreamWaitEvent(st, w.done, 0));
 
-  int route, tc, engine, gt_opt, wait_test, coupling, fp64_arith, win_orders;
+  int route, tc, engine, gt_opt, wait_test, coupling, fp64_arith, win_orders, rot_engine;
   int64_t chunk_opt;
   int dd_nt = 0, dd_form = -1, tuned_engine = -1;
   int cc_nt = 0, cc_form = -1;
@@ -784,6 +814,7 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
     coupling = ctx->opt_coupling;
     fp64_arith = ctx->opt_fp64_arith;
     win_orders = ctx->opt_window_orders;
+    rot_engine = ctx->opt_rotwin_engine;
     // a tile shape the batch-plan tuner measured for this shape, if any
     // (FP64: both arithmetics allowed; FP32: the tensor cores where they apply)
     const int allowed = f64 ? 6 : ((tc_supported(Lh, Na) && Lh <= 16) ? 5 : 4);
@@ -976,6 +1007,24 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
       LAUNCH(SLSHT_STAGE_BETA, ax,
              launch_rotwin_f64((const double2*)h_dev, (const double*)dt, (const double2*)eg, Lh, Nb, Ng,
                                (double2*)w.H, ax, qmask));
+    else if ((rot_engine == 2 || (rot_engine == 0 && Lh > 16)) && rotwin_tc_supported(Lh, Ng)) {
+      const void* rtab;
+      {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        CKS(get_rtab(ctx, Lh, Nb, ax, &rtab));
+      }
+      if (wait_test) {   // SLSHT_OPT_WAIT_TEST: this launch withholds its first d chunk
+        tc_arm_wait_test();
+        wait_test = 0;
+        std::lock_guard<std::mutex> g(ctx->mu);
+        ctx->opt_wait_test = 0;
+      }
+      CKS(ws_reserve(ctx, w, &w.rtw, &w.rtw_cap, rotwin_tc_window_bytes(Lh)));
+      LAUNCH(SLSHT_STAGE_BETA, ax,
+             launch_rotwin_tc_window((const double2*)h_dev, (const float2*)eg, qmask, Lh, Ng, w.rtw, ax));
+      LAUNCH(SLSHT_STAGE_BETA, ax,
+             launch_rotwin_tc(rtab, w.rtw, Lh, Nb, Ng, (float2*)w.H, ctx->num_sms, ax));
+    }
     else
       LAUNCH(SLSHT_STAGE_BETA, ax,
              launch_rotwin_f32((const double2*)h_dev, (const float*)dt, (const float2*)eg, Lh, Nb, Ng,
@@ -1521,6 +1570,8 @@ struct slsht_batch {
   std::vector<BItem> bitem;             // alpha view of every item (index = item)
   std::vector<BTile> tiles[3];          // CUDA-core tiles per kernel (0 FP64, 1 FP32, 2 double-float)
   std::vector<int> tc_items;
+  struct RotTc { int rot; const void* tab; void* wbuf; };
+  std::vector<RotTc> rot_tc;            // rotated windows on the tensor cores (FP32, wide windows)
   void *d_cpl = nullptr, *d_cblk = nullptr, *d_rot = nullptr, *d_rblk = nullptr, *d_bitem = nullptr;
   void* d_kblk = nullptr;
   void* d_tiles[3] = {nullptr, nullptr, nullptr};
@@ -1824,6 +1875,12 @@ static int batch_enqueue(slsht_batch* b, cudaStream_t st) {
   if (e != cudaSuccess) { record_cuda_error("launch_batch_kdd", e); return SLSHT_E_CUDA; }
   e = launch_batch_rotwin((const BRot*)b->d_rot, (const BRotBlk*)b->d_rblk, (int)b->rblk.size(), b->rot_smem, st);
   if (e != cudaSuccess) { record_cuda_error("launch_batch_rotwin", e); return SLSHT_E_CUDA; }
+  for (const auto& rt : b->rot_tc) {
+    const BRot& r = b->rot[rt.rot];
+    e = launch_rotwin_tc_window(r.h, (const float2*)r.eg, r.qmask, r.Lh, r.Ng, rt.wbuf, st);
+    if (e == cudaSuccess) e = launch_rotwin_tc(rt.tab, rt.wbuf, r.Lh, r.Nb, r.Ng, (float2*)r.H, ctx->num_sms, st);
+    if (e != cudaSuccess) { record_cuda_error("launch_rotwin_tc", e); return SLSHT_E_CUDA; }
+  }
   for (int pi = 0; pi < 3; ++pi) {
     e = launch_batch_alpha(pi, (const BItem*)b->d_bitem, (const BTile*)b->d_tiles[pi], (int)b->tiles[pi].size(),
                            b->d_counter + pi, b->alpha_grid[pi], b->alpha_smem[pi], st);
@@ -2023,6 +2080,36 @@ static int batch_build(slsht_batch* b, const slsht_batch_item* src, int32_t n, c
       if (!rot_native[r]) b->rot[r].H = nullptr;
       if (!rot_dd[r]) b->rot[r].Hdd = nullptr;
     }
+    // wide FP32 windows on the tensor cores (SLSHT_OPT_ROTWIN_ENGINE 0 or 2):
+    // their blocks leave the CUDA-core rotated-window launch
+    int rot_engine;
+    {
+      std::lock_guard<std::mutex> g(ctx->mu);
+      rot_engine = ctx->opt_rotwin_engine;
+    }
+    std::vector<char> on_tc(b->rot.size(), 0);
+    for (size_t r = 0; r < b->rot.size(); ++r) {
+      const BRot& br = b->rot[r];
+      if (br.prec != 1 || br.H == nullptr || !rotwin_tc_supported(br.Lh, br.Ng)) continue;
+      if (!(rot_engine == 2 || (rot_engine == 0 && br.Lh > 16))) continue;
+      slsht_batch::RotTc rt{(int)r, nullptr, nullptr};
+      {
+        std::lock_guard<std::mutex> g(ctx->mu);
+        CKS(get_rtab(ctx, br.Lh, br.Nb, b->cs, &rt.tab));
+      }
+      CKS(batch_alloc(b, rotwin_tc_window_bytes(br.Lh), &rt.wbuf));
+      b->rot_tc.push_back(rt);
+      on_tc[r] = 1;
+    }
+    if (!b->rot_tc.empty()) {
+      std::vector<BRotBlk> keep;
+      for (const BRotBlk& rb : b->rblk)
+        if (!on_tc[rb.rot]) keep.push_back(rb);
+      b->rblk.swap(keep);
+      if (!b->rblk.empty())
+        CK(cudaMemcpyAsync(b->d_rblk, b->rblk.data(), sizeof(BRotBlk) * b->rblk.size(), cudaMemcpyHostToDevice,
+                           b->cs));
+    }
     b->kblk.clear();
     for (int ci = 0; ci < (int)b->cpl.size(); ++ci)
       if (cpl_dd[ci])
@@ -2076,7 +2163,7 @@ static int batch_build(slsht_batch* b, const slsht_batch_item* src, int32_t n, c
   CKS(batch_alloc(b, 16, &ctr));
   b->d_counter = (int*)ctr;
   b->k_couple = (b->cblk.empty() ? 0 : 1) + (b->kblk.empty() ? 0 : 1);
-  b->k_rot = b->rblk.empty() ? 0 : 1;
+  b->k_rot = (b->rblk.empty() ? 0 : 1) + 2 * (int)b->rot_tc.size();
   b->kernels = b->k_couple + b->k_rot + b->k_alpha;
   // one direct run: every g_out holds its result, and every launch path
   // (attributes, the tensor-core error word) is set up before the capture

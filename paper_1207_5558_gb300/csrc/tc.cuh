@@ -66,6 +66,22 @@ cudaError_t launch_alpha_tc64(const void* xblob, const void* etab, int Lh, int N
 // and reports through the error word; that launch's output is not computed.
 void tc_arm_wait_test();
 int tc_take_wait_test();
+// The rotated window of an FP32_BULK call on the tensor cores (rotwin_tc.cu):
+// H (the tiled layout of h_index) from the split-FP16 d(beta) image `tab`
+// (launch_rotwin_tc_table, built once per (Lh, Nb) from the FP32 d(beta)
+// table dt, rotwin_tc_table_bytes bytes) and the window operand images of the
+// call `wbuf` (launch_rotwin_tc_window from h, the FP32 gamma phases eg and
+// qmask as for launch_rotwin_f32, rotwin_tc_window_bytes bytes).
+// N_gamma <= 128.  Like the alpha kernels it takes tc_arm_wait_test() (the
+// first d chunk is then never fetched).
+bool rotwin_tc_supported(int Lh, int Ng);
+size_t rotwin_tc_table_bytes(int Lh, int Nb);
+cudaError_t launch_rotwin_tc_table(const float* dt, int Lh, int Nb, void* tab, cudaStream_t st);
+size_t rotwin_tc_window_bytes(int Lh);
+cudaError_t launch_rotwin_tc_window(const double2* h, const float2* eg, const uint32_t* qmask, int Lh, int Ng,
+                                   void* wbuf, cudaStream_t st);
+cudaError_t launch_rotwin_tc(const void* tab, const void* wbuf, int Lh, int Nb, int Ng, float2* H, int num_sms,
+                             cudaStream_t st);
 // Device error word shared by the tensor-core kernels (allocated on first use).
 int* tc_error_word();
 // Non-zero (and cleared) if a tensor-core kernel gave up on a bounded wait

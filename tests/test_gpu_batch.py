@@ -200,6 +200,34 @@ def test_batch_matches_per_call_forward(pkg, ctx):
         b.close()
 
 
+def test_wide_fp32_window_on_tensor_cores(pkg, ctx):
+    """A plan rotates wide FP32 windows (L_h > 16) on the tensor cores by
+    default (window-operand kernel + tensor-core kernel in place of the
+    CUDA-core launch): it matches the oracle, the per-call forward, and a plan
+    made with the CUDA-core window (SLSHT_OPT_ROTWIN_ENGINE 1)."""
+    Lf, Lh, grid = 10, 24, (61, 12, 47)
+    f, h = synth.signal_powerlaw(Lf, 51), synth.window_cn(Lh, 52, decay=1.0)
+    pairs = synth.pairs_random(Lf + Lh - 1, 10, 53)
+    ref = O.forward_coeff(f, h, Lf, Lh, pairs, grid)
+    out = {}
+    for eng in (0, 1):
+        ctx.set_option(pkg.SLSHT_OPT_ROTWIN_ENGINE, eng)
+        try:
+            b = ctx.batch([_item(Lf, Lh, grid, _dev(f), _dev(h), pairs, 1)])
+            try:
+                out[eng] = (b.outputs[0].cpu().numpy(), b.query(pkg.SLSHT_BQ_KERNELS))
+            finally:
+                b.close()
+        finally:
+            ctx.set_option(pkg.SLSHT_OPT_ROTWIN_ENGINE, 0)
+    (tc, k_tc), (cc, k_cc) = out[0], out[1]
+    assert rel(tc, ref) < TOL[1] and rel(cc, ref) < TOL[1]
+    assert rel(tc, cc) < 5e-6
+    assert k_tc == k_cc + 1
+    call = ctx.forward(Lf, Lh, grid, f, h, pairs, prec=1).cpu().numpy()
+    assert rel(tc, call) < 5e-6
+
+
 def test_batch_argument_errors(pkg, ctx):
     import torch
     Lf, Lh, grid = 4, 2, (3, 2, 3)

@@ -278,19 +278,20 @@ def test_gaunt_table_mirror_pairs_with_duplicates(ctx):
     assert rel(g, O.forward_coeff(f, h, Lf, Lh, pairs, grid)) < TOL64
 
 
-@pytest.mark.parametrize("name,prec,Lh,engine", [
-    ("fused", 1, 5, 0),              # k_alpha_fused: producer warps in the alpha kernel
-    ("two_kernel", 1, 5, 2),         # k_alpha_tc fed by k_xa_from_h
-    ("wide", 1, 20, 0),              # k_alpha_tcw (16 < L_h <= 64)
-    ("fp64_digits", 0, 5, 0),        # k_alpha_tc64 (FP64 from exact digit products)
+@pytest.mark.parametrize("name,prec,Lh,engine,rot", [
+    ("fused", 1, 5, 0, 0),           # k_alpha_fused: producer warps in the alpha kernel
+    ("two_kernel", 1, 5, 2, 0),      # k_alpha_tc fed by k_xa_from_h
+    ("wide", 1, 20, 0, 0),           # k_alpha_tcw (16 < L_h <= 64)
+    ("fp64_digits", 0, 5, 0, 0),     # k_alpha_tc64 (FP64 from exact digit products)
+    ("rotated_window", 1, 20, 0, 2), # k_rotwin_tc (the rotated window on the tensor cores)
 ])
-def test_bounded_wait_expiry_reports_and_context_recovers(ctx, name, prec, Lh, engine):
-    """The timeout path of every tensor-core alpha kernel: with one internal
+def test_bounded_wait_expiry_reports_and_context_recovers(ctx, name, prec, Lh, engine, rot):
+    """The timeout path of every tensor-core kernel: with one internal
     hand-off withheld (SLSHT_OPT_WAIT_TEST: the fused kernel's first A tile is
-    never handed to the issuer; the other kernels' first A operand is never
-    fetched) the bounded waits expire, the kernel leaves cleanly,
-    slsht_get_stats reports SLSHT_E_TIMEOUT, and the next call on the same
-    context is correct."""
+    never handed to the issuer; the other alpha kernels' first A operand and
+    the rotated window's first d chunk are never fetched) the bounded waits
+    expire, the kernel leaves cleanly, slsht_get_stats reports
+    SLSHT_E_TIMEOUT, and the next call on the same context is correct."""
     import torch
     import paper_1207_5558_gb300 as pkg
     from paper_1207_5558_gb300 import _abi
@@ -299,6 +300,7 @@ def test_bounded_wait_expiry_reports_and_context_recovers(ctx, name, prec, Lh, e
     h = synth.window_cn(Lh, 82)
     pairs = synth.pairs_bands([2, 9])
     ctx.set_option(pkg.SLSHT_OPT_ALPHA_ENGINE, engine)
+    ctx.set_option(pkg.SLSHT_OPT_ROTWIN_ENGINE, rot)
     try:
         ctx.stats(reset=True)
         ctx.set_option(pkg.SLSHT_OPT_WAIT_TEST, 1)
@@ -313,6 +315,7 @@ def test_bounded_wait_expiry_reports_and_context_recovers(ctx, name, prec, Lh, e
     finally:
         ctx.set_option(pkg.SLSHT_OPT_WAIT_TEST, 0)
         ctx.set_option(pkg.SLSHT_OPT_ALPHA_ENGINE, 0)
+        ctx.set_option(pkg.SLSHT_OPT_ROTWIN_ENGINE, 0)
 
 
 @pytest.mark.parametrize("prec,engine,arith", [(0, 0, 0), (0, 0, 1), (0, 0, 3), (1, 0, 0), (1, 1, 0), (1, 2, 0)])

@@ -44,8 +44,12 @@ def steerable_window(Lh, N, seed):
     return h / np.linalg.norm(h)
 
 
-@pytest.mark.parametrize("prec,Lh,arith", [(0, 12, 0), (0, 12, 1), (0, 20, 0), (1, 12, 0), (1, 24, 0)])
-def test_steerable_window_skips_zero_orders(ctx, prec, Lh, arith):
+@pytest.mark.parametrize("prec,Lh,arith,rot", [(0, 12, 0, 0), (0, 12, 1, 0), (0, 20, 0, 0), (1, 12, 0, 0),
+                                               (1, 24, 0, 1), (1, 24, 0, 2)])
+def test_steerable_window_skips_zero_orders(ctx, prec, Lh, arith, rot):
+    """SLSHT_OPT_WINDOW_ORDERS 1 leaves the window's vanishing orders out of
+    the rotated window (CUDA cores: skipped; tensor cores, rot 2: zero columns
+    of K) with the same bits as the full sum, and matches the oracle."""
     import torch
     import paper_1207_5558_gb300 as pkg
     Lf, N = 18, 3
@@ -54,6 +58,7 @@ def test_steerable_window_skips_zero_orders(ctx, prec, Lh, arith):
     h = steerable_window(Lh, N, 302)
     pairs = synth.pairs_bands([0, 7, 17, Lf + Lh - 2])
     ctx.set_option(pkg.SLSHT_OPT_FP64_ARITH, arith)
+    ctx.set_option(pkg.SLSHT_OPT_ROTWIN_ENGINE, rot)
     try:
         full = ctx.forward(Lf, Lh, grid, f, h, pairs, prec=prec).cpu().numpy()
         ctx.set_option(pkg.SLSHT_OPT_WINDOW_ORDERS, 1)
@@ -62,6 +67,7 @@ def test_steerable_window_skips_zero_orders(ctx, prec, Lh, arith):
     finally:
         ctx.set_option(pkg.SLSHT_OPT_WINDOW_ORDERS, 0)
         ctx.set_option(pkg.SLSHT_OPT_FP64_ARITH, 0)
+        ctx.set_option(pkg.SLSHT_OPT_ROTWIN_ENGINE, 0)
     assert np.array_equal(steer, full)
     ref = O.forward_coeff(f, h, Lf, Lh, pairs, grid)
     assert _rel(steer, ref) < TOL[prec]
@@ -112,3 +118,40 @@ def test_steer_gamma_from_basis_orientations(ctx, prec, N):
     assert _rel(out.cpu().numpy(), ref) < TOL[prec]
     with pytest.raises(pkg.SlshtError):            # too few orientations for the band
         pkg.slsht_steer_gamma(ctx.h, pkg.make_desc(Lf, Lh, coarse, prec), g, len(pairs), gam, len(gam), Q + 1, out)
+
+
+@pytest.mark.parametrize("Lh,grid,orders", [
+    (16, (35, 18, 31), 0),
+    (24, (47, 24, 47), 0),
+    (40, (81, 20, 127), 0),          # two K chunks, 127 gamma samples on the 128 TMEM lanes
+    (24, (47, 24, 47), 1),           # a steerable window: the inactive orders are zero columns of K
+    (5, (130, 10, 9), 0),            # ragged row tiles, short K
+    (64, (129, 33, 128), 0),         # L_h = 64: K = 127 in two chunks, all 128 lanes, 33 beta rows
+    (64, (129, 7, 65), 2),           # few beta rows: tiles that span several betas; rounding-level orders
+])
+def test_rotated_window_on_tensor_cores(ctx, Lh, grid, orders):
+    """The rotated window on the tensor cores (SLSHT_OPT_ROTWIN_ENGINE = 2,
+    split-FP16 products) against the oracle and the CUDA-core window (1),
+    FP32_BULK; the default (0) takes the tensor cores for L_h > 16."""
+    import paper_1207_5558_gb300 as pkg
+    Lf = 12
+    f = synth.signal_powerlaw(Lf, 330 + Lh)
+    h = steerable_window(Lh, 4, 331) if orders else synth.window_cn(Lh, 331, decay=1.0)
+    pairs = synth.pairs_bands([0, 5, 11, Lf + Lh - 2])
+    if Lh > 40:
+        pairs = pairs[::9]                         # keeps the oracle to seconds at L_h = 64
+    ctx.set_option(pkg.SLSHT_OPT_WINDOW_ORDERS, orders)
+    try:
+        ctx.set_option(pkg.SLSHT_OPT_ROTWIN_ENGINE, 1)
+        cc = ctx.forward(Lf, Lh, grid, f, h, pairs, prec=1).cpu().numpy()
+        ctx.set_option(pkg.SLSHT_OPT_ROTWIN_ENGINE, 2)
+        tc = ctx.forward(Lf, Lh, grid, f, h, pairs, prec=1).cpu().numpy()
+        ctx.set_option(pkg.SLSHT_OPT_ROTWIN_ENGINE, 0)
+        default = ctx.forward(Lf, Lh, grid, f, h, pairs, prec=1).cpu().numpy()
+    finally:
+        ctx.set_option(pkg.SLSHT_OPT_ROTWIN_ENGINE, 0)
+        ctx.set_option(pkg.SLSHT_OPT_WINDOW_ORDERS, 0)
+    ref = O.forward_coeff(f, h, Lf, Lh, pairs, grid)
+    assert _rel(tc, ref) < TOL[1]
+    assert _rel(tc, cc) < 5e-6
+    assert np.array_equal(default, tc if Lh > 16 else cc)   # the default: the tensor cores for L_h > 16
