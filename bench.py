@@ -46,7 +46,9 @@ def parse():
     ap.add_argument("--profile-rotwin-engine", type=int, default=0, choices=(0, 1, 2),
                     help="SLSHT_OPT_ROTWIN_ENGINE of a --profile-pairs case (2: the tensor cores)")
     ap.add_argument("--profile-workload", type=int, default=3, choices=(3, 5),
-                    help="workload of --profile-pairs (5: its band limits on 256 beta rows)")
+                    help="workload of --profile-pairs (5: its band limits on --profile-beta-rows beta rows)")
+    ap.add_argument("--profile-beta-rows", type=int, default=256,
+                    help="beta rows of a workload-5 --profile-pairs case (2048: the full grid)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=2000,
@@ -351,21 +353,21 @@ def serve_bench(pkg, device, n, rate, seed=4000, max_outstanding_bytes=48 << 30,
                         "outstanding outputs capped at 48 GB, later arrivals wait (latency from arrival)"}
 
 
-def profile_case(pkg, n, prec=1, wl=3, fp64_arith=0, rotwin_engine=0):
+def profile_case(pkg, n, prec=1, wl=3, fp64_arith=0, rotwin_engine=0, beta_rows=256):
     """A small case for kernel captures: one chunk of 48 pairs per launch, a
     few GB on the device, two forward passes, then two inverses of the result
     (prec 1: FP32_BULK, 0: FP64).  wl 3: the last n pairs of workload 3; wl 5:
     the first n pairs of workload 5 (its band limits, window and N_alpha,
-    N_gamma) on 256 of its beta rows.  fp64_arith: SLSHT_OPT_FP64_ARITH."""
+    N_gamma) on beta_rows of its beta rows.  fp64_arith: SLSHT_OPT_FP64_ARITH."""
     import numpy as np
     import torch
     import synth
-    ctx = pkg.Context(0, 16 << 30)
+    ctx = pkg.Context(0, (16 << 30) if beta_rows <= 256 else (48 << 30))
     if wl == 5:
         c5 = synth.CONFIGS[5]
         h, _ = ctx.window_ellipse(c5["Lh"], *synth.ellipse_from_axes(8.0, 3.0))
         f, _, pairs = synth.config_inputs(5, window_cache=h)
-        c = dict(c5, grid=(c5["grid"][0], 256, c5["grid"][2]))
+        c = dict(c5, grid=(c5["grid"][0], beta_rows, c5["grid"][2]))
         sub = np.ascontiguousarray(pairs[:n])
     else:
         c = synth.CONFIGS[3]
@@ -531,7 +533,7 @@ def main():
         return
     if args.profile_pairs > 0:
         profile_case(pkg, args.profile_pairs, args.profile_prec, args.profile_workload, args.profile_fp64_arith,
-                     args.profile_rotwin_engine)
+                     args.profile_rotwin_engine, args.profile_beta_rows)
         return
     dist = None
     if world > 1:

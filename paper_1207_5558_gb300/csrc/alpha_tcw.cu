@@ -18,10 +18,11 @@
 // per-column power-of-two scale that puts its largest entry in [2^14, 2^15))
 // and D = A_hi B_hi + A_hi B_lo + A_lo B_hi accumulates in FP32.
 //
-// Two kernels: k_xaw_from_h (CUDA cores) forms X for one 128-column tile of
-// a group of pairs from the rotated window H, folds it into P and M, scales,
-// splits and writes the swizzled A operand (A_re and A_im, NKF K-chunks of
-// 32 KB each) and the column scales to a blob in global memory; k_alpha_tcw
+// The producer (CUDA cores, two passes: k_xw_x forms X in FP32 for a group
+// of up to 16 pairs from the rotated window H, with each column's slot bound;
+// k_xaw_split folds X into P and M, scales, splits and writes the swizzled A
+// operand -- A_re and A_im, NKF K-chunks of 32 KB each -- and the column
+// scales to a blob in global memory); k_alpha_tcw
 // (persistent, one CTA per SM, work item = (pair, tile)) keeps the item's
 // whole A operand in shared memory, streams the E-table K-chunks (32 KB each)
 // through a ring of 3 or 4 stages with cp.async.bulk, issues the MMAs from
@@ -36,10 +37,6 @@
 #include "tc.cuh"
 #include "tc_ptx.cuh"
 
-#define XW_COLS 16                      // columns per producer block
-#define XW_PARTS (TC_M / XW_COLS)
-#define XW_PP 4                         // pairs per producer block
-#define XW_THREADS 256
 #define TCW_NA 128                      // alpha rows per chunk (MMA N)
 
 // A-operand K-chunks per tile: 2 NKF (A_re then A_im, NKF chunks of 64 each)
@@ -52,30 +49,32 @@ bool tcw_supported(int Lh, int Na) { return Lh > 16 && Lh <= 64 && Na >= 1; }
 size_t tcw_etab_bytes(int Na, int Lh) { return (size_t)tcw_chunks(Na) * (tcw_nk(Lh) / 2) * TC_B_BYTES; }
 
 // per pair: tiles x 2 NKF x 32 KB of A, one float scale per padded column,
-// then room for the coupling rows of a producer group as floats, interleaved
-// [pq][XW_PP] (the producer's operand; used in the group's first pair)
+// room for the coupling rows of a producer group of up to XA_MAXP pairs as
+// floats, interleaved [pq][XA_MAXP] (used in the group's first pair), and the
+// pair's X_q(j) in FP32, [tile][q + L_h - 1][128 columns] (the producer's
+// first pass writes it, its second pass scales and splits it into A)
+#define XA_MAXP 16
 static inline size_t tcw_scales_bytes(size_t tiles) { return ((tiles * TC_M * sizeof(float)) + 1023) / 1024 * 1024; }
+static inline size_t tcw_kf_bytes(int Lh) { return ((size_t)Lh * Lh * XA_MAXP * sizeof(float2) + 1023) / 1024 * 1024; }
+static inline size_t tcw_xf_bytes(size_t tiles, int Lh) { return tiles * (size_t)(2 * Lh - 1) * TC_M * sizeof(float2); }
 size_t tcw_xblob_bytes(int Nb, int Ng, int Lh) {
   const size_t t = (size_t)tcw_tiles(Nb, Ng);
-  const size_t kf = ((size_t)Lh * Lh * XW_PP * sizeof(float2) + 1023) / 1024 * 1024;
-  return t * (size_t)tcw_nk(Lh) * TC_A_BYTES + tcw_scales_bytes(t) + kf;
+  return t * (size_t)tcw_nk(Lh) * TC_A_BYTES + tcw_scales_bytes(t) + tcw_kf_bytes(Lh) + tcw_xf_bytes(t, Lh);
 }
 
-// The coupling rows of the launch's pairs as floats: one conversion per
-// coefficient (float/double conversions share the slow FP64 pipe on this
-// GPU; the producer then reads floats), pair i at [pq][i % XW_PP] of its
-// group's first blob; the slots of a short last group are zero.
-__global__ void k_kf_from_kc(const double2* __restrict__ kc, int n2, int npairs, unsigned char* __restrict__ xblob,
-                             size_t blob_stride, size_t kf_off) {
-  const int pair = blockIdx.y, g0 = pair - pair % XW_PP;
-  float2* kf = reinterpret_cast<float2*>(xblob + (size_t)g0 * blob_stride + kf_off);
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n2; t += gridDim.x * blockDim.x) {
+// The coupling rows of a group of up to XA_MAXP pairs as floats: one
+// conversion per coefficient (float/double conversions share the slow FP64
+// pipe on this GPU; the producer then reads floats), pair v of the group at
+// [pq][v]; the slots past the group's last pair are zero.
+__global__ void k_kf_from_kc(const double2* __restrict__ kc, int n2, int ng, float2* __restrict__ kf) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n2 * XA_MAXP; t += gridDim.x * blockDim.x) {
+    const int pq = t / XA_MAXP, v = t % XA_MAXP;
     float2 o = make_float2(0.f, 0.f);
-    if (pair < npairs) {
-      const double2 v = kc[(size_t)pair * n2 + t];
-      o = make_float2((float)v.x, (float)v.y);
+    if (v < ng) {
+      const double2 x = kc[(size_t)v * n2 + pq];
+      o = make_float2((float)x.x, (float)x.y);
     }
-    kf[(size_t)t * XW_PP + pair % XW_PP] = o;
+    kf[t] = o;
   }
 }
 
@@ -114,169 +113,187 @@ cudaError_t launch_tcw_etab(void* etab, int Na, int Lh, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------- A operand from H
-// X_q(j) = sum_{p>=|q|} k(p,q) H^p_q(j) for up to XW_PP pairs and one eighth
-// of a 128-column tile: a block serves XW_COLS columns of XW_PP pairs, so every
-// H value it loads feeds the multiply-adds of all its pairs (H is read from L2
-// once per group of XW_PP pairs); the groups of one tile are adjacent blocks,
-// so each H tile is read from HBM about once.
-//   phase 1: one item per (q, two adjacent columns), its degrees p >= |q| (H
-//            loads coalesced across columns, k broadcast through the cache)
-//            into the shared tiles sX[pair][q + Lh - 1][column] (complex);
-//   phase 2: per (pair, column), the largest |entry| of A_re and A_im (from
-//            P_r and M_r) -> scale 2^e into [2^14, 2^15);
-//   phase 3: per (pair, column, operand, 8 slots): P_r / M_r, scale, split
-//            into FP16 hi/lo, store swizzled into its K-chunk.  Columns
-//            beyond J are zero.
+// Two passes.  k_xw_x: X_q(j) = sum_{p>=|q|} k(p,q) H^p_q(j) for a group of
+// up to XA_MAXP pairs, one block per (128-column tile, order q), one thread
+// per column: the thread keeps its column's sums for every pair of the group
+// in registers, so each H value (one coalesced row of the tiled layout per
+// degree, read from HBM once per group) feeds 4 NP multiply-adds, with the
+// group's k(., q) in shared memory (broadcast reads) and the next four
+// degrees' H loads issued before the current four are used.  X goes to the
+// pair's FP32 region, and 2 max(|Re X|, |Im X|), a bound of every slot built
+// from the column's X (|Re P_r| <= |Re X_r| + |Re X_-r|, ...) and at most
+// twice the largest one (X_r = (P_r + M_r) / 2), raises the column's entry in
+// the pair's scale array (atomicMax on the float bits, entries >= 0).
+// k_xaw_split: one thread per (pair, column, 8 orders r): scale 2^e from
+// that bound into [2^13, 2^15), P_r = X_r + X_-r, M_r = X_r - X_-r (P_0 = X_0,
+// M_0 = 0), every slot scaled, split into FP16 hi/lo and stored swizzled into
+// its K-chunk (A_re[r] = Re P_r, A_re[KP + r] = Im M_r, A_im[r] = Im P_r,
+// A_im[KP + r] = -Re M_r; zero for r >= L_h).  Columns beyond J are zero.
 
-// H values of columns j, j + 1 (the second zero when two is false)
-__device__ __forceinline__ float4 xw_ld2(const float2* p, bool two) {
-  if (two) return __ldg(reinterpret_cast<const float4*>(p));
-  const float2 a = __ldg(p);
-  return make_float4(a.x, a.y, 0.f, 0.f);
-}
-// x_v += k_v h for the four pairs v of a group and two columns: acc[v] =
-// (re, im) of both columns, h = (H of column 0, H of column 1)
-__device__ __forceinline__ void xw_mac2(float4* acc, float4 k01, float4 k23, float4 h) {
-  const float kr[XW_PP] = {k01.x, k01.z, k23.x, k23.z}, ki[XW_PP] = {k01.y, k01.w, k23.y, k23.w};
+// Complex multiply-adds of the group's pairs for one column: sk[i][v] =
+// k(p, q) of pair v, h = H^p_q of the column.
+template <int NP>
+__device__ __forceinline__ void xw_mac(const float2 (*sk)[NP], int i, float2 h, float* ar, float* ai) {
 #pragma unroll
-  for (int v = 0; v < XW_PP; ++v) {
-    acc[v].x = fmaf(kr[v], h.x, acc[v].x); acc[v].x = fmaf(-ki[v], h.y, acc[v].x);
-    acc[v].y = fmaf(kr[v], h.y, acc[v].y); acc[v].y = fmaf(ki[v], h.x, acc[v].y);
-    acc[v].z = fmaf(kr[v], h.z, acc[v].z); acc[v].z = fmaf(-ki[v], h.w, acc[v].z);
-    acc[v].w = fmaf(kr[v], h.w, acc[v].w); acc[v].w = fmaf(ki[v], h.z, acc[v].w);
+  for (int v = 0; v < NP; ++v) {
+    const float2 kv = sk[i][v];
+    ar[v] = fmaf(kv.x, h.x, ar[v]); ar[v] = fmaf(-kv.y, h.y, ar[v]);
+    ai[v] = fmaf(kv.x, h.y, ai[v]); ai[v] = fmaf(kv.y, h.x, ai[v]);
   }
 }
 
-// slot k of operand m (0: A_re, 1: A_im) of one column from its X row xs
-// (xs[(q + Lh - 1) * XW_COLS] = X_q)
-__device__ __forceinline__ float xw_slot(const float2* xs, int Lh, int KP, int m, int k) {
-  const int r = k < KP ? k : k - KP;
-  if (r >= Lh) return 0.f;
-  const float2 xp = xs[(size_t)(Lh - 1 + r) * XW_COLS];
-  if (k < KP) {                                     // P_r
-    if (r == 0) return m == 0 ? xp.x : xp.y;
-    const float2 xm = xs[(size_t)(Lh - 1 - r) * XW_COLS];
-    return m == 0 ? xp.x + xm.x : xp.y + xm.y;
-  }
-  if (r == 0) return 0.f;                           // M_0
-  const float2 xm = xs[(size_t)(Lh - 1 - r) * XW_COLS];
-  return m == 0 ? xp.y - xm.y : -(xp.x - xm.x);    // Im M_r | -Re M_r
-}
-
-__global__ void __launch_bounds__(XW_THREADS, 3)
-k_xaw_from_h(const float2* __restrict__ H, int Lh, int J, int nkf, unsigned char* __restrict__ xblob,
-             size_t blob_stride, int tiles, size_t kf_off, int npairs) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int K = 2 * Lh - 1, KF = 64 * nkf, KP = KF / 2;
-  float2* sX = reinterpret_cast<float2*>(smem_raw);                     // [XW_PP][K][XW_COLS]
-  int* sEx = reinterpret_cast<int*>(sX + (size_t)XW_PP * K * XW_COLS);  // [XW_PP][XW_COLS]
-  // pair groups vary fastest: the blocks of one H tile run together and share it in L2
-  const int groups = (npairs + XW_PP - 1) / XW_PP;
-  const int pb = (int)(blockIdx.x % groups) * XW_PP, part = (int)(blockIdx.x / groups);
-  const int tile = part / XW_PARTS, r0 = (part % XW_PARTS) * XW_COLS;
-  const int npp = min(XW_PP, npairs - pb);
-  const int n2 = Lh * Lh;
-  // k(p,q) of the group's pairs: two 16-byte loads per pq
-  const float4* kp = reinterpret_cast<const float4*>(xblob + (size_t)pb * blob_stride + kf_off);
-  const int jt = tile * TC_M + r0;
-  // items (q, column pair): one 16-byte H load serves two adjacent columns
-  for (int it = threadIdx.x; it < K * (XW_COLS / 2); it += XW_THREADS) {
-    const int u = it / (XW_COLS / 2), r = 2 * (it % (XW_COLS / 2));
-    const int q = u - (Lh - 1), aq = q < 0 ? -q : q;
-    const int j = jt + r;
-    float4 acc[XW_PP];                              // (re, im) of columns r and r + 1
-#pragma unroll
-    for (int v = 0; v < XW_PP; ++v) acc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (j < J) {
-      // j is even, so (j, j + 1) share a 128-column tile and a 16-byte H word
-      const float2* hp = H + h_index(0, j, n2);      // row pq at hp + pq * 128
-      const bool two = j + 1 < J;
-      int p = aq;
-      for (; p + 3 < Lh; p += 4) {                  // four degrees' loads in flight per step
-        float4 hv[4];
-#pragma unroll
-        for (int w = 0; w < 4; ++w) hv[w] = xw_ld2(hp + (size_t)((p + w) * (p + w) + (p + w) + q) * 128, two);
-#pragma unroll
-        for (int w = 0; w < 4; ++w) {
-          const int pq = (p + w) * (p + w) + (p + w) + q;
-          xw_mac2(acc, __ldg(kp + 2 * pq), __ldg(kp + 2 * pq + 1), hv[w]);
-        }
-      }
-      for (; p < Lh; ++p) {
-        const int pq = p * p + p + q;
-        xw_mac2(acc, __ldg(kp + 2 * pq), __ldg(kp + 2 * pq + 1), xw_ld2(hp + (size_t)pq * 128, two));
-      }
-    }
-#pragma unroll
-    for (int v = 0; v < XW_PP; ++v) *reinterpret_cast<float4*>(sX + ((size_t)v * K + u) * XW_COLS + r) = acc[v];
+template <int NP>
+__global__ void __launch_bounds__(TC_M) k_xw_x(const float2* __restrict__ H, const float2* __restrict__ kf, int Lh,
+                                               int J, int ng, unsigned char* __restrict__ xblob, size_t blob_stride,
+                                               size_t xf_off, size_t sc_off) {
+  __shared__ float2 sk[64][NP];                     // k(p, q) of the group, p = |q| + row
+  const int tile = blockIdx.x, u = blockIdx.y, q = u - (Lh - 1), aq = q < 0 ? -q : q;
+  const int n2 = Lh * Lh, P = Lh - aq, K = 2 * Lh - 1;
+  for (int t = threadIdx.x; t < P * NP; t += TC_M) {
+    const int i = t / NP, v = t % NP, pd = aq + i;
+    sk[i][v] = kf[(size_t)(pd * pd + pd + q) * XA_MAXP + v];
   }
   __syncthreads();
-  {   // four threads per (pair, column), then a shuffle across the four
-    const int col = threadIdx.x / 4, sub = threadIdx.x % 4;      // col < XW_PP * XW_COLS = 64
-    const float2* xs = sX + (size_t)(col / XW_COLS) * K * XW_COLS + (col % XW_COLS);
-    float mx = 0.f;
-    for (int k = sub; k < KF; k += 4)
-      mx = fmaxf(mx, fmaxf(fabsf(xw_slot(xs, Lh, KP, 0, k)), fabsf(xw_slot(xs, Lh, KP, 1, k))));
-    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
-    if (sub == 0) {
-      int ex = 0;
-      if (mx > 0.f) frexpf(mx, &ex);
-      sEx[col] = mx > 0.f ? min(125, max(-125, 15 - ex)) : 0;
-    }
-  }
-  __syncthreads();
-  // items (pair v, operand m, 8-slot chunk k0, column r), column fastest
-  for (int it = threadIdx.x; it < npp * 2 * (KF / 8) * XW_COLS; it += XW_THREADS) {
-    const int r = it % XW_COLS, k0 = ((it / XW_COLS) % (KF / 8)) * 8;
-    const int m = (it / (XW_COLS * (KF / 8))) % 2, v = it / (XW_COLS * (KF / 8) * 2);
-    const int e = sEx[v * XW_COLS + r];
-    const float sc = __int_as_float((127 + e) << 23);
-    const float2* xs = sX + (size_t)v * K * XW_COLS + r;
-    __align__(16) __half hi[8], lo[8];
+  const int col = threadIdx.x, j = tile * TC_M + col;
+  float ar[NP], ai[NP];
 #pragma unroll
-    for (int w = 0; w < 8; ++w) {
-      const float x = xw_slot(xs, Lh, KP, m, k0 + w) * sc;
-      hi[w] = __float2half_rn(x);
-      lo[w] = __float2half_rn(x - __half2float(hi[w]));
+  for (int v = 0; v < NP; ++v) ar[v] = ai[v] = 0.f;
+  if (j < J) {                                       // H past column J is never written
+    const float2* hp = H + (size_t)tile * n2 * TC_M + col;   // row pq at hp + pq * 128
+    float2 cur[4], nxt[4];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      const int pd = aq + w;
+      cur[w] = w < P ? __ldg(hp + (size_t)(pd * pd + pd + q) * TC_M) : make_float2(0.f, 0.f);
     }
-    unsigned char* blob = xblob + (size_t)(pb + v) * blob_stride;
-    unsigned char* cb = blob + ((size_t)tile * 2 * nkf + m * nkf + k0 / TC_KB) * TC_A_BYTES;
-    *reinterpret_cast<uint4*>(cb + sw128_off(r0 + r, k0 % TC_KB)) = *reinterpret_cast<uint4*>(hi);
-    *reinterpret_cast<uint4*>(cb + TC_A_HALF + sw128_off(r0 + r, k0 % TC_KB)) = *reinterpret_cast<uint4*>(lo);
-    if (k0 == 0 && m == 0) {
-      float* scales = reinterpret_cast<float*>(blob + (size_t)tiles * 2 * nkf * TC_A_BYTES);
-      scales[jt + r] = jt + r < J ? __int_as_float((127 - e) << 23) : 0.f;
+    for (int i = 0; i < P; i += 4) {
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {                  // the next four degrees, in flight meanwhile
+        const int pd = aq + i + 4 + w;
+        nxt[w] = i + 4 + w < P ? __ldg(hp + (size_t)(pd * pd + pd + q) * TC_M) : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int w = 0; w < 4; ++w)
+        if (i + w < P) xw_mac<NP>(sk, i + w, cur[w], ar, ai);
+#pragma unroll
+      for (int w = 0; w < 4; ++w) cur[w] = nxt[w];
     }
   }
+#pragma unroll
+  for (int v = 0; v < NP; ++v)
+    if (v < ng) {
+      unsigned char* blob = xblob + (size_t)v * blob_stride;
+      reinterpret_cast<float2*>(blob + xf_off)[((size_t)tile * K + u) * TC_M + col] = make_float2(ar[v], ai[v]);
+      if (j < J) atomicMax(reinterpret_cast<int*>(blob + sc_off) + j, __float_as_int(2.f * fmaxf(fabsf(ar[v]), fabsf(ai[v]))));
+    }
 }
 
-static size_t xaw_smem(int Lh) {
-  return sizeof(float2) * (size_t)XW_PP * (2 * Lh - 1) * XW_COLS + sizeof(int) * XW_PP * XW_COLS;
+// The coupling rows of a group as floats (k_kf_from_kc) and its pairs' column
+// maxima cleared.
+__global__ void k_xw_clear(int n, int ng, unsigned char* __restrict__ xblob, size_t blob_stride, size_t sc_off) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < (long long)n * ng;
+       t += (long long)gridDim.x * blockDim.x)
+    reinterpret_cast<int*>(xblob + (size_t)(t / n) * blob_stride + sc_off)[t % n] = 0;
+}
+
+// FP16 hi and lo of 8 scaled values as two 16-byte units
+__device__ __forceinline__ void xw_split8(const float* x, float sc, uint4* hi, uint4* lo) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int w = 0; w < 4; ++w) {
+    const float x0 = x[2 * w] * sc, x1 = x[2 * w + 1] * sc;
+    const __half2 a = __floats2half2_rn(x0, x1);
+    const float2 af = __half22float2(a);
+    const __half2 b = __floats2half2_rn(x0 - af.x, x1 - af.y);
+    h[w] = *reinterpret_cast<const uint32_t*>(&a);
+    l[w] = *reinterpret_cast<const uint32_t*>(&b);
+  }
+  *hi = make_uint4(h[0], h[1], h[2], h[3]);
+  *lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// One thread per (pair, column, group of 8 orders r): the warp's lanes are 32
+// / NRG columns x the NRG = KP / 8 groups, so each of its 16-byte stores
+// (8 slots of one part) fills whole rows of the swizzled image (512 or 256
+// contiguous bytes per instruction).
+__global__ void __launch_bounds__(256) k_xaw_split(int Lh, int J, int nkf, unsigned char* __restrict__ xblob,
+                                                   size_t blob_stride, int tiles, size_t xf_off) {
+  const int KP = 32 * nkf, K = 2 * Lh - 1, nrg = KP / 8, cpw = 32 / nrg;
+  const int pair = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int col = (blockIdx.x * 8 + warp) * cpw + lane / nrg;     // column of the pair's padded list
+  const int rg = lane % nrg, tile = col / TC_M, row = col % TC_M, j = col;
+  if (tile >= tiles) return;                         // whole warps: tiles x 128 is a multiple of cpw
+  unsigned char* blob = xblob + (size_t)pair * blob_stride;
+  // X_q of the column at x0[q * 128], q = -(Lh-1) .. Lh-1
+  const float2* x0 = reinterpret_cast<const float2*>(blob + xf_off) + ((size_t)tile * K + (Lh - 1)) * TC_M + row;
+  float* scales = reinterpret_cast<float*>(blob + (size_t)tiles * 2 * nkf * TC_A_BYTES);
+  const float mx = j < J ? scales[j] : 0.f;          // the column's slot bound (k_xw_x)
+  int ex = 0;
+  if (mx > 0.f) frexpf(mx, &ex);
+  const int e = mx > 0.f ? min(125, max(-125, 15 - ex)) : 0;
+  const float sc = __int_as_float((127 + e) << 23);
+  float a[4][8];                                     // Re P, Im P, Im M, -Re M of the group's 8 orders
+#pragma unroll
+  for (int w = 0; w < 8; ++w) {
+    const int r = rg * 8 + w;
+    float2 xp = make_float2(0.f, 0.f), xm = make_float2(0.f, 0.f);
+    if (r < Lh) xp = __ldg(x0 + (ptrdiff_t)r * TC_M);
+    if (r > 0 && r < Lh) xm = __ldg(x0 - (ptrdiff_t)r * TC_M);
+    const bool z = r == 0;
+    a[0][w] = z ? xp.x : xp.x + xm.x;
+    a[1][w] = z ? xp.y : xp.y + xm.y;
+    a[2][w] = z ? 0.f : xp.y - xm.y;
+    a[3][w] = z ? 0.f : -(xp.x - xm.x);
+  }
+  // A_re K-chunks, then A_im: (m * nkf + slot / 64) x 32 KB, hi then lo;
+  // A_re P part (Re P), A_im P part (Im P), A_re M part (Im M), A_im M part (-Re M)
+  unsigned char* ab = blob + (size_t)tile * 2 * nkf * TC_A_BYTES;
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    const int m = g & 1, k = (g < 2 ? 0 : KP) + rg * 8;
+    unsigned char* cb = ab + (size_t)(m * nkf + (k >> 6)) * TC_A_BYTES + sw128_off(row, k & 63);
+    uint4 hi, lo;
+    xw_split8(a[g], sc, &hi, &lo);
+    *reinterpret_cast<uint4*>(cb) = hi;
+    *reinterpret_cast<uint4*>(cb + TC_A_HALF) = lo;
+  }
+  __syncwarp();                                      // every lane has read the column's bound
+  if (rg == 0) scales[j] = j < J ? __int_as_float((127 - e) << 23) : 0.f;
 }
 
 cudaError_t launch_xaw_from_h(const double2* kc, const float2* H, int Lh, int Nb, int Ng, int npairs, void* xblob,
                               cudaStream_t st) {
   if (npairs <= 0) return cudaSuccess;
   if (Lh <= 16 || Lh > 64) return cudaErrorInvalidValue;
-  const int nkf = tcw_nk(Lh) / 2, tiles = tcw_tiles(Nb, Ng);
-  const long long blocks = (long long)((npairs + XW_PP - 1) / XW_PP) * XW_PARTS * tiles;
-  static_assert(XW_PP == 4, "xw_mac2 takes the coupling rows of four pairs");
-  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-  // the ceiling of the largest case (L_h = 64), set once (never inside a stream capture)
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_xaw_from_h, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xaw_smem(64));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  const int nkf = tcw_nk(Lh) / 2, tiles = tcw_tiles(Nb, Ng), n2 = Lh * Lh;
+  if (npairs > 65535) return cudaErrorInvalidValue;
   const size_t stride = tcw_xblob_bytes(Nb, Ng, Lh);
-  const size_t kf_off = (size_t)tiles * 2 * nkf * TC_A_BYTES + tcw_scales_bytes(tiles);
-  const int groups = (npairs + XW_PP - 1) / XW_PP;
-  k_kf_from_kc<<<dim3((Lh * Lh + 255) / 256, groups * XW_PP), 256, 0, st>>>(kc, Lh * Lh, npairs,
-                                                                           (unsigned char*)xblob, stride, kf_off);
-  k_xaw_from_h<<<(unsigned)blocks, XW_THREADS, xaw_smem(Lh), st>>>(H, Lh, Nb * Ng, nkf, (unsigned char*)xblob,
-                                                                   stride, tiles, kf_off, npairs);
+  const size_t sc_off = (size_t)tiles * 2 * nkf * TC_A_BYTES;
+  const size_t kf_off = sc_off + tcw_scales_bytes(tiles);
+  const size_t xf_off = kf_off + tcw_kf_bytes(Lh);
+  unsigned char* xb = (unsigned char*)xblob;
+  // first pass, per group of up to XA_MAXP pairs: X in FP32 and the columns'
+  // slot bounds
+  for (int g0 = 0; g0 < npairs; g0 += XA_MAXP) {
+    const int ng = std::min(XA_MAXP, npairs - g0);
+    unsigned char* gb = xb + (size_t)g0 * stride;
+    float2* kf = reinterpret_cast<float2*>(gb + kf_off);
+    k_kf_from_kc<<<(n2 * XA_MAXP + 255) / 256, 256, 0, st>>>(kc + (size_t)g0 * n2, n2, ng, kf);
+    const int n = tiles * TC_M;
+    k_xw_clear<<<(unsigned)std::min<long long>(((long long)n * ng + 255) / 256, 4096), 256, 0, st>>>(n, ng, gb, stride,
+                                                                                                    sc_off);
+    const dim3 grid(tiles, 2 * Lh - 1);
+    if (ng <= 4)
+      k_xw_x<4><<<grid, TC_M, 0, st>>>(H, kf, Lh, Nb * Ng, ng, gb, stride, xf_off, sc_off);
+    else if (ng <= 8)
+      k_xw_x<8><<<grid, TC_M, 0, st>>>(H, kf, Lh, Nb * Ng, ng, gb, stride, xf_off, sc_off);
+    else
+      k_xw_x<16><<<grid, TC_M, 0, st>>>(H, kf, Lh, Nb * Ng, ng, gb, stride, xf_off, sc_off);
+  }
+  // second pass: scales and the split A operands
+  const int cols_per_block = 8 * (32 / (4 * nkf));   // 8 warps of 32 / (KP / 8) columns
+  k_xaw_split<<<dim3((tiles * TC_M + cols_per_block - 1) / cols_per_block, npairs), 256, 0, st>>>(
+      Lh, Nb * Ng, nkf, xb, stride, tiles, xf_off);
   return cudaGetLastError();
 }
 
