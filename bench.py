@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="Poisson-arriving requests of the serving run (0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-only", action="store_true",
+                    help="run the serving measurement alone and print its record (diagnostics, not the bench line)")
     ap.add_argument("--profile-case", default="", choices=("", "window", "inverse_alt", "serve"),
                     help="small case for kernel captures, then exit: the L_h = 64 window generator (8 x 3 "
                          "degree ellipse), the inverse without h_0^0 at workload-2 sizes, or 300 served requests")
@@ -277,6 +279,7 @@ def serve_bench(pkg, device, n, rate, seed=4000, max_outstanding_bytes=48 << 30,
         ctx.poll(tk)
     torch.cuda.synchronize()
     done_at = np.full(n, np.nan)
+    submit_at = np.full(n, np.nan)
     parts = np.full((n, 4), np.nan)            # queue, host issue, device, total (library clock), ms
     # a seeded sample of requests whose results are kept for the oracle check
     # of the CPU leg: both precisions, the widest window and the largest signal
@@ -301,6 +304,7 @@ def serve_bench(pkg, device, n, rate, seed=4000, max_outstanding_bytes=48 << 30,
             if outstanding and out_bytes + nbytes > max_outstanding_bytes:
                 break
             g = torch.empty((len(r["pairs"]),) + tuple(r["grid"]), dtype=dt, device="cuda:%d" % device)
+            submit_at[i] = time.perf_counter() - t0
             tk = ctx.submit(r["Lf"], r["Lh"], r["grid"], r["f"], r["h"], r["pairs"], g, prec=r["prec"])
             outstanding[tk] = (i, g, nbytes)
             out_bytes += nbytes
@@ -331,6 +335,20 @@ def serve_bench(pkg, device, n, rate, seed=4000, max_outstanding_bytes=48 << 30,
         v = pt[:, col]
         return {"p50": float(np.percentile(v, 50)), "p99": float(np.percentile(v, 99)), "mean": float(v.mean())}
     slow = np.argsort(lat)[-max(1, len(lat) // 100):]          # the slowest 1 %
+    idx = np.nonzero(ok)[0]
+    wait = (submit_at[ok] - arrivals[ok]) * 1e3                 # arrival to submission (the output cap)
+    by_class = {}
+    for prec in (0, 1):
+        for Lh in (4, 8, 16, 32):
+            sel = np.array([reqs[k]["prec"] == prec and reqs[k]["Lh"] == Lh for k in idx])
+            if not sel.any():
+                continue
+            by_class["%s_Lh%d" % ("fp64" if prec == 0 else "fp32", Lh)] = {
+                "requests": int(sel.sum()), "p50_ms": float(np.percentile(lat[sel], 50)),
+                "p99_ms": float(np.percentile(lat[sel], 99)),
+                "mean_samples": float(np.mean([len(reqs[k]["pairs"]) * np.prod(reqs[k]["grid"]) for k in idx[sel]])),
+                "mean_queue_ms": float(pt[sel, 0].mean()), "mean_device_ms": float(pt[sel, 2].mean()),
+                "mean_wait_behind_cap_ms": float(wait[sel].mean())}
     return {"requests": n, "completed": int(ok.sum()), "offered_rate_per_s": rate,
             "achieved_rate_per_s": float(ok.sum() / span), "sustained": bool(ok.sum() / span >= 0.95 * rate),
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
@@ -338,6 +356,8 @@ def serve_bench(pkg, device, n, rate, seed=4000, max_outstanding_bytes=48 << 30,
             "g_samples_per_s": done_samples / span, "span_s": float(span),
             "mean_samples_per_request": done_samples / max(1, ok.sum()),
             "breakdown_ms": {"queue": pct(0), "host_issue": pct(1), "device": pct(2), "library_total": pct(3),
+                             "wait_behind_cap": {"p50": float(np.percentile(wait, 50)),
+                                                 "p99": float(np.percentile(wait, 99))},
                              "slowest_1pct_mean": {"queue": float(pt[slow, 0].mean()),
                                                    "device": float(pt[slow, 2].mean()),
                                                    "samples": float(np.mean([len(reqs[k]["pairs"]) * np.prod(
@@ -346,7 +366,9 @@ def serve_bench(pkg, device, n, rate, seed=4000, max_outstanding_bytes=48 << 30,
                                      "host issue = building + launching its first tick, device = start of its "
                                      "first tick to the end of its last (device clock); latency above is from "
                                      "arrival (includes the wait behind the output cap)"},
-            "engine": "ticks of persistent batched kernels replayed from a captured graph (two lanes)",
+            "by_class": by_class,
+            "engine": "ticks of persistent batched kernels replayed from a captured graph (an express lane and "
+                      "two bulk lanes)",
             "kept_for_oracle": kept,
             "workload": "L_f in {32..512}, L_h in {4,8,16,32}, 1-8 degrees x all m, native grid "
                         "2L_h-1 x L_h x 2L_h-1, FP64/FP32_BULK 50/50, Poisson arrivals (seed 4000); "
@@ -534,6 +556,11 @@ def main():
     if args.profile_pairs > 0:
         profile_case(pkg, args.profile_pairs, args.profile_prec, args.profile_workload, args.profile_fp64_arith,
                      args.profile_rotwin_engine, args.profile_beta_rows)
+        return
+    if args.serve_only:
+        rec = serve_bench(pkg, local, args.serve_requests, args.serve_rate)
+        rec.pop("kept_for_oracle", None)
+        print(json.dumps(rec))
         return
     dist = None
     if world > 1:

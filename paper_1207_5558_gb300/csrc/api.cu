@@ -122,6 +122,8 @@ struct Workspace {
   // Gaunt coefficient table of the last pair list this workspace saw
   void* gt = nullptr; size_t gt_cap = 0;
   void* gtw = nullptr; size_t gtw_cap = 0;   // its work items (pair, mirror pair)
+  void* cw = nullptr; size_t cw_cap = 0;     // the 3j-chain coupling's work items (pair, mirror pair)
+  std::vector<int32_t> cw_host;
   // real-field calls: the computed pairs, their output slots (host copies kept
   // until the next call: sources of the uploads) and the device slot map
   std::vector<int32_t> rf_lm, rf_slots;
@@ -202,6 +204,7 @@ struct SvLane {
 // Serving arena (per lane): list capacities, sizes of the staged-input and
 // device-only data regions, and the tick budget.
 #define SV_ITEMS 1024                         // request chunks per tick
+static_assert(SV_ITEMS <= SERVE_CPL_MAX, "a tick's coupling index fits its work-item encoding");
 #define SV_PAIRS (1 << 17)                    // pairs per tick (coupling lists)
 #define SV_RBLK (1 << 18)                     // rotated-window blocks per tick
 #define SV_TILES (1 << 20)                    // alpha tiles per tick and precision
@@ -385,6 +388,7 @@ static void ws_release(slsht_ctx* c, Workspace& w) {
   ctx_free(c, w.H, w.H_cap);
   ctx_free(c, w.gt, w.gt_cap);
   ctx_free(c, w.gtw, w.gtw_cap);
+  ctx_free(c, w.cw, w.cw_cap);
   ctx_free(c, w.rfs, w.rfs_cap);
   ctx_free(c, w.ms, w.ms_cap);
   ctx_free(c, w.kdd, w.kdd_cap);
@@ -982,8 +986,14 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
     LAUNCH(SLSHT_STAGE_COUPLE, ax,
            launch_couple_apply((const double2*)f_dev, Lh, (const int2*)lm_dev, n_pairs, w.gt, (double2*)w.kc, ax));
   } else {
+    // 3j chains in the call; a pair and its mirror (l, -m) share theirs
+    mirror_work(lm_host, n_pairs, &w.cw_host);
+    const int nwork = (int)(w.cw_host.size() / 2);
+    CKS(ws_reserve(ctx, w, &w.cw, &w.cw_cap, sizeof(int32_t) * w.cw_host.size()));
+    CK(cudaMemcpyAsync(w.cw, w.cw_host.data(), sizeof(int32_t) * w.cw_host.size(), cudaMemcpyHostToDevice, ax));
     LAUNCH(SLSHT_STAGE_COUPLE, ax,
-           launch_couple((const double2*)f_dev, Lf, Lh, (const int2*)lm_dev, n_pairs, (double2*)w.kc, ax));
+           launch_couple((const double2*)f_dev, Lf, Lh, (const int2*)lm_dev, n_pairs, (double2*)w.kc, ax,
+                         (const int2*)w.cw, nwork));
   }
   // route 1: the window rotated to every (beta, gamma) sample, once per call
   // (SLSHT_OPT_WINDOW_ORDERS: over the window's active orders only)
@@ -2705,6 +2715,7 @@ static int sv_tick(slsht_ctx* c, SvLane& ln, std::unique_lock<std::mutex>& lk) {
   int nrot = 0;
   bool wait_lane[SERVE_LANES] = {false};
   std::vector<SvTc> tcs;
+  std::vector<int32_t> mw;                               // a chunk's coupling work items
   CK(cudaEventRecord(ln.ev_a, ln.st));
   // items in decreasing tile cost, so the large tiles start first
   std::vector<int> order(ch.size());
@@ -2781,7 +2792,10 @@ static int sv_tick(slsht_ctx* c, SvLane& ln, std::unique_lock<std::mutex>& lk) {
     }
     const int idx = (int)ii;
     const int cls = Lh <= 16 ? 0 : (Lh <= 32 ? 1 : 2);
-    for (int pr = 0; pr < np; ++pr) cplp[cls][hdr[cls]++] = make_int2(idx, pr);
+    // the chunk's pairs, a pair and its mirror (l, -m) in one work item
+    mirror_work(r.lm.data() + 2 * (size_t)k.p0, np, &mw);
+    for (size_t wi = 0; wi < mw.size(); wi += 2)
+      cplp[cls][hdr[cls]++] = serve_couple_entry(idx, mw[wi], mw[wi + 1]);
     if (dd)
       for (int pr = 0; pr < np; ++pr) kblk[hdr[3]++] = BCplBlk{idx, pr};
     if (k.comp_h) {                                      // the window, once per request

@@ -85,10 +85,17 @@ cudaError_t launch_batch_alpha(int prec, const BItem* items, const BTile* tiles,
 
 // The serving path's launches (fixed grids, work counts read from device
 // memory, so that one captured graph serves ticks of any composition):
-//   launch_serve_couple  k of the {coupling, pair} list by 3j chains in the
-//                        call (cls 0: L_h <= 16, 1: <= 32, 2: <= 64)
+//   launch_serve_couple  k of the list of work items by 3j chains in the call
+//                        (cls 0: L_h <= 16, 1: <= 32, 2: <= 64); an item is
+//                        serve_couple_entry(coupling, pair, mirror): the
+//                        mirror pair (l, -m) of the same coupling (-1: none)
+//                        gets its k from the same chains
 //   launch_batch_kdd_n, launch_batch_rotwin_n, launch_batch_alpha_n
 //                        as above with the block / tile count *n.
+#define SERVE_CPL_MAX 1024               // couplings a serving tick may list (its chunks)
+__host__ __device__ inline int2 serve_couple_entry(int cpl, int pair, int mirror) {
+  return make_int2(cpl + SERVE_CPL_MAX * (mirror + 1), pair);
+}
 cudaError_t launch_serve_couple(int cls, const BCouple* cpl, const int2* list, const int* n, int grid,
                                 cudaStream_t st);
 cudaError_t launch_batch_kdd_n(const BCouple* cpl, const BCplBlk* blk, const int* n, int grid, cudaStream_t st);

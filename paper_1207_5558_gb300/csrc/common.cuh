@@ -44,9 +44,12 @@ cudaError_t launch_phase_dd(float4* tab, int N, int R, int r0, cudaStream_t st);
 // beta quadrature weights q_b, b < Nb (see the inverse).
 cudaError_t launch_beta_weights(double* w, int Nb, cudaStream_t st);
 
-// k_lm(p, q) for each pair: kc[pair * Lh*Lh + p*p + p + q] (complex128).
-cudaError_t launch_couple(const double2* f, int Lf, int Lh, const int2* lm, int npairs,
-                          double2* kc, cudaStream_t st);
+// k_lm(p, q) for each pair: kc[pair * Lh*Lh + p*p + p + q] (complex128), by
+// 3j chains in FP64.  work (nullable, device): nwork items (pair, mirror index
+// of (l, -m) or -1), every pair in exactly one item (mirror_work on the host):
+// the mirror's k comes from the same chains.
+cudaError_t launch_couple(const double2* f, int Lf, int Lh, const int2* lm, int npairs, double2* kc, cudaStream_t st,
+                          const int2* work = nullptr, int nwork = 0);
 
 // The same k through a signal-independent table of Gaunt coefficients:
 // launch_gaunt_table fills `table` (gaunt_table_bytes) for a pair list from

@@ -6,16 +6,6 @@
 #include "batch.cuh"
 #include "couple_dev.cuh"
 
-// 1/x for a positive integer-valued x: float reciprocal refined by two
-// Newton-Raphson steps, r <- r (2 - x r), to full double precision.
-__device__ __forceinline__ double rcp_newton(double x) {
-  double r = (double)__frcp_rn((float)x);
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  return fma(r, e, r);
-}
-
 // 3j symbols (j1 j2 j3; m1 m2 m3), m1 = -m2 - m3, for every j1 in
 // [j1min, j1max] = [max(|j2-j3|, |m1|), j2 + j3], into f[0 .. n-1].
 // Schulten-Gordon recurrence in j1:
@@ -29,9 +19,12 @@ __device__ __forceinline__ double rcp_newton(double x) {
 // When j1min = 0 (j2 = j3, m1 = 0) the recurrence is silent at j1 = 0 and the
 // first step uses f(1)/f(0) = m2 / sqrt(j2 (j2 + 1)).
 // A(j1) and 1/A(j1) come from one rsqrt of the polynomial A^2 and are carried
-// from step to step.  Returns n (0 if the chain is empty).
+// from step to step; the reciprocals 1/j1 come from the table rc (rc[j - rbase]
+// = 1/j, correctly rounded, for every j1 + 1 of the chain).  Returns n (0 if
+// the chain is empty).
 template <int CMAX>
-__device__ int threej_chain(int j2, int j3, int m2, int m3, double* f, double* bwd, int* j1min_out) {
+__device__ int threej_chain(int j2, int j3, int m2, int m3, double* f, double* bwd, int* j1min_out,
+                            const double* rc, int rbase) {
   const int m1 = -m2 - m3;
   const int j1min = max(abs(j2 - j3), abs(m1));
   const int j1max = j2 + j3;
@@ -65,7 +58,7 @@ __device__ int threej_chain(int j2, int j3, int m2, int m3, double* f, double* b
         f[1] = (double)m2 * rsqrt((double)j2 * (j2 + 1.0));
       } else {
         const double prev = i > 0 ? f[i - 1] : 0.0;
-        f[i + 1] = -(B(j1) * f[i] + (j1 + 1.0) * acur * prev) * rn * rcp_newton((double)j1);
+        f[i + 1] = -(B(j1) * f[i] + (j1 + 1.0) * acur * prev) * rn * rc[j1 - rbase];
       }
       acur = p2 * rn;
     };
@@ -83,7 +76,7 @@ __device__ int threej_chain(int j2, int j3, int m2, int m3, double* f, double* b
       const double p2 = A2(j1);
       const double r = rsqrt(p2);
       const double nxt = (kb + 1 < n) ? bwd[kb + 1] : 0.0;
-      bwd[kb - 1] = -(B(j1) * bwd[kb] + j1 * anext * nxt) * r * rcp_newton(j1 + 1.0);
+      bwd[kb - 1] = -(B(j1) * bwd[kb] + j1 * anext * nxt) * r * rc[j1 + 1 - rbase];
       anext = p2 * r;
       --kb;
       if (fabs(bwd[kb]) < fabs(bwd[kb + 1])) break;
@@ -108,18 +101,24 @@ __device__ int threej_chain(int j2, int j3, int m2, int m3, double* f, double* b
   return n;
 }
 
-// One pair's k_lm(p, q), every item t = p*p + p + q, by one CTA.  First the
-// CTA builds, in shared memory (w0s), the (l' p l; 0 0 0) family for every
-// p < Lh: the two-term relation
+// Shared per-pair tables of a CTA (couple_setup): w0s, the (l' p l; 0 0 0)
+// family of every p < Lh by the two-term relation
 //   f(j1+1) = -sqrt((j1^2-d^2)(S^2-j1^2) / (((j1+1)^2-d^2)(S^2-(j1+1)^2))) f(j1-1),
 // d = p - l, S = p + l + 1, over the even j1 + p + l, normalised by
-// sum (2 j1 + 1) f^2 = 1 with sgn f(p + l) = (-1)^{p-l}.  Then item t runs
-// the (l' p l; m-q q -m) chain and accumulates k_lm(p, q) into kc[t].  Every
-// thread of the block takes part (the block may call it again after it).
-template <int CMAX>
-__device__ __forceinline__ void couple_pair_chains(const double2* __restrict__ f, int Lf, int Lh, int l, int m,
-                                                   double2* __restrict__ kc, double* w0s) {
-  __syncthreads();                              // w0s of a previous call is read
+// sum (2 j1 + 1) f^2 = 1 with sgn f(p + l) = (-1)^{p-l}, stored already
+// multiplied by the rest of T that does not depend on q or the chain:
+// (-1)^m sqrt((2p+1)(2l+1)/(4 pi)) sqrt(2 l' + 1); and rcs, the reciprocals
+// 1/j for j in [rbase, l + Lh] (every j1 + 1 of the pair's chains, rbase =
+// max(0, l - Lh + 1)) for threej_chain.  Every thread of the block takes
+// part (the block may call it again after it).
+#define COUPLE_RCS (2 * SLSHT_MAX_LH + 2)
+__device__ __forceinline__ int couple_setup(int Lh, int l, int m, double* w0s, double* rcs) {
+  __syncthreads();                              // the tables of a previous call are read
+  const int rbase = max(0, l - Lh + 1);
+  for (int i = threadIdx.x; i <= l + Lh - rbase; i += blockDim.x) {
+    const int j = rbase + i;
+    rcs[i] = j > 0 ? 1.0 / (double)j : 0.0;
+  }
   for (int p = threadIdx.x; p < Lh; p += blockDim.x) {
     double* w = w0s + p * (p + 1) / 2;
     const int j0 = abs(p - l), cnt = min(p, l) + 1;
@@ -135,19 +134,48 @@ __device__ __forceinline__ void couple_pair_chains(const double2* __restrict__ f
     double s0 = rsqrt(norm);
     const double want = ((p - l) & 1) ? -1.0 : 1.0;
     if (v * want < 0.0) s0 = -s0;
-    for (int i = 0; i < cnt; ++i) w[i] *= s0;
+    const double pre = ((m & 1) ? -1.0 : 1.0) *
+                       sqrt((2.0 * p + 1.0) * (2.0 * l + 1.0) / (4.0 * 3.14159265358979323846));
+    for (int i = 0; i < cnt; ++i) w[i] *= s0 * pre * sqrt(2.0 * (j0 + 2 * i) + 1.0);
   }
   __syncthreads();
+  return rbase;
+}
+
+// (p, q) of item t = p*p + p + q
+__device__ __forceinline__ void couple_item(int t, int* p_out, int* q_out) {
+  int p = (int)sqrt((double)t);
+  while (p * p > t) --p;
+  while ((p + 1) * (p + 1) <= t) ++p;
+  *p_out = p;
+  *q_out = t - p * p - p;
+}
+
+// One pair's k_lm(p, q), every item t = p*p + p + q, by one CTA: item (p, q)
+// runs the (l' p l; m-q q -m) chain and accumulates
+//   k_lm(p, q) = sum_l' f_{l', m-q} T(l', m-q; p, q; l, m).
+// Mirror items share their chain: with q -> -q and m -> -m,
+//   (l' p l; -m+q, -q, m) = (-1)^{l'+p+l} (l' p l; m-q, q, -m),
+// and l'+p+l is even wherever (l' p l; 0 0 0) is non-zero, so item (p, -q)
+// of the pair (l, -m) has the same T with f_{l', -(m-q)}: kcm (nullable) is
+// that pair's k row, filled from the same chains; for m = 0 the pair is its
+// own mirror and only the items q >= 0 run chains (q > 0 also fill (p, -q)).
+template <int CMAX>
+__device__ __forceinline__ void couple_pair_chains(const double2* __restrict__ f, int Lf, int Lh, int l, int m,
+                                                   double2* __restrict__ kc, double2* __restrict__ kcm, double* w0s,
+                                                   double* rcs) {
+  const int rbase = couple_setup(Lh, l, m, w0s, rcs);
   const int nitems = Lh * Lh;
+  const bool self = m == 0;
   double fm[CMAX], bwd[CMAX];
   for (int t = threadIdx.x; t < nitems; t += blockDim.x) {
-    int p = (int)sqrt((double)t);
-    while (p * p > t) --p;
-    while ((p + 1) * (p + 1) <= t) ++p;
-    const int q = t - p * p - p;
-    double2 acc = make_double2(0.0, 0.0);
+    int p, q;
+    couple_item(t, &p, &q);
+    if (self && q < 0) continue;                    // filled by the item (p, -q)
+    const bool two = kcm != nullptr || (self && q > 0);
+    double2 acc = make_double2(0.0, 0.0), accm = make_double2(0.0, 0.0);
     int j1min_m;
-    const int nm = threej_chain<CMAX>(p, l, q, -m, fm, bwd, &j1min_m);
+    const int nm = threej_chain<CMAX>(p, l, q, -m, fm, bwd, &j1min_m, rcs, rbase);
     if (nm > 0) {
       const double* w = w0s + p * (p + 1) / 2;
       const int j0 = abs(p - l);
@@ -157,41 +185,55 @@ __device__ __forceinline__ void couple_pair_chains(const double2* __restrict__ f
       int i0 = (j1min_m - j0 + 1) / 2;
       if (i0 < 0) i0 = 0;
       for (int j1 = j0 + 2 * i0; j1 <= jend; j1 += 2) {
-        const double c = sqrt(2.0 * j1 + 1.0) * w[(j1 - j0) >> 1] * fm[j1 - j1min_m];
+        const double c = w[(j1 - j0) >> 1] * fm[j1 - j1min_m];
         const double2 fv = f[j1 * j1 + j1 + mu];
         acc.x = fma(c, fv.x, acc.x);
         acc.y = fma(c, fv.y, acc.y);
+        if (two) {
+          const double2 fw = f[j1 * j1 + j1 - mu];
+          accm.x = fma(c, fw.x, accm.x);
+          accm.y = fma(c, fw.y, accm.y);
+        }
       }
-      const double pre = ((m & 1) ? -1.0 : 1.0) *
-                         sqrt((2.0 * p + 1.0) * (2.0 * l + 1.0) / (4.0 * 3.14159265358979323846));
-      acc.x *= pre;
-      acc.y *= pre;
     }
     kc[t] = acc;
+    if (kcm != nullptr) kcm[p * p + p - q] = accm;
+    else if (self && q > 0) kc[p * p + p - q] = accm;
   }
 }
 
-// One CTA per pair.
+// One CTA per work item: pair work[i].x, and the mirror pair work[i].y
+// (l, -m) filled from the same chains (-1: none); without a work list, one
+// CTA per pair.
 template <int CMAX>
 __global__ void __launch_bounds__(256) k_couple(const double2* __restrict__ f, int Lf, int Lh,
-                                                const int2* __restrict__ lm, double2* __restrict__ kc) {
+                                                const int2* __restrict__ lm, const int2* __restrict__ work,
+                                                double2* __restrict__ kc) {
   __shared__ double w0s[SLSHT_MAX_LH * (SLSHT_MAX_LH + 1) / 2];
-  const int pair = blockIdx.x;
-  couple_pair_chains<CMAX>(f, Lf, Lh, lm[pair].x, lm[pair].y, kc + (size_t)pair * Lh * Lh, w0s);
+  __shared__ double rcs[COUPLE_RCS];
+  const int2 wk = work != nullptr ? work[blockIdx.x] : make_int2((int)blockIdx.x, -1);
+  const size_t n2 = (size_t)Lh * Lh;
+  couple_pair_chains<CMAX>(f, Lf, Lh, lm[wk.x].x, lm[wk.x].y, kc + (size_t)wk.x * n2,
+                           wk.y >= 0 ? kc + (size_t)wk.y * n2 : nullptr, w0s, rcs);
 }
 
 // The same for the pairs of many couplings (serving ticks): blocks stride
-// over the list {coupling, pair} of *n entries.
+// over the list of *n work items {coupling + SERVE_CPL_MAX (mirror + 1), pair}
+// (serve_couple_entry), pair and mirror indices within the coupling's list.
 template <int CMAX>
 __global__ void __launch_bounds__(256) k_serve_couple(const BCouple* __restrict__ cpl, const int2* __restrict__ list,
                                                       const int* __restrict__ n) {
   __shared__ double w0s[SLSHT_MAX_LH * (SLSHT_MAX_LH + 1) / 2];
+  __shared__ double rcs[COUPLE_RCS];
   const int cnt = *n;
   for (int i = blockIdx.x; i < cnt; i += gridDim.x) {
     const int2 e = list[i];
-    const BCouple c = cpl[e.x];
+    const int ci = e.x % SERVE_CPL_MAX, mir = e.x / SERVE_CPL_MAX - 1;
+    const BCouple c = cpl[ci];
     const int2 pr = c.lm[e.y];
-    couple_pair_chains<CMAX>(c.f, c.Lf, c.Lh, pr.x, pr.y, c.kc + (size_t)e.y * c.Lh * c.Lh, w0s);
+    const size_t n2 = (size_t)c.Lh * c.Lh;
+    couple_pair_chains<CMAX>(c.f, c.Lf, c.Lh, pr.x, pr.y, c.kc + (size_t)e.y * n2,
+                             mir >= 0 ? c.kc + (size_t)mir * n2 : nullptr, w0s, rcs);
   }
 }
 
@@ -203,17 +245,18 @@ cudaError_t launch_serve_couple(int cls, const BCouple* cpl, const int2* list, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_couple(const double2* f, int Lf, int Lh, const int2* lm, int npairs,
-                          double2* kc, cudaStream_t st) {
+cudaError_t launch_couple(const double2* f, int Lf, int Lh, const int2* lm, int npairs, double2* kc, cudaStream_t st,
+                          const int2* work, int nwork) {
   if (npairs <= 0) return cudaSuccess;
   const int threads = Lh * Lh < 256 ? ((Lh * Lh + 31) / 32) * 32 : 256;
+  const int grid = work != nullptr ? nwork : npairs;
   // same carveout as the kernels it runs beside (see the tensor-core alpha stage)
   cudaFuncSetAttribute(k_couple<32>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   cudaFuncSetAttribute(k_couple<64>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   cudaFuncSetAttribute(k_couple<128>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-  if (Lh <= 16) k_couple<32><<<npairs, threads, 0, st>>>(f, Lf, Lh, lm, kc);
-  else if (Lh <= 32) k_couple<64><<<npairs, threads, 0, st>>>(f, Lf, Lh, lm, kc);
-  else k_couple<128><<<npairs, threads, 0, st>>>(f, Lf, Lh, lm, kc);
+  if (Lh <= 16) k_couple<32><<<grid, threads, 0, st>>>(f, Lf, Lh, lm, work, kc);
+  else if (Lh <= 32) k_couple<64><<<grid, threads, 0, st>>>(f, Lf, Lh, lm, work, kc);
+  else k_couple<128><<<grid, threads, 0, st>>>(f, Lf, Lh, lm, work, kc);
   return cudaGetLastError();
 }
 
@@ -230,41 +273,30 @@ cudaError_t launch_couple(const double2* f, int Lf, int Lh, const int2* lm, int 
 // and l'+p+l is even wherever (l' p l; 0 0 0) is non-zero, so
 // T(l', -m+q; p, -q; l, -m) = T(l', m-q; p, q; l, m) with the same l' range:
 // work item w = (pair, mirror) fills item (p, q) of `pair` and item (p, -q) of
-// `mirror` (when mirror >= 0) from one chain.
+// `mirror` (when mirror >= 0) from one chain; a pair with m = 0 is its own
+// mirror (its items q > 0 also fill (p, -q)).
 template <int CMAX>
 __global__ void __launch_bounds__(256) k_gaunt_table(int Lf, int Lh, const int2* __restrict__ lm,
                                                      const int2* __restrict__ work, double* __restrict__ coef,
                                                      int2* __restrict__ meta) {
   __shared__ double w0s[SLSHT_MAX_LH * (SLSHT_MAX_LH + 1) / 2];
+  __shared__ double rcs[COUPLE_RCS];
   const int pair = work[blockIdx.x].x, mirror = work[blockIdx.x].y;
   const int l = lm[pair].x, m = lm[pair].y;
-  for (int p = threadIdx.x; p < Lh; p += blockDim.x) {
-    double* w = w0s + p * (p + 1) / 2;
-    const int j0 = abs(p - l), cnt = min(p, l) + 1;
-    const double dd = (double)(p - l), SS = (double)(p + l + 1);
-    double v = 1.0, norm = 2.0 * j0 + 1.0;
-    w[0] = 1.0;
-    for (int i = 1; i < cnt; ++i) {
-      const double x = (double)(j0 + 2 * i - 1), y = x + 1.0;
-      v *= -sqrt(((x * x - dd * dd) * (SS * SS - x * x)) / ((y * y - dd * dd) * (SS * SS - y * y)));
-      w[i] = v;
-      norm += (2.0 * (j0 + 2 * i) + 1.0) * v * v;
-    }
-    double s0 = rsqrt(norm);
-    const double want = ((p - l) & 1) ? -1.0 : 1.0;
-    if (v * want < 0.0) s0 = -s0;
-    for (int i = 0; i < cnt; ++i) w[i] *= s0;
-  }
-  __syncthreads();
+  const int rbase = couple_setup(Lh, l, m, w0s, rcs);
   const int n2 = Lh * Lh;
+  // the item (p, -q) that shares the chain of (p, q): the mirror pair's, or,
+  // for m = 0, the pair's own (then only the items q >= 0 run chains)
+  const bool self = m == 0;
   double fm[CMAX], bwd[CMAX];
   for (int t = threadIdx.x; t < n2; t += blockDim.x) {
-    int p = (int)sqrt((double)t);
-    while (p * p > t) --p;
-    while ((p + 1) * (p + 1) <= t) ++p;
-    const int q = t - p * p - p;
+    int p, q;
+    couple_item(t, &p, &q);
+    if (self && q < 0) continue;
+    const int tm = p * p + p - q;
+    const int opair = mirror >= 0 ? mirror : (self && q > 0 ? pair : -1);
     int j1min_m, first = 0, cnt = 0;
-    const int nm = threej_chain<CMAX>(p, l, q, -m, fm, bwd, &j1min_m);
+    const int nm = threej_chain<CMAX>(p, l, q, -m, fm, bwd, &j1min_m, rcs, rbase);
     if (nm > 0) {
       const double* w = w0s + p * (p + 1) / 2;
       const int j0 = abs(p - l);
@@ -272,21 +304,18 @@ __global__ void __launch_bounds__(256) k_gaunt_table(int Lf, int Lh, const int2*
       int i0 = (j1min_m - j0 + 1) / 2;
       if (i0 < 0) i0 = 0;
       first = j0 + 2 * i0;
-      const double pre = ((m & 1) ? -1.0 : 1.0) *
-                         sqrt((2.0 * p + 1.0) * (2.0 * l + 1.0) / (4.0 * 3.14159265358979323846));
-      const int tm = p * p + p - q;          // the mirror pair's item (p, -q)
       for (int j1 = first; j1 <= jend; j1 += 2, ++cnt) {
-        const double c = pre * sqrt(2.0 * j1 + 1.0) * w[(j1 - j0) >> 1] * fm[j1 - j1min_m];
+        const double c = w[(j1 - j0) >> 1] * fm[j1 - j1min_m];
         coef[((size_t)pair * Lh + cnt) * n2 + t] = c;
-        if (mirror >= 0) coef[((size_t)mirror * Lh + cnt) * n2 + tm] = c;
+        if (opair >= 0) coef[((size_t)opair * Lh + cnt) * n2 + tm] = c;
       }
     }
     for (int i = cnt; i < Lh; ++i) {
       coef[((size_t)pair * Lh + i) * n2 + t] = 0.0;
-      if (mirror >= 0) coef[((size_t)mirror * Lh + i) * n2 + (p * p + p - q)] = 0.0;
+      if (opair >= 0) coef[((size_t)opair * Lh + i) * n2 + tm] = 0.0;
     }
     meta[(size_t)pair * n2 + t] = make_int2(first, cnt);
-    if (mirror >= 0) meta[(size_t)mirror * n2 + (p * p + p - q)] = make_int2(first, cnt);
+    if (opair >= 0) meta[(size_t)opair * n2 + tm] = make_int2(first, cnt);
   }
 }
 

@@ -15,19 +15,21 @@
 // split parts, already in the 128-byte swizzled K-major image the MMAs read,
 // are built once per context from the FP32 d(beta) table (launch_rotwin_tc_table,
 // one 32 KB image of hi and lo parts per (degree, 128-row tile, 64-wide K
-// chunk), and one scale per row).  The window operand B_p changes with h and
-// is built in shared memory per degree, with the window's inactive orders
-// (qmask) as zero columns.
+// chunk), and one scale per row).  The window operand B_p changes with h: a
+// small kernel per call (launch_rotwin_tc_window) writes it per degree in the
+// same image form, with the window's inactive orders (qmask) as zero columns.
 //
 // The kernel is persistent (one CTA per SM over a contiguous range of the
-// (degree, row tile) list, the ranges of equal traffic) and warp-specialised: warp 0 streams the d images
-// through a ring of three stages with cp.async.bulk; warp 1 issues the MMAs
-// into two TMEM accumulators (2 x (Re, Im) x 128 columns: all 512) and
-// commits them to mbarriers; warps 2..9 build the window operand when the
-// degree changes and drain the accumulators (two warps per TMEM lane quadrant,
-// each half of the 128 rows) while the next tile's products run.  Every wait
-// is bounded: on expiry the CTA raises its abort flag, every role leaves its
-// loop, copies and products in flight complete, and the error word is set.
+// (degree, row tile) list, the ranges of equal traffic) and warp-specialised:
+// warp 0 streams the d chunks through a ring of three stages with
+// cp.async.bulk and, when the degree changes and the previous degree's
+// products have completed, the new degree's window operand; warp 1 issues the
+// MMAs into two TMEM accumulators (2 x (Re, Im) x 128 columns: all 512) and
+// commits them to mbarriers; warps 2..9 drain the accumulators (two warps per
+// TMEM lane quadrant, each half of the 128 rows) while the next tile's
+// products run.  Every wait is bounded: on expiry the CTA raises its abort
+// flag, every role leaves its loop, copies and products in flight complete,
+// and the error word is set.
 #include <cuda_fp16.h>
 
 #include "common.cuh"

@@ -278,6 +278,35 @@ def test_gaunt_table_mirror_pairs_with_duplicates(ctx):
     assert rel(g, O.forward_coeff(f, h, Lf, Lh, pairs, grid)) < TOL64
 
 
+@pytest.mark.parametrize("Lh", [7, 24, 40])
+def test_coupling_chains_share_mirror_items(ctx, Lh):
+    """The 3j chains of the call (SLSHT_OPT_GAUNT_TABLE 2) run once for a
+    pair and its mirror (l, -m), and once for the items (p, q), (p, -q) of an
+    m = 0 pair: a list with matched and unmatched mirrors, a repeated pair, a
+    pair listed before its mirror and after it, against the oracle and the
+    Gaunt-table route (every chain length class: L_h <= 16, <= 32, <= 64)."""
+    import paper_1207_5558_gb300 as pkg
+    Lf = 30
+    grid = (2 * (Lf + Lh) - 1, 12, 2 * Lh - 1)
+    f = synth.signal_powerlaw(Lf, 171)
+    h = synth.window_cn(Lh, 172, decay=1.0)
+    pairs = np.concatenate([np.array([[11, 4], [11, 4], [11, -4], [20, 0], [13, -7], [3, 2], [29 + Lh // 2, 5],
+                                      [29 + Lh // 2, -5], [8, -3]], dtype=np.int32),
+                            synth.pairs_bands([Lf + Lh - 2])[::3]])
+    ctx.set_option(pkg.SLSHT_OPT_GAUNT_TABLE, 2)
+    try:
+        chains = _fw(ctx, Lf, Lh, grid, f, h, pairs, 0)
+        ctx.set_option(pkg.SLSHT_OPT_GAUNT_TABLE, 1)
+        table = _fw(ctx, Lf, Lh, grid, f, h, pairs, 0)
+    finally:
+        ctx.set_option(pkg.SLSHT_OPT_GAUNT_TABLE, 0)
+    assert rel(chains, table) < 1e-13
+    ref = O.forward_coeff(f, h, Lf, Lh, pairs, grid)
+    assert rel(chains, ref) < TOL64
+    for i in range(len(pairs)):                      # every pair, mirrors and duplicates included
+        assert rel(chains[i], ref[i]) < 1e-11, i
+
+
 @pytest.mark.parametrize("name,prec,Lh,engine,rot", [
     ("fused", 1, 5, 0, 0),           # k_alpha_fused: producer warps in the alpha kernel
     ("two_kernel", 1, 5, 2, 0),      # k_alpha_tc fed by k_xa_from_h
