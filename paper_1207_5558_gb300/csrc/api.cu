@@ -214,6 +214,7 @@ static_assert(SV_ITEMS <= SERVE_CPL_MAX, "a tick's coupling index fits its work-
 #define SV_CHUNK_SAMPLES (8ll << 20)          // first share of one request in a tick
 #define SV_HPOOL_BYTES ((size_t)4 << 30)      // rotated windows of the started requests
 #define SV_EXPRESS_SAMPLES (4ll << 20)        // requests this small run on the express lane
+#define SV_MEDIUM_SAMPLES (64ll << 20)        // bulk lane 1 serves requests up to this size first
 
 // Byte offsets of a serving arena's regions (the same in the pinned stage,
 // which mirrors the lists and the staged inputs).
@@ -2619,8 +2620,20 @@ static int sv_tick(slsht_ctx* c, SvLane& ln, std::unique_lock<std::mutex>& lk) {
   size_t dev = 0, in = 0;
   int npairs[3] = {0, 0, 0}, nkblk = 0, nrblk = 0;
   const bool express = &ln == &c->lanes[0];
-  for (auto& up : c->active) {
-    Request& r = *up;
+  // bulk lane 1 takes the medium requests first (arrival order among them),
+  // then the rest, so a medium request does not wait behind the large ones
+  // that lane 2 works through first come first served
+  std::vector<Request*> cand;
+  cand.reserve(c->active.size());
+  const bool medium_first = &ln == &c->lanes[1];
+  for (int pass = 0; pass < (medium_first ? 2 : 1); ++pass)
+    for (auto& up : c->active) {
+      const slsht_desc& d = up->desc;
+      const bool medium = (long long)up->n_pairs * d.n_alpha * d.n_beta * d.n_gamma <= SV_MEDIUM_SAMPLES;
+      if (!medium_first || medium == (pass == 0)) cand.push_back(up.get());
+    }
+  for (Request* rp : cand) {
+    Request& r = *rp;
     if (r.next >= r.n_pairs) continue;
     if (samples >= SV_TICK_SAMPLES || (int)ch.size() >= SV_ITEMS) break;
     const slsht_desc& d = r.desc;
