@@ -66,7 +66,12 @@ size_t tcw_xblob_bytes(int Nb, int Ng, int Lh) {
 // conversion per coefficient (float/double conversions share the slow FP64
 // pipe on this GPU; the producer then reads floats), pair v of the group at
 // [pq][v]; the slots past the group's last pair are zero.
-__global__ void k_kf_from_kc(const double2* __restrict__ kc, int n2, int ng, float2* __restrict__ kf) {
+__global__ void k_kf_from_kc(const double2* __restrict__ kc, int n2, int npairs, unsigned char* __restrict__ xblob,
+                             size_t blob_stride, size_t kf_off) {
+  // group blockIdx.y: pairs g0 .. g0 + ng - 1, its table in the group's first blob
+  const int g0 = blockIdx.y * XA_MAXP, ng = min(XA_MAXP, npairs - g0);
+  kc += (size_t)g0 * n2;
+  float2* kf = reinterpret_cast<float2*>(xblob + (size_t)g0 * blob_stride + kf_off);
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n2 * XA_MAXP; t += gridDim.x * blockDim.x) {
     const int pq = t / XA_MAXP, v = t % XA_MAXP;
     float2 o = make_float2(0.f, 0.f);
@@ -143,10 +148,14 @@ __device__ __forceinline__ void xw_mac(const float2 (*sk)[NP], int i, float2 h, 
 }
 
 template <int NP>
-__global__ void __launch_bounds__(TC_M) k_xw_x(const float2* __restrict__ H, const float2* __restrict__ kf, int Lh,
-                                               int J, int ng, unsigned char* __restrict__ xblob, size_t blob_stride,
+__global__ void __launch_bounds__(TC_M) k_xw_x(const float2* __restrict__ H, int Lh, int J, int npairs,
+                                               unsigned char* __restrict__ xblob, size_t blob_stride, size_t kf_off,
                                                size_t xf_off, size_t sc_off) {
   __shared__ float2 sk[64][NP];                     // k(p, q) of the group, p = |q| + row
+  // group blockIdx.z: pairs g0 .. g0 + ng - 1 (blobs from g0), couplings in g0's blob
+  const int g0 = blockIdx.z * XA_MAXP, ng = min(NP, npairs - g0);
+  xblob += (size_t)g0 * blob_stride;
+  const float2* kf = reinterpret_cast<const float2*>(xblob + kf_off);
   const int tile = blockIdx.x, u = blockIdx.y, q = u - (Lh - 1), aq = q < 0 ? -q : q;
   const int n2 = Lh * Lh, P = Lh - aq, K = 2 * Lh - 1;
   for (int t = threadIdx.x; t < P * NP; t += TC_M) {
@@ -188,8 +197,7 @@ __global__ void __launch_bounds__(TC_M) k_xw_x(const float2* __restrict__ H, con
     }
 }
 
-// The coupling rows of a group as floats (k_kf_from_kc) and its pairs' column
-// maxima cleared.
+// The column maxima of every pair cleared (before k_xw_x raises them).
 __global__ void k_xw_clear(int n, int ng, unsigned char* __restrict__ xblob, size_t blob_stride, size_t sc_off) {
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < (long long)n * ng;
        t += (long long)gridDim.x * blockDim.x)
@@ -272,24 +280,21 @@ cudaError_t launch_xaw_from_h(const double2* kc, const float2* H, int Lh, int Nb
   const size_t kf_off = sc_off + tcw_scales_bytes(tiles);
   const size_t xf_off = kf_off + tcw_kf_bytes(Lh);
   unsigned char* xb = (unsigned char*)xblob;
-  // first pass, per group of up to XA_MAXP pairs: X in FP32 and the columns'
-  // slot bounds
-  for (int g0 = 0; g0 < npairs; g0 += XA_MAXP) {
-    const int ng = std::min(XA_MAXP, npairs - g0);
-    unsigned char* gb = xb + (size_t)g0 * stride;
-    float2* kf = reinterpret_cast<float2*>(gb + kf_off);
-    k_kf_from_kc<<<(n2 * XA_MAXP + 255) / 256, 256, 0, st>>>(kc + (size_t)g0 * n2, n2, ng, kf);
-    const int n = tiles * TC_M;
-    k_xw_clear<<<(unsigned)std::min<long long>(((long long)n * ng + 255) / 256, 4096), 256, 0, st>>>(n, ng, gb, stride,
-                                                                                                    sc_off);
-    const dim3 grid(tiles, 2 * Lh - 1);
-    if (ng <= 4)
-      k_xw_x<4><<<grid, TC_M, 0, st>>>(H, kf, Lh, Nb * Ng, ng, gb, stride, xf_off, sc_off);
-    else if (ng <= 8)
-      k_xw_x<8><<<grid, TC_M, 0, st>>>(H, kf, Lh, Nb * Ng, ng, gb, stride, xf_off, sc_off);
-    else
-      k_xw_x<16><<<grid, TC_M, 0, st>>>(H, kf, Lh, Nb * Ng, ng, gb, stride, xf_off, sc_off);
-  }
+  // first pass, every group of up to XA_MAXP pairs in one launch: X in FP32
+  // and the columns' slot bounds
+  const int groups = (npairs + XA_MAXP - 1) / XA_MAXP;
+  if (groups > 65535) return cudaErrorInvalidValue;
+  k_kf_from_kc<<<dim3((n2 * XA_MAXP + 255) / 256, groups), 256, 0, st>>>(kc, n2, npairs, xb, stride, kf_off);
+  const int n = tiles * TC_M;
+  k_xw_clear<<<(unsigned)std::min<long long>(((long long)n * npairs + 255) / 256, 8192), 256, 0, st>>>(n, npairs, xb,
+                                                                                                     stride, sc_off);
+  const dim3 grid(tiles, 2 * Lh - 1, groups);
+  if (npairs <= 4)
+    k_xw_x<4><<<grid, TC_M, 0, st>>>(H, Lh, Nb * Ng, npairs, xb, stride, kf_off, xf_off, sc_off);
+  else if (npairs <= 8)
+    k_xw_x<8><<<grid, TC_M, 0, st>>>(H, Lh, Nb * Ng, npairs, xb, stride, kf_off, xf_off, sc_off);
+  else
+    k_xw_x<16><<<grid, TC_M, 0, st>>>(H, Lh, Nb * Ng, npairs, xb, stride, kf_off, xf_off, sc_off);
   // second pass: scales and the split A operands
   const int cols_per_block = 8 * (32 / (4 * nkf));   // 8 warps of 32 / (KP / 8) columns
   k_xaw_split<<<dim3((tiles * TC_M + cols_per_block - 1) / cols_per_block, npairs), 256, 0, st>>>(

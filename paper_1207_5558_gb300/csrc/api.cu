@@ -1549,6 +1549,14 @@ struct BatchItemHost {
 // and the alpha kernel do not share SMs (the alpha kernel holds a whole SM's
 // shared memory), so a chunk's only cost is the X scratch.
 #define XW_CHUNK 16
+// Pairs per producer + alpha launch of the wide engine in plans and serving:
+// XW_CHUNK, or more when a pair's operand blob is small (up to 256 MB of
+// blobs, 128 pairs), so that requests of many pairs on small grids do not
+// become hundreds of short launches.
+static int xw_chunk_pairs(int Nb, int Ng, int Lh) {
+  const size_t per = std::max<size_t>(1, tcw_xblob_bytes(Nb, Ng, Lh));
+  return (int)std::max<size_t>(XW_CHUNK, std::min<size_t>(((size_t)256 << 20) / per, 128));
+}
 
 #define ENG_NATIVE 0
 #define ENG_DD 1
@@ -2163,8 +2171,8 @@ static int batch_build(slsht_batch* b, const slsht_batch_item* src, int32_t n, c
       b->k_alpha += 2 * ((it.npairs + it.xw_pairs - 1) / it.xw_pairs);
     } else if (it.d.L_h <= 16) {
       b->k_alpha++;
-    } else {   // wide: producer + alpha kernel per chunk of XW_CHUNK pairs
-      it.xw_pairs = std::min(it.npairs, XW_CHUNK);
+    } else {   // wide: producer + alpha kernel per chunk of xw_chunk_pairs pairs
+      it.xw_pairs = std::min(it.npairs, xw_chunk_pairs(it.d.n_beta, it.d.n_gamma, it.d.L_h));
       CKS(batch_alloc(b, tcw_xblob_bytes(it.d.n_beta, it.d.n_gamma, it.d.L_h) * it.xw_pairs, &it.xw));
       b->k_alpha += 2 * ((it.npairs + it.xw_pairs - 1) / it.xw_pairs);
     }
@@ -2412,12 +2420,14 @@ static bool sv_ddform(const Request& r) {
 }
 // The tensor-core engines' operand scratch of a chunk of np pairs (the FP64
 // digits of up to T64_CHUNK pairs, the wide FP32 engine's operand of up to
-// XW_CHUNK pairs; none for the fused FP32 kernel).
+// xw_chunk_pairs pairs; none for the fused FP32 kernel).
 static size_t sv_xw_bytes(const Request& r, int np) {
   const slsht_desc& d = r.desc;
   if (r.engine != ENG_TC) return 0;
   if (d.prec == SLSHT_FP64) return sv_up(tc64_xblob_bytes(d.n_beta, d.n_gamma) * (size_t)std::min(np, T64_CHUNK));
-  if (d.L_h > 16) return sv_up(tcw_xblob_bytes(d.n_beta, d.n_gamma, d.L_h) * (size_t)std::min(np, XW_CHUNK));
+  if (d.L_h > 16)
+    return sv_up(tcw_xblob_bytes(d.n_beta, d.n_gamma, d.L_h) *
+                 (size_t)std::min(np, xw_chunk_pairs(d.n_beta, d.n_gamma, d.L_h)));
   return 0;
 }
 // Bytes of a request's rotated window in the pool (with the double-float
@@ -2505,7 +2515,7 @@ static void sv_choose(slsht_ctx* c, Request& r) {
 
 // The tensor-core launches of one chunk (after the graph's coupling and
 // rotated window): the fused FP32 kernel (L_h <= 16), the wide engine's
-// producer and alpha kernel per XW_CHUNK pairs, or the FP64 digit producer and
+// producer and alpha kernel per xw_chunk_pairs pairs, or the FP64 digit producer and
 // alpha kernel per T64_CHUNK pairs.
 struct SvTc {
   const double2* kc;
@@ -2536,8 +2546,9 @@ static cudaError_t sv_tc_launch(slsht_ctx* c, const SvTc& t, cudaStream_t st) {
   if (t.Lh <= 16)
     return launch_alpha_fused(t.kc, (const float2*)t.H, t.etab, t.Lh, t.Na, t.Nb, t.Ng, t.np, (float2*)t.g,
                               c->num_sms, 0, nullptr, st);
-  for (int off = 0; off < t.np; off += XW_CHUNK) {
-    const int n = std::min(XW_CHUNK, t.np - off);
+  const int xc = xw_chunk_pairs(t.Nb, t.Ng, t.Lh);
+  for (int off = 0; off < t.np; off += xc) {
+    const int n = std::min(xc, t.np - off);
     cudaError_t e = launch_xaw_from_h(t.kc + (size_t)off * n2, (const float2*)t.H, t.Lh, t.Nb, t.Ng, n, t.xw, st);
     if (e == cudaSuccess)
       e = launch_alpha_tcw(t.xw, t.etab, t.Lh, t.Na, t.Nb, t.Ng, n, (float2*)t.g + per_pair * off, c->num_sms, nullptr,
