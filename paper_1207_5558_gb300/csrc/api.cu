@@ -786,6 +786,19 @@ static int dd_rule_cols(int Lh, long long J) {
   return nt;
 }
 
+// Pairs a chunk of the wide tensor-core engine (calls, plans, serving): the
+// producer reads H from HBM once per group of 16 pairs, and the producer and
+// the alpha kernel do not share SMs (the alpha kernel holds a whole SM's
+// shared memory), so a chunk's cost is its operand scratch: XW_CHUNK pairs,
+// or more when a pair's operand blob is small (up to 256 MB of blobs, 128
+// pairs), so that requests of many pairs on small grids do not become
+// hundreds of short launches.
+#define XW_CHUNK 16
+static int xw_chunk_pairs(int Nb, int Ng, int Lh) {
+  const size_t per = std::max<size_t>(1, tcw_xblob_bytes(Nb, Ng, Lh));
+  return (int)std::max<size_t>(XW_CHUNK, std::min<size_t>(((size_t)256 << 20) / per, 128));
+}
+
 // Pairs a chunk of an FP64 tensor-core call or plan item (digit producer +
 // alpha kernel).
 #define T64_CHUNK 48
@@ -911,8 +924,9 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
     const size_t target = (size_t)96 << 20;
     P = (int)std::max<size_t>(1, std::min<size_t>((size_t)n_pairs, target / std::max<size_t>(1, x_per_pair)));
     P = std::min(P, 256);
-    // the wide engine's producer reads H once per chunk: up to 16 pairs a chunk
-    if (wide) P = std::max(P, std::min<int>(n_pairs, 16));
+    // the wide engine's producer reads H once per group of 16 pairs, and a
+    // chunk is one launch of each of its kernels: xw_chunk_pairs a chunk
+    if (wide) P = std::min<int>(n_pairs, xw_chunk_pairs(Nb, Ng, Lh));
     // the FP64 tensor-core kernel is persistent over (pair, tile) items: up to
     // 48 pairs a chunk keep its last wave short (about 20 items a CTA at
     // workload 3's 62 tiles a pair)
@@ -1543,20 +1557,6 @@ struct BatchItemHost {
   void* xw = nullptr;                  // wide tensor-core items: A-operand scratch of xw_pairs pairs
   int xw_pairs = 0;
 };
-
-// Pairs a chunk of a wide tensor-core item: the producer reads H once per
-// chunk (from HBM once, from L2 once per group of four pairs); the producer
-// and the alpha kernel do not share SMs (the alpha kernel holds a whole SM's
-// shared memory), so a chunk's only cost is the X scratch.
-#define XW_CHUNK 16
-// Pairs per producer + alpha launch of the wide engine in plans and serving:
-// XW_CHUNK, or more when a pair's operand blob is small (up to 256 MB of
-// blobs, 128 pairs), so that requests of many pairs on small grids do not
-// become hundreds of short launches.
-static int xw_chunk_pairs(int Nb, int Ng, int Lh) {
-  const size_t per = std::max<size_t>(1, tcw_xblob_bytes(Nb, Ng, Lh));
-  return (int)std::max<size_t>(XW_CHUNK, std::min<size_t>(((size_t)256 << 20) / per, 128));
-}
 
 #define ENG_NATIVE 0
 #define ENG_DD 1
