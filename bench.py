@@ -945,6 +945,20 @@ def main():
         ctx.profile(False)
         ms = e0.elapsed_time(e1)
         st = ctx.stats(reset=True)
+        # the inversion round trip of the 16 pairs (Sec. III-C): f_lm from the 136 GB of g
+        fd_out = torch.empty(len(p5), dtype=torch.complex128, device="cuda")
+        pkg.slsht_inverse(ctx.h, desc, gb, complex(h5[0]), p5d, len(p5), fd_out, stream)
+        barrier()
+        e0.record(stream)
+        pkg.slsht_inverse(ctx.h, desc, gb, complex(h5[0]), p5d, len(p5), fd_out, stream)
+        e1.record(stream)
+        barrier()
+        inv_ms = e0.elapsed_time(e1)
+        ftrue = f5[p5[:, 0] ** 2 + p5[:, 0] + p5[:, 1]]
+        fr = fd_out.cpu().numpy()
+        inversion = {"ms": inv_ms, "g_read_TB_per_s": smp * 8.0 / (inv_ms / 1e3) / 1e12,
+                     "rel_l2_recovered_f": float(np.linalg.norm(fr - ftrue) / np.linalg.norm(ftrue))}
+        del fd_out
         # the rotated window on the CUDA cores (SLSHT_OPT_ROTWIN_ENGINE = 1), over
         # all orders and over the window's active orders only (SLSHT_OPT_WINDOW_ORDERS
         # = 2: the ellipse window's odd orders are at the rounding level)
@@ -992,6 +1006,7 @@ def main():
                "rotated_window": "tensor cores (the default for L_h > 16): split-FP16 products, the d(beta) "
                                  "operand's split parts built once per context",
                "rotated_window_cuda_cores": cuda_cores,
+               "inversion_round_trip": inversion,
                "note": "stage times from events around each launch (beta_gamma: the rotated window and the alpha "
                        "operand producer); the alpha fraction is the g bytes over the alpha kernels' summed time "
                        "against the measured copy bandwidth; rotated_window_cuda_cores: the same call with "
