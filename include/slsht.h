@@ -463,7 +463,10 @@ int slsht_get_stats(slsht_ctx* ctx, slsht_stats* out, int reset);
  *                            producer kernel; 3: one fused kernel (producer
  *                            warps build the tensor-core operand in shared
  *                            memory; route 1 only); 4: CUDA cores, direct sum
- *                            only.  Tensor cores: FP32_BULK and L_h <= 16 only.
+ *                            only.  Tensor cores: FP32_BULK with L_h <= 16
+ *                            (2 and 3), and the wide engine for
+ *                            16 < L_h <= 64 (orders +-q paired, producer in
+ *                            two passes), which 0 and 2 select there.
  *                            0 (default): 3 where it applies, else 2, else 1.
  *  SLSHT_OPT_CHUNK_PAIRS  pairs per launch chunk (scratch size).
  *  SLSHT_OPT_GAUNT_TABLE  the 3j part of the coupling (Sec. III-B: T through

@@ -278,6 +278,29 @@ def test_gaunt_table_mirror_pairs_with_duplicates(ctx):
     assert rel(g, O.forward_coeff(f, h, Lf, Lh, pairs, grid)) < TOL64
 
 
+@pytest.mark.parametrize("npairs", [3, 7, 37])
+def test_wide_engine_pair_group_sizes(ctx, npairs):
+    """The wide engine's producer in groups of up to 16 pairs (one launch
+    over every group, with the group's sums in registers: 4, 8 or 16 of them
+    a thread): 3, 7 and 37 pairs (two full groups and a group of 5), FP32_BULK
+    at L_h = 20 and 40, against the oracle and the CUDA-core alpha stage."""
+    import paper_1207_5558_gb300 as pkg
+    Lf = 14
+    for Lh in (20, 40):
+        grid = (2 * (Lf + Lh) - 1, 10, 2 * Lh - 1)
+        f = synth.signal_powerlaw(Lf, 181 + Lh)
+        h = synth.window_cn(Lh, 182 + Lh, decay=1.0)
+        pairs = synth.pairs_random(Lf + Lh - 1, npairs, 183 + npairs)
+        g = _fw(ctx, Lf, Lh, grid, f, h, pairs, 1)
+        assert rel(g, O.forward_coeff(f, h, Lf, Lh, pairs, grid)) < TOL32
+        ctx.set_option(pkg.SLSHT_OPT_ALPHA_ENGINE, 1)
+        try:
+            cc = _fw(ctx, Lf, Lh, grid, f, h, pairs, 1)
+        finally:
+            ctx.set_option(pkg.SLSHT_OPT_ALPHA_ENGINE, 0)
+        assert rel(g, cc) < 5e-6
+
+
 @pytest.mark.parametrize("Lh", [7, 24, 40])
 def test_coupling_chains_share_mirror_items(ctx, Lh):
     """The 3j chains of the call (SLSHT_OPT_GAUNT_TABLE 2) run once for a

@@ -128,6 +128,8 @@ def test_steer_gamma_from_basis_orientations(ctx, prec, N):
     (5, (130, 10, 9), 0),            # ragged row tiles, short K
     (64, (129, 33, 128), 0),         # L_h = 64: K = 127 in two chunks, all 128 lanes, 33 beta rows
     (64, (129, 7, 65), 2),           # few beta rows: tiles that span several betas; rounding-level orders
+    (20, (41, 1, 1), 0),             # one beta row, one gamma sample: a tile per degree, most rows padding
+    (17, (35, 3, 2), 0),             # the smallest window on the default path (L_h > 16), two gamma samples
 ])
 def test_rotated_window_on_tensor_cores(ctx, Lh, grid, orders):
     """The rotated window on the tensor cores (SLSHT_OPT_ROTWIN_ENGINE = 2,
