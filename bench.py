@@ -60,7 +60,7 @@ def parse():
                     help="small case for kernel captures, then exit: the L_h = 64 window generator (8 x 3 "
                          "degree ellipse), the inverse without h_0^0 at workload-2 sizes, 300 served requests, "
                          "or two calls per precision of a large serving-shaped request (L_f = 256, L_h = 32, "
-                         "4 degrees x all m on the 63 x 32 x 63 grid)")
+                         "degrees 150 and 250 with all m on the 63 x 32 x 63 grid)")
     ap.add_argument("--profile-pairs", type=int, default=0,
                     help="profiling case: two forwards (FP32_BULK) over the last N pairs of map 0, "
                          "48 pairs per chunk, then exit")
@@ -439,12 +439,13 @@ def profile_case_other(pkg, case):
         Lh, Lf = 32, 256
         grid = serve_native(Lh)
         f, h = synth.signal_powerlaw(Lf, 1), synth.window_cn(Lh, 2, decay=1.0)
-        pairs = np.ascontiguousarray(synth.pairs_bands([100, 150, 200, 250]))
+        pairs = np.ascontiguousarray(synth.pairs_bands([150, 250]))
         for prec in (1, 0):
             g = torch.empty((len(pairs),) + grid, dtype=torch.complex64 if prec else torch.complex128, device="cuda")
             for _ in range(2):
                 pkg.slsht_forward(ctx.h, pkg.make_desc(Lf, Lh, grid, prec), f, h, pairs, len(pairs), g)
-        torch.cuda.synchronize()
+            torch.cuda.synchronize()
+            del g
         print(json.dumps({"profile_case": case, "pairs": len(pairs), "grid": list(grid)}))
     else:
         reqs = serve_requests(300, 4000)
