@@ -536,8 +536,10 @@ int slsht_get_stats(slsht_ctx* ctx, slsht_stats* out, int reset);
  *  SLSHT_OPT_ROTWIN_ENGINE FP32_BULK calls: the rotated window on 1 the
  *                            CUDA cores, or 2 the tensor cores where they
  *                            apply (n_gamma <= 128); 0, the default: the
- *                            tensor cores for L_h > 16 where they apply, else
- *                            the CUDA cores.  On the tensor cores: split-FP16
+ *                            tensor cores for L_h > 16 where they apply and
+ *                            the context's budget holds their d(beta) image
+ *                            with a quarter of the budget to spare, else the
+ *                            CUDA cores.  On the tensor cores: split-FP16
  *                            products with FP32 accumulation, each MMA tile
  *                            the gamma samples (128 rows) by 128 (beta, q)
  *                            rows of one degree, Re and Im in two

@@ -509,6 +509,15 @@ static int get_dtab(slsht_ctx* ctx, int Lh, int Nb, int prec, cudaStream_t st, c
   return SLSHT_OK;
 }
 
+// Whether the context holds the tensor-core rotated window's d(beta) image of
+// (Lh, Nb), or has room for it beside a quarter of its budget left for the
+// call's own buffers (the default engine takes the CUDA cores otherwise).
+static bool rtab_fits(slsht_ctx* ctx, int Lh, int Nb) {
+  std::lock_guard<std::mutex> g(ctx->mu);
+  if (ctx->rtab.count(std::make_tuple(Lh, Nb))) return true;
+  return ctx->used.load() + rotwin_tc_table_bytes(Lh, Nb) + ctx->budget / 4 <= ctx->budget;
+}
+
 // The tensor-core rotated window's split-FP16 d(beta) images (from the FP32
 // d table; once per (Lh, Nb)).
 static int get_rtab(slsht_ctx* ctx, int Lh, int Nb, cudaStream_t st, const void** out) {
@@ -1032,7 +1041,8 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
       LAUNCH(SLSHT_STAGE_BETA, ax,
              launch_rotwin_f64((const double2*)h_dev, (const double*)dt, (const double2*)eg, Lh, Nb, Ng,
                                (double2*)w.H, ax, qmask));
-    else if ((rot_engine == 2 || (rot_engine == 0 && Lh > 16)) && rotwin_tc_supported(Lh, Ng)) {
+    else if ((rot_engine == 2 || (rot_engine == 0 && Lh > 16)) && rotwin_tc_supported(Lh, Ng) &&
+             (rot_engine == 2 || rtab_fits(ctx, Lh, Nb))) {
       const void* rtab;
       {
         std::lock_guard<std::mutex> g(ctx->mu);
@@ -2110,7 +2120,7 @@ static int batch_build(slsht_batch* b, const slsht_batch_item* src, int32_t n, c
     for (size_t r = 0; r < b->rot.size(); ++r) {
       const BRot& br = b->rot[r];
       if (br.prec != 1 || br.H == nullptr || !rotwin_tc_supported(br.Lh, br.Ng)) continue;
-      if (!(rot_engine == 2 || (rot_engine == 0 && br.Lh > 16))) continue;
+      if (!(rot_engine == 2 || (rot_engine == 0 && br.Lh > 16 && rtab_fits(ctx, br.Lh, br.Nb)))) continue;
       slsht_batch::RotTc rt{(int)r, nullptr, nullptr};
       {
         std::lock_guard<std::mutex> g(ctx->mu);

@@ -157,3 +157,49 @@ def test_rotated_window_on_tensor_cores(ctx, Lh, grid, orders):
     assert _rel(tc, ref) < TOL[1]
     assert _rel(tc, cc) < 5e-6
     assert np.array_equal(default, tc if Lh > 16 else cc)   # the default: the tensor cores for L_h > 16
+
+
+def _rtab_bytes(Lh, Nb):
+    """Bytes of the tensor-core rotated window's d(beta) image: a 32 KB block
+    per (degree, tile of 128 (beta, q) rows, 64-wide K chunk) and a float per
+    row."""
+    tiles = chunks = 0
+    for p in range(Lh):
+        t = (Nb * (2 * p + 1) + 127) // 128
+        tiles += t
+        chunks += t * ((2 * p + 1 + 63) // 64)
+    return chunks * 32768 + tiles * 128 * 4
+
+
+def test_rotated_window_engine_falls_back_within_budget():
+    """The default engine leaves the tensor cores for the CUDA cores when the
+    context's budget cannot hold the d(beta) image (with a quarter of the
+    budget to spare); forcing the tensor cores then fails with
+    SLSHT_E_NOMEM.  The fallback's g equals the CUDA-core engine's bits."""
+    import torch
+    import paper_1207_5558_gb300 as pkg
+    from paper_1207_5558_gb300 import _abi
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    Lf, Lh, grid = 12, 40, (81, 64, 127)
+    f = synth.signal_powerlaw(Lf, 341)
+    h = synth.window_cn(Lh, 342, decay=1.0)
+    pairs = synth.pairs_bands([5])
+    big = pkg.Context(0, 4 << 30)
+    try:
+        big.set_option(pkg.SLSHT_OPT_ROTWIN_ENGINE, 1)
+        cc = big.forward(Lf, Lh, grid, f, h, pairs, prec=1).cpu().numpy()
+        need = pkg.slsht_mem_used(big.h)
+    finally:
+        big.close()
+    small = pkg.Context(0, need + _rtab_bytes(Lh, grid[1]) // 2)
+    try:
+        got = small.forward(Lf, Lh, grid, f, h, pairs, prec=1).cpu().numpy()
+        assert np.array_equal(got, cc)
+        small.set_option(pkg.SLSHT_OPT_ROTWIN_ENGINE, 2)
+        with pytest.raises(pkg.SlshtError) as e:
+            small.forward(Lf, Lh, grid, f, h, pairs, prec=1)
+        assert e.value.code == _abi.SLSHT_E_NOMEM
+    finally:
+        small.close()
+
