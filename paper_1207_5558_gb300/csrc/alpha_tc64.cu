@@ -463,12 +463,15 @@ k_alpha_tc64(const unsigned char* __restrict__ xblob, size_t blob_stride, int ti
             ar[w] = __uint_as_float(vr[w][u]);
             ai[w] = __uint_as_float(vi[w][u]);
           }
+          // padding columns past J and rows past N_alpha are exact zeros that
+          // would take the assembly's FP64 branch: only live samples are formed
+          const bool live = jin && a0 + u < Na;
+          if (!live) continue;
           float rh, rl, ih, il;
           t64_combine2(ar, ai, &rh, &rl, &ih, &il);
           const double re = dd_to_double(rh, rl, sc), im = dd_to_double(ih, il, sc);
-          const bool live = jin && a0 + u < Na;
-          if (live) __stcs(gp + (size_t)(a0 + u) * J, make_double2(re, im));
-          if (live && gm != nullptr) {   // (l, -m): (-1)^m conj g, signs on the bit patterns
+          __stcs(gp + (size_t)(a0 + u) * J, make_double2(re, im));
+          if (gm != nullptr) {           // (l, -m): (-1)^m conj g, signs on the bit patterns
             const unsigned long long br = (unsigned long long)__double_as_longlong(re) ^ msgn;
             const unsigned long long bi = (unsigned long long)__double_as_longlong(im) ^ msgn ^ (1ull << 63);
             __stcs(gm + (size_t)(a0 + u) * J,

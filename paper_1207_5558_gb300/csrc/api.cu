@@ -936,10 +936,14 @@ static int forward_core(slsht_ctx* ctx, Workspace& w, const slsht_desc* d, const
     // the wide engine's producer reads H once per group of 16 pairs, and a
     // chunk is one launch of each of its kernels: xw_chunk_pairs a chunk
     if (wide) P = std::min<int>(n_pairs, xw_chunk_pairs(Nb, Ng, Lh));
-    // the FP64 tensor-core kernel is persistent over (pair, tile) items: up to
-    // 48 pairs a chunk keep its last wave short (about 20 items a CTA at
-    // workload 3's 62 tiles a pair)
-    if (t64) P = std::max(P, std::min<int>(n_pairs, T64_CHUNK));
+    // the FP64 tensor-core kernel is persistent over (pair, tile) items: at
+    // least 48 pairs a chunk keep its last wave short (about 20 items a CTA at
+    // workload 3's 62 tiles a pair), and on small grids up to 256 MB of digit
+    // operands a chunk (fewer launches, each with more items a CTA)
+    if (t64)
+      P = std::min<int>(n_pairs, (int)std::max<size_t>(T64_CHUNK, std::min<size_t>(((size_t)256 << 20) /
+                                                                                     std::max<size_t>(1, x_per_pair),
+                                                                                     1024)));
   }
   if (host_out) {
     // staging buffers for the chunk outputs (double-buffered, D2H on the copy stream)
