@@ -267,6 +267,7 @@ __device__ __forceinline__ void ba_tile(const BItem& it, const BTile& tl, unsign
     kp = nullptr;
   }
   const T2* H = reinterpret_cast<const T2*>(it.H);
+  const bool om = sizeof(T) == sizeof(float) && h_order_major(Lh);   // the FP32 wide window's row order
   // X_q for the tile's columns: four degrees' loads in flight per step
   for (int e = tid; e < K * NT; e += BA_THREADS) {
     const int qi = e / NT, c = e - qi * NT;
@@ -281,7 +282,7 @@ __device__ __forceinline__ void ba_tile(const BItem& it, const BTile& tl, unsign
           const int p = p0 + v;
           if (p < Lh) {
             const int pq = p * p + p + q;
-            hv[v] = H[h_index(pq, j, n2)];
+            hv[v] = H[h_index(om ? h_row(p, q, Lh, true) : pq, j, n2)];
             if (staged) {
               kv[v] = kp[pq];
             } else {

@@ -96,6 +96,20 @@ cudaError_t launch_betagamma_f32(const double2* kc, const double2* h, const floa
 __host__ __device__ __forceinline__ size_t h_index(int pq, int j, int n2) {
   return ((size_t)(j >> 7) * (size_t)n2 + (size_t)pq) * 128 + (size_t)(j & 127);
 }
+// Row of (p, q) in a tile of H.  In pq order it is p*p + p + q.  The FP32
+// window of a band limit L_h > 16 is stored order-major instead: the rows of
+// order q (its degrees p = |q| .. L_h - 1) are one contiguous run, the runs in
+// order q = -(L_h - 1) .. L_h - 1, so that the wide engine's per-order
+// products read each (tile, order) as one block.  Both orders use the same
+// n2 = L_h^2 rows.
+__host__ __device__ __forceinline__ int h_row(int p, int q, int Lh, bool order_major) {
+  if (!order_major) return p * p + p + q;
+  const int a = q < 0 ? -q : q, m = Lh - 1;
+  const int off = q <= 0 ? (m - a) * (m - a + 1) / 2 : m * (m + 1) / 2 + q * Lh - q * (q - 1) / 2;
+  return off + p - a;
+}
+// Whether the FP32 window of band limit Lh is stored order-major.
+__host__ __device__ __forceinline__ bool h_order_major(int Lh) { return Lh > 16; }
 // Elements of the tiled H for J columns.
 __host__ __device__ __forceinline__ size_t h_elems(size_t J, int n2) { return (J + 127) / 128 * 128 * (size_t)n2; }
 

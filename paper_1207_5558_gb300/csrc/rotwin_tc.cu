@@ -436,7 +436,7 @@ k_rotwin_tc(const unsigned char* __restrict__ img, const float* __restrict__ rs,
         const int bb = R / w;
         rsc[ps] = __ldg(rs + (size_t)t * RT_ROWS + n);
         rb[ps] = bb;
-        roff[ps] = (p * p + R - bb * w) * 128;
+        roff[ps] = h_row(p, R - bb * w - p, Lh, h_order_major(Lh)) * 128;
       }
       const int acc = i & 1;
       // one lane waits, the warp follows: tcgen05.ld needs a converged warp

@@ -171,10 +171,11 @@ __device__ __forceinline__ void rotwin_block_smem_to(const double2* __restrict__
       const int bi = r / w, qi = r - bi * w;
       const int jb = (b0 + bi) * Ng + c0;
       const T sg = (qi & 1) ? (T)-1 : (T)1;             // (-1)^{q+p}
+      const int hr = h_row(p, qi - p, Lh, sizeof(T) == 4 && h_order_major(Lh));
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const int c = cg + 8 * k;
-        if (c < ncr) store(h_index(p * p + qi, jb + c, n2), sg * re[a][k], sg * im[a][k]);
+        if (c < ncr) store(h_index(hr, jb + c, n2), sg * re[a][k], sg * im[a][k]);
       }
     }
   }
