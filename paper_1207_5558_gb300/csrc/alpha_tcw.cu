@@ -134,23 +134,14 @@ cudaError_t launch_tcw_etab(void* etab, int Na, int Lh, cudaStream_t st) {
 
 // ---------------------------------------------------------------- A operand from H
 // Two passes.  k_xw_tc (below): X_q(j) = sum_{p>=|q|} k(p,q) H^p_q(j) for a
-// group of up to XA_MAXP pairs, per (128-column tile, order q).  X goes to
-// the pair's FP32 region, and 2 max(|Re X|, |Im X|), a bound of every slot built
-// from the column's X (|Re P_r| <= |Re X_r| + |Re X_-r|, ...) and at most
-// twice the largest one (X_r = (P_r + M_r) / 2), raises the column's entry in
-// the pair's scale array (atomicMax on the float bits, entries >= 0).
-// k_xaw_split: one thread per (pair, column, 8 orders r): scale 2^e from
-// that bound into [2^13, 2^15), P_r = X_r + X_-r, M_r = X_r - X_-r (P_0 = X_0,
-// M_0 = 0), every slot scaled, split into FP16 hi/lo and stored swizzled into
-// its K-chunk (A_re[r] = Re P_r, A_re[KP + r] = Im M_r, A_im[r] = Im P_r,
-// A_im[KP + r] = -Re M_r; zero for r >= L_h).  Columns beyond J are zero.
-
-// The column maxima of every pair cleared (before k_xw_tc raises them).
-__global__ void k_xw_clear(int n, int ng, unsigned char* __restrict__ xblob, size_t blob_stride, size_t sc_off) {
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < (long long)n * ng;
-       t += (long long)gridDim.x * blockDim.x)
-    reinterpret_cast<int*>(xblob + (size_t)(t / n) * blob_stride + sc_off)[t % n] = 0;
-}
+// group of up to XA_MAXP pairs, per (order q, 128-column tile), into the
+// pair's FP32 region.  k_xaw_split: one thread per (pair, column, 8 orders
+// r): P_r = X_r + X_-r, M_r = X_r - X_-r (P_0 = X_0, M_0 = 0), the column's
+// largest slot (a shuffle over the lanes of the column) sets its scale 2^e
+// into [2^14, 2^15), every slot scaled, split into FP16 hi/lo and stored
+// swizzled into its K-chunk (A_re[r] = Re P_r, A_re[KP + r] = Im M_r,
+// A_im[r] = Im P_r, A_im[KP + r] = -Re M_r; zero for r >= L_h), and 2^-e goes
+// to the pair's scale array.  Columns beyond J are zero.
 
 // FP16 hi and lo of 8 scaled values as two 16-byte units
 __device__ __forceinline__ void xw_split8(const float* x, float sc, uint4* hi, uint4* lo) {
@@ -183,11 +174,6 @@ __global__ void __launch_bounds__(256) k_xaw_split(int Lh, int J, int nkf, unsig
   // X_q of the column at x0[q * 128], q = -(Lh-1) .. Lh-1
   const float2* x0 = reinterpret_cast<const float2*>(blob + xf_off) + ((size_t)tile * K + (Lh - 1)) * TC_M + row;
   float* scales = reinterpret_cast<float*>(blob + (size_t)tiles * 2 * nkf * TC_A_BYTES);
-  const float mx = j < J ? scales[j] : 0.f;          // the column's slot bound (k_xw_tc)
-  int ex = 0;
-  if (mx > 0.f) frexpf(mx, &ex);
-  const int e = mx > 0.f ? min(125, max(-125, 15 - ex)) : 0;
-  const float sc = __int_as_float((127 + e) << 23);
   float a[4][8];                                     // Re P, Im P, Im M, -Re M of the group's 8 orders
 #pragma unroll
   for (int w = 0; w < 8; ++w) {
@@ -201,6 +187,17 @@ __global__ void __launch_bounds__(256) k_xaw_split(int Lh, int J, int nkf, unsig
     a[2][w] = z ? 0.f : xp.y - xm.y;
     a[3][w] = z ? 0.f : -(xp.x - xm.x);
   }
+  float mx = 0.f;                                    // the column's largest slot: its nrg lanes together
+#pragma unroll
+  for (int g = 0; g < 4; ++g)
+#pragma unroll
+    for (int w = 0; w < 8; ++w) mx = fmaxf(mx, fabsf(a[g][w]));
+  for (int o = nrg >> 1; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (j >= J) mx = 0.f;
+  int ex = 0;
+  if (mx > 0.f) frexpf(mx, &ex);
+  const int e = mx > 0.f ? min(125, max(-125, 15 - ex)) : 0;
+  const float sc = __int_as_float((127 + e) << 23);
   // A_re K-chunks, then A_im: (m * nkf + slot / 64) x 32 KB, hi then lo;
   // A_re P part (Re P), A_im P part (Im P), A_re M part (Im M), A_im M part (-Re M)
   unsigned char* ab = blob + (size_t)tile * 2 * nkf * TC_A_BYTES;
@@ -213,7 +210,6 @@ __global__ void __launch_bounds__(256) k_xaw_split(int Lh, int J, int nkf, unsig
     *reinterpret_cast<uint4*>(cb) = hi;
     *reinterpret_cast<uint4*>(cb + TC_A_HALF) = lo;
   }
-  __syncwarp();                                      // every lane has read the column's bound
   if (rg == 0) scales[j] = j < J ? __int_as_float((127 - e) << 23) : 0.f;
 }
 
@@ -306,25 +302,26 @@ __global__ void __launch_bounds__(256) k_xwb(int Lh, int npairs, unsigned char* 
 }
 
 #define XT_ROWB (TC_M * 8)              // one H row of a tile: 128 columns x float2
-#define XT_HSTAGE (XT_DEG * XT_ROWB)    // 32 KB of H rows
-#define XT_S (XT_HSTAGE + XT_BIMG)      // stage: the chunk's H rows, then its coupling image
-#define XT_NS 4
+#define XT_HSTAGE (XT_DEG * XT_ROWB)    // ring stage: a chunk's H rows, 32 KB
+#define XT_NS 4                         // H ring stages
 #define XT_NACC 2                       // TMEM accumulators
 #define XT_ACC (XT_MAXCH * 64)          // columns of one accumulator (64 a chunk)
+#define XT_NA 4                         // TMEM A stages, and the coupling image ring (same index)
 #define XT_ASTAGE 64                    // TMEM columns of one A stage
 #define XT_ACOL (XT_NACC * XT_ACC)      // first TMEM column of the A stages
 #ifndef XT_GROUPS
 #define XT_GROUPS 2                     // converter groups of 4 warps, taking the chunks in turn
 #endif
 #define XT_CONV (4 * XT_GROUPS)         // converter warps
-#define XT_META (XT_NS + XT_NACC + XT_GROUPS)   // per-item scale slots (reuse distance, see the converters)
-#define XT_EPI0 (2 + XT_CONV)           // first epilogue warp
-#define XT_THREADS (32 * (XT_EPI0 + 4)) // loader, MMA issuer, converters, 4 epilogue warps
+#define XT_META (XT_NA + XT_NACC + XT_GROUPS)   // per-item scale slots (reuse distance, see the converters)
+#define XT_EPI0 (3 + XT_CONV)           // first epilogue warp
+#define XT_THREADS (32 * (XT_EPI0 + 4)) // H loader, MMA issuer, image loader, converters, 4 epilogue warps
 #define XT_META_BYTES (XT_META * XT_MAXCH * TC_M * 4)
-#define XT_SMEM (XT_NS * XT_S + XT_META_BYTES + 1024 + 512)
+#define XT_SMEM (XT_NA * XT_BIMG + XT_NS * XT_HSTAGE + XT_META_BYTES + 1024 + 512)
 
 struct XtBars {
-  uint64_t full[XT_NS], free[XT_NS], ready[XT_NS], acc_full[XT_NACC], acc_empty[XT_NACC], meta_full[XT_META], drain;
+  uint64_t full[XT_NS], free[XT_NS], bfull[XT_NA], ready[XT_NA], afree[XT_NA], acc_full[XT_NACC],
+      acc_empty[XT_NACC], meta_full[XT_META], drain;
   uint32_t tmem_base;
   int abort_flag;
 };
@@ -368,12 +365,13 @@ __device__ inline int xt_first(long long x, int Lh, int ng, long long ctile) {
 
 __global__ void __launch_bounds__(XT_THREADS, 1)
 k_xw_tc(const float2* __restrict__ H, int Lh, int J, int tiles, int npairs, unsigned char* __restrict__ xblob,
-        size_t blob_stride, size_t kb_off, size_t xf_off, size_t sc_off, int* __restrict__ err) {
+        size_t blob_stride, size_t kb_off, size_t xf_off, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* ring = sm;                                       // XT_NS x (H rows, coupling image)
-  float* meta = reinterpret_cast<float*>(ring + XT_NS * XT_S);    // [XT_META][XT_MAXCH][128]
-  XtBars* bars = reinterpret_cast<XtBars*>(ring + XT_NS * XT_S + XT_META_BYTES);
+  unsigned char* bring = sm;                                      // XT_NA x a chunk's coupling image
+  unsigned char* ring = sm + XT_NA * XT_BIMG;                     // XT_NS x a chunk's H rows
+  float* meta = reinterpret_cast<float*>(ring + XT_NS * XT_HSTAGE);   // [XT_META][XT_MAXCH][128]
+  XtBars* bars = reinterpret_cast<XtBars*>(ring + XT_NS * XT_HSTAGE + XT_META_BYTES);
   volatile int* abort_flag = &bars->abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int K = 2 * Lh - 1, n2 = Lh * Lh;
@@ -390,10 +388,14 @@ k_xw_tc(const float2* __restrict__ H, int Lh, int J, int tiles, int npairs, unsi
   if (threadIdx.x == 0) {
     for (int i = 0; i < XT_NS; ++i) {
       mbar_init(smem_u32(&bars->full[i]), 1);
-      // the converter group's 4 warps (rows read) and the MMA commit (the
-      // coupling image and the TMEM A stage of the same index read)
-      mbar_init(smem_u32(&bars->free[i]), 5);
+      mbar_init(smem_u32(&bars->free[i]), 4);      // the converter group's 4 warps: rows read
+    }
+    for (int i = 0; i < XT_NA; ++i) {
+      mbar_init(smem_u32(&bars->bfull[i]), 1);
       mbar_init(smem_u32(&bars->ready[i]), 4);
+      // MMA commit: the products of the A stage and of the image slot of this
+      // index completed
+      mbar_init(smem_u32(&bars->afree[i]), 1);
     }
     for (int i = 0; i < XT_NACC; ++i) {
       mbar_init(smem_u32(&bars->acc_full[i]), 1);
@@ -415,9 +417,8 @@ k_xw_tc(const float2* __restrict__ H, int Lh, int J, int tiles, int npairs, unsi
   const uint32_t tmem = bars->tmem_base;
 
   if (warp == 0) {
-    // ---------------- loader: per chunk, its H rows (one contiguous run of the
-    // order-major tile, 1 KB a degree) and its coupling image, two bulk
-    // copies, once the stage's previous chunk is read and multiplied
+    // ---------------- H loader: per chunk its H rows (one contiguous run of the
+    // order-major tile, one bulk copy) into a ring stage the converters have read
     if (lane == 0) {
       int armed[XT_NS];
 #pragma unroll
@@ -433,11 +434,9 @@ k_xw_tc(const float2* __restrict__ H, int Lh, int J, int tiles, int npairs, unsi
           const uint32_t ph = (uint32_t)((bc / XT_NS) & 1);
           if (!(ok = mbar_wait_n(smem_u32(&bars->free[s]), ph ^ 1u, abort_flag, TC_WAIT_LIMIT))) break;
           const int rows = min(XT_DEG, P - c * XT_DEG);
-          unsigned char* stg = ring + (size_t)s * XT_S;
           const uint32_t fb = smem_u32(&bars->full[s]);
-          mbar_expect_tx(fb, (uint32_t)(rows * XT_ROWB + XT_BIMG));
-          bulk_g2s(smem_u32(stg), hb + (size_t)c * XT_DEG * XT_ROWB, (uint32_t)(rows * XT_ROWB), fb);
-          bulk_g2s(smem_u32(stg + XT_HSTAGE), kb + ((size_t)u * XT_MAXCH + c) * XT_BIMG, XT_BIMG, fb);
+          mbar_expect_tx(fb, (uint32_t)(rows * XT_ROWB));
+          bulk_g2s(smem_u32(ring + (size_t)s * XT_HSTAGE), hb + (size_t)c * XT_DEG * XT_ROWB, (uint32_t)(rows * XT_ROWB), fb);
 #pragma unroll
           for (int i = 0; i < XT_NS; ++i)
             if (i == s) armed[i] = (int)ph;
@@ -452,15 +451,48 @@ k_xw_tc(const float2* __restrict__ H, int Lh, int J, int tiles, int npairs, unsi
         }
       }
     }
+  } else if (warp == 2) {
+    // ---------------- image loader: per chunk its coupling image into the slot
+    // of its A stage index, once that slot's previous products have completed
+    if (lane == 0) {
+      int armed[XT_NA];
+#pragma unroll
+      for (int i = 0; i < XT_NA; ++i) armed[i] = -1;
+      long long bc = 0;
+      bool ok = true;
+      for (int t = i0; t < i1 && ok; ++t) {
+        const int u = t % K, q = u - (Lh - 1), P = Lh - (q < 0 ? -q : q);
+        for (int c = 0; c * XT_DEG < P; ++c, ++bc) {
+          const int s = (int)(bc % XT_NA);
+          const uint32_t ph = (uint32_t)((bc / XT_NA) & 1);
+          if (!(ok = mbar_wait_n(smem_u32(&bars->afree[s]), ph ^ 1u, abort_flag, TC_WAIT_LIMIT))) break;
+          const uint32_t fb = smem_u32(&bars->bfull[s]);
+          mbar_expect_tx(fb, XT_BIMG);
+          bulk_g2s(smem_u32(bring + (size_t)s * XT_BIMG), kb + ((size_t)u * XT_MAXCH + c) * XT_BIMG, XT_BIMG, fb);
+#pragma unroll
+          for (int i = 0; i < XT_NA; ++i)
+            if (i == s) armed[i] = (int)ph;
+        }
+      }
+      if (!ok) *abort_flag = 1;
+#pragma unroll
+      for (int i = 0; i < XT_NA; ++i) {
+        if (armed[i] >= 0) {
+          uint32_t n = 0;
+          while (!mbar_test(smem_u32(&bars->bfull[i]), (uint32_t)armed[i]) && ++n < TC_WAIT_LIMIT) {}
+        }
+      }
+    }
   } else if (warp == 1) {
     // ---------------- MMA issuer: per chunk c of item i, one N = 64 product per
-    // live K = 16 slice of the TMEM A stage and the staged coupling image,
-    // into accumulator i % XT_NACC, columns 64 c ..; one commit frees the stage
+    // live K = 16 slice of the TMEM A stage and the chunk's coupling image,
+    // into accumulator i % XT_NACC, columns 64 c ..; one commit a chunk frees
+    // the A stage and the image slot
     if (lane == 0) {
       const uint32_t idesc = umma_idesc_f16(128, 64);
       long long bc = 0;
-      bool ok = true;
       int li = 0;
+      bool ok = true;
       for (int t = i0; t < i1 && ok; ++t, ++li) {
         const int u = t % K, q = u - (Lh - 1), P = Lh - (q < 0 ? -q : q);
         const int a = li % XT_NACC;
@@ -469,20 +501,19 @@ k_xw_tc(const float2* __restrict__ H, int Lh, int J, int tiles, int npairs, unsi
           break;
         tc_fence_after();
         for (int c = 0; c * XT_DEG < P; ++c, ++bc) {
-          const int s = (int)(bc % XT_NS);
-          const uint32_t ph = (uint32_t)((bc / XT_NS) & 1);
-          // the coupling image landed, and the converters filled the A stage
-          if (!(ok = mbar_wait_n(smem_u32(&bars->full[s]), ph, abort_flag, TC_WAIT_LIMIT))) break;
-          if (!(ok = mbar_wait_n(smem_u32(&bars->ready[s]), ph, abort_flag, TC_WAIT_LIMIT))) break;
+          const int sa = (int)(bc % XT_NA);
+          const uint32_t ph = (uint32_t)((bc / XT_NA) & 1);
+          if (!(ok = mbar_wait_n(smem_u32(&bars->bfull[sa]), ph, abort_flag, TC_WAIT_LIMIT))) break;
+          if (!(ok = mbar_wait_n(smem_u32(&bars->ready[sa]), ph, abort_flag, TC_WAIT_LIMIT))) break;
           tc_fence_after();
           const int nst = P - c * XT_DEG > 16 ? 8 : 4;   // slices of the live degree halves
-          const uint32_t at = tmem + (uint32_t)(XT_ACOL + s * XT_ASTAGE);
-          const uint32_t bb = smem_u32(ring + (size_t)s * XT_S + XT_HSTAGE);
+          const uint32_t at = tmem + (uint32_t)(XT_ACOL + sa * XT_ASTAGE);
+          const uint32_t bb = smem_u32(bring + (size_t)sa * XT_BIMG);
           const uint32_t d = tmem + (uint32_t)(a * XT_ACC + c * 64);
           for (int st = 0; st < nst; ++st)
             umma_f16_ta(d, at + (uint32_t)(8 * st), sw128_desc(bb + (uint32_t)((st >> 2) * XT_BATOM)) + (uint64_t)(2 * (st & 3)),
                         idesc, st > 0 ? 1u : 0u);
-          umma_commit(smem_u32(&bars->free[s]));
+          umma_commit(smem_u32(&bars->afree[sa]));
         }
         if (!ok) break;
         umma_commit(smem_u32(&bars->acc_full[a]));
@@ -497,22 +528,21 @@ k_xw_tc(const float2* __restrict__ H, int Lh, int J, int tiles, int npairs, unsi
     // chunks in turn, thread = column of the tile = TMEM lane (warp % 4
     // picks the lane quadrant).  Per chunk: the column's largest |value|
     // over the staged rows (zero past the order's degrees and past column
-    // J), its scale, then per live half of the degrees the split A row into
-    // the stage's TMEM columns, and the inverse scale into the item's meta
-    // slot.  The stage's TMEM columns are free once its rows have landed: the
-    // loader refilled the stage only after the products of its previous
-    // chunk had completed.  Slot li % XT_META is written after that wait, so
-    // the products of the chunk XT_NS earlier have completed; its item is at
-    // most XT_NS items back and was issued only after the epilogue had
-    // released item li - XT_NS - XT_NACC, so the epilogue has read that
-    // slot's previous item.  Every converter warp arrives on the item's meta
-    // barrier, also when its group had none of the item's chunks: a warp
-    // arriving for item li has passed the stage wait of one of its chunks in
-    // the XT_GROUPS items before, so the epilogue has released item
-    // li - XT_GROUPS - XT_NS - XT_NACC, and XT_GROUPS more slots of distance
+    // J) and its scale; once the A stage's previous products have completed,
+    // per live half of the degrees the split A row into the stage's TMEM
+    // columns; then the ring stage is released and the inverse scale goes to
+    // the item's meta slot.  Slot li % XT_META is written after the A stage
+    // wait, so the products of the chunk XT_NA earlier have completed; its
+    // item is at most XT_NA items back and was issued only after the
+    // epilogue had released item li - XT_NA - XT_NACC, so the epilogue has
+    // read that slot's previous item.  Every converter warp arrives on the
+    // item's meta barrier, also when its group had none of the item's chunks:
+    // a warp arriving for item li has passed the A stage wait of one of its
+    // chunks in the XT_GROUPS items before, so the epilogue has released item
+    // li - XT_GROUPS - XT_NA - XT_NACC, and XT_GROUPS more slots of distance
     // keep the warp from completing a slot's next phase before the epilogue
     // has waited on the current one.
-    const int grp = (warp - 2) >> 2, quad = warp & 3, col = quad * 32 + lane;
+    const int grp = (warp - 3) >> 2, quad = warp & 3, col = quad * 32 + lane;
     const uint32_t tl = (uint32_t)(quad * 32) << 16;
     long long bc = 0;
     bool ok = true;
@@ -523,13 +553,12 @@ k_xw_tc(const float2* __restrict__ H, int Lh, int J, int tiles, int npairs, unsi
       const int ms = li % XT_META;
       for (int c = 0; c * XT_DEG < P; ++c, ++bc) {
         if ((int)(bc % XT_GROUPS) != grp) continue;
-        const int s = (int)(bc % XT_NS);
+        const int s = (int)(bc % XT_NS), sa = (int)(bc % XT_NA);
         int got = 0;
         if (lane == 0) got = mbar_wait_n(smem_u32(&bars->full[s]), (uint32_t)((bc / XT_NS) & 1), abort_flag, TC_WAIT_LIMIT);
         got = __shfl_sync(0xffffffffu, got, 0);
         if (!(ok = got != 0)) break;
-        tc_fence_after();
-        const float2* hs = reinterpret_cast<const float2*>(ring + (size_t)s * XT_S) + col;
+        const float2* hs = reinterpret_cast<const float2*>(ring + (size_t)s * XT_HSTAGE) + col;
         const int rows = live ? min(XT_DEG, P - c * XT_DEG) : 0;
         float mx = 0.f;
         for (int i = 0; i < rows; ++i) {
@@ -540,6 +569,11 @@ k_xw_tc(const float2* __restrict__ H, int Lh, int J, int tiles, int npairs, unsi
         if (mx > 0.f) frexpf(mx, &ex);
         const int es = mx > 0.f ? min(125, max(-125, 15 - ex)) : 0;
         const float sc = __int_as_float((127 + es) << 23);
+        if (lane == 0)
+          got = mbar_wait_n(smem_u32(&bars->afree[sa]), (uint32_t)(((bc / XT_NA) & 1) ^ 1), abort_flag, TC_WAIT_LIMIT);
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if (!(ok = got != 0)) break;
+        tc_fence_after();
         const int nh = P - c * XT_DEG > 16 ? 2 : 1;   // live degree halves (warp-uniform)
         for (int h = 0; h < nh; ++h) {
           uint32_t w[32];   // Re hi, Im hi, Re lo, Im lo: 8 columns each, two FP16 a column
@@ -552,7 +586,7 @@ k_xw_tc(const float2* __restrict__ H, int Lh, int J, int tiles, int npairs, unsi
             w[e] = xt_split2(a.x * sc, b.x * sc, &w[16 + e]);
             w[8 + e] = xt_split2(a.y * sc, b.y * sc, &w[24 + e]);
           }
-          tmem_st32(tmem + tl + (uint32_t)(XT_ACOL + s * XT_ASTAGE + 32 * h), w);
+          tmem_st32(tmem + tl + (uint32_t)(XT_ACOL + sa * XT_ASTAGE + 32 * h), w);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&bars->free[s]));   // the rows are read
@@ -560,7 +594,7 @@ k_xw_tc(const float2* __restrict__ H, int Lh, int J, int tiles, int npairs, unsi
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&bars->ready[s]));
+        if (lane == 0) mbar_arrive(smem_u32(&bars->ready[sa]));
       }
       if (!ok) break;
       __syncwarp();
@@ -569,32 +603,13 @@ k_xw_tc(const float2* __restrict__ H, int Lh, int J, int tiles, int npairs, unsi
     if (!ok) *abort_flag = 1;
   } else {
     // ---------------- epilogue: the last four warps, TMEM lane quadrant warp % 4 =
-    // the tile's columns; X of the group's pairs (the sum of each chunk's hi
-    // and lo column halves, both scales undone), and each column's running
-    // slot bound over the tile's orders, raised once per tile
+    // the tile's columns; X of the group's pairs: the sum of each chunk's hi
+    // and lo column halves, both scales undone
     const int quad = warp & 3, row = quad * 32 + lane;
-    float bmax[XA_MAXP];
-#pragma unroll
-    for (int v = 0; v < XA_MAXP; ++v) bmax[v] = 0.f;
-    int cur = -1;
     bool ok = true;
     int li = 0;
-    for (int t = i0; t <= i1 && ok; ++t, ++li) {
-      const int tile = t / K;
-      if (tile != cur || t == i1) {   // the finished tile's bounds
-        const int jc = cur * TC_M + row;
-        if (cur >= 0 && jc < J) {
-#pragma unroll
-          for (int v = 0; v < XA_MAXP; ++v)
-            if (v < ng)
-              atomicMax(reinterpret_cast<int*>(xblob + (size_t)v * blob_stride + sc_off) + jc, __float_as_int(bmax[v]));
-        }
-#pragma unroll
-        for (int v = 0; v < XA_MAXP; ++v) bmax[v] = 0.f;
-        cur = tile;
-      }
-      if (t == i1) break;
-      const int u = t - tile * K, q = u - (Lh - 1), P = Lh - (q < 0 ? -q : q);
+    for (int t = i0; t < i1 && ok; ++t, ++li) {
+      const int tile = t / K, u = t - tile * K, q = u - (Lh - 1), P = Lh - (q < 0 ? -q : q);
       const int a = li % XT_NACC, ms = li % XT_META;
       int got = 0;
       if (lane == 0)
@@ -628,10 +643,7 @@ k_xw_tc(const float2* __restrict__ H, int Lh, int J, int tiles, int npairs, unsi
       const size_t xo = xf_off + (((size_t)tile * K + u) * TC_M + row) * sizeof(float2);
 #pragma unroll
       for (int v = 0; v < XA_MAXP; ++v)
-        if (v < ng) {
-          *reinterpret_cast<float2*>(xblob + (size_t)v * blob_stride + xo) = make_float2(x[v], x[16 + v]);
-          bmax[v] = fmaxf(bmax[v], 2.f * fmaxf(fabsf(x[v]), fabsf(x[16 + v])));
-        }
+        if (v < ng) *reinterpret_cast<float2*>(xblob + (size_t)v * blob_stride + xo) = make_float2(x[v], x[16 + v]);
     }
     if (!ok) *abort_flag = 1;
   }
@@ -654,13 +666,9 @@ cudaError_t launch_xaw_from_h(const double2* kc, const float2* H, int Lh, int Nb
   const size_t xf_off = kb_off + tcw_kb_bytes(Lh);
   unsigned char* xb = (unsigned char*)xblob;
   // first pass, every group of up to XA_MAXP pairs in one launch: X in FP32
-  // and the columns' slot bounds
   const int groups = (npairs + XA_MAXP - 1) / XA_MAXP;
   if (groups > 65535) return cudaErrorInvalidValue;
   k_kf_from_kc<<<dim3((n2 * XA_MAXP + 255) / 256, groups), 256, 0, st>>>(kc, n2, npairs, xb, stride, kf_off);
-  const int n = tiles * TC_M;
-  k_xw_clear<<<(unsigned)std::min<long long>(((long long)n * npairs + 255) / 256, 8192), 256, 0, st>>>(n, npairs, xb,
-                                                                                                     stride, sc_off);
   static bool attr = false;
   static int nsm = 0;
   if (!attr) {
@@ -678,7 +686,7 @@ cudaError_t launch_xaw_from_h(const double2* kc, const float2* H, int Lh, int Nb
   const long long items = (long long)tiles * (2 * Lh - 1);
   const int gx = (int)std::min<long long>(items, nsm);
   k_xw_tc<<<dim3(gx, groups), XT_THREADS, XT_SMEM, st>>>(H, Lh, Nb * Ng, tiles, npairs, xb, stride, kb_off, xf_off,
-                                                         sc_off, err);
+                                                         err);
   // second pass: scales and the split A operands
   const int cols_per_block = 8 * (32 / (4 * nkf));   // 8 warps of 32 / (KP / 8) columns
   k_xaw_split<<<dim3((tiles * TC_M + cols_per_block - 1) / cols_per_block, npairs), 256, 0, st>>>(
@@ -947,5 +955,5 @@ cudaError_t launch_alpha_tcw(const void* xblob, const void* etab, int Lh, int Na
 }
 
 static_assert(sizeof(XtBars) <= 512, "the first pass's bookkeeping fits the space XT_SMEM keeps for it");
-static_assert(XT_ACOL + XT_NS * XT_ASTAGE <= 512, "the first pass's accumulators and A stages fit TMEM");
+static_assert(XT_ACOL + XT_NA * XT_ASTAGE <= 512, "the first pass's accumulators and A stages fit TMEM");
 static_assert(XT_SMEM <= 232448, "one CTA's shared memory");
