@@ -71,10 +71,17 @@ static inline size_t tcw_kb_bytes(int Lh) {
   return n * XT_BIMG + (n * sizeof(float) + 1023) / 1024 * 1024;
 }
 static inline size_t tcw_xf_bytes(size_t tiles, int Lh) { return tiles * (size_t)(2 * Lh - 1) * TC_M * sizeof(float2); }
+// The first pass runs on the tensor cores (k_xw_tc, persistent) when the
+// grid gives its CTAs at least 32 (tile, order) items each on 152 SMs;
+// below that the pipeline's start-up outweighs its rate and the CUDA-core
+// first pass (k_xw_x, one block per item) is faster.  Only then does a blob
+// hold the coupling images.
+#define XT_MIN_ITEMS (32 * 152)
+static inline bool xt_use_tc(long long tiles, int Lh) { return tiles * (2 * Lh - 1) >= XT_MIN_ITEMS; }
 size_t tcw_xblob_bytes(int Nb, int Ng, int Lh) {
   const size_t t = (size_t)tcw_tiles(Nb, Ng);
-  return t * (size_t)tcw_nk(Lh) * TC_A_BYTES + tcw_scales_bytes(t) + tcw_kf_bytes(Lh) + tcw_kb_bytes(Lh) +
-         tcw_xf_bytes(t, Lh);
+  return t * (size_t)tcw_nk(Lh) * TC_A_BYTES + tcw_scales_bytes(t) + tcw_kf_bytes(Lh) +
+         (xt_use_tc((long long)t, Lh) ? tcw_kb_bytes(Lh) : 0) + tcw_xf_bytes(t, Lh);
 }
 
 // The coupling rows of a group of up to XA_MAXP pairs as floats: one
@@ -133,15 +140,75 @@ cudaError_t launch_tcw_etab(void* etab, int Na, int Lh, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------- A operand from H
-// Two passes.  k_xw_tc (below): X_q(j) = sum_{p>=|q|} k(p,q) H^p_q(j) for a
-// group of up to XA_MAXP pairs, per (order q, 128-column tile), into the
-// pair's FP32 region.  k_xaw_split: one thread per (pair, column, 8 orders
+// Two passes.  The first: X_q(j) = sum_{p>=|q|} k(p,q) H^p_q(j) for a group
+// of up to XA_MAXP pairs, per (128-column tile, order q), into the pair's
+// FP32 region, by k_xw_tc (below) on large grids and by k_xw_x on small ones.  k_xaw_split: one thread per (pair, column, 8 orders
 // r): P_r = X_r + X_-r, M_r = X_r - X_-r (P_0 = X_0, M_0 = 0), the column's
 // largest slot (a shuffle over the lanes of the column) sets its scale 2^e
 // into [2^14, 2^15), every slot scaled, split into FP16 hi/lo and stored
 // swizzled into its K-chunk (A_re[r] = Re P_r, A_re[KP + r] = Im M_r,
 // A_im[r] = Im P_r, A_im[KP + r] = -Re M_r; zero for r >= L_h), and 2^-e goes
 // to the pair's scale array.  Columns beyond J are zero.
+
+// k_xw_x: one block per (128-column tile, order q), one thread per column;
+// the thread keeps its column's sums for every pair of the group in
+// registers, so each H value (one coalesced row per degree; the order's rows
+// are one run of the order-major tile) feeds 4 NP multiply-adds, with the
+// group's k(., q) in shared memory (broadcast reads) and the next four
+// degrees' H loads issued before the current four are used.
+template <int NP>
+__device__ __forceinline__ void xw_mac(const float2 (*sk)[NP], int i, float2 h, float* ar, float* ai) {
+#pragma unroll
+  for (int v = 0; v < NP; ++v) {
+    const float2 kv = sk[i][v];
+    ar[v] = fmaf(kv.x, h.x, ar[v]); ar[v] = fmaf(-kv.y, h.y, ar[v]);
+    ai[v] = fmaf(kv.x, h.y, ai[v]); ai[v] = fmaf(kv.y, h.x, ai[v]);
+  }
+}
+
+template <int NP>
+__global__ void __launch_bounds__(TC_M) k_xw_x(const float2* __restrict__ H, int Lh, int J, int npairs,
+                                               unsigned char* __restrict__ xblob, size_t blob_stride, size_t kf_off,
+                                               size_t xf_off) {
+  __shared__ float2 sk[64][NP];                     // k(p, q) of the group, p = |q| + row
+  // group blockIdx.z: pairs g0 .. g0 + ng - 1 (blobs from g0), couplings in g0's blob
+  const int g0 = blockIdx.z * XA_MAXP, ng = min(NP, npairs - g0);
+  xblob += (size_t)g0 * blob_stride;
+  const float2* kf = reinterpret_cast<const float2*>(xblob + kf_off);
+  const int tile = blockIdx.x, u = blockIdx.y, q = u - (Lh - 1), aq = q < 0 ? -q : q;
+  const int n2 = Lh * Lh, P = Lh - aq, K = 2 * Lh - 1;
+  for (int t = threadIdx.x; t < P * NP; t += TC_M) {
+    const int i = t / NP, v = t % NP, pd = aq + i;
+    sk[i][v] = kf[(size_t)(pd * pd + pd + q) * XA_MAXP + v];
+  }
+  __syncthreads();
+  const int col = threadIdx.x, j = tile * TC_M + col;
+  float ar[NP], ai[NP];
+#pragma unroll
+  for (int v = 0; v < NP; ++v) ar[v] = ai[v] = 0.f;
+  if (j < J) {                                       // H past column J is never written
+    // degree aq + i of order q at hp + i * 128
+    const float2* hp = H + ((size_t)tile * n2 + h_row(aq, q, Lh, true)) * TC_M + col;
+    float2 cur[4], nxt[4];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) cur[w] = w < P ? __ldg(hp + (size_t)w * TC_M) : make_float2(0.f, 0.f);
+    for (int i = 0; i < P; i += 4) {
+#pragma unroll
+      for (int w = 0; w < 4; ++w)                    // the next four degrees, in flight meanwhile
+        nxt[w] = i + 4 + w < P ? __ldg(hp + (size_t)(i + 4 + w) * TC_M) : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int w = 0; w < 4; ++w)
+        if (i + w < P) xw_mac<NP>(sk, i + w, cur[w], ar, ai);
+#pragma unroll
+      for (int w = 0; w < 4; ++w) cur[w] = nxt[w];
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < NP; ++v)
+    if (v < ng)
+      reinterpret_cast<float2*>(xblob + (size_t)v * blob_stride + xf_off)[((size_t)tile * K + u) * TC_M + col] =
+          make_float2(ar[v], ai[v]);
+}
 
 // FP16 hi and lo of 8 scaled values as two 16-byte units
 __device__ __forceinline__ void xw_split8(const float* x, float sc, uint4* hi, uint4* lo) {
@@ -663,30 +730,40 @@ cudaError_t launch_xaw_from_h(const double2* kc, const float2* H, int Lh, int Nb
   const size_t sc_off = (size_t)tiles * 2 * nkf * TC_A_BYTES;
   const size_t kf_off = sc_off + tcw_scales_bytes(tiles);
   const size_t kb_off = kf_off + tcw_kf_bytes(Lh);
-  const size_t xf_off = kb_off + tcw_kb_bytes(Lh);
+  const size_t xf_off = kb_off + (xt_use_tc(tiles, Lh) ? tcw_kb_bytes(Lh) : 0);
   unsigned char* xb = (unsigned char*)xblob;
   // first pass, every group of up to XA_MAXP pairs in one launch: X in FP32
   const int groups = (npairs + XA_MAXP - 1) / XA_MAXP;
   if (groups > 65535) return cudaErrorInvalidValue;
   k_kf_from_kc<<<dim3((n2 * XA_MAXP + 255) / 256, groups), 256, 0, st>>>(kc, n2, npairs, xb, stride, kf_off);
-  static bool attr = false;
-  static int nsm = 0;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_xw_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, XT_SMEM);
-    if (e != cudaSuccess) return e;
-    int dev = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    attr = true;
+  if (!xt_use_tc(tiles, Lh)) {
+    const dim3 grid(tiles, 2 * Lh - 1, groups);
+    if (npairs <= 4)
+      k_xw_x<4><<<grid, TC_M, 0, st>>>(H, Lh, Nb * Ng, npairs, xb, stride, kf_off, xf_off);
+    else if (npairs <= 8)
+      k_xw_x<8><<<grid, TC_M, 0, st>>>(H, Lh, Nb * Ng, npairs, xb, stride, kf_off, xf_off);
+    else
+      k_xw_x<16><<<grid, TC_M, 0, st>>>(H, Lh, Nb * Ng, npairs, xb, stride, kf_off, xf_off);
+  } else {
+    static bool attr = false;
+    static int nsm = 0;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(k_xw_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, XT_SMEM);
+      if (e != cudaSuccess) return e;
+      int dev = 0;
+      if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+      if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+      attr = true;
+    }
+    int* err = tc_error_word();
+    if (!err) return cudaErrorMemoryAllocation;
+    k_xwb<<<dim3(2 * Lh - 1, XT_MAXCH, groups), 256, 0, st>>>(Lh, npairs, xb, stride, kf_off, kb_off);
+    // persistent: one CTA per SM per group, each over a contiguous item range
+    const long long items = (long long)tiles * (2 * Lh - 1);
+    const int gx = (int)std::min<long long>(items, nsm);
+    k_xw_tc<<<dim3(gx, groups), XT_THREADS, XT_SMEM, st>>>(H, Lh, Nb * Ng, tiles, npairs, xb, stride, kb_off, xf_off,
+                                                           err);
   }
-  int* err = tc_error_word();
-  if (!err) return cudaErrorMemoryAllocation;
-  k_xwb<<<dim3(2 * Lh - 1, XT_MAXCH, groups), 256, 0, st>>>(Lh, npairs, xb, stride, kf_off, kb_off);
-  // persistent: one CTA per SM per group, each over a contiguous item range
-  const long long items = (long long)tiles * (2 * Lh - 1);
-  const int gx = (int)std::min<long long>(items, nsm);
-  k_xw_tc<<<dim3(gx, groups), XT_THREADS, XT_SMEM, st>>>(H, Lh, Nb * Ng, tiles, npairs, xb, stride, kb_off, xf_off,
-                                                         err);
   // second pass: scales and the split A operands
   const int cols_per_block = 8 * (32 / (4 * nkf));   // 8 warps of 32 / (KP / 8) columns
   k_xaw_split<<<dim3((tiles * TC_M + cols_per_block - 1) / cols_per_block, npairs), 256, 0, st>>>(

@@ -130,6 +130,8 @@ def test_steer_gamma_from_basis_orientations(ctx, prec, N):
     (64, (129, 7, 65), 2),           # few beta rows: tiles that span several betas; rounding-level orders
     (20, (41, 1, 1), 0),             # one beta row, one gamma sample: a tile per degree, most rows padding
     (17, (35, 3, 2), 0),             # the smallest window on the default path (L_h > 16), two gamma samples
+    (64, (9, 40, 128), 0),           # 40 tiles x 127 orders: the wide producer's first pass on the tensor cores
+    (24, (9, 104, 128), 1),          # the same at L_h = 24 (one 32-degree chunk an order), steerable window
 ])
 def test_rotated_window_on_tensor_cores(ctx, Lh, grid, orders):
     """The rotated window on the tensor cores (SLSHT_OPT_ROTWIN_ENGINE = 2,
@@ -140,8 +142,8 @@ def test_rotated_window_on_tensor_cores(ctx, Lh, grid, orders):
     f = synth.signal_powerlaw(Lf, 330 + Lh)
     h = steerable_window(Lh, 4, 331) if orders else synth.window_cn(Lh, 331, decay=1.0)
     pairs = synth.pairs_bands([0, 5, 11, Lf + Lh - 2])
-    if Lh > 40:
-        pairs = pairs[::9]                         # keeps the oracle to seconds at L_h = 64
+    if Lh > 40 or grid[1] * grid[2] > 8000:
+        pairs = pairs[::9]                         # keeps the oracle to seconds at L_h = 64 and on large grids
     ctx.set_option(pkg.SLSHT_OPT_WINDOW_ORDERS, orders)
     try:
         ctx.set_option(pkg.SLSHT_OPT_ROTWIN_ENGINE, 1)
