@@ -18,11 +18,12 @@
 // per-column power-of-two scale that puts its largest entry in [2^14, 2^15))
 // and D = A_hi B_hi + A_hi B_lo + A_lo B_hi accumulates in FP32.
 //
-// The producer (two passes: k_xw_tc forms X in FP32 for a group of up to 16
-// pairs from the rotated window H on the tensor cores, with each column's
-// slot bound; k_xaw_split folds X into P and M, scales, splits and writes the
-// swizzled A operand -- A_re and A_im, NKF K-chunks of 32 KB each -- and the
-// column scales to a blob in global memory); k_alpha_tcw
+// The producer (two passes: k_xw_tc on the tensor cores, or k_xw_x on the
+// CUDA cores for small grids, forms X in FP32 for a group of up to 16 pairs
+// from the rotated window H; k_xaw_split folds X into P and M, scales each
+// column by its largest slot, splits and writes the swizzled A operand --
+// A_re and A_im, NKF K-chunks of 32 KB each -- and the column scales to a
+// blob in global memory); k_alpha_tcw
 // (persistent, one CTA per SM, work item = (pair, tile)) keeps the item's
 // whole A operand in shared memory, streams the E-table K-chunks (32 KB each)
 // through a ring of 3 or 4 stages with cp.async.bulk, issues the MMAs from
