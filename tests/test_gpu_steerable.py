@@ -130,7 +130,7 @@ def test_steer_gamma_from_basis_orientations(ctx, prec, N):
     (64, (129, 7, 65), 2),           # few beta rows: tiles that span several betas; rounding-level orders
     (20, (41, 1, 1), 0),             # one beta row, one gamma sample: a tile per degree, most rows padding
     (17, (35, 3, 2), 0),             # the smallest window on the default path (L_h > 16), two gamma samples
-    (64, (9, 40, 128), 0),           # 40 tiles x 127 orders: the wide producer's first pass on the tensor cores
+    (64, (9, 41, 127), 0),           # 41 tiles x 127 orders: the wide producer's first pass on the tensor cores, ragged last tile
     (24, (9, 104, 128), 1),          # the same at L_h = 24 (one 32-degree chunk an order), steerable window
 ])
 def test_rotated_window_on_tensor_cores(ctx, Lh, grid, orders):
