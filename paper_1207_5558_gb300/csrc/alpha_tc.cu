@@ -51,7 +51,6 @@ size_t tc_xblob_bytes(int Nb, int Ng, int Lh) {
 // a = c*64+n (cos at k = 15+q | sin at k = 47+q), rows 64+n -> (-sin | cos); zeros
 // beyond Na and for |q| >= Lh.
 __global__ void k_tc_etab(unsigned char* __restrict__ etab, int Na, int Lh) {
-  const int K = 2 * Lh - 1;
   const int c = blockIdx.x;
   unsigned char* base = etab + (size_t)c * TC_B_BYTES;
   for (int t = threadIdx.x; t < TC_N * TC_KB; t += blockDim.x) {
@@ -139,7 +138,6 @@ k_betagamma_tc(const double2* __restrict__ kc, const double2* __restrict__ h, co
   // ---- G for the CTA's beta rows, folded into Gp / Gm
   for (int t = threadIdx.x; t < K * Lh; t += blockDim.x) {
     const int qi = t / Lh, s = t % Lh;
-    const int q = qi - (Lh - 1);
     float pr[TC_NBB], pi[TC_NBB], mr[TC_NBB], mi[TC_NBB];
 #pragma unroll
     for (int u = 0; u < TC_NBB; ++u) pr[u] = pi[u] = mr[u] = mi[u] = 0.f;
